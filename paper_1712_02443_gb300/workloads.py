@@ -1,0 +1,259 @@
+"""Seeded synthetic workloads: meshes, array layouts, incidence angles, test vectors.
+
+This module holds geometry and random numbers only, none of the method's
+arithmetic (no basis functions, integrals, grids or operators).  Both the
+CPU oracle and the CUDA library consume what it produces, so it is the one
+module they share.
+
+Units: lengths in wavelengths (lambda = 1, k0 = 2*pi).
+
+Workloads (the paper measures on its own reflectarray/helix geometries, which
+it does not publish; these seeded loop arrays stand in for them):
+
+* square PEC loop, outer side 0.4, trace width 0.04, zero thickness, z = 0,
+  meshed by a seeded Delaunay triangulation (~400 RWG edges);
+* equivalent box 0.45 x 0.45 x 0.1 around each element, structured mesh with
+  outward-oriented triangles (~300 RWG edges);
+* arrays of such elements on a 0.5 pitch in the z = 0 plane;
+* PEC spheres (icosphere) for the Mie-series checks.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.spatial import Delaunay
+
+MASTER_SEED = 20171206
+
+
+def rng(config_index: int, stream: int = 0) -> np.random.Generator:
+    """Independent PCG64 substream for (config, stream)."""
+    return np.random.Generator(np.random.PCG64([MASTER_SEED, int(config_index), int(stream)]))
+
+
+@dataclass
+class Mesh:
+    """Triangle mesh: vertices (nv, 3) float64 and triangles (nt, 3) int32."""
+
+    xyz: np.ndarray
+    tri: np.ndarray
+    name: str = ""
+
+    def __post_init__(self):
+        self.xyz = np.ascontiguousarray(self.xyz, dtype=np.float64)
+        self.tri = np.ascontiguousarray(self.tri, dtype=np.int32)
+
+    def translated(self, d) -> "Mesh":
+        return Mesh(self.xyz + np.asarray(d, dtype=np.float64)[None, :], self.tri.copy(), self.name)
+
+    def areas(self) -> np.ndarray:
+        p = self.xyz[self.tri]
+        return 0.5 * np.linalg.norm(np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), axis=1)
+
+
+def _square_ring(side: float, n_per_side: int) -> np.ndarray:
+    """Points on the boundary of a centred square, n_per_side segments per side, CCW."""
+    h = side / 2.0
+    corners = np.array([[-h, -h], [h, -h], [h, h], [-h, h]])
+    pts = []
+    for c in range(4):
+        a, b = corners[c], corners[(c + 1) % 4]
+        for i in range(n_per_side):
+            t = i / n_per_side
+            pts.append(a + t * (b - a))
+    return np.array(pts)
+
+
+def square_loop_mesh(outer: float = 0.4, width: float = 0.04, spacing: float = 0.0185,
+                     gen: np.random.Generator | None = None, jitter: float = 0.25) -> Mesh:
+    """Seeded Delaunay mesh of a square annulus (zero-thickness PEC loop) at z = 0.
+
+    Nodes: the outer and inner boundary squares at `spacing`, plus a middle ring
+    whose nodes are shifted along the ring by up to +-jitter*spacing (seeded).
+    """
+    if gen is None:
+        gen = rng(0, 1)
+    inner = outer - 2.0 * width
+    n_out = max(4, int(round(outer / spacing)))
+    n_in = max(4, int(round(inner / spacing)))
+    mid = outer - width
+    n_mid = max(4, int(round(mid / spacing)))
+    p_out = _square_ring(outer, n_out)
+    p_in = _square_ring(inner, n_in)
+    p_mid = _square_ring(mid, n_mid)
+    # jitter the middle ring along its sides (corners stay put)
+    hmid = mid / 2.0
+    step = mid / n_mid
+    for i in range(len(p_mid)):
+        if i % n_mid == 0:
+            continue
+        side = i // n_mid
+        d = np.array([[1, 0], [0, 1], [-1, 0], [0, -1]][side], dtype=np.float64)
+        p_mid[i] += d * gen.uniform(-jitter, jitter) * step
+    pts = np.vstack([p_out, p_mid, p_in])
+    dt = Delaunay(pts)
+    tri = dt.simplices.copy()
+    cen = pts[tri].mean(axis=1)
+    hi = inner / 2.0
+    keep = ~((np.abs(cen[:, 0]) < hi) & (np.abs(cen[:, 1]) < hi))
+    tri = tri[keep]
+    # CCW orientation (normal +z)
+    p = pts[tri]
+    cr = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0])
+    flip = cr < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    xyz = np.zeros((len(pts), 3))
+    xyz[:, :2] = pts
+    m = Mesh(xyz, tri, "square_loop")
+    area = m.areas().sum()
+    want = outer * outer - inner * inner
+    if abs(area - want) > 1e-9 * want or m.areas().min() < 1e-6 * want / len(tri):
+        raise RuntimeError("loop triangulation failed validation; change the seed or spacing")
+    return m
+
+
+def box_mesh(lx: float = 0.45, ly: float = 0.45, lz: float = 0.1,
+             nx: int = 6, ny: int = 6, nz: int = 1) -> Mesh:
+    """Structured, closed, outward-oriented triangulation of a centred box."""
+    verts: dict[tuple[int, int, int], int] = {}
+    xyz: list[list[float]] = []
+    n = (nx, ny, nz)
+    L = (lx, ly, lz)
+
+    def vid(i, j, k):
+        key = (i, j, k)
+        if key not in verts:
+            verts[key] = len(xyz)
+            xyz.append([-L[0] / 2 + L[0] * i / nx, -L[1] / 2 + L[1] * j / ny, -L[2] / 2 + L[2] * k / nz])
+        return verts[key]
+
+    tris: list[list[int]] = []
+    for axis in range(3):
+        b, c = (axis + 1) % 3, (axis + 2) % 3  # e_b x e_c = e_axis
+        for side in (0, 1):
+            for ib in range(n[b]):
+                for ic in range(n[c]):
+                    def node(db, dc):
+                        idx = [0, 0, 0]
+                        idx[axis] = side * n[axis]
+                        idx[b] = ib + db
+                        idx[c] = ic + dc
+                        return vid(*idx)
+                    q00, q10, q11, q01 = node(0, 0), node(1, 0), node(1, 1), node(0, 1)
+                    if side == 1:  # outward normal +e_axis: (b, c) order is CCW
+                        tris.append([q00, q10, q11])
+                        tris.append([q00, q11, q01])
+                    else:          # outward normal -e_axis: reverse
+                        tris.append([q00, q11, q10])
+                        tris.append([q00, q01, q11])
+    return Mesh(np.array(xyz), np.array(tris), "box")
+
+
+def icosphere_mesh(radius: float = 0.2, level: int = 2) -> Mesh:
+    """Icosahedron subdivided `level` times and projected on the sphere (outward CCW)."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]]
+    f = [[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4], [11, 10, 2],
+         [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5],
+         [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]]
+    verts = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    faces = [list(x) for x in f]
+    for _ in range(level):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                p = verts[a] + verts[b]
+                verts.append(p / np.linalg.norm(p))
+                cache[key] = len(verts) - 1
+            return cache[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [[a, ab, ca], [b, bc, ab], [c, ca, bc], [ab, bc, ca]]
+        faces = nf
+    xyz = np.array(verts) * radius
+    tri = np.array(faces)
+    p = xyz[tri]
+    nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    flip = (nrm * p.mean(axis=1)).sum(axis=1) < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    return Mesh(xyz, tri, "sphere")
+
+
+@dataclass
+class ElementType:
+    """One distinct array element: scatterer mesh and its equivalent surface."""
+
+    scatterer: Mesh
+    equiv: Mesh
+    name: str = ""
+
+
+@dataclass
+class ArrayLayout:
+    """Elements on a square lattice: element e has type types[e] and centre offsets[e]."""
+
+    types: list
+    type_of: np.ndarray
+    offsets: np.ndarray
+    nx: int = 0
+    ny: int = 0
+    pitch: float = 0.5
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_elem(self) -> int:
+        return len(self.type_of)
+
+
+def loop_element(outer: float = 0.4, config_index: int = 0, stream: int = 1,
+                 box=(0.45, 0.45, 0.1), box_div=(6, 6, 1)) -> ElementType:
+    m = square_loop_mesh(outer=outer, gen=rng(config_index, stream))
+    b = box_mesh(*box, *box_div)
+    return ElementType(m, b, f"loop{outer:g}")
+
+
+def loop_array(nx: int, ny: int, pitch: float = 0.5, outers=(0.4,), config_index: int = 0) -> ArrayLayout:
+    """nx x ny array of loop elements; with several outer sizes, types are drawn
+    uniformly per cell from a seeded stream."""
+    types = [loop_element(o, config_index, 1 + i) for i, o in enumerate(outers)]
+    if len(types) == 1:
+        type_of = np.zeros(nx * ny, dtype=np.int32)
+    else:
+        type_of = rng(config_index, 100).integers(0, len(types), size=nx * ny).astype(np.int32)
+    offs = np.zeros((nx * ny, 3))
+    e = 0
+    for j in range(ny):
+        for i in range(nx):
+            offs[e] = (pitch * i, pitch * j, 0.0)
+            e += 1
+    return ArrayLayout(types, type_of, offs, nx, ny, pitch)
+
+
+def planewave_grid(n_theta: int = 8, n_phi: int = 8, theta_max_deg: float = 60.0, phi_max_deg: float = 90.0):
+    """(theta, phi, pol) for an n_theta x n_phi incidence grid; pol alternates
+    theta-hat (0) / phi-hat (1) with the parity of (i + j)."""
+    th = np.deg2rad(np.linspace(0.0, theta_max_deg, n_theta))
+    ph = np.deg2rad(np.linspace(0.0, phi_max_deg, n_phi))
+    T, P, POL = [], [], []
+    for i in range(n_theta):
+        for j in range(n_phi):
+            T.append(th[i]); P.append(ph[j]); POL.append((i + j) % 2)
+    return np.array(T), np.array(P), np.array(POL, dtype=np.int32)
+
+
+def random_cvec(n: int, config_index: int = 0, stream: int = 7, nrhs: int = 1) -> np.ndarray:
+    """Seeded complex128 test vector(s), shape (n,) or (n, nrhs)."""
+    g = rng(config_index, stream)
+    shape = (n,) if nrhs == 1 else (n, nrhs)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+# Default AIM grid phase for the loop arrays: grid nodes at phase + h*Z^3.
+# Chosen so that no equivalent-box basis centroid falls on a rounding tie.
+DEFAULT_GRID_PHASE = (0.0137, 0.0291, 0.0913)
