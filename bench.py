@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the macromodel + AIM hot path on the 16 x 16 loop array.
+
+One step = one whole pass of the hot path on one synthetic request: plane-wave
+excitation (normal incidence, x-pol), then GMRES on
+(D - G T A^-1 B) E^ = V^ with the complex64 AIM operator (macromodel GEMM,
+projection, FFT convolution, interpolation, near-field SpMV), FP64
+Arnoldi/Givens, and FP64 iterative refinement against the complex128 operator,
+to a relative residual of 1e-4.
+
+Reported: value = operator applications per second inside the solve steps
+(matvecs/s, whole job over all ranks); solves/s; the same solve with the plain
+FP64 GPU form (complex128 operator, no refinement); p50/p99 step latency; an
+end-to-end leg through the public API with host copies; the roofline of the
+dominant kernel from CUDA events recorded live in the timed region; the CPU
+oracle's throughput on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "16x16 array of PEC square loops (0.4 lambda, 0.04 trace), 0.5 lambda pitch, box 0.45x0.45x0.1"
+TOL = 1e-4
+NX = NY = 16
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for r in self.rows if r[0] == str(self.index)] or self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def stage_bytes(stage: str, info: dict, nrhs: int, cs: int, nh: int, S: int) -> float:
+    """Algorithmic bytes of one launch of a stage (operator data read once, vectors once)."""
+    N = info["n_unknowns"]
+    nnz = info["nnz_near"]
+    Nx, Ny, Nz = info["grid"]
+    Px, Py, Pz = info["fft"]
+    ng = Nx * Ny * Nz
+    if stage == "near":      # values + int32 columns + int64 row pointers + u gather + y read/write
+        return (cs + 4) * nnz + 8 * (N + 1) + cs * N * nrhs + 2 * cs * N * nrhs
+    if stage == "gemm":      # x read, u and v written, [M; D] of one type
+        return 3 * cs * N * nrhs + 2 * cs * nh * nh
+    if stage == "project":   # u read, grids written (weights per type are L2-resident)
+        return cs * N * nrhs + 4 * cs * ng * nrhs
+    if stage == "interp":    # grids read, v read, y written
+        return 4 * cs * ng * nrhs + 2 * cs * N * nrhs
+    if stage == "fft_fwd":
+        return 4 * cs * nrhs * (ng + Nx * Py * Pz)
+    if stage == "fft_conv":
+        return 4 * cs * nrhs * 2 * Nx * Py * Pz + cs * Px * Py * Pz
+    if stage == "fft_inv":
+        return 4 * cs * nrhs * (ng + Nx * Py * Pz)
+    return 0.0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300.arrays import loop_array
+    from paper_1712_02443_gb300.build import build
+
+    build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    t0 = time.time()
+    ctx = mm.mm_ctx_create(local)
+    la = loop_array(ctx, NX, NY)
+    setup_s = time.time() - t0
+    info = la.info
+    N = la.n
+    st = torch.cuda.current_stream()
+    V = torch.empty(N, dtype=torch.complex128, device="cuda")
+    E = torch.empty_like(V)
+    th, ph, pol = [0.0], [0.0], [0]
+
+    def step(prec=mm.MM_C64, refine=1):
+        mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
+        return mm.mm_solve(la.array, 1, V, E, tol=TOL, restart=50, max_iter=2000, precision=prec, refine=refine,
+                           inner_tol=1e-5, stream=st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: mixed-precision solves
+    mm.mm_profile_enable(la.array, True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    matvecs = 0
+    iters = []
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                      if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        for k in range(args.steps):
+            s = step()
+            matvecs += s["matvecs"]
+            iters.append(s["iterations"])
+            ev[k + 1].record(st)
+        torch.cuda.synchronize()
+        barrier()
+    prof = mm.mm_profile_read(la.array)
+    mm.mm_profile_enable(la.array, False)
+    lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    solves_per_s = world * args.steps / (t_ms / 1e3)
+    matvecs_per_s = world * matvecs / (t_ms / 1e3)
+
+    # ---- plain FP64 GPU form (complex128 operator, FP64 GMRES, no refinement)
+    k64 = max(3, min(args.steps, 5))
+    step(mm.MM_C128, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mv64 = 0
+    e0.record(st)
+    for _ in range(k64):
+        mv64 += step(mm.MM_C128, 0)["matvecs"]
+    e1.record(st)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+
+    # ---- end to end through the public API: host angles in, solution copied to pinned host memory
+    Eh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    mv_e2e = 0
+    for _ in range(args.steps):
+        mv_e2e += step()["matvecs"]
+        Eh.copy_(E, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+
+    # ---- roofline of the dominant kernel (live CUDA events over the timed region)
+    hbm, bf16, src = _peaks()
+    dom = max((k for k in prof if k != "krylov"), key=lambda k: prof[k]["ms"])
+    launches = max(1, prof[dom]["launches"])
+    avg_s = prof[dom]["ms"] / 1e3 / launches
+    nb = stage_bytes(dom, info, 1, 8, N // (NX * NY), 27)
+    achieved = nb / avg_s / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        from paper_1712_02443_gb300.build import _digest
+        if tr.get("digest") == _digest() and dom in tr.get("per_launch_bytes", {}):
+            traffic = tr["per_launch_bytes"][dom]
+    except Exception:
+        pass
+    gpu_launches = int(sum(v["launches"] for v in prof.values()))
+    stages = {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
+                  "us_per_launch": round(1e3 * v["ms"] / max(1, v["launches"]), 2)} for k, v in prof.items()}
+    out = {
+        "metric": "macromodel-AIM matvecs/s and solves/s vs plain FP64 GPU form; p50/p99 latency",
+        "value": round(matvecs_per_s, 1),
+        "unit": "matvecs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "precision": "complex64 operator (FP32 FFT, SpMV, macromodel GEMM); FP64 Arnoldi, Givens, refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": N, "nrhs": 1, "tol": TOL, "restart": 50,
+                   "grid": list(info["grid"]), "fft": list(info["fft"]), "nnz_near": info["nnz_near"],
+                   "aim": {"h": 0.1, "order": 2, "n_nf": 3}, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "operator larger than L2 (near-field CSR %.2f GB complex64)" % (12e-9 * info["nnz_near"])},
+        "solves_per_s": round(solves_per_s, 2),
+        "matvecs_per_solve": round(matvecs / args.steps, 1),
+        "gmres_iterations_per_solve": round(sum(iters) / len(iters), 1),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
+        "fp64_plain_form": {"solves_per_s": round(world * k64 / (t64 / 1e3), 2),
+                            "matvecs_per_s": round(world * mv64 / (t64 / 1e3), 1),
+                            "matvecs_per_solve": round(mv64 / k64, 1)},
+        "speedup_vs_fp64_form_solves": round(solves_per_s / (world * k64 / (t64 / 1e3)), 3),
+        "e2e": {"value": round(world * mv_e2e / e2e_s, 1), "unit": "matvecs/s",
+                "solves_per_s": round(world * args.steps / e2e_s, 2),
+                "h2d_bytes_per_step": 8 + 8 + 4, "d2h_bytes_per_step": 16 * N},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_source": src, "algorithmic_bytes_per_launch": int(nb)},
+        "stages": stages,
+        "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+        "setup_s": round(setup_s, 2),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+    mm.mm_array_destroy(la.array)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _oracle_c2():
+    """Oracle objects for the benchmark workload (set-up, not timed)."""
+    from paper_1712_02443_gb300 import workloads as wl
+    from oracle.aim import AIMArray, AIMParams
+    from oracle.macromodel import build_element
+    K0 = 2.0 * np.pi
+    lay = wl.loop_array(NX, NY)
+    et = lay.types[0]
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    A = AIMArray([em], lay.type_of, lay.offsets, AIMParams(0.1, 2, 3, wl.DEFAULT_GRID_PHASE), K0, rows_only=True)
+    return A
+
+
+def _oracle_matvec_seconds(A, rows_G, x, reps=1):
+    """One oracle operator application on the full array, with the near field applied
+    on a row sample and scaled to all rows.  Returns seconds."""
+    n_s = rows_G.shape[0]
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        u = A.macro(x)
+        v = A.dapply(x)
+        yff = A.far(u)
+        t1 = time.perf_counter()
+        yn = rows_G @ u
+        t2 = time.perf_counter()
+        _ = v[:n_s] - yff[:n_s] - yn
+        t = (t1 - t0) + (t2 - t1) * (A.n / n_s)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def cpu_baseline(budget_s=20.0):
+    from paper_1712_02443_gb300 import workloads as wl
+    A = _oracle_c2()
+    x = wl.random_cvec(A.n, 1, 7)
+    g = np.random.default_rng(5)
+    rows = np.sort(g.choice(A.n, 1024, replace=False))
+    G = A.near_field_rows(rows)
+    t = _oracle_matvec_seconds(A, G, x)
+    reps = max(1, min(10, int(budget_s / max(t, 1e-3))))
+    t = _oracle_matvec_seconds(A, G, x, reps)
+    return {"value": round(1.0 / t, 4), "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+            "host_cpus": os.cpu_count(),
+            "sample": "oracle complex128 operator on the full 16x16 array: macromodel blocks, AIM projection, "
+                      "FFT convolution and interpolation on all %d unknowns; near field on 1024 sampled rows "
+                      "scaled to all rows; best of %d" % (A.n, reps)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1712_02443_gb300 import workloads as wl
+    A = _oracle_c2()
+    x = wl.random_cvec(A.n, 1, 7)
+    rows = np.sort(np.random.default_rng(5).choice(A.n, 1024, replace=False))
+    G = A.near_field_rows(rows)
+    for _ in range(args.warmup):
+        _oracle_matvec_seconds(A, G, x)
+    ts = [_oracle_matvec_seconds(A, G, x) for _ in range(args.steps)]
+    total = sum(ts)
+    val = args.steps / total
+    out = {"impl": "reference", "metric": "macromodel-AIM matvecs/s and solves/s vs plain FP64 GPU form; p50/p99 latency",
+           "value": round(val, 4), "unit": "matvecs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "unknowns": A.n, "nrhs": 1},
+           "cpu_baseline": {"value": round(val, 4), "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+                            "host_cpus": os.cpu_count(),
+                            "sample": "one step = one oracle operator application on the full array with the "
+                                      "near field on 1024 sampled rows scaled to all rows"},
+           "e2e": {"value": round(val, 4), "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * macroaim.h -- C ABI of libmacroaim: GB300-native macromodel + AIM solver for
+ * scattering from large arrays of PEC elements.
+ *
+ * Method: U. R. Patel, P. Triverio, S. V. Hum, "A Macromodeling Approach to
+ * Efficiently Compute Scattering from Large Arrays of Complex Scatterers"
+ * (arXiv 1712.02443).  Every entry point cites the passage that defines what it
+ * computes.
+ *
+ * Conventions
+ *  - Every call returns mm_status (0 = MM_OK).  No exception or abort crosses
+ *    the ABI.  mm_last_error(ctx) returns a context-owned message for the last
+ *    failure on that context (valid until the next call on it).
+ *  - Handles are opaque and owned by the library; free each with its *_destroy.
+ *    Destroy arrays before the types they use, types before meshes, and all of
+ *    them before their context.
+ *  - Input arrays are owned by the caller and copied during the call.
+ *  - Units: lengths in wavelengths (the caller scales), k0 in rad/length.
+ *    Time convention exp(+j w t); G(R) = exp(-j k0 R)/(4 pi R).
+ *  - Complex numbers are interleaved (re, im): double[2] for MM_C128,
+ *    float[2] for MM_C64.
+ *  - Vectors over the array's unknowns are element-major (all unknowns of
+ *    element 0, then element 1, ...; Sec. III), with the right-hand sides
+ *    innermost: entry (n, j) of an (N x nrhs) block is at index n*nrhs + j.
+ *  - Arguments named *_dev are device pointers on the context's device;
+ *    `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered: they return once the work is queued unless stated
+ *    otherwise.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef MACROAIM_H
+#define MACROAIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mm_status {
+  MM_OK = 0,
+  MM_EINVAL = 1,      /* invalid argument, mesh or configuration            */
+  MM_ENOMEM = 2,      /* host or device allocation failed                   */
+  MM_ECUDA = 3,       /* CUDA runtime error (message has the CUDA string)   */
+  MM_ENOCONV = 4,     /* iterative solve stopped at max_iter unconverged    */
+  MM_EBREAKDOWN = 5,  /* Krylov breakdown or non-finite residual            */
+  MM_ETIMEOUT = 6,    /* a bounded device wait gave up                      */
+  MM_EBUSY = 7,       /* resource in use                                    */
+  MM_EINTERNAL = 8    /* internal consistency check failed                  */
+} mm_status;
+
+typedef enum mm_precision {
+  MM_C64 = 0,   /* complex64 operator (FP32 FFT, SpMV, macromodel product) */
+  MM_C128 = 1   /* complex128 operator (the plain FP64 GPU form)           */
+} mm_precision;
+
+typedef struct mm_ctx mm_ctx;
+typedef struct mm_mesh mm_mesh;
+typedef struct mm_type mm_type;
+typedef struct mm_array mm_array;
+
+/* ------------------------------------------------------------------ context
+ * device >= 0 : CUDA device ordinal (must be an sm_103 GPU);
+ * device == -1: host-only context.  Set-up calls (meshes, element types,
+ *   arrays) run and can be inspected; every device call returns MM_EINVAL.  */
+mm_status mm_ctx_create(int device, mm_ctx** out);
+void mm_ctx_destroy(mm_ctx* ctx);
+const char* mm_last_error(const mm_ctx* ctx);
+/* Number of worker threads used by host set-up (default: hardware threads). */
+mm_status mm_ctx_set_threads(mm_ctx* ctx, int nthreads);
+
+/* -------------------------------------------------------------------- mesh
+ * A triangulated surface: vertices xyz (nv x 3, double), triangles tri
+ * (nt x 3, int32, 0-based).  Scatterer surfaces S_m may be open; equivalent
+ * surfaces must be closed, manifold and outward-oriented (counter-clockwise
+ * seen from outside) -- Sec. II-A.  RWG functions live on interior edges,
+ * numbered in lexicographic order of (min vertex, max vertex).
+ * Errors: MM_EINVAL for indices out of range, degenerate triangles or
+ * non-manifold edges.                                                        */
+mm_status mm_mesh_create(mm_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                         mm_mesh** out);
+/* n_rwg: number of RWG functions; closed: 1 if closed and outward-oriented.  */
+mm_status mm_mesh_info(const mm_mesh* mesh, int64_t* n_rwg, int32_t* closed);
+void mm_mesh_destroy(mm_mesh* mesh);
+
+/* ------------------------------------------------------------ element type
+ * Macromodel of one distinct element (Sec. II): fills the six Stratton-Chu
+ * matrices of eqs. (EFIEdiscretized1)-(EFIEdiscretized2) (eqs. (Gm_EJ_1)-(G3)),
+ * LU-factors G^(E^,H^) (eq. (Hdiscretized1)), forms A, B (eq. (JM)), T
+ * (eq. (Tm1)) and the composed block M = T A^-1 B applied in eq.
+ * (MV_product1), plus D (Sec. IV).  Host FP64; computed once per distinct
+ * element and shared by every identical element of an array (Sec. III).
+ * The dual functions of eq. (Ehat_expand) are built on the barycentric
+ * refinement of `equiv`.  `equiv` must be closed; k0 > 0.                    */
+typedef struct mm_em_opts {
+  double k0;     /* wavenumber (2*pi for lengths in wavelengths)             */
+  double eta0;   /* free-space impedance; <= 0 selects 376.730313668          */
+} mm_em_opts;
+mm_status mm_element_type_create(mm_ctx* ctx, const mm_mesh* scatterer, const mm_mesh* equiv,
+                                 const mm_em_opts* opts, mm_type** out);
+typedef enum mm_type_matrix_id {
+  MM_MAT_M = 0,     /* T A^-1 B           (N^ x N^)  */
+  MM_MAT_D = 1,     /* <f^_m, n x f^'_n>  (N^ x N^)  */
+  MM_MAT_T = 2,     /* eq. (Tm1)          (N^ x N)   */
+  MM_MAT_A = 3,     /* eq. (JM)           (N x N)    */
+  MM_MAT_B = 4,     /* eq. (JM)           (N x N^)   */
+  MM_MAT_GHH = 5,   /* G^(E^,H^)          (N^ x N^)  */
+  MM_MAT_GHE = 6    /* G^(E^,E^)          (N^ x N^)  */
+} mm_type_matrix_id;
+/* Copies matrix `which` (row-major, complex128 interleaved) into out_host
+ * (may be NULL to query the shape).  rows/cols receive its shape.            */
+mm_status mm_type_matrix(const mm_type* type, int32_t which, double* out_host, int64_t* rows, int64_t* cols);
+void mm_type_destroy(mm_type* type);
+
+/* ------------------------------------------------------------------- array
+ * Array of n_elem elements (Sec. III); element e has type types[e] and is
+ * translated by offsets_xyz[3e..3e+2].  Builds the AIM operator of Sec. V:
+ * grid nodes at phase + h*Z^3, stencils of (order+1)^3 nodes, projection
+ * weights matching all moments up to degree `order` per axis, the Green's
+ * spectrum of the zero-padded grid, and the precorrected near-field matrix
+ * over basis pairs whose stencil anchors are within n_nf cells (Chebyshev).
+ * Relative element offsets must be integer multiples of h (lattice-aligned
+ * elements share projection weights and near-field blocks).
+ * With a device context the operator is uploaded to the device.
+ * Errors: MM_EINVAL (offsets off the lattice, a basis centroid on a rounding
+ * tie of the grid, order < 1), MM_ENOMEM, MM_ECUDA.                          */
+typedef struct mm_aim_opts {
+  double h;          /* grid spacing                                          */
+  int32_t order;     /* stencil order N_O (N_O + 1 nodes per axis)            */
+  int32_t n_nf;      /* near-field radius N_NF in grid cells                  */
+  double phase[3];   /* position of one grid node                             */
+} mm_aim_opts;
+mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* types, const double* offsets_xyz,
+                          const mm_aim_opts* opts, mm_array** out);
+typedef struct mm_array_info {
+  int64_t n_unknowns;    /* N^ = sum of the elements' equivalent unknowns     */
+  int64_t n_elem;
+  int64_t n_types;
+  int64_t grid[3];       /* AIM grid nodes per axis                           */
+  int64_t fft[3];        /* padded FFT lengths per axis                       */
+  int64_t nnz_near;      /* near-field nonzeros                               */
+  int64_t device_bytes;  /* resident operator bytes on the device             */
+} mm_array_info;
+mm_status mm_array_info_get(const mm_array* array, mm_array_info* info);
+/* Device bytes a solve with nrhs columns needs beyond the resident operator
+ * (Krylov basis of `restart` + 1 vectors, work vectors, grids).              */
+mm_status mm_array_footprint(const mm_array* array, int32_t nrhs, int32_t precision, int32_t restart,
+                             size_t* bytes);
+/* Host copies of set-up data (testing, inspection, checkpointing):
+ *   MM_EXPORT_ANCHORS  int64 (N^ x 3)   stencil anchors (grid indices)
+ *   MM_EXPORT_PI       double (N^ x S x 4) projection weights (psi = x,y,z,phi)
+ *   MM_EXPORT_NEAR_PTR int64 (N^ + 1)   CSR row pointer of the near field
+ *   MM_EXPORT_NEAR_COL int32 (nnz)      CSR columns
+ *   MM_EXPORT_NEAR_VAL double (2 nnz)   CSR values, complex128
+ *   MM_EXPORT_GHAT     double (2 P)     Green's spectrum, complex128, x slowest
+ * `out` may be NULL to query the element count (`count`).                   */
+typedef enum mm_export_id {
+  MM_EXPORT_ANCHORS = 0, MM_EXPORT_PI = 1, MM_EXPORT_NEAR_PTR = 2, MM_EXPORT_NEAR_COL = 3,
+  MM_EXPORT_NEAR_VAL = 4, MM_EXPORT_GHAT = 5
+} mm_export_id;
+mm_status mm_array_export(const mm_array* array, int32_t which, void* out, int64_t* count);
+void mm_array_destroy(mm_array* array);
+
+/* --------------------------------------------------------------- hot path
+ * y = (D - G^(E^,J^) T A^-1 B) x, eq. (MV_product1), for nrhs columns, with
+ * G^(E^,J^) applied by AIM (Sec. V): per-type macromodel product u = M x and
+ * v = D x, projection of u onto the grid (step i), FFT convolution with the
+ * Green's spectrum (step ii), interpolation (step iii), near-field product,
+ * y = v - (G_FF u + G_NF u).  x_dev, y_dev: (N^ x nrhs) complex in
+ * `precision`; must not alias.  Queued on `stream`.                          */
+mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
+                   void* stream);
+/* Same operator with host buffers: copies x in, applies, copies y out, and
+ * returns after the result is in y_host (synchronous).                       */
+mm_status mm_apply_host(mm_array* array, int32_t nrhs, const void* x_host, void* y_host, int32_t precision);
+
+/* Excitation V^ for nrhs plane waves (Sec. IV, eq. (V1), tested with the
+ * equivalent-surface RWG functions): V^_n = <f^_n, n x n x E_inc> =
+ * -<f^_n, E_inc>, E_inc = p exp(-j k0 k^.r), k^ = -(sin t cos p, sin t sin p,
+ * cos t) (arriving from (theta, phi)), p = theta^ (pol 0) or phi^ (pol 1),
+ * |E0| = 1.  theta/phi/pol are host arrays of length nrhs; V_dev is
+ * (N^ x nrhs) in `precision`.                                                 */
+mm_status mm_rhs_planewave(mm_array* array, int32_t nrhs, const double* theta, const double* phi,
+                           const int32_t* pol, void* V_dev, int32_t precision, void* stream);
+
+/* GMRES solve of (D - G T A^-1 B) E^ = V^ (eq. (finalsystem); Sec. V) for
+ * nrhs independent columns, x0 = 0.  precision MM_C128: plain FP64 GMRES on
+ * the complex128 operator.  precision MM_C64 with refine = 1: complex64
+ * operator inside GMRES (FP64 Arnoldi and Givens), wrapped in FP64
+ * iterative refinement against the complex128 operator until
+ * ||V^ - Z E^|| <= tol ||V^|| per column.  V_dev, E_dev: (N^ x nrhs)
+ * complex128.  Synchronous: returns when done.  MM_ENOCONV if max_iter was
+ * reached (E_dev holds the last iterate).                                     */
+typedef struct mm_solve_opts {
+  double tol;         /* relative residual target per column                  */
+  int32_t restart;    /* GMRES(m) restart length                              */
+  int32_t max_iter;   /* total inner iterations bound                         */
+  int32_t precision;  /* operator precision inside GMRES                      */
+  int32_t refine;     /* 1: FP64 outer refinement (needs precision MM_C64)    */
+  double inner_tol;   /* inner GMRES tolerance when refining                  */
+} mm_solve_opts;
+typedef struct mm_solve_stats {
+  int32_t iterations;     /* inner GMRES iterations (max over columns)        */
+  int32_t matvecs;        /* operator applications (all precisions)           */
+  int32_t refinements;    /* outer refinement steps                           */
+  int32_t converged;      /* 1 if every column met tol                        */
+  double rel_residual;    /* max over columns of ||V - Z E||/||V||            */
+} mm_solve_stats;
+mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev, const mm_solve_opts* opts,
+                   mm_solve_stats* stats, void* stream);
+
+/* ----------------------------------------------------------- profiling
+ * With profiling enabled, every stage of every product is bracketed by CUDA
+ * events on the caller's stream (a few microseconds of host overhead per
+ * stage) and kernel launches are counted.  mm_profile_read synchronises the
+ * recorded events and returns per-stage totals since the last enable:
+ * ms[s] = summed device time of stage s, launches[s] = kernel launches of
+ * stage s (arrays of MM_STAGE_COUNT entries).  Disabled by default.          */
+typedef enum mm_stage {
+  MM_STAGE_GEMM = 0,     /* macromodel product [M; D] x                      */
+  MM_STAGE_PROJECT = 1,  /* step (i)                                         */
+  MM_STAGE_FFT_FWD = 2,  /* step (ii): z DFT + y FFT                         */
+  MM_STAGE_FFT_CONV = 3, /* step (ii): x FFT, spectrum multiply, inverse x  */
+  MM_STAGE_FFT_INV = 4,  /* step (ii): inverse y FFT + z DFT                 */
+  MM_STAGE_INTERP = 5,   /* step (iii) and y = D x - y_ff                    */
+  MM_STAGE_NEAR = 6,     /* near-field product                               */
+  MM_STAGE_KRYLOV = 7,   /* GMRES orthogonalisation, updates, conversions    */
+  MM_STAGE_COUNT = 8
+} mm_stage;
+mm_status mm_profile_enable(mm_array* array, int32_t enable);
+mm_status mm_profile_read(mm_array* array, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MACROAIM_H */

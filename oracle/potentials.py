@@ -21,7 +21,7 @@ where sgn(0) = 0: on the plane the gradient is the principal value (the
 half-residue of the K operator is added separately).  Heights |d| and edge
 distances |t0| below 1e-10 * sqrt(area) are set to exactly 0 (rounding noise
 of coplanar points); a point on an edge segment itself (R0 = 0 between the
-end points) takes f2 = 0, the principal value across that edge.
+end points) or on an end point takes f2 = 0, the principal value across that edge.
 """
 from __future__ import annotations
 
@@ -35,10 +35,12 @@ def _f2(lp, lm, Rp, Rm, R0sq):
 
     Branches on the signs of l+- (l+ > l- always): both >= 0, both <= 0, or
     straddling (then R- + l- = R0^2/(R- - l-))."""
-    out = np.empty_like(lp)
+    out = np.zeros_like(lp)
     a = lm >= 0.0
     b = (~a) & (lp <= 0.0)
     c = ~(a | b)
+    a = a & (Rm + lm > 0.0)          # an end point itself: principal value, 0
+    b = b & (Rp - lp > 0.0)
     out[a] = np.log((Rp[a] + lp[a]) / (Rm[a] + lm[a]))
     out[b] = np.log((Rm[b] - lm[b]) / (Rp[b] - lp[b]))
     c0 = c & (R0sq == 0.0)          # on the edge segment itself: principal value, 0

@@ -1,0 +1,656 @@
+// C ABI of libmacroaim (see include/macroaim.h for the contract of each call).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "aim_setup.h"
+#include "device.h"
+#include "internal.h"
+#include "macroaim.h"
+#include "solver.h"
+
+struct mm_ctx {
+  int device = -1;
+  int nthreads = 1;
+  std::string err;
+};
+struct mm_mesh {
+  mm_ctx* ctx;
+  mm::Mesh m;
+};
+struct mm_type {
+  mm_ctx* ctx;
+  mm::TypeModel tm;
+};
+struct mm_array {
+  mm_ctx* ctx = nullptr;
+  std::vector<const mm_type*> types;
+  mm::ArrayHost ah;
+  mm::DevArray da;
+  bool on_device = false;
+  double k0 = 0, eta0 = 0;
+  int32_t* elem_of = nullptr;     // device: element of each unknown
+  double** geo_ptrs = nullptr;    // device: per-type geometry pointers
+  double* d_ang = nullptr;        // device: theta, phi scratch for the excitation
+  int32_t* d_pol = nullptr;
+  int ang_cap = 0;
+  void* hx = nullptr;             // device staging for mm_apply_host
+  void* hy = nullptr;
+  size_t h_cap = 0;
+  std::unique_ptr<mm::Solver> solver;
+  ~mm_array();
+};
+
+namespace {
+
+mm_status fail(mm_ctx* ctx, mm_status code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define API_TRY try {
+#define API_CATCH(ctx)                                             \
+  }                                                                \
+  catch (const mm::Error& e) {                                     \
+    return fail(ctx, e.code, e.msg);                               \
+  }                                                                \
+  catch (const std::bad_alloc&) {                                  \
+    return fail(ctx, MM_ENOMEM, "host allocation failed");         \
+  }                                                                \
+  catch (...) {                                                    \
+    return fail(ctx, MM_EINTERNAL, "unexpected exception");        \
+  }
+
+#define CU(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t _e = (x);                                                                  \
+    if (_e != cudaSuccess) throw mm::Error{MM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(_e)}; \
+  } while (0)
+
+template <typename T>
+T* dev_upload(const T* h, size_t n, size_t& acc) {
+  T* d = nullptr;
+  if (n == 0) n = 1;
+  CU(cudaMalloc(&d, sizeof(T) * n));
+  acc += sizeof(T) * n;
+  if (h) CU(cudaMemcpy(d, h, sizeof(T) * n, cudaMemcpyHostToDevice));
+  return d;
+}
+
+template <typename R>
+void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
+  if (p.ready) return;
+  auto& da = a->da;
+  const auto& ah = a->ah;
+  typedef typename mm::V2<R>::T C;
+  p.W.resize(da.n_types);
+  p.Pi.resize(da.n_types);
+  for (int64_t t = 0; t < da.n_types; ++t) {
+    const auto& tm = a->types[t]->tm;
+    int64_t Nh = tm.Nh;
+    std::vector<C> W(2 * Nh * Nh);
+    for (int64_t i = 0; i < Nh * Nh; ++i) {
+      W[i].x = (R)tm.M[i].real(); W[i].y = (R)tm.M[i].imag();
+      W[Nh * Nh + i].x = (R)tm.D[i].real(); W[Nh * Nh + i].y = (R)tm.D[i].imag();
+    }
+    p.W[t] = dev_upload(W.data(), W.size(), da.bytes);
+    const auto& Pi = ah.tai[t].Pi;
+    std::vector<R> P(Pi.size());
+    for (size_t i = 0; i < Pi.size(); ++i) P[i] = (R)Pi[i];
+    p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
+  }
+  {
+    std::vector<C> v(ah.val.size());
+    for (size_t i = 0; i < v.size(); ++i) { v[i].x = (R)ah.val[i].real(); v[i].y = (R)ah.val[i].imag(); }
+    p.val = dev_upload(v.data(), v.size(), da.bytes);
+  }
+  {
+    const int64_t Px = ah.fft[0], Py = ah.fft[1], Pz = ah.fft[2];
+    std::vector<C> g(Px * Py * Pz);
+    for (int64_t i = 0; i < Px; ++i)
+      for (int64_t j = 0; j < Py; ++j)
+        for (int64_t l = 0; l < Pz; ++l) {
+          const auto& z = ah.Ghat[(i * Py + j) * Pz + l];
+          C& o = g[(j * Pz + l) * Px + i];
+          o.x = (R)z.real(); o.y = (R)z.imag();
+        }
+    p.Ghat = dev_upload(g.data(), g.size(), da.bytes);
+  }
+  auto tw = [&](int64_t L) {
+    std::vector<C> t(L);
+    for (int64_t k = 0; k < L; ++k) {
+      double th = -2.0 * M_PI * (double)k / (double)L;
+      t[k].x = (R)std::cos(th); t[k].y = (R)std::sin(th);
+    }
+    return dev_upload(t.data(), t.size(), da.bytes);
+  };
+  p.twx = tw(ah.fft[0]);
+  p.twy = tw(ah.fft[1]);
+  p.twz = tw(ah.fft[2]);
+  p.ready = true;
+}
+
+template <typename R>
+void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
+  if (w.nrhs == nrhs) return;
+  typedef typename mm::V2<R>::T C;
+  for (void* q : {w.u, w.v, w.grid, w.spec})
+    if (q) cudaFree(q);
+  w = mm::Work();
+  auto& da = a->da;
+  size_t vec = sizeof(C) * (size_t)da.N * nrhs;
+  size_t g = sizeof(C) * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2];
+  size_t s = sizeof(C) * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2];
+  CU(cudaMalloc(&w.u, vec));
+  CU(cudaMalloc(&w.v, vec));
+  CU(cudaMalloc(&w.grid, g));
+  CU(cudaMalloc(&w.spec, s));
+  w.bytes = 2 * vec + g + s;
+  w.nrhs = nrhs;
+}
+
+void free_prec_f(mm::DevPrec<float>& p) {
+  for (void* q : p.W) cudaFree(q);
+  for (void* q : p.Pi) cudaFree(q);
+  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz})
+    if (q) cudaFree(q);
+}
+void free_prec_d(mm::DevPrec<double>& p) {
+  for (void* q : p.W) cudaFree(q);
+  for (void* q : p.Pi) cudaFree(q);
+  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz})
+    if (q) cudaFree(q);
+}
+
+}  // namespace
+
+mm_array::~mm_array() {
+  solver.reset();
+  if (!on_device) return;
+  cudaSetDevice(da.device);
+  free_prec_f(da.pf);
+  free_prec_d(da.pd);
+  for (mm::Work* w : {&da.wf, &da.wd})
+    for (void* q : {w->u, w->v, w->grid, w->spec})
+      if (q) cudaFree(q);
+  for (auto* p : da.anc) cudaFree(p);
+  for (auto* p : da.geo) cudaFree(p);
+  for (auto* p : da.elems) cudaFree(p);
+  for (void* q : {(void*)da.off, (void*)da.boxorg, (void*)da.type_of, (void*)da.eoff, (void*)da.rowptr,
+                  (void*)da.col, (void*)elem_of, (void*)geo_ptrs, (void*)d_ang, (void*)d_pol, hx, hy})
+    if (q) cudaFree(q);
+}
+
+extern "C" {
+
+mm_status mm_ctx_create(int device, mm_ctx** out) {
+  if (!out) return MM_EINVAL;
+  *out = nullptr;
+  auto* c = new (std::nothrow) mm_ctx();
+  if (!c) return MM_ENOMEM;
+  c->nthreads = std::max(1u, std::thread::hardware_concurrency());
+  c->device = device;
+  if (device >= 0) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device >= n) {
+      delete c;
+      return MM_ECUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+      delete c;
+      return MM_ECUDA;
+    }
+    if (!(prop.major == 10 && prop.minor == 3)) {  // built for sm_103a only
+      delete c;
+      return MM_EINVAL;
+    }
+  } else if (device != -1) {
+    delete c;
+    return MM_EINVAL;
+  }
+  *out = c;
+  return MM_OK;
+}
+
+void mm_ctx_destroy(mm_ctx* ctx) { delete ctx; }
+
+const char* mm_last_error(const mm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mm_status mm_ctx_set_threads(mm_ctx* ctx, int nthreads) {
+  if (!ctx || nthreads < 1) return MM_EINVAL;
+  ctx->nthreads = nthreads;
+  return MM_OK;
+}
+
+mm_status mm_mesh_create(mm_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, mm_mesh** out) {
+  if (!ctx || !xyz || !tri || !out) return fail(ctx, MM_EINVAL, "null argument");
+  API_TRY
+  auto m = std::make_unique<mm_mesh>();
+  m->ctx = ctx;
+  mm::build_mesh(m->m, xyz, nv, tri, nt);
+  *out = m.release();
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_mesh_info(const mm_mesh* mesh, int64_t* n_rwg, int32_t* closed) {
+  if (!mesh) return MM_EINVAL;
+  if (n_rwg) *n_rwg = mesh->m.nrwg();
+  if (closed) *closed = mesh->m.closed ? 1 : 0;
+  return MM_OK;
+}
+
+void mm_mesh_destroy(mm_mesh* mesh) { delete mesh; }
+
+mm_status mm_element_type_create(mm_ctx* ctx, const mm_mesh* scatterer, const mm_mesh* equiv, const mm_em_opts* opts,
+                                 mm_type** out) {
+  if (!ctx || !scatterer || !equiv || !opts || !out) return fail(ctx, MM_EINVAL, "null argument");
+  if (!(opts->k0 > 0)) return fail(ctx, MM_EINVAL, "k0 must be positive");
+  if (!equiv->m.closed) return fail(ctx, MM_EINVAL, "equivalent surface must be closed and outward-oriented");
+  API_TRY
+  auto t = std::make_unique<mm_type>();
+  t->ctx = ctx;
+  t->tm.scat = scatterer->m;
+  t->tm.eq = equiv->m;
+  t->tm.em.k = opts->k0;
+  t->tm.em.eta0 = opts->eta0 > 0 ? opts->eta0 : 376.730313668;
+  t->tm.em.nthreads = ctx->nthreads;
+  mm::build_type(t->tm);
+  *out = t.release();
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_type_matrix(const mm_type* type, int32_t which, double* out_host, int64_t* rows, int64_t* cols) {
+  if (!type) return MM_EINVAL;
+  const auto& tm = type->tm;
+  const std::vector<mm::cd>* M = nullptr;
+  int64_t r = 0, c = 0;
+  switch (which) {
+    case MM_MAT_M: M = &tm.M; r = tm.Nh; c = tm.Nh; break;
+    case MM_MAT_D: M = &tm.D; r = tm.Nh; c = tm.Nh; break;
+    case MM_MAT_T: M = &tm.T; r = tm.Nh; c = tm.N; break;
+    case MM_MAT_A: M = &tm.A; r = tm.N; c = tm.N; break;
+    case MM_MAT_B: M = &tm.B; r = tm.N; c = tm.Nh; break;
+    case MM_MAT_GHH: M = &tm.GHH; r = tm.Nh; c = tm.Nh; break;
+    case MM_MAT_GHE: M = &tm.GHE; r = tm.Nh; c = tm.Nh; break;
+    default: return MM_EINVAL;
+  }
+  if (rows) *rows = r;
+  if (cols) *cols = c;
+  if (out_host) std::memcpy(out_host, M->data(), sizeof(mm::cd) * r * c);
+  return MM_OK;
+}
+
+void mm_type_destroy(mm_type* type) { delete type; }
+
+mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* types, const double* offsets_xyz,
+                          const mm_aim_opts* opts, mm_array** out) {
+  if (!ctx || !types || !offsets_xyz || !opts || !out || n_elem < 1) return fail(ctx, MM_EINVAL, "invalid argument");
+  API_TRY
+  auto a = std::make_unique<mm_array>();
+  a->ctx = ctx;
+  std::vector<int32_t> type_of(n_elem);
+  std::vector<const mm::TypeModel*> tms;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    if (!types[e]) return fail(ctx, MM_EINVAL, "null element type");
+    auto it = std::find(a->types.begin(), a->types.end(), types[e]);
+    if (it == a->types.end()) {
+      type_of[e] = (int32_t)a->types.size();
+      a->types.push_back(types[e]);
+      tms.push_back(&types[e]->tm);
+    } else {
+      type_of[e] = (int32_t)(it - a->types.begin());
+    }
+  }
+  mm::EM em = tms[0]->em;
+  for (auto* t : tms)
+    if (t->em.k != em.k || t->em.eta0 != em.eta0) return fail(ctx, MM_EINVAL, "element types differ in k0 or eta0");
+  em.nthreads = ctx->nthreads;
+  a->k0 = em.k;
+  a->eta0 = em.eta0;
+  std::vector<mm::Vec3> offs(n_elem);
+  for (int64_t e = 0; e < n_elem; ++e) offs[e] = {offsets_xyz[3 * e], offsets_xyz[3 * e + 1], offsets_xyz[3 * e + 2]};
+  mm::AimOpts ao{opts->h, opts->order, opts->n_nf, {opts->phase[0], opts->phase[1], opts->phase[2]}};
+  mm::build_array_host(a->ah, tms, type_of, offs, ao, em);
+  auto& ah = a->ah;
+  auto& da = a->da;
+  da.N = ah.N;
+  da.n_elem = n_elem;
+  da.n_types = (int64_t)tms.size();
+  da.nnz = ah.rowptr[ah.N];
+  for (int i = 0; i < 3; ++i) {
+    da.grid[i] = (int)ah.grid[i];
+    da.fft[i] = (int)ah.fft[i];
+  }
+  auto o1 = mm::stencil_1d(opts->order);
+  da.n1 = (int)o1.size();
+  da.S = da.n1 * da.n1 * da.n1;
+  da.o1lo = o1.front();
+  da.cA[0] = ah.c_A.real(); da.cA[1] = ah.c_A.imag();
+  da.cphi[0] = ah.c_phi.real(); da.cphi[1] = ah.c_phi.imag();
+  da.px = mm::make_plan(da.fft[0]);
+  da.py = mm::make_plan(da.fft[1]);
+  if (da.px.nst < 0 || da.py.nst < 0) throw mm::Error{MM_EINTERNAL, "FFT length without a radix plan"};
+  if (da.fft[2] > 64 || da.grid[2] > 32)
+    throw mm::Error{MM_EINVAL, "grid extent along z too large for the direct z transform (<= 32 nodes)"};
+  if (ctx->device >= 0) {
+    CU(cudaSetDevice(ctx->device));
+    da.device = ctx->device;
+    a->on_device = true;
+    size_t& acc = da.bytes;
+    std::vector<std::vector<int32_t>> elems(da.n_types);
+    for (int64_t e = 0; e < n_elem; ++e) elems[type_of[e]].push_back((int32_t)e);
+    std::vector<double*> gptr(da.n_types);
+    for (int64_t t = 0; t < da.n_types; ++t) {
+      const auto& ta = ah.tai[t];
+      const auto& eq = tms[t]->eq;
+      int64_t Nh = tms[t]->Nh;
+      da.Nh.push_back(Nh);
+      for (int i = 0; i < 3; ++i) da.box.push_back((int)ta.box_dim[i]);
+      std::vector<int32_t> anc(3 * Nh);
+      for (int64_t n = 0; n < Nh; ++n)
+        for (int i = 0; i < 3; ++i) anc[3 * n + i] = (int32_t)(ta.anc[3 * n + i] - ta.box_lo[i]);
+      da.anc.push_back(dev_upload(anc.data(), anc.size(), acc));
+      std::vector<double> geo(13 * Nh);
+      for (int64_t n = 0; n < Nh; ++n) {
+        mm::Vec3 pa = eq.v[eq.edge_a[n]], pb = eq.v[eq.edge_b[n]], pp = eq.v[eq.vplus[n]], pm = eq.v[eq.vminus[n]];
+        double g[13] = {pa.x, pa.y, pa.z, pb.x, pb.y, pb.z, pp.x, pp.y, pp.z, pm.x, pm.y, pm.z, eq.length[n]};
+        std::copy(g, g + 13, &geo[13 * n]);
+      }
+      da.geo.push_back(dev_upload(geo.data(), geo.size(), acc));
+      gptr[t] = da.geo.back();
+      da.elems.push_back(dev_upload(elems[t].data(), elems[t].size(), acc));
+      da.n_of_type.push_back((int64_t)elems[t].size());
+    }
+    a->geo_ptrs = dev_upload(gptr.data(), gptr.size(), acc);
+    da.off = dev_upload(ah.off.data(), ah.off.size(), acc);
+    std::vector<int32_t> boxorg(3 * n_elem), eo;
+    std::vector<double> eoff(3 * n_elem);
+    for (int64_t e = 0; e < n_elem; ++e) {
+      const auto& ta = ah.tai[type_of[e]];
+      for (int i = 0; i < 3; ++i) boxorg[3 * e + i] = (int32_t)(ta.box_lo[i] + ah.base[3 * e + i]);
+      eoff[3 * e] = offs[e].x; eoff[3 * e + 1] = offs[e].y; eoff[3 * e + 2] = offs[e].z;
+    }
+    da.boxorg = dev_upload(boxorg.data(), boxorg.size(), acc);
+    da.type_of = dev_upload(type_of.data(), type_of.size(), acc);
+    da.eoff = dev_upload(eoff.data(), eoff.size(), acc);
+    std::vector<int32_t> eof(ah.N);
+    for (int64_t e = 0; e < n_elem; ++e)
+      for (int64_t n = ah.off[e]; n < ah.off[e + 1]; ++n) eof[n] = (int32_t)e;
+    a->elem_of = dev_upload(eof.data(), eof.size(), acc);
+    da.rowptr = dev_upload(ah.rowptr.data(), ah.rowptr.size(), acc);
+    da.col = dev_upload(ah.col.data(), ah.col.size(), acc);
+    upload_precision<float>(a.get(), da.pf);
+    CU(mm::kernels_init(da));
+  }
+  *out = a.release();
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_array_info_get(const mm_array* a, mm_array_info* info) {
+  if (!a || !info) return MM_EINVAL;
+  info->n_unknowns = a->ah.N;
+  info->n_elem = a->ah.n_elem;
+  info->n_types = (int64_t)a->types.size();
+  for (int i = 0; i < 3; ++i) {
+    info->grid[i] = a->ah.grid[i];
+    info->fft[i] = a->ah.fft[i];
+  }
+  info->nnz_near = a->ah.rowptr.empty() ? 0 : a->ah.rowptr.back();
+  info->device_bytes = (int64_t)a->da.bytes;
+  return MM_OK;
+}
+
+mm_status mm_array_footprint(const mm_array* a, int32_t nrhs, int32_t precision, int32_t restart, size_t* bytes) {
+  if (!a || !bytes || nrhs < 1 || restart < 1) return MM_EINVAL;
+  const auto& da = a->da;
+  size_t cs = precision == MM_C128 ? 16 : 8;
+  size_t vec = cs * (size_t)da.N * nrhs;
+  size_t g = cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2];
+  size_t s = cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2];
+  size_t kry = 16 * (size_t)da.N * nrhs * (restart + 4) + 16 * (size_t)da.N * nrhs;
+  *bytes = 2 * vec + g + s + kry;
+  return MM_OK;
+}
+
+mm_status mm_array_export(const mm_array* a, int32_t which, void* out, int64_t* count) {
+  if (!a || !count) return MM_EINVAL;
+  const auto& ah = a->ah;
+  switch (which) {
+    case MM_EXPORT_ANCHORS: {
+      *count = 3 * ah.N;
+      if (out) {
+        int64_t* o = static_cast<int64_t*>(out);
+        for (int64_t e = 0; e < ah.n_elem; ++e) {
+          const auto& ta = ah.tai[ah.type_of[e]];
+          for (int64_t n = 0; n < ta.Nh; ++n)
+            for (int i = 0; i < 3; ++i) o[3 * (ah.off[e] + n) + i] = ta.anc[3 * n + i] + ah.base[3 * e + i];
+        }
+      }
+      return MM_OK;
+    }
+    case MM_EXPORT_PI: {
+      const int S = ah.tai[0].S;
+      *count = ah.N * S * 4;
+      if (out) {
+        double* o = static_cast<double*>(out);
+        for (int64_t e = 0; e < ah.n_elem; ++e) {
+          const auto& ta = ah.tai[ah.type_of[e]];
+          std::memcpy(o + ah.off[e] * S * 4, ta.Pi.data(), sizeof(double) * ta.Pi.size());
+        }
+      }
+      return MM_OK;
+    }
+    case MM_EXPORT_NEAR_PTR:
+      *count = (int64_t)ah.rowptr.size();
+      if (out) std::memcpy(out, ah.rowptr.data(), sizeof(int64_t) * ah.rowptr.size());
+      return MM_OK;
+    case MM_EXPORT_NEAR_COL:
+      *count = (int64_t)ah.col.size();
+      if (out) std::memcpy(out, ah.col.data(), sizeof(int32_t) * ah.col.size());
+      return MM_OK;
+    case MM_EXPORT_NEAR_VAL:
+      *count = 2 * (int64_t)ah.val.size();
+      if (out) std::memcpy(out, ah.val.data(), sizeof(mm::cd) * ah.val.size());
+      return MM_OK;
+    case MM_EXPORT_GHAT:
+      *count = 2 * (int64_t)ah.Ghat.size();
+      if (out) std::memcpy(out, ah.Ghat.data(), sizeof(mm::cd) * ah.Ghat.size());
+      return MM_OK;
+    default:
+      return MM_EINVAL;
+  }
+}
+
+void mm_array_destroy(mm_array* a) { delete a; }
+
+mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !x_dev || !y_dev || x_dev == y_dev) return fail(ctx, MM_EINVAL, "invalid apply arguments");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (precision == MM_C64) {
+    ensure_work<float>(a, a->da.wf, nrhs);
+    e = mm::matvec<float>(a->da, a->da.pf, a->da.wf, nrhs, x_dev, y_dev, st);
+  } else if (precision == MM_C128) {
+    upload_precision<double>(a, a->da.pd);
+    ensure_work<double>(a, a->da.wd, nrhs);
+    e = mm::matvec<double>(a->da, a->da.pd, a->da.wd, nrhs, x_dev, y_dev, st);
+  } else {
+    return fail(ctx, MM_EINVAL, "unknown precision");
+  }
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("matvec: ") + cudaGetErrorString(e));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_apply_host(mm_array* a, int32_t nrhs, const void* x_host, void* y_host, int32_t precision) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !x_host || !y_host) return fail(ctx, MM_EINVAL, "invalid apply arguments");
+  if (precision != MM_C64 && precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  size_t bytes = (precision == MM_C128 ? 16 : 8) * (size_t)a->da.N * nrhs;
+  if (a->h_cap < bytes) {
+    if (a->hx) cudaFree(a->hx);
+    if (a->hy) cudaFree(a->hy);
+    a->hx = a->hy = nullptr;
+    CU(cudaMalloc(&a->hx, bytes));
+    CU(cudaMalloc(&a->hy, bytes));
+    a->h_cap = bytes;
+  }
+  CU(cudaMemcpyAsync(a->hx, x_host, bytes, cudaMemcpyHostToDevice, 0));
+  mm_status s = mm_apply(a, nrhs, a->hx, a->hy, precision, nullptr);
+  if (s != MM_OK) return s;
+  CU(cudaMemcpyAsync(y_host, a->hy, bytes, cudaMemcpyDeviceToHost, 0));
+  CU(cudaStreamSynchronize(0));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_rhs_planewave(mm_array* a, int32_t nrhs, const double* theta, const double* phi, const int32_t* pol,
+                           void* V_dev, int32_t precision, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !theta || !phi || !pol || !V_dev) return fail(ctx, MM_EINVAL, "invalid excitation arguments");
+  for (int j = 0; j < nrhs; ++j)
+    if (pol[j] != 0 && pol[j] != 1) return fail(ctx, MM_EINVAL, "pol must be 0 (theta) or 1 (phi)");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (a->ang_cap < nrhs) {
+    if (a->d_ang) cudaFree(a->d_ang);
+    if (a->d_pol) cudaFree(a->d_pol);
+    a->d_ang = nullptr;
+    a->d_pol = nullptr;
+    CU(cudaMalloc(&a->d_ang, sizeof(double) * 2 * nrhs));
+    CU(cudaMalloc(&a->d_pol, sizeof(int32_t) * nrhs));
+    a->ang_cap = nrhs;
+  }
+  std::vector<double> ang(2 * nrhs);
+  std::copy(theta, theta + nrhs, ang.begin());
+  std::copy(phi, phi + nrhs, ang.begin() + nrhs);
+  CU(cudaMemcpyAsync(a->d_ang, ang.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(a->d_pol, pol, sizeof(int32_t) * nrhs, cudaMemcpyHostToDevice, st));
+  mm::Rule r7 = mm::rule_tri7();
+  mm::QuadRule q;
+  q.n = r7.n();
+  for (int i = 0; i < q.n; ++i) {
+    q.b0[i] = r7.b0[i]; q.b1[i] = r7.b1[i]; q.b2[i] = r7.b2[i]; q.w[i] = r7.w[i];
+  }
+  cudaError_t e;
+  if (precision == MM_C64)
+    e = mm::rhs_planewave<float>(a->da, a->elem_of, a->geo_ptrs, nrhs, a->d_ang, a->d_ang + nrhs, a->d_pol, a->k0, q,
+                                 V_dev, st);
+  else if (precision == MM_C128)
+    e = mm::rhs_planewave<double>(a->da, a->elem_of, a->geo_ptrs, nrhs, a->d_ang, a->d_ang + nrhs, a->d_pol, a->k0,
+                                  q, V_dev, st);
+  else
+    return fail(ctx, MM_EINVAL, "unknown precision");
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("excitation: ") + cudaGetErrorString(e));
+  // the host staging of the angles must stay valid until the copies ran
+  CU(cudaStreamSynchronize(st));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, const mm_solve_opts* opts,
+                   mm_solve_stats* stats, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !V_dev || !E_dev || !opts || V_dev == E_dev) return fail(ctx, MM_EINVAL, "invalid solve arguments");
+  if (!(opts->tol > 0) || opts->restart < 1 || opts->max_iter < 1) return fail(ctx, MM_EINVAL, "invalid solve options");
+  if (opts->precision != MM_C64 && opts->precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (opts->refine && opts->precision != MM_C64) return fail(ctx, MM_EINVAL, "refinement needs precision MM_C64");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!a->solver) a->solver = std::make_unique<mm::Solver>();
+  mm::Solver& S = *a->solver;
+  S.prof = &a->da.prof;
+  mm::Status s = S.ensure(a->da.N, nrhs, opts->restart);
+  if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
+  upload_precision<double>(a, a->da.pd);
+  ensure_work<double>(a, a->da.wd, nrhs);
+  ensure_work<float>(a, a->da.wf, nrhs);
+  mm_array* arr = a;
+  S.op64 = [arr, nrhs](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
+    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2);
+    if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
+    return {MM_OK, ""};
+  };
+  S.op32 = [arr, nrhs](const void* in, void* out, cudaStream_t s2) -> mm::Status {
+    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, in, out, s2);
+    if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
+    return {MM_OK, ""};
+  };
+  int iters = 0, refs = 0;
+  double relres = 0;
+  bool conv = false;
+  s = S.solve(static_cast<const double2*>(V_dev), static_cast<double2*>(E_dev), opts->tol, opts->precision,
+              opts->refine, opts->inner_tol > 0 ? opts->inner_tol : 1e-2, opts->max_iter, iters, refs, relres, conv,
+              st);
+  if (stats) {
+    stats->iterations = iters;
+    stats->matvecs = S.matvecs;
+    stats->refinements = refs;
+    stats->converged = conv ? 1 : 0;
+    stats->rel_residual = relres;
+  }
+  if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
+  if (!conv) return fail(ctx, MM_ENOCONV, "GMRES reached max_iter before the tolerance");
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_profile_enable(mm_array* a, int32_t enable) {
+  if (!a) return MM_EINVAL;
+  if (!a->on_device) return fail(a->ctx, MM_EINVAL, "array has no device (host-only context)");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  for (auto& r : a->da.prof.recs) {
+    cudaEventSynchronize(r.b);
+  }
+  a->da.prof.reset();
+  a->da.prof.on = enable != 0;
+  return MM_OK;
+  API_CATCH(a->ctx)
+}
+
+mm_status mm_profile_read(mm_array* a, double* ms, int64_t* launches) {
+  if (!a || !ms || !launches) return MM_EINVAL;
+  if (!a->on_device) return fail(a->ctx, MM_EINVAL, "array has no device (host-only context)");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  for (int i = 0; i < MM_STAGE_COUNT; ++i) {
+    ms[i] = 0;
+    launches[i] = a->da.prof.launches[i];
+  }
+  for (auto& r : a->da.prof.recs) {
+    CU(cudaEventSynchronize(r.b));
+    float t = 0;
+    CU(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.stage] += t;
+  }
+  return MM_OK;
+  API_CATCH(a->ctx)
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Device-side structures and kernel launchers of libmacroaim.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace mm {
+
+template <typename R> struct V2;
+template <> struct V2<float> { typedef float2 T; };
+template <> struct V2<double> { typedef double2 T; };
+
+// Stage profiler: CUDA events around stages on the launching stream.
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int open_stage = -1;
+  cudaEvent_t open_ev = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int stage, cudaStream_t st) {
+    if (!on) return;
+    open_stage = stage;
+    open_ev = get();
+    cudaEventRecord(open_ev, st);
+  }
+  void end(cudaStream_t st, int nlaunch) {
+    if (!on) return;
+    cudaEvent_t b = get();
+    cudaEventRecord(b, st);
+    recs.push_back({open_stage, open_ev, b});
+    launches[open_stage] += nlaunch;
+  }
+  void reset() {
+    for (auto& r : recs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+    for (auto& l : launches) l = 0;
+  }
+  ~Profiler() {
+    reset();
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Radix plan of one FFT length (radices from {8, 4, 2, 3, 5, 7}).
+struct FftPlan {
+  int L = 1;
+  int nst = 0;
+  int rad[16] = {0};
+};
+FftPlan make_plan(int L);
+
+// Operator data in one precision (R = float for MM_C64, double for MM_C128).
+template <typename R>
+struct DevPrec {
+  bool ready = false;
+  std::vector<void*> W;   // per type: stacked [M_t; D_t], 2 Nh x Nh complex, row-major
+  std::vector<R*> Pi;     // per type: Nh x S x 4 projection weights
+  void* val = nullptr;    // near-field values (nnz complex)
+  void* Ghat = nullptr;   // Green's spectrum [ky][kz][kx] complex, divided by Px Py Pz
+  void* twx = nullptr;    // exp(-2 pi i k / Px), k < Px
+  void* twy = nullptr;
+  void* twz = nullptr;
+};
+
+// Work buffers for one (precision, nrhs) pair.
+struct Work {
+  int nrhs = 0;
+  void* u = nullptr;      // N x nrhs   macromodel product T A^-1 B x
+  void* v = nullptr;      // N x nrhs   D x
+  void* grid = nullptr;   // 4 nrhs x Nx x Ny x Nz   grid charges/currents, then potentials
+  void* spec = nullptr;   // 4 nrhs x Nx x Py x Pz   partial spectra
+  size_t bytes = 0;
+};
+
+struct DevArray {
+  int device = 0;
+  int64_t N = 0, n_elem = 0, n_types = 0, nnz = 0;
+  int grid[3] = {0, 0, 0}, fft[3] = {0, 0, 0};
+  int S = 0, n1 = 0, o1lo = 0;
+  double cA[2] = {0, 0}, cphi[2] = {0, 0};
+  // per type (host mirrors + device pointers)
+  std::vector<int64_t> Nh;
+  std::vector<int> box;                 // 3 per type
+  std::vector<int32_t*> anc;            // per type: Nh x 3 box-local anchors
+  std::vector<double*> geo;             // per type: Nh x 13 (pa, pb, p+, p-, length), local coordinates
+  std::vector<int32_t*> elems;          // per type: element ids of that type
+  std::vector<int64_t> n_of_type;
+  // per element
+  int64_t* off = nullptr;               // n_elem + 1
+  int32_t* boxorg = nullptr;            // n_elem x 3: global grid coordinates of the type box origin
+  int32_t* type_of = nullptr;
+  double* eoff = nullptr;               // n_elem x 3 element offsets
+  // near field pattern (shared by both precisions)
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  FftPlan px, py;
+  DevPrec<float> pf;
+  DevPrec<double> pd;
+  Work wf, wd;
+  Profiler prof;
+  size_t bytes = 0;                     // resident operator bytes
+  // host copies kept for lazy upload of the other precision
+  std::vector<std::vector<double>> hW;  // per type: 2 Nh x Nh complex128 interleaved
+  std::vector<std::vector<double>> hPi;
+  std::vector<double> hval, hGhat;      // complex128 interleaved
+};
+
+template <typename R>
+cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st);
+template <typename R>
+size_t fft_smem_bytes(const DevArray& a, int which);
+cudaError_t kernels_init(DevArray& a);
+
+}  // namespace mm

@@ -1,0 +1,609 @@
+// Hot-path kernels of the macromodel + AIM matrix-vector product (eq. (MV_product1)):
+//
+//   y = D x - (G_FF + G_NF) T A^-1 B x,
+//   G_FF = sum_psi I_psi H_psi P_psi        (Sec. V, steps (i)-(iii))
+//
+//  k_macro_gemm   u = M_t x_e and v = D_t x_e for every element of type t (stacked
+//                 [M_t; D_t], one GEMM per type, shared by identical elements, Sec. III)
+//  k_project      step (i): grid currents (psi = x, y, z) and charges (phi) on each
+//                 element's stencil box, accumulated in shared memory, flushed with
+//                 atomics (neighbouring boxes overlap)
+//  k_fft_fwd_planes / k_fft_conv_lines / k_fft_inv_planes
+//                 step (ii): zero-padded 3D FFT convolution with the Green's
+//                 spectrum; direct DFT along the short z axis, Stockham mixed-radix
+//                 FFTs along y and x in shared memory, the spectrum multiply fused
+//                 between the forward and inverse x transforms
+//  k_interp       step (iii): interpolation with I = P^T, psi-sum with c_A, c_phi,
+//                 and y = v - y_ff
+//  k_spmv_near    y -= G_NF u, precorrected near field (CSR, warp per row)
+//
+// Layouts: vectors element-major with RHS innermost; grids [4 nrhs][Nx][Ny][Nz]
+// (batch b = psi * nrhs + j); partial spectra [b][x][ky][kz]; Green's spectrum
+// [ky][kz][kx].
+#include <cstdio>
+
+#include "device.h"
+
+namespace mm {
+
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  T c;
+  c.x = a.x * b.x - a.y * b.y;
+  c.y = a.x * b.y + a.y * b.x;
+  return c;
+}
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) {
+  T c;
+  c.x = a.x + b.x;
+  c.y = a.y + b.y;
+  return c;
+}
+template <typename T> __device__ __forceinline__ T csub(T a, T b) {
+  T c;
+  c.x = a.x - b.x;
+  c.y = a.y - b.y;
+  return c;
+}
+template <typename T, typename R> __device__ __forceinline__ T cscale(T a, R s) {
+  T c;
+  c.x = a.x * s;
+  c.y = a.y * s;
+  return c;
+}
+template <typename T> __device__ __forceinline__ T czero() {
+  T c;
+  c.x = 0;
+  c.y = 0;
+  return c;
+}
+
+FftPlan make_plan(int L) {
+  FftPlan p;
+  p.L = L;
+  int n = L;
+  for (int r : {8, 4, 2, 3, 5, 7})
+    while (n % r == 0 && p.nst < 16) {
+      p.rad[p.nst++] = r;
+      n /= r;
+    }
+  if (n != 1) p.nst = -1;
+  return p;
+}
+
+// ---------------------------------------------------------------- A1: macromodel GEMM
+// C (2Nh x ncols) = W (2Nh x Nh) X (Nh x ncols); column c = j * nrhs + rhs of element elems[j].
+template <typename R>
+__global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __restrict__ W, int Nh,
+                                                    const int32_t* __restrict__ elems, int ncols, int nrhs,
+                                                    const int64_t* __restrict__ off,
+                                                    const typename V2<R>::T* __restrict__ x,
+                                                    typename V2<R>::T* __restrict__ u,
+                                                    typename V2<R>::T* __restrict__ v) {
+  typedef typename V2<R>::T C;
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ C As[BK][BM + 1];
+  __shared__ C Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  const int M2 = 2 * Nh;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  // per-thread B column bases for loading
+  for (int k0 = 0; k0 < Nh; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      int r = e / BK, kk = e % BK;
+      int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M2 && gk < Nh) ? W[(int64_t)gr * Nh + gk] : czero<C>();
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int kk = e / BN, c = e % BN;
+      int gc = col0 + c, gk = k0 + kk;
+      C val = czero<C>();
+      if (gc < ncols && gk < Nh) {
+        int j = gc / nrhs, rr = gc % nrhs;
+        val = x[(off[elems[j]] + gk) * nrhs + rr];
+      }
+      Bs[kk][c] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
+          acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gr = row0 + ty * 4 + i;
+    if (gr >= M2) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gc = col0 + tx * 4 + j;
+      if (gc >= ncols) continue;
+      int e = elems[gc / nrhs], rr = gc % nrhs;
+      if (gr < Nh)
+        u[(off[e] + gr) * nrhs + rr] = acc[i][j];
+      else
+        v[(off[e] + gr - Nh) * nrhs + rr] = acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- A2: projection (step i)
+// One CTA per element; the element's stencil box (bx x by x bz nodes) for all
+// psi and a chunk of RHS lives in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
+                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
+                                                 const int32_t* __restrict__ boxorg, int nrhs, int rc,
+                                                 const typename V2<R>::T* __restrict__ u, int Nx, int Ny, int Nz,
+                                                 typename V2<R>::T* __restrict__ grid) {
+  typedef typename V2<R>::T C;
+  extern __shared__ unsigned char smem_raw[];
+  R* box = reinterpret_cast<R*>(smem_raw);  // [psi][c][node][re/im]
+  const int e = elems[blockIdx.x];
+  const int nodes = bx * by * bz;
+  const int64_t o = off[e];
+  const int gx0 = boxorg[3 * e], gy0 = boxorg[3 * e + 1], gz0 = boxorg[3 * e + 2];
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  for (int c0 = 0; c0 < nrhs; c0 += rc) {
+    const int cn = min(rc, nrhs - c0);
+    for (int i = threadIdx.x; i < 4 * cn * nodes * 2; i += blockDim.x) box[i] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < Nh * S; p += blockDim.x) {
+      const int n = p / S, s = p % S;
+      const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+      const int nx = anc[3 * n] + o1lo + ix, ny = anc[3 * n + 1] + o1lo + iy, nz = anc[3 * n + 2] + o1lo + iz;
+      const int node = (nx * by + ny) * bz + nz;
+      const R* w = Pi + ((int64_t)n * S + s) * 4;
+      const R w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+      for (int c = 0; c < cn; ++c) {
+        const C uv = u[(o + n) * nrhs + c0 + c];
+        R* b0 = box + 2 * ((0 * cn + c) * nodes + node);
+        R* b1 = box + 2 * ((1 * cn + c) * nodes + node);
+        R* b2 = box + 2 * ((2 * cn + c) * nodes + node);
+        R* b3 = box + 2 * ((3 * cn + c) * nodes + node);
+        atomicAdd(b0, w0 * uv.x); atomicAdd(b0 + 1, w0 * uv.y);
+        atomicAdd(b1, w1 * uv.x); atomicAdd(b1 + 1, w1 * uv.y);
+        atomicAdd(b2, w2 * uv.x); atomicAdd(b2 + 1, w2 * uv.y);
+        atomicAdd(b3, w3 * uv.x); atomicAdd(b3 + 1, w3 * uv.y);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * cn * nodes; i += blockDim.x) {
+      const int node = i % nodes, pc = i / nodes;
+      const int psi = pc / cn, c = pc % cn;
+      const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+      const R re = box[2 * i], im = box[2 * i + 1];
+      if (re == 0 && im == 0) continue;
+      const int64_t b = (int64_t)psi * nrhs + c0 + c;
+      R* g = reinterpret_cast<R*>(grid + b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz));
+      atomicAdd(g, re);
+      atomicAdd(g + 1, im);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- A3: FFT convolution (step ii)
+template <typename C, int RADIX, bool INV>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
+                                               const C* __restrict__ tw, int lane, int nlanes) {
+  const int nb = L / RADIX;
+  const int st = L / (Ns * RADIX);
+  const int stR = L / RADIX;
+  for (int j = lane; j < nb; j += nlanes) {
+    const int k = j % Ns;
+    C v[RADIX];
+#pragma unroll
+    for (int q = 0; q < RADIX; ++q) v[q] = a[j + q * nb];
+#pragma unroll
+    for (int q = 1; q < RADIX; ++q) {
+      C w = tw[q * k * st];
+      if (INV) w.y = -w.y;
+      v[q] = cmul(v[q], w);
+    }
+    const int base = (j / Ns) * Ns * RADIX + k;
+#pragma unroll
+    for (int p = 0; p < RADIX; ++p) {
+      C acc = v[0];
+#pragma unroll
+      for (int q = 1; q < RADIX; ++q) {
+        C w = tw[((p * q) % RADIX) * stR];
+        if (INV) w.y = -w.y;
+        acc = cadd(acc, cmul(v[q], w));
+      }
+      b[base + p * Ns] = acc;
+    }
+  }
+}
+
+// Warp-level Stockham FFT of one line held in shared memory (buffers a, b of
+// length L); returns the buffer that holds the result.
+template <typename C, bool INV>
+__device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
+  int Ns = 1;
+  for (int s = 0; s < P.nst; ++s) {
+    const int r = P.rad[s];
+    switch (r) {
+      case 8: stockham_stage<C, 8, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      case 4: stockham_stage<C, 4, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      case 2: stockham_stage<C, 2, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      case 3: stockham_stage<C, 3, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      case 5: stockham_stage<C, 5, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      default: stockham_stage<C, 7, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+    }
+    __syncwarp();
+    C* t = a;
+    a = b;
+    b = t;
+    Ns *= r;
+  }
+  return a;
+}
+
+// Forward: z DFT (direct, Nz -> Pz) then y FFT (Ny -> Py) of plane (b, x).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T* __restrict__ grid, int Nx, int Ny,
+                                                        int Nz, FftPlan py, int Pz,
+                                                        const typename V2<R>::T* __restrict__ twy,
+                                                        const typename V2<R>::T* __restrict__ twz,
+                                                        typename V2<R>::T* __restrict__ spec) {
+  typedef typename V2<R>::T C;
+  extern __shared__ unsigned char smem_raw[];
+  const int Py = py.L;
+  C* ty = reinterpret_cast<C*>(smem_raw);
+  C* tz = ty + Py;
+  C* b0 = tz + Pz;            // [kz][y]
+  C* b1 = b0 + Pz * Py;       // [kz][y]
+  const int x = blockIdx.x, b = blockIdx.y;
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
+  const C* src = grid + ((int64_t)b * Nx + x) * Ny * Nz;
+  for (int i = threadIdx.x; i < Ny * Nz; i += blockDim.x) b1[i] = src[i];   // staging [y][z]
+  __syncthreads();
+  for (int i = threadIdx.x; i < Pz * Py; i += blockDim.x) {
+    const int kz = i / Py, y = i % Py;
+    C acc = czero<C>();
+    if (y < Ny)
+      for (int z = 0; z < Nz; ++z) acc = cadd(acc, cmul(b1[y * Nz + z], tz[(kz * z) % Pz]));
+    b0[i] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  C* res = nullptr;
+  for (int kz = warp; kz < Pz; kz += nw) res = warp_fft<C, false>(b0 + kz * Py, b1 + kz * Py, py, ty, lane);
+  __syncthreads();
+  const bool in_b0 = (py.nst % 2) == 0;
+  (void)res;
+  const C* out = in_b0 ? b0 : b1;
+  C* dst = spec + ((int64_t)b * Nx + x) * Py * Pz;
+  for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
+    const int ky = i / Pz, kz = i % Pz;
+    dst[i] = out[kz * Py + ky];
+  }
+}
+
+// x FFT (Nx -> Px), multiply by the Green's spectrum, inverse x FFT (keep Nx),
+// for the Pz lines of one (b, ky); warp per line.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_conv_lines(typename V2<R>::T* __restrict__ spec, int Nx, int Py,
+                                                        int Pz, FftPlan px, const typename V2<R>::T* __restrict__ twx,
+                                                        const typename V2<R>::T* __restrict__ Ghat) {
+  typedef typename V2<R>::T C;
+  extern __shared__ unsigned char smem_raw[];
+  const int Px = px.L;
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* b0 = tx + Px;            // [kz][x]
+  C* b1 = b0 + Pz * Px;
+  const int ky = blockIdx.x, b = blockIdx.y;
+  for (int i = threadIdx.x; i < Px; i += blockDim.x) tx[i] = twx[i];
+  C* base = spec + (int64_t)b * Nx * Py * Pz + (int64_t)ky * Pz;
+  for (int i = threadIdx.x; i < Pz * Px; i += blockDim.x) {
+    const int x = i / Pz, kz = i % Pz;
+    if (x < Px) b0[kz * Px + x] = (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int kz = warp; kz < Pz; kz += nw) {
+    C* a = b0 + kz * Px;
+    C* c = b1 + kz * Px;
+    C* r = warp_fft<C, false>(a, c, px, tx, lane);
+    const C* g = Ghat + ((int64_t)ky * Pz + kz) * Px;
+    for (int i = lane; i < Px; i += 32) r[i] = cmul(r[i], g[i]);
+    __syncwarp();
+    C* other = (r == a) ? c : a;
+    warp_fft<C, true>(r, other, px, tx, lane);
+  }
+  __syncthreads();
+  // after 2 nst stages the result is back in the buffer that held the input
+  const C* out = b0;
+  for (int i = threadIdx.x; i < Pz * Nx; i += blockDim.x) {
+    const int x = i / Pz, kz = i % Pz;
+    base[(int64_t)x * Py * Pz + kz] = out[kz * Px + x];
+  }
+}
+
+// Inverse: y FFT (keep Ny) then z DFT (keep Nz) of plane (b, x).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_inv_planes(const typename V2<R>::T* __restrict__ spec, int Nx, int Ny,
+                                                        int Nz, FftPlan py, int Pz,
+                                                        const typename V2<R>::T* __restrict__ twy,
+                                                        const typename V2<R>::T* __restrict__ twz,
+                                                        typename V2<R>::T* __restrict__ grid) {
+  typedef typename V2<R>::T C;
+  extern __shared__ unsigned char smem_raw[];
+  const int Py = py.L;
+  C* ty = reinterpret_cast<C*>(smem_raw);
+  C* tz = ty + Py;
+  C* b0 = tz + Pz;
+  C* b1 = b0 + Pz * Py;
+  const int x = blockIdx.x, b = blockIdx.y;
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
+  const C* src = spec + ((int64_t)b * Nx + x) * Py * Pz;
+  for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
+    const int ky = i / Pz, kz = i % Pz;
+    b0[kz * Py + ky] = src[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int kz = warp; kz < Pz; kz += nw) warp_fft<C, true>(b0 + kz * Py, b1 + kz * Py, py, ty, lane);
+  __syncthreads();
+  const C* res = (py.nst % 2 == 0) ? b0 : b1;
+  C* dst = grid + ((int64_t)b * Nx + x) * Ny * Nz;
+  for (int i = threadIdx.x; i < Ny * Nz; i += blockDim.x) {
+    const int y = i / Nz, z = i % Nz;
+    C acc = czero<C>();
+    for (int kz = 0; kz < Pz; ++kz) {
+      C w = tz[(kz * z) % Pz];
+      w.y = -w.y;
+      acc = cadd(acc, cmul(res[kz * Py + y], w));
+    }
+    dst[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- A4: interpolation (step iii)
+// y = v - [c_A sum_{xyz} Pi.Phi + c_phi Pi_phi.Phi_phi]; one CTA per element.
+template <typename R>
+__global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+                                                int bx, int by, int bz, const int32_t* __restrict__ anc,
+                                                const R* __restrict__ Pi, const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ boxorg, int nrhs, int rc,
+                                                const typename V2<R>::T* __restrict__ grid, int Nx, int Ny, int Nz,
+                                                R cAr, R cAi, R cPr, R cPi,
+                                                const typename V2<R>::T* __restrict__ v,
+                                                typename V2<R>::T* __restrict__ y) {
+  typedef typename V2<R>::T C;
+  extern __shared__ unsigned char smem_raw[];
+  C* box = reinterpret_cast<C*>(smem_raw);  // [psi][c][node]
+  const int e = elems[blockIdx.x];
+  const int nodes = bx * by * bz;
+  const int64_t o = off[e];
+  const int gx0 = boxorg[3 * e], gy0 = boxorg[3 * e + 1], gz0 = boxorg[3 * e + 2];
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  C cA, cP;
+  cA.x = cAr; cA.y = cAi; cP.x = cPr; cP.y = cPi;
+  for (int c0 = 0; c0 < nrhs; c0 += rc) {
+    const int cn = min(rc, nrhs - c0);
+    for (int i = threadIdx.x; i < 4 * cn * nodes; i += blockDim.x) {
+      const int node = i % nodes, pc = i / nodes;
+      const int psi = pc / cn, c = pc % cn;
+      const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+      const int64_t b = (int64_t)psi * nrhs + c0 + c;
+      box[i] = grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < Nh * cn; p += blockDim.x) {
+      const int n = p / cn, c = p % cn;
+      C sA = czero<C>(), sP = czero<C>();
+      const int ax = anc[3 * n] + o1lo, ay = anc[3 * n + 1] + o1lo, az = anc[3 * n + 2] + o1lo;
+      for (int s = 0; s < S; ++s) {
+        const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+        const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
+        const R* w = Pi + ((int64_t)n * S + s) * 4;
+        const C f0 = box[(0 * cn + c) * nodes + node];
+        const C f1 = box[(1 * cn + c) * nodes + node];
+        const C f2 = box[(2 * cn + c) * nodes + node];
+        const C f3 = box[(3 * cn + c) * nodes + node];
+        sA.x += w[0] * f0.x + w[1] * f1.x + w[2] * f2.x;
+        sA.y += w[0] * f0.y + w[1] * f1.y + w[2] * f2.y;
+        sP.x += w[3] * f3.x;
+        sP.y += w[3] * f3.y;
+      }
+      const C yff = cadd(cmul(cA, sA), cmul(cP, sP));
+      const int64_t idx = (o + n) * nrhs + c0 + c;
+      y[idx] = csub(v[idx], yff);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- A5: near field
+// y[row] -= sum_k val[k] u[col[k]]; warp per row, RHS columns in passes of RC.
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col,
+                                                   const typename V2<R>::T* __restrict__ val, int nrhs,
+                                                   const typename V2<R>::T* __restrict__ u,
+                                                   typename V2<R>::T* __restrict__ y) {
+  typedef typename V2<R>::T C;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= N) return;
+  const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+  for (int c0 = 0; c0 < nrhs; c0 += RC) {
+    C acc[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[c] = czero<C>();
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const C a = val[p];
+      const int64_t cidx = (int64_t)col[p] * nrhs + c0;
+#pragma unroll
+      for (int c = 0; c < RC; ++c)
+        if (c0 + c < nrhs) {
+          const C b = u[cidx + c];
+          acc[c].x += a.x * b.x - a.y * b.y;
+          acc[c].y += a.x * b.y + a.y * b.x;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, s);
+        acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, s);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < RC; ++c)
+        if (c0 + c < nrhs) {
+          const int64_t idx = row * nrhs + c0 + c;
+          y[idx] = csub(y[idx], acc[c]);
+        }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+size_t fft_smem_bytes(const DevArray& a, int which) {
+  const size_t cs = sizeof(typename V2<R>::T);
+  const int Py = a.fft[1], Pz = a.fft[2], Px = a.fft[0];
+  if (which == 0) return cs * ((size_t)Py + Pz + 2 * (size_t)Pz * Py);
+  return cs * ((size_t)Px + 2 * (size_t)Pz * Px);
+}
+
+static int box_rc(const DevArray& a, int t, int nrhs, size_t csize, size_t limit) {
+  const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+  int rc = nrhs;
+  while (rc > 1 && 4 * rc * nodes * csize > limit) rc = (rc + 1) / 2;
+  return rc;
+}
+
+cudaError_t kernels_init(DevArray& a) {
+  const int lim = 200 * 1024;
+  cudaError_t e;
+#define MM_ATTR(K)                                                                \
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e != cudaSuccess) return e;
+  MM_ATTR(k_fft_fwd_planes<float>) MM_ATTR(k_fft_fwd_planes<double>)
+  MM_ATTR(k_fft_conv_lines<float>) MM_ATTR(k_fft_conv_lines<double>)
+  MM_ATTR(k_fft_inv_planes<float>) MM_ATTR(k_fft_inv_planes<double>)
+  MM_ATTR(k_project<float>) MM_ATTR(k_project<double>)
+  MM_ATTR(k_interp<float>) MM_ATTR(k_interp<double>)
+#undef MM_ATTR
+  (void)a;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st) {
+  typedef typename V2<R>::T C;
+  const C* x = static_cast<const C*>(xv);
+  C* y = static_cast<C*>(yv);
+  C* u = static_cast<C*>(w.u);
+  C* v = static_cast<C*>(w.v);
+  C* grid = static_cast<C*>(w.grid);
+  C* spec = static_cast<C*>(w.spec);
+  const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
+  const int Px = a.fft[0], Py = a.fft[1], Pz = a.fft[2];
+  const int B = 4 * nrhs;
+  const size_t gbytes = sizeof(C) * (size_t)B * Nx * Ny * Nz;
+  cudaError_t e = cudaMemsetAsync(grid, 0, gbytes, st);
+  if (e != cudaSuccess) return e;
+  Profiler& pr = a.prof;
+  // A1: u = M x, v = D x, per type
+  pr.begin(0, st);
+  int nl = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const int ncols = (int)(a.n_of_type[t] * nrhs);
+    dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
+    k_macro_gemm<R><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off, x, u, v);
+    ++nl;
+  }
+  pr.end(st, nl);
+  // A2: projection
+  const size_t slim = 96 * 1024;
+  pr.begin(1, st);
+  nl = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
+    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+    const size_t sm = 4 * rc * nodes * sizeof(C);
+    k_project<R><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+        a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+        p.Pi[t], a.off, a.boxorg, nrhs, rc, u, Nx, Ny, Nz, grid);
+    ++nl;
+  }
+  pr.end(st, nl);
+  // A3: FFT convolution
+  pr.begin(2, st);
+  k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
+      grid, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), spec);
+  pr.end(st, 1);
+  pr.begin(3, st);
+  k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), st>>>(
+      spec, Nx, Py, Pz, a.px, static_cast<const C*>(p.twx), static_cast<const C*>(p.Ghat));
+  pr.end(st, 1);
+  pr.begin(4, st);
+  k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
+      spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
+  pr.end(st, 1);
+  (void)Px;
+  // A4: interpolation, y = v - y_ff
+  pr.begin(5, st);
+  nl = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
+    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+    const size_t sm = 4 * rc * nodes * sizeof(C);
+    k_interp<R><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+        a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+        p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v, y);
+    ++nl;
+  }
+  pr.end(st, nl);
+  // A5: y -= G_NF u
+  if (a.nnz > 0) {
+    pr.begin(6, st);
+    const unsigned blocks = (unsigned)((a.N + 7) / 8);
+    if (nrhs == 1)
+      k_spmv_near<R, 1><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
+    else if (nrhs <= 4)
+      k_spmv_near<R, 4><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
+    else
+      k_spmv_near<R, 8><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
+    pr.end(st, 1);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t);
+template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t);
+template size_t fft_smem_bytes<float>(const DevArray&, int);
+template size_t fft_smem_bytes<double>(const DevArray&, int);
+
+}  // namespace mm

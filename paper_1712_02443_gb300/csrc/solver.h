@@ -1,0 +1,58 @@
+// Batched GMRES with FP64 Arnoldi and FP64 iterative refinement (device side).
+#pragma once
+
+#include <complex>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "macroaim.h"
+
+namespace mm {
+
+struct Status {
+  mm_status code;
+  std::string msg;
+};
+
+// Quadrature rule passed by value to kernels (at most 16 points).
+struct QuadRule {
+  int n;
+  double b0[16], b1[16], b2[16], w[16];
+};
+
+class Solver {
+ public:
+  // operators on device vectors of the current (N, r): complex128 and complex64
+  std::function<Status(const double2*, double2*, cudaStream_t)> op64;
+  std::function<Status(const void*, void*, cudaStream_t)> op32;
+  int matvecs = 0;
+  Profiler* prof = nullptr;   // optional stage profiler (Krylov kernels)
+
+  ~Solver() { release(); }
+  Status ensure(int64_t N, int r, int m);
+  void release();
+  Status solve(const double2* b, double2* x, double tol, int prec, int refine, double inner_tol, int max_iter,
+               int& iters, int& refinements, double& relres, bool& converged, cudaStream_t st);
+  size_t bytes() const { return bytes_; }
+
+ private:
+  Status apply(const double2* in, double2* out, int prec, cudaStream_t st);
+  Status dots(const double2* V, int64_t vstride, int nvec, const double2* w, double2* out, cudaStream_t st);
+  Status norms(const double2* a, std::vector<double>& out, cudaStream_t st);
+  Status gmres(const double2* b, double2* x, const std::vector<double>& tol_abs, int prec, int max_iter, int& iters,
+               std::vector<double>& res, cudaStream_t st);
+  int64_t N_ = 0;
+  int r_ = 0, m_ = 0, nblk_ = 1;
+  void *V_ = nullptr, *w_ = nullptr, *t_ = nullptr, *x32_ = nullptr, *y32_ = nullptr;
+  void *partial_ = nullptr, *h_ = nullptr, *h2_ = nullptr, *scale_ = nullptr, *active_ = nullptr, *dx_ = nullptr;
+  size_t bytes_ = 0;
+};
+
+template <typename R>
+cudaError_t rhs_planewave(const DevArray& a, const int32_t* elem_of, const double* const* geo, int nrhs,
+                          const double* th, const double* ph, const int32_t* pol, double k0, const QuadRule& q,
+                          void* V, cudaStream_t st);
+
+}  // namespace mm

@@ -1,0 +1,84 @@
+"""Writes the oracle's expected values used by the GPU parity tests and smoke().
+
+Calls only the CPU oracle (oracle/) and the seeded input generators; nothing
+here comes from the CUDA path.  Re-run after any change to the oracle's
+arithmetic:  python tests/golden/make_golden.py
+
+Files (numpy .npz, complex128):
+  c1_2x2.npz      2x2 loop array: x, y = Z_AIM x (full), V (theta=0 x-pol),
+                  E = solution of the AIM system to 1e-12, and E_dense (dense
+                  exterior operator) for reference.
+  ragged_3x5.npz  3x5 loop array, 3 right-hand sides: y (N x 3, full) for
+                  x = workloads.random_cvec(N, 0, 8, nrhs=3) (checksum stored).
+  c2_16x16.npz    16x16 loop array: sampled rows and y[rows] for
+                  x = workloads.random_cvec(N, 1, 7) (checksum stored).
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from paper_1712_02443_gb300 import workloads as wl  # noqa: E402
+from oracle.aim import AIMArray, AIMParams, BlockCache  # noqa: E402
+from oracle.gmres import gmres  # noqa: E402
+from oracle.macromodel import build_element, dense_exterior_operator, translated_rwg  # noqa: E402
+from oracle.operators import excitation  # noqa: E402
+
+K0 = 2.0 * np.pi
+H, ORDER, NNF = 0.1, 2, 3
+
+
+def _check(x):
+    """Checksum of a seeded input (the tests regenerate x from its seed)."""
+    return np.array([x.sum(), (np.abs(x) ** 2).sum()])
+
+
+def main():
+    t0 = time.time()
+    et = wl.loop_element()
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    params = AIMParams(H, ORDER, NNF, wl.DEFAULT_GRID_PHASE)
+    blocks = BlockCache([em], K0)
+    print("element", time.time() - t0)
+
+    # c1: 2x2
+    lay = wl.loop_array(2, 2)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0, blocks=blocks)
+    x = wl.random_cvec(A.n, 0, 7)
+    y = A.matvec(x)
+    V = np.concatenate([excitation(translated_rwg(em.rwg_e, o), 0.0, 0.0, 0, K0)[:, 0] for o in lay.offsets])
+    E, it, hist = gmres(A.matvec, V, tol=1e-12, restart=100, max_iter=2000)
+    Z = dense_exterior_operator([em], lay.type_of, lay.offsets, K0)
+    Ed = np.linalg.solve(Z, V)
+    np.savez_compressed(os.path.join(HERE, "c1_2x2.npz"), x=x, y=y, V=V, E=E, E_dense=Ed,
+                        offsets=lay.offsets, gmres_iters=it)
+    print("c1", time.time() - t0, "iters", it)
+
+    # ragged 3x5, 3 RHS
+    lay = wl.loop_array(3, 5)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0, blocks=blocks)
+    X = wl.random_cvec(A.n, 0, 8, nrhs=3)
+    Y = np.stack([A.matvec(X[:, j]) for j in range(3)], axis=1)
+    np.savez_compressed(os.path.join(HERE, "ragged_3x5.npz"), x_check=_check(X), y=Y, offsets=lay.offsets)
+    print("ragged", time.time() - t0)
+
+    # c2: 16x16, sampled rows
+    lay = wl.loop_array(16, 16)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0, blocks=blocks, rows_only=True)
+    x = wl.random_cvec(A.n, 1, 7)
+    g = wl.rng(1, 9)
+    rows = np.unique(np.concatenate([np.arange(8), A.n - 8 + np.arange(8), g.choice(A.n, 48, replace=False)]))
+    yr = A.matvec_rows(x, rows)
+    np.savez_compressed(os.path.join(HERE, "c2_16x16.npz"), x_check=_check(x), rows=rows, y_rows=yr)
+    print("c2", time.time() - t0)
+
+
+if __name__ == "__main__":
+    main()

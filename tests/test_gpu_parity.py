@@ -1,0 +1,149 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Expected values come from tests/golden/make_golden.py (oracle only) or are
+computed live by the oracle.  Tolerances:
+* complex128 operator: rounding only (different summation order, FFT sizes):
+  relative L2 <= 1e-11, worst element <= 1e-10 of max |y|;
+* complex64 operator: FP32 arithmetic over sums of a few hundred terms
+  (GEMM k = N^_t, ~400 near-field terms, FFT) gives ~1e-6 relative per entry;
+  the bar is relative L2 <= 2e-5 and worst element <= 1e-4 of max |y|.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1712_02443_gb300 as mm  # noqa: E402
+from paper_1712_02443_gb300 import workloads as wl  # noqa: E402
+from paper_1712_02443_gb300.arrays import loop_array  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+K0 = 2.0 * np.pi
+TOL = {mm.MM_C128: (1e-11, 1e-10), mm.MM_C64: (2e-5, 1e-4)}
+DT = {mm.MM_C128: torch.complex128, mm.MM_C64: torch.complex64}
+
+
+def _close(got, ref, prec):
+    l2, worst = TOL[prec]
+    got = np.asarray(got)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    w = np.abs(got - ref).max() / np.abs(ref).max()
+    assert rel <= l2 and w <= worst, (rel, w)
+    return rel, w
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1712_02443_gb300.build import build
+    build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = mm.mm_ctx_create(0)
+    yield c
+    mm.mm_ctx_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def c1(ctx):
+    la = loop_array(ctx, 2, 2)
+    yield la
+    la.close()
+
+
+def _apply(la, x, prec, nrhs=1):
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(DT[prec]).cuda()
+    yd = torch.empty_like(xd)
+    mm.mm_apply(la.array, nrhs, xd, yd, prec, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_c1_matvec(c1, prec):
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    assert c1.n == len(g["x"])
+    _close(_apply(c1, g["x"], prec), g["y"], prec)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_ragged_multi_rhs(ctx, c1, prec):
+    g = np.load(os.path.join(GOLD, "ragged_3x5.npz"))
+    la = loop_array(ctx, 3, 5, types=c1.types)
+    try:
+        X = wl.random_cvec(la.n, 0, 8, nrhs=3)
+        assert np.allclose([X.sum(), (np.abs(X) ** 2).sum()], g["x_check"])
+        _close(_apply(la, X, prec, nrhs=3), g["y"], prec)
+        # each column alone equals its column in the batch (same result alone and batched)
+        y1 = _apply(la, np.ascontiguousarray(X[:, 1]), prec)
+        _close(y1, g["y"][:, 1], prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_c2_full_size_sampled_rows(ctx, c1, prec):
+    """16 x 16 array (the benchmark workload), single RHS: sampled rows vs the oracle."""
+    g = np.load(os.path.join(GOLD, "c2_16x16.npz"))
+    la = loop_array(ctx, 16, 16, types=c1.types)
+    try:
+        x = wl.random_cvec(la.n, 1, 7)
+        assert np.allclose([x.sum(), (np.abs(x) ** 2).sum()], g["x_check"])
+        y = _apply(la, x, prec)
+        _close(y[g["rows"]], g["y_rows"], prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_single_element_matvec(ctx, c1, loop_model, prec):
+    """Degenerate array of one element: no coupling to other elements."""
+    from oracle.aim import AIMArray, AIMParams
+    lay = wl.loop_array(1, 1)
+    A = AIMArray([loop_model], lay.type_of, lay.offsets, AIMParams(0.1, 2, 3, wl.DEFAULT_GRID_PHASE), K0)
+    la = loop_array(ctx, 1, 1, types=c1.types)
+    try:
+        x = wl.random_cvec(la.n, 0, 11)
+        _close(_apply(la, x, prec), A.matvec(x), prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_planewave_excitation(c1, prec):
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    V = torch.empty(c1.n, dtype=DT[prec], device="cuda")
+    mm.mm_rhs_planewave(c1.array, [0.0], [0.0], [0], V, prec, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    _close(V.cpu().numpy().astype(np.complex128), g["V"], prec)
+
+
+@pytest.mark.parametrize("prec,refine", [(mm.MM_C128, 0), (mm.MM_C64, 1)])
+def test_c1_solve(c1, prec, refine):
+    """GMRES to 1e-6 (the 2x2 configuration's tolerance): solution vs the oracle's
+    1e-12 solve of the same AIM system; error <= cond * tol."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    V = torch.from_numpy(g["V"]).cuda()
+    E = torch.empty_like(V)
+    st = mm.mm_solve(c1.array, 1, V, E, tol=1e-6, restart=50, max_iter=500, precision=prec, refine=refine)
+    assert st["converged"] and st["rel_residual"] <= 1e-6
+    Eg = E.cpu().numpy()
+    err = np.linalg.norm(Eg - g["E"]) / np.linalg.norm(g["E"])
+    assert err <= 1e-4, err
+
+
+def test_apply_host_matches_device(c1):
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    x = np.ascontiguousarray(g["x"].astype(np.complex64))
+    y = np.zeros_like(x)
+    mm.mm_apply_host(c1.array, 1, x, y, mm.MM_C64)
+    _close(y.astype(np.complex128), g["y"], mm.MM_C64)
+
+
+def test_aliasing_arguments_rejected(c1):
+    x = torch.zeros(c1.n, dtype=torch.complex64, device="cuda")
+    with pytest.raises(mm.MacroAIMError) as e:
+        mm.mm_apply(c1.array, 1, x, x, mm.MM_C64)
+    assert e.value.status == mm.MM_EINVAL
