@@ -172,7 +172,9 @@ def run_ours(args, rank, world, local):
             ev[k + 1].record(st)
         torch.cuda.synchronize()
         barrier()
-    prof = mm.mm_profile_read(la.array)
+    prof = mm.mm_profile_read(la.array, mm.MM_C64)
+    prof128 = mm.mm_profile_read(la.array, mm.MM_C128)
+    prof_all = mm.mm_profile_read(la.array, -1)
     mm.mm_profile_enable(la.array, False)
     lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     t_ms = ev[0].elapsed_time(ev[-1])
@@ -223,9 +225,12 @@ def run_ours(args, rank, world, local):
             traffic = tr["per_launch_bytes"][dom]
     except Exception:
         pass
-    gpu_launches = int(sum(v["launches"] for v in prof.values()))
-    stages = {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
-                  "us_per_launch": round(1e3 * v["ms"] / max(1, v["launches"]), 2)} for k, v in prof.items()}
+    gpu_launches = int(sum(v["launches"] for v in prof_all.values()))
+
+    def table(pr):
+        return {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
+                    "us_per_launch": round(1e3 * v["ms"] / max(1, v["launches"]), 2)} for k, v in pr.items()}
+    stages = {"c64": table(prof), "c128": {k: v for k, v in table(prof128).items() if k != "krylov"}}
     out = {
         "metric": "macromodel-AIM matvecs/s and solves/s vs plain FP64 GPU form; p50/p99 latency",
         "value": round(matvecs_per_s, 1),

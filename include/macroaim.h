@@ -214,9 +214,11 @@ mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev
  * With profiling enabled, every stage of every product is bracketed by CUDA
  * events on the caller's stream (a few microseconds of host overhead per
  * stage) and kernel launches are counted.  mm_profile_read synchronises the
- * recorded events and returns per-stage totals since the last enable:
- * ms[s] = summed device time of stage s, launches[s] = kernel launches of
- * stage s (arrays of MM_STAGE_COUNT entries).  Disabled by default.          */
+ * recorded events and returns per-stage totals since the last enable, for the
+ * products at `precision` (MM_C64, MM_C128, or -1 for both; the Krylov stage
+ * is always included): ms[s] = summed device time of stage s, launches[s] =
+ * kernel launches of stage s (arrays of MM_STAGE_COUNT entries).  Disabled
+ * by default.                                                                 */
 typedef enum mm_stage {
   MM_STAGE_GEMM = 0,     /* macromodel product [M; D] x                      */
   MM_STAGE_PROJECT = 1,  /* step (i)                                         */
@@ -229,7 +231,7 @@ typedef enum mm_stage {
   MM_STAGE_COUNT = 8
 } mm_stage;
 mm_status mm_profile_enable(mm_array* array, int32_t enable);
-mm_status mm_profile_read(mm_array* array, double* ms, int64_t* launches);
+mm_status mm_profile_read(mm_array* array, int32_t precision, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

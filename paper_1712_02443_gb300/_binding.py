@@ -81,7 +81,7 @@ _SIGS = {
     "mm_rhs_planewave": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.c_int32, P]),
     "mm_solve": (ct.c_int, [P, ct.c_int32, P, P, ct.POINTER(mm_solve_opts), ct.POINTER(mm_solve_stats), P]),
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
-    "mm_profile_read": (ct.c_int, [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
 }
 
 _lib = None
@@ -272,8 +272,8 @@ def mm_profile_enable(array, enable: bool = True) -> None:
     _check(load().mm_profile_enable(array, 1 if enable else 0), _ctx_of.get(array.value))
 
 
-def mm_profile_read(array) -> dict:
+def mm_profile_read(array, precision: int = -1) -> dict:
     ms = (ct.c_double * len(STAGES))()
     nl = (ct.c_int64 * len(STAGES))()
-    _check(load().mm_profile_read(array, ms, nl), _ctx_of.get(array.value))
+    _check(load().mm_profile_read(array, precision, ms, nl), _ctx_of.get(array.value))
     return {name: {"ms": ms[i], "launches": nl[i]} for i, name in enumerate(STAGES)}

@@ -105,8 +105,18 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
     p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
   }
   {
-    std::vector<C> v(ah.val.size());
-    for (size_t i = 0; i < v.size(); ++i) { v[i].x = (R)ah.val[i].real(); v[i].y = (R)ah.val[i].imag(); }
+    // near-field values in the padded row layout of da.rowptr (pad entries are 0)
+    std::vector<C> v(da.nnz_padded);
+    for (auto& z : v) { z.x = 0; z.y = 0; }
+    int64_t q = 0;
+    for (int64_t i = 0; i < ah.N; ++i) {
+      int64_t len = ah.rowptr[i + 1] - ah.rowptr[i];
+      for (int64_t k = 0; k < len; ++k) {
+        const auto& z = ah.val[ah.rowptr[i] + k];
+        v[q + k].x = (R)z.real(); v[q + k].y = (R)z.imag();
+      }
+      q += (len + 3) / 4 * 4;
+    }
     p.val = dev_upload(v.data(), v.size(), da.bytes);
   }
   {
@@ -386,8 +396,19 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     for (int64_t e = 0; e < n_elem; ++e)
       for (int64_t n = ah.off[e]; n < ah.off[e + 1]; ++n) eof[n] = (int32_t)e;
     a->elem_of = dev_upload(eof.data(), eof.size(), acc);
-    da.rowptr = dev_upload(ah.rowptr.data(), ah.rowptr.size(), acc);
-    da.col = dev_upload(ah.col.data(), ah.col.size(), acc);
+    {
+      // rows padded to multiples of 4 entries; pad columns point at the row itself
+      std::vector<int64_t> rp(ah.N + 1, 0);
+      for (int64_t i = 0; i < ah.N; ++i) rp[i + 1] = rp[i] + (ah.rowptr[i + 1] - ah.rowptr[i] + 3) / 4 * 4;
+      std::vector<int32_t> cl(rp[ah.N]);
+      for (int64_t i = 0; i < ah.N; ++i) {
+        int64_t len = ah.rowptr[i + 1] - ah.rowptr[i];
+        for (int64_t k = 0; k < rp[i + 1] - rp[i]; ++k) cl[rp[i] + k] = k < len ? ah.col[ah.rowptr[i] + k] : (int32_t)i;
+      }
+      da.nnz_padded = rp[ah.N];
+      da.rowptr = dev_upload(rp.data(), rp.size(), acc);
+      da.col = dev_upload(cl.data(), cl.size(), acc);
+    }
     upload_precision<float>(a.get(), da.pf);
     CU(mm::kernels_init(da));
   }
@@ -634,20 +655,30 @@ mm_status mm_profile_enable(mm_array* a, int32_t enable) {
   API_CATCH(a->ctx)
 }
 
-mm_status mm_profile_read(mm_array* a, double* ms, int64_t* launches) {
-  if (!a || !ms || !launches) return MM_EINVAL;
+mm_status mm_profile_read(mm_array* a, int32_t precision, double* ms, int64_t* launches) {
+  if (!a || !ms || !launches || precision < -1 || precision > 1) return MM_EINVAL;
   if (!a->on_device) return fail(a->ctx, MM_EINVAL, "array has no device (host-only context)");
   API_TRY
   CU(cudaSetDevice(a->da.device));
+  // slots 0-7: complex64 stages and the (FP64) Krylov stage; 8-14: complex128 stages
+  auto wanted = [&](int slot) {
+    if (slot == MM_STAGE_KRYLOV) return true;
+    if (precision == MM_C64) return slot < 8;
+    if (precision == MM_C128) return slot >= 8;
+    return true;
+  };
   for (int i = 0; i < MM_STAGE_COUNT; ++i) {
     ms[i] = 0;
-    launches[i] = a->da.prof.launches[i];
+    launches[i] = 0;
   }
+  for (int slot = 0; slot < 16; ++slot)
+    if (wanted(slot)) launches[slot % 8] += a->da.prof.launches[slot];
   for (auto& r : a->da.prof.recs) {
+    if (!wanted(r.stage)) continue;
     CU(cudaEventSynchronize(r.b));
     float t = 0;
     CU(cudaEventElapsedTime(&t, r.a, r.b));
-    ms[r.stage] += t;
+    ms[r.stage % 8] += t;
   }
   return MM_OK;
   API_CATCH(a->ctx)

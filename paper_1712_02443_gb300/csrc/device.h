@@ -21,7 +21,7 @@ struct Profiler {
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  int64_t launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[16] = {0};   // slots 0-7: complex64 stages (7 = Krylov), 8-14: complex128 stages
   int open_stage = -1;
   cudaEvent_t open_ev = nullptr;
   cudaEvent_t get() {
@@ -111,8 +111,9 @@ struct DevArray {
   int32_t* type_of = nullptr;
   double* eoff = nullptr;               // n_elem x 3 element offsets
   // near field pattern (shared by both precisions)
-  int64_t* rowptr = nullptr;
+  int64_t* rowptr = nullptr;            // rows padded to multiples of 4 entries (zero values)
   int32_t* col = nullptr;
+  int64_t nnz_padded = 0;
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;

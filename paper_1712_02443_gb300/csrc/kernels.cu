@@ -72,7 +72,9 @@ FftPlan make_plan(int L) {
 
 // ---------------------------------------------------------------- A1: macromodel GEMM
 // C (2Nh x ncols) = W (2Nh x Nh) X (Nh x ncols); column c = j * nrhs + rhs of element elems[j].
-template <typename R>
+// Rows [0, Nh) go to u = M x, rows [Nh, 2Nh) to v = D x.  BM x BN tile per CTA of
+// 256 threads, each thread a TM x TN block of outputs.
+template <typename R, int BM, int BN>
 __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __restrict__ W, int Nh,
                                                     const int32_t* __restrict__ elems, int ncols, int nrhs,
                                                     const int64_t* __restrict__ off,
@@ -80,47 +82,49 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
                                                     typename V2<R>::T* __restrict__ u,
                                                     typename V2<R>::T* __restrict__ v) {
   typedef typename V2<R>::T C;
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BK = 16;
+  constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
+  __shared__ int64_t colbase[BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
   const int M2 = 2 * Nh;
-  C acc[4][4];
+  for (int c = tid; c < BN; c += 256) {
+    const int gc = col0 + c;
+    colbase[c] = gc < ncols ? off[elems[gc / nrhs]] * nrhs + gc % nrhs : -1;
+  }
+  C acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
-  // per-thread B column bases for loading
+    for (int j = 0; j < TN; ++j) acc[i][j] = czero<C>();
+  __syncthreads();
   for (int k0 = 0; k0 < Nh; k0 += BK) {
     for (int e = tid; e < BM * BK; e += 256) {
-      int r = e / BK, kk = e % BK;
-      int gr = row0 + r, gk = k0 + kk;
+      const int r = e / BK, kk = e % BK;
+      const int gr = row0 + r, gk = k0 + kk;
       As[kk][r] = (gr < M2 && gk < Nh) ? W[(int64_t)gr * Nh + gk] : czero<C>();
     }
     for (int e = tid; e < BN * BK; e += 256) {
-      int kk = e / BN, c = e % BN;
-      int gc = col0 + c, gk = k0 + kk;
-      C val = czero<C>();
-      if (gc < ncols && gk < Nh) {
-        int j = gc / nrhs, rr = gc % nrhs;
-        val = x[(off[elems[j]] + gk) * nrhs + rr];
-      }
-      Bs[kk][c] = val;
+      const int c = e % BN, kk = e / BN;
+      const int gk = k0 + kk;
+      const int64_t cb = colbase[c];
+      Bs[kk][c] = (cb >= 0 && gk < Nh) ? x[cb + (int64_t)gk * nrhs] : czero<C>();
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      C a[4], b[4];
+      C a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
           acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
         }
@@ -128,18 +132,18 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int gr = row0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    const int gr = row0 + ty * TM + i;
     if (gr >= M2) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int gc = col0 + tx * 4 + j;
-      if (gc >= ncols) continue;
-      int e = elems[gc / nrhs], rr = gc % nrhs;
+    for (int j = 0; j < TN; ++j) {
+      const int c = tx * TN + j;
+      const int64_t cb = colbase[c];
+      if (cb < 0) continue;
       if (gr < Nh)
-        u[(off[e] + gr) * nrhs + rr] = acc[i][j];
+        u[cb + (int64_t)gr * nrhs] = acc[i][j];
       else
-        v[(off[e] + gr - Nh) * nrhs + rr] = acc[i][j];
+        v[cb + (int64_t)(gr - Nh) * nrhs] = acc[i][j];
     }
   }
 }
@@ -437,7 +441,53 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
 }
 
 // ---------------------------------------------------------------- A5: near field
-// y[row] -= sum_k val[k] u[col[k]]; warp per row, RHS columns in passes of RC.
+// y[row] -= sum_k val[k] u[col[k]].  Rows are padded to multiples of 4 entries
+// (zero values), so a lane reads 4 columns with one 16-byte load and 4 values
+// with 16-byte loads.  Single RHS: warp per row.
+template <typename R>
+__global__ void __launch_bounds__(256) k_spmv_near1(int64_t N, const int64_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col,
+                                                    const typename V2<R>::T* __restrict__ val,
+                                                    const typename V2<R>::T* __restrict__ u,
+                                                    typename V2<R>::T* __restrict__ y) {
+  typedef typename V2<R>::T C;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= N) return;
+  const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+  R ar = 0, ai = 0;
+  for (int64_t p = p0 + 4 * lane; p < p1; p += 128) {
+    const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + p));
+    C v[4];
+    if (sizeof(R) == 4) {
+      const float4 a01 = __ldg(reinterpret_cast<const float4*>(val + p));
+      const float4 a23 = __ldg(reinterpret_cast<const float4*>(val + p + 2));
+      v[0].x = a01.x; v[0].y = a01.y; v[1].x = a01.z; v[1].y = a01.w;
+      v[2].x = a23.x; v[2].y = a23.y; v[3].x = a23.z; v[3].y = a23.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = val[p + q];
+    }
+    const C b0 = u[c4.x], b1 = u[c4.y], b2 = u[c4.z], b3 = u[c4.w];
+    ar += v[0].x * b0.x - v[0].y * b0.y + v[1].x * b1.x - v[1].y * b1.y;
+    ai += v[0].x * b0.y + v[0].y * b0.x + v[1].x * b1.y + v[1].y * b1.x;
+    ar += v[2].x * b2.x - v[2].y * b2.y + v[3].x * b3.x - v[3].y * b3.y;
+    ai += v[2].x * b2.y + v[2].y * b2.x + v[3].x * b3.y + v[3].y * b3.x;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, s);
+    ai += __shfl_xor_sync(0xffffffffu, ai, s);
+  }
+  if (lane == 0) {
+    C o = y[row];
+    o.x -= ar;
+    o.y -= ai;
+    y[row] = o;
+  }
+}
+
+// Several RHS: warp per row, RHS columns in passes of RC.
 template <typename R, int RC>
 __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ col,
@@ -531,21 +581,30 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   cudaError_t e = cudaMemsetAsync(grid, 0, gbytes, st);
   if (e != cudaSuccess) return e;
   Profiler& pr = a.prof;
+  const int sb = sizeof(R) == 8 ? 8 : 0;   // profiler slot base of this precision
   // A1: u = M x, v = D x, per type
-  pr.begin(0, st);
+  pr.begin(sb + 0, st);
   int nl = 0;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
     const int Nh = (int)a.Nh[t];
     const int ncols = (int)(a.n_of_type[t] * nrhs);
-    dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
-    k_macro_gemm<R><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off, x, u, v);
+    const int64_t big = (int64_t)((2 * Nh + 63) / 64) * ((ncols + 63) / 64);
+    if (big >= 2 * 152) {
+      dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
+      k_macro_gemm<R, 64, 64><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off,
+                                                 x, u, v);
+    } else {
+      dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
+      k_macro_gemm<R, 32, 32><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off,
+                                                 x, u, v);
+    }
     ++nl;
   }
   pr.end(st, nl);
   // A2: projection
   const size_t slim = 96 * 1024;
-  pr.begin(1, st);
+  pr.begin(sb + 1, st);
   nl = 0;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
@@ -559,21 +618,21 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   }
   pr.end(st, nl);
   // A3: FFT convolution
-  pr.begin(2, st);
+  pr.begin(sb + 2, st);
   k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
       grid, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), spec);
   pr.end(st, 1);
-  pr.begin(3, st);
+  pr.begin(sb + 3, st);
   k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), st>>>(
       spec, Nx, Py, Pz, a.px, static_cast<const C*>(p.twx), static_cast<const C*>(p.Ghat));
   pr.end(st, 1);
-  pr.begin(4, st);
+  pr.begin(sb + 4, st);
   k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
       spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
   pr.end(st, 1);
   (void)Px;
   // A4: interpolation, y = v - y_ff
-  pr.begin(5, st);
+  pr.begin(sb + 5, st);
   nl = 0;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
@@ -588,10 +647,10 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   pr.end(st, nl);
   // A5: y -= G_NF u
   if (a.nnz > 0) {
-    pr.begin(6, st);
+    pr.begin(sb + 6, st);
     const unsigned blocks = (unsigned)((a.N + 7) / 8);
     if (nrhs == 1)
-      k_spmv_near<R, 1><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
+      k_spmv_near1<R><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), u, y);
     else if (nrhs <= 4)
       k_spmv_near<R, 4><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
     else

@@ -198,10 +198,13 @@ Status Solver::apply(const Z* in, Z* out, int prec, cudaStream_t st) {
   return {MM_OK, ""};
 }
 
-// Restarted GMRES on A x = b (x accumulates; starts from the given x).
-// tol_abs[j]: absolute residual target of column j.  Returns iterations used.
-Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int prec, int max_iter, int& iters,
-                     std::vector<double>& res, cudaStream_t st) {
+// Restarted GMRES on A x = b; x accumulates.  x_zero: x is 0 on entry, so the
+// first residual is b itself (no product).  A cycle stops at the restart length
+// or when every column's Givens residual estimate meets tol_abs; in the latter
+// case GMRES returns (the caller checks the true residual).  tol_abs[j] is the
+// absolute residual target of column j.
+Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& tol_abs, int prec, int max_iter,
+                     int& iters, std::vector<double>& res, cudaStream_t st) {
   const int64_t N = N_;
   const int r = r_, m = m_;
   const int64_t n = N * r;
@@ -214,15 +217,21 @@ Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int p
   res.assign(r, 0.0);
   std::vector<std::complex<double>> Hh((size_t)(m + 1) * m * r), cs((size_t)m * r), sn((size_t)m * r),
       g((size_t)(m + 1) * r);
-  std::vector<Z> hbuf((size_t)(m + 1) * r), h2buf(r);
+  std::vector<Z> hbuf((size_t)(m + 1) * r), hb2((size_t)(m + 1) * r);
   std::vector<int32_t> active(r), kdone(r);
   std::vector<double> sc(r);
+  bool first = true;
   for (;;) {
     // r0 = b - A x
-    Status s = apply(x, w, prec, st);
-    if (s.code != MM_OK) return s;
-    k_sub<<<grid_for(n), 256, 0, st>>>(b, w, n, w);
-    s = dots(w, 0, 1, w, h, st);
+    if (first && x_zero) {
+      MM_CK(cudaMemcpyAsync(w, b, sizeof(Z) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      Status s0 = apply(x, w, prec, st);
+      if (s0.code != MM_OK) return s0;
+      k_sub<<<grid_for(n), 256, 0, st>>>(b, w, n, w);
+    }
+    first = false;
+    Status s = dots(w, 0, 1, w, h, st);
     if (s.code != MM_OK) return s;
     MM_CK(cudaMemcpyAsync(hbuf.data(), h, sizeof(Z) * r, cudaMemcpyDeviceToHost, st));
     MM_CK(cudaStreamSynchronize(st));
@@ -242,8 +251,8 @@ Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int p
     MM_CK(cudaMemcpyAsync(scale_, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
     MM_CK(cudaMemcpyAsync(active_, active.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, st));
     k_scale_cols<<<grid_for(n), 256, 0, st>>>(w, static_cast<double*>(scale_), static_cast<int32_t*>(active_), N, r, V);
-    int k = 0;
-    for (; k < m && iters < max_iter; ++k) {
+    bool all_met = false;
+    for (int k = 0; k < m && iters < max_iter; ++k) {
       s = apply(V + (int64_t)k * vs, w, prec, st);
       if (s.code != MM_OK) return s;
       // classical Gram-Schmidt, twice
@@ -260,7 +269,6 @@ Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int p
       s = dots(w, 0, 1, w, h2 + (size_t)(k + 1) * r, st);
       if (s.code != MM_OK) return s;
       MM_CK(cudaMemcpyAsync(hbuf.data(), h, sizeof(Z) * (size_t)(k + 1) * r, cudaMemcpyDeviceToHost, st));
-      std::vector<Z> hb2((size_t)(k + 2) * r);
       MM_CK(cudaMemcpyAsync(hb2.data(), h2, sizeof(Z) * (size_t)(k + 2) * r, cudaMemcpyDeviceToHost, st));
       MM_CK(cudaStreamSynchronize(st));
       ++iters;
@@ -304,7 +312,7 @@ Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int p
         }
       }
       if (!still) {
-        ++k;
+        all_met = true;
         break;
       }
       MM_CK(cudaMemcpyAsync(scale_, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
@@ -329,9 +337,14 @@ Status Solver::gmres(const Z* b, Z* x, const std::vector<double>& tol_abs, int p
     }
     if (kmax > 0) {
       MM_CK(cudaMemcpyAsync(h, y.data(), sizeof(Z) * (size_t)kmax * r, cudaMemcpyHostToDevice, st));
+      if (prof) prof->begin(7, st);
       k_add_basis<<<grid_for(n), 256, 0, st>>>(V, vs, h, kmax, N, r, x);
+      if (prof) prof->end(st, 1);
       MM_CK(cudaGetLastError());
     }
+    // the synchronous copy of y must complete before the host vector goes away
+    MM_CK(cudaStreamSynchronize(st));
+    if (all_met || iters >= max_iter) return {MM_OK, ""};
   }
 }
 
@@ -353,55 +366,57 @@ Status Solver::solve(const Z* b, Z* x, double tol, int prec, int refine, double 
   iters = 0;
   refinements = 0;
   matvecs = 0;
-  std::vector<double> bn;
+  std::vector<double> bn, rn, res;
   Status s = norms(b, bn, st);
   if (s.code != MM_OK) return s;
   MM_CK(cudaMemsetAsync(x, 0, sizeof(Z) * n, st));
-  std::vector<double> res;
+  Z* rr = static_cast<Z*>(t_);
+  auto done = [&]() {
+    bool d = true;
+    for (int j = 0; j < r_; ++j) d &= rn[j] <= tol * bn[j];
+    return d;
+  };
   if (prec == MM_C128 || !refine) {
+    // plain GMRES at one precision; the true residual (same precision) confirms each exit
     std::vector<double> tabs(r_);
     for (int j = 0; j < r_; ++j) tabs[j] = tol * bn[j];
-    int it = 0;
-    s = gmres(b, x, tabs, prec, max_iter, it, res, st);
-    if (s.code != MM_OK) return s;
-    iters = it;
-  } else {
-    // FP64 iterative refinement: residual with the complex128 operator, correction
-    // from GMRES on the complex64 operator.
-    Z* rr = static_cast<Z*>(t_);
-    Z* dx = static_cast<Z*>(dx_);
+    bool x_zero = true;
     for (;;) {
-      s = apply(x, rr, MM_C128, st);
-      if (s.code != MM_OK) break;
+      int it = 0;
+      s = gmres(b, x, x_zero, tabs, prec, max_iter - iters, it, res, st);
+      if (s.code != MM_OK) return s;
+      iters += it;
+      x_zero = false;
+      s = apply(x, rr, prec, st);
+      if (s.code != MM_OK) return s;
       k_sub<<<grid_for(n), 256, 0, st>>>(b, rr, n, rr);
-      std::vector<double> rn;
       s = norms(rr, rn, st);
-      if (s.code != MM_OK) break;
-      bool done = true;
-      for (int j = 0; j < r_; ++j) done &= rn[j] <= tol * bn[j];
-      if (done || iters >= max_iter) break;
-      ++refinements;
+      if (s.code != MM_OK) return s;
+      if (done() || iters >= max_iter || it == 0) break;
+    }
+  } else {
+    // FP64 iterative refinement: GMRES on the complex64 operator solves for the
+    // correction of the current residual, computed with the complex128 operator.
+    Z* dx = static_cast<Z*>(dx_);
+    MM_CK(cudaMemcpyAsync(rr, b, sizeof(Z) * n, cudaMemcpyDeviceToDevice, st));
+    rn = bn;
+    for (;;) {
       std::vector<double> tabs(r_);
       for (int j = 0; j < r_; ++j) tabs[j] = std::max(inner_tol * rn[j], 0.5 * tol * bn[j]);
-      cudaMemsetAsync(dx, 0, sizeof(Z) * n, st);
       int it = 0;
-      // GMRES overwrites its work vectors but not rr; keep rr as the right-hand side
-      s = gmres(rr, dx, tabs, MM_C64, max_iter - iters, it, res, st);
-      if (s.code != MM_OK) break;
+      s = gmres(rr, dx, true, tabs, MM_C64, max_iter - iters, it, res, st);
+      if (s.code != MM_OK) return s;
       iters += it;
+      ++refinements;
       k_add<<<grid_for(n), 256, 0, st>>>(dx, n, x);
-      if (it == 0) break;
+      s = apply(x, rr, MM_C128, st);
+      if (s.code != MM_OK) return s;
+      k_sub<<<grid_for(n), 256, 0, st>>>(b, rr, n, rr);
+      s = norms(rr, rn, st);
+      if (s.code != MM_OK) return s;
+      if (done() || iters >= max_iter || it == 0) break;
     }
-    if (s.code != MM_OK) return s;
   }
-  // final true residual with the complex128 operator
-  Z* rr = static_cast<Z*>(t_);
-  s = apply(x, rr, MM_C128, st);
-  if (s.code != MM_OK) return s;
-  k_sub<<<grid_for(n), 256, 0, st>>>(b, rr, n, rr);
-  std::vector<double> rn;
-  s = norms(rr, rn, st);
-  if (s.code != MM_OK) return s;
   relres = 0;
   converged = true;
   for (int j = 0; j < r_; ++j) {

@@ -41,8 +41,8 @@ class Solver {
   Status apply(const double2* in, double2* out, int prec, cudaStream_t st);
   Status dots(const double2* V, int64_t vstride, int nvec, const double2* w, double2* out, cudaStream_t st);
   Status norms(const double2* a, std::vector<double>& out, cudaStream_t st);
-  Status gmres(const double2* b, double2* x, const std::vector<double>& tol_abs, int prec, int max_iter, int& iters,
-               std::vector<double>& res, cudaStream_t st);
+  Status gmres(const double2* b, double2* x, bool x_zero, const std::vector<double>& tol_abs, int prec, int max_iter,
+               int& iters, std::vector<double>& res, cudaStream_t st);
   int64_t N_ = 0;
   int r_ = 0, m_ = 0, nblk_ = 1;
   void *V_ = nullptr, *w_ = nullptr, *t_ = nullptr, *x32_ = nullptr, *y32_ = nullptr;
