@@ -404,6 +404,7 @@ Status Solver::solve(const Z* b, Z* x, double tol, int prec, int refine, double 
       std::vector<double> tabs(r_);
       for (int j = 0; j < r_; ++j) tabs[j] = std::max(inner_tol * rn[j], 0.5 * tol * bn[j]);
       int it = 0;
+      MM_CK(cudaMemsetAsync(dx, 0, sizeof(Z) * n, st));
       s = gmres(rr, dx, true, tabs, MM_C64, max_iter - iters, it, res, st);
       if (s.code != MM_OK) return s;
       iters += it;
