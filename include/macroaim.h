@@ -210,6 +210,34 @@ typedef struct mm_solve_stats {
 mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev, const mm_solve_opts* opts,
                    mm_solve_stats* stats, void* stream);
 
+/* ------------------------------------------------- allocation-free product
+ * The same product as mm_apply, for callers that cannot allocate device
+ * memory: code running inside a framework that has reserved all device
+ * memory for its own pool, real-time loops where a cudaMalloc would stall or
+ * synchronise the device, or kernels issued from a thread that must not touch
+ * the allocator.  The paper has no counterpart; this is a library service.
+ *
+ * Instead of the array's work buffers it uses one scratch array of at most
+ * 16 MiB that lives in the library's device image (every GPU that loads the
+ * library holds it until the process exits).  The caller still passes x_dev
+ * and y_dev.  The call allocates nothing: no cudaMalloc, cudaFree or other
+ * allocating routine.  Requirements and limits:
+ *  - the scratch must hold u, v (N^ x nrhs each), the 4 nrhs grids and the
+ *    partial spectra at `precision`; larger requests return MM_EINVAL with
+ *    the bytes needed (the 16x16 loop array fits at either precision);
+ *  - the complex64 operator is resident from mm_array_create; the complex128
+ *    operator is uploaded by the first mm_apply or mm_solve at complex128, so
+ *    call one of those first or this returns MM_EINVAL;
+ *  - the first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress, once per device, with that device current); make
+ *    that first call before any stream capture;
+ *  - every call shares the one scratch array and leaves its contents behind;
+ *    calls that overlap on the GPU (other streams, other arrays, other
+ *    threads) race on it: serialise them;
+ *  - stage profiling is suspended during the call.                             */
+mm_status mm_apply_noalloc(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
+                           void* stream);
+
 /* ----------------------------------------------------------- profiling
  * With profiling enabled, every stage of every product is bracketed by CUDA
  * events on the caller's stream (a few microseconds of host overhead per

@@ -78,6 +78,7 @@ _SIGS = {
     "mm_array_destroy": (None, [P]),
     "mm_apply": (ct.c_int, [P, ct.c_int32, P, P, ct.c_int32, P]),
     "mm_apply_host": (ct.c_int, [P, ct.c_int32, P, P, ct.c_int32]),
+    "mm_apply_noalloc": (ct.c_int, [P, ct.c_int32, P, P, ct.c_int32, P]),
     "mm_rhs_planewave": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.c_int32, P]),
     "mm_solve": (ct.c_int, [P, ct.c_int32, P, P, ct.POINTER(mm_solve_opts), ct.POINTER(mm_solve_stats), P]),
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
@@ -241,6 +242,12 @@ def mm_array_destroy(array) -> None:
 
 def mm_apply(array, nrhs: int, x_dev, y_dev, precision: int, stream=None) -> None:
     _check(load().mm_apply(array, nrhs, _ptr(x_dev), _ptr(y_dev), precision, _stream(stream)),
+           _ctx_of.get(array.value))
+
+
+def mm_apply_noalloc(array, nrhs: int, x_dev, y_dev, precision: int, stream=None) -> None:
+    """mm_apply without any device allocation (shared static scratch of at most 16 MiB)."""
+    _check(load().mm_apply_noalloc(array, nrhs, _ptr(x_dev), _ptr(y_dev), precision, _stream(stream)),
            _ctx_of.get(array.value))
 
 

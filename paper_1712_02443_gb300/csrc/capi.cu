@@ -3,7 +3,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -685,3 +687,70 @@ mm_status mm_profile_read(mm_array* a, int32_t precision, double* ms, int64_t* l
 }
 
 }  // extern "C"
+
+// ---- allocation-free product ---------------------------------------------------
+// Scratch for mm_apply_noalloc: a static device array in this translation unit.
+// Host code must not take its address directly (that is a host-side stand-in);
+// the device address comes from cudaGetSymbolAddress, looked up once per device.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mutex;
+std::map<int, void*> g_noalloc_ptr;
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
+                                      void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !x_dev || !y_dev || x_dev == y_dev) return fail(ctx, MM_EINVAL, "invalid apply arguments");
+  if (precision != MM_C64 && precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (precision == MM_C128 && !a->da.pd.ready)
+    return fail(ctx, MM_EINVAL,
+                "complex128 operator not resident: call mm_apply or mm_solve at complex128 once before");
+  const auto& da = a->da;
+  const size_t cs = precision == MM_C128 ? 16 : 8;
+  const size_t vec = align256(cs * (size_t)da.N * nrhs);
+  const size_t grid = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2]);
+  const size_t spec = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2]);
+  const size_t need = 2 * vec + grid + spec;
+  if (need > kNoAllocScratchBytes)
+    return fail(ctx, MM_EINVAL,
+                "mm_apply_noalloc needs " + std::to_string(need) + " bytes of scratch; the static maximum is " +
+                    std::to_string(kNoAllocScratchBytes) + " bytes (use mm_apply)");
+  cudaError_t e = cudaSetDevice(da.device);
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    auto it = g_noalloc_ptr.find(da.device);
+    if (it == g_noalloc_ptr.end()) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(ctx, MM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      it = g_noalloc_ptr.emplace(da.device, p).first;
+    }
+    base = static_cast<unsigned char*>(it->second);
+  }
+  mm::Work w;
+  w.nrhs = nrhs;
+  w.u = base;
+  w.v = base + vec;
+  w.grid = base + 2 * vec;
+  w.spec = base + 2 * vec + grid;
+  w.bytes = need;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool prof_on = a->da.prof.on;
+  a->da.prof.on = false;   // profiling creates CUDA events
+  if (precision == MM_C64)
+    e = mm::matvec<float>(a->da, a->da.pf, w, nrhs, x_dev, y_dev, st);
+  else
+    e = mm::matvec<double>(a->da, a->da.pd, w, nrhs, x_dev, y_dev, st);
+  a->da.prof.on = prof_on;
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("matvec: ") + cudaGetErrorString(e));
+  return MM_OK;
+}
