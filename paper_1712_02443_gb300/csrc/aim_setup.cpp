@@ -79,6 +79,33 @@ int64_t fft_good_length(int64_t n) {
   return m;
 }
 
+// Padded length for the device's shared-memory Stockham FFT: the 2,3,5,7-smooth
+// length in [n, 2n] with the lowest modelled cost L * sum over stages of a
+// per-radix weight (radices taken as 4s first, then 2, 3, 5, 7).
+int64_t fft_fast_length(int64_t n) {
+  n = std::max<int64_t>(n, 1);
+  int64_t best = fft_good_length(n);
+  double best_cost = 1e300;
+  for (int64_t L = n; L <= 2 * n; ++L) {
+    if (!fft_length_ok(L)) continue;
+    int64_t m = L;
+    double w = 0;
+    for (int r : {4, 2, 3, 5, 7}) {
+      const double wr = r == 4 ? 1.25 : r == 2 ? 1.0 : r == 3 ? 1.6 : r == 5 ? 2.6 : 3.6;
+      while (m % r == 0) {
+        m /= r;
+        w += wr + 0.3;
+      }
+    }
+    const double cost = (double)L * w;
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = L;
+    }
+  }
+  return best;
+}
+
 // ---- stencils and weights ------------------------------------------------------
 std::vector<int> stencil_1d(int order) {
   int n = order + 1;
@@ -235,7 +262,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
   }
   for (int a = 0; a < 3; ++a) {
     ah.grid[a] = hi[a] - lo[a] + 1;
-    ah.fft[a] = fft_good_length(2 * ah.grid[a] - 1);
+    ah.fft[a] = a < 2 ? fft_fast_length(2 * ah.grid[a] - 1) : fft_good_length(2 * ah.grid[a] - 1);
     ah.lo[a] = lo[a];
   }
   ah.base.assign(3 * ne, 0);

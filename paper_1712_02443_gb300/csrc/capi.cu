@@ -101,9 +101,13 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
       W[Nh * Nh + i].x = (R)tm.D[i].real(); W[Nh * Nh + i].y = (R)tm.D[i].imag();
     }
     p.W[t] = dev_upload(W.data(), W.size(), da.bytes);
+    // device layout [s][n][4]: consecutive bases of one stencil node are contiguous
     const auto& Pi = ah.tai[t].Pi;
+    const int S = ah.tai[t].S;
     std::vector<R> P(Pi.size());
-    for (size_t i = 0; i < Pi.size(); ++i) P[i] = (R)Pi[i];
+    for (int64_t n = 0; n < Nh; ++n)
+      for (int sn = 0; sn < S; ++sn)
+        for (int c = 0; c < 4; ++c) P[((size_t)sn * Nh + n) * 4 + c] = (R)Pi[((size_t)n * S + sn) * 4 + c];
     p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
   }
   {
@@ -193,6 +197,8 @@ mm_array::~mm_array() {
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
   for (auto* p : da.elems) cudaFree(p);
+  for (auto* p : da.inv_ptr) cudaFree(p);
+  for (auto* p : da.inv_ent) cudaFree(p);
   for (void* q : {(void*)da.off, (void*)da.boxorg, (void*)da.type_of, (void*)da.eoff, (void*)da.rowptr,
                   (void*)da.col, (void*)elem_of, (void*)geo_ptrs, (void*)d_ang, (void*)d_pol, hx, hy})
     if (q) cudaFree(q);
@@ -381,6 +387,26 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
       gptr[t] = da.geo.back();
       da.elems.push_back(dev_upload(elems[t].data(), elems[t].size(), acc));
       da.n_of_type.push_back((int64_t)elems[t].size());
+      {
+        // inverse stencil lists: for each node of the type's box, the (basis, stencil node) pairs touching it
+        const int bx = (int)ta.box_dim[0], by = (int)ta.box_dim[1], bz = (int)ta.box_dim[2];
+        const int nodes = bx * by * bz, n1 = da.n1, S = da.S;
+        if (Nh >= 65536 || S >= 65536) throw mm::Error{MM_EINVAL, "element type too large for the projection lists"};
+        std::vector<std::vector<int32_t>> lists(nodes);
+        for (int64_t n = 0; n < Nh; ++n)
+          for (int sn = 0; sn < S; ++sn) {
+            const int ix = sn % n1, iy = (sn / n1) % n1, iz = sn / (n1 * n1);
+            const int x = anc[3 * n] + da.o1lo + ix, y = anc[3 * n + 1] + da.o1lo + iy, z = anc[3 * n + 2] + da.o1lo + iz;
+            lists[(x * by + y) * bz + z].push_back((int32_t)(n | (sn << 16)));
+          }
+        std::vector<int32_t> ptr(nodes + 1, 0), ent;
+        for (int q = 0; q < nodes; ++q) {
+          ptr[q + 1] = ptr[q] + (int32_t)lists[q].size();
+          ent.insert(ent.end(), lists[q].begin(), lists[q].end());
+        }
+        da.inv_ptr.push_back(dev_upload(ptr.data(), ptr.size(), acc));
+        da.inv_ent.push_back(dev_upload(ent.data(), ent.size(), acc));
+      }
     }
     a->geo_ptrs = dev_upload(gptr.data(), gptr.size(), acc);
     da.off = dev_upload(ah.off.data(), ah.off.size(), acc);

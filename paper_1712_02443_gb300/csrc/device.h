@@ -74,7 +74,7 @@ template <typename R>
 struct DevPrec {
   bool ready = false;
   std::vector<void*> W;   // per type: stacked [M_t; D_t], 2 Nh x Nh complex, row-major
-  std::vector<R*> Pi;     // per type: Nh x S x 4 projection weights
+  std::vector<R*> Pi;     // per type: S x Nh x 4 projection weights (stencil node outermost)
   void* val = nullptr;    // near-field values (nnz complex)
   void* Ghat = nullptr;   // Green's spectrum [ky][kz][kx] complex, divided by Px Py Pz
   void* twx = nullptr;    // exp(-2 pi i k / Px), k < Px
@@ -104,6 +104,8 @@ struct DevArray {
   std::vector<int32_t*> anc;            // per type: Nh x 3 box-local anchors
   std::vector<double*> geo;             // per type: Nh x 13 (pa, pb, p+, p-, length), local coordinates
   std::vector<int32_t*> elems;          // per type: element ids of that type
+  std::vector<int32_t*> inv_ptr;        // per type: box node -> first stencil entry touching it (nodes + 1)
+  std::vector<int32_t*> inv_ent;        // per type: stencil entries n | (s << 16), grouped by box node
   std::vector<int64_t> n_of_type;
   // per element
   int64_t* off = nullptr;               // n_elem + 1

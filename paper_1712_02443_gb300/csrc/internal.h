@@ -122,5 +122,6 @@ void build_type(TypeModel& tm);
 void fft_inplace(std::vector<cd>& a, int64_t n, int64_t stride, int64_t count, int64_t dist, int sign);
 bool fft_length_ok(int64_t n);
 int64_t fft_good_length(int64_t n);
+int64_t fft_fast_length(int64_t n);
 
 }  // namespace mm

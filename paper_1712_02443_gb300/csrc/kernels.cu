@@ -61,7 +61,7 @@ FftPlan make_plan(int L) {
   FftPlan p;
   p.L = L;
   int n = L;
-  for (int r : {8, 4, 2, 3, 5, 7})
+  for (int r : {4, 2, 3, 5, 7})
     while (n % r == 0 && p.nst < 16) {
       p.rad[p.nst++] = r;
       n /= r;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
       As[kk][r] = (gr < M2 && gk < Nh) ? W[(int64_t)gr * Nh + gk] : czero<C>();
     }
     for (int e = tid; e < BN * BK; e += 256) {
-      const int c = e % BN, kk = e / BN;
+      const int kk = e % BK, c = e / BK;   // lanes run along k: one element's vector is contiguous
       const int gk = k0 + kk;
       const int64_t cb = colbase[c];
       Bs[kk][c] = (cb >= 0 && gk < Nh) ? x[cb + (int64_t)gk * nrhs] : czero<C>();
@@ -149,57 +149,80 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
 }
 
 // ---------------------------------------------------------------- A2: projection (step i)
-// One CTA per element; the element's stencil box (bx x by x bz nodes) for all
-// psi and a chunk of RHS lives in shared memory.
-template <typename R>
-__global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
-                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
-                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
-                                                 const int32_t* __restrict__ boxorg, int nrhs, int rc,
-                                                 const typename V2<R>::T* __restrict__ u, int Nx, int Ny, int Nz,
-                                                 typename V2<R>::T* __restrict__ grid) {
+// One CTA per element.  Each thread owns nodes of the element's stencil box and
+// gathers the (basis, stencil node) contributions listed for that node (lists
+// precomputed per type), so there are no shared-memory atomics; the box is
+// then added into the global grids (neighbouring boxes overlap: atomics).
+template <typename C> __device__ __forceinline__ void atomic_add_c(C* p, C v);
+template <> __device__ __forceinline__ void atomic_add_c<float2>(float2* p, float2 v) { atomicAdd(p, v); }
+template <> __device__ __forceinline__ void atomic_add_c<double2>(double2* p, double2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+template <typename R> struct W4;
+template <> struct W4<float> {
+  typedef float4 T;
+  static __device__ __forceinline__ float4 load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+};
+template <> struct W4<double> {
+  struct T { double x, y, z, w; };
+  static __device__ __forceinline__ T load(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return T{a.x, a.y, b.x, b.y};
+  }
+};
+
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+                                                 const int32_t* __restrict__ inv_ptr,
+                                                 const int32_t* __restrict__ inv_ent, const R* __restrict__ Pi,
+                                                 const int64_t* __restrict__ off, const int32_t* __restrict__ boxorg,
+                                                 int nrhs, const typename V2<R>::T* __restrict__ u, int Nx, int Ny,
+                                                 int Nz, typename V2<R>::T* __restrict__ grid) {
   typedef typename V2<R>::T C;
   extern __shared__ unsigned char smem_raw[];
-  R* box = reinterpret_cast<R*>(smem_raw);  // [psi][c][node][re/im]
+  C* us = reinterpret_cast<C*>(smem_raw);  // [n][c] element's u for this RHS chunk
   const int e = elems[blockIdx.x];
   const int nodes = bx * by * bz;
   const int64_t o = off[e];
   const int gx0 = boxorg[3 * e], gy0 = boxorg[3 * e + 1], gz0 = boxorg[3 * e + 2];
   const int64_t gstride = (int64_t)Nx * Ny * Nz;
-  for (int c0 = 0; c0 < nrhs; c0 += rc) {
-    const int cn = min(rc, nrhs - c0);
-    for (int i = threadIdx.x; i < 4 * cn * nodes * 2; i += blockDim.x) box[i] = 0;
-    __syncthreads();
-    for (int p = threadIdx.x; p < Nh * S; p += blockDim.x) {
-      const int n = p / S, s = p % S;
-      const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
-      const int nx = anc[3 * n] + o1lo + ix, ny = anc[3 * n + 1] + o1lo + iy, nz = anc[3 * n + 2] + o1lo + iz;
-      const int node = (nx * by + ny) * bz + nz;
-      const R* w = Pi + ((int64_t)n * S + s) * 4;
-      const R w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
-      for (int c = 0; c < cn; ++c) {
-        const C uv = u[(o + n) * nrhs + c0 + c];
-        R* b0 = box + 2 * ((0 * cn + c) * nodes + node);
-        R* b1 = box + 2 * ((1 * cn + c) * nodes + node);
-        R* b2 = box + 2 * ((2 * cn + c) * nodes + node);
-        R* b3 = box + 2 * ((3 * cn + c) * nodes + node);
-        atomicAdd(b0, w0 * uv.x); atomicAdd(b0 + 1, w0 * uv.y);
-        atomicAdd(b1, w1 * uv.x); atomicAdd(b1 + 1, w1 * uv.y);
-        atomicAdd(b2, w2 * uv.x); atomicAdd(b2 + 1, w2 * uv.y);
-        atomicAdd(b3, w3 * uv.x); atomicAdd(b3 + 1, w3 * uv.y);
-      }
+  for (int c0 = 0; c0 < nrhs; c0 += RC) {
+    const int cn = min(RC, nrhs - c0);
+    for (int i = threadIdx.x; i < Nh * RC; i += blockDim.x) {
+      const int n = i / RC, c = i % RC;
+      us[i] = c < cn ? u[(o + n) * nrhs + c0 + c] : czero<C>();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * cn * nodes; i += blockDim.x) {
-      const int node = i % nodes, pc = i / nodes;
-      const int psi = pc / cn, c = pc % cn;
+    for (int node = threadIdx.x; node < nodes; node += blockDim.x) {
+      C acc[4][RC];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < RC; ++c) acc[q][c] = czero<C>();
+      const int q0 = inv_ptr[node], q1 = inv_ptr[node + 1];
+      if (q0 == q1) continue;
+      for (int q = q0; q < q1; ++q) {
+        const int ent = __ldg(inv_ent + q);
+        const int n = ent & 0xffff, sn = ent >> 16;
+        const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)sn * Nh + n) * 4);
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+          const C uv = us[n * RC + c];
+          acc[0][c].x += w.x * uv.x; acc[0][c].y += w.x * uv.y;
+          acc[1][c].x += w.y * uv.x; acc[1][c].y += w.y * uv.y;
+          acc[2][c].x += w.z * uv.x; acc[2][c].y += w.z * uv.y;
+          acc[3][c].x += w.w * uv.x; acc[3][c].y += w.w * uv.y;
+        }
+      }
       const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
-      const R re = box[2 * i], im = box[2 * i + 1];
-      if (re == 0 && im == 0) continue;
-      const int64_t b = (int64_t)psi * nrhs + c0 + c;
-      R* g = reinterpret_cast<R*>(grid + b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz));
-      atomicAdd(g, re);
-      atomicAdd(g + 1, im);
+      const int64_t gidx = ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+          if (c < cn) atomic_add_c(grid + ((int64_t)q * nrhs + c0 + c) * gstride + gidx, acc[q][c]);
     }
     __syncthreads();
   }
@@ -212,28 +235,45 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
   const int nb = L / RADIX;
   const int st = L / (Ns * RADIX);
   const int stR = L / RADIX;
+  C wr[RADIX];   // roots of unity of order RADIX (conjugated for the inverse)
+#pragma unroll
+  for (int m = 0; m < RADIX; ++m) {
+    wr[m] = tw[m * stR];
+    if (INV) wr[m].y = -wr[m].y;
+  }
   for (int j = lane; j < nb; j += nlanes) {
     const int k = j % Ns;
     C v[RADIX];
 #pragma unroll
     for (int q = 0; q < RADIX; ++q) v[q] = a[j + q * nb];
-#pragma unroll
-    for (int q = 1; q < RADIX; ++q) {
-      C w = tw[q * k * st];
-      if (INV) w.y = -w.y;
-      v[q] = cmul(v[q], w);
-    }
-    const int base = (j / Ns) * Ns * RADIX + k;
-#pragma unroll
-    for (int p = 0; p < RADIX; ++p) {
-      C acc = v[0];
+    if (k != 0) {
 #pragma unroll
       for (int q = 1; q < RADIX; ++q) {
-        C w = tw[((p * q) % RADIX) * stR];
+        C w = tw[q * k * st];
         if (INV) w.y = -w.y;
-        acc = cadd(acc, cmul(v[q], w));
+        v[q] = cmul(v[q], w);
       }
-      b[base + p * Ns] = acc;
+    }
+    const int base = (j / Ns) * Ns * RADIX + k;
+    if (RADIX == 2) {
+      b[base] = cadd(v[0], v[1]);
+      b[base + Ns] = csub(v[0], v[1]);
+    } else if (RADIX == 4) {
+      const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+      C jb1;   // -i*b1 forward, +i*b1 inverse
+      if (INV) { jb1.x = -b1.y; jb1.y = b1.x; } else { jb1.x = b1.y; jb1.y = -b1.x; }
+      b[base] = cadd(a0, b0);
+      b[base + Ns] = cadd(a1, jb1);
+      b[base + 2 * Ns] = csub(a0, b0);
+      b[base + 3 * Ns] = csub(a1, jb1);
+    } else {
+#pragma unroll
+      for (int p = 0; p < RADIX; ++p) {
+        C acc = v[0];
+#pragma unroll
+        for (int q = 1; q < RADIX; ++q) acc = cadd(acc, cmul(v[q], wr[(p * q) % RADIX]));
+        b[base + p * Ns] = acc;
+      }
     }
   }
 }
@@ -422,15 +462,15 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
       for (int s = 0; s < S; ++s) {
         const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
         const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
-        const R* w = Pi + ((int64_t)n * S + s) * 4;
+        const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)s * Nh + n) * 4);
         const C f0 = box[(0 * cn + c) * nodes + node];
         const C f1 = box[(1 * cn + c) * nodes + node];
         const C f2 = box[(2 * cn + c) * nodes + node];
         const C f3 = box[(3 * cn + c) * nodes + node];
-        sA.x += w[0] * f0.x + w[1] * f1.x + w[2] * f2.x;
-        sA.y += w[0] * f0.y + w[1] * f1.y + w[2] * f2.y;
-        sP.x += w[3] * f3.x;
-        sP.y += w[3] * f3.y;
+        sA.x += w.x * f0.x + w.y * f1.x + w.z * f2.x;
+        sA.y += w.x * f0.y + w.y * f1.y + w.z * f2.y;
+        sP.x += w.w * f3.x;
+        sP.y += w.w * f3.y;
       }
       const C yff = cadd(cmul(cA, sA), cmul(cP, sP));
       const int64_t idx = (o + n) * nrhs + c0 + c;
@@ -558,7 +598,8 @@ cudaError_t kernels_init(DevArray& a) {
   MM_ATTR(k_fft_fwd_planes<float>) MM_ATTR(k_fft_fwd_planes<double>)
   MM_ATTR(k_fft_conv_lines<float>) MM_ATTR(k_fft_conv_lines<double>)
   MM_ATTR(k_fft_inv_planes<float>) MM_ATTR(k_fft_inv_planes<double>)
-  MM_ATTR(k_project<float>) MM_ATTR(k_project<double>)
+  MM_ATTR((k_project<float, 1>)) MM_ATTR((k_project<double, 1>)) MM_ATTR((k_project<float, 4>))
+  MM_ATTR((k_project<double, 4>))
   MM_ATTR(k_interp<float>) MM_ATTR(k_interp<double>)
 #undef MM_ATTR
   (void)a;
@@ -603,20 +644,22 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   }
   pr.end(st, nl);
   // A2: projection
-  const size_t slim = 96 * 1024;
   pr.begin(sb + 1, st);
   nl = 0;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
-    const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
-    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
-    const size_t sm = 4 * rc * nodes * sizeof(C);
-    k_project<R><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
-        a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
-        p.Pi[t], a.off, a.boxorg, nrhs, rc, u, Nx, Ny, Nz, grid);
+    const int Nh = (int)a.Nh[t];
+    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
+    if (nrhs == 1)
+      k_project<R, 1><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh, st>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+    else
+      k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, st>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
     ++nl;
   }
   pr.end(st, nl);
+  const size_t slim = 96 * 1024;
   // A3: FFT convolution
   pr.begin(sb + 2, st);
   k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
