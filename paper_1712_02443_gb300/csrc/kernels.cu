@@ -73,8 +73,10 @@ FftPlan make_plan(int L) {
 // ---------------------------------------------------------------- A1: macromodel GEMM
 // C (2Nh x ncols) = W (2Nh x Nh) X (Nh x ncols); column c = j * nrhs + rhs of element elems[j].
 // Rows [0, Nh) go to u = M x, rows [Nh, 2Nh) to v = D x.  BM x BN tile per CTA of
-// 256 threads, each thread a TM x TN block of outputs.
-template <typename R, int BM, int BN>
+// 256 threads (each a TM x TN block of outputs), BK-deep k slices staged in
+// shared memory; the next slice is loaded into registers while the current one
+// is multiplied (the product is latency-bound at these sizes).
+template <typename R, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __restrict__ W, int Nh,
                                                     const int32_t* __restrict__ elems, int ncols, int nrhs,
                                                     const int64_t* __restrict__ off,
@@ -82,8 +84,8 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
                                                     typename V2<R>::T* __restrict__ u,
                                                     typename V2<R>::T* __restrict__ v) {
   typedef typename V2<R>::T C;
-  constexpr int BK = 16;
   constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;   // elements each thread stages per slice
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
   __shared__ int64_t colbase[BN];
@@ -101,19 +103,42 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = czero<C>();
   __syncthreads();
-  for (int k0 = 0; k0 < Nh; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 256) {
+  C ra[LA], rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
       const int r = e / BK, kk = e % BK;
       const int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < M2 && gk < Nh) ? W[(int64_t)gr * Nh + gk] : czero<C>();
+      ra[q] = (gr < M2 && gk < Nh) ? W[(int64_t)gr * Nh + gk] : czero<C>();
     }
-    for (int e = tid; e < BN * BK; e += 256) {
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
       const int kk = e % BK, c = e / BK;   // lanes run along k: one element's vector is contiguous
       const int gk = k0 + kk;
       const int64_t cb = colbase[c];
-      Bs[kk][c] = (cb >= 0 && gk < Nh) ? x[cb + (int64_t)gk * nrhs] : czero<C>();
+      rb[q] = (cb >= 0 && gk < Nh) ? x[cb + (int64_t)gk * nrhs] : czero<C>();
     }
-    __syncthreads();
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      As[e % BK][e / BK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      Bs[e % BK][e / BK] = rb[q];
+    }
+  };
+  load(0);
+  store();
+  __syncthreads();
+  for (int k0 = 0; k0 < Nh; k0 += BK) {
+    const bool more = k0 + BK < Nh;
+    if (more) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       C a[TM], b[TN];
@@ -130,6 +155,10 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
         }
     }
     __syncthreads();
+    if (more) {
+      store();
+      __syncthreads();
+    }
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -203,17 +232,26 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
         for (int c = 0; c < RC; ++c) acc[q][c] = czero<C>();
       const int q0 = inv_ptr[node], q1 = inv_ptr[node + 1];
       if (q0 == q1) continue;
-      for (int q = q0; q < q1; ++q) {
-        const int ent = __ldg(inv_ent + q);
-        const int n = ent & 0xffff, sn = ent >> 16;
-        const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)sn * Nh + n) * 4);
+      for (int q = q0; q < q1; q += 4) {
+        int ent[4];
+        typename W4<R>::T w[4];
 #pragma unroll
-        for (int c = 0; c < RC; ++c) {
-          const C uv = us[n * RC + c];
-          acc[0][c].x += w.x * uv.x; acc[0][c].y += w.x * uv.y;
-          acc[1][c].x += w.y * uv.x; acc[1][c].y += w.y * uv.y;
-          acc[2][c].x += w.z * uv.x; acc[2][c].y += w.z * uv.y;
-          acc[3][c].x += w.w * uv.x; acc[3][c].y += w.w * uv.y;
+        for (int t = 0; t < 4; ++t) ent[t] = q + t < q1 ? __ldg(inv_ent + q + t) : -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (ent[t] >= 0) w[t] = W4<R>::load(Pi + ((int64_t)(ent[t] >> 16) * Nh + (ent[t] & 0xffff)) * 4);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (ent[t] < 0) continue;
+          const int n = ent[t] & 0xffff;
+#pragma unroll
+          for (int c = 0; c < RC; ++c) {
+            const C uv = us[n * RC + c];
+            acc[0][c].x += w[t].x * uv.x; acc[0][c].y += w[t].x * uv.y;
+            acc[1][c].x += w[t].y * uv.x; acc[1][c].y += w[t].y * uv.y;
+            acc[2][c].x += w[t].z * uv.x; acc[2][c].y += w[t].z * uv.y;
+            acc[3][c].x += w[t].w * uv.x; acc[3][c].y += w[t].w * uv.y;
+          }
         }
       }
       const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
@@ -229,6 +267,11 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
 }
 
 // ---------------------------------------------------------------- A3: FFT convolution (step ii)
+// Line buffers in shared memory hold element i at PAD(i) = i + i/16, which
+// breaks the bank conflicts of the strided Stockham stores.
+__device__ __forceinline__ int PAD(int i) { return i + (i >> 4); }
+__host__ __device__ inline int padded_len(int L) { return L + (L >> 4) + 1; }
+
 template <typename C, int RADIX, bool INV>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
                                                const C* __restrict__ tw, int lane, int nlanes) {
@@ -245,7 +288,7 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
     const int k = j % Ns;
     C v[RADIX];
 #pragma unroll
-    for (int q = 0; q < RADIX; ++q) v[q] = a[j + q * nb];
+    for (int q = 0; q < RADIX; ++q) v[q] = a[PAD(j + q * nb)];
     if (k != 0) {
 #pragma unroll
       for (int q = 1; q < RADIX; ++q) {
@@ -256,23 +299,23 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
     }
     const int base = (j / Ns) * Ns * RADIX + k;
     if (RADIX == 2) {
-      b[base] = cadd(v[0], v[1]);
-      b[base + Ns] = csub(v[0], v[1]);
+      b[PAD(base)] = cadd(v[0], v[1]);
+      b[PAD(base + Ns)] = csub(v[0], v[1]);
     } else if (RADIX == 4) {
       const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
       C jb1;   // -i*b1 forward, +i*b1 inverse
       if (INV) { jb1.x = -b1.y; jb1.y = b1.x; } else { jb1.x = b1.y; jb1.y = -b1.x; }
-      b[base] = cadd(a0, b0);
-      b[base + Ns] = cadd(a1, jb1);
-      b[base + 2 * Ns] = csub(a0, b0);
-      b[base + 3 * Ns] = csub(a1, jb1);
+      b[PAD(base)] = cadd(a0, b0);
+      b[PAD(base + Ns)] = cadd(a1, jb1);
+      b[PAD(base + 2 * Ns)] = csub(a0, b0);
+      b[PAD(base + 3 * Ns)] = csub(a1, jb1);
     } else {
 #pragma unroll
       for (int p = 0; p < RADIX; ++p) {
         C acc = v[0];
 #pragma unroll
         for (int q = 1; q < RADIX; ++q) acc = cadd(acc, cmul(v[q], wr[(p * q) % RADIX]));
-        b[base + p * Ns] = acc;
+        b[PAD(base + p * Ns)] = acc;
       }
     }
   }
@@ -314,8 +357,9 @@ __global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T*
   const int Py = py.L;
   C* ty = reinterpret_cast<C*>(smem_raw);
   C* tz = ty + Py;
-  C* b0 = tz + Pz;            // [kz][y]
-  C* b1 = b0 + Pz * Py;       // [kz][y]
+  const int LpY = padded_len(Py);
+  C* b0 = tz + Pz;            // [kz][PAD(y)]
+  C* b1 = b0 + Pz * LpY;      // [kz][PAD(y)]
   const int x = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
@@ -327,12 +371,12 @@ __global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T*
     C acc = czero<C>();
     if (y < Ny)
       for (int z = 0; z < Nz; ++z) acc = cadd(acc, cmul(b1[y * Nz + z], tz[(kz * z) % Pz]));
-    b0[i] = acc;
+    b0[kz * LpY + PAD(y)] = acc;
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   C* res = nullptr;
-  for (int kz = warp; kz < Pz; kz += nw) res = warp_fft<C, false>(b0 + kz * Py, b1 + kz * Py, py, ty, lane);
+  for (int kz = warp; kz < Pz; kz += nw) res = warp_fft<C, false>(b0 + kz * LpY, b1 + kz * LpY, py, ty, lane);
   __syncthreads();
   const bool in_b0 = (py.nst % 2) == 0;
   (void)res;
@@ -340,7 +384,7 @@ __global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T*
   C* dst = spec + ((int64_t)b * Nx + x) * Py * Pz;
   for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
     const int ky = i / Pz, kz = i % Pz;
-    dst[i] = out[kz * Py + ky];
+    dst[i] = out[kz * LpY + PAD(ky)];
   }
 }
 
@@ -354,23 +398,24 @@ __global__ void __launch_bounds__(256) k_fft_conv_lines(typename V2<R>::T* __res
   extern __shared__ unsigned char smem_raw[];
   const int Px = px.L;
   C* tx = reinterpret_cast<C*>(smem_raw);
-  C* b0 = tx + Px;            // [kz][x]
-  C* b1 = b0 + Pz * Px;
+  const int LpX = padded_len(Px);
+  C* b0 = tx + Px;            // [kz][PAD(x)]
+  C* b1 = b0 + Pz * LpX;
   const int ky = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Px; i += blockDim.x) tx[i] = twx[i];
   C* base = spec + (int64_t)b * Nx * Py * Pz + (int64_t)ky * Pz;
   for (int i = threadIdx.x; i < Pz * Px; i += blockDim.x) {
     const int x = i / Pz, kz = i % Pz;
-    if (x < Px) b0[kz * Px + x] = (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
+    if (x < Px) b0[kz * LpX + PAD(x)] = (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   for (int kz = warp; kz < Pz; kz += nw) {
-    C* a = b0 + kz * Px;
-    C* c = b1 + kz * Px;
+    C* a = b0 + kz * LpX;
+    C* c = b1 + kz * LpX;
     C* r = warp_fft<C, false>(a, c, px, tx, lane);
     const C* g = Ghat + ((int64_t)ky * Pz + kz) * Px;
-    for (int i = lane; i < Px; i += 32) r[i] = cmul(r[i], g[i]);
+    for (int i = lane; i < Px; i += 32) r[PAD(i)] = cmul(r[PAD(i)], g[i]);
     __syncwarp();
     C* other = (r == a) ? c : a;
     warp_fft<C, true>(r, other, px, tx, lane);
@@ -380,7 +425,7 @@ __global__ void __launch_bounds__(256) k_fft_conv_lines(typename V2<R>::T* __res
   const C* out = b0;
   for (int i = threadIdx.x; i < Pz * Nx; i += blockDim.x) {
     const int x = i / Pz, kz = i % Pz;
-    base[(int64_t)x * Py * Pz + kz] = out[kz * Px + x];
+    base[(int64_t)x * Py * Pz + kz] = out[kz * LpX + PAD(x)];
   }
 }
 
@@ -396,19 +441,20 @@ __global__ void __launch_bounds__(256) k_fft_inv_planes(const typename V2<R>::T*
   const int Py = py.L;
   C* ty = reinterpret_cast<C*>(smem_raw);
   C* tz = ty + Py;
+  const int LpY = padded_len(Py);
   C* b0 = tz + Pz;
-  C* b1 = b0 + Pz * Py;
+  C* b1 = b0 + Pz * LpY;
   const int x = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
   const C* src = spec + ((int64_t)b * Nx + x) * Py * Pz;
   for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
     const int ky = i / Pz, kz = i % Pz;
-    b0[kz * Py + ky] = src[i];
+    b0[kz * LpY + PAD(ky)] = src[i];
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int kz = warp; kz < Pz; kz += nw) warp_fft<C, true>(b0 + kz * Py, b1 + kz * Py, py, ty, lane);
+  for (int kz = warp; kz < Pz; kz += nw) warp_fft<C, true>(b0 + kz * LpY, b1 + kz * LpY, py, ty, lane);
   __syncthreads();
   const C* res = (py.nst % 2 == 0) ? b0 : b1;
   C* dst = grid + ((int64_t)b * Nx + x) * Ny * Nz;
@@ -418,7 +464,7 @@ __global__ void __launch_bounds__(256) k_fft_inv_planes(const typename V2<R>::T*
     for (int kz = 0; kz < Pz; ++kz) {
       C w = tz[(kz * z) % Pz];
       w.y = -w.y;
-      acc = cadd(acc, cmul(res[kz * Py + y], w));
+      acc = cadd(acc, cmul(res[kz * LpY + PAD(y)], w));
     }
     dst[i] = acc;
   }
@@ -578,8 +624,8 @@ template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which) {
   const size_t cs = sizeof(typename V2<R>::T);
   const int Py = a.fft[1], Pz = a.fft[2], Px = a.fft[0];
-  if (which == 0) return cs * ((size_t)Py + Pz + 2 * (size_t)Pz * Py);
-  return cs * ((size_t)Px + 2 * (size_t)Pz * Px);
+  if (which == 0) return cs * ((size_t)Py + Pz + 2 * (size_t)Pz * padded_len(Py));
+  return cs * ((size_t)Px + 2 * (size_t)Pz * padded_len(Px));
 }
 
 static int box_rc(const DevArray& a, int t, int nrhs, size_t csize, size_t limit) {
@@ -631,14 +677,15 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const int Nh = (int)a.Nh[t];
     const int ncols = (int)(a.n_of_type[t] * nrhs);
     const int64_t big = (int64_t)((2 * Nh + 63) / 64) * ((ncols + 63) / 64);
+    constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
     if (big >= 2 * 152) {
       dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
-      k_macro_gemm<R, 64, 64><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off,
-                                                 x, u, v);
+      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs,
+                                                     a.off, x, u, v);
     } else {
       dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
-      k_macro_gemm<R, 32, 32><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs, a.off,
-                                                 x, u, v);
+      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs,
+                                                      a.off, x, u, v);
     }
     ++nl;
   }

@@ -122,6 +122,318 @@ __global__ void k_add(const Z* __restrict__ d, int64_t n, Z* __restrict__ x) {
     x[t] = make_double2(x[t].x + d[t].x, x[t].y + d[t].y);
 }
 
+
+// ---------------------------------------------------------------- device-side GMRES cycle
+// State of one GMRES cycle for r independent columns, all in device memory.
+// The Arnoldi index k lives on the device so every iteration issues the same
+// kernels; the host only watches a mapped flag one iteration behind.
+struct GmresDev {
+  int* k;          // completed Arnoldi steps in this cycle (index of the next basis vector)
+  int* active;     // r
+  int* kdone;      // r
+  double* tol;     // r  absolute residual targets
+  double* res;     // r  residual estimates
+  double* scale;   // r  1/||w|| for the next basis vector (0 when inactive)
+  Z* g;            // (m+1) r
+  Z* cs;           // m r
+  Z* sn;           // m r
+  Z* H;            // r (m+1) m, column j, Arnoldi column k: H[(j m + k)(m+1) + i]
+  Z* y;            // m r
+  int* flag;       // mapped host memory: [0] any column active, [1] k, [2] max kdone
+  int m, r;
+};
+
+static_assert(sizeof(GmresDev) <= 160, "GmresDev must fit Solver::gdev_");
+
+// V[k] = w * scale (per column); out = V[k] converted to the operator precision.
+template <typename T>
+__global__ void k_fetch(Z* __restrict__ V, int64_t vs, const Z* __restrict__ w, GmresDev gd, int64_t n,
+                        T* __restrict__ out) {
+  const int k = *gd.k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % gd.r);
+    const double sc = gd.scale[j];
+    const Z v = make_double2(w[t].x * sc, w[t].y * sc);
+    V[(int64_t)k * vs + t] = v;
+    T o;
+    o.x = v.x;
+    o.y = v.y;
+    out[t] = o;
+  }
+}
+
+__device__ __forceinline__ Z warp_sum(Z v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, s);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, s);
+  }
+  return v;
+}
+
+// Partial dot products of w with V_0..V_k over one block of rows:
+// P[(i r + j) nblk + blk].  `sh` holds (m+1) x nwarps partial sums.
+__device__ void block_dots(const Z* __restrict__ V, int64_t vs, const Z* __restrict__ w, int k, int64_t n0,
+                           int64_t n1, int r, int j, int blk, int nblk, Z* sh, Z* __restrict__ P) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int i = 0; i <= k; ++i) {
+    Z acc = make_double2(0, 0);
+    const Z* vi = V + (int64_t)i * vs;
+    for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+      const int64_t t = nn * r + j;
+      const Z p = zconjmul(vi[t], w[t]);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) sh[i * nw + warp] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    Z acc = make_double2(0, 0);
+    for (int q = 0; q < nw; ++q) {
+      acc.x += sh[i * nw + q].x;
+      acc.y += sh[i * nw + q].y;
+    }
+    P[((int64_t)i * r + j) * nblk + blk] = acc;
+  }
+}
+
+// CGS pass 1: partial <V_i, w>, i <= k.  Grid (nblk, r).
+__global__ void k_cgs_dots(const Z* __restrict__ V, int64_t vs, const Z* __restrict__ w, GmresDev gd, int64_t N,
+                           int nblk, Z* __restrict__ P1) {
+  extern __shared__ Z sh[];
+  const int k = *gd.k, j = blockIdx.y, blk = blockIdx.x;
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  block_dots(V, vs, w, k, n0, n1, gd.r, j, blk, nblk, sh, P1);
+}
+
+// Sum of the partials of column j for i <= k into hs[i] (shared memory).
+__device__ void reduce_partials(const Z* __restrict__ P, int k, int r, int j, int nblk, Z* hs) {
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    Z acc = make_double2(0, 0);
+    for (int b = 0; b < nblk; ++b) {
+      const Z v = P[((int64_t)i * r + j) * nblk + b];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    hs[i] = acc;
+  }
+  __syncthreads();
+}
+
+// w -= sum_i V_i h_i over this block's rows, then partial <V_i, w> (CGS pass 2 dots).
+__global__ void k_cgs_update_dots(const Z* __restrict__ V, int64_t vs, GmresDev gd, const Z* __restrict__ P1,
+                                  Z* __restrict__ w, int64_t N, int nblk, Z* __restrict__ P2) {
+  extern __shared__ Z sh[];
+  const int k = *gd.k, j = blockIdx.y, blk = blockIdx.x, r = gd.r;
+  Z* hs = sh;                      // m+1
+  Z* ws = sh + (gd.m + 1);         // (m+1) x nwarps
+  reduce_partials(P1, k, r, j, nblk, hs);
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+    const int64_t t = nn * r + j;
+    Z a = w[t];
+    for (int i = 0; i <= k; ++i) {
+      const Z p = zmul(V[(int64_t)i * vs + t], hs[i]);
+      a.x -= p.x;
+      a.y -= p.y;
+    }
+    w[t] = a;
+  }
+  __syncthreads();
+  block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2);
+}
+
+// w -= sum_i V_i h2_i, then partial ||w||^2: PN[j nblk + blk].
+__global__ void k_cgs_update_norm(const Z* __restrict__ V, int64_t vs, GmresDev gd, const Z* __restrict__ P2,
+                                  Z* __restrict__ w, int64_t N, int nblk, double* __restrict__ PN) {
+  extern __shared__ Z sh[];
+  const int k = *gd.k, j = blockIdx.y, blk = blockIdx.x, r = gd.r;
+  reduce_partials(P2, k, r, j, nblk, sh);
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  double acc = 0;
+  for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+    const int64_t t = nn * r + j;
+    Z a = w[t];
+    for (int i = 0; i <= k; ++i) {
+      const Z p = zmul(V[(int64_t)i * vs + t], sh[i]);
+      a.x -= p.x;
+      a.y -= p.y;
+    }
+    w[t] = a;
+    acc += a.x * a.x + a.y * a.y;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  __shared__ double red[32];
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t2 = 0;
+    for (int q = 0; q < (int)blockDim.x / 32; ++q) t2 += red[q];
+    PN[(int64_t)j * nblk + blk] = t2;
+  }
+}
+
+// Partial ||w_j||^2 over a block of rows.  Grid (nblk, r).
+__global__ void k_norm_partial(const Z* __restrict__ w, int64_t N, int r, int nblk, double* __restrict__ PN) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  double acc = 0;
+  for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+    const Z a = w[nn * r + j];
+    acc += a.x * a.x + a.y * a.y;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  __shared__ double red[32];
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t2 = 0;
+    for (int q = 0; q < (int)blockDim.x / 32; ++q) t2 += red[q];
+    PN[(int64_t)j * nblk + blk] = t2;
+  }
+}
+
+// Cycle start: beta_j = ||r0_j||, g = (beta, 0, ...), active = beta > tol, scale = 1/beta.
+__global__ void k_cycle_init(GmresDev gd, const double* __restrict__ PN, int nblk) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < gd.r; j += blockDim.x) {
+    double s2 = 0;
+    for (int b = 0; b < nblk; ++b) s2 += PN[(int64_t)j * nblk + b];
+    const double beta = sqrt(fmax(0.0, s2));
+    for (int i = 0; i <= gd.m; ++i) gd.g[(int64_t)i * gd.r + j] = make_double2(0, 0);
+    gd.g[j] = make_double2(beta, 0);
+    gd.res[j] = beta;
+    const int act = (beta > gd.tol[j]) && isfinite(beta);
+    gd.active[j] = act;
+    gd.kdone[j] = 0;
+    gd.scale[j] = act ? 1.0 / beta : 0.0;
+    if (act) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *gd.k = 0;
+    gd.flag[0] = any;
+    gd.flag[1] = 0;
+    gd.flag[2] = 0;
+    __threadfence_system();
+  }
+}
+
+// Arnoldi column k: H[:, k] = h1 + h2, ||w|| from the norm partials; previous
+// Givens rotations, a new one, the residual estimate; then k += 1.  One block,
+// a warp per column.
+__global__ void k_givens(GmresDev gd, const Z* __restrict__ P1, const Z* __restrict__ P2,
+                         const double* __restrict__ PN, int nblk) {
+  extern __shared__ Z hcol[];      // (m+2) per warp
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int k = *gd.k, m = gd.m, r = gd.r;
+  Z* hc = hcol + warp * (m + 2);
+  for (int j = warp; j < r; j += nw) {
+    if (!gd.active[j]) continue;   // warp-uniform
+    for (int i = lane; i <= k; i += 32) {
+      Z acc = make_double2(0, 0);
+      for (int b = 0; b < nblk; ++b) {
+        const Z a = P1[((int64_t)i * r + j) * nblk + b], c = P2[((int64_t)i * r + j) * nblk + b];
+        acc.x += a.x + c.x;
+        acc.y += a.y + c.y;
+      }
+      hc[i] = acc;
+    }
+    double s2 = 0;
+    for (int b = lane; b < nblk; b += 32) s2 += PN[(int64_t)j * nblk + b];
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, s);
+    __syncwarp();
+    if (lane == 0) {
+      const double hn = sqrt(fmax(0.0, s2));
+      Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
+      for (int i = 0; i < k; ++i) {   // previous rotations [[conj c, conj s], [-s, c]]
+        const Z c = gd.cs[(int64_t)i * r + j], sg = gd.sn[(int64_t)i * r + j];
+        const Z a = hc[i], bb = hc[i + 1];
+        const Z t1 = zconjmul(c, a), t2 = zconjmul(sg, bb);
+        const Z u1 = zmul(sg, a), u2 = zmul(c, bb);
+        hc[i] = make_double2(t1.x + t2.x, t1.y + t2.y);
+        hc[i + 1] = make_double2(u2.x - u1.x, u2.y - u1.y);
+      }
+      const Z a = hc[k];
+      const double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
+      const Z c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1, 0);
+      const Z sg = den > 0 ? make_double2(hn / den, 0) : make_double2(0, 0);
+      gd.cs[(int64_t)k * r + j] = c;
+      gd.sn[(int64_t)k * r + j] = sg;
+      hc[k] = make_double2(den, 0);
+      for (int i = 0; i <= k; ++i) H[i] = hc[i];
+      const Z gk = gd.g[(int64_t)k * r + j];
+      const Z sgk = zmul(sg, gk);
+      gd.g[(int64_t)(k + 1) * r + j] = make_double2(-sgk.x, -sgk.y);
+      gd.g[(int64_t)k * r + j] = zconjmul(c, gk);
+      const double res = sqrt(sgk.x * sgk.x + sgk.y * sgk.y);
+      gd.res[j] = res;
+      gd.kdone[j] = k + 1;
+      const int stop = !(res > gd.tol[j]) || hn == 0.0 || !isfinite(hn);
+      gd.active[j] = stop ? 0 : 1;
+      gd.scale[j] = stop ? 0.0 : 1.0 / hn;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0, kd = 0;
+    for (int j = 0; j < r; ++j) {
+      any |= gd.active[j];
+      kd = max(kd, gd.kdone[j]);
+    }
+    *gd.k = k + 1;
+    gd.flag[0] = any;
+    gd.flag[1] = k + 1;
+    gd.flag[2] = kd;
+    __threadfence_system();
+  }
+}
+
+// y_j = H_j^-1 g_j by back substitution over kdone_j columns (lane 0 of a warp per column).
+__global__ void k_solve_y(GmresDev gd) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int m = gd.m, r = gd.r;
+  for (int j = warp; j < r; j += nw) {
+    if (lane != 0) continue;
+    const int kj = gd.kdone[j];
+    for (int i = m - 1; i >= kj; --i) gd.y[(int64_t)i * r + j] = make_double2(0, 0);
+    for (int i = kj - 1; i >= 0; --i) {
+      Z acc = gd.g[(int64_t)i * r + j];
+      for (int q = i + 1; q < kj; ++q) {
+        const Z p = zmul(gd.H[((int64_t)j * m + q) * (m + 1) + i], gd.y[(int64_t)q * r + j]);
+        acc.x -= p.x;
+        acc.y -= p.y;
+      }
+      const Z d = gd.H[((int64_t)j * m + i) * (m + 1) + i];
+      const double dd = d.x * d.x + d.y * d.y;
+      gd.y[(int64_t)i * r + j] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+    }
+  }
+}
+
+// x[n, j] += sum_{i < k} V_i[n, j] y[i r + j], k read from the device.
+__global__ void k_add_basis_dev(const Z* __restrict__ V, int64_t vs, GmresDev gd, int64_t n, Z* __restrict__ x) {
+  const int k = *gd.k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % gd.r);
+    Z acc = x[t];
+    for (int i = 0; i < k; ++i) {
+      const Z p = zmul(V[(int64_t)i * vs + t], gd.y[(int64_t)i * gd.r + j]);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+    x[t] = acc;
+  }
+}
+
 static unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -152,14 +464,55 @@ Status Solver::ensure(int64_t N, int r, int m) {
   MM_CK(cudaMalloc(&scale_, sizeof(double) * r));
   MM_CK(cudaMalloc(&active_, sizeof(int32_t) * r));
   MM_CK(cudaMalloc(&dx_, vec));
-  bytes_ = vec * (m + 4) + sizeof(float2) * 2 * (size_t)N * r;
+  MM_CK(cudaMalloc(&x64_, vec));
+  MM_CK(cudaMalloc(&P1_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
+  MM_CK(cudaMalloc(&P2_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
+  MM_CK(cudaMalloc(&PN_, sizeof(double) * (size_t)r * nblk_));
+  {
+    // GMRES cycle state: k, active, kdone, tol, res, scale, g, cs, sn, H, y
+    size_t b = 0;
+    auto take = [&](size_t bytes) { size_t o = b; b += (bytes + 255) / 256 * 256; return o; };
+    size_t o_k = take(sizeof(int)), o_act = take(sizeof(int) * r), o_kd = take(sizeof(int) * r);
+    size_t o_tol = take(sizeof(double) * r), o_res = take(sizeof(double) * r), o_sc = take(sizeof(double) * r);
+    size_t o_g = take(sizeof(Z) * (m + 1) * r), o_cs = take(sizeof(Z) * m * r), o_sn = take(sizeof(Z) * m * r);
+    size_t o_H = take(sizeof(Z) * (size_t)r * (m + 1) * m), o_y = take(sizeof(Z) * (size_t)m * r);
+    MM_CK(cudaMalloc(&gstate_, b));
+    char* base = static_cast<char*>(gstate_);
+    GmresDev& g = *reinterpret_cast<GmresDev*>(gdev_);
+    g.k = reinterpret_cast<int*>(base + o_k);
+    g.active = reinterpret_cast<int*>(base + o_act);
+    g.kdone = reinterpret_cast<int*>(base + o_kd);
+    g.tol = reinterpret_cast<double*>(base + o_tol);
+    g.res = reinterpret_cast<double*>(base + o_res);
+    g.scale = reinterpret_cast<double*>(base + o_sc);
+    g.g = reinterpret_cast<Z*>(base + o_g);
+    g.cs = reinterpret_cast<Z*>(base + o_cs);
+    g.sn = reinterpret_cast<Z*>(base + o_sn);
+    g.H = reinterpret_cast<Z*>(base + o_H);
+    g.y = reinterpret_cast<Z*>(base + o_y);
+    g.m = m;
+    g.r = r;
+    MM_CK(cudaHostAlloc(&flag_h_, sizeof(int) * 4, cudaHostAllocMapped));
+    void* fd = nullptr;
+    MM_CK(cudaHostGetDevicePointer(&fd, flag_h_, 0));
+    g.flag = static_cast<int*>(fd);
+    MM_CK(cudaEventCreateWithFlags(&ev_[0], cudaEventDisableTiming));
+    MM_CK(cudaEventCreateWithFlags(&ev_[1], cudaEventDisableTiming));
+  }
+  bytes_ = vec * (m + 5) + sizeof(float2) * 2 * (size_t)N * r;
   return {MM_OK, ""};
 }
 
 void Solver::release() {
-  void* ps[] = {V_, w_, t_, x32_, y32_, partial_, h_, h2_, scale_, active_, dx_};
+  void* ps[] = {V_, w_, t_, x32_, y32_, partial_, h_, h2_, scale_, active_, dx_, x64_, P1_, P2_, PN_, gstate_};
   for (void* p : ps)
     if (p) cudaFree(p);
+  if (flag_h_) cudaFreeHost(flag_h_);
+  for (auto& e : ev_)
+    if (e) cudaEventDestroy(e);
+  ev_[0] = ev_[1] = nullptr;
+  flag_h_ = nullptr;
+  x64_ = P1_ = P2_ = PN_ = gstate_ = nullptr;
   V_ = w_ = t_ = nullptr;
   x32_ = y32_ = nullptr;
   partial_ = nullptr;
@@ -199,9 +552,11 @@ Status Solver::apply(const Z* in, Z* out, int prec, cudaStream_t st) {
 }
 
 // Restarted GMRES on A x = b; x accumulates.  x_zero: x is 0 on entry, so the
-// first residual is b itself (no product).  A cycle stops at the restart length
-// or when every column's Givens residual estimate meets tol_abs; in the latter
-// case GMRES returns (the caller checks the true residual).  tol_abs[j] is the
+// first residual is b itself (no product).  The cycle runs on the device
+// (Arnoldi index, Hessenberg, Givens rotations and residual estimates live in
+// device memory); the host issues iteration it while waiting for iteration
+// it - 1, so at most one iteration per cycle runs after convergence (its
+// columns are inactive and do not change the solution).  tol_abs[j] is the
 // absolute residual target of column j.
 Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& tol_abs, int prec, int max_iter,
                      int& iters, std::vector<double>& res, cudaStream_t st) {
@@ -211,18 +566,18 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
   const int64_t vs = n;
   Z* V = static_cast<Z*>(V_);
   Z* w = static_cast<Z*>(w_);
-  Z* h = static_cast<Z*>(h_);
-  Z* h2 = static_cast<Z*>(h2_);
+  GmresDev gd = *reinterpret_cast<GmresDev*>(gdev_);
+  volatile int* flag = static_cast<volatile int*>(flag_h_);
   iters = 0;
   res.assign(r, 0.0);
-  std::vector<std::complex<double>> Hh((size_t)(m + 1) * m * r), cs((size_t)m * r), sn((size_t)m * r),
-      g((size_t)(m + 1) * r);
-  std::vector<Z> hbuf((size_t)(m + 1) * r), hb2((size_t)(m + 1) * r);
-  std::vector<int32_t> active(r), kdone(r);
-  std::vector<double> sc(r);
+  MM_CK(cudaMemcpyAsync(gd.tol, tol_abs.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+  const int nw = 8;
+  const size_t sh_dots = sizeof(Z) * (size_t)(m + 1) * nw;
+  const size_t sh_upd = sizeof(Z) * (size_t)(m + 1) * (nw + 1);
+  const size_t sh_giv = sizeof(Z) * (size_t)(m + 2) * nw;
   bool first = true;
   for (;;) {
-    // r0 = b - A x
+    // r0 = b - A x, its norm, cycle initialisation
     if (first && x_zero) {
       MM_CK(cudaMemcpyAsync(w, b, sizeof(Z) * n, cudaMemcpyDeviceToDevice, st));
     } else {
@@ -231,120 +586,74 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
       k_sub<<<grid_for(n), 256, 0, st>>>(b, w, n, w);
     }
     first = false;
-    Status s = dots(w, 0, 1, w, h, st);
-    if (s.code != MM_OK) return s;
-    MM_CK(cudaMemcpyAsync(hbuf.data(), h, sizeof(Z) * r, cudaMemcpyDeviceToHost, st));
+    k_norm_partial<<<dim3(nblk_, r), 256, 0, st>>>(w, N, r, nblk_, static_cast<double*>(PN_));
+    k_cycle_init<<<1, 256, 0, st>>>(gd, static_cast<const double*>(PN_), nblk_);
+    MM_CK(cudaGetLastError());
     MM_CK(cudaStreamSynchronize(st));
-    bool any = false;
-    for (int j = 0; j < r; ++j) {
-      double beta = std::sqrt(std::max(0.0, hbuf[j].x));
-      res[j] = beta;
-      if (!std::isfinite(beta)) return {MM_EBREAKDOWN, "non-finite residual in GMRES"};
-      active[j] = beta > tol_abs[j];
-      any |= (bool)active[j];
-      sc[j] = beta > 0 ? 1.0 / beta : 0.0;
-      for (int i = 0; i <= m; ++i) g[(size_t)i * r + j] = 0;
-      g[j] = beta;
-      kdone[j] = 0;
-    }
-    if (!any || iters >= max_iter) return {MM_OK, ""};
-    MM_CK(cudaMemcpyAsync(scale_, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-    MM_CK(cudaMemcpyAsync(active_, active.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, st));
-    k_scale_cols<<<grid_for(n), 256, 0, st>>>(w, static_cast<double*>(scale_), static_cast<int32_t*>(active_), N, r, V);
-    bool all_met = false;
-    for (int k = 0; k < m && iters < max_iter; ++k) {
-      s = apply(V + (int64_t)k * vs, w, prec, st);
-      if (s.code != MM_OK) return s;
-      // classical Gram-Schmidt, twice
-      s = dots(V, vs, k + 1, w, h, st);
-      if (s.code != MM_OK) return s;
-      if (prof) prof->begin(7, st);
-      k_orth_update<<<grid_for(n), 256, 0, st>>>(V, vs, h, k + 1, N, r, w);
-      if (prof) prof->end(st, 1);
-      s = dots(V, vs, k + 1, w, h2, st);
-      if (s.code != MM_OK) return s;
-      if (prof) prof->begin(7, st);
-      k_orth_update<<<grid_for(n), 256, 0, st>>>(V, vs, h2, k + 1, N, r, w);
-      if (prof) prof->end(st, 1);
-      s = dots(w, 0, 1, w, h2 + (size_t)(k + 1) * r, st);
-      if (s.code != MM_OK) return s;
-      MM_CK(cudaMemcpyAsync(hbuf.data(), h, sizeof(Z) * (size_t)(k + 1) * r, cudaMemcpyDeviceToHost, st));
-      MM_CK(cudaMemcpyAsync(hb2.data(), h2, sizeof(Z) * (size_t)(k + 2) * r, cudaMemcpyDeviceToHost, st));
-      MM_CK(cudaStreamSynchronize(st));
-      ++iters;
-      bool still = false;
+    if (!flag[0] || iters >= max_iter) {
+      std::vector<double> rr(r);
+      MM_CK(cudaMemcpy(rr.data(), gd.res, sizeof(double) * r, cudaMemcpyDeviceToHost));
       for (int j = 0; j < r; ++j) {
-        if (!active[j]) {
-          sc[j] = 0.0;
-          continue;
-        }
-        std::complex<double>* H = &Hh[(size_t)j * (m + 1) * m];   // column-major (m+1) x m per column j
-        for (int i = 0; i <= k; ++i)
-          H[(size_t)k * (m + 1) + i] = std::complex<double>(hbuf[(size_t)i * r + j].x + hb2[(size_t)i * r + j].x,
-                                                            hbuf[(size_t)i * r + j].y + hb2[(size_t)i * r + j].y);
-        double hn = std::sqrt(std::max(0.0, hb2[(size_t)(k + 1) * r + j].x));
-        if (!std::isfinite(hn)) return {MM_EBREAKDOWN, "non-finite Arnoldi norm"};
-        H[(size_t)k * (m + 1) + k + 1] = hn;
-        for (int i = 0; i < k; ++i) {
-          std::complex<double> c = cs[(size_t)i * r + j], sg = sn[(size_t)i * r + j];
-          std::complex<double> a = H[(size_t)k * (m + 1) + i], bb = H[(size_t)k * (m + 1) + i + 1];
-          H[(size_t)k * (m + 1) + i] = std::conj(c) * a + std::conj(sg) * bb;
-          H[(size_t)k * (m + 1) + i + 1] = -sg * a + c * bb;
-        }
-        std::complex<double> a = H[(size_t)k * (m + 1) + k], bb = H[(size_t)k * (m + 1) + k + 1];
-        double den = std::sqrt(std::norm(a) + std::norm(bb));
-        std::complex<double> c = den > 0 ? a / den : 1.0, sg = den > 0 ? bb / den : 0.0;
-        cs[(size_t)k * r + j] = c;
-        sn[(size_t)k * r + j] = sg;
-        H[(size_t)k * (m + 1) + k] = den;
-        H[(size_t)k * (m + 1) + k + 1] = 0.0;
-        std::complex<double> gk = g[(size_t)k * r + j];
-        g[(size_t)(k + 1) * r + j] = -sg * gk;
-        g[(size_t)k * r + j] = std::conj(c) * gk;
-        kdone[j] = k + 1;
-        res[j] = std::abs(g[(size_t)(k + 1) * r + j]);
-        if (res[j] <= tol_abs[j] || hn == 0.0) {
-          active[j] = 0;
-          sc[j] = 0.0;
-        } else {
-          sc[j] = 1.0 / hn;
-          still = true;
-        }
+        res[j] = rr[j];
+        if (!std::isfinite(rr[j])) return {MM_EBREAKDOWN, "non-finite residual in GMRES"};
       }
-      if (!still) {
-        all_met = true;
-        break;
-      }
-      MM_CK(cudaMemcpyAsync(scale_, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-      MM_CK(cudaMemcpyAsync(active_, active.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, st));
-      k_scale_cols<<<grid_for(n), 256, 0, st>>>(w, static_cast<double*>(scale_), static_cast<int32_t*>(active_), N, r,
-                                                V + (int64_t)(k + 1) * vs);
+      return {MM_OK, ""};
     }
-    // y_j = H_j^-1 g_j (upper triangular), x += V y
-    int kmax = 0;
-    for (int j = 0; j < r; ++j) kmax = std::max(kmax, kdone[j]);
-    std::vector<Z> y((size_t)std::max(kmax, 1) * r, make_double2(0, 0));
-    for (int j = 0; j < r; ++j) {
-      int kj = kdone[j];
-      std::complex<double>* H = &Hh[(size_t)j * (m + 1) * m];
-      std::vector<std::complex<double>> yy(kj);
-      for (int i = kj - 1; i >= 0; --i) {
-        std::complex<double> acc = g[(size_t)i * r + j];
-        for (int q = i + 1; q < kj; ++q) acc -= H[(size_t)q * (m + 1) + i] * yy[q];
-        yy[i] = acc / H[(size_t)i * (m + 1) + i];
+    bool stopped = false;
+    int launched = 0;
+    for (int it = 0; it < m && iters + it < max_iter; ++it) {
+      // fetch V[k] = w / ||w|| and hand it to the operator
+      if (prec == MM_C128) {
+        k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
+        Status s1 = op64(static_cast<const Z*>(x64_), w, st);
+        if (s1.code != MM_OK) return s1;
+      } else {
+        if (prof) prof->begin(7, st);
+        k_fetch<float2><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<float2*>(x32_));
+        if (prof) prof->end(st, 1);
+        Status s1 = op32(x32_, y32_, st);
+        if (s1.code != MM_OK) return s1;
+        if (prof) prof->begin(7, st);
+        k_to_c128<<<grid_for(n), 256, 0, st>>>(static_cast<const float2*>(y32_), w, n);
+        if (prof) prof->end(st, 1);
       }
-      for (int i = 0; i < kj; ++i) y[(size_t)i * r + j] = make_double2(yy[i].real(), yy[i].imag());
-    }
-    if (kmax > 0) {
-      MM_CK(cudaMemcpyAsync(h, y.data(), sizeof(Z) * (size_t)kmax * r, cudaMemcpyHostToDevice, st));
+      ++matvecs;
       if (prof) prof->begin(7, st);
-      k_add_basis<<<grid_for(n), 256, 0, st>>>(V, vs, h, kmax, N, r, x);
-      if (prof) prof->end(st, 1);
+      k_cgs_dots<<<dim3(nblk_, r), 32 * nw, sh_dots, st>>>(V, vs, w, gd, N, nblk_, static_cast<Z*>(P1_));
+      k_cgs_update_dots<<<dim3(nblk_, r), 32 * nw, sh_upd, st>>>(V, vs, gd, static_cast<const Z*>(P1_), w, N, nblk_,
+                                                                 static_cast<Z*>(P2_));
+      k_cgs_update_norm<<<dim3(nblk_, r), 32 * nw, sizeof(Z) * (m + 1), st>>>(
+          V, vs, gd, static_cast<const Z*>(P2_), w, N, nblk_, static_cast<double*>(PN_));
+      k_givens<<<1, 32 * nw, sh_giv, st>>>(gd, static_cast<const Z*>(P1_), static_cast<const Z*>(P2_),
+                                           static_cast<const double*>(PN_), nblk_);
+      if (prof) prof->end(st, 4);
       MM_CK(cudaGetLastError());
+      MM_CK(cudaEventRecord(ev_[it & 1], st));
+      launched = it + 1;
+      if (it >= 1) {
+        MM_CK(cudaEventSynchronize(ev_[(it - 1) & 1]));
+        if (!flag[0]) {
+          stopped = true;
+          break;
+        }
+      }
     }
-    // the synchronous copy of y must complete before the host vector goes away
+    MM_CK(cudaEventSynchronize(ev_[(launched - 1) & 1]));
+    if (!flag[0]) stopped = true;
+    k_solve_y<<<1, 32 * nw, 0, st>>>(gd);
+    if (prof) prof->begin(7, st);
+    k_add_basis_dev<<<grid_for(n), 256, 0, st>>>(V, vs, gd, n, x);
+    if (prof) prof->end(st, 1);
+    MM_CK(cudaGetLastError());
     MM_CK(cudaStreamSynchronize(st));
-    if (all_met || iters >= max_iter) return {MM_OK, ""};
+    iters += flag[2];
+    std::vector<double> rr(r);
+    MM_CK(cudaMemcpy(rr.data(), gd.res, sizeof(double) * r, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < r; ++j) {
+      res[j] = rr[j];
+      if (!std::isfinite(rr[j])) return {MM_EBREAKDOWN, "non-finite residual in GMRES"};
+    }
+    if (stopped || iters >= max_iter) return {MM_OK, ""};
   }
 }
 

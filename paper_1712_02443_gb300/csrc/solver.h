@@ -47,6 +47,9 @@ class Solver {
   int r_ = 0, m_ = 0, nblk_ = 1;
   void *V_ = nullptr, *w_ = nullptr, *t_ = nullptr, *x32_ = nullptr, *y32_ = nullptr;
   void *partial_ = nullptr, *h_ = nullptr, *h2_ = nullptr, *scale_ = nullptr, *active_ = nullptr, *dx_ = nullptr;
+  void *x64_ = nullptr, *P1_ = nullptr, *P2_ = nullptr, *PN_ = nullptr, *gstate_ = nullptr, *flag_h_ = nullptr;
+  alignas(16) unsigned char gdev_[160] = {0};   // GmresDev (device pointers of the cycle state)
+  cudaEvent_t ev_[2] = {nullptr, nullptr};
   size_t bytes_ = 0;
 };
 
