@@ -141,6 +141,7 @@ typedef struct mm_array_info {
   int64_t fft[3];        /* padded FFT lengths per axis                       */
   int64_t nnz_near;      /* near-field nonzeros                               */
   int64_t device_bytes;  /* resident operator bytes on the device             */
+  int64_t n_scat_unknowns; /* N_s = sum of the elements' scatterer RWG unknowns */
 } mm_array_info;
 mm_status mm_array_info_get(const mm_array* array, mm_array_info* info);
 /* Device bytes a solve with nrhs columns needs beyond the resident operator
@@ -183,6 +184,31 @@ mm_status mm_apply_host(mm_array* array, int32_t nrhs, const void* x_host, void*
  * (N^ x nrhs) in `precision`.                                                 */
 mm_status mm_rhs_planewave(mm_array* array, int32_t nrhs, const double* theta, const double* phi,
                            const int32_t* pol, void* V_dev, int32_t precision, void* stream);
+
+/* Currents of a solution (Sec. II, eq. (JABE) and eq. (Tm1); Sec. IV after
+ * eq. (finalsystem)): per element, J_e = -A_t^-1 B_t E^_e on the scatterer
+ * (RWG coefficients on S_e, N_t per element) and J^_e = T_t J_e on the
+ * equivalent surface (N^_t per element).  E_dev: (N^ x nrhs) complex128.
+ * J_dev: (N_s x nrhs) complex128 with N_s = sum of the elements' scatterer
+ * unknowns (mm_array_info.n_scat_unknowns), element-major, or NULL; Jhat_dev:
+ * (N^ x nrhs) complex128 or NULL.  FP64 throughout.  Queued on `stream`.    */
+mm_status mm_currents(mm_array* array, int32_t nrhs, const void* E_dev, void* J_dev, void* Jhat_dev, void* stream);
+
+/* Far-field pattern radiated by the equivalent currents (the radiation
+ * integral of the array's patterns, Sec. VI): with E ~ F exp(-j k0 r)/r,
+ *   F(r^) = -j k0 eta0/(4 pi) (I - r^ r^) . sum_n J^_n int f^_n exp(j k0 r^.r') dS'
+ * (7-point rule per triangle; phases reduced in FP64, exponentials and sums in
+ * FP32).  r^ = (sin t cos p, sin t sin p, cos t) for host arrays theta, phi of
+ * length ndir.  Jhat_dev: (N^ x nrhs) complex128; F_dev: (ndir x nrhs x 3)
+ * complex128, Cartesian components.  Queued on `stream`.                       */
+mm_status mm_farfield(mm_array* array, int32_t nrhs, const void* Jhat_dev, int64_t ndir, const double* theta,
+                      const double* phi, void* F_dev, void* stream);
+
+/* Bistatic RCS sigma = 4 pi |F|^2 / |E0|^2 (|E0| = 1; lambda^2 units when
+ * k0 = 2 pi) from mm_farfield, written to sigma_host (ndir x nrhs).
+ * Synchronous.                                                                */
+mm_status mm_rcs(mm_array* array, int32_t nrhs, const void* Jhat_dev, int64_t ndir, const double* theta,
+                 const double* phi, double* sigma_host);
 
 /* GMRES solve of (D - G T A^-1 B) E^ = V^ (eq. (finalsystem); Sec. V) for
  * nrhs independent columns, x0 = 0.  precision MM_C128: plain FP64 GMRES on

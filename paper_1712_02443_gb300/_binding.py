@@ -43,7 +43,7 @@ class mm_aim_opts(ct.Structure):
 class mm_array_info(ct.Structure):
     _fields_ = [("n_unknowns", ct.c_int64), ("n_elem", ct.c_int64), ("n_types", ct.c_int64),
                 ("grid", ct.c_int64 * 3), ("fft", ct.c_int64 * 3), ("nnz_near", ct.c_int64),
-                ("device_bytes", ct.c_int64)]
+                ("device_bytes", ct.c_int64), ("n_scat_unknowns", ct.c_int64)]
 
 
 class mm_solve_opts(ct.Structure):
@@ -81,6 +81,9 @@ _SIGS = {
     "mm_apply_noalloc": (ct.c_int, [P, ct.c_int32, P, P, ct.c_int32, P]),
     "mm_rhs_planewave": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.c_int32, P]),
     "mm_solve": (ct.c_int, [P, ct.c_int32, P, P, ct.POINTER(mm_solve_opts), ct.POINTER(mm_solve_stats), P]),
+    "mm_currents": (ct.c_int, [P, ct.c_int32, P, P, P, P]),
+    "mm_farfield": (ct.c_int, [P, ct.c_int32, P, ct.c_int64, P, P, P, P]),
+    "mm_rcs": (ct.c_int, [P, ct.c_int32, P, ct.c_int64, P, P, P]),
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
     "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
 }
@@ -212,7 +215,8 @@ def mm_array_info_get(array) -> dict:
     i = mm_array_info()
     _check(load().mm_array_info_get(array, ct.byref(i)), _ctx_of.get(array.value))
     return {"n_unknowns": i.n_unknowns, "n_elem": i.n_elem, "n_types": i.n_types, "grid": tuple(i.grid),
-            "fft": tuple(i.fft), "nnz_near": i.nnz_near, "device_bytes": i.device_bytes}
+            "fft": tuple(i.fft), "nnz_near": i.nnz_near, "device_bytes": i.device_bytes,
+            "n_scat_unknowns": i.n_scat_unknowns}
 
 
 def mm_array_footprint(array, nrhs: int, precision: int, restart: int) -> int:
@@ -261,6 +265,27 @@ def mm_rhs_planewave(array, theta, phi, pol, V_dev, precision: int, stream=None)
     po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
     _check(load().mm_rhs_planewave(array, len(th), _ptr(th), _ptr(ph), _ptr(po), _ptr(V_dev), precision,
                                    _stream(stream)), _ctx_of.get(array.value))
+
+
+def mm_currents(array, nrhs: int, E_dev, J_dev=None, Jhat_dev=None, stream=None) -> None:
+    _check(load().mm_currents(array, nrhs, _ptr(E_dev), _ptr(J_dev), _ptr(Jhat_dev), _stream(stream)),
+           _ctx_of.get(array.value))
+
+
+def mm_farfield(array, nrhs: int, Jhat_dev, theta, phi, F_dev, stream=None) -> None:
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    _check(load().mm_farfield(array, nrhs, _ptr(Jhat_dev), len(th), _ptr(th), _ptr(ph), _ptr(F_dev), _stream(stream)),
+           _ctx_of.get(array.value))
+
+
+def mm_rcs(array, nrhs: int, Jhat_dev, theta, phi) -> np.ndarray:
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    out = np.zeros((len(th), nrhs), dtype=np.float64)
+    _check(load().mm_rcs(array, nrhs, _ptr(Jhat_dev), len(th), _ptr(th), _ptr(ph), _ptr(out)),
+           _ctx_of.get(array.value))
+    return out
 
 
 def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_iter: int = 1000,

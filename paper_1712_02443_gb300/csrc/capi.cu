@@ -14,6 +14,7 @@
 #include "device.h"
 #include "internal.h"
 #include "macroaim.h"
+#include "post.h"
 #include "solver.h"
 
 struct mm_ctx {
@@ -45,6 +46,12 @@ struct mm_array {
   void* hy = nullptr;
   size_t h_cap = 0;
   std::unique_ptr<mm::Solver> solver;
+  // post-processing operators (uploaded on first use): per type -A^-1 B and T, scatterer offsets
+  std::vector<void*> d_JE, d_T;
+  int64_t* d_offs = nullptr;
+  std::vector<int64_t> offs;      // host: scatterer unknown offsets (n_elem + 1)
+  double* d_dir = nullptr;        // device: theta, phi of the far-field directions
+  int64_t dir_cap = 0;
   ~mm_array();
 };
 
@@ -200,8 +207,11 @@ mm_array::~mm_array() {
   for (auto* p : da.inv_ptr) cudaFree(p);
   for (auto* p : da.inv_ent) cudaFree(p);
   for (void* q : {(void*)da.off, (void*)da.boxorg, (void*)da.type_of, (void*)da.eoff, (void*)da.rowptr,
-                  (void*)da.col, (void*)elem_of, (void*)geo_ptrs, (void*)d_ang, (void*)d_pol, hx, hy})
+                  (void*)da.col, (void*)elem_of, (void*)geo_ptrs, (void*)d_ang, (void*)d_pol, hx, hy, (void*)d_offs,
+                  (void*)d_dir})
     if (q) cudaFree(q);
+  for (void* q : d_JE) cudaFree(q);
+  for (void* q : d_T) cudaFree(q);
 }
 
 extern "C" {
@@ -334,6 +344,8 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
   em.nthreads = ctx->nthreads;
   a->k0 = em.k;
   a->eta0 = em.eta0;
+  a->offs.assign(n_elem + 1, 0);
+  for (int64_t e = 0; e < n_elem; ++e) a->offs[e + 1] = a->offs[e] + tms[type_of[e]]->N;
   std::vector<mm::Vec3> offs(n_elem);
   for (int64_t e = 0; e < n_elem; ++e) offs[e] = {offsets_xyz[3 * e], offsets_xyz[3 * e + 1], offsets_xyz[3 * e + 2]};
   mm::AimOpts ao{opts->h, opts->order, opts->n_nf, {opts->phase[0], opts->phase[1], opts->phase[2]}};
@@ -456,6 +468,7 @@ mm_status mm_array_info_get(const mm_array* a, mm_array_info* info) {
   }
   info->nnz_near = a->ah.rowptr.empty() ? 0 : a->ah.rowptr.back();
   info->device_bytes = (int64_t)a->da.bytes;
+  info->n_scat_unknowns = a->offs.empty() ? 0 : a->offs.back();
   return MM_OK;
 }
 
@@ -666,6 +679,111 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
   if (!conv) return fail(ctx, MM_ENOCONV, "GMRES reached max_iter before the tolerance");
   return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_currents(mm_array* a, int32_t nrhs, const void* E_dev, void* J_dev, void* Jhat_dev, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !E_dev) return fail(ctx, MM_EINVAL, "invalid currents arguments");
+  if (!J_dev && !Jhat_dev) return MM_OK;
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  auto& da = a->da;
+  if (a->d_JE.empty()) {
+    size_t acc = 0;
+    for (int64_t t = 0; t < da.n_types; ++t) {
+      const auto& tm = a->types[t]->tm;
+      a->d_JE.push_back(dev_upload(tm.JE.data(), tm.JE.size(), acc));
+      a->d_T.push_back(dev_upload(tm.T.data(), tm.T.size(), acc));
+    }
+    a->d_offs = dev_upload(a->offs.data(), a->offs.size(), acc);
+    da.bytes += acc;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* J = J_dev;
+  void* tmp = nullptr;
+  if (!J) {   // J^ alone still needs J
+    CU(cudaMallocAsync(&tmp, sizeof(double2) * (size_t)a->offs.back() * nrhs, st));
+    J = tmp;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int64_t t = 0; t < da.n_types && e == cudaSuccess; ++t) {
+    const auto& tm = a->types[t]->tm;
+    e = mm::elem_gemm(a->d_JE[t], (int)tm.N, (int)tm.Nh, da.elems[t], (int)da.n_of_type[t], nrhs, da.off, E_dev,
+                      a->d_offs, J, st);
+    if (e == cudaSuccess && Jhat_dev)
+      e = mm::elem_gemm(a->d_T[t], (int)tm.Nh, (int)tm.N, da.elems[t], (int)da.n_of_type[t], nrhs, a->d_offs, J,
+                        da.off, Jhat_dev, st);
+  }
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("currents: ") + cudaGetErrorString(e));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_farfield(mm_array* a, int32_t nrhs, const void* Jhat_dev, int64_t ndir, const double* theta,
+                      const double* phi, void* F_dev, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || nrhs > 65535 || !Jhat_dev || ndir < 0 || ndir > 2147483647LL || (ndir > 0 && (!theta || !phi)) ||
+      !F_dev)
+    return fail(ctx, MM_EINVAL, "invalid far-field arguments");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (a->dir_cap < ndir) {
+    if (a->d_dir) cudaFree(a->d_dir);
+    a->d_dir = nullptr;
+    CU(cudaMalloc(&a->d_dir, sizeof(double) * 2 * (size_t)ndir));
+    a->dir_cap = ndir;
+  }
+  std::vector<double> dirs(2 * (size_t)ndir);
+  std::copy(theta, theta + ndir, dirs.begin());
+  std::copy(phi, phi + ndir, dirs.begin() + ndir);
+  CU(cudaMemcpyAsync(a->d_dir, dirs.data(), sizeof(double) * 2 * (size_t)ndir, cudaMemcpyHostToDevice, st));
+  mm::Rule r7 = mm::rule_tri7();
+  mm::QuadRule q;
+  q.n = r7.n();
+  for (int i = 0; i < q.n; ++i) {
+    q.b0[i] = r7.b0[i]; q.b1[i] = r7.b1[i]; q.b2[i] = r7.b2[i]; q.w[i] = r7.w[i];
+  }
+  cudaError_t e = mm::farfield(a->da, a->elem_of, a->geo_ptrs, nrhs, Jhat_dev, ndir, a->d_dir, a->d_dir + ndir, a->k0,
+                               a->eta0, q, F_dev, st);
+  if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("far field: ") + cudaGetErrorString(e));
+  CU(cudaStreamSynchronize(st));   // the host staging of the directions is released on return
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_rcs(mm_array* a, int32_t nrhs, const void* Jhat_dev, int64_t ndir, const double* theta, const double* phi,
+                 double* sigma_host) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!sigma_host) return fail(ctx, MM_EINVAL, "null sigma");
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  void* F = nullptr;
+  CU(cudaMalloc(&F, sizeof(double2) * 3 * (size_t)std::max<int64_t>(ndir, 1) * nrhs));
+  mm_status s = mm_farfield(a, nrhs, Jhat_dev, ndir, theta, phi, F, nullptr);
+  if (s == MM_OK) {
+    std::vector<double2> h(3 * (size_t)ndir * nrhs);
+    cudaError_t e = cudaMemcpy(h.data(), F, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cudaFree(F);
+      return fail(ctx, MM_ECUDA, std::string("rcs copy: ") + cudaGetErrorString(e));
+    }
+    for (int64_t i = 0; i < ndir * nrhs; ++i) {
+      double p = 0;
+      for (int c = 0; c < 3; ++c) p += h[3 * i + c].x * h[3 * i + c].x + h[3 * i + c].y * h[3 * i + c].y;
+      sigma_host[i] = 4.0 * M_PI * p;
+    }
+  }
+  cudaFree(F);
+  return s;
   API_CATCH(ctx)
 }
 

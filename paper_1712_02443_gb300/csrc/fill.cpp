@@ -401,6 +401,8 @@ void build_type(TypeModel& tm) {
   std::vector<cd> Y = tm.B;
   lu_solve(la, Y, Nh, em.nthreads);             // A^-1 B
   gemm(tm.T, Y, tm.M, Nh, N, Nh, em.nthreads);  // M = T A^-1 B
+  tm.JE.resize(Y.size());
+  for (size_t i = 0; i < Y.size(); ++i) tm.JE[i] = -Y[i];
 }
 
 }  // namespace mm

@@ -115,6 +115,7 @@ struct TypeModel {
   EM em;
   int64_t N = 0, Nh = 0;
   std::vector<cd> M, D, T, A, B, GHH, GHE;   // row-major
+  std::vector<cd> JE;                         // -A^-1 B (N x N^): scatterer currents from E^, eq. (JABE)
 };
 void build_type(TypeModel& tm);
 

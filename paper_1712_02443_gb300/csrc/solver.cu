@@ -3,11 +3,15 @@
 // independent columns for several right-hand sides, and FP64 iterative
 // refinement around a complex64 inner operator.  Also the plane-wave
 // excitation kernel (Sec. IV, eq. (V1)).
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstdio>
 #include <vector>
 
 #include "solver.h"
+
+namespace cg = cooperative_groups;
 
 namespace mm {
 
@@ -434,6 +438,177 @@ __global__ void k_add_basis_dev(const Z* __restrict__ V, int64_t vs, GmresDev gd
   }
 }
 
+
+// One Arnoldi step for all columns in a single cooperative launch (all blocks
+// resident; grid-wide barriers between the phases, no spin-waits of our own):
+//  0. w = operator output (complex64 -> FP64) on this block's rows;
+//  1. partial <V_i, w>, i <= k;                         [grid sync]
+//  2. h = sum of partials; w -= V h; partial <V_i, w>;  [grid sync]
+//  3. h2 = sum of partials; w -= V h2; partial ||w||^2; [grid sync]
+//  4. block 0: Hessenberg column h + h2, Givens, residual estimate, k += 1;
+//                                                       [grid sync]
+//  5. V[k+1] = w / ||w|| (0 for finished columns), next operator input.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t vs, Z* __restrict__ w,
+                                                      const Tin* __restrict__ yin, Tout* __restrict__ xnext,
+                                                      GmresDev gd, int64_t N, Z* __restrict__ P1,
+                                                      Z* __restrict__ P2, double* __restrict__ PN) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ Z sm[];
+  const int m = gd.m, r = gd.r;
+  const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  Z* hs = sm;                        // (m+1) r   h, then h + h2 in block 0
+  Z* h2s = hs + (m + 1) * r;         // (m+1) r
+  Z* ws = h2s + (m + 1) * r;         // (m+1) nw  warp partials
+  const int k = *gd.k;
+  const int nblk = gridDim.x, blk = blockIdx.x;
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  // phase 0
+  if (yin != nullptr)
+    for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) w[t] = make_double2((double)yin[t].x, (double)yin[t].y);
+  __syncthreads();
+  // phase 1
+  for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P1), __syncthreads();
+  grid.sync();
+  // phase 2
+  for (int j = 0; j < r; ++j) {
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+      Z acc = make_double2(0, 0);
+      for (int b = 0; b < nblk; ++b) {
+        const Z v = P1[((int64_t)i * r + j) * nblk + b];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      hs[i * r + j] = acc;
+    }
+  }
+  __syncthreads();
+  for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
+    const int j = (int)(t % r);
+    Z a = w[t];
+    for (int i = 0; i <= k; ++i) {
+      const Z p = zmul(V[(int64_t)i * vs + t], hs[i * r + j]);
+      a.x -= p.x;
+      a.y -= p.y;
+    }
+    w[t] = a;
+  }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2), __syncthreads();
+  grid.sync();
+  // phase 3
+  for (int j = 0; j < r; ++j) {
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+      Z acc = make_double2(0, 0);
+      for (int b = 0; b < nblk; ++b) {
+        const Z v = P2[((int64_t)i * r + j) * nblk + b];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      h2s[i * r + j] = acc;
+    }
+  }
+  __syncthreads();
+  {
+    for (int j = 0; j < r; ++j) {
+      double acc = 0;
+      for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+        const int64_t t = nn * r + j;
+        Z a = w[t];
+        for (int i = 0; i <= k; ++i) {
+          const Z p = zmul(V[(int64_t)i * vs + t], h2s[i * r + j]);
+          a.x -= p.x;
+          a.y -= p.y;
+        }
+        w[t] = a;
+        acc += a.x * a.x + a.y * a.y;
+      }
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+      if (lane == 0) ws[warp].x = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t2 = 0;
+        for (int q = 0; q < nw; ++q) t2 += ws[q].x;
+        PN[(int64_t)j * nblk + blk] = t2;
+      }
+      __syncthreads();
+    }
+  }
+  grid.sync();
+  // phase 4: block 0, warp per column
+  if (blk == 0) {
+    for (int j = warp; j < r; j += nw) {
+      if (!gd.active[j]) continue;
+      double s2 = 0;
+      for (int b = lane; b < nblk; b += 32) s2 += PN[(int64_t)j * nblk + b];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, s);
+      if (lane == 0) {
+        Z* hc = hs;  // column j lives at hs[i r + j]
+        for (int i = 0; i <= k; ++i) {
+          hc[i * r + j].x += h2s[i * r + j].x;
+          hc[i * r + j].y += h2s[i * r + j].y;
+        }
+        const double hn = sqrt(fmax(0.0, s2));
+        Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
+        for (int i = 0; i < k; ++i) {   // previous rotations [[conj c, conj s], [-s, c]]
+          const Z c = gd.cs[(int64_t)i * r + j], sg = gd.sn[(int64_t)i * r + j];
+          const Z a = hc[i * r + j], bb = hc[(i + 1) * r + j];
+          const Z t1 = zconjmul(c, a), t2 = zconjmul(sg, bb);
+          const Z u1 = zmul(sg, a), u2 = zmul(c, bb);
+          hc[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
+          hc[(i + 1) * r + j] = make_double2(u2.x - u1.x, u2.y - u1.y);
+        }
+        const Z a = hc[k * r + j];   // rotated entry k; the new rotation pairs it with hn
+        const double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
+        const Z c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1, 0);
+        const Z sg = den > 0 ? make_double2(hn / den, 0) : make_double2(0, 0);
+        gd.cs[(int64_t)k * r + j] = c;
+        gd.sn[(int64_t)k * r + j] = sg;
+        for (int i = 0; i < k; ++i) H[i] = hc[i * r + j];
+        H[k] = make_double2(den, 0);
+        const Z gk = gd.g[(int64_t)k * r + j];
+        const Z sgk = zmul(sg, gk);
+        gd.g[(int64_t)(k + 1) * r + j] = make_double2(-sgk.x, -sgk.y);
+        gd.g[(int64_t)k * r + j] = zconjmul(c, gk);
+        const double res = sqrt(sgk.x * sgk.x + sgk.y * sgk.y);
+        gd.res[j] = res;
+        gd.kdone[j] = k + 1;
+        const int stop = !(res > gd.tol[j]) || hn == 0.0 || !isfinite(hn);
+        gd.active[j] = stop ? 0 : 1;
+        gd.scale[j] = stop ? 0.0 : 1.0 / hn;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int any = 0, kd = 0;
+      for (int j = 0; j < r; ++j) {
+        any |= gd.active[j];
+        kd = max(kd, gd.kdone[j]);
+      }
+      *gd.k = k + 1;
+      gd.flag[0] = any;
+      gd.flag[1] = k + 1;
+      gd.flag[2] = kd;
+      __threadfence_system();
+    }
+  }
+  grid.sync();
+  // phase 5: next basis vector and the next operator input
+  for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
+    const int j = (int)(t % r);
+    const double sc = gd.scale[j];
+    const Z v = make_double2(w[t].x * sc, w[t].y * sc);
+    V[(int64_t)(k + 1) * vs + t] = v;
+    Tout o;
+    o.x = v.x;
+    o.y = v.y;
+    xnext[t] = o;
+  }
+}
+
 static unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -451,7 +626,27 @@ Status Solver::ensure(int64_t N, int r, int m) {
   if (N == N_ && r == r_ && m <= m_) return {MM_OK, ""};
   release();
   N_ = N; r_ = r; m_ = m;
-  nblk_ = (int)std::min<int64_t>(128, std::max<int64_t>(1, N / 2048));
+  {
+    // partial-sum blocks: the co-resident grid of the cooperative Arnoldi step
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    coop_smem_ = sizeof(Z) * (size_t)(m + 1) * (2 * r + 8);
+    coop_ok_ = coop_smem_ <= 200 * 1024;
+    if (coop_ok_) {
+      MM_CK(cudaFuncSetAttribute(k_arnoldi_step<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coop_smem_));
+      MM_CK(cudaFuncSetAttribute(k_arnoldi_step<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coop_smem_));
+      int p1 = 0, p2 = 0;
+      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_arnoldi_step<float2, float2>, 256, coop_smem_));
+      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_arnoldi_step<double2, double2>, 256, coop_smem_));
+      per = std::min(std::min(p1, p2), 2);
+      coop_ok_ = per >= 1;
+    }
+    int64_t want = coop_ok_ ? (int64_t)sms * per : 128;
+    nblk_ = (int)std::max<int64_t>(1, std::min<int64_t>(want, (N + 63) / 64));
+  }
   size_t vec = sizeof(Z) * (size_t)N * r;
   MM_CK(cudaMalloc(&V_, vec * (m + 1)));
   MM_CK(cudaMalloc(&w_, vec));
@@ -601,32 +796,60 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     }
     bool stopped = false;
     int launched = 0;
+    // first basis vector V[0] = r0/||r0|| and the operator input
+    if (prec == MM_C128)
+      k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
+    else
+      k_fetch<float2><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<float2*>(x32_));
     for (int it = 0; it < m && iters + it < max_iter; ++it) {
-      // fetch V[k] = w / ||w|| and hand it to the operator
+      const void* yin = nullptr;
       if (prec == MM_C128) {
-        k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
         Status s1 = op64(static_cast<const Z*>(x64_), w, st);
         if (s1.code != MM_OK) return s1;
       } else {
-        if (prof) prof->begin(7, st);
-        k_fetch<float2><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<float2*>(x32_));
-        if (prof) prof->end(st, 1);
         Status s1 = op32(x32_, y32_, st);
         if (s1.code != MM_OK) return s1;
-        if (prof) prof->begin(7, st);
-        k_to_c128<<<grid_for(n), 256, 0, st>>>(static_cast<const float2*>(y32_), w, n);
-        if (prof) prof->end(st, 1);
+        yin = y32_;
       }
       ++matvecs;
       if (prof) prof->begin(7, st);
-      k_cgs_dots<<<dim3(nblk_, r), 32 * nw, sh_dots, st>>>(V, vs, w, gd, N, nblk_, static_cast<Z*>(P1_));
-      k_cgs_update_dots<<<dim3(nblk_, r), 32 * nw, sh_upd, st>>>(V, vs, gd, static_cast<const Z*>(P1_), w, N, nblk_,
-                                                                 static_cast<Z*>(P2_));
-      k_cgs_update_norm<<<dim3(nblk_, r), 32 * nw, sizeof(Z) * (m + 1), st>>>(
-          V, vs, gd, static_cast<const Z*>(P2_), w, N, nblk_, static_cast<double*>(PN_));
-      k_givens<<<1, 32 * nw, sh_giv, st>>>(gd, static_cast<const Z*>(P1_), static_cast<const Z*>(P2_),
-                                           static_cast<const double*>(PN_), nblk_);
-      if (prof) prof->end(st, 4);
+      if (coop_ok_) {
+        Z* Vp = V;
+        int64_t vsp = vs;
+        Z* wp = w;
+        Z* P1p = static_cast<Z*>(P1_);
+        Z* P2p = static_cast<Z*>(P2_);
+        double* PNp = static_cast<double*>(PN_);
+        int64_t Np = N;
+        if (prec == MM_C128) {
+          const double2* yp = nullptr;
+          double2* xp = static_cast<double2*>(x64_);
+          void* args[] = {&Vp, &vsp, &wp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
+          MM_CK(cudaLaunchCooperativeKernel((void*)k_arnoldi_step<double2, double2>, dim3(nblk_), dim3(256), args,
+                                            coop_smem_, st));
+        } else {
+          const float2* yp = static_cast<const float2*>(yin);
+          float2* xp = static_cast<float2*>(x32_);
+          void* args[] = {&Vp, &vsp, &wp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
+          MM_CK(cudaLaunchCooperativeKernel((void*)k_arnoldi_step<float2, float2>, dim3(nblk_), dim3(256), args,
+                                            coop_smem_, st));
+        }
+        if (prof) prof->end(st, 1);
+      } else {
+        if (yin) k_to_c128<<<grid_for(n), 256, 0, st>>>(static_cast<const float2*>(yin), w, n);
+        k_cgs_dots<<<dim3(nblk_, r), 32 * nw, sh_dots, st>>>(V, vs, w, gd, N, nblk_, static_cast<Z*>(P1_));
+        k_cgs_update_dots<<<dim3(nblk_, r), 32 * nw, sh_upd, st>>>(V, vs, gd, static_cast<const Z*>(P1_), w, N,
+                                                                   nblk_, static_cast<Z*>(P2_));
+        k_cgs_update_norm<<<dim3(nblk_, r), 32 * nw, sizeof(Z) * (m + 1), st>>>(
+            V, vs, gd, static_cast<const Z*>(P2_), w, N, nblk_, static_cast<double*>(PN_));
+        k_givens<<<1, 32 * nw, sh_giv, st>>>(gd, static_cast<const Z*>(P1_), static_cast<const Z*>(P2_),
+                                             static_cast<const double*>(PN_), nblk_);
+        if (prec == MM_C128)
+          k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
+        else
+          k_fetch<float2><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<float2*>(x32_));
+        if (prof) prof->end(st, yin ? 6 : 5);
+      }
       MM_CK(cudaGetLastError());
       MM_CK(cudaEventRecord(ev_[it & 1], st));
       launched = it + 1;

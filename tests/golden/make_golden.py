@@ -6,8 +6,9 @@ arithmetic:  python tests/golden/make_golden.py
 
 Files (numpy .npz, complex128):
   c1_2x2.npz      2x2 loop array: x, y = Z_AIM x (full), V (theta=0 x-pol),
-                  E = solution of the AIM system to 1e-12, and E_dense (dense
-                  exterior operator) for reference.
+                  E = solution of the AIM system to 1e-12, E_dense (dense
+                  exterior operator) for reference, the currents J, J^ of E,
+                  and the far field F and RCS of J^ on 38 directions.
   ragged_3x5.npz  3x5 loop array, 3 right-hand sides: y (N x 3, full) for
                   x = workloads.random_cvec(N, 0, 8, nrhs=3) (checksum stored).
   c2_16x16.npz    16x16 loop array: sampled rows and y[rows] for
@@ -29,7 +30,9 @@ from paper_1712_02443_gb300 import workloads as wl  # noqa: E402
 from oracle.aim import AIMArray, AIMParams, BlockCache  # noqa: E402
 from oracle.gmres import gmres  # noqa: E402
 from oracle.macromodel import build_element, dense_exterior_operator, translated_rwg  # noqa: E402
-from oracle.operators import excitation  # noqa: E402
+from oracle.basis import build_rwg  # noqa: E402
+from oracle.mom import merge_meshes  # noqa: E402
+from oracle.operators import excitation, far_field, rcs  # noqa: E402
 
 K0 = 2.0 * np.pi
 H, ORDER, NNF = 0.1, 2, 3
@@ -57,8 +60,18 @@ def main():
     E, it, hist = gmres(A.matvec, V, tol=1e-12, restart=100, max_iter=2000)
     Z = dense_exterior_operator([em], lay.type_of, lay.offsets, K0)
     Ed = np.linalg.solve(Z, V)
+    # currents of the solution (eq. (JABE), eq. (Tm1)) and the far field of J^
+    nh = em.rwg_e.n
+    JJ = [em.currents(E[e * nh:(e + 1) * nh]) for e in range(len(lay.offsets))]
+    J = np.concatenate([c[0] for c in JJ])
+    Jh = np.concatenate([c[1] for c in JJ])
+    xyz, tri = merge_meshes([lay.types[0].equiv.translated(o) for o in lay.offsets])
+    rw = build_rwg(xyz, tri)
+    th = np.deg2rad(np.concatenate([np.arange(0, 181, 10.0), np.arange(0, 181, 10.0)]))
+    ph = np.deg2rad(np.concatenate([np.zeros(19), np.full(19, 90.0)]))
+    F = far_field(rw, Jh, th, ph, K0)
     np.savez_compressed(os.path.join(HERE, "c1_2x2.npz"), x=x, y=y, V=V, E=E, E_dense=Ed,
-                        offsets=lay.offsets, gmres_iters=it)
+                        offsets=lay.offsets, gmres_iters=it, J=J, Jhat=Jh, theta=th, phi=ph, F=F, sigma=rcs(F))
     print("c1", time.time() - t0, "iters", it)
 
     # ragged 3x5, 3 RHS

@@ -147,3 +147,33 @@ def test_aliasing_arguments_rejected(c1):
     with pytest.raises(mm.MacroAIMError) as e:
         mm.mm_apply(c1.array, 1, x, x, mm.MM_C64)
     assert e.value.status == mm.MM_EINVAL
+
+
+def test_currents_match_oracle(c1):
+    """J = -A^-1 B E^ and J^ = T J per element (eqs. (JABE), (Tm1)), FP64."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    E = torch.from_numpy(g["E"]).cuda()
+    ns = c1.info["n_scat_unknowns"]
+    assert ns == len(g["J"])
+    J = torch.empty(ns, dtype=torch.complex128, device="cuda")
+    Jh = torch.empty_like(E)
+    mm.mm_currents(c1.array, 1, E, J, Jh, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    for got, ref in ((J.cpu().numpy(), g["J"]), (Jh.cpu().numpy(), g["Jhat"])):
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+def test_farfield_and_rcs_match_oracle(c1):
+    """Far field of J^ (FP32 exponentials and sums): relative L2 <= 1e-5; RCS within
+    0.01 dB wherever sigma is within 40 dB of its maximum."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    Jh = torch.from_numpy(g["Jhat"]).cuda()
+    nd = len(g["theta"])
+    F = torch.empty(nd * 3, dtype=torch.complex128, device="cuda")
+    mm.mm_farfield(c1.array, 1, Jh, g["theta"], g["phi"], F, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    Fg = F.cpu().numpy().reshape(nd, 3)
+    assert np.linalg.norm(Fg - g["F"]) / np.linalg.norm(g["F"]) <= 1e-5
+    sig = mm.mm_rcs(c1.array, 1, Jh, g["theta"], g["phi"])[:, 0]
+    top = g["sigma"] >= g["sigma"].max() * 1e-4
+    assert np.abs(10 * np.log10(sig[top] / g["sigma"][top])).max() <= 0.01
