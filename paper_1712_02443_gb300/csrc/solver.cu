@@ -176,21 +176,32 @@ __device__ __forceinline__ Z warp_sum(Z v) {
 }
 
 // Partial dot products of w with V_0..V_k over one block of rows:
-// P[(i r + j) nblk + blk].  `sh` holds (m+1) x nwarps partial sums.
+// P[(i r + j) nblk + blk].  `sh` holds (m+1) x nwarps partial sums.  Four basis
+// vectors per pass keep several loads in flight.
 __device__ void block_dots(const Z* __restrict__ V, int64_t vs, const Z* __restrict__ w, int k, int64_t n0,
                            int64_t n1, int r, int j, int blk, int nblk, Z* sh, Z* __restrict__ P) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int i = 0; i <= k; ++i) {
-    Z acc = make_double2(0, 0);
-    const Z* vi = V + (int64_t)i * vs;
+  for (int i0 = 0; i0 <= k; i0 += 4) {
+    Z acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0, 0);
     for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
       const int64_t t = nn * r + j;
-      const Z p = zconjmul(vi[t], w[t]);
-      acc.x += p.x;
-      acc.y += p.y;
+      const Z wt = w[t];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (i0 + q <= k) {
+          const Z p = zconjmul(V[(int64_t)(i0 + q) * vs + t], wt);
+          acc[q].x += p.x;
+          acc[q].y += p.y;
+        }
+      }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) sh[i * nw + warp] = acc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const Z a = warp_sum(acc[q]);
+      if (lane == 0 && i0 + q <= k) sh[(i0 + q) * nw + warp] = a;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
@@ -201,6 +212,23 @@ __device__ void block_dots(const Z* __restrict__ V, int64_t vs, const Z* __restr
     }
     P[((int64_t)i * r + j) * nblk + blk] = acc;
   }
+}
+
+// dst[i r + j] = sum over blocks of P for i <= k and all columns: a warp per (i, j).
+__device__ void reduce_all_partials(const Z* __restrict__ P, int k, int r, int nblk, Z* dst) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int p = warp; p < (k + 1) * r; p += nw) {
+    const int i = p / r, j = p % r;
+    const Z* src = P + ((int64_t)i * r + j) * nblk;
+    Z acc = make_double2(0, 0);
+    for (int b = lane; b < nblk; b += 32) {
+      acc.x += src[b].x;
+      acc.y += src[b].y;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) dst[i * r + j] = acc;
+  }
+  __syncthreads();
 }
 
 // CGS pass 1: partial <V_i, w>, i <= k.  Grid (nblk, r).
@@ -471,21 +499,11 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P1), __syncthreads();
   grid.sync();
   // phase 2
-  for (int j = 0; j < r; ++j) {
-    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-      Z acc = make_double2(0, 0);
-      for (int b = 0; b < nblk; ++b) {
-        const Z v = P1[((int64_t)i * r + j) * nblk + b];
-        acc.x += v.x;
-        acc.y += v.y;
-      }
-      hs[i * r + j] = acc;
-    }
-  }
-  __syncthreads();
+  reduce_all_partials(P1, k, r, nblk, hs);
   for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
     const int j = (int)(t % r);
     Z a = w[t];
+#pragma unroll 4
     for (int i = 0; i <= k; ++i) {
       const Z p = zmul(V[(int64_t)i * vs + t], hs[i * r + j]);
       a.x -= p.x;
@@ -497,24 +515,14 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2), __syncthreads();
   grid.sync();
   // phase 3
-  for (int j = 0; j < r; ++j) {
-    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-      Z acc = make_double2(0, 0);
-      for (int b = 0; b < nblk; ++b) {
-        const Z v = P2[((int64_t)i * r + j) * nblk + b];
-        acc.x += v.x;
-        acc.y += v.y;
-      }
-      h2s[i * r + j] = acc;
-    }
-  }
-  __syncthreads();
+  reduce_all_partials(P2, k, r, nblk, h2s);
   {
     for (int j = 0; j < r; ++j) {
       double acc = 0;
       for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
         const int64_t t = nn * r + j;
         Z a = w[t];
+#pragma unroll 4
         for (int i = 0; i <= k; ++i) {
           const Z p = zmul(V[(int64_t)i * vs + t], h2s[i * r + j]);
           a.x -= p.x;
