@@ -13,6 +13,10 @@ Files (numpy .npz, complex128):
                   x = workloads.random_cvec(N, 0, 8, nrhs=3) (checksum stored).
   c2_16x16.npz    16x16 loop array: sampled rows and y[rows] for
                   x = workloads.random_cvec(N, 1, 7) (checksum stored).
+  c3_types_6x6.npz  6x6 array of the four loop types (outer 0.30/0.34/0.38/0.42,
+                  seeded per cell), 64 right-hand sides: sampled rows of
+                  y = Z_AIM X for X = workloads.random_cvec(N, 2, 7, nrhs=64),
+                  and of the plane-wave excitation for the 8 x 8 incidence grid.
 """
 from __future__ import annotations
 
@@ -91,6 +95,30 @@ def main():
     yr = A.matvec_rows(x, rows)
     np.savez_compressed(os.path.join(HERE, "c2_16x16.npz"), x_check=_check(x), rows=rows, y_rows=yr)
     print("c2", time.time() - t0)
+
+    # c3 family: four element types, 64 right-hand sides (a 6x6 instance)
+    outers = (0.30, 0.34, 0.38, 0.42)
+    lay = wl.loop_array(6, 6, outers=outers, config_index=2)
+    ems = [build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0) for et in lay.types]
+    print("c3 elements", time.time() - t0)
+    A = AIMArray(ems, lay.type_of, lay.offsets, params, K0, rows_only=True)
+    X = wl.random_cvec(A.n, 2, 7, nrhs=64)
+    g = wl.rng(2, 9)
+    rows = np.unique(np.concatenate([np.arange(4), A.n - 4 + np.arange(4), g.choice(A.n, 40, replace=False)]))
+    G = A.near_field_rows(rows)
+    Y = np.zeros((len(rows), 64), dtype=np.complex128)
+    for j in range(64):
+        u = A.macro(X[:, j])
+        Y[:, j] = A.dapply(X[:, j], rows) - (A.far(u, rows) + G @ u)
+    th, ph, pol = wl.planewave_grid()
+    Vr = np.zeros((len(rows), 64), dtype=np.complex128)
+    for e in np.unique(A.elem_of[rows]):
+        sel = np.where(A.elem_of[rows] == e)[0]
+        Ve = excitation(translated_rwg(ems[lay.type_of[e]].rwg_e, lay.offsets[e]), th, ph, pol, K0)
+        Vr[sel] = Ve[rows[sel] - A.off[e]]
+    np.savez_compressed(os.path.join(HERE, "c3_types_6x6.npz"), x_check=_check(X), rows=rows, y_rows=Y, V_rows=Vr,
+                        type_of=lay.type_of)
+    print("c3", time.time() - t0)
 
 
 if __name__ == "__main__":

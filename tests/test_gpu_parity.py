@@ -177,3 +177,55 @@ def test_farfield_and_rcs_match_oracle(c1):
     sig = mm.mm_rcs(c1.array, 1, Jh, g["theta"], g["phi"])[:, 0]
     top = g["sigma"] >= g["sigma"].max() * 1e-4
     assert np.abs(10 * np.log10(sig[top] / g["sigma"][top])).max() <= 0.01
+
+
+C3_OUTERS = (0.30, 0.34, 0.38, 0.42)
+
+
+@pytest.fixture(scope="module")
+def c3(ctx):
+    la = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2)
+    yield la
+    la.close()
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_c3_four_types_64_rhs(c3, prec):
+    """Four element types drawn per cell, 64 right-hand sides in one product:
+    sampled rows of all 64 columns and of the 8 x 8 plane-wave excitation."""
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    assert np.array_equal(c3.layout.type_of, g["type_of"])
+    X = wl.random_cvec(c3.n, 2, 7, nrhs=64)
+    assert np.allclose([X.sum(), (np.abs(X) ** 2).sum()], g["x_check"])
+    Y = _apply(c3, X, prec, nrhs=64)
+    _close(Y[g["rows"]], g["y_rows"], prec)
+    th, ph, pol = wl.planewave_grid()
+    V = torch.empty(c3.n * 64, dtype=DT[prec], device="cuda")
+    mm.mm_rhs_planewave(c3.array, th, ph, pol, V, prec, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    Vh = V.cpu().numpy().astype(np.complex128).reshape(c3.n, 64)
+    _close(Vh[g["rows"]], g["V_rows"], prec)
+
+
+def test_c3_batched_solve_equals_columns_alone(c3):
+    """64 incidences solved together (independent Krylov spaces, one product per
+    iteration) give the same solutions as the columns solved alone, within the
+    solver tolerance (P13), and every column meets it."""
+    th, ph, pol = wl.planewave_grid()
+    st = torch.cuda.current_stream()
+    V = torch.empty(c3.n * 64, dtype=torch.complex128, device="cuda")
+    mm.mm_rhs_planewave(c3.array, th, ph, pol, V, mm.MM_C128, st)
+    E = torch.empty_like(V)
+    s = mm.mm_solve(c3.array, 64, V, E, tol=1e-4, restart=50, max_iter=2000, precision=mm.MM_C64, refine=1,
+                    inner_tol=1e-5, stream=st)
+    assert s["converged"] and s["rel_residual"] <= 1e-4
+    Eb = E.cpu().numpy().reshape(c3.n, 64)
+    for j in (0, 37):
+        V1 = torch.empty(c3.n, dtype=torch.complex128, device="cuda")
+        mm.mm_rhs_planewave(c3.array, [th[j]], [ph[j]], [pol[j]], V1, mm.MM_C128, st)
+        E1 = torch.empty_like(V1)
+        s1 = mm.mm_solve(c3.array, 1, V1, E1, tol=1e-4, restart=50, max_iter=2000, precision=mm.MM_C64, refine=1,
+                         inner_tol=1e-5, stream=st)
+        assert s1["converged"]
+        e1 = E1.cpu().numpy()
+        assert np.linalg.norm(Eb[:, j] - e1) / np.linalg.norm(e1) <= 2e-3
