@@ -111,6 +111,8 @@ typedef enum mm_type_matrix_id {
 /* Copies matrix `which` (row-major, complex128 interleaved) into out_host
  * (may be NULL to query the shape).  rows/cols receive its shape.            */
 mm_status mm_type_matrix(const mm_type* type, int32_t which, double* out_host, int64_t* rows, int64_t* cols);
+/* Unknown counts of a type: n_scat = N (RWG on the scatterer), n_equiv = N^. */
+mm_status mm_type_info(const mm_type* type, int64_t* n_scat, int64_t* n_equiv);
 void mm_type_destroy(mm_type* type);
 
 /* ------------------------------------------------------------------- array
@@ -263,6 +265,45 @@ mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev
  *  - stage profiling is suspended during the call.                             */
 mm_status mm_apply_noalloc(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                            void* stream);
+
+/* ----------------------------------------------------------------- server
+ * A solve server for streams of requests (the library's request loop; the
+ * paper has none).  mm_server_create starts `workers` threads on `device`,
+ * each with its own context and CUDA stream.  A submitted request (copied) is
+ * admitted when its estimated device footprint fits in hbm_budget_bytes (0:
+ * 80 % of the free device memory) minus the requests in flight; admitted
+ * requests run concurrently (array set-up, plane-wave excitation, GMRES, copy
+ * of E^ to the host), so a request that arrives while others run starts as
+ * soon as a worker and memory are free.  Element types are shared read-only
+ * and must outlive the server.  mm_server_poll returns MM_EBUSY while the
+ * request runs (wait = 0) or blocks until it is done (wait = 1); E_host, if
+ * not NULL, receives E^ (N^ x nrhs complex128; E_count doubles available).
+ * mm_server_release forgets a finished request.                               */
+typedef struct mm_server mm_server;
+typedef struct mm_request {
+  int64_t n_elem;
+  const mm_type* const* types;   /* per element                                */
+  const double* offsets_xyz;     /* n_elem x 3                                 */
+  mm_aim_opts aim;
+  int32_t nrhs;
+  const double* theta;           /* nrhs incidences (see mm_rhs_planewave)     */
+  const double* phi;
+  const int32_t* pol;
+  mm_solve_opts solve;
+} mm_request;
+typedef struct mm_result {
+  int32_t done;
+  int32_t status;                /* mm_status of the request                   */
+  int64_t n_unknowns;
+  mm_solve_stats stats;
+  double queue_s, setup_s, solve_s, latency_s;   /* wall times, seconds       */
+} mm_result;
+mm_status mm_server_create(int device, int32_t workers, size_t hbm_budget_bytes, mm_server** out);
+mm_status mm_server_submit(mm_server* server, const mm_request* request, uint64_t* ticket);
+mm_status mm_server_poll(mm_server* server, uint64_t ticket, int32_t wait, mm_result* result, double* E_host,
+                         int64_t E_count);
+mm_status mm_server_release(mm_server* server, uint64_t ticket);
+void mm_server_destroy(mm_server* server);
 
 /* ----------------------------------------------------------- profiling
  * With profiling enabled, every stage of every product is bracketed by CUDA

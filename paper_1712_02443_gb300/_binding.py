@@ -56,6 +56,18 @@ class mm_solve_stats(ct.Structure):
                 ("converged", ct.c_int32), ("rel_residual", ct.c_double)]
 
 
+class mm_request(ct.Structure):
+    _fields_ = [("n_elem", ct.c_int64), ("types", ct.POINTER(ct.c_void_p)), ("offsets_xyz", ct.c_void_p),
+                ("aim", mm_aim_opts), ("nrhs", ct.c_int32), ("theta", ct.c_void_p), ("phi", ct.c_void_p),
+                ("pol", ct.c_void_p), ("solve", mm_solve_opts)]
+
+
+class mm_result(ct.Structure):
+    _fields_ = [("done", ct.c_int32), ("status", ct.c_int32), ("n_unknowns", ct.c_int64),
+                ("stats", mm_solve_stats), ("queue_s", ct.c_double), ("setup_s", ct.c_double),
+                ("solve_s", ct.c_double), ("latency_s", ct.c_double)]
+
+
 P = ct.c_void_p
 PP = ct.POINTER(ct.c_void_p)
 I64P = ct.POINTER(ct.c_int64)
@@ -70,6 +82,7 @@ _SIGS = {
     "mm_mesh_destroy": (None, [P]),
     "mm_element_type_create": (ct.c_int, [P, P, P, ct.POINTER(mm_em_opts), PP]),
     "mm_type_matrix": (ct.c_int, [P, ct.c_int32, P, I64P, I64P]),
+    "mm_type_info": (ct.c_int, [P, I64P, I64P]),
     "mm_type_destroy": (None, [P]),
     "mm_array_create": (ct.c_int, [P, ct.c_int64, PP, P, ct.POINTER(mm_aim_opts), PP]),
     "mm_array_info_get": (ct.c_int, [P, ct.POINTER(mm_array_info)]),
@@ -84,6 +97,11 @@ _SIGS = {
     "mm_currents": (ct.c_int, [P, ct.c_int32, P, P, P, P]),
     "mm_farfield": (ct.c_int, [P, ct.c_int32, P, ct.c_int64, P, P, P, P]),
     "mm_rcs": (ct.c_int, [P, ct.c_int32, P, ct.c_int64, P, P, P]),
+    "mm_server_create": (ct.c_int, [ct.c_int, ct.c_int32, ct.c_size_t, PP]),
+    "mm_server_submit": (ct.c_int, [P, ct.POINTER(mm_request), ct.POINTER(ct.c_uint64)]),
+    "mm_server_poll": (ct.c_int, [P, ct.c_uint64, ct.c_int32, ct.POINTER(mm_result), P, ct.c_int64]),
+    "mm_server_release": (ct.c_int, [P, ct.c_uint64]),
+    "mm_server_destroy": (None, [P]),
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
     "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
 }
@@ -195,6 +213,12 @@ def mm_type_matrix(typ, which: int) -> np.ndarray:
     out = np.zeros((r.value, c.value), dtype=np.complex128)
     _check(load().mm_type_matrix(typ, which, _ptr(out), ct.byref(r), ct.byref(c)), ctx)
     return out
+
+
+def mm_type_info(typ):
+    a, b = ct.c_int64(), ct.c_int64()
+    _check(load().mm_type_info(typ, ct.byref(a), ct.byref(b)), _ctx_of.get(typ.value))
+    return a.value, b.value
 
 
 def mm_type_destroy(typ) -> None:
@@ -309,3 +333,54 @@ def mm_profile_read(array, precision: int = -1) -> dict:
     nl = (ct.c_int64 * len(STAGES))()
     _check(load().mm_profile_read(array, precision, ms, nl), _ctx_of.get(array.value))
     return {name: {"ms": ms[i], "launches": nl[i]} for i, name in enumerate(STAGES)}
+
+
+# ---------------------------------------------------------------------------- server
+def mm_server_create(device: int = 0, workers: int = 2, hbm_budget_bytes: int = 0):
+    h = ct.c_void_p()
+    _check(load().mm_server_create(device, workers, hbm_budget_bytes, ct.byref(h)), None)
+    return h
+
+
+def mm_server_submit(server, types, offsets, theta, phi, pol, tol: float, h: float = 0.1, order: int = 2,
+                     n_nf: int = 3, phase=(0.0137, 0.0291, 0.0913), restart: int = 50, max_iter: int = 2000,
+                     precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-5) -> int:
+    """Submits one request; its inputs are copied before this returns."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.float64).reshape(-1, 3)
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
+    arr = (ct.c_void_p * len(types))(*[t.value for t in types])
+    q = mm_request(len(types), ct.cast(arr, ct.POINTER(ct.c_void_p)), offsets.ctypes.data_as(ct.c_void_p),
+                   mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase)), len(th), th.ctypes.data_as(ct.c_void_p),
+                   ph.ctypes.data_as(ct.c_void_p), po.ctypes.data_as(ct.c_void_p),
+                   mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol))
+    t = ct.c_uint64()
+    _check(load().mm_server_submit(server, ct.byref(q), ct.byref(t)), None)
+    return t.value
+
+
+def mm_server_poll(server, ticket: int, wait: bool = True, nrhs: int = 1, want_solution: bool = True):
+    """Returns (result dict, E or None); result['done'] is False while it runs."""
+    r = mm_result()
+    st = load().mm_server_poll(server, ticket, 1 if wait else 0, ct.byref(r), None, 0)
+    if st == MM_EBUSY:
+        return {"done": False}, None
+    _check(st, None)
+    E = None
+    if want_solution and r.status in (MM_OK, MM_ENOCONV):
+        buf = np.zeros(2 * r.n_unknowns * nrhs, dtype=np.float64)
+        _check(load().mm_server_poll(server, ticket, 1, ct.byref(r), buf.ctypes.data_as(ct.c_void_p), len(buf)), None)
+        E = buf.view(np.complex128).reshape(r.n_unknowns, nrhs)
+    res = {"done": True, "status": r.status, "n_unknowns": r.n_unknowns, "iterations": r.stats.iterations,
+           "matvecs": r.stats.matvecs, "converged": bool(r.stats.converged), "rel_residual": r.stats.rel_residual,
+           "queue_s": r.queue_s, "setup_s": r.setup_s, "solve_s": r.solve_s, "latency_s": r.latency_s}
+    return res, E
+
+
+def mm_server_release(server, ticket: int) -> None:
+    _check(load().mm_server_release(server, ticket), None)
+
+
+def mm_server_destroy(server) -> None:
+    load().mm_server_destroy(server)

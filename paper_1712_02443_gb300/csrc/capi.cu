@@ -317,6 +317,13 @@ mm_status mm_type_matrix(const mm_type* type, int32_t which, double* out_host, i
   return MM_OK;
 }
 
+mm_status mm_type_info(const mm_type* type, int64_t* n_scat, int64_t* n_equiv) {
+  if (!type) return MM_EINVAL;
+  if (n_scat) *n_scat = type->tm.N;
+  if (n_equiv) *n_equiv = type->tm.Nh;
+  return MM_OK;
+}
+
 void mm_type_destroy(mm_type* type) { delete type; }
 
 mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* types, const double* offsets_xyz,

@@ -1,0 +1,93 @@
+"""Solve server: requests of different sizes admitted by device footprint and
+run concurrently; each result is the same alone and in the mix (P13)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1712_02443_gb300 as mm  # noqa: E402
+from paper_1712_02443_gb300 import workloads as wl  # noqa: E402
+from paper_1712_02443_gb300.arrays import build_types  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+OUTERS = (0.30, 0.34, 0.38, 0.42)
+
+
+@pytest.fixture(scope="module")
+def family():
+    from paper_1712_02443_gb300.build import build
+    build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = mm.mm_ctx_create(0)
+    base = wl.loop_array(2, 2, outers=OUTERS, config_index=2)
+    meshes, types = build_types(ctx, base)
+    yield types
+    for t in types:
+        mm.mm_type_destroy(t)
+    for m in meshes:
+        mm.mm_mesh_destroy(m)
+    mm.mm_ctx_destroy(ctx)
+
+
+def _requests():
+    """Seeded mix: sides 2..4, 1..4 right-hand sides, tolerances 1e-3 / 1e-4."""
+    g = wl.rng(4, 1)
+    reqs = []
+    for i in range(7):
+        side = int(g.integers(2, 5))
+        nrhs = int(g.integers(1, 5))
+        lay = wl.loop_array(side, side, outers=OUTERS, config_index=2)
+        type_of = g.integers(0, 4, size=side * side)
+        th = g.uniform(0, np.pi / 3, nrhs)
+        ph = g.uniform(0, np.pi / 2, nrhs)
+        pol = g.integers(0, 2, nrhs)
+        tol = 1e-4 if i % 2 == 0 else 1e-3
+        reqs.append((type_of, lay.offsets, th, ph, pol, tol))
+    return reqs
+
+
+def _submit(sv, types, req):
+    type_of, offs, th, ph, pol, tol = req
+    return mm.mm_server_submit(sv, [types[t] for t in type_of], offs, th, ph, pol, tol)
+
+
+def test_result_same_alone_and_in_mix(family):
+    reqs = _requests()
+    probe = 2
+    sv = mm.mm_server_create(0, workers=1)
+    try:
+        t = _submit(sv, family, reqs[probe])
+        res_alone, E_alone = mm.mm_server_poll(sv, t, wait=True, nrhs=len(reqs[probe][2]))
+    finally:
+        mm.mm_server_destroy(sv)
+    assert res_alone["status"] == 0 and res_alone["converged"]
+    sv = mm.mm_server_create(0, workers=3)
+    try:
+        tickets = [_submit(sv, family, q) for q in reqs]
+        out = [mm.mm_server_poll(sv, tk, wait=True, nrhs=len(q[2])) for tk, q in zip(tickets, reqs)]
+    finally:
+        mm.mm_server_destroy(sv)
+    for (res, E), q in zip(out, reqs):
+        assert res["status"] == 0 and res["converged"] and res["rel_residual"] <= q[5]
+        assert res["latency_s"] >= res["setup_s"] + res["solve_s"] - 1e-6
+    E_mix = out[probe][1]
+    # both solves meet the same residual tolerance; their difference is bounded by it (times cond ~ 10)
+    tol = reqs[probe][5]
+    assert np.linalg.norm(E_mix - E_alone) / np.linalg.norm(E_alone) <= 20 * tol
+
+
+def test_admission_by_footprint(family):
+    """A budget that fits one request at a time still completes every request."""
+    reqs = _requests()[:3]
+    sv = mm.mm_server_create(0, workers=3, hbm_budget_bytes=1)
+    try:
+        tickets = [_submit(sv, family, q) for q in reqs]
+        out = [mm.mm_server_poll(sv, tk, wait=True, nrhs=len(q[2]), want_solution=False)[0]
+               for tk, q in zip(tickets, reqs)]
+    finally:
+        mm.mm_server_destroy(sv)
+    assert all(r["status"] == 0 and r["converged"] for r in out)
+    # with room for one at a time, requests ran one after another
+    starts = sorted(r["queue_s"] for r in out)
+    assert starts[-1] > 0
