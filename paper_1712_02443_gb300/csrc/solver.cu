@@ -467,14 +467,49 @@ __global__ void k_add_basis_dev(const Z* __restrict__ V, int64_t vs, GmresDev gd
 }
 
 
+// Partial ||w_j||^2 over this block's rows into PN[j nblk + blk] (all columns).
+__device__ void block_norms(const Z* __restrict__ w, int64_t n0, int64_t n1, int r, int blk, int nblk, Z* ws,
+                            double* __restrict__ PN) {
+  const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int j = 0; j < r; ++j) {
+    double acc = 0;
+    for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
+      const Z a = w[nn * r + j];
+      acc += a.x * a.x + a.y * a.y;
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+    if (lane == 0) ws[warp].x = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t2 = 0;
+      for (int q = 0; q < nw; ++q) t2 += ws[q].x;
+      PN[(int64_t)j * nblk + blk] = t2;
+    }
+    __syncthreads();
+  }
+}
+
+// sum over blocks of PN for column j (same order in every block)
+__device__ __forceinline__ double sum_blocks(const double* __restrict__ PN, int j, int nblk) {
+  double t = 0;
+  for (int b = 0; b < nblk; ++b) t += PN[(int64_t)j * nblk + b];
+  return t;
+}
+
 // One Arnoldi step for all columns in a single cooperative launch (all blocks
-// resident; grid-wide barriers between the phases, no spin-waits of our own):
+// resident; grid-wide barriers between the phases, no spin-waits of our own).
+// Classical Gram-Schmidt with selective reorthogonalisation: the second pass
+// runs only for columns whose norm fell below 1/sqrt(2) of its value before
+// the first pass (Daniel, Gragg, Kaufman and Stewart 1976); the decision is
+// the same in every block, so every block takes the same grid barriers.
 //  0. w = operator output (complex64 -> FP64) on this block's rows;
-//  1. partial <V_i, w>, i <= k;                         [grid sync]
-//  2. h = sum of partials; w -= V h; partial <V_i, w>;  [grid sync]
-//  3. h2 = sum of partials; w -= V h2; partial ||w||^2; [grid sync]
-//  4. block 0: Hessenberg column h + h2, Givens, residual estimate, k += 1;
-//                                                       [grid sync]
+//  1. partial <V_i, w>, i <= k, and ||w||^2;            [grid sync]
+//  2. h = sum of partials; w -= V h; partial ||w||^2;   [grid sync]
+//  3. if a column needs it: partial <V_i, w> [grid sync], h2, w -= V h2,
+//     partial ||w||^2                                   [grid sync]
+//  4. block 0: Hessenberg column h + h2, Givens rotations, residual
+//     estimate, k += 1;                                 [grid sync]
 //  5. V[k+1] = w / ||w|| (0 for finished columns), next operator input.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t vs, Z* __restrict__ w,
@@ -491,12 +526,17 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   const int k = *gd.k;
   const int nblk = gridDim.x, blk = blockIdx.x;
   const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  double* PN0 = PN;                              // ||w||^2 before the first pass
+  double* PN1 = PN + (int64_t)r * nblk;          // after the first pass
+  double* PN2 = PN + 2 * (int64_t)r * nblk;      // after the second pass
   // phase 0
   if (yin != nullptr)
-    for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) w[t] = make_double2((double)yin[t].x, (double)yin[t].y);
+    for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x)
+      w[t] = make_double2((double)yin[t].x, (double)yin[t].y);
   __syncthreads();
   // phase 1
   for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P1), __syncthreads();
+  block_norms(w, n0, n1, r, blk, nblk, ws, PN0);
   grid.sync();
   // phase 2
   reduce_all_partials(P1, k, r, nblk, hs);
@@ -512,44 +552,64 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
     w[t] = a;
   }
   __syncthreads();
-  for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2), __syncthreads();
+  block_norms(w, n0, n1, r, blk, nblk, ws, PN1);
   grid.sync();
-  // phase 3
-  reduce_all_partials(P2, k, r, nblk, h2s);
-  {
+  // phase 3: selective reorthogonalisation
+  int* need = reinterpret_cast<int*>(ws + (m + 1) * nw);   // r flags (shared)
+  __shared__ int any_s;
+  if (threadIdx.x == 0) any_s = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    const double b0 = sum_blocks(PN0, j, nblk), b1 = sum_blocks(PN1, j, nblk);
+    need[j] = gd.active[j] && (b1 < 0.5 * b0);
+    if (need[j]) atomicOr(&any_s, 1);
+  }
+  __syncthreads();
+  const bool any_reorth = any_s != 0;
+  for (int i = threadIdx.x; i < (m + 1) * r; i += blockDim.x) h2s[i] = make_double2(0, 0);
+  __syncthreads();
+  if (any_reorth) {
     for (int j = 0; j < r; ++j) {
-      double acc = 0;
-      for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
-        const int64_t t = nn * r + j;
-        Z a = w[t];
-#pragma unroll 4
-        for (int i = 0; i <= k; ++i) {
-          const Z p = zmul(V[(int64_t)i * vs + t], h2s[i * r + j]);
-          a.x -= p.x;
-          a.y -= p.y;
-        }
-        w[t] = a;
-        acc += a.x * a.x + a.y * a.y;
-      }
-#pragma unroll
-      for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
-      if (lane == 0) ws[warp].x = acc;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t2 = 0;
-        for (int q = 0; q < nw; ++q) t2 += ws[q].x;
-        PN[(int64_t)j * nblk + blk] = t2;
-      }
+      if (need[j]) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2);
       __syncthreads();
     }
+    grid.sync();
+    for (int p = warp; p < (k + 1) * r; p += nw) {
+      const int i = p / r, j = p % r;
+      if (!need[j]) continue;
+      const Z* src = P2 + ((int64_t)i * r + j) * nblk;
+      Z acc = make_double2(0, 0);
+      for (int b = lane; b < nblk; b += 32) {
+        acc.x += src[b].x;
+        acc.y += src[b].y;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) h2s[i * r + j] = acc;
+    }
+    __syncthreads();
+    for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
+      const int j = (int)(t % r);
+      if (!need[j]) continue;
+      Z a = w[t];
+#pragma unroll 4
+      for (int i = 0; i <= k; ++i) {
+        const Z p = zmul(V[(int64_t)i * vs + t], h2s[i * r + j]);
+        a.x -= p.x;
+        a.y -= p.y;
+      }
+      w[t] = a;
+    }
+    __syncthreads();
+    block_norms(w, n0, n1, r, blk, nblk, ws, PN2);
+    grid.sync();
   }
-  grid.sync();
   // phase 4: block 0, warp per column
   if (blk == 0) {
     for (int j = warp; j < r; j += nw) {
       if (!gd.active[j]) continue;
+      const double* PNf = (any_reorth && need[j]) ? PN2 : PN1;
       double s2 = 0;
-      for (int b = lane; b < nblk; b += 32) s2 += PN[(int64_t)j * nblk + b];
+      for (int b = lane; b < nblk; b += 32) s2 += PNf[(int64_t)j * nblk + b];
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, s);
       if (lane == 0) {
@@ -639,7 +699,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    coop_smem_ = sizeof(Z) * (size_t)(m + 1) * (2 * r + 8);
+    coop_smem_ = sizeof(Z) * (size_t)(m + 1) * (2 * r + 8) + sizeof(int) * (size_t)r + 16;
     coop_ok_ = coop_smem_ <= 200 * 1024;
     if (coop_ok_) {
       MM_CK(cudaFuncSetAttribute(k_arnoldi_step<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -670,7 +730,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
   MM_CK(cudaMalloc(&x64_, vec));
   MM_CK(cudaMalloc(&P1_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
   MM_CK(cudaMalloc(&P2_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
-  MM_CK(cudaMalloc(&PN_, sizeof(double) * (size_t)r * nblk_));
+  MM_CK(cudaMalloc(&PN_, sizeof(double) * 3 * (size_t)r * nblk_));
   {
     // GMRES cycle state: k, active, kdone, tol, res, scale, g, cs, sn, H, y
     size_t b = 0;
