@@ -51,8 +51,11 @@ typedef enum mm_status {
 } mm_status;
 
 typedef enum mm_precision {
-  MM_C64 = 0,   /* complex64 operator (FP32 FFT, SpMV, macromodel product) */
-  MM_C128 = 1   /* complex128 operator (the plain FP64 GPU form)           */
+  MM_C64 = 0,       /* complex64 operator (FP32 FFT, SpMV, macromodel product)   */
+  MM_C128 = 1,      /* complex128 operator (the plain FP64 GPU form)             */
+  MM_C64_BF16 = 2,  /* complex64 operator, macromodel product on tensor cores   */
+                    /* with BF16 inputs and FP32 accumulation (vectors: c64)     */
+  MM_C64_F16 = 3    /* same with FP16 inputs                                     */
 } mm_precision;
 
 typedef struct mm_ctx mm_ctx;
@@ -225,7 +228,7 @@ typedef struct mm_solve_opts {
   int32_t restart;    /* GMRES(m) restart length                              */
   int32_t max_iter;   /* total inner iterations bound                         */
   int32_t precision;  /* operator precision inside GMRES                      */
-  int32_t refine;     /* 1: FP64 outer refinement (needs precision MM_C64)    */
+  int32_t refine;     /* 1: FP64 outer refinement (needs a complex64 mode)    */
   double inner_tol;   /* inner GMRES tolerance when refining                  */
 } mm_solve_opts;
 typedef struct mm_solve_stats {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmacroaim.so")
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENOCONV, MM_EBREAKDOWN, MM_ETIMEOUT, MM_EBUSY, MM_EINTERNAL = range(9)
 STATUS_NAMES = ["MM_OK", "MM_EINVAL", "MM_ENOMEM", "MM_ECUDA", "MM_ENOCONV", "MM_EBREAKDOWN", "MM_ETIMEOUT",
                 "MM_EBUSY", "MM_EINTERNAL"]
-MM_C64, MM_C128 = 0, 1
+MM_C64, MM_C128, MM_C64_BF16, MM_C64_F16 = 0, 1, 2, 3
 MM_MAT_M, MM_MAT_D, MM_MAT_T, MM_MAT_A, MM_MAT_B, MM_MAT_GHH, MM_MAT_GHE = range(7)
 STAGES = ["gemm", "project", "fft_fwd", "fft_conv", "fft_inv", "interp", "near", "krylov"]
 MM_EXPORT_ANCHORS, MM_EXPORT_PI, MM_EXPORT_NEAR_PTR, MM_EXPORT_NEAR_COL, MM_EXPORT_NEAR_VAL, MM_EXPORT_GHAT = range(6)

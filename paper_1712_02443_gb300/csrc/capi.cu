@@ -16,6 +16,10 @@
 #include "macroaim.h"
 #include "post.h"
 #include "solver.h"
+#include "tc_gemm.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 struct mm_ctx {
   int device = -1;
@@ -158,11 +162,86 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
   p.ready = true;
 }
 
+// Packed real operand of the tensor-core GEMM for one 16-bit format (mode 1 BF16,
+// 2 FP16): per type, row 2i = [Re W_i, -Im W_i], row 2i+1 = [Im W_i, Re W_i]
+// for W = [M; D], padded to the tile sizes.
+void upload_tc(mm_array* a, int mode) {
+  auto& p = a->da.pf;
+  const int slot = mode - 1;
+  if (!p.Atc[slot].empty()) return;
+  auto& da = a->da;
+  const int TM = mm::tc_tile_m(), TK = mm::tc_tile_k();
+  p.Mp.resize(da.n_types);
+  p.Kp.resize(da.n_types);
+  for (int64_t t = 0; t < da.n_types; ++t) {
+    const auto& tm = a->types[t]->tm;
+    const int64_t Nh = tm.Nh;
+    const int Mp = (int)((4 * Nh + TM - 1) / TM * TM), Kp = (int)((2 * Nh + TK - 1) / TK * TK);
+    p.Mp[t] = Mp;
+    p.Kp[t] = Kp;
+    std::vector<uint16_t> A((size_t)Mp * Kp, 0);
+    auto cvt = [&](double v) -> uint16_t {
+      if (mode == 1) {
+        __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+        return *reinterpret_cast<uint16_t*>(&b);
+      }
+      __half h = __float2half_rn((float)v);
+      return *reinterpret_cast<uint16_t*>(&h);
+    };
+    for (int64_t i = 0; i < 2 * Nh; ++i) {
+      const std::vector<mm::cd>& W = i < Nh ? tm.M : tm.D;
+      const int64_t ii = i < Nh ? i : i - Nh;
+      for (int64_t k = 0; k < Nh; ++k) {
+        const mm::cd w = W[ii * Nh + k];
+        A[(size_t)(2 * i) * Kp + k] = cvt(w.real());
+        A[(size_t)(2 * i) * Kp + Nh + k] = cvt(-w.imag());
+        A[(size_t)(2 * i + 1) * Kp + k] = cvt(w.imag());
+        A[(size_t)(2 * i + 1) * Kp + Nh + k] = cvt(w.real());
+      }
+    }
+    p.Atc[slot].push_back(dev_upload(A.data(), A.size(), da.bytes));
+  }
+}
+
+void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
+  auto& da = a->da;
+  size_t need = 0;
+  const int TN = mm::tc_tile_n(), TK = mm::tc_tile_k();
+  for (int64_t t = 0; t < da.n_types; ++t) {
+    const int64_t ncols = da.n_of_type[t] * nrhs;
+    const int64_t Np = (ncols + TN - 1) / TN * TN;
+    const int64_t Kp = (2 * da.Nh[t] + TK - 1) / TK * TK;
+    need = std::max(need, (size_t)(Np * Kp));
+  }
+  if (w.bt_cap < need) {
+    if (w.bt) cudaFree(w.bt);
+    w.bt = nullptr;
+    CU(cudaMalloc(&w.bt, sizeof(uint16_t) * need));
+    w.bt_cap = need;
+  }
+  if (!w.err) {
+    CU(cudaMalloc(&w.err, sizeof(int)));
+    CU(cudaMemset(w.err, 0, sizeof(int)));
+  }
+}
+
+// A bounded wait of the tensor-core GEMM expired (checked where the call synchronises).
+mm_status check_tc(mm_array* a) {
+  int h = 0;
+  if (!a->da.wf.err) return MM_OK;
+  if (cudaMemcpy(&h, a->da.wf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
+  if (h) {
+    cudaMemset(a->da.wf.err, 0, sizeof(int));
+    return fail(a->ctx, MM_ETIMEOUT, "a tensor-core GEMM wait expired; results of that product are invalid");
+  }
+  return MM_OK;
+}
+
 template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
-  for (void* q : {w.u, w.v, w.grid, w.spec})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -178,6 +257,8 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
 }
 
 void free_prec_f(mm::DevPrec<float>& p) {
+  for (auto& v : p.Atc)
+    for (void* q : v) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz})
@@ -199,7 +280,7 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
@@ -551,9 +632,14 @@ mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, in
   CU(cudaSetDevice(a->da.device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (precision == MM_C64) {
+  if (precision == MM_C64 || precision == MM_C64_BF16 || precision == MM_C64_F16) {
+    const int mode = precision == MM_C64 ? 0 : (precision == MM_C64_BF16 ? 1 : 2);
     ensure_work<float>(a, a->da.wf, nrhs);
-    e = mm::matvec<float>(a->da, a->da.pf, a->da.wf, nrhs, x_dev, y_dev, st);
+    if (mode) {
+      upload_tc(a, mode);
+      ensure_tc_work(a, a->da.wf, nrhs);
+    }
+    e = mm::matvec<float>(a->da, a->da.pf, a->da.wf, nrhs, x_dev, y_dev, st, mode);
   } else if (precision == MM_C128) {
     upload_precision<double>(a, a->da.pd);
     ensure_work<double>(a, a->da.wd, nrhs);
@@ -571,7 +657,7 @@ mm_status mm_apply_host(mm_array* a, int32_t nrhs, const void* x_host, void* y_h
   mm_ctx* ctx = a->ctx;
   if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
   if (nrhs < 1 || !x_host || !y_host) return fail(ctx, MM_EINVAL, "invalid apply arguments");
-  if (precision != MM_C64 && precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (precision < MM_C64 || precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
   API_TRY
   CU(cudaSetDevice(a->da.device));
   size_t bytes = (precision == MM_C128 ? 16 : 8) * (size_t)a->da.N * nrhs;
@@ -588,7 +674,7 @@ mm_status mm_apply_host(mm_array* a, int32_t nrhs, const void* x_host, void* y_h
   if (s != MM_OK) return s;
   CU(cudaMemcpyAsync(y_host, a->hy, bytes, cudaMemcpyDeviceToHost, 0));
   CU(cudaStreamSynchronize(0));
-  return MM_OK;
+  return check_tc(a);
   API_CATCH(ctx)
 }
 
@@ -646,8 +732,9 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
   if (nrhs < 1 || !V_dev || !E_dev || !opts || V_dev == E_dev) return fail(ctx, MM_EINVAL, "invalid solve arguments");
   if (!(opts->tol > 0) || opts->restart < 1 || opts->max_iter < 1) return fail(ctx, MM_EINVAL, "invalid solve options");
-  if (opts->precision != MM_C64 && opts->precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
-  if (opts->refine && opts->precision != MM_C64) return fail(ctx, MM_EINVAL, "refinement needs precision MM_C64");
+  if (opts->precision < MM_C64 || opts->precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (opts->refine && opts->precision == MM_C128)
+    return fail(ctx, MM_EINVAL, "refinement needs a complex64 operator precision");
   API_TRY
   CU(cudaSetDevice(a->da.device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -659,21 +746,27 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   upload_precision<double>(a, a->da.pd);
   ensure_work<double>(a, a->da.wd, nrhs);
   ensure_work<float>(a, a->da.wf, nrhs);
+  const int mode = opts->precision == MM_C64_BF16 ? 1 : (opts->precision == MM_C64_F16 ? 2 : 0);
+  if (mode) {
+    upload_tc(a, mode);
+    ensure_tc_work(a, a->da.wf, nrhs);
+  }
   mm_array* arr = a;
   S.op64 = [arr, nrhs](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
     cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
-  S.op32 = [arr, nrhs](const void* in, void* out, cudaStream_t s2) -> mm::Status {
-    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, in, out, s2);
+  S.op32 = [arr, nrhs, mode](const void* in, void* out, cudaStream_t s2) -> mm::Status {
+    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, in, out, s2, mode);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
   int iters = 0, refs = 0;
   double relres = 0;
   bool conv = false;
-  s = S.solve(static_cast<const double2*>(V_dev), static_cast<double2*>(E_dev), opts->tol, opts->precision,
+  s = S.solve(static_cast<const double2*>(V_dev), static_cast<double2*>(E_dev), opts->tol,
+              opts->precision == MM_C128 ? MM_C128 : MM_C64,
               opts->refine, opts->inner_tol > 0 ? opts->inner_tol : 1e-2, opts->max_iter, iters, refs, relres, conv,
               st);
   if (stats) {
@@ -684,6 +777,10 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     stats->rel_residual = relres;
   }
   if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
+  if (mode) {
+    const mm_status t = check_tc(a);
+    if (t != MM_OK) return t;
+  }
   if (!conv) return fail(ctx, MM_ENOCONV, "GMRES reached max_iter before the tolerance");
   return MM_OK;
   API_CATCH(ctx)

@@ -80,6 +80,9 @@ struct DevPrec {
   void* twx = nullptr;    // exp(-2 pi i k / Px), k < Px
   void* twy = nullptr;
   void* twz = nullptr;
+  // tensor-core macromodel operands (complex64 modes): per type packed [M; D]
+  std::vector<void*> Atc[2];   // [0] BF16, [1] FP16; (Mp x Kp) 16-bit
+  std::vector<int> Mp, Kp;
 };
 
 // Work buffers for one (precision, nrhs) pair.
@@ -89,6 +92,9 @@ struct Work {
   void* v = nullptr;      // N x nrhs   D x
   void* grid = nullptr;   // 4 nrhs x Nx x Ny x Nz   grid charges/currents, then potentials
   void* spec = nullptr;   // 4 nrhs x Nx x Py x Pz   partial spectra
+  void* bt = nullptr;     // packed right-hand sides of the tensor-core GEMM
+  size_t bt_cap = 0;      // elements
+  int* err = nullptr;     // device error flag of bounded waits
   size_t bytes = 0;
 };
 
@@ -128,8 +134,10 @@ struct DevArray {
   std::vector<double> hval, hGhat;      // complex128 interleaved
 };
 
+// gemm_mode: 0 CUDA-core GEMM; 1 BF16 / 2 FP16 tensor-core GEMM (complex64 only)
 template <typename R>
-cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st);
+cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st,
+                   int gemm_mode = 0);
 template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which);
 cudaError_t kernels_init(DevArray& a);

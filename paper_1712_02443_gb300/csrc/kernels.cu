@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "device.h"
+#include "tc_gemm.h"
 
 namespace mm {
 
@@ -648,12 +649,15 @@ cudaError_t kernels_init(DevArray& a) {
   MM_ATTR((k_project<double, 4>))
   MM_ATTR(k_interp<float>) MM_ATTR(k_interp<double>)
 #undef MM_ATTR
+  e = tc_gemm_init();
+  if (e != cudaSuccess) return e;
   (void)a;
   return cudaSuccess;
 }
 
 template <typename R>
-cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st) {
+cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st,
+                   int gemm_mode) {
   typedef typename V2<R>::T C;
   const C* x = static_cast<const C*>(xv);
   C* y = static_cast<C*>(yv);
@@ -672,7 +676,18 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A1: u = M x, v = D x, per type
   pr.begin(sb + 0, st);
   int nl = 0;
-  for (int64_t t = 0; t < a.n_types; ++t) {
+  if (sizeof(R) == 4 && gemm_mode != 0) {
+    for (int64_t t = 0; t < a.n_types; ++t) {
+      if (a.n_of_type[t] == 0) continue;
+      cudaError_t e2 = tc_macro_gemm(gemm_mode == 1, static_cast<const uint16_t*>(p.Atc[gemm_mode - 1][t]), p.Mp[t],
+                                     p.Kp[t], (int)a.Nh[t], a.elems[t], (int)a.n_of_type[t], nrhs, a.off,
+                                     reinterpret_cast<const float2*>(x), static_cast<uint16_t*>(w.bt), w.bt_cap,
+                                     reinterpret_cast<float2*>(u), reinterpret_cast<float2*>(v), w.err, st);
+      if (e2 != cudaSuccess) return e2;
+      nl += 2;
+    }
+  }
+  for (int64_t t = 0; t < a.n_types && !(sizeof(R) == 4 && gemm_mode != 0); ++t) {
     if (a.n_of_type[t] == 0) continue;
     const int Nh = (int)a.Nh[t];
     const int ncols = (int)(a.n_of_type[t] * nrhs);
@@ -750,8 +765,8 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   return cudaGetLastError();
 }
 
-template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t);
-template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t);
+template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t, int);
+template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t, int);
 template size_t fft_smem_bytes<float>(const DevArray&, int);
 template size_t fft_smem_bytes<double>(const DevArray&, int);
 
