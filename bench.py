@@ -352,6 +352,54 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+def run_gemm_shape(args):
+    """Tensor-core macromodel GEMM at the 64 x 64 precision-configuration shape:
+    box 0.45 x 0.45 x 0.1 meshed 8 x 8 x 2 (576 RWG), 8 right-hand sides,
+    4096 elements; far-field operator only so that the array fits without its
+    near-field matrix.  Times the GEMM stage (operand packing + tcgen05 GEMM)
+    with CUDA events and reports it against the measured BF16 peak."""
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.build import build
+    build()
+    ctx = mm.mm_ctx_create(0)
+    et = wl.loop_element(box_div=(8, 8, 2))
+    ms = mm.mm_mesh_create(ctx, et.scatterer.xyz, et.scatterer.tri)
+    me = mm.mm_mesh_create(ctx, et.equiv.xyz, et.equiv.tri)
+    ty = mm.mm_element_type_create(ctx, ms, me, 2 * np.pi)
+    nx = args.gemm_side
+    lay = wl.loop_array(nx, nx)
+    arr = mm.mm_array_create(ctx, [ty] * lay.n_elem, lay.offsets, 0.1, 2, -1, wl.DEFAULT_GRID_PHASE)
+    info = mm.mm_array_info_get(arr)
+    nrhs = args.gemm_nrhs
+    N = info["n_unknowns"]
+    nh = N // lay.n_elem
+    x = torch.randn(N * nrhs, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+    hbm, bf16_peak, src = _peaks()
+    out = {"metric": "macromodel GEMM (tensor cores) TFLOP/s", "workload": "%dx%d elements, N^_t = %d, %d RHS"
+           % (nx, nx, nh, nrhs), "unknowns": N}
+    for name, prec in (("bf16", mm.MM_C64_BF16), ("fp16", mm.MM_C64_F16), ("fp32_cuda_cores", mm.MM_C64)):
+        for _ in range(args.warmup):
+            mm.mm_apply(arr, nrhs, x, y, prec, st)
+        torch.cuda.synchronize()
+        mm.mm_profile_enable(arr, True)
+        for _ in range(args.steps):
+            mm.mm_apply(arr, nrhs, x, y, prec, st)
+        torch.cuda.synchronize()
+        pr = mm.mm_profile_read(arr, mm.MM_C64)
+        mm.mm_profile_enable(arr, False)
+        ms_per = pr["gemm"]["ms"] / args.steps
+        flops = 2.0 * (4 * nh) * (2 * nh) * (lay.n_elem * nrhs)   # real form of the complex [M; D] x
+        out[name] = {"ms": round(ms_per, 4), "tflops": round(flops / (ms_per * 1e-3) / 1e12, 1),
+                     "frac_of_bf16_peak": round(flops / (ms_per * 1e-3) / 1e12 / bf16_peak, 4)}
+    out["peak_bf16_tflops"] = bf16_peak
+    out["peak_source"] = src
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,7 +408,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--gemm", action="store_true", help="time the tensor-core macromodel GEMM at the 64x64 shape")
+    ap.add_argument("--gemm-side", type=int, default=64)
+    ap.add_argument("--gemm-nrhs", type=int, default=8)
     args = ap.parse_args()
+    if args.gemm:
+        return run_gemm_shape(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

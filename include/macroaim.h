@@ -133,7 +133,8 @@ void mm_type_destroy(mm_type* type);
 typedef struct mm_aim_opts {
   double h;          /* grid spacing                                          */
   int32_t order;     /* stencil order N_O (N_O + 1 nodes per axis)            */
-  int32_t n_nf;      /* near-field radius N_NF in grid cells                  */
+  int32_t n_nf;      /* near-field radius N_NF in grid cells; -1: no near-field
+                        correction (far-field operator only, for studies)     */
   double phase[3];   /* position of one grid node                             */
 } mm_aim_opts;
 mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* types, const double* offsets_xyz,

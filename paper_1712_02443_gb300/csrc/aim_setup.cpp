@@ -224,7 +224,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
   int64_t ne = (int64_t)type_of.size();
   int64_t nty = (int64_t)types.size();
   if (ne < 1) throw Error{MM_EINVAL, "array has no elements"};
-  if (!(o.h > 0) || o.order < 1 || o.order > 8 || o.n_nf < 0) throw Error{MM_EINVAL, "invalid AIM options"};
+  if (!(o.h > 0) || o.order < 1 || o.order > 8 || o.n_nf < -1) throw Error{MM_EINVAL, "invalid AIM options"};
   ah.opts = o;
   ah.type_of = type_of;
   ah.n_elem = ne;
@@ -311,7 +311,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
     ah.Ghat = std::move(K);
   }
   // near field: blocks per (type, type, lattice offset)
-  const int nnf = o.n_nf;
+  const int nnf = o.n_nf;   // -1: no near-field correction
   int64_t ext[3] = {0, 0, 0};
   for (int64_t t = 0; t < nty; ++t)
     for (int a = 0; a < 3; ++a) ext[a] = std::max(ext[a], ah.tai[t].box_dim[a]);
@@ -330,7 +330,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
   for (int a = 0; a < 3; ++a) Rs[a] = ext[a] + nnf;
   // offset table for the grid part: |a_m - a_n| <= nnf, stencil offsets <= order
   HTable H;
-  H.R = nnf + o1.back() - o1.front();
+  H.R = std::max(nnf, 0) + o1.back() - o1.front();
   {
     int w = 2 * H.R + 1;
     H.v.assign((size_t)w * w * w, cd(0, 0));

@@ -88,10 +88,10 @@ mm_status fail(mm_ctx* ctx, mm_status code, const std::string& msg) {
 template <typename T>
 T* dev_upload(const T* h, size_t n, size_t& acc) {
   T* d = nullptr;
-  if (n == 0) n = 1;
-  CU(cudaMalloc(&d, sizeof(T) * n));
-  acc += sizeof(T) * n;
-  if (h) CU(cudaMemcpy(d, h, sizeof(T) * n, cudaMemcpyHostToDevice));
+  const size_t cap = n == 0 ? 1 : n;   // empty arrays still get a valid pointer
+  CU(cudaMalloc(&d, sizeof(T) * cap));
+  acc += sizeof(T) * cap;
+  if (h && n > 0) CU(cudaMemcpy(d, h, sizeof(T) * n, cudaMemcpyHostToDevice));
   return d;
 }
 
@@ -176,7 +176,8 @@ void upload_tc(mm_array* a, int mode) {
   for (int64_t t = 0; t < da.n_types; ++t) {
     const auto& tm = a->types[t]->tm;
     const int64_t Nh = tm.Nh;
-    const int Mp = (int)((4 * Nh + TM - 1) / TM * TM), Kp = (int)((2 * Nh + TK - 1) / TK * TK);
+    const int64_t Nhp = mm::tc_k_split((int)Nh);   // the imaginary half starts here
+    const int Mp = (int)((4 * Nh + TM - 1) / TM * TM), Kp = (int)((Nhp + Nh + TK - 1) / TK * TK);
     p.Mp[t] = Mp;
     p.Kp[t] = Kp;
     std::vector<uint16_t> A((size_t)Mp * Kp, 0);
@@ -194,9 +195,9 @@ void upload_tc(mm_array* a, int mode) {
       for (int64_t k = 0; k < Nh; ++k) {
         const mm::cd w = W[ii * Nh + k];
         A[(size_t)(2 * i) * Kp + k] = cvt(w.real());
-        A[(size_t)(2 * i) * Kp + Nh + k] = cvt(-w.imag());
+        A[(size_t)(2 * i) * Kp + Nhp + k] = cvt(-w.imag());
         A[(size_t)(2 * i + 1) * Kp + k] = cvt(w.imag());
-        A[(size_t)(2 * i + 1) * Kp + Nh + k] = cvt(w.real());
+        A[(size_t)(2 * i + 1) * Kp + Nhp + k] = cvt(w.real());
       }
     }
     p.Atc[slot].push_back(dev_upload(A.data(), A.size(), da.bytes));
@@ -210,13 +211,16 @@ void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
   for (int64_t t = 0; t < da.n_types; ++t) {
     const int64_t ncols = da.n_of_type[t] * nrhs;
     const int64_t Np = (ncols + TN - 1) / TN * TN;
-    const int64_t Kp = (2 * da.Nh[t] + TK - 1) / TK * TK;
+    const int64_t Kp = (mm::tc_k_split((int)da.Nh[t]) + da.Nh[t] + TK - 1) / TK * TK;
     need = std::max(need, (size_t)(Np * Kp));
   }
   if (w.bt_cap < need) {
     if (w.bt) cudaFree(w.bt);
     w.bt = nullptr;
     CU(cudaMalloc(&w.bt, sizeof(uint16_t) * need));
+    // entries the packing never writes (between the halves) meet zero columns
+    // of A; they start at zero so that they are finite
+    CU(cudaMemset(w.bt, 0, sizeof(uint16_t) * need));
     w.bt_cap = need;
   }
   if (!w.err) {

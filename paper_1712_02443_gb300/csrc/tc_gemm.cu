@@ -7,18 +7,41 @@
 //                    (W = [M; D] stacked, so i runs over 2 Nh output rows);
 //   B (ncols x 2 Nh): column (element, rhs) = [Re x_e, Im x_e];
 //   C = A B^T: row 2i = Re out_i, row 2i+1 = Im out_i.
-// Both operands are K-major in global memory, padded to multiples of the tile.
+// Both operands are K-major in global memory; A is padded to the tile with
+// zeros, B is read through a tensor map whose out-of-range box entries are
+// zero-filled by the copy engine.
 //
-// Kernel: one CTA per 128 x 128 output tile, 128 threads.  K slices of 64
-// elements (128 bytes per row) are staged in shared memory in the 128-byte
-// swizzled K-major layout, double-buffered; thread 0 issues four
-// tcgen05.mma (K = 16 each) per slice and commits them to an mbarrier; the
-// accumulator lives in 128 TMEM columns.  Every mbarrier wait is bounded: on
-// expiry the kernel records an error and stops issuing work.
+// K is laid out as [Re part: Nh entries | zeros up to Nhp = Nh rounded up to 8 |
+// Im part: Nh entries], so that both halves of a B row start 16-byte aligned.
+//
+// Kernel: persistent, one CTA per SM, 320 threads in three roles, CM CTAs per
+// cluster (CM = 1 or 2) working on CM consecutive M tiles of one N tile.
+//   warp 0     one lane issues TMA copies of its 128 x 64 A slice and of its
+//              share (256/CM rows) of the 256 x 64 B slice, the latter
+//              multicast to every CTA of the cluster, into a 4-stage ring of
+//              128-byte-swizzled K-major buffers;
+//   warp 1     allocates 512 TMEM columns; one lane issues tcgen05.mma
+//              (M 128, N 256, K 16) and commits each stage back to its slot;
+//   warps 2-9  epilogue: tcgen05.ld of the accumulator (each warp reads the
+//              TMEM lane quarter warp % 4 and one half of the columns), Re/Im
+//              pairing through a shared staging tile, column-per-lane stores
+//              of complex rows to u (rows < Nh) or v.
+// Two accumulators (2 x 256 columns) let the epilogue of one tile overlap the
+// main loop of the next.  Tiles are ordered M-fastest so that the CTAs working
+// at one time share their B slices in L2; with CM = 2 each B slice is read from
+// L2 once per cluster, so L2 serves 32 KB instead of 48 KB per 128 x 256 x 64
+// step.  A stage is refilled only after the products of every CTA that holds
+// a copy of it have completed (each CTA's commit arrives on the stage barrier
+// of all CTAs in the cluster).  Every mbarrier wait is bounded in
+// time; on expiry the kernel records an error, the other roles stop, copies
+// and products in flight are waited for (bounded) and TMEM is freed.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <cstdlib>
+#include <mutex>
 
 #include "tc_gemm.h"
 
@@ -26,12 +49,22 @@ namespace mm {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 128, TBK = 64;
-constexpr uint32_t kTmemCols = 128;
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr int TBM = 128, TBN = 256, TBK = 64, STAGES = 4;
+constexpr int A_BYTES = TBM * TBK * 2;   // 16 KB
+constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t kTmemCols = 2 * TBN;
+constexpr int kThreads = 320;   // producer warp, MMA warp, 8 epilogue warps
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 // UMMA shared-memory descriptor: K-major, 128-byte swizzle, 1024-byte atoms.
@@ -45,211 +78,503 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor for kind::f16: FP32 accumulate, K-major A and B.
+// Instruction descriptor for kind::f16: FP32 accumulate, K-major A and B, M 128, N 256.
 __host__ __device__ constexpr uint32_t make_idesc(bool bf16) {
   return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(TBN >> 3) << 17) |
          ((uint32_t)(TBM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 
-// Copies a 128 x 64 tile (K-major rows of 128 bytes) into the swizzled layout.
-__device__ __forceinline__ void load_tile(const uint16_t* __restrict__ g, int64_t ld, int row0, int k0,
-                                          unsigned char* s) {
-  for (int c = threadIdx.x; c < 128 * 8; c += blockDim.x) {
-    const int r = c >> 3, ch = c & 7;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(g + (int64_t)(row0 + r) * ld + k0 + ch * 8));
-    *reinterpret_cast<uint4*>(s + r * 128 + ((ch ^ (r & 7)) << 4)) = v;
+// Waits for completion of the phase with the given parity.  Gives up after
+// kWaitNs, or (when stop is non-null) as soon as another role has aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stop) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (stop && *stop) return false;
+      if (global_ns() - t0 > kWaitNs) return false;
+    }
   }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint32_t dst, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint32_t dst, uint32_t bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
 }
 
 }  // namespace
 
 // C (Mp x Np, FP32) = A (Mp x Kp) B^T (Np x Kp); epilogue writes complex rows
 // (2i, 2i+1) of C to out_u (i < Nh) or out_v (i >= Nh) for column n = j*nrhs+c.
-template <bool BF16>
-__global__ void __launch_bounds__(128) k_tc_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B,
-                                                 int Kp, int Nh, int ncols, int nrhs, const int32_t* __restrict__ elems,
-                                                 const int64_t* __restrict__ off, float2* __restrict__ out_u,
-                                                 float2* __restrict__ out_v, int* __restrict__ err) {
+template <bool BF16, int CM>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int num_m,
+              int num_groups, int nk, int Nh, int ncols, int nrhs, const int32_t* __restrict__ elems,
+              const int64_t* __restrict__ off, float2* __restrict__ out_u, float2* __restrict__ out_v,
+              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned stage buffers
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sA[2] = {base, base + 16384};
-  unsigned char* sB[2] = {base + 32768, base + 49152};
-  __shared__ __align__(8) uint64_t mbar[2];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
-  const int nk = Kp / TBK;
+  __shared__ int abort_flag;
+  volatile int* stop = &abort_flag;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // tile groups: CM consecutive M tiles of one N tile per cluster
+  const int num_mg = (num_m + CM - 1) / CM;
+  const int rank = CM > 1 ? (int)cluster_rank() : 0;
+  const int cid = blockIdx.x / CM, ncl = gridDim.x / CM;
+  constexpr uint16_t kMask = (uint16_t)((1u << CM) - 1);
+  constexpr int B_ROWS = TBN / CM;   // B rows this CTA copies (and multicasts)
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), CM);   // one commit from each CTA of the cluster
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull_bar[b]), 1);
+      mbar_init(smem_u32(&tempty_bar[b]), 8);   // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
-  load_tile(A, Kp, m0, 0, sA[0]);
-  load_tile(B, Kp, n0, 0, sB[0]);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (CM > 1) cluster_sync();   // peers signal these barriers: all must be initialised first
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = make_idesc(BF16);
-  bool ok = true;
-  int uses[2] = {0, 0};
-  for (int kt = 0; kt < nk && ok; ++kt) {
-    const int s = kt & 1;
-    if (tid == 0) {
-      const uint64_t da = make_desc(smem_u32(sA[s])), db = make_desc(smem_u32(sB[s]));
-#pragma unroll
-      for (int kk = 0; kk < TBK / 16; ++kk) {
-        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t a = da + (uint64_t)((kk * 32) >> 4), b = db + (uint64_t)((kk * 32) >> 4);
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mbar[s]))
-                   : "memory");
-    }
-    ++uses[s];
-    if (kt + 1 < nk) {
-      const int s1 = s ^ 1;
-      // the products that read stage s1 must be done before it is overwritten;
-      // thread 0 waits (bounded) and the barrier makes the outcome block-uniform
-      bool w_ok = true;
-      if (uses[s1] > 0 && tid == 0) w_ok = mbar_wait(smem_u32(&mbar[s1]), (uses[s1] - 1) & 1);
-      ok = __syncthreads_and(w_ok) != 0;
-      if (ok) {
-        load_tile(A, Kp, m0, (kt + 1) * TBK, sA[s1]);
-        load_tile(B, Kp, n0, (kt + 1) * TBK, sB[s1]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-  }
-  // wait for the last slice's products (they complete after all earlier ones)
-  {
-    bool w_ok = ok;
-    if (ok && nk > 0 && tid == 0) {
-      const int sl = (nk - 1) & 1;
-      w_ok = mbar_wait(smem_u32(&mbar[sl]), (uses[sl] - 1) & 1);
-    }
-    ok = __syncthreads_and(w_ok) != 0;
-  }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // epilogue: warp w holds rows 32w..32w+31; lane pairs (2i, 2i+1) are (Re, Im)
-    const int row = m0 + warp * 32 + lane;
-    const int orow = row >> 1;                 // complex output row in the stacked [M; D]
-    for (int c0 = 0; c0 < TBN; c0 += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float v = __uint_as_float(r[q]);
-        const float im = __shfl_down_sync(0xffffffffu, v, 1);
-        const int n = n0 + c0 + q;
-        if ((lane & 1) == 0 && n < ncols && orow < 2 * Nh) {
-          const int j = n / nrhs, cc = n % nrhs;
-          const int64_t e0 = off[elems[j]];
-          const float2 o = make_float2(v, im);
-          if (orow < Nh)
-            out_u[(e0 + orow) * nrhs + cc] = o;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer
+      uint32_t it = 0;
+      bool ok = true;
+      for (int g = cid; g < num_groups && ok; g += ncl) {
+        const int m0 = ((g % num_mg) * CM + rank) * TBM, n0 = (g / num_mg) * TBN;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          unsigned char* sa = base + s * STAGE_BYTES;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          tma_load_2d(&tmA, smem_u32(sa), fb, kt * TBK, m0);
+          if (CM == 1)
+            tma_load_2d(&tmB, smem_u32(sa + A_BYTES), fb, kt * TBK, n0);
           else
-            out_v[(e0 + orow - Nh) * nrhs + cc] = o;
+            tma_load_2d_mc(&tmB, smem_u32(sa + A_BYTES + rank * B_ROWS * 128), fb, kt * TBK, n0 + rank * B_ROWS,
+                           kMask);
         }
       }
+      if (!ok && !*stop) {
+        *stop = 1;
+        atomicExch(err, 1);
+      }
+      // copies still in flight land before the CTA's shared memory is released
+      for (uint32_t q = it > (uint32_t)STAGES ? it - STAGES : 0; q < it; ++q)
+        mbar_wait(smem_u32(&full_bar[q % STAGES]), (q / STAGES) & 1, nullptr);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t idesc = make_idesc(BF16);
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int g = cid; g < num_groups && ok; g += ncl, ++lt) {
+        const uint32_t b = lt & 1, ub = lt >> 1;
+        if (!mbar_wait(smem_u32(&tempty_bar[b]), (ub & 1) ^ 1, stop)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + b * TBN;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(smem_u32(&full_bar[s]), r & 1, stop)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
+          const uint64_t da = make_desc(sa), db = make_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TBK / 16; ++kk) {
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t a = da + (uint64_t)((kk * 32) >> 4), bb = db + (uint64_t)((kk * 32) >> 4);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(a), "l"(bb), "r"(idesc), "r"(acc));
+          }
+          if (CM == 1)
+            umma_commit(smem_u32(&empty_bar[s]));
+          else
+            umma_commit_mc(smem_u32(&empty_bar[s]), kMask);
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&tfull_bar[b]));
+      }
+      if (!ok && !*stop) {
+        *stop = 1;
+        atomicExch(err, 1);
+      }
+      // every product issued here completes before TMEM and the stage buffers go away
+      umma_commit(smem_u32(&drain_bar));
+      mbar_wait(smem_u32(&drain_bar), 0, nullptr);
+    }
+  } else {
+    // ---- epilogue (warps 2-9).  Warp w reads TMEM lane quarter q = w % 4 (C
+    // rows m0 + 32q .. +31, complex rows i0 .. i0+15) and column half
+    // (w - 2) / 4 of the accumulator.  Per 16-column chunk: TMEM -> registers
+    // (lane = C row) -> shared staging [16 complex rows][16 columns] (row
+    // stride 17 float2: the Re/Im writes of the 32 lanes fall in 32 distinct
+    // banks) -> global, lanes 0-15 / 16-31 take one column each of two
+    // consecutive rows, so a store instruction covers runs of consecutive
+    // right-hand sides of one or more elements.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    float2* stage = reinterpret_cast<float2*>(base + STAGES * STAGE_BYTES) + (warp - 2) * (16 * 17);
+    float* stage_f = reinterpret_cast<float*>(stage);
+    constexpr int NCH = TBN / 2 / 16;   // 16-column chunks per warp
+    const int col = lane & 15, rsub = lane >> 4;
+    uint32_t lt = 0;
+    bool ok = true;
+    for (int g = cid; g < num_groups; g += ncl, ++lt) {
+      const uint32_t b = lt & 1, ub = lt >> 1;
+      const int m0 = ((g % num_mg) * CM + rank) * TBM;
+      const int nw = (g / num_mg) * TBN + half * (TBN / 2);   // first column of this warp
+      // output offsets of this lane's column in each chunk, loaded while the
+      // accumulator is still being computed
+      int64_t eb[NCH];
+      int ccol[NCH];
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        const int n = nw + 16 * k + col;
+        const int je = n < ncols ? n / nrhs : 0;
+        ccol[k] = n < ncols ? n - je * nrhs : -1;
+        eb[k] = elems[je];
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) eb[k] = off[eb[k]];
+      int w_ok = 1;
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&tfull_bar[b]), ub & 1, stop) ? 1 : 0;
+      w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+      if (!w_ok) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int i0 = (m0 + 32 * q) >> 1;        // first complex output row of this warp
+      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + b * TBN + half * (TBN / 2);
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        uint32_t r[16];
+        tmem_ld16(tbase + 16 * k, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // lane = C row 2*(lane/2) + (lane&1): Re (even) or Im (odd) of complex row lane/2
+#pragma unroll
+        for (int c = 0; c < 16; ++c) stage_f[(lane >> 1) * 34 + 2 * c + (lane & 1)] = __uint_as_float(r[c]);
+        __syncwarp();
+        const int cc = ccol[k];
+        if (cc >= 0) {
+          const int64_t e_base = eb[k];
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int rr = 2 * it + rsub, i = i0 + rr;
+            if (i < 2 * Nh) {
+              const float2 val = stage[rr * 17 + col];
+              if (i < Nh)
+                out_u[(e_base + i) * nrhs + cc] = val;
+              else
+                out_v[(e_base + i - Nh) * nrhs + cc] = val;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
+    }
+    if (!ok && lane == 0 && !*stop) {
+      *stop = 1;
+      atomicExch(err, 1);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  // peers may still multicast into this CTA's buffers or arrive on its
+  // barriers until they are done: leave together
+  if (CM > 1) cluster_sync();
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
 }
 
-// B^T operand: column n = (element elems[n / nrhs], rhs n % nrhs) -> [Re x, Im x], padded.
+// B operand rows: row n = (element elems[n / nrhs], rhs n % nrhs) holds
+// Re x_e(:, rhs) at [0, Nh) and Im x_e(:, rhs) at [Nhp, Nhp + Nh), 16-bit
+// floats (entries outside are not written: A is zero there and the tensor map
+// ends at Nhp + Nh).  Thread (element j, rhs c, row group g) reads rows
+// 8g .. 8g+7 of x_e(:, c) (eight independent loads; consecutive threads take
+// consecutive right-hand sides, so each load instruction uses whole sectors)
+// and writes them as one 16-byte store per half.
 template <bool BF16>
-__global__ void k_pack_b(const float2* __restrict__ x, int Nh, int ncols, int nrhs, const int32_t* __restrict__ elems,
-                         const int64_t* __restrict__ off, int Np, int Kp, uint16_t* __restrict__ Bt) {
-  const int64_t total = (int64_t)Np * Kp;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int n = (int)(t / Kp), kq = (int)(t % Kp);
-    float v = 0.f;
-    if (n < ncols && kq < 2 * Nh) {
-      const int j = n / nrhs, c = n % nrhs;
-      const int kk = kq < Nh ? kq : kq - Nh;
-      const float2 xv = x[(off[elems[j]] + kk) * nrhs + c];
-      v = kq < Nh ? xv.x : xv.y;
-    }
-    uint16_t h;
+__global__ void __launch_bounds__(256) k_pack_b(const float2* __restrict__ x, int Nh, int Nhp, int nrhs, int nel,
+                                                const int32_t* __restrict__ elems, const int64_t* __restrict__ off,
+                                                int Kp, uint16_t* __restrict__ Bt) {
+  auto cvt = [](float f) -> uint32_t {
     if (BF16) {
-      const __nv_bfloat16 b = __float2bfloat16_rn(v);
-      h = *reinterpret_cast<const uint16_t*>(&b);
-    } else {
-      const __half b = __float2half_rn(v);
-      h = *reinterpret_cast<const uint16_t*>(&b);
+      const __nv_bfloat16 b = __float2bfloat16_rn(f);
+      return *reinterpret_cast<const uint16_t*>(&b);
     }
-    Bt[t] = h;
+    const __half h = __float2half_rn(f);
+    return *reinterpret_cast<const uint16_t*>(&h);
+  };
+  const int ng = (Nh + 7) >> 3;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ng * nrhs) return;
+  const int g = i / nrhs, c = i - g * nrhs, kb = 8 * g;
+  for (int j = blockIdx.y; j < nel; j += gridDim.y) {
+    const float2* src = x + (off[elems[j]] + kb) * nrhs + c;
+    uint16_t* dre = Bt + ((int64_t)j * nrhs + c) * Kp + kb;
+    uint16_t* dim = dre + Nhp;
+    if (kb + 8 <= Nh) {
+      float2 v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = __ldg(src + (int64_t)t * nrhs);
+      uint32_t wr[4], wi[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        wr[t] = cvt(v[2 * t].x) | (cvt(v[2 * t + 1].x) << 16);
+        wi[t] = cvt(v[2 * t].y) | (cvt(v[2 * t + 1].y) << 16);
+      }
+      *reinterpret_cast<uint4*>(dre) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+      *reinterpret_cast<uint4*>(dim) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+    } else {
+      for (int t = 0; t < Nh - kb; ++t) {
+        const float2 v = __ldg(src + (int64_t)t * nrhs);
+        dre[t] = (uint16_t)cvt(v.x);
+        dim[t] = (uint16_t)cvt(v.y);
+      }
+    }
   }
 }
 
-size_t tc_smem_bytes() { return 4 * 16384 + 1024; }
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+int g_sms[64] = {0};
+
+// 2-D tensor map over a row-major (rows x inner) 16-bit matrix with row stride
+// ld elements; box = box_inner x box_rows, 128-byte swizzle, zero fill outside.
+bool encode_2d(CUtensorMap* m, bool bf16, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
+               uint32_t box_inner, uint32_t box_rows) {
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {box_inner, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// stage ring + epilogue staging (8 warps x 16 x 17 complex) + alignment slack
+size_t tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 8 * 16 * 17 * 8 + 1024; }
+
+int tc_k_split(int Nh) { return (Nh + 7) / 8 * 8; }
+
+// CTAs per cluster along M.  1 by default: multicasting B to a pair measured
+// no faster on GB300 (the main loop is not bound by L2 reads) and pads an odd
+// number of M tiles.
+int g_cluster_m = 1;
+
+void tc_set_cluster(int cm) { g_cluster_m = cm == 1 ? 1 : 2; }
 
 cudaError_t tc_gemm_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes());
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    // tuning override: MACROAIM_TC_CLUSTER=2 multicasts B slices to CTA pairs
+    if (const char* c = std::getenv("MACROAIM_TC_CLUSTER")) tc_set_cluster(std::atoi(c));
+  });
+  if (!g_encode) return cudaErrorNotSupported;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+  if (dev >= 0 && dev < 64) {
+    e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+#define MM_TC_ATTR(B, C)                                                                                  \
+  e = cudaFuncSetAttribute(k_tc_gemm<B, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()); \
+  if (e != cudaSuccess) return e;
+  MM_TC_ATTR(true, 1) MM_TC_ATTR(false, 1) MM_TC_ATTR(true, 2) MM_TC_ATTR(false, 2)
+#undef MM_TC_ATTR
+  return cudaSuccess;
 }
+
+namespace {
+
+template <bool BF16, int CM>
+cudaError_t launch_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, int num_m, int num_n, int nk, int Nh,
+                      int ncols, int nrhs, const int32_t* elems, const int64_t* off, float2* u, float2* v, int* err,
+                      int sms, cudaStream_t st) {
+  const int num_groups = (num_m + CM - 1) / CM * num_n;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = tc_smem_bytes();
+  cfg.stream = st;
+  int clusters = sms / CM;
+  if (CM > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(CM * clusters));
+    // co-resident clusters, queried once per device (-1: query failed)
+    static int active_cache[64];
+    static std::once_flag active_once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64) {
+      std::call_once(active_once[dev], [&] {
+        int a = 0;
+        active_cache[dev] =
+            cudaOccupancyMaxActiveClusters(&a, k_tc_gemm<BF16, CM>, &cfg) == cudaSuccess && a > 0 ? a : -1;
+      });
+      if (active_cache[dev] > 0) clusters = std::min(clusters, active_cache[dev]);
+    }
+  }
+  clusters = std::max(1, std::min(clusters, num_groups));
+  cfg.gridDim = dim3((unsigned)(CM * clusters));
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm<BF16, CM>, tmA, tmB, num_m, num_groups, nk, Nh, ncols, nrhs, elems, off,
+                            u, v, err);
+}
+
+}  // namespace
 
 cudaError_t tc_macro_gemm(bool bf16, const uint16_t* A, int Mp, int Kp, int Nh, const int32_t* elems, int nel,
                           int nrhs, const int64_t* off, const float2* x, uint16_t* Bt, size_t bt_cap, float2* u,
                           float2* v, int* err, cudaStream_t st) {
   const int ncols = nel * nrhs;
-  const int Np = (ncols + TBN - 1) / TBN * TBN;
-  if ((size_t)Np * Kp > bt_cap) return cudaErrorInvalidValue;
-  const int64_t total = (int64_t)Np * Kp;
-  const unsigned pb = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  if (bf16)
-    k_pack_b<true><<<pb, 256, 0, st>>>(x, Nh, ncols, nrhs, elems, off, Np, Kp, Bt);
-  else
-    k_pack_b<false><<<pb, 256, 0, st>>>(x, Nh, ncols, nrhs, elems, off, Np, Kp, Bt);
-  dim3 g(Mp / TBM, Np / TBN);
-  if (bf16)
-    k_tc_gemm<true><<<g, 128, tc_smem_bytes(), st>>>(A, Bt, Kp, Nh, ncols, nrhs, elems, off, u, v, err);
-  else
-    k_tc_gemm<false><<<g, 128, tc_smem_bytes(), st>>>(A, Bt, Kp, Nh, ncols, nrhs, elems, off, u, v, err);
-  return cudaGetLastError();
+  if (ncols <= 0) return cudaSuccess;
+  const int Nhp = tc_k_split(Nh);
+  if (!g_encode || Mp % TBM || Kp % TBK || Nhp + Nh > Kp || (size_t)ncols * Kp > bt_cap) return cudaErrorInvalidValue;
+  {
+    const int items = ((Nh + 7) / 8) * nrhs;
+    dim3 pg((unsigned)((items + 255) / 256), (unsigned)std::min(nel, 65535));
+    if (bf16)
+      k_pack_b<true><<<pg, 256, 0, st>>>(x, Nh, Nhp, nrhs, nel, elems, off, Kp, Bt);
+    else
+      k_pack_b<false><<<pg, 256, 0, st>>>(x, Nh, Nhp, nrhs, nel, elems, off, Kp, Bt);
+  }
+  const int cm = g_cluster_m;
+  CUtensorMap tmA, tmB;
+  if (!encode_2d(&tmA, bf16, A, (uint64_t)Kp, (uint64_t)Mp, (uint64_t)Kp, TBK, TBM) ||
+      !encode_2d(&tmB, bf16, Bt, (uint64_t)(Nhp + Nh), (uint64_t)ncols, (uint64_t)Kp, TBK, TBN / cm))
+    return cudaErrorInvalidValue;
+  const int num_m = Mp / TBM, num_n = (ncols + TBN - 1) / TBN;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int sms = (dev >= 0 && dev < 64 && g_sms[dev] > 0) ? g_sms[dev] : 148;
+  const int nk = Kp / TBK;
+  if (cm == 1)
+    return bf16 ? launch_tc<true, 1>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st)
+                : launch_tc<false, 1>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st);
+  return bf16 ? launch_tc<true, 2>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st)
+              : launch_tc<false, 2>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st);
 }
 
 int tc_tile_m() { return TBM; }

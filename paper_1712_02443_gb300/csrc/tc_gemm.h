@@ -13,6 +13,10 @@ int tc_tile_m();
 int tc_tile_n();
 int tc_tile_k();
 size_t tc_smem_bytes();
+// Offset of the imaginary half in the K dimension of both operands (Nh rounded up to 8).
+int tc_k_split(int Nh);
+// CTAs per cluster along M (1, the default: no multicast; 2: B slices multicast to both).
+void tc_set_cluster(int cm);
 cudaError_t tc_gemm_init();
 // u, v (complex64) = [M; D] x for the elements of one type.  A: packed real
 // operator (Mp x Kp, 16-bit, K-major); Bt: scratch for the packed right-hand

@@ -229,3 +229,22 @@ def test_c3_batched_solve_equals_columns_alone(c3):
         assert s1["converged"]
         e1 = E1.cpu().numpy()
         assert np.linalg.norm(Eb[:, j] - e1) / np.linalg.norm(e1) <= 2e-3
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_far_field_only_operator(ctx, c1, loop_model, prec):
+    """N_NF = -1 drops the precorrection: y = D x - I H P T A^-1 B x (no G_NF term),
+    3 x 2 array, three right-hand sides."""
+    from oracle.aim import AIMArray, AIMParams
+    lay = wl.loop_array(3, 2)
+    A = AIMArray([loop_model], lay.type_of, lay.offsets, AIMParams(0.1, 2, -1, wl.DEFAULT_GRID_PHASE), K0)
+    assert A.GNF.nnz == 0
+    la = loop_array(ctx, 3, 2, n_nf=-1, types=c1.types)
+    try:
+        assert la.info["nnz_near"] == 0
+        X = wl.random_cvec(la.n, 0, 13, nrhs=3)
+        Y = _apply(la, X, prec, nrhs=3)
+        ref = np.stack([A.matvec(np.ascontiguousarray(X[:, j])) for j in range(3)], axis=1)
+        _close(Y, ref, prec)
+    finally:
+        mm.mm_array_destroy(la.array)

@@ -79,3 +79,44 @@ def test_tensorcore_solve_refined(c1, prec):
     assert st["converged"] and st["rel_residual"] <= 1e-6
     err = np.linalg.norm(E.cpu().numpy() - g["E"]) / np.linalg.norm(g["E"])
     assert err <= 1e-4, err
+
+
+C3_OUTERS = (0.30, 0.34, 0.38, 0.42)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C64_F16, mm.MM_C64_BF16])
+def test_tensorcore_four_types_64_rhs(c1, prec):
+    """Four element types, 64 right-hand sides (whole-element 8-column output
+    groups): sampled rows of all 64 columns vs the oracle."""
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    la = loop_array(c1.ctx, 6, 6, outers=C3_OUTERS, config_index=2)
+    try:
+        X = wl.random_cvec(la.n, 2, 7, nrhs=64)
+        Y = _apply(la, X, prec, nrhs=64)[g["rows"]]
+        rel = np.linalg.norm(Y - g["y_rows"]) / np.linalg.norm(g["y_rows"])
+        assert rel <= BAR[prec], rel
+    finally:
+        la.close()
+
+
+def test_tensorcore_many_tiles_per_cta(c1, loop_model):
+    """32 x 32 array, 16 right-hand sides: 16384 columns, 576 output tiles of
+    128 x 256, about four per CTA of the persistent kernel, so each CTA reuses
+    both accumulators.  Far-field operator only (N_NF = -1) so that the
+    oracle's full product is cheap; columns 8-15 are 1j times columns 0-7, whose
+    products follow by linearity.  The whole product is compared, both formats."""
+    from oracle.aim import AIMArray, AIMParams
+    lay = wl.loop_array(32, 32)
+    A = AIMArray([loop_model], lay.type_of, lay.offsets, AIMParams(0.1, 2, -1, wl.DEFAULT_GRID_PHASE), 2 * np.pi)
+    la = loop_array(c1.ctx, 32, 32, n_nf=-1, types=c1.types)
+    try:
+        X8 = wl.random_cvec(la.n, 0, 14, nrhs=8)
+        ref8 = np.stack([A.matvec(np.ascontiguousarray(X8[:, j])) for j in range(8)], axis=1)
+        X = np.concatenate([X8, 1j * X8], axis=1)
+        ref = np.concatenate([ref8, 1j * ref8], axis=1)
+        for prec in (mm.MM_C64_F16, mm.MM_C64_BF16):
+            Y = _apply(la, X, prec, nrhs=16)
+            rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+            assert rel <= BAR[prec], (prec, rel)
+    finally:
+        mm.mm_array_destroy(la.array)

@@ -129,3 +129,15 @@ def test_rounding_tie_rejected(host_ctx, lib_c1):
     ty = lib_c1.types[0]
     with pytest.raises(mm.MacroAIMError):
         mm.mm_array_create(host_ctx, [ty], np.zeros((1, 3)), 0.1, 2, 3, (0.0137, 0.0291, 0.0))
+
+
+def test_near_field_radius_options(host_ctx, lib_c1):
+    """N_NF = -1 builds the far-field-only operator (no near-field rows); below -1 is refused."""
+    ty = lib_c1.types[0]
+    arr = mm.mm_array_create(host_ctx, [ty, ty], np.array([[0, 0, 0], [0.5, 0, 0]]), 0.1, 2, -1,
+                             wl.DEFAULT_GRID_PHASE)
+    assert mm.mm_array_info_get(arr)["nnz_near"] == 0
+    mm.mm_array_destroy(arr)
+    with pytest.raises(mm.MacroAIMError) as e:
+        mm.mm_array_create(host_ctx, [ty], np.zeros((1, 3)), 0.1, 2, -2, wl.DEFAULT_GRID_PHASE)
+    assert e.value.status == mm.MM_EINVAL
