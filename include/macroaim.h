@@ -231,6 +231,12 @@ typedef struct mm_solve_opts {
   int32_t precision;  /* operator precision inside GMRES                      */
   int32_t refine;     /* 1: FP64 outer refinement (needs a complex64 mode)    */
   double inner_tol;   /* inner GMRES tolerance when refining                  */
+  int32_t orth;       /* Arnoldi orthogonalisation (classical Gram-Schmidt):
+                         0 = automatic (default): one pass for the inner
+                         solves of refinement, whose error the FP64 outer
+                         residual corrects; selective second pass otherwise;
+                         1 = one pass; 2 = second pass only for columns whose
+                         norm fell below 1/sqrt(2); 3 = two passes always      */
 } mm_solve_opts;
 typedef struct mm_solve_stats {
   int32_t iterations;     /* inner GMRES iterations (max over columns)        */

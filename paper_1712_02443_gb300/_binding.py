@@ -48,7 +48,7 @@ class mm_array_info(ct.Structure):
 
 class mm_solve_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
-                ("refine", ct.c_int32), ("inner_tol", ct.c_double)]
+                ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32)]
 
 
 class mm_solve_stats(ct.Structure):
@@ -313,8 +313,9 @@ def mm_rcs(array, nrhs: int, Jhat_dev, theta, phi) -> np.ndarray:
 
 
 def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_iter: int = 1000,
-             precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2, stream=None, check: bool = True):
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol)
+             precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2, stream=None, check: bool = True,
+             orth: int = 0):
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth)
     s = mm_solve_stats()
     st = load().mm_solve(array, nrhs, _ptr(V_dev), _ptr(E_dev), ct.byref(o), ct.byref(s), _stream(stream))
     stats = {"iterations": s.iterations, "matvecs": s.matvecs, "refinements": s.refinements,

@@ -737,6 +737,7 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (nrhs < 1 || !V_dev || !E_dev || !opts || V_dev == E_dev) return fail(ctx, MM_EINVAL, "invalid solve arguments");
   if (!(opts->tol > 0) || opts->restart < 1 || opts->max_iter < 1) return fail(ctx, MM_EINVAL, "invalid solve options");
   if (opts->precision < MM_C64 || opts->precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (opts->orth < 0 || opts->orth > 3) return fail(ctx, MM_EINVAL, "orth must be 0, 1, 2 or 3");
   if (opts->refine && opts->precision == MM_C128)
     return fail(ctx, MM_EINVAL, "refinement needs a complex64 operator precision");
   API_TRY
@@ -745,6 +746,8 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (!a->solver) a->solver = std::make_unique<mm::Solver>();
   mm::Solver& S = *a->solver;
   S.prof = &a->da.prof;
+  // Arnoldi mode of the kernel: 1 one pass, 2 selective second pass, 3 two passes
+  S.orth = opts->orth != 0 ? opts->orth : (opts->refine ? 1 : 2);
   mm::Status s = S.ensure(a->da.N, nrhs, opts->restart);
   if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
   upload_precision<double>(a, a->da.pd);

@@ -145,6 +145,7 @@ struct GmresDev {
   Z* y;            // m r
   int* flag;       // mapped host memory: [0] any column active, [1] k, [2] max kdone
   int m, r;
+  int orth;        // 1 one Gram-Schmidt pass, 2 selective second pass, 3 two passes
 };
 
 static_assert(sizeof(GmresDev) <= 160, "GmresDev must fit Solver::gdev_");
@@ -274,6 +275,10 @@ __global__ void k_cgs_update_dots(const Z* __restrict__ V, int64_t vs, GmresDev 
     w[t] = a;
   }
   __syncthreads();
+  if (gd.orth == 1) {   // one pass: the second-pass coefficients are zero
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) P2[((int64_t)i * r + j) * nblk + blk] = make_double2(0, 0);
+    return;
+  }
   block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2);
 }
 
@@ -501,8 +506,9 @@ __device__ __forceinline__ double sum_blocks(const double* __restrict__ PN, int 
 // resident; grid-wide barriers between the phases, no spin-waits of our own).
 // Classical Gram-Schmidt with selective reorthogonalisation: the second pass
 // runs only for columns whose norm fell below 1/sqrt(2) of its value before
-// the first pass (Daniel, Gragg, Kaufman and Stewart 1976); the decision is
-// the same in every block, so every block takes the same grid barriers.
+// the first pass (Daniel, Gragg, Kaufman and Stewart 1976; gd.orth = 2), never
+// (gd.orth = 1) or always (gd.orth = 3); the decision is the same in every
+// block, so every block takes the same grid barriers.
 //  0. w = operator output (complex64 -> FP64) on this block's rows;
 //  1. partial <V_i, w>, i <= k, and ||w||^2;            [grid sync]
 //  2. h = sum of partials; w -= V h; partial ||w||^2;   [grid sync]
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   __syncthreads();
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     const double b0 = sum_blocks(PN0, j, nblk), b1 = sum_blocks(PN1, j, nblk);
-    need[j] = gd.active[j] && (b1 < 0.5 * b0);
+    need[j] = gd.active[j] && (gd.orth == 3 || (gd.orth == 2 && b1 < 0.5 * b0));
     if (need[j]) atomicOr(&any_s, 1);
   }
   __syncthreads();
@@ -830,6 +836,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
   Z* V = static_cast<Z*>(V_);
   Z* w = static_cast<Z*>(w_);
   GmresDev gd = *reinterpret_cast<GmresDev*>(gdev_);
+  gd.orth = orth;
   volatile int* flag = static_cast<volatile int*>(flag_h_);
   iters = 0;
   res.assign(r, 0.0);

@@ -29,6 +29,7 @@ class Solver {
   std::function<Status(const void*, void*, cudaStream_t)> op32;
   int matvecs = 0;
   Profiler* prof = nullptr;   // optional stage profiler (Krylov kernels)
+  int orth = 2;               // 1 one pass, 2 selective second pass, 3 two passes
 
   ~Solver() { release(); }
   Status ensure(int64_t N, int r, int m);

@@ -248,3 +248,27 @@ def test_far_field_only_operator(ctx, c1, loop_model, prec):
         _close(Y, ref, prec)
     finally:
         mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec,refine,orth", [(mm.MM_C128, 0, 1), (mm.MM_C128, 0, 3), (mm.MM_C64, 1, 2),
+                                              (mm.MM_C64, 1, 3)])
+def test_c1_solve_orthogonalisation_modes(c1, prec, refine, orth):
+    """Every Arnoldi orthogonalisation mode (one classical Gram-Schmidt pass,
+    selective second pass, two passes) reaches the oracle's solution within the
+    solver tolerance."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    V = torch.from_numpy(g["V"]).cuda()
+    E = torch.empty_like(V)
+    st = mm.mm_solve(c1.array, 1, V, E, tol=1e-6, restart=50, max_iter=500, precision=prec, refine=refine,
+                     orth=orth)
+    assert st["converged"] and st["rel_residual"] <= 1e-6
+    err = np.linalg.norm(E.cpu().numpy() - g["E"]) / np.linalg.norm(g["E"])
+    assert err <= 1e-4, err
+
+
+def test_orthogonalisation_mode_out_of_range_rejected(c1):
+    V = torch.zeros(c1.n, dtype=torch.complex128, device="cuda")
+    E = torch.empty_like(V)
+    with pytest.raises(mm.MacroAIMError) as e:
+        mm.mm_solve(c1.array, 1, V, E, tol=1e-6, orth=4)
+    assert e.value.status == mm.MM_EINVAL
