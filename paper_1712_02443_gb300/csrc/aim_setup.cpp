@@ -484,6 +484,20 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
     }
   });
   ah.n_blocks = (int64_t)blocks.size();
+  ah.nf_blocks.resize(blocks.size());
+  for (size_t id = 0; id < blocks.size(); ++id) {
+    auto& d = ah.nf_blocks[id];
+    const auto& key = block_keys[id];
+    d.ta = (int32_t)key[0];
+    d.tb = (int32_t)key[1];
+    for (int a = 0; a < 3; ++a) d.dL[a] = key[2 + a];
+    d.Na = types[key[0]]->Nh;
+    d.Nb = types[key[1]]->Nh;
+    d.ptr = std::move(blocks[id].ptr);
+    d.col = std::move(blocks[id].col);
+    d.val = std::move(blocks[id].val);
+  }
+  ah.nf_nbr = std::move(nbr);
 }
 
 }  // namespace mm

@@ -40,6 +40,19 @@ struct ArrayHost {
   std::vector<cd> val;
   cd c_A, c_phi;
   int64_t n_blocks = 0;
+  // the near field before expansion: distinct (type, type, lattice offset)
+  // blocks (sparse rows, local columns) and, per element, its neighbours with
+  // the block that couples them (rows of element e, columns of the neighbour)
+  struct NearBlock {
+    int32_t ta = 0, tb = 0;
+    int64_t dL[3] = {0, 0, 0};
+    int64_t Na = 0, Nb = 0;
+    std::vector<int64_t> ptr;   // Na + 1 (empty: no near pairs)
+    std::vector<int32_t> col;
+    std::vector<cd> val;
+  };
+  std::vector<NearBlock> nf_blocks;
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> nf_nbr;   // (neighbour element, block id)
 };
 
 std::vector<int> stencil_1d(int order);

@@ -136,6 +136,23 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
     }
     p.val = dev_upload(v.data(), v.size(), da.bytes);
   }
+  if (da.nfb_entries > 0) {
+    // near-field blocks, dense row-major (zeros outside the near pairs)
+    std::vector<C> d((size_t)da.nfb_entries);
+    for (auto& z : d) { z.x = 0; z.y = 0; }
+    int64_t o = 0;
+    for (const auto& b : ah.nf_blocks) {
+      if (b.ptr.empty()) continue;
+      for (int64_t m = 0; m < b.Na; ++m)
+        for (int64_t q = b.ptr[m]; q < b.ptr[m + 1]; ++q) {
+          C& z = d[(size_t)(o + m * b.Nb + b.col[q])];
+          z.x = (R)b.val[q].real();
+          z.y = (R)b.val[q].imag();
+        }
+      o += b.Na * b.Nb;
+    }
+    p.nfb_val = dev_upload(d.data(), d.size(), da.bytes);
+  }
   {
     const int64_t Px = ah.fft[0], Py = ah.fft[1], Pz = ah.fft[2];
     std::vector<C> g(Px * Py * Pz);
@@ -265,13 +282,13 @@ void free_prec_f(mm::DevPrec<float>& p) {
     for (void* q : v) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
-  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz})
+  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
 }
 void free_prec_d(mm::DevPrec<double>& p) {
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
-  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz})
+  for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
 }
 
@@ -297,6 +314,10 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : d_JE) cudaFree(q);
   for (void* q : d_T) cudaFree(q);
+  for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist})
+    if (q) cudaFree(q);
+  for (auto& g : da.nfg)
+    if (g.pairs) cudaFree(g.pairs);
 }
 
 extern "C" {
@@ -540,6 +561,59 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
       da.nnz_padded = rp[ah.N];
       da.rowptr = dev_upload(rp.data(), rp.size(), acc);
       da.col = dev_upload(cl.data(), cl.size(), acc);
+    }
+    {
+      // near field as blocks: shapes, dense offsets, non-zero k tiles per
+      // 64-row tile, and the element pairs of each lattice offset
+      const auto& nb = ah.nf_blocks;
+      const int64_t nbk = (int64_t)nb.size();
+      int64_t maxNa = 0;
+      for (const auto& b : nb)
+        if (!b.ptr.empty()) maxNa = std::max(maxNa, b.Na);
+      const int nmt = (int)((maxNa + 63) / 64);
+      std::vector<int32_t> na(nbk, 0), nbv(nbk, 0), tptr(nbk * std::max(nmt, 1) + 1, 0), tl;
+      std::vector<int64_t> boff(nbk, 0);
+      int64_t o = 0;
+      for (int64_t q = 0; q < nbk; ++q) {
+        const auto& b = nb[q];
+        na[q] = (int32_t)b.Na;
+        nbv[q] = (int32_t)b.Nb;
+        boff[q] = o;
+        std::vector<char> used;
+        for (int mt = 0; mt < nmt; ++mt) {
+          tptr[q * nmt + mt] = (int32_t)tl.size();
+          if (b.ptr.empty() || (int64_t)mt * 64 >= b.Na) continue;
+          used.assign((size_t)((b.Nb + 15) / 16), 0);
+          for (int64_t m = (int64_t)mt * 64; m < std::min<int64_t>(b.Na, (int64_t)mt * 64 + 64); ++m)
+            for (int64_t e = b.ptr[m]; e < b.ptr[m + 1]; ++e) used[b.col[e] / 16] = 1;
+          for (size_t kt = 0; kt < used.size(); ++kt)
+            if (used[kt]) tl.push_back((int32_t)kt);
+        }
+        if (!b.ptr.empty()) o += b.Na * b.Nb;
+      }
+      tptr[nbk * nmt] = (int32_t)tl.size();
+      da.nfb_entries = o;
+      if (o > 0) {
+        da.nfb_nmt = nmt;
+        da.nfb_na = dev_upload(na.data(), na.size(), acc);
+        da.nfb_nb = dev_upload(nbv.data(), nbv.size(), acc);
+        da.nfb_off = dev_upload(boff.data(), boff.size(), acc);
+        da.nfb_tptr = dev_upload(tptr.data(), tptr.size(), acc);
+        da.nfb_tlist = dev_upload(tl.data(), tl.size(), acc);
+        std::map<std::array<int64_t, 3>, std::vector<int4>> groups;
+        for (int64_t e = 0; e < n_elem; ++e)
+          for (const auto& pr : ah.nf_nbr[e]) {
+            const auto& b = nb[pr.second];
+            if (b.ptr.empty()) continue;
+            groups[{b.dL[0], b.dL[1], b.dL[2]}].push_back(make_int4((int)e, (int)pr.first, (int)pr.second, 0));
+          }
+        for (auto& g : groups) {
+          mm::DevArray::NfGroup ng;
+          ng.npairs = (int64_t)g.second.size();
+          ng.pairs = dev_upload(g.second.data(), g.second.size(), acc);
+          da.nfg.push_back(ng);
+        }
+      }
     }
     upload_precision<float>(a.get(), da.pf);
     CU(mm::kernels_init(da));

@@ -83,6 +83,7 @@ struct DevPrec {
   // tensor-core macromodel operands (complex64 modes): per type packed [M; D]
   std::vector<void*> Atc[2];   // [0] BF16, [1] FP16; (Mp x Kp) 16-bit
   std::vector<int> Mp, Kp;
+  void* nfb_val = nullptr;     // near-field blocks, dense row-major, at DevArray::nfb_off
 };
 
 // Work buffers for one (precision, nrhs) pair.
@@ -122,6 +123,22 @@ struct DevArray {
   int64_t* rowptr = nullptr;            // rows padded to multiples of 4 entries (zero values)
   int32_t* col = nullptr;
   int64_t nnz_padded = 0;
+  // near field as translation-invariant blocks (used for 8 or more right-hand
+  // sides): per distinct block its shape and dense offset; per (block, 64-row
+  // tile) the 16-column k tiles that hold a non-zero; element pairs grouped by
+  // lattice offset so that each group touches every output element at most once
+  int nfb_nmt = 0;                      // 64-row tiles of the tallest block
+  int32_t* nfb_na = nullptr;            // per block: rows (N^ of the row type)
+  int32_t* nfb_nb = nullptr;            // per block: columns
+  int64_t* nfb_off = nullptr;           // per block: first entry in the dense values
+  int32_t* nfb_tptr = nullptr;          // blocks x nfb_nmt + 1
+  int32_t* nfb_tlist = nullptr;         // k-tile indices
+  int64_t nfb_entries = 0;              // dense complex entries over all blocks
+  struct NfGroup {
+    int64_t npairs = 0;
+    int4* pairs = nullptr;              // (row element, column element, block, 0)
+  };
+  std::vector<NfGroup> nfg;
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;

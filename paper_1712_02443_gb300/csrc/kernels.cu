@@ -620,6 +620,92 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
   }
 }
 
+// y_a -= B_q u_b for the element pairs (a, b, q) of one lattice offset (each
+// row element appears once per offset, so no two CTAs write the same output).
+// B_q is a dense near-field block (rows of element a's type, columns of b's);
+// only its 16-column k tiles that hold a non-zero in this 64-row tile are
+// visited.  CTA = (pair, 64-row tile) x TN right-hand sides; thread (ty, tx)
+// accumulates a 4 x 4 complex sub-tile in registers.
+template <typename R, int TN>
+__global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
+    const int4* __restrict__ pairs, int nmt, const typename V2<R>::T* __restrict__ vals,
+    const int64_t* __restrict__ boff, const int32_t* __restrict__ bna, const int32_t* __restrict__ bnb,
+    const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int64_t* __restrict__ off, int nrhs,
+    const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
+  typedef typename V2<R>::T C;
+  constexpr int TM = 64, TK = 16, TX = TN / 4, NT = 16 * TX;
+  __shared__ C As[TK][TM + 1];
+  __shared__ C Bs[TK][TN];
+  const int4 pr = pairs[blockIdx.x / nmt];
+  const int mt = blockIdx.x % nmt;
+  const int q = pr.z, Na = bna[q], Nb = bnb[q];
+  const int m0 = mt * TM;
+  if (m0 >= Na) return;
+  const int c0 = blockIdx.y * TN;
+  const C* Bq = vals + boff[q];
+  const int64_t ub = off[pr.y], ya = off[pr.x];
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  const int e1 = tptr[q * nmt + mt + 1];
+  for (int e = tptr[q * nmt + mt]; e < e1; ++e) {
+    const int k0 = tlist[e] * TK;
+    for (int idx = tid; idx < TM * TK; idx += NT) {
+      const int m = idx / TK, kk = idx % TK;
+      As[kk][m] = (m0 + m < Na && k0 + kk < Nb) ? Bq[(int64_t)(m0 + m) * Nb + k0 + kk] : czero<C>();
+    }
+    for (int idx = tid; idx < TK * TN; idx += NT) {
+      const int kk = idx / TN, cc = idx % TN;
+      Bs[kk][cc] = (k0 + kk < Nb && c0 + cc < nrhs) ? u[(ub + k0 + kk) * nrhs + c0 + cc] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
+          acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= Na) break;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      if (c < nrhs) {
+        const int64_t idx = (ya + m) * nrhs + c;
+        y[idx] = csub(y[idx], acc[i][j]);
+      }
+    }
+  }
+}
+
+template <typename R, int TN>
+static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
+                               typename V2<R>::T* y, cudaStream_t st, int& nl) {
+  for (const auto& g : a.nfg) {
+    dim3 grid((unsigned)(g.npairs * a.nfb_nmt), (unsigned)((nrhs + TN - 1) / TN));
+    k_near_blocks<R, TN><<<grid, 16 * (TN / 4), 0, st>>>(
+        g.pairs, a.nfb_nmt, static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_na, a.nfb_nb,
+        a.nfb_tptr, a.nfb_tlist, a.off, nrhs, u, y);
+    ++nl;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which) {
@@ -750,8 +836,20 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     ++nl;
   }
   pr.end(st, nl);
-  // A5: y -= G_NF u
-  if (a.nnz > 0) {
+  // A5: y -= G_NF u; blocks for 8 or more right-hand sides, CSR rows otherwise
+  if (a.nnz > 0 && nrhs >= 8 && a.nfb_entries > 0 && p.nfb_val != nullptr) {
+    pr.begin(sb + 6, st);
+    nl = 0;
+    if (nrhs >= 48)
+      near_blocks_launch<R, 64>(a, p, nrhs, u, y, st, nl);
+    else if (nrhs >= 24)
+      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl);
+    else if (nrhs >= 12)
+      near_blocks_launch<R, 16>(a, p, nrhs, u, y, st, nl);
+    else
+      near_blocks_launch<R, 8>(a, p, nrhs, u, y, st, nl);
+    pr.end(st, nl);
+  } else if (a.nnz > 0) {
     pr.begin(sb + 6, st);
     const unsigned blocks = (unsigned)((a.N + 7) / 8);
     if (nrhs == 1)

@@ -495,6 +495,99 @@ __device__ void block_norms(const Z* __restrict__ w, int64_t n0, int64_t n1, int
   }
 }
 
+struct DAcc {   // complex FP64 accumulator
+  double x, y;
+  __device__ DAcc operator+(const DAcc& o) const { return {x + o.x, y + o.y}; }
+};
+__device__ __forceinline__ double shfl_x(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ DAcc shfl_x(DAcc a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)};
+}
+
+// Sums of per-thread values a[q] (q < NQ) over the threads that hold the
+// same column (j = tid % r, tid < S = (blockDim / r) r) into out(q, j) for
+// j < r, in a fixed thread order (the same result on every run).  When r
+// divides 32 the lanes of one column are folded by shuffles first.  red holds
+// NQ blockDim values.
+template <int NQ, typename T, typename F>
+__device__ __forceinline__ void column_reduce(const T (&a)[NQ], int r, T* red, F out) {
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = blockDim.x / 32, B = blockDim.x;
+  const int S = (B / r) * r;
+  if (r <= 32 && (32 % r) == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T v = a[q];
+      for (int o = 16; o >= r; o >>= 1) v = v + shfl_x(v, o);
+      if (lane < r) red[q * B + warp * r + lane] = v;
+    }
+    __syncthreads();
+    for (int it = tid; it < NQ * r; it += B) {
+      const int q = it / r, j = it - q * r;
+      T s = red[q * B + j];
+      for (int w = 1; w < nw; ++w) s = s + red[q * B + w * r + j];
+      out(q, j, s);
+    }
+  } else {
+    if (tid < S)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) red[q * B + tid] = a[q];
+    __syncthreads();
+    const int G = S / r;
+    for (int it = tid; it < NQ * r; it += B) {
+      const int q = it / r, j = it - q * r;
+      T s = red[q * B + j];
+      for (int g = 1; g < G; ++g) s = s + red[q * B + g * r + j];
+      out(q, j, s);
+    }
+  }
+  __syncthreads();
+}
+
+// Partial <V_i, w_j> over this block's rows for every i <= k and every column
+// j in one pass: P[(i r + j) nblk + blk].  Threads stride the flat index
+// n r + j by S = (blockDim / r) r, so each keeps one column and the loads of a
+// warp are contiguous; basis vectors are taken four at a time.  r <= blockDim.
+__device__ void block_dots_all(const Z* __restrict__ V, int64_t vs, const Z* __restrict__ w, int k, int64_t n0,
+                               int64_t n1, int r, int blk, int nblk, DAcc* red, Z* __restrict__ P) {
+  const int tid = threadIdx.x;
+  const int S = (blockDim.x / r) * r;
+  const int64_t t1 = n1 * r;
+  for (int i0 = 0; i0 <= k; i0 += 4) {
+    DAcc acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = {0, 0};
+    if (tid < S)
+      for (int64_t t = n0 * r + tid; t < t1; t += S) {
+        const Z wt = w[t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (i0 + q <= k) {
+            const Z p = zconjmul(V[(int64_t)(i0 + q) * vs + t], wt);
+            acc[q].x += p.x;
+            acc[q].y += p.y;
+          }
+      }
+    column_reduce<4>(acc, r, red, [&](int q, int j, DAcc v) {
+      if (i0 + q <= k) P[((int64_t)(i0 + q) * r + j) * nblk + blk] = make_double2(v.x, v.y);
+    });
+  }
+}
+
+// Partial ||w_j||^2 over this block's rows for every column: PN[j nblk + blk].
+__device__ void block_norms_all(const Z* __restrict__ w, int64_t n0, int64_t n1, int r, int blk, int nblk, double* red,
+                                double* __restrict__ PN) {
+  const int tid = threadIdx.x;
+  const int S = (blockDim.x / r) * r;
+  double acc = 0;
+  if (tid < S)
+    for (int64_t t = n0 * r + tid; t < n1 * r; t += S) {
+      const Z a = w[t];
+      acc += a.x * a.x + a.y * a.y;
+    }
+  const double a1[1] = {acc};
+  column_reduce<1>(a1, r, red, [&](int, int j, double v) { PN[(int64_t)j * nblk + blk] = v; });
+}
+
 // sum over blocks of PN for column j (same order in every block)
 __device__ __forceinline__ double sum_blocks(const double* __restrict__ PN, int j, int nblk) {
   double t = 0;
@@ -528,7 +621,9 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   Z* hs = sm;                        // (m+1) r   h, then h + h2 in block 0
   Z* h2s = hs + (m + 1) * r;         // (m+1) r
-  Z* ws = h2s + (m + 1) * r;         // (m+1) nw  warp partials
+  Z* ws = h2s + (m + 1) * r;         // max((m+1) nw, 4 blockDim) warp / column partials
+  const int wsn = max((m + 1) * nw, 4 * (int)blockDim.x);
+  const bool all_cols = r <= (int)blockDim.x;   // one pass over all columns
   const int k = *gd.k;
   const int nblk = gridDim.x, blk = blockIdx.x;
   const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
@@ -541,8 +636,13 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       w[t] = make_double2((double)yin[t].x, (double)yin[t].y);
   __syncthreads();
   // phase 1
-  for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P1), __syncthreads();
-  block_norms(w, n0, n1, r, blk, nblk, ws, PN0);
+  if (all_cols) {
+    block_dots_all(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P1);
+    block_norms_all(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN0);
+  } else {
+    for (int j = 0; j < r; ++j) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P1), __syncthreads();
+    block_norms(w, n0, n1, r, blk, nblk, ws, PN0);
+  }
   grid.sync();
   // phase 2
   reduce_all_partials(P1, k, r, nblk, hs);
@@ -558,10 +658,13 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
     w[t] = a;
   }
   __syncthreads();
-  block_norms(w, n0, n1, r, blk, nblk, ws, PN1);
+  if (all_cols)
+    block_norms_all(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN1);
+  else
+    block_norms(w, n0, n1, r, blk, nblk, ws, PN1);
   grid.sync();
   // phase 3: selective reorthogonalisation
-  int* need = reinterpret_cast<int*>(ws + (m + 1) * nw);   // r flags (shared)
+  int* need = reinterpret_cast<int*>(ws + wsn);   // r flags (shared)
   __shared__ int any_s;
   if (threadIdx.x == 0) any_s = 0;
   __syncthreads();
@@ -575,9 +678,13 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   for (int i = threadIdx.x; i < (m + 1) * r; i += blockDim.x) h2s[i] = make_double2(0, 0);
   __syncthreads();
   if (any_reorth) {
-    for (int j = 0; j < r; ++j) {
-      if (need[j]) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2);
-      __syncthreads();
+    if (all_cols) {
+      block_dots_all(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P2);
+    } else {
+      for (int j = 0; j < r; ++j) {
+        if (need[j]) block_dots(V, vs, w, k, n0, n1, r, j, blk, nblk, ws, P2);
+        __syncthreads();
+      }
     }
     grid.sync();
     for (int p = warp; p < (k + 1) * r; p += nw) {
@@ -606,7 +713,10 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       w[t] = a;
     }
     __syncthreads();
-    block_norms(w, n0, n1, r, blk, nblk, ws, PN2);
+    if (all_cols)
+      block_norms_all(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN2);
+    else
+      block_norms(w, n0, n1, r, blk, nblk, ws, PN2);
     grid.sync();
   }
   // phase 4: block 0, warp per column
@@ -705,7 +815,9 @@ Status Solver::ensure(int64_t N, int r, int m) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    coop_smem_ = sizeof(Z) * (size_t)(m + 1) * (2 * r + 8) + sizeof(int) * (size_t)r + 16;
+    // hs, h2s: (m+1) r each; ws: max((m+1) warps, block threads); need flags
+    coop_smem_ = sizeof(Z) * ((size_t)(m + 1) * 2 * r + std::max<size_t>((size_t)(m + 1) * 8, 4 * 256)) +
+                 sizeof(int) * (size_t)r + 16;
     coop_ok_ = coop_smem_ <= 200 * 1024;
     if (coop_ok_) {
       MM_CK(cudaFuncSetAttribute(k_arnoldi_step<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -272,3 +272,16 @@ def test_orthogonalisation_mode_out_of_range_rejected(c1):
     with pytest.raises(mm.MacroAIMError) as e:
         mm.mm_solve(c1.array, 1, V, E, tol=1e-6, orth=4)
     assert e.value.status == mm.MM_EINVAL
+
+
+@pytest.mark.parametrize("nrhs", [8, 12, 24])
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_c3_block_near_field_column_tiles(c3, prec, nrhs):
+    """8 or more right-hand sides take the near field as dense translation-invariant
+    blocks (one launch per lattice offset) instead of CSR rows; 8, 12 and 24 columns
+    exercise the 8-, 16- and 32-column tiles and the ragged column edge.  The first
+    nrhs columns of the 64-column oracle product are the reference."""
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    X = wl.random_cvec(c3.n, 2, 7, nrhs=64)
+    Y = _apply(c3, np.ascontiguousarray(X[:, :nrhs]), prec, nrhs=nrhs)
+    _close(Y[g["rows"]], g["y_rows"][:, :nrhs], prec)
