@@ -136,6 +136,15 @@ typedef struct mm_aim_opts {
   int32_t n_nf;      /* near-field radius N_NF in grid cells; -1: no near-field
                         correction (far-field operator only, for studies)     */
   double phase[3];   /* position of one grid node                             */
+  int32_t near_csr;  /* the near field is always kept as translation-invariant
+                        (type, type, lattice offset) blocks, which the device
+                        products use; the expanded CSR matrix is assembled
+                        for inspection (MM_EXPORT_NEAR_*) and for the
+                        complex128 products, which stream it (the dense blocks
+                        cost more at GB300's FP64 rate): 0 = automatic (always
+                        on host-only contexts; on a device when its values in
+                        both precisions and its columns fit in 8 GiB), 1 =
+                        always, 2 = never                                      */
 } mm_aim_opts;
 mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* types, const double* offsets_xyz,
                           const mm_aim_opts* opts, mm_array** out);
@@ -148,6 +157,9 @@ typedef struct mm_array_info {
   int64_t nnz_near;      /* near-field nonzeros                               */
   int64_t device_bytes;  /* resident operator bytes on the device             */
   int64_t n_scat_unknowns; /* N_s = sum of the elements' scatterer RWG unknowns */
+  int64_t n_near_blocks; /* distinct (type, type, lattice offset) near blocks   */
+  int64_t near_block_entries; /* their dense complex entries (device: one copy per precision) */
+  int32_t near_format;   /* how the device applies the near field: 0 blocks, 1 CSR rows */
 } mm_array_info;
 mm_status mm_array_info_get(const mm_array* array, mm_array_info* info);
 /* Device bytes a solve with nrhs columns needs beyond the resident operator
@@ -158,6 +170,8 @@ mm_status mm_array_footprint(const mm_array* array, int32_t nrhs, int32_t precis
  *   MM_EXPORT_ANCHORS  int64 (N^ x 3)   stencil anchors (grid indices)
  *   MM_EXPORT_PI       double (N^ x S x 4) projection weights (psi = x,y,z,phi)
  *   MM_EXPORT_NEAR_PTR int64 (N^ + 1)   CSR row pointer of the near field
+ *                                       (the three NEAR exports need the CSR:
+ *                                       MM_EINVAL when it was not assembled)
  *   MM_EXPORT_NEAR_COL int32 (nnz)      CSR columns
  *   MM_EXPORT_NEAR_VAL double (2 nnz)   CSR values, complex128
  *   MM_EXPORT_GHAT     double (2 P)     Green's spectrum, complex128, x slowest

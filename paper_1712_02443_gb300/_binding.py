@@ -37,13 +37,15 @@ class mm_em_opts(ct.Structure):
 
 
 class mm_aim_opts(ct.Structure):
-    _fields_ = [("h", ct.c_double), ("order", ct.c_int32), ("n_nf", ct.c_int32), ("phase", ct.c_double * 3)]
+    _fields_ = [("h", ct.c_double), ("order", ct.c_int32), ("n_nf", ct.c_int32), ("phase", ct.c_double * 3),
+                ("near_csr", ct.c_int32)]
 
 
 class mm_array_info(ct.Structure):
     _fields_ = [("n_unknowns", ct.c_int64), ("n_elem", ct.c_int64), ("n_types", ct.c_int64),
                 ("grid", ct.c_int64 * 3), ("fft", ct.c_int64 * 3), ("nnz_near", ct.c_int64),
-                ("device_bytes", ct.c_int64), ("n_scat_unknowns", ct.c_int64)]
+                ("device_bytes", ct.c_int64), ("n_scat_unknowns", ct.c_int64), ("n_near_blocks", ct.c_int64),
+                ("near_block_entries", ct.c_int64), ("near_format", ct.c_int32)]
 
 
 class mm_solve_opts(ct.Structure):
@@ -225,10 +227,10 @@ def mm_type_destroy(typ) -> None:
     load().mm_type_destroy(typ)
 
 
-def mm_array_create(ctx, types, offsets, h: float, order: int, n_nf: int, phase):
+def mm_array_create(ctx, types, offsets, h: float, order: int, n_nf: int, phase, near_csr: int = 0):
     offsets = np.ascontiguousarray(offsets, dtype=np.float64).reshape(-1, 3)
     arr = (ct.c_void_p * len(types))(*[t.value for t in types])
-    o = mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase))
+    o = mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase), near_csr)
     hnd = ct.c_void_p()
     _check(load().mm_array_create(ctx, len(types), ct.cast(arr, PP), _ptr(offsets), ct.byref(o), ct.byref(hnd)), ctx)
     _ctx_of[hnd.value] = ctx
@@ -240,6 +242,8 @@ def mm_array_info_get(array) -> dict:
     _check(load().mm_array_info_get(array, ct.byref(i)), _ctx_of.get(array.value))
     return {"n_unknowns": i.n_unknowns, "n_elem": i.n_elem, "n_types": i.n_types, "grid": tuple(i.grid),
             "fft": tuple(i.fft), "nnz_near": i.nnz_near, "device_bytes": i.device_bytes,
+            "n_near_blocks": i.n_near_blocks, "near_block_entries": i.near_block_entries,
+            "near_format": "csr" if i.near_format == 1 else "blocks",
             "n_scat_unknowns": i.n_scat_unknowns}
 
 

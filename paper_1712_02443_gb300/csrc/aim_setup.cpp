@@ -448,6 +448,15 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
       }
     });
   }
+  ah.nnz_near = 0;
+  for (int64_t e = 0; e < ne; ++e)
+    for (auto& pr : nbr[e])
+      if (!blocks[pr.second].ptr.empty()) ah.nnz_near += blocks[pr.second].ptr.back();
+  if (o.csr_max_nnz >= 0 && ah.nnz_near > o.csr_max_nnz) {
+    ah.rowptr.clear();
+    ah.col.clear();
+    ah.val.clear();
+  } else {
   // assemble the global CSR, rows element-major, columns ascending
   ah.rowptr.assign(ah.N + 1, 0);
   for (int64_t e = 0; e < ne; ++e) {
@@ -483,6 +492,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
       }
     }
   });
+  }
   ah.n_blocks = (int64_t)blocks.size();
   ah.nf_blocks.resize(blocks.size());
   for (size_t id = 0; id < blocks.size(); ++id) {

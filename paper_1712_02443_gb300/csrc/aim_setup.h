@@ -12,6 +12,7 @@ struct AimOpts {
   int order;
   int n_nf;
   Vec3 phase;
+  int64_t csr_max_nnz = -1;   // assemble the expanded near-field CSR up to this many non-zeros (-1: always)
 };
 
 // Anchors and projection weights of one element type, placed at the array's
@@ -38,6 +39,7 @@ struct ArrayHost {
   std::vector<int64_t> rowptr;  // near field CSR
   std::vector<int32_t> col;
   std::vector<cd> val;
+  int64_t nnz_near = 0;         // near-field non-zeros (whether or not the CSR is assembled)
   cd c_A, c_phi;
   int64_t n_blocks = 0;
   // the near field before expansion: distinct (type, type, lattice offset)

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -121,7 +122,7 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
         for (int c = 0; c < 4; ++c) P[((size_t)sn * Nh + n) * 4 + c] = (R)Pi[((size_t)n * S + sn) * 4 + c];
     p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
   }
-  {
+  if (da.nnz > 0) {
     // near-field values in the padded row layout of da.rowptr (pad entries are 0)
     std::vector<C> v(da.nnz_padded);
     for (auto& z : v) { z.x = 0; z.y = 0; }
@@ -316,8 +317,8 @@ mm_array::~mm_array() {
   for (void* q : d_T) cudaFree(q);
   for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist})
     if (q) cudaFree(q);
-  for (auto& g : da.nfg)
-    if (g.pairs) cudaFree(g.pairs);
+  for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
+    if (q) cudaFree(q);
 }
 
 extern "C" {
@@ -461,14 +462,29 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
   for (int64_t e = 0; e < n_elem; ++e) a->offs[e + 1] = a->offs[e] + tms[type_of[e]]->N;
   std::vector<mm::Vec3> offs(n_elem);
   for (int64_t e = 0; e < n_elem; ++e) offs[e] = {offsets_xyz[3 * e], offsets_xyz[3 * e + 1], offsets_xyz[3 * e + 2]};
+  if (opts->near_csr < 0 || opts->near_csr > 2) return fail(ctx, MM_EINVAL, "near_csr must be 0, 1 or 2");
   mm::AimOpts ao{opts->h, opts->order, opts->n_nf, {opts->phase[0], opts->phase[1], opts->phase[2]}};
+  {
+    // tuning override: MACROAIM_NEAR=csr applies the near field as CSR rows (and needs them)
+    const char* nm = std::getenv("MACROAIM_NEAR");
+    const bool want = nm && std::string(nm) == "csr";
+    // automatic on a device: a moderate CSR (values of both precisions and
+    // columns within 8 GiB) is assembled for the complex128 products, which run
+    // faster from CSR rows at GB300's FP64 rate than from the dense blocks
+    if (opts->near_csr == 1 || (opts->near_csr == 0 && (ctx->device < 0 || want)))
+      ao.csr_max_nnz = -1;
+    else if (opts->near_csr == 2)
+      ao.csr_max_nnz = 0;
+    else
+      ao.csr_max_nnz = ((int64_t)8 << 30) / 28;
+  }
   mm::build_array_host(a->ah, tms, type_of, offs, ao, em);
   auto& ah = a->ah;
   auto& da = a->da;
   da.N = ah.N;
   da.n_elem = n_elem;
   da.n_types = (int64_t)tms.size();
-  da.nnz = ah.rowptr[ah.N];
+  da.nnz = ah.rowptr.empty() ? 0 : ah.rowptr[ah.N];
   for (int i = 0; i < 3; ++i) {
     da.grid[i] = (int)ah.grid[i];
     da.fft[i] = (int)ah.fft[i];
@@ -549,7 +565,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     for (int64_t e = 0; e < n_elem; ++e)
       for (int64_t n = ah.off[e]; n < ah.off[e + 1]; ++n) eof[n] = (int32_t)e;
     a->elem_of = dev_upload(eof.data(), eof.size(), acc);
-    {
+    if (!ah.rowptr.empty()) {
       // rows padded to multiples of 4 entries; pad columns point at the row itself
       std::vector<int64_t> rp(ah.N + 1, 0);
       for (int64_t i = 0; i < ah.N; ++i) rp[i + 1] = rp[i] + (ah.rowptr[i + 1] - ah.rowptr[i] + 3) / 4 * 4;
@@ -600,19 +616,28 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         da.nfb_off = dev_upload(boff.data(), boff.size(), acc);
         da.nfb_tptr = dev_upload(tptr.data(), tptr.size(), acc);
         da.nfb_tlist = dev_upload(tl.data(), tl.size(), acc);
-        std::map<std::array<int64_t, 3>, std::vector<int4>> groups;
+        std::vector<std::vector<int2>> groups(nbk);
         for (int64_t e = 0; e < n_elem; ++e)
-          for (const auto& pr : ah.nf_nbr[e]) {
-            const auto& b = nb[pr.second];
-            if (b.ptr.empty()) continue;
-            groups[{b.dL[0], b.dL[1], b.dL[2]}].push_back(make_int4((int)e, (int)pr.first, (int)pr.second, 0));
-          }
-        for (auto& g : groups) {
+          for (const auto& pr : ah.nf_nbr[e])
+            if (!nb[pr.second].ptr.empty()) groups[pr.second].push_back(make_int2((int)e, (int)pr.first));
+        std::vector<int2> allp;
+        for (int64_t q = 0; q < nbk; ++q) {
+          if (groups[q].empty()) continue;
           mm::DevArray::NfGroup ng;
-          ng.npairs = (int64_t)g.second.size();
-          ng.pairs = dev_upload(g.second.data(), g.second.size(), acc);
+          ng.q = (int)q;
+          ng.Na = (int)nb[q].Na;
+          ng.first_pair = (int64_t)allp.size();
+          ng.npairs = (int64_t)groups[q].size();
+          allp.insert(allp.end(), groups[q].begin(), groups[q].end());
           da.nfg.push_back(ng);
         }
+        static_assert(sizeof(mm::DevArray::NfGroup) == 24, "group record layout shared with the kernel");
+        da.nfg_pairs = dev_upload(allp.data(), allp.size(), acc);
+        da.nfg_dev = dev_upload(reinterpret_cast<const unsigned char*>(da.nfg.data()),
+                                sizeof(mm::DevArray::NfGroup) * da.nfg.size(), acc);
+        // tuning override: MACROAIM_NEAR=csr (CSR rows, when assembled)
+        if (const char* nm = std::getenv("MACROAIM_NEAR"))
+          if (std::string(nm) == "csr") da.near_mode = 2;
       }
     }
     upload_precision<float>(a.get(), da.pf);
@@ -632,9 +657,17 @@ mm_status mm_array_info_get(const mm_array* a, mm_array_info* info) {
     info->grid[i] = a->ah.grid[i];
     info->fft[i] = a->ah.fft[i];
   }
-  info->nnz_near = a->ah.rowptr.empty() ? 0 : a->ah.rowptr.back();
+  info->nnz_near = a->ah.nnz_near;
   info->device_bytes = (int64_t)a->da.bytes;
   info->n_scat_unknowns = a->offs.empty() ? 0 : a->offs.back();
+  info->n_near_blocks = 0;
+  info->near_block_entries = 0;
+  for (const auto& b : a->ah.nf_blocks)
+    if (!b.ptr.empty()) {
+      ++info->n_near_blocks;
+      info->near_block_entries += b.Na * b.Nb;
+    }
+  info->near_format = (a->da.near_mode == 2 && a->da.nnz > 0) ? 1 : 0;
   return MM_OK;
 }
 
@@ -678,6 +711,16 @@ mm_status mm_array_export(const mm_array* a, int32_t which, void* out, int64_t* 
       }
       return MM_OK;
     }
+    case MM_EXPORT_NEAR_PTR:
+    case MM_EXPORT_NEAR_COL:
+    case MM_EXPORT_NEAR_VAL:
+      if (ah.rowptr.empty() && ah.nnz_near > 0)
+        return fail(a->ctx, MM_EINVAL, "near-field CSR not assembled (create the array with near_csr = 1)");
+      break;
+    default:
+      break;
+  }
+  switch (which) {
     case MM_EXPORT_NEAR_PTR:
       *count = (int64_t)ah.rowptr.size();
       if (out) std::memcpy(out, ah.rowptr.data(), sizeof(int64_t) * ah.rowptr.size());

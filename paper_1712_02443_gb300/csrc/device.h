@@ -134,11 +134,15 @@ struct DevArray {
   int32_t* nfb_tptr = nullptr;          // blocks x nfb_nmt + 1
   int32_t* nfb_tlist = nullptr;         // k-tile indices
   int64_t nfb_entries = 0;              // dense complex entries over all blocks
-  struct NfGroup {
-    int64_t npairs = 0;
-    int4* pairs = nullptr;              // (row element, column element, block, 0)
+  struct NfGroup {                      // the element pairs coupled by one block (host mirror)
+    int q = 0;                          // block id
+    int Na = 0;                         // its rows
+    int64_t first_pair = 0, npairs = 0; // range in nfg_pairs
   };
   std::vector<NfGroup> nfg;
+  void* nfg_dev = nullptr;              // device copy of nfg (same layout)
+  int2* nfg_pairs = nullptr;            // (row element, column element), grouped by block
+  int near_mode = 0;                    // 0 blocks; 2 CSR rows (when assembled)
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;

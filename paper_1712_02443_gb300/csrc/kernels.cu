@@ -620,48 +620,113 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
   }
 }
 
-// y_a -= B_q u_b for the element pairs (a, b, q) of one lattice offset (each
-// row element appears once per offset, so no two CTAs write the same output).
-// B_q is a dense near-field block (rows of element a's type, columns of b's);
-// only its 16-column k tiles that hold a non-zero in this 64-row tile are
-// visited.  CTA = (pair, 64-row tile) x TN right-hand sides; thread (ty, tx)
-// accumulates a 4 x 4 complex sub-tile in registers.
+// y_a -= B_q u_b over all element pairs (a, b) and their distinct near-field
+// blocks q, in one launch.  B_q is dense (rows of a's type, columns of b's);
+// only its 16-column k tiles that hold a non-zero in the CTA's 64-row tile are
+// visited.  The GEMM's columns are (pair, right-hand side), n = p nrhs + c, so
+// one right-hand side still fills the tiles.  Tiles are numbered group by
+// group (group = the pairs of one block: row tiles x column tiles); a CTA
+// finds its group by a prefix over the group sizes.  A row element has up to
+// one pair per lattice offset, so its outputs receive several block products:
+// they are accumulated with atomic adds (summation order not fixed).
+struct NearGroupDev {
+  int q, Na;
+  int64_t first_pair, npairs;
+};
+
 template <typename R, int TN>
 __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
-    const int4* __restrict__ pairs, int nmt, const typename V2<R>::T* __restrict__ vals,
-    const int64_t* __restrict__ boff, const int32_t* __restrict__ bna, const int32_t* __restrict__ bnb,
-    const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int64_t* __restrict__ off, int nrhs,
-    const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
+    const NearGroupDev* __restrict__ groups, int ngroups, const int2* __restrict__ pairs,
+    const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
+    int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int64_t* __restrict__ off,
+    int nrhs, int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
   typedef typename V2<R>::T C;
   constexpr int TM = 64, TK = 16, TX = TN / 4, NT = 16 * TX;
   __shared__ C As[TK][TM + 1];
-  __shared__ C Bs[TK][TN];
-  const int4 pr = pairs[blockIdx.x / nmt];
-  const int mt = blockIdx.x % nmt;
-  const int q = pr.z, Na = bna[q], Nb = bnb[q];
-  const int m0 = mt * TM;
-  if (m0 >= Na) return;
-  const int c0 = blockIdx.y * TN;
-  const C* Bq = vals + boff[q];
-  const int64_t ub = off[pr.y], ya = off[pr.x];
+  __shared__ C Bs[TK][TN + 1];
+  __shared__ int64_t cin[TN], cout[TN];   // u / y index of row 0 of each column, -1 past the end
+  __shared__ int s_g, s_mt;
+  __shared__ int64_t s_ct;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const int part = blockIdx.y;   // which of the ksplit shares of the row tile's k tiles
+  if (tid == 0) {
+    int64_t t = blockIdx.x;
+    int g = 0;
+    for (; g < ngroups; ++g) {
+      const int64_t nct = (groups[g].npairs * nrhs + TN - 1) / TN;
+      const int64_t nt = nct * ((groups[g].Na + TM - 1) / TM);
+      if (t < nt) {
+        s_mt = (int)(t / nct);
+        s_ct = t % nct;
+        break;
+      }
+      t -= nt;
+    }
+    s_g = g;
+  }
+  __syncthreads();
+  if (s_g >= ngroups) return;
+  const NearGroupDev gr = groups[s_g];
+  const int mt = s_mt, q = gr.q, Na = gr.Na, Nb = bnb[q];
+  const int m0 = mt * TM;
+  const int64_t ncol = gr.npairs * nrhs, n0 = s_ct * TN;
+  const C* Bq = vals + boff[q];
+  for (int cc = tid; cc < TN; cc += NT) {
+    const int64_t n = n0 + cc;
+    if (n < ncol) {
+      const int64_t pp = n / nrhs;
+      const int c = (int)(n - pp * nrhs);
+      const int2 pr = pairs[gr.first_pair + pp];
+      cin[cc] = off[pr.y] * nrhs + c;
+      cout[cc] = off[pr.x] * nrhs + c;
+    } else {
+      cin[cc] = -1;
+      cout[cc] = -1;
+    }
+  }
   C acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
-  const int e1 = tptr[q * nmt + mt + 1];
-  for (int e = tptr[q * nmt + mt]; e < e1; ++e) {
+  __syncthreads();
+  const bool kfast = nrhs < 16;   // few right-hand sides: a column's rows are the contiguous run
+  const int ea = tptr[q * nmt + mt], eb = tptr[q * nmt + mt + 1];
+  const int e0 = ea + (int)((int64_t)(eb - ea) * part / ksplit), e1 = ea + (int)((int64_t)(eb - ea) * (part + 1) / ksplit);
+  if (e0 == e1) return;   // nothing in this share
+  // the next k tile is loaded into registers while the current one is used
+  constexpr int NA = TM * TK / NT, NB = TK * TN / NT;
+  C ra[NA], rb[NB];
+  auto fetch = [&](int e) {
     const int k0 = tlist[e] * TK;
-    for (int idx = tid; idx < TM * TK; idx += NT) {
-      const int m = idx / TK, kk = idx % TK;
-      As[kk][m] = (m0 + m < Na && k0 + kk < Nb) ? Bq[(int64_t)(m0 + m) * Nb + k0 + kk] : czero<C>();
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int idx = tid + r * NT, m = idx / TK, kk = idx % TK;
+      ra[r] = (m0 + m < Na && k0 + kk < Nb) ? Bq[(int64_t)(m0 + m) * Nb + k0 + kk] : czero<C>();
     }
-    for (int idx = tid; idx < TK * TN; idx += NT) {
-      const int kk = idx / TN, cc = idx % TN;
-      Bs[kk][cc] = (k0 + kk < Nb && c0 + cc < nrhs) ? u[(ub + k0 + kk) * nrhs + c0 + cc] : czero<C>();
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int idx = tid + r * NT;
+      const int kk = kfast ? idx % TK : idx / TN, cc = kfast ? idx / TK : idx % TN;
+      const int64_t ci = cin[cc];
+      rb[r] = (ci >= 0 && k0 + kk < Nb) ? u[ci + (int64_t)(k0 + kk) * nrhs] : czero<C>();
+    }
+  };
+  if (e0 < e1) fetch(e0);
+  for (int e = e0; e < e1; ++e) {
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      const int idx = tid + r * NT;
+      As[idx % TK][idx / TK] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const int idx = tid + r * NT;
+      const int kk = kfast ? idx % TK : idx / TN, cc = kfast ? idx / TK : idx % TN;
+      Bs[kk][cc] = rb[r];
     }
     __syncthreads();
+    if (e + 1 < e1) fetch(e + 1);
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       C a[4], b[4];
@@ -680,15 +745,16 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
-    if (m >= Na) break;
+  for (int j = 0; j < 4; ++j) {
+    const int64_t co = cout[tx * 4 + j];
+    if (co < 0) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx * 4 + j;
-      if (c < nrhs) {
-        const int64_t idx = (ya + m) * nrhs + c;
-        y[idx] = csub(y[idx], acc[i][j]);
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty * 4 + i;
+      if (m < Na) {
+        R* dst = reinterpret_cast<R*>(y + co + (int64_t)m * nrhs);
+        atomicAdd(dst, -acc[i][j].x);
+        atomicAdd(dst + 1, -acc[i][j].y);
       }
     }
   }
@@ -697,13 +763,17 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
 template <typename R, int TN>
 static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
                                typename V2<R>::T* y, cudaStream_t st, int& nl) {
-  for (const auto& g : a.nfg) {
-    dim3 grid((unsigned)(g.npairs * a.nfb_nmt), (unsigned)((nrhs + TN - 1) / TN));
-    k_near_blocks<R, TN><<<grid, 16 * (TN / 4), 0, st>>>(
-        g.pairs, a.nfb_nmt, static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_na, a.nfb_nb,
-        a.nfb_tptr, a.nfb_tlist, a.off, nrhs, u, y);
-    ++nl;
-  }
+  int64_t tiles = 0;
+  for (const auto& g : a.nfg) tiles += ((g.npairs * nrhs + TN - 1) / TN) * ((g.Na + 63) / 64);
+  if (tiles == 0) return;
+  // few output tiles: split each row tile's k tiles over four CTAs (the
+  // outputs are accumulated atomically anyway)
+  const int ksplit = tiles < 4 * 152 ? 4 : 1;
+  k_near_blocks<R, TN><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
+      reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_pairs,
+      static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, a.nfb_nmt, a.nfb_tptr, a.nfb_tlist,
+      a.off, nrhs, ksplit, u, y);
+  ++nl;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -836,18 +906,20 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     ++nl;
   }
   pr.end(st, nl);
-  // A5: y -= G_NF u; blocks for 8 or more right-hand sides, CSR rows otherwise
-  if (a.nnz > 0 && nrhs >= 8 && a.nfb_entries > 0 && p.nfb_val != nullptr) {
+  // A5: y -= G_NF u, as dense blocks (columns = pairs x right-hand sides), or
+  // as CSR rows when the array asked for them (DevArray::near_mode)
+  // complex128 products take CSR rows when assembled (FP64 arithmetic on the
+  // dense blocks costs more than streaming the CSR from HBM)
+  const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
+  if (a.nfb_entries > 0 && p.nfb_val != nullptr && !csr) {
     pr.begin(sb + 6, st);
     nl = 0;
-    if (nrhs >= 48)
+    int64_t cols = 0;
+    for (const auto& g : a.nfg) cols += g.npairs * nrhs;
+    if (cols >= (int64_t)64 * 4 * 152)
       near_blocks_launch<R, 64>(a, p, nrhs, u, y, st, nl);
-    else if (nrhs >= 24)
-      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl);
-    else if (nrhs >= 12)
-      near_blocks_launch<R, 16>(a, p, nrhs, u, y, st, nl);
     else
-      near_blocks_launch<R, 8>(a, p, nrhs, u, y, st, nl);
+      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl);
     pr.end(st, nl);
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, st);

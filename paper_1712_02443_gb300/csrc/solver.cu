@@ -74,17 +74,34 @@ __global__ void k_dot_final(const double* __restrict__ partial, int nvec, int r,
   out[t] = make_double2(sr, si);
 }
 
+// acc += conj(v) w and a -= v h with four FP64 fused multiply-adds each (the
+// FP64 pipe bounds the Arnoldi step on GB300: the zmul-then-add form takes six).
+__device__ __forceinline__ void zconj_fma(const Z v, const Z w, Z& acc) {
+  acc.x = fma(v.x, w.x, acc.x);
+  acc.x = fma(v.y, w.y, acc.x);
+  acc.y = fma(v.x, w.y, acc.y);
+  acc.y = fma(-v.y, w.x, acc.y);
+}
+__device__ __forceinline__ void zsub_mul(const Z v, const Z h, Z& a) {
+  a.x = fma(-v.x, h.x, a.x);
+  a.x = fma(v.y, h.y, a.x);
+  a.y = fma(-v.x, h.y, a.y);
+  a.y = fma(-v.y, h.x, a.y);
+}
+__device__ __forceinline__ void zadd_mul(const Z v, const Z h, Z& a) {
+  a.x = fma(v.x, h.x, a.x);
+  a.x = fma(-v.y, h.y, a.x);
+  a.y = fma(v.x, h.y, a.y);
+  a.y = fma(v.y, h.x, a.y);
+}
+
 // w[n, j] -= sum_{i < nvec} V_i[n, j] h[i * r + j]
 __global__ void k_orth_update(const Z* __restrict__ V, int64_t vstride, const Z* __restrict__ h, int nvec, int64_t N,
                               int r, Z* __restrict__ w) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N * r; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(t % r);
     Z acc = w[t];
-    for (int i = 0; i < nvec; ++i) {
-      Z p = zmul(V[(int64_t)i * vstride + t], h[i * r + j]);
-      acc.x -= p.x;
-      acc.y -= p.y;
-    }
+    for (int i = 0; i < nvec; ++i) zsub_mul(V[(int64_t)i * vstride + t], h[i * r + j], acc);
     w[t] = acc;
   }
 }
@@ -106,11 +123,7 @@ __global__ void k_add_basis(const Z* __restrict__ V, int64_t vstride, const Z* _
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N * r; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(t % r);
     Z acc = x[t];
-    for (int i = 0; i < nvec; ++i) {
-      Z p = zmul(V[(int64_t)i * vstride + t], y[i * r + j]);
-      acc.x += p.x;
-      acc.y += p.y;
-    }
+    for (int i = 0; i < nvec; ++i) zadd_mul(V[(int64_t)i * vstride + t], y[i * r + j], acc);
     x[t] = acc;
   }
 }
@@ -190,13 +203,8 @@ __device__ void block_dots(const Z* __restrict__ V, int64_t vs, const Z* __restr
       const int64_t t = nn * r + j;
       const Z wt = w[t];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (i0 + q <= k) {
-          const Z p = zconjmul(V[(int64_t)(i0 + q) * vs + t], wt);
-          acc[q].x += p.x;
-          acc[q].y += p.y;
-        }
-      }
+      for (int q = 0; q < 4; ++q)
+        if (i0 + q <= k) zconj_fma(V[(int64_t)(i0 + q) * vs + t], wt, acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -268,9 +276,7 @@ __global__ void k_cgs_update_dots(const Z* __restrict__ V, int64_t vs, GmresDev 
     const int64_t t = nn * r + j;
     Z a = w[t];
     for (int i = 0; i <= k; ++i) {
-      const Z p = zmul(V[(int64_t)i * vs + t], hs[i]);
-      a.x -= p.x;
-      a.y -= p.y;
+      zsub_mul(V[(int64_t)i * vs + t], hs[i], a);
     }
     w[t] = a;
   }
@@ -294,12 +300,10 @@ __global__ void k_cgs_update_norm(const Z* __restrict__ V, int64_t vs, GmresDev 
     const int64_t t = nn * r + j;
     Z a = w[t];
     for (int i = 0; i <= k; ++i) {
-      const Z p = zmul(V[(int64_t)i * vs + t], sh[i]);
-      a.x -= p.x;
-      a.y -= p.y;
+      zsub_mul(V[(int64_t)i * vs + t], sh[i], a);
     }
     w[t] = a;
-    acc += a.x * a.x + a.y * a.y;
+    acc = fma(a.x, a.x, fma(a.y, a.y, acc));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
@@ -320,7 +324,7 @@ __global__ void k_norm_partial(const Z* __restrict__ w, int64_t N, int r, int nb
   double acc = 0;
   for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
     const Z a = w[nn * r + j];
-    acc += a.x * a.x + a.y * a.y;
+    acc = fma(a.x, a.x, fma(a.y, a.y, acc));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
@@ -463,9 +467,7 @@ __global__ void k_add_basis_dev(const Z* __restrict__ V, int64_t vs, GmresDev gd
     const int j = (int)(t % gd.r);
     Z acc = x[t];
     for (int i = 0; i < k; ++i) {
-      const Z p = zmul(V[(int64_t)i * vs + t], gd.y[(int64_t)i * gd.r + j]);
-      acc.x += p.x;
-      acc.y += p.y;
+      zadd_mul(V[(int64_t)i * vs + t], gd.y[(int64_t)i * gd.r + j], acc);
     }
     x[t] = acc;
   }
@@ -480,7 +482,7 @@ __device__ void block_norms(const Z* __restrict__ w, int64_t n0, int64_t n1, int
     double acc = 0;
     for (int64_t nn = n0 + threadIdx.x; nn < n1; nn += blockDim.x) {
       const Z a = w[nn * r + j];
-      acc += a.x * a.x + a.y * a.y;
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
@@ -562,9 +564,9 @@ __device__ void block_dots_all(const Z* __restrict__ V, int64_t vs, const Z* __r
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (i0 + q <= k) {
-            const Z p = zconjmul(V[(int64_t)(i0 + q) * vs + t], wt);
-            acc[q].x += p.x;
-            acc[q].y += p.y;
+            Z a = make_double2(acc[q].x, acc[q].y);
+            zconj_fma(V[(int64_t)(i0 + q) * vs + t], wt, a);
+            acc[q] = {a.x, a.y};
           }
       }
     column_reduce<4>(acc, r, red, [&](int q, int j, DAcc v) {
@@ -582,7 +584,7 @@ __device__ void block_norms_all(const Z* __restrict__ w, int64_t n0, int64_t n1,
   if (tid < S)
     for (int64_t t = n0 * r + tid; t < n1 * r; t += S) {
       const Z a = w[t];
-      acc += a.x * a.x + a.y * a.y;
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
     }
   const double a1[1] = {acc};
   column_reduce<1>(a1, r, red, [&](int, int j, double v) { PN[(int64_t)j * nblk + blk] = v; });
@@ -651,9 +653,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
     Z a = w[t];
 #pragma unroll 4
     for (int i = 0; i <= k; ++i) {
-      const Z p = zmul(V[(int64_t)i * vs + t], hs[i * r + j]);
-      a.x -= p.x;
-      a.y -= p.y;
+      zsub_mul(V[(int64_t)i * vs + t], hs[i * r + j], a);
     }
     w[t] = a;
   }
@@ -706,9 +706,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       Z a = w[t];
 #pragma unroll 4
       for (int i = 0; i <= k; ++i) {
-        const Z p = zmul(V[(int64_t)i * vs + t], h2s[i * r + j]);
-        a.x -= p.x;
-        a.y -= p.y;
+        zsub_mul(V[(int64_t)i * vs + t], h2s[i * r + j], a);
       }
       w[t] = a;
     }

@@ -285,3 +285,77 @@ def test_c3_block_near_field_column_tiles(c3, prec, nrhs):
     X = wl.random_cvec(c3.n, 2, 7, nrhs=64)
     Y = _apply(c3, np.ascontiguousarray(X[:, :nrhs]), prec, nrhs=nrhs)
     _close(Y[g["rows"]], g["y_rows"][:, :nrhs], prec)
+
+
+@pytest.fixture()
+def near_csr_env(monkeypatch):
+    """Arrays created under this fixture assemble the near-field CSR and apply the
+    near field as CSR rows (the choice is read when the array is created)."""
+    monkeypatch.setenv("MACROAIM_NEAR", "csr")
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_block_near_field_few_rhs(ctx, c3, prec, nrhs):
+    """Blocks with one or three right-hand sides: the GEMM's columns are (element
+    pair, right-hand side), so one right-hand side still fills the tiles."""
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    la = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2, types=c3.types)
+    try:
+        X = wl.random_cvec(la.n, 2, 7, nrhs=64)
+        Y = _apply(la, np.ascontiguousarray(X[:, :nrhs]), prec, nrhs=nrhs).reshape(la.n, nrhs)
+        _close(Y[g["rows"]], g["y_rows"][:, :nrhs], prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_c2_full_size_csr_near_field(ctx, c1, near_csr_env, prec):
+    """16 x 16 array, one right-hand side, near field as CSR rows (the alternative
+    to the blocks): sampled rows vs the oracle."""
+    g = np.load(os.path.join(GOLD, "c2_16x16.npz"))
+    la = loop_array(ctx, 16, 16, types=c1.types)
+    try:
+        assert la.info["nnz_near"] > 0
+        x = wl.random_cvec(la.n, 1, 7)
+        _close(_apply(la, x, prec)[g["rows"]], g["y_rows"], prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_csr_near_field_multi_rhs(ctx, c3, near_csr_env, prec):
+    """CSR rows with 3 (4-column chunks) and 12 (8-column chunks) right-hand sides."""
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    la = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2, types=c3.types)
+    try:
+        X = wl.random_cvec(la.n, 2, 7, nrhs=64)
+        for nrhs in (3, 12):
+            Y = _apply(la, np.ascontiguousarray(X[:, :nrhs]), prec, nrhs=nrhs).reshape(la.n, nrhs)
+            _close(Y[g["rows"]], g["y_rows"][:, :nrhs], prec)
+    finally:
+        mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_near_csr_never_assembled(ctx, c1, prec):
+    """near_csr = 2: the blocks alone carry the near field in both precisions (the
+    form large arrays use); info still counts its non-zeros, the CSR export is
+    refused, and the product still matches the oracle."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    lay = wl.loop_array(2, 2)
+    arr = mm.mm_array_create(ctx, [c1.types[0]] * lay.n_elem, lay.offsets, 0.1, 2, 3, wl.DEFAULT_GRID_PHASE,
+                             near_csr=2)
+    try:
+        info = mm.mm_array_info_get(arr)
+        assert info["nnz_near"] > 0 and info["near_format"] == "blocks"
+        with pytest.raises(mm.MacroAIMError) as e:
+            mm.mm_array_export(arr, mm.MM_EXPORT_NEAR_PTR)
+        assert e.value.status == mm.MM_EINVAL
+        xd = torch.from_numpy(g["x"]).to(DT[prec]).cuda()
+        yd = torch.empty_like(xd)
+        mm.mm_apply(arr, 1, xd, yd, prec, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        _close(yd.cpu().numpy().astype(np.complex128), g["y"], prec)
+    finally:
+        mm.mm_array_destroy(arr)
