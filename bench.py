@@ -298,6 +298,8 @@ def run_ours(args, rank, world, local):
     mm.mm_array_destroy(la.array)
     if rank == 0 and not args.no_tensor_gemm:
         out["tensor_gemm"] = tensor_gemm_measure(ctx, 64, 8, 10, 3)
+    if rank == 0 and args.serve_requests > 0:
+        out["serving"] = serving_measure(ctx, args.serve_requests, args.serve_min_side, args.serve_max_side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     if rank == 0:
@@ -430,6 +432,114 @@ def tensor_gemm_measure(ctx, side: int, nrhs: int, steps: int, warmup: int) -> d
     return out
 
 
+SERVE_OUTERS = (0.30, 0.34, 0.38, 0.42)   # the four loop types of the batched configuration
+
+
+def serving_requests(n_req: int, min_side: int, max_side: int, seed_stream: int = 5):
+    """Seeded request mix: square arrays (side uniform in [min_side, max_side]), 1-4 of
+    the four loop types drawn per cell, 1-16 plane waves on the 8 x 8 (theta, phi) grid,
+    tolerance 1e-3 or 1e-4 alternating."""
+    from paper_1712_02443_gb300 import workloads as wl
+    g = wl.rng(4, seed_stream)
+    th_all, ph_all, pol_all = wl.planewave_grid()
+    reqs = []
+    for i in range(n_req):
+        side = int(g.integers(min_side, max_side + 1))
+        ntypes = int(g.integers(1, 5))
+        fam = g.choice(4, size=ntypes, replace=False)
+        type_of = fam[g.integers(0, ntypes, size=side * side)]
+        nrhs = int(g.integers(1, 17))
+        pick = g.choice(64, size=nrhs, replace=False)
+        lay = wl.loop_array(side, side, outers=SERVE_OUTERS, config_index=2)
+        reqs.append({"type_of": type_of, "offsets": lay.offsets, "theta": th_all[pick], "phi": ph_all[pick],
+                     "pol": pol_all[pick], "tol": 1e-4 if i % 2 == 0 else 1e-3, "nrhs": nrhs, "side": side})
+    return reqs
+
+
+def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int = 4) -> dict:
+    """Serving: (1) the requests submitted at once (saturation throughput), (2) a seeded
+    Poisson stream at 0.8 x that rate (p50 / p99 latency from submission to result),
+    (3) the plain FP64 form one request at a time (complex128 operator, FP64 GMRES,
+    no refinement).  Requests run on the solve server's workers (own context and
+    stream each, admission by device footprint); every latency includes the array's
+    set-up."""
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.arrays import build_types
+    base = wl.loop_array(2, 2, outers=SERVE_OUTERS, config_index=2)
+    meshes, types = build_types(ctx, base)
+    reqs = serving_requests(n_req, min_side, max_side)
+    total_rhs = sum(r["nrhs"] for r in reqs)
+
+    def submit(sv, r, **kw):
+        return mm.mm_server_submit(sv, [types[t] for t in r["type_of"]], r["offsets"], r["theta"], r["phi"],
+                                   r["pol"], r["tol"], **kw)
+
+    def collect(sv, tickets):
+        out = []
+        for t, r in zip(tickets, reqs):
+            res, _ = mm.mm_server_poll(sv, t, wait=True, nrhs=r["nrhs"], want_solution=False)
+            mm.mm_server_release(sv, t)
+            out.append(res)
+        return out
+
+    # (1) burst: saturation throughput
+    sv = mm.mm_server_create(0, workers=workers)
+    t0 = time.perf_counter()
+    tickets = [submit(sv, r) for r in reqs]
+    burst = collect(sv, tickets)
+    t_burst = time.perf_counter() - t0
+    mm.mm_server_destroy(sv)
+    sat = n_req / t_burst
+    # (2) Poisson arrivals at 0.8 x the saturation rate
+    rate = 0.8 * sat
+    gaps = wl.rng(4, 6).exponential(1.0 / rate, size=n_req)
+    sv = mm.mm_server_create(0, workers=workers)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, at in zip(reqs, np.cumsum(gaps) - gaps[0]):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(submit(sv, r))
+    stream = collect(sv, tickets)
+    t_stream = time.perf_counter() - t0
+    mm.mm_server_destroy(sv)
+    lat = np.array([x["latency_s"] for x in stream]) * 1e3
+    # (3) plain FP64 form, one request at a time
+    sv = mm.mm_server_create(0, workers=1)
+    t0 = time.perf_counter()
+    fp64 = []
+    for r in reqs:
+        t = submit(sv, r, precision=mm.MM_C128, refine=0)
+        res, _ = mm.mm_server_poll(sv, t, wait=True, nrhs=r["nrhs"], want_solution=False)
+        mm.mm_server_release(sv, t)
+        fp64.append(res)
+    t_fp64 = time.perf_counter() - t0
+    mm.mm_server_destroy(sv)
+    for t in types:
+        mm.mm_type_destroy(t)
+    for m in meshes:
+        mm.mm_mesh_destroy(m)
+    ok = all(x["status"] == 0 and x["converged"] for x in burst + stream + fp64)
+    return {
+        "workload": "%d requests, square arrays of side %d..%d, 1-4 loop types, %d plane-wave solves in all, "
+                    "tol 1e-3/1e-4" % (n_req, min_side, max_side, total_rhs),
+        "workers": workers,
+        "all_converged": ok,
+        "failures": [x["message"] for x in burst + stream + fp64 if not (x["status"] == 0 and x["converged"])][:4],
+        "saturation": {"requests_per_s": round(sat, 3), "solves_per_s": round(total_rhs / t_burst, 2)},
+        "poisson": {"rate_requests_per_s": round(rate, 3), "requests_per_s": round(n_req / t_stream, 3),
+                    "solves_per_s": round(total_rhs / t_stream, 2),
+                    "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
+                                   "p99": round(float(np.percentile(lat, 99)), 1)},
+                    "queue_ms_mean": round(1e3 * float(np.mean([x["queue_s"] for x in stream])), 1),
+                    "setup_ms_mean": round(1e3 * float(np.mean([x["setup_s"] for x in stream])), 1)},
+        "fp64_one_at_a_time": {"requests_per_s": round(n_req / t_fp64, 3), "solves_per_s": round(total_rhs / t_fp64, 2)},
+        "speedup_vs_fp64_one_at_a_time": round(t_fp64 / t_stream, 2),
+    }
+
+
 def run_gemm_shape(args):
     import torch  # noqa: F401
     import paper_1712_02443_gb300 as mm
@@ -452,6 +562,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--gemm", action="store_true", help="time the tensor-core macromodel GEMM at the 64x64 shape")
     ap.add_argument("--no-tensor-gemm", action="store_true", help="skip the tensor-core GEMM line of the report")
+    ap.add_argument("--serve-requests", type=int, default=12, help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--serve-min-side", type=int, default=8)
+    ap.add_argument("--serve-max-side", type=int, default=24)
     ap.add_argument("--gemm-side", type=int, default=64)
     ap.add_argument("--gemm-nrhs", type=int, default=8)
     args = ap.parse_args()

@@ -321,6 +321,7 @@ typedef struct mm_result {
   int64_t n_unknowns;
   mm_solve_stats stats;
   double queue_s, setup_s, solve_s, latency_s;   /* wall times, seconds       */
+  char message[160];             /* failure message ("" when status is MM_OK)  */
 } mm_result;
 mm_status mm_server_create(int device, int32_t workers, size_t hbm_budget_bytes, mm_server** out);
 mm_status mm_server_submit(mm_server* server, const mm_request* request, uint64_t* ticket);

@@ -67,7 +67,7 @@ class mm_request(ct.Structure):
 class mm_result(ct.Structure):
     _fields_ = [("done", ct.c_int32), ("status", ct.c_int32), ("n_unknowns", ct.c_int64),
                 ("stats", mm_solve_stats), ("queue_s", ct.c_double), ("setup_s", ct.c_double),
-                ("solve_s", ct.c_double), ("latency_s", ct.c_double)]
+                ("solve_s", ct.c_double), ("latency_s", ct.c_double), ("message", ct.c_char * 160)]
 
 
 P = ct.c_void_p
@@ -379,7 +379,8 @@ def mm_server_poll(server, ticket: int, wait: bool = True, nrhs: int = 1, want_s
         E = buf.view(np.complex128).reshape(r.n_unknowns, nrhs)
     res = {"done": True, "status": r.status, "n_unknowns": r.n_unknowns, "iterations": r.stats.iterations,
            "matvecs": r.stats.matvecs, "converged": bool(r.stats.converged), "rel_residual": r.stats.rel_residual,
-           "queue_s": r.queue_s, "setup_s": r.setup_s, "solve_s": r.solve_s, "latency_s": r.latency_s}
+           "queue_s": r.queue_s, "setup_s": r.setup_s, "solve_s": r.solve_s, "latency_s": r.latency_s,
+           "message": r.message.decode(errors="replace")}
     return res, E
 
 

@@ -394,7 +394,9 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
         }
     std::sort(nbr[e].begin(), nbr[e].end());
   }
-  // fill each distinct block: exact Galerkin entries minus the grid part, near pairs only
+  // fill each distinct block: exact Galerkin entries minus the grid part, near
+  // pairs only; a block computed by an earlier array with the same types and
+  // AIM options is taken from the row type's cache
   for (size_t id = 0; id < blocks.size(); ++id) {
     auto key = block_keys[id];
     const TypeModel* ta = types[key[0]];
@@ -403,6 +405,17 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
     int64_t Na = ta->Nh, Nb = tb->Nh;
     int64_t dL[3] = {key[2], key[3], key[4]};
     Block& blk = blocks[id];
+    NearBlockKey ck{tb, {dL[0], dL[1], dL[2]}, o.h, {o.phase.x, o.phase.y, o.phase.z}, o.order, o.n_nf};
+    {
+      std::lock_guard<std::mutex> lk(ta->nf_mu);
+      auto it = ta->nf_cache.find(ck);
+      if (it != ta->nf_cache.end()) {
+        blk.ptr = it->second->ptr;
+        blk.col = it->second->col;
+        blk.val = it->second->val;
+        continue;
+      }
+    }
     blk.ptr.assign(Na + 1, 0);
     std::vector<std::vector<int32_t>> cols(Na);
     bool any = false;
@@ -416,7 +429,12 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
           any = true;
         }
       }
-    if (!any) continue;
+    if (!any) {   // no near pairs: remembered as an empty block
+      blk.ptr.clear();
+      std::lock_guard<std::mutex> lk(ta->nf_mu);
+      ta->nf_cache.emplace(ck, std::make_shared<NearBlockData>());
+      continue;
+    }
     std::vector<cd> G;
     fill_efie(ta->eq, tb->eq, block_rel[id], em, G);
     for (auto& x : G) x *= ah.c_A;   // G^(E^,J^) = -j w mu0 Lmat
@@ -447,6 +465,12 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
         }
       }
     });
+    auto d = std::make_shared<NearBlockData>();
+    d->ptr = blk.ptr;
+    d->col = blk.col;
+    d->val = blk.val;
+    std::lock_guard<std::mutex> lk(ta->nf_mu);
+    ta->nf_cache.emplace(ck, std::move(d));
   }
   ah.nnz_near = 0;
   for (int64_t e = 0; e < ne; ++e)

@@ -5,6 +5,9 @@
 #include <cstdint>
 #include <functional>
 #include <string>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "macroaim.h"
@@ -109,6 +112,32 @@ void lu_factor(LU& lu, std::vector<cd> a, int64_t n);
 // Solves A X = B in place for B (n x ncols, row-major).
 void lu_solve(const LU& lu, std::vector<cd>& b, int64_t ncols, int nthreads);
 
+// A near-field block of a row type against a column type at one lattice
+// offset (sparse rows, local columns): exact Galerkin entries minus the grid
+// part over the near pairs.
+struct NearBlockData {
+  std::vector<int64_t> ptr;   // rows + 1 (empty: no near pairs)
+  std::vector<int32_t> col;
+  std::vector<cd> val;
+};
+// Key of a cached block: column type, lattice offset, AIM options.
+struct NearBlockKey {
+  const void* col_type;
+  int64_t dL[3];
+  double h, phase[3];
+  int order, n_nf;
+  bool operator<(const NearBlockKey& o) const {
+    if (col_type != o.col_type) return col_type < o.col_type;
+    for (int a = 0; a < 3; ++a)
+      if (dL[a] != o.dL[a]) return dL[a] < o.dL[a];
+    if (h != o.h) return h < o.h;
+    for (int a = 0; a < 3; ++a)
+      if (phase[a] != o.phase[a]) return phase[a] < o.phase[a];
+    if (order != o.order) return order < o.order;
+    return n_nf < o.n_nf;
+  }
+};
+
 struct TypeModel {
   Mesh scat, eq;
   DualSet duals;
@@ -116,6 +145,11 @@ struct TypeModel {
   int64_t N = 0, Nh = 0;
   std::vector<cd> M, D, T, A, B, GHH, GHE;   // row-major
   std::vector<cd> JE;                         // -A^-1 B (N x N^): scatterer currents from E^, eq. (JABE)
+  // near-field blocks with this type as the row type, computed by earlier
+  // arrays (identical for every array with the same AIM options): arrays built
+  // from the same types, on any thread, reuse them
+  mutable std::mutex nf_mu;
+  mutable std::map<NearBlockKey, std::shared_ptr<const NearBlockData>> nf_cache;
 };
 void build_type(TypeModel& tm);
 

@@ -9,7 +9,9 @@
 // arrives while others run starts as soon as a worker and memory are free.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <complex>
 #include <condition_variable>
 #include <deque>
@@ -195,11 +197,12 @@ mm_status mm_server_submit(mm_server* sv, const mm_request* q, uint64_t* ticket)
   r->ph.assign(q->phi, q->phi + q->nrhs);
   r->pol.assign(q->pol, q->pol + q->nrhs);
   r->opts = q->solve;
-  // footprint estimate: near field (~650 entries per row in both precisions),
-  // Krylov basis and work vectors, grids
-  const size_t nnz = (size_t)nh * 650;
-  r->est = nnz * (12 + 20) + (size_t)nh * q->nrhs * 16 * (q->solve.restart + 8) + (size_t)nh * q->nrhs * 256 +
-           (size_t)ns * 64;
+  // footprint estimate: Krylov basis and work vectors, grids, the near-field
+  // blocks and, when the array assembles it (moderate sizes), the near-field
+  // CSR (~650 entries per row, values of both precisions and columns)
+  const size_t csr = std::min<size_t>((size_t)nh * 650 * 28, (size_t)8 << 30);
+  r->est = csr + (size_t)nh * q->nrhs * 16 * (q->solve.restart + 8) + (size_t)nh * q->nrhs * 256 + (size_t)ns * 64 +
+           ((size_t)64 << 20);
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -229,6 +232,7 @@ mm_status mm_server_poll(mm_server* sv, uint64_t ticket, int32_t wait, mm_result
   res->setup_s = r->t_setup - r->t_start;
   res->solve_s = r->t_end - r->t_setup;
   res->latency_s = r->t_end - r->t_submit;
+  std::snprintf(res->message, sizeof(res->message), "%s", r->err.c_str());
   if (E_host) {
     if (E_count < 2 * r->n * r->nrhs) return MM_EINVAL;
     std::copy(r->E.begin(), r->E.end(), E_host);

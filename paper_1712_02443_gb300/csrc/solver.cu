@@ -816,12 +816,16 @@ Status Solver::ensure(int64_t N, int r, int m) {
     // hs, h2s: (m+1) r each; ws: max((m+1) warps, block threads); need flags
     coop_smem_ = sizeof(Z) * ((size_t)(m + 1) * 2 * r + std::max<size_t>((size_t)(m + 1) * 8, 4 * 256)) +
                  sizeof(int) * (size_t)r + 16;
-    coop_ok_ = coop_smem_ <= 200 * 1024;
+    constexpr int kCoopSmemMax = 200 * 1024;
+    coop_ok_ = coop_smem_ <= (size_t)kCoopSmemMax;
     if (coop_ok_) {
+      // The attribute is per kernel and process-wide: it is set to the one fixed
+      // ceiling (never to this solver's size), so that solvers of other sizes on
+      // other threads cannot lower it under a launch of this one.
       MM_CK(cudaFuncSetAttribute(k_arnoldi_step<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)coop_smem_));
+                                 kCoopSmemMax));
       MM_CK(cudaFuncSetAttribute(k_arnoldi_step<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)coop_smem_));
+                                 kCoopSmemMax));
       int p1 = 0, p2 = 0;
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_arnoldi_step<float2, float2>, 256, coop_smem_));
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_arnoldi_step<double2, double2>, 256, coop_smem_));

