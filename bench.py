@@ -298,6 +298,8 @@ def run_ours(args, rank, world, local):
     mm.mm_array_destroy(la.array)
     if rank == 0 and not args.no_tensor_gemm:
         out["tensor_gemm"] = tensor_gemm_measure(ctx, 64, 8, 10, 3)
+    if rank == 0 and not args.no_batched:
+        out["batched"] = batched_measure(ctx)
     if rank == 0 and args.serve_requests > 0:
         out["serving"] = serving_measure(ctx, args.serve_requests, args.serve_min_side, args.serve_max_side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -540,6 +542,49 @@ def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int 
     }
 
 
+def batched_measure(ctx, side: int = 32) -> dict:
+    """Batching: side x side array of the four loop types (drawn per cell), the 64
+    plane waves of the 8 x 8 (theta, phi) grid solved together (one product per
+    GMRES iteration for all 64 columns), GMRES to 1e-4 with FP64 refinement.  One
+    batch per macromodel precision (FP32 CUDA cores; FP16 tensor cores), timed with
+    CUDA events; L2 flushed first."""
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.arrays import loop_array
+    t0 = time.time()
+    la = loop_array(ctx, side, side, outers=SERVE_OUTERS, config_index=2)
+    setup_s = time.time() - t0
+    st = torch.cuda.current_stream()
+    th, ph, pol = wl.planewave_grid()
+    V = torch.empty(la.n * 64, dtype=torch.complex128, device="cuda")
+    E = torch.empty_like(V)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": "%dx%d array, 4 loop types, 64 plane waves (8 x 8 theta, phi grid), tol 1e-4" % (side, side),
+           "unknowns": la.n, "nnz_near": la.info["nnz_near"], "setup_s": round(setup_s, 2)}
+    for name, prec, inner in (("fp32_gemm", mm.MM_C64, 1e-5), ("fp16_tensor_gemm", mm.MM_C64_F16, 1e-3)):
+        flush.fill_(1)
+        mm.mm_profile_enable(la.array, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
+        s = mm.mm_solve(la.array, 64, V, E, tol=1e-4, restart=50, max_iter=3000, precision=prec, refine=1,
+                        inner_tol=inner, stream=st, check=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        pr = mm.mm_profile_read(la.array, mm.MM_C64)
+        mm.mm_profile_enable(la.array, False)
+        t = e0.elapsed_time(e1) / 1e3
+        it = max(1, s["iterations"])
+        out[name] = {"s_per_batch": round(t, 3), "solves_per_s": round(64 / t, 2), "converged": s["converged"],
+                     "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
+                     "refinements": s["refinements"],
+                     "ms_per_iteration": {k: round(v["ms"] / it, 3) for k, v in pr.items() if v["launches"]}}
+    del flush
+    la.close()
+    return out
+
+
 def run_gemm_shape(args):
     import torch  # noqa: F401
     import paper_1712_02443_gb300 as mm
@@ -562,6 +607,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--gemm", action="store_true", help="time the tensor-core macromodel GEMM at the 64x64 shape")
     ap.add_argument("--no-tensor-gemm", action="store_true", help="skip the tensor-core GEMM line of the report")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-plane-wave batched solve")
     ap.add_argument("--serve-requests", type=int, default=12, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-min-side", type=int, default=8)
     ap.add_argument("--serve-max-side", type=int, default=24)

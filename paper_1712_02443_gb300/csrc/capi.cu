@@ -57,6 +57,9 @@ struct mm_array {
   std::vector<int64_t> offs;      // host: scatterer unknown offsets (n_elem + 1)
   double* d_dir = nullptr;        // device: theta, phi of the far-field directions
   int64_t dir_cap = 0;
+  // host: per type, the near-field block ordering of its bases (sorted position ->
+  // basis) and its inverse
+  std::vector<std::vector<int32_t>> nf_perm, nf_iperm;
   ~mm_array();
 };
 
@@ -144,9 +147,10 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
     int64_t o = 0;
     for (const auto& b : ah.nf_blocks) {
       if (b.ptr.empty()) continue;
+      const auto &ia = a->nf_iperm[b.ta], &ib = a->nf_iperm[b.tb];   // original -> sorted position
       for (int64_t m = 0; m < b.Na; ++m)
         for (int64_t q = b.ptr[m]; q < b.ptr[m + 1]; ++q) {
-          C& z = d[(size_t)(o + m * b.Nb + b.col[q])];
+          C& z = d[(size_t)(o + (int64_t)ia[m] * b.Nb + ib[b.col[q]])];
           z.x = (R)b.val[q].real();
           z.y = (R)b.val[q].imag();
         }
@@ -315,7 +319,8 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : d_JE) cudaFree(q);
   for (void* q : d_T) cudaFree(q);
-  for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist})
+  for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist,
+                  (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
   for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
     if (q) cudaFree(q);
@@ -583,6 +588,29 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
       // 64-row tile, and the element pairs of each lattice offset
       const auto& nb = ah.nf_blocks;
       const int64_t nbk = (int64_t)nb.size();
+      // per type: bases sorted by anchor (y, then x, then z), so that the near
+      // pairs of a block gather into fewer 64 x 16 tiles
+      a->nf_perm.assign(da.n_types, {});
+      a->nf_iperm.assign(da.n_types, {});
+      std::vector<int32_t> perm_all, perm_off(da.n_types, 0);
+      for (int64_t t = 0; t < da.n_types; ++t) {
+        const auto& ta = ah.tai[t];
+        std::vector<int32_t> pm(ta.Nh);
+        for (int64_t i = 0; i < ta.Nh; ++i) pm[i] = (int32_t)i;
+        std::stable_sort(pm.begin(), pm.end(), [&](int32_t x, int32_t y) {
+          const int64_t* ax = &ta.anc[3 * x];
+          const int64_t* ay = &ta.anc[3 * y];
+          if (ax[1] != ay[1]) return ax[1] < ay[1];
+          if (ax[0] != ay[0]) return ax[0] < ay[0];
+          return ax[2] < ay[2];
+        });
+        std::vector<int32_t> ip(ta.Nh);
+        for (int64_t i = 0; i < ta.Nh; ++i) ip[pm[i]] = (int32_t)i;
+        perm_off[t] = (int32_t)perm_all.size();
+        perm_all.insert(perm_all.end(), pm.begin(), pm.end());
+        a->nf_perm[t] = std::move(pm);
+        a->nf_iperm[t] = std::move(ip);
+      }
       int64_t maxNa = 0;
       for (const auto& b : nb)
         if (!b.ptr.empty()) maxNa = std::max(maxNa, b.Na);
@@ -600,8 +628,9 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
           tptr[q * nmt + mt] = (int32_t)tl.size();
           if (b.ptr.empty() || (int64_t)mt * 64 >= b.Na) continue;
           used.assign((size_t)((b.Nb + 15) / 16), 0);
+          const auto &pa = a->nf_perm[b.ta], &ib = a->nf_iperm[b.tb];
           for (int64_t m = (int64_t)mt * 64; m < std::min<int64_t>(b.Na, (int64_t)mt * 64 + 64); ++m)
-            for (int64_t e = b.ptr[m]; e < b.ptr[m + 1]; ++e) used[b.col[e] / 16] = 1;
+            for (int64_t e = b.ptr[pa[m]]; e < b.ptr[pa[m] + 1]; ++e) used[ib[b.col[e]] / 16] = 1;
           for (size_t kt = 0; kt < used.size(); ++kt)
             if (used[kt]) tl.push_back((int32_t)kt);
         }
@@ -616,6 +645,14 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         da.nfb_off = dev_upload(boff.data(), boff.size(), acc);
         da.nfb_tptr = dev_upload(tptr.data(), tptr.size(), acc);
         da.nfb_tlist = dev_upload(tl.data(), tl.size(), acc);
+        std::vector<int32_t> bpa(nbk, 0), bpb(nbk, 0);
+        for (int64_t q = 0; q < nbk; ++q) {
+          bpa[q] = perm_off[nb[q].ta];
+          bpb[q] = perm_off[nb[q].tb];
+        }
+        da.nfb_perm = dev_upload(perm_all.data(), perm_all.size(), acc);
+        da.nfb_pa = dev_upload(bpa.data(), bpa.size(), acc);
+        da.nfb_pb = dev_upload(bpb.data(), bpb.size(), acc);
         std::vector<std::vector<int2>> groups(nbk);
         for (int64_t e = 0; e < n_elem; ++e)
           for (const auto& pr : ah.nf_nbr[e])

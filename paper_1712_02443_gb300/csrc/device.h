@@ -133,6 +133,9 @@ struct DevArray {
   int64_t* nfb_off = nullptr;           // per block: first entry in the dense values
   int32_t* nfb_tptr = nullptr;          // blocks x nfb_nmt + 1
   int32_t* nfb_tlist = nullptr;         // k-tile indices
+  int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
+  int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm
+  int32_t* nfb_pb = nullptr;            // per block: offset of its column type's ordering
   int64_t nfb_entries = 0;              // dense complex entries over all blocks
   struct NfGroup {                      // the element pairs coupled by one block (host mirror)
     int q = 0;                          // block id

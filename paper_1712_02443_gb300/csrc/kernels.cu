@@ -623,8 +623,10 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
 // y_a -= B_q u_b over all element pairs (a, b) and their distinct near-field
 // blocks q, in one launch.  B_q is dense (rows of a's type, columns of b's);
 // only its 16-column k tiles that hold a non-zero in the CTA's 64-row tile are
-// visited.  The GEMM's columns are (pair, right-hand side), n = p nrhs + c, so
-// one right-hand side still fills the tiles.  Tiles are numbered group by
+// visited; each type's bases are stored in anchor order (perm: sorted position
+// -> basis), which gathers the near pairs into fewer tiles.  The GEMM's
+// columns are (pair, right-hand side), n = p nrhs + c, so one right-hand side
+// still fills the tiles.  Tiles are numbered group by
 // group (group = the pairs of one block: row tiles x column tiles); a CTA
 // finds its group by a prefix over the group sizes.  A row element has up to
 // one pair per lattice offset, so its outputs receive several block products:
@@ -638,8 +640,9 @@ template <typename R, int TN>
 __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
     const NearGroupDev* __restrict__ groups, int ngroups, const int2* __restrict__ pairs,
     const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
-    int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int64_t* __restrict__ off,
-    int nrhs, int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
+    int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ bpa, const int32_t* __restrict__ bpb, const int64_t* __restrict__ off, int nrhs,
+    int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
   typedef typename V2<R>::T C;
   constexpr int TM = 64, TK = 16, TX = TN / 4, NT = 16 * TX;
   __shared__ C As[TK][TM + 1];
@@ -671,6 +674,8 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
   const int m0 = mt * TM;
   const int64_t ncol = gr.npairs * nrhs, n0 = s_ct * TN;
   const C* Bq = vals + boff[q];
+  const int32_t* pa = perm + bpa[q];   // the block's rows and columns are in anchor order
+  const int32_t* pb = perm + bpb[q];
   for (int cc = tid; cc < TN; cc += NT) {
     const int64_t n = n0 + cc;
     if (n < ncol) {
@@ -709,7 +714,7 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
       const int idx = tid + r * NT;
       const int kk = kfast ? idx % TK : idx / TN, cc = kfast ? idx / TK : idx % TN;
       const int64_t ci = cin[cc];
-      rb[r] = (ci >= 0 && k0 + kk < Nb) ? u[ci + (int64_t)(k0 + kk) * nrhs] : czero<C>();
+      rb[r] = (ci >= 0 && k0 + kk < Nb) ? u[ci + (int64_t)pb[k0 + kk] * nrhs] : czero<C>();
     }
   };
   if (e0 < e1) fetch(e0);
@@ -752,7 +757,7 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
     for (int i = 0; i < 4; ++i) {
       const int m = m0 + ty * 4 + i;
       if (m < Na) {
-        R* dst = reinterpret_cast<R*>(y + co + (int64_t)m * nrhs);
+        R* dst = reinterpret_cast<R*>(y + co + (int64_t)pa[m] * nrhs);
         atomicAdd(dst, -acc[i][j].x);
         atomicAdd(dst + 1, -acc[i][j].y);
       }
@@ -772,7 +777,7 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
   k_near_blocks<R, TN><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
       reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_pairs,
       static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, a.nfb_nmt, a.nfb_tptr, a.nfb_tlist,
-      a.off, nrhs, ksplit, u, y);
+      a.nfb_perm, a.nfb_pa, a.nfb_pb, a.off, nrhs, ksplit, u, y);
   ++nl;
 }
 
