@@ -511,10 +511,67 @@ __device__ __forceinline__ DAcc shfl_x(DAcc a, int o) {
 // j < r, in a fixed thread order (the same result on every run).  When r
 // divides 32 the lanes of one column are folded by shuffles first.  red holds
 // NQ blockDim values.
+// Warp sums of eight values at once: at each butterfly level a lane keeps half
+// of its values (the half chosen by its lane bit) and adds the partner's copy of
+// that half, so the eight sums take 4 + 2 + 1 + 1 + 1 shuffle-adds instead of
+// 8 x 5.  Afterwards lane 4 v (v < 8) holds the warp sum of value v.
+__device__ __forceinline__ double warp_sum8(double (&v)[8]) {
+  const int lane = threadIdx.x % 32;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {   // offset 16: keep values 0-3 (bit clear) or 4-7
+    const bool hi = lane & 16;
+    const double send = hi ? v[q] : v[q + 4];
+    const double got = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[q] = (hi ? v[q + 4] : v[q]) + got;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {   // offset 8: keep 0-1 or 2-3 of those
+    const bool hi = lane & 8;
+    const double send = hi ? v[q] : v[q + 2];
+    const double got = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[q] = (hi ? v[q + 2] : v[q]) + got;
+  }
+  {   // offset 4: keep 0 or 1
+    const bool hi = lane & 4;
+    const double send = hi ? v[0] : v[1];
+    const double got = __shfl_xor_sync(0xffffffffu, send, 4);
+    v[0] = (hi ? v[1] : v[0]) + got;
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
 template <int NQ, typename T, typename F>
 __device__ __forceinline__ void column_reduce(const T (&a)[NQ], int r, T* red, F out) {
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32, nw = blockDim.x / 32, B = blockDim.x;
   const int S = (B / r) * r;
+  if constexpr (NQ == 4 && sizeof(T) == 16) {
+    if (r == 1) {   // one column: the eight real values of the four sums in one warp pass
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[2 * q] = a[q].x;
+        v[2 * q + 1] = a[q].y;
+      }
+      const double sum = warp_sum8(v);
+      double* rd = reinterpret_cast<double*>(red);
+      if ((lane & 3) == 0) rd[(lane >> 2) * nw + warp] = sum;   // value index lane / 4
+      __syncthreads();
+      if (tid < NQ) {
+        T s;
+        s.x = 0;
+        s.y = 0;
+        for (int w = 0; w < nw; ++w) {
+          s.x += rd[(2 * tid) * nw + w];
+          s.y += rd[(2 * tid + 1) * nw + w];
+        }
+        out(tid, 0, s);
+      }
+      __syncthreads();
+      return;
+    }
+  }
   if (r <= 32 && (32 % r) == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -829,7 +886,9 @@ Status Solver::ensure(int64_t N, int r, int m) {
       int p1 = 0, p2 = 0;
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_arnoldi_step<float2, float2>, 256, coop_smem_));
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_arnoldi_step<double2, double2>, 256, coop_smem_));
-      per = std::min(std::min(p1, p2), 2);
+      // one CTA per SM: the rows per thread double, which halves the share of
+      // the FP64 reductions in the step
+      per = std::min(std::min(p1, p2), 1);
       coop_ok_ = per >= 1;
     }
     int64_t want = coop_ok_ ? (int64_t)sms * per : 128;
