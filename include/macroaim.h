@@ -109,7 +109,9 @@ typedef enum mm_type_matrix_id {
   MM_MAT_A = 3,     /* eq. (JM)           (N x N)    */
   MM_MAT_B = 4,     /* eq. (JM)           (N x N^)   */
   MM_MAT_GHH = 5,   /* G^(E^,H^)          (N^ x N^)  */
-  MM_MAT_GHE = 6    /* G^(E^,E^)          (N^ x N^)  */
+  MM_MAT_GHE = 6,   /* G^(E^,E^)          (N^ x N^)  */
+  MM_MAT_PJ = 7     /* (D - G^(E^,H^) M)^-1 (N^ x N^): inverse of the element's
+                       own block of the array system (block-Jacobi)          */
 } mm_type_matrix_id;
 /* Copies matrix `which` (row-major, complex128 interleaved) into out_host
  * (may be NULL to query the shape).  rows/cols receive its shape.            */
@@ -251,6 +253,11 @@ typedef struct mm_solve_opts {
                          residual corrects; selective second pass otherwise;
                          1 = one pass; 2 = second pass only for columns whose
                          norm fell below 1/sqrt(2); 3 = two passes always      */
+  int32_t precond;    /* 0 = none; 1 = block-Jacobi: right preconditioning by
+                         the inverse of every element's own block (MM_MAT_PJ),
+                         shared by identical elements.  The solution is the
+                         same; GMRES needs fewer iterations.  Not a method of
+                         the paper (which names ILU), a library option.         */
 } mm_solve_opts;
 typedef struct mm_solve_stats {
   int32_t iterations;     /* inner GMRES iterations (max over columns)        */

@@ -21,7 +21,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENOCONV, MM_EBREAKDOWN, MM_ETIMEOUT, M
 STATUS_NAMES = ["MM_OK", "MM_EINVAL", "MM_ENOMEM", "MM_ECUDA", "MM_ENOCONV", "MM_EBREAKDOWN", "MM_ETIMEOUT",
                 "MM_EBUSY", "MM_EINTERNAL"]
 MM_C64, MM_C128, MM_C64_BF16, MM_C64_F16 = 0, 1, 2, 3
-MM_MAT_M, MM_MAT_D, MM_MAT_T, MM_MAT_A, MM_MAT_B, MM_MAT_GHH, MM_MAT_GHE = range(7)
+MM_MAT_M, MM_MAT_D, MM_MAT_T, MM_MAT_A, MM_MAT_B, MM_MAT_GHH, MM_MAT_GHE, MM_MAT_PJ = range(8)
 STAGES = ["gemm", "project", "fft_fwd", "fft_conv", "fft_inv", "interp", "near", "krylov"]
 MM_EXPORT_ANCHORS, MM_EXPORT_PI, MM_EXPORT_NEAR_PTR, MM_EXPORT_NEAR_COL, MM_EXPORT_NEAR_VAL, MM_EXPORT_GHAT = range(6)
 
@@ -50,7 +50,7 @@ class mm_array_info(ct.Structure):
 
 class mm_solve_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
-                ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32)]
+                ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32), ("precond", ct.c_int32)]
 
 
 class mm_solve_stats(ct.Structure):
@@ -318,8 +318,8 @@ def mm_rcs(array, nrhs: int, Jhat_dev, theta, phi) -> np.ndarray:
 
 def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_iter: int = 1000,
              precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2, stream=None, check: bool = True,
-             orth: int = 0):
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth)
+             orth: int = 0, precond: int = 0):
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond)
     s = mm_solve_stats()
     st = load().mm_solve(array, nrhs, _ptr(V_dev), _ptr(E_dev), ct.byref(o), ct.byref(s), _stream(stream))
     stats = {"iterations": s.iterations, "matvecs": s.matvecs, "refinements": s.refinements,
@@ -349,7 +349,7 @@ def mm_server_create(device: int = 0, workers: int = 2, hbm_budget_bytes: int = 
 
 def mm_server_submit(server, types, offsets, theta, phi, pol, tol: float, h: float = 0.1, order: int = 2,
                      n_nf: int = 3, phase=(0.0137, 0.0291, 0.0913), restart: int = 50, max_iter: int = 2000,
-                     precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-5) -> int:
+                     precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-5, precond: int = 0) -> int:
     """Submits one request; its inputs are copied before this returns."""
     offsets = np.ascontiguousarray(offsets, dtype=np.float64).reshape(-1, 3)
     th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
@@ -359,7 +359,7 @@ def mm_server_submit(server, types, offsets, theta, phi, pol, tol: float, h: flo
     q = mm_request(len(types), ct.cast(arr, ct.POINTER(ct.c_void_p)), offsets.ctypes.data_as(ct.c_void_p),
                    mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase)), len(th), th.ctypes.data_as(ct.c_void_p),
                    ph.ctypes.data_as(ct.c_void_p), po.ctypes.data_as(ct.c_void_p),
-                   mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol))
+                   mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, 0, precond))
     t = ct.c_uint64()
     _check(load().mm_server_submit(server, ct.byref(q), ct.byref(t)), None)
     return t.value

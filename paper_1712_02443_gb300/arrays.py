@@ -55,3 +55,16 @@ def loop_array(ctx, nx: int, ny: int, outers=(0.4,), config_index: int = 0, h: f
     la = LibArray(ctx, arr, layout, list(types), meshes)
     la.info = b.mm_array_info_get(arr)
     return la
+
+
+def multiscale_array(ctx, nx: int, ny: int, meander=None, box_div=(8, 8, 2), h: float = H, order: int = ORDER,
+                     n_nf: int = N_NF, phase=wl.DEFAULT_GRID_PHASE, types=None, near_csr: int = 0) -> LibArray:
+    """nx x ny array of the multiscale element (loop with a meandered inner trace)."""
+    layout = wl.multiscale_array(nx, ny, meander=meander, box_div=box_div)
+    meshes = []
+    if types is None:
+        meshes, types = build_types(ctx, layout)
+    arr = b.mm_array_create(ctx, [types[0]] * layout.n_elem, layout.offsets, h, order, n_nf, phase, near_csr)
+    la = LibArray(ctx, arr, layout, list(types), meshes)
+    la.info = b.mm_array_info_get(arr)
+    return la

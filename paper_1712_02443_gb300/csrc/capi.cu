@@ -226,6 +226,28 @@ void upload_tc(mm_array* a, int mode) {
   }
 }
 
+// Block-Jacobi operators per type (inverse self blocks), uploaded on first use.
+template <typename R>
+void upload_pj(mm_array* a, mm::DevPrec<R>& p) {
+  if (!p.PJ.empty()) return;
+  typedef typename mm::V2<R>::T C;
+  for (int64_t t = 0; t < a->da.n_types; ++t) {
+    const auto& tm = a->types[t]->tm;
+    std::vector<C> W(tm.PJ.size());
+    for (size_t i = 0; i < W.size(); ++i) {
+      W[i].x = (R)tm.PJ[i].real();
+      W[i].y = (R)tm.PJ[i].imag();
+    }
+    p.PJ.push_back(dev_upload(W.data(), W.size(), a->da.bytes));
+  }
+}
+
+template <typename R>
+void ensure_pt(mm_array* a, mm::Work& w, int nrhs) {
+  if (w.pt) return;
+  CU(cudaMalloc(&w.pt, sizeof(typename mm::V2<R>::T) * (size_t)a->da.N * nrhs));
+}
+
 void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
   auto& da = a->da;
   size_t need = 0;
@@ -267,7 +289,7 @@ template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
-  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -289,8 +311,10 @@ void free_prec_f(mm::DevPrec<float>& p) {
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
+  for (void* q : p.PJ) cudaFree(q);
 }
 void free_prec_d(mm::DevPrec<double>& p) {
+  for (void* q : p.PJ) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
@@ -306,7 +330,7 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
@@ -421,6 +445,7 @@ mm_status mm_type_matrix(const mm_type* type, int32_t which, double* out_host, i
     case MM_MAT_B: M = &tm.B; r = tm.N; c = tm.Nh; break;
     case MM_MAT_GHH: M = &tm.GHH; r = tm.Nh; c = tm.Nh; break;
     case MM_MAT_GHE: M = &tm.GHE; r = tm.Nh; c = tm.Nh; break;
+    case MM_MAT_PJ: M = &tm.PJ; r = tm.Nh; c = tm.Nh; break;
     default: return MM_EINVAL;
   }
   if (rows) *rows = r;
@@ -892,6 +917,7 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (!(opts->tol > 0) || opts->restart < 1 || opts->max_iter < 1) return fail(ctx, MM_EINVAL, "invalid solve options");
   if (opts->precision < MM_C64 || opts->precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
   if (opts->orth < 0 || opts->orth > 3) return fail(ctx, MM_EINVAL, "orth must be 0, 1, 2 or 3");
+  if (opts->precond < 0 || opts->precond > 1) return fail(ctx, MM_EINVAL, "precond must be 0 or 1");
   if (opts->refine && opts->precision == MM_C128)
     return fail(ctx, MM_EINVAL, "refinement needs a complex64 operator precision");
   API_TRY
@@ -913,13 +939,33 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     ensure_tc_work(a, a->da.wf, nrhs);
   }
   mm_array* arr = a;
-  S.op64 = [arr, nrhs](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
-    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2);
+  const bool pj = opts->precond == 1;
+  if (pj) {
+    // right preconditioning: GMRES runs on Z P^-1 (P = the elements' own blocks)
+    upload_pj<double>(a, a->da.pd);
+    upload_pj<float>(a, a->da.pf);
+    ensure_pt<double>(a, a->da.wd, nrhs);
+    ensure_pt<float>(a, a->da.wf, nrhs);
+  }
+  S.op64 = [arr, nrhs, pj](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
+    const void* x = in;
+    if (pj) {
+      cudaError_t e = mm::precond_apply<double>(arr->da, arr->da.pd, nrhs, in, arr->da.wd.pt, s2);
+      if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
+      x = arr->da.wd.pt;
+    }
+    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, x, out, s2);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
-  S.op32 = [arr, nrhs, mode](const void* in, void* out, cudaStream_t s2) -> mm::Status {
-    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, in, out, s2, mode);
+  S.op32 = [arr, nrhs, mode, pj](const void* in, void* out, cudaStream_t s2) -> mm::Status {
+    const void* x = in;
+    if (pj) {
+      cudaError_t e = mm::precond_apply<float>(arr->da, arr->da.pf, nrhs, in, arr->da.wf.pt, s2);
+      if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
+      x = arr->da.wf.pt;
+    }
+    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, x, out, s2, mode);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
@@ -930,6 +976,11 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
               opts->precision == MM_C128 ? MM_C128 : MM_C64,
               opts->refine, opts->inner_tol > 0 ? opts->inner_tol : 1e-2, opts->max_iter, iters, refs, relres, conv,
               st);
+  if (pj && (s.code == MM_OK || s.code == MM_ENOCONV)) {
+    // the solution of Z P^-1 y = V is y; E = P^-1 y
+    CU(mm::precond_apply<double>(a->da, a->da.pd, nrhs, E_dev, a->da.wd.pt, st));
+    CU(cudaMemcpyAsync(E_dev, a->da.wd.pt, sizeof(double2) * (size_t)a->da.N * nrhs, cudaMemcpyDeviceToDevice, st));
+  }
   if (stats) {
     stats->iterations = iters;
     stats->matvecs = S.matvecs;

@@ -84,6 +84,7 @@ struct DevPrec {
   std::vector<void*> Atc[2];   // [0] BF16, [1] FP16; (Mp x Kp) 16-bit
   std::vector<int> Mp, Kp;
   void* nfb_val = nullptr;     // near-field blocks, dense row-major, at DevArray::nfb_off
+  std::vector<void*> PJ;       // per type: block-Jacobi operator (Nh x Nh), uploaded on first use
 };
 
 // Work buffers for one (precision, nrhs) pair.
@@ -96,6 +97,7 @@ struct Work {
   void* bt = nullptr;     // packed right-hand sides of the tensor-core GEMM
   size_t bt_cap = 0;      // elements
   int* err = nullptr;     // device error flag of bounded waits
+  void* pt = nullptr;     // N x nrhs   preconditioned vector (block-Jacobi)
   size_t bytes = 0;
 };
 
@@ -162,6 +164,9 @@ struct DevArray {
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st,
                    int gemm_mode = 0);
+// y = P^-1 x with P^-1 the per-type block-Jacobi operators (p.PJ).
+template <typename R>
+cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* x, void* y, cudaStream_t st);
 template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which);
 cudaError_t kernels_init(DevArray& a);

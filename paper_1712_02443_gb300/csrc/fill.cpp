@@ -403,6 +403,20 @@ void build_type(TypeModel& tm) {
   gemm(tm.T, Y, tm.M, Nh, N, Nh, em.nthreads);  // M = T A^-1 B
   tm.JE.resize(Y.size());
   for (size_t i = 0; i < Y.size(); ++i) tm.JE[i] = -Y[i];
+  {
+    // block-Jacobi preconditioner: the inverse of the element's own block of the
+    // array system, D - G^(E^,H^) M (eq. (MV_product1) restricted to one element;
+    // G^(E^,H^) is the EFIE operator of the equivalent surface on itself)
+    std::vector<cd> GM;
+    gemm(tm.GHH, tm.M, GM, Nh, Nh, Nh, em.nthreads);
+    std::vector<cd> S(Nh * Nh);
+    for (int64_t i = 0; i < Nh * Nh; ++i) S[i] = tm.D[i] - GM[i];
+    LU ls;
+    lu_factor(ls, S, Nh);
+    tm.PJ.assign(Nh * Nh, cd(0, 0));
+    for (int64_t i = 0; i < Nh; ++i) tm.PJ[i * Nh + i] = cd(1, 0);
+    lu_solve(ls, tm.PJ, Nh, em.nthreads);
+  }
 }
 
 }  // namespace mm

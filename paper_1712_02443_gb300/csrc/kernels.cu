@@ -78,7 +78,7 @@ FftPlan make_plan(int L) {
 // shared memory; the next slice is loaded into registers while the current one
 // is multiplied (the product is latency-bound at these sizes).
 template <typename R, int BM, int BN, int BK>
-__global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __restrict__ W, int Nh,
+__global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __restrict__ W, int Nh, int rows,
                                                     const int32_t* __restrict__ elems, int ncols, int nrhs,
                                                     const int64_t* __restrict__ off,
                                                     const typename V2<R>::T* __restrict__ x,
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
-  const int M2 = 2 * Nh;
+  const int M2 = rows;   // 2 Nh for the stacked [M; D]; Nh for a single operator (u only)
   for (int c = tid; c < BN; c += 256) {
     const int gc = col0 + c;
     colbase[c] = gc < ncols ? off[elems[gc / nrhs]] * nrhs + gc % nrhs : -1;
@@ -856,12 +856,12 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
     if (big >= 2 * 152) {
       dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
-      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs,
-                                                     a.off, x, u, v);
+      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, 2 * Nh, a.elems[t], ncols,
+                                                     nrhs, a.off, x, u, v);
     } else {
       dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
-      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, a.elems[t], ncols, nrhs,
-                                                      a.off, x, u, v);
+      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, 2 * Nh, a.elems[t], ncols,
+                                                      nrhs, a.off, x, u, v);
     }
     ++nl;
   }
@@ -940,6 +940,35 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* xv, void* yv, cudaStream_t st) {
+  typedef typename V2<R>::T C;
+  const C* x = static_cast<const C*>(xv);
+  C* y = static_cast<C*>(yv);
+  a.prof.begin(sizeof(R) == 8 ? 8 : 0, st);   // counted with the macromodel stage
+  int nl = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const int ncols = (int)(a.n_of_type[t] * nrhs);
+    constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
+    if ((int64_t)((Nh + 63) / 64) * ((ncols + 63) / 64) >= 2 * 152) {
+      dim3 g((Nh + 63) / 64, (ncols + 63) / 64);
+      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(static_cast<const C*>(p.PJ[t]), Nh, Nh, a.elems[t], ncols,
+                                                     nrhs, a.off, x, y, nullptr);
+    } else {
+      dim3 g((Nh + 31) / 32, (ncols + 31) / 32);
+      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(static_cast<const C*>(p.PJ[t]), Nh, Nh, a.elems[t], ncols,
+                                                      nrhs, a.off, x, y, nullptr);
+    }
+    ++nl;
+  }
+  a.prof.end(st, nl);
+  return cudaGetLastError();
+}
+
+template cudaError_t precond_apply<float>(DevArray&, DevPrec<float>&, int, const void*, void*, cudaStream_t);
+template cudaError_t precond_apply<double>(DevArray&, DevPrec<double>&, int, const void*, void*, cudaStream_t);
 template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t, int);
 template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t, int);
 template size_t fft_smem_bytes<float>(const DevArray&, int);

@@ -235,6 +235,72 @@ def loop_array(nx: int, ny: int, pitch: float = 0.5, outers=(0.4,), config_index
     return ArrayLayout(types, type_of, offs, nx, ny, pitch)
 
 
+def meander_mesh(extent: float = 0.28, width: float = 0.01, gap: float = 0.005, dx: float = 0.005) -> Mesh:
+    """Serpentine strip at z = 0 inside a square of side `extent` (centred): runs
+    along x of trace width `width`, separated by `gap` (the smallest feature),
+    joined at alternating ends by connectors of height `gap`.  Structured mesh:
+    every run is a row of dx x width quads, every connector one dx x gap quad
+    sharing its edges with the runs' end cells; each quad is split into two
+    triangles (normal +z)."""
+    pitch = width + gap
+    n_runs = int(np.floor((extent + gap) / pitch + 1e-9))
+    nx = int(round(extent / dx))
+    x = -extent / 2 + dx * np.arange(nx + 1)
+    y0 = -(n_runs * pitch - gap) / 2
+    xyz, tri = [], []
+    rows = []   # per run: (bottom node ids, top node ids)
+    for k in range(n_runs):
+        yb = y0 + k * pitch
+        bot = [len(xyz) + i for i in range(nx + 1)]
+        xyz += [[xi, yb, 0.0] for xi in x]
+        top = [len(xyz) + i for i in range(nx + 1)]
+        xyz += [[xi, yb + width, 0.0] for xi in x]
+        rows.append((bot, top))
+        for i in range(nx):
+            a, b, c, d = bot[i], bot[i + 1], top[i + 1], top[i]
+            tri += [[a, b, c], [a, c, d]]
+    for k in range(n_runs - 1):
+        i = nx - 1 if k % 2 == 0 else 0          # right end after even runs, left end after odd ones
+        a, b = rows[k][1][i], rows[k][1][i + 1]   # top edge of run k
+        c, d = rows[k + 1][0][i + 1], rows[k + 1][0][i]   # bottom edge of run k + 1
+        tri += [[a, b, c], [a, c, d]]
+    return Mesh(np.array(xyz), np.array(tri, dtype=np.int64), "meander")
+
+
+# Reduced multiscale element for oracle parity (the oracle's dense fills of the
+# full 2547-RWG element take minutes): the same loop, a coarser meander (7 runs
+# of 0.02-wide trace, 0.01 gaps: 535 RWG in all), the 6 x 6 x 1 box.
+MEANDER_REDUCED = dict(extent=0.2, width=0.02, gap=0.01, dx=0.02)
+MEANDER_REDUCED_BOX = (6, 6, 1)
+
+
+def merge_meshes(a: Mesh, b: Mesh, name: str = "") -> Mesh:
+    return Mesh(np.vstack([a.xyz, b.xyz]), np.vstack([a.tri, b.tri + len(a.xyz)]), name)
+
+
+def multiscale_element(config_index: int = 3, stream: int = 1, meander=None,
+                       box=(0.45, 0.45, 0.1), box_div=(8, 8, 2)) -> ElementType:
+    """Multiscale element: the 0.4-wavelength square loop with a meandered trace
+    inside it (0.005-wavelength gaps and cells), in the 0.45 x 0.45 x 0.1 box meshed
+    8 x 8 x 2 (576 RWG).  `meander` overrides the meander_mesh arguments."""
+    ring = square_loop_mesh(outer=0.4, gen=rng(config_index, stream))
+    mz = meander_mesh(**(meander or {}))
+    return ElementType(merge_meshes(ring, mz, "loop_meander"), box_mesh(*box, *box_div), "loop_meander")
+
+
+def multiscale_array(nx: int, ny: int, pitch: float = 0.5, config_index: int = 3, meander=None,
+                     box_div=(8, 8, 2)) -> ArrayLayout:
+    """nx x ny array of identical multiscale elements."""
+    et = multiscale_element(config_index, 1, meander, box_div=box_div)
+    offs = np.zeros((nx * ny, 3))
+    e = 0
+    for j in range(ny):
+        for i in range(nx):
+            offs[e] = (pitch * i, pitch * j, 0.0)
+            e += 1
+    return ArrayLayout([et], np.zeros(nx * ny, dtype=np.int32), offs, nx, ny, pitch)
+
+
 def planewave_grid(n_theta: int = 8, n_phi: int = 8, theta_max_deg: float = 60.0, phi_max_deg: float = 90.0):
     """(theta, phi, pol) for an n_theta x n_phi incidence grid; pol alternates
     theta-hat (0) / phi-hat (1) with the parity of (i + j)."""

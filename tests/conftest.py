@@ -32,6 +32,15 @@ def c1_layout():
 
 
 @pytest.fixture(scope="session")
+def meander_model():
+    """Oracle macromodel of the reduced multiscale element (loop + meander, 6x6x1 box)."""
+    from paper_1712_02443_gb300 import workloads as wl
+    from oracle.macromodel import build_element
+    et = wl.multiscale_element(meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    return build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+
+
+@pytest.fixture(scope="session")
 def c1_dense(loop_model, c1_layout):
     from oracle.macromodel import dense_exterior_operator
     return dense_exterior_operator([loop_model], c1_layout.type_of, c1_layout.offsets, K0)

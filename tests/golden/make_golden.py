@@ -17,6 +17,12 @@ Files (numpy .npz, complex128):
                   seeded per cell), 64 right-hand sides: sampled rows of
                   y = Z_AIM X for X = workloads.random_cvec(N, 2, 7, nrhs=64),
                   and of the plane-wave excitation for the 8 x 8 incidence grid.
+  c4_meander_2x2.npz  2x2 array of the reduced multiscale element (loop with a
+                  meandered inner trace, workloads.MEANDER_REDUCED, 6x6x1 box):
+                  Y = Z_AIM X (full) for X = workloads.random_cvec(N, 3, 7, nrhs=8),
+                  V (theta = 0, x-pol) and E = its solution to 1e-12.
+
+python tests/golden/make_golden.py [c4]   (c4: only the multiscale file)
 """
 from __future__ import annotations
 
@@ -121,5 +127,25 @@ def main():
     print("c3", time.time() - t0)
 
 
+def multiscale():
+    t0 = time.time()
+    et = wl.multiscale_element(meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    print("multiscale element", time.time() - t0)
+    lay = wl.multiscale_array(2, 2, meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    A = AIMArray([em], lay.type_of, lay.offsets, AIMParams(H, ORDER, NNF, wl.DEFAULT_GRID_PHASE), K0)
+    X = wl.random_cvec(A.n, 3, 7, nrhs=8)
+    Y = np.stack([A.matvec(np.ascontiguousarray(X[:, j])) for j in range(8)], axis=1)
+    V = np.concatenate([excitation(translated_rwg(em.rwg_e, o), 0.0, 0.0, 0, K0)[:, 0] for o in lay.offsets])
+    E, it, hist = gmres(A.matvec, V, tol=1e-12, restart=200, max_iter=2000)
+    print("gmres", it, hist[-1])
+    np.savez_compressed(os.path.join(HERE, "c4_meander_2x2.npz"), x_check=_check(X), y=Y, V=V, E=E)
+    print("c4", time.time() - t0)
+
+
 if __name__ == "__main__":
-    main()
+    if sys.argv[1:] == ["c4"]:
+        multiscale()
+    else:
+        main()
+        multiscale()

@@ -359,3 +359,18 @@ def test_near_csr_never_assembled(ctx, c1, prec):
         _close(yd.cpu().numpy().astype(np.complex128), g["y"], prec)
     finally:
         mm.mm_array_destroy(arr)
+
+
+@pytest.mark.parametrize("prec,refine", [(mm.MM_C128, 0), (mm.MM_C64, 1)])
+def test_c1_solve_block_jacobi(c1, prec, refine):
+    """Right block-Jacobi preconditioning leaves the solution unchanged (oracle's
+    1e-12 solution within 1e-4 at tol 1e-6) and needs fewer GMRES iterations."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    V = torch.from_numpy(g["V"]).cuda()
+    E = torch.empty_like(V)
+    st0 = mm.mm_solve(c1.array, 1, V, E, tol=1e-6, restart=50, max_iter=500, precision=prec, refine=refine)
+    st = mm.mm_solve(c1.array, 1, V, E, tol=1e-6, restart=50, max_iter=500, precision=prec, refine=refine, precond=1)
+    assert st["converged"] and st["rel_residual"] <= 1e-6
+    assert st["iterations"] < st0["iterations"], (st["iterations"], st0["iterations"])
+    err = np.linalg.norm(E.cpu().numpy() - g["E"]) / np.linalg.norm(g["E"])
+    assert err <= 1e-4, err

@@ -163,3 +163,27 @@ def test_near_blocks_reused_across_arrays_are_identical(host_ctx, lib_c1):
     finally:
         mm.mm_array_destroy(fresh)
         mm.mm_array_destroy(again)
+
+
+def test_multiscale_type_matrices_match_oracle(host_ctx, meander_model):
+    """The multiscale element (two conductors: the loop and a meandered trace with
+    gaps as narrow as its cells) through the library's FP64 element build."""
+    from paper_1712_02443_gb300.arrays import multiscale_array
+    la = multiscale_array(host_ctx, 1, 1, meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    try:
+        ty = la.types[0]
+        assert mm.mm_type_info(ty) == (meander_model.rwg_s.n, meander_model.rwg_e.n)
+        for which, R in ((mm.MM_MAT_M, meander_model.M), (mm.MM_MAT_D, meander_model.D),
+                         (mm.MM_MAT_T, meander_model.T)):
+            L = mm.mm_type_matrix(ty, which)
+            assert np.abs(L - R).max() <= 1e-10 * np.abs(R).max(), which
+    finally:
+        la.close()
+
+
+def test_block_jacobi_operator_matches_oracle(lib_c1, loop_model):
+    """MM_MAT_PJ is the inverse of the element's own block D - G^(E^,H^) M, formed
+    from the oracle's matrices by numpy's inverse."""
+    ref = np.linalg.inv(loop_model.D - loop_model.G_hEH @ loop_model.M)
+    L = mm.mm_type_matrix(lib_c1.types[0], mm.MM_MAT_PJ)
+    assert np.abs(L - ref).max() <= 1e-9 * np.abs(ref).max()
