@@ -150,10 +150,12 @@ def run_ours(args, rank, world, local):
     E = torch.empty_like(V)
     th, ph, pol = [0.0], [0.0], [0]
 
-    def step(prec=mm.MM_C64, refine=1):
+    pc = 0 if args.no_precond else 1
+
+    def step(prec=mm.MM_C64, refine=1, precond=None):
         mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
         return mm.mm_solve(la.array, 1, V, E, tol=TOL, restart=50, max_iter=2000, precision=prec, refine=refine,
-                           inner_tol=1e-5, stream=st)
+                           inner_tol=1e-5, stream=st, precond=pc if precond is None else precond)
 
     for _ in range(args.warmup):
         step()
@@ -208,6 +210,22 @@ def run_ours(args, rank, world, local):
         e1.record(st)
         torch.cuda.synchronize()
         t64 += e0.elapsed_time(e1)
+
+    # ---- the mixed-precision form without the block-Jacobi preconditioner (reference)
+    unpc = None
+    if pc:
+        step(precond=0)
+        mv0, t0ms = 0, 0.0
+        for k in range(k64):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            mv0 += step(precond=0)["matvecs"]
+            e1.record(st)
+            torch.cuda.synchronize()
+            t0ms += e0.elapsed_time(e1)
+        unpc = {"solves_per_s": round(world * k64 / (t0ms / 1e3), 2),
+                "matvecs_per_s": round(world * mv0 / (t0ms / 1e3), 1), "matvecs_per_solve": round(mv0 / k64, 1)}
 
     # ---- end to end through the public API: host angles in, solution copied to pinned host memory
     Eh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
@@ -264,6 +282,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "precision": "complex64 operator (FP32 FFT, SpMV, macromodel GEMM); FP64 Arnoldi, Givens, refinement",
+        "preconditioner": "block-Jacobi (inverse element self blocks), right, in both forms" if pc else "none",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": N, "nrhs": 1, "tol": TOL, "restart": 50,
                    "grid": list(info["grid"]), "fft": list(info["fft"]), "nnz_near": info["nnz_near"],
@@ -279,6 +298,7 @@ def run_ours(args, rank, world, local):
                             "matvecs_per_s": round(world * mv64 / (t64 / 1e3), 1),
                             "matvecs_per_solve": round(mv64 / k64, 1)},
         "speedup_vs_fp64_form_solves": round(solves_per_s / (world * k64 / (t64 / 1e3)), 3),
+        "without_preconditioner": unpc,
         "e2e": {"value": round(world * mv_e2e / e2e_s, 1), "unit": "matvecs/s",
                 "solves_per_s": round(world * args.steps / e2e_s, 2),
                 "h2d_bytes_per_step": 8 + 8 + 4, "d2h_bytes_per_step": 16 * N},
@@ -300,6 +320,8 @@ def run_ours(args, rank, world, local):
         out["tensor_gemm"] = tensor_gemm_measure(ctx, 64, 8, 10, 3)
     if rank == 0 and not args.no_batched:
         out["batched"] = batched_measure(ctx)
+    if rank == 0 and args.precision_config:
+        out["precision"] = precision_measure(ctx)
     if rank == 0 and args.serve_requests > 0:
         out["serving"] = serving_measure(ctx, args.serve_requests, args.serve_min_side, args.serve_max_side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -475,7 +497,7 @@ def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int 
 
     def submit(sv, r, **kw):
         return mm.mm_server_submit(sv, [types[t] for t in r["type_of"]], r["offsets"], r["theta"], r["phi"],
-                                   r["pol"], r["tol"], **kw)
+                                   r["pol"], r["tol"], precond=1, **kw)
 
     def collect(sv, tickets):
         out = []
@@ -528,6 +550,7 @@ def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int 
         "workload": "%d requests, square arrays of side %d..%d, 1-4 loop types, %d plane-wave solves in all, "
                     "tol 1e-3/1e-4" % (n_req, min_side, max_side, total_rhs),
         "workers": workers,
+        "preconditioner": "block-Jacobi in both forms",
         "all_converged": ok,
         "failures": [x["message"] for x in burst + stream + fp64 if not (x["status"] == 0 and x["converged"])][:4],
         "saturation": {"requests_per_s": round(sat, 3), "solves_per_s": round(total_rhs / t_burst, 2)},
@@ -561,15 +584,17 @@ def batched_measure(ctx, side: int = 32) -> dict:
     E = torch.empty_like(V)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     out = {"workload": "%dx%d array, 4 loop types, 64 plane waves (8 x 8 theta, phi grid), tol 1e-4" % (side, side),
+           "preconditioner": "block-Jacobi unless named otherwise",
            "unknowns": la.n, "nnz_near": la.info["nnz_near"], "setup_s": round(setup_s, 2)}
-    for name, prec, inner in (("fp32_gemm", mm.MM_C64, 1e-5), ("fp16_tensor_gemm", mm.MM_C64_F16, 1e-3)):
+    for name, prec, inner, pc in (("fp32_gemm", mm.MM_C64, 1e-5, 1), ("fp16_tensor_gemm", mm.MM_C64_F16, 1e-3, 1),
+                                  ("fp16_tensor_gemm_no_precond", mm.MM_C64_F16, 1e-3, 0)):
         flush.fill_(1)
         mm.mm_profile_enable(la.array, True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
         s = mm.mm_solve(la.array, 64, V, E, tol=1e-4, restart=50, max_iter=3000, precision=prec, refine=1,
-                        inner_tol=inner, stream=st, check=False)
+                        inner_tol=inner, stream=st, check=False, precond=pc)
         e1.record(st)
         torch.cuda.synchronize()
         pr = mm.mm_profile_read(la.array, mm.MM_C64)
@@ -581,6 +606,56 @@ def batched_measure(ctx, side: int = 32) -> dict:
                      "refinements": s["refinements"],
                      "ms_per_iteration": {k: round(v["ms"] / it, 3) for k, v in pr.items() if v["launches"]}}
     del flush
+    la.close()
+    return out
+
+
+def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
+    """Precision configuration: side x side array of the multiscale element (square
+    loop with a meandered inner trace, 2547 scatterer RWG, 0.005-wavelength gaps; box
+    meshed 8 x 8 x 2, 576 RWG), nrhs plane waves (the first nrhs of the 8 x 8
+    grid), refined to 1e-4 with the macromodel GEMM in BF16 and FP16 on tensor cores
+    and in FP32 on CUDA cores; FP32 FFT and near field, FP64 Arnoldi and residuals.
+    The oracle cannot run at this size: each 16-bit result is compared with the
+    FP32-GEMM result (the oracle comparison is made on a 2 x 2 sub-array in the
+    tests)."""
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.arrays import multiscale_array
+    t0 = time.time()
+    la = multiscale_array(ctx, side, side)
+    setup_s = time.time() - t0
+    st = torch.cuda.current_stream()
+    th, ph, pol = wl.planewave_grid()
+    V = torch.empty(la.n * nrhs, dtype=torch.complex128, device="cuda")
+    mm.mm_rhs_planewave(la.array, th[:nrhs], ph[:nrhs], pol[:nrhs], V, mm.MM_C128, st)
+    out = {"workload": "%dx%d multiscale elements (loop + meander, 2547 RWG; box 576 RWG), %d plane waves, tol 1e-4"
+           % (side, side, nrhs), "preconditioner": "block-Jacobi", "unknowns": la.n, "nnz_near": la.info["nnz_near"],
+           "near_field": la.info["near_format"], "setup_s": round(setup_s, 1)}
+    sols = {}
+    for name, prec, inner in (("bf16", mm.MM_C64_BF16, 1e-3), ("fp16", mm.MM_C64_F16, 1e-3),
+                              ("fp32", mm.MM_C64, 1e-5)):
+        E = torch.empty_like(V)
+        mm.mm_profile_enable(la.array, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s = mm.mm_solve(la.array, nrhs, V, E, tol=1e-4, restart=50, max_iter=3000, precision=prec, refine=1,
+                        inner_tol=inner, stream=st, check=False, precond=1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        pr = mm.mm_profile_read(la.array, -1)
+        mm.mm_profile_enable(la.array, False)
+        t = e0.elapsed_time(e1) / 1e3
+        it = max(1, s["iterations"])
+        sols[name] = E.cpu().numpy()
+        out[name] = {"s_per_batch": round(t, 3), "solves_per_s": round(nrhs / t, 3), "converged": s["converged"],
+                     "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
+                     "refinements": s["refinements"], "matvecs": s["matvecs"],
+                     "stage_ms_total": {k: round(v["ms"], 1) for k, v in pr.items() if v["launches"]}}
+    ref = sols["fp32"]
+    for name in ("bf16", "fp16"):
+        out[name]["rel_diff_vs_fp32_gemm_solution"] = float(np.linalg.norm(sols[name] - ref) / np.linalg.norm(ref))
     la.close()
     return out
 
@@ -607,7 +682,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--gemm", action="store_true", help="time the tensor-core macromodel GEMM at the 64x64 shape")
     ap.add_argument("--no-tensor-gemm", action="store_true", help="skip the tensor-core GEMM line of the report")
+    ap.add_argument("--no-precond", action="store_true", help="solve without the block-Jacobi preconditioner")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-plane-wave batched solve")
+    ap.add_argument("--precision-config", action="store_true",
+                    help="also solve the 64x64 multiscale array (8 plane waves, 16-bit tensor-core GEMM)")
     ap.add_argument("--serve-requests", type=int, default=12, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-min-side", type=int, default=8)
     ap.add_argument("--serve-max-side", type=int, default=24)
