@@ -348,7 +348,7 @@ __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
 
 // Forward: z DFT (direct, Nz -> Pz) then y FFT (Ny -> Py) of plane (b, x).
 template <typename R>
-__global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T* __restrict__ grid, int Nx, int Ny,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(const typename V2<R>::T* __restrict__ grid, int Nx, int Ny,
                                                         int Nz, FftPlan py, int Pz,
                                                         const typename V2<R>::T* __restrict__ twy,
                                                         const typename V2<R>::T* __restrict__ twz,
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) k_fft_fwd_planes(const typename V2<R>::T*
 // x FFT (Nx -> Px), multiply by the Green's spectrum, inverse x FFT (keep Nx),
 // for the Pz lines of one (b, ky); warp per line.
 template <typename R>
-__global__ void __launch_bounds__(256) k_fft_conv_lines(typename V2<R>::T* __restrict__ spec, int Nx, int Py,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(typename V2<R>::T* __restrict__ spec, int Nx, int Py,
                                                         int Pz, FftPlan px, const typename V2<R>::T* __restrict__ twx,
                                                         const typename V2<R>::T* __restrict__ Ghat) {
   typedef typename V2<R>::T C;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) k_fft_conv_lines(typename V2<R>::T* __res
 
 // Inverse: y FFT (keep Ny) then z DFT (keep Nz) of plane (b, x).
 template <typename R>
-__global__ void __launch_bounds__(256) k_fft_inv_planes(const typename V2<R>::T* __restrict__ spec, int Nx, int Ny,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(const typename V2<R>::T* __restrict__ spec, int Nx, int Ny,
                                                         int Nz, FftPlan py, int Pz,
                                                         const typename V2<R>::T* __restrict__ twy,
                                                         const typename V2<R>::T* __restrict__ twz,
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) k_fft_inv_planes(const typename V2<R>::T*
 
 // ---------------------------------------------------------------- A4: interpolation (step iii)
 // y = v - [c_A sum_{xyz} Pi.Phi + c_phi Pi_phi.Phi_phi]; one CTA per element.
-template <typename R>
+template <typename R, int CR>
 __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
@@ -502,26 +502,46 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
       box[i] = grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < Nh * cn; p += blockDim.x) {
-      const int n = p / cn, c = p % cn;
-      C sA = czero<C>(), sP = czero<C>();
+    // item = (basis n, chunk of CR right-hand sides); consecutive threads take
+    // consecutive bases (contiguous weights); each stencil weight and node index
+    // is loaded once for the whole chunk
+    const int nch = (cn + CR - 1) / CR;
+    for (int p = threadIdx.x; p < Nh * nch; p += blockDim.x) {
+      const int n = p % Nh, cb = (p / Nh) * CR;
+      C sA[CR], sP[CR];
+#pragma unroll
+      for (int c = 0; c < CR; ++c) {
+        sA[c] = czero<C>();
+        sP[c] = czero<C>();
+      }
       const int ax = anc[3 * n] + o1lo, ay = anc[3 * n + 1] + o1lo, az = anc[3 * n + 2] + o1lo;
       for (int s = 0; s < S; ++s) {
         const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
         const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
         const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)s * Nh + n) * 4);
-        const C f0 = box[(0 * cn + c) * nodes + node];
-        const C f1 = box[(1 * cn + c) * nodes + node];
-        const C f2 = box[(2 * cn + c) * nodes + node];
-        const C f3 = box[(3 * cn + c) * nodes + node];
-        sA.x += w.x * f0.x + w.y * f1.x + w.z * f2.x;
-        sA.y += w.x * f0.y + w.y * f1.y + w.z * f2.y;
-        sP.x += w.w * f3.x;
-        sP.y += w.w * f3.y;
+        const C* b0 = box + cb * nodes + node;
+#pragma unroll
+        for (int c = 0; c < CR; ++c) {
+          if (cb + c < cn) {
+            const C f0 = b0[(0 * cn + c) * nodes];
+            const C f1 = b0[(1 * cn + c) * nodes];
+            const C f2 = b0[(2 * cn + c) * nodes];
+            const C f3 = b0[(3 * cn + c) * nodes];
+            sA[c].x += w.x * f0.x + w.y * f1.x + w.z * f2.x;
+            sA[c].y += w.x * f0.y + w.y * f1.y + w.z * f2.y;
+            sP[c].x += w.w * f3.x;
+            sP[c].y += w.w * f3.y;
+          }
+        }
       }
-      const C yff = cadd(cmul(cA, sA), cmul(cP, sP));
-      const int64_t idx = (o + n) * nrhs + c0 + c;
-      y[idx] = csub(v[idx], yff);
+#pragma unroll
+      for (int c = 0; c < CR; ++c) {
+        if (cb + c < cn) {
+          const C yff = cadd(cmul(cA, sA[c]), cmul(cP, sP[c]));
+          const int64_t idx = (o + n) * nrhs + c0 + cb + c;
+          y[idx] = csub(v[idx], yff);
+        }
+      }
     }
     __syncthreads();
   }
@@ -781,6 +801,8 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
   ++nl;
 }
 
+// (The FFT kernels' complex64 forms are bounded to 3 CTAs per SM, which they
+// reach without spilling; the transforms are latency-bound.)
 // ---------------------------------------------------------------- launchers
 template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which) {
@@ -808,7 +830,8 @@ cudaError_t kernels_init(DevArray& a) {
   MM_ATTR(k_fft_inv_planes<float>) MM_ATTR(k_fft_inv_planes<double>)
   MM_ATTR((k_project<float, 1>)) MM_ATTR((k_project<double, 1>)) MM_ATTR((k_project<float, 4>))
   MM_ATTR((k_project<double, 4>))
-  MM_ATTR(k_interp<float>) MM_ATTR(k_interp<double>)
+  MM_ATTR((k_interp<float, 1>)) MM_ATTR((k_interp<double, 1>)) MM_ATTR((k_interp<float, 8>))
+  MM_ATTR((k_interp<double, 8>))
 #undef MM_ATTR
   e = tc_gemm_init();
   if (e != cudaSuccess) return e;
@@ -905,9 +928,16 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
     const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
     const size_t sm = 4 * rc * nodes * sizeof(C);
-    k_interp<R><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
-        a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
-        p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v, y);
+    if (rc >= 8)
+      k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
+          y);
+    else
+      k_interp<R, 1><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
+          y);
     ++nl;
   }
   pr.end(st, nl);
