@@ -358,6 +358,10 @@ typedef enum mm_stage {
   MM_STAGE_COUNT = 8
 } mm_stage;
 mm_status mm_profile_enable(mm_array* array, int32_t enable);
+/* Which stages record while profiling is enabled: bit s of stage_mask for stage
+ * s (both precisions; default all).  Recording fewer stages perturbs the timed
+ * work less (each recorded stage adds two CUDA event records per product).   */
+mm_status mm_profile_stages(mm_array* array, uint32_t stage_mask);
 mm_status mm_profile_read(mm_array* array, int32_t precision, double* ms, int64_t* launches);
 
 #ifdef __cplusplus

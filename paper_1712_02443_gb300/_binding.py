@@ -105,6 +105,7 @@ _SIGS = {
     "mm_server_release": (ct.c_int, [P, ct.c_uint64]),
     "mm_server_destroy": (None, [P]),
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
+    "mm_profile_stages": (ct.c_int, [P, ct.c_uint32]),
     "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
 }
 
@@ -331,6 +332,12 @@ def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_
 
 def mm_profile_enable(array, enable: bool = True) -> None:
     _check(load().mm_profile_enable(array, 1 if enable else 0), _ctx_of.get(array.value))
+
+
+def mm_profile_stages(array, stages=None) -> None:
+    """Record only the named stages (None: all)."""
+    mask = 0xFF if stages is None else sum(1 << STAGES.index(s) for s in stages)
+    _check(load().mm_profile_stages(array, mask), _ctx_of.get(array.value))
 
 
 def mm_profile_read(array, precision: int = -1) -> dict:

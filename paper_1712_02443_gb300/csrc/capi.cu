@@ -1117,6 +1117,12 @@ mm_status mm_profile_enable(mm_array* a, int32_t enable) {
   API_CATCH(a->ctx)
 }
 
+mm_status mm_profile_stages(mm_array* a, uint32_t stage_mask) {
+  if (!a) return MM_EINVAL;
+  a->da.prof.mask = stage_mask & 0xFFu;
+  return MM_OK;
+}
+
 mm_status mm_profile_read(mm_array* a, int32_t precision, double* ms, int64_t* launches) {
   if (!a || !ms || !launches || precision < -1 || precision > 1) return MM_EINVAL;
   if (!a->on_device) return fail(a->ctx, MM_EINVAL, "array has no device (host-only context)");

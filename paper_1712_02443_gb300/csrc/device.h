@@ -34,14 +34,18 @@ struct Profiler {
     cudaEventCreate(&e);
     return e;
   }
+  uint32_t mask = 0xFFu;          // stages that record (bit s: stage s of either precision)
   void begin(int stage, cudaStream_t st) {
-    if (!on) return;
+    if (!on || !((mask >> (stage % 8)) & 1u)) {
+      open_stage = -1;
+      return;
+    }
     open_stage = stage;
     open_ev = get();
     cudaEventRecord(open_ev, st);
   }
   void end(cudaStream_t st, int nlaunch) {
-    if (!on) return;
+    if (!on || open_stage < 0) return;
     cudaEvent_t b = get();
     cudaEventRecord(b, st);
     recs.push_back({open_stage, open_ev, b});

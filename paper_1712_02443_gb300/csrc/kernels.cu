@@ -502,6 +502,32 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
       box[i] = grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
     }
     __syncthreads();
+    if constexpr (CR == 1) {
+      // item = (basis n, right-hand side c)
+      for (int p = threadIdx.x; p < Nh * cn; p += blockDim.x) {
+        const int n = p / cn, c = p % cn;
+        C sA = czero<C>(), sP = czero<C>();
+        const int ax = anc[3 * n] + o1lo, ay = anc[3 * n + 1] + o1lo, az = anc[3 * n + 2] + o1lo;
+        for (int s = 0; s < S; ++s) {
+          const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+          const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
+          const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)s * Nh + n) * 4);
+          const C f0 = box[(0 * cn + c) * nodes + node];
+          const C f1 = box[(1 * cn + c) * nodes + node];
+          const C f2 = box[(2 * cn + c) * nodes + node];
+          const C f3 = box[(3 * cn + c) * nodes + node];
+          sA.x += w.x * f0.x + w.y * f1.x + w.z * f2.x;
+          sA.y += w.x * f0.y + w.y * f1.y + w.z * f2.y;
+          sP.x += w.w * f3.x;
+          sP.y += w.w * f3.y;
+        }
+        const C yff = cadd(cmul(cA, sA), cmul(cP, sP));
+        const int64_t idx = (o + n) * nrhs + c0 + c;
+        y[idx] = csub(v[idx], yff);
+      }
+      __syncthreads();
+      continue;
+    }
     // item = (basis n, chunk of CR right-hand sides); consecutive threads take
     // consecutive bases (contiguous weights); each stencil weight and node index
     // is loaded once for the whole chunk
