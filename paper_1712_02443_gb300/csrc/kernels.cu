@@ -58,6 +58,28 @@ template <typename T> __device__ __forceinline__ T czero() {
   return c;
 }
 
+// Block-wide staging copy: store(i, load(i)) for i < n, with U loads per
+// thread issued before their stores.  (Written as one loop, each load would
+// wait on the shared-memory store of the previous one: one memory latency per
+// element and thread.)
+template <int U, typename T, typename Load, typename Store>
+__device__ __forceinline__ void staged_copy(int n, Load load, Store store) {
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i < n) v[u] = load(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i < n) store(i, v[u]);
+    }
+  }
+}
+
+
 FftPlan make_plan(int L) {
   FftPlan p;
   p.L = L;
@@ -220,10 +242,13 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
   const int64_t gstride = (int64_t)Nx * Ny * Nz;
   for (int c0 = 0; c0 < nrhs; c0 += RC) {
     const int cn = min(RC, nrhs - c0);
-    for (int i = threadIdx.x; i < Nh * RC; i += blockDim.x) {
-      const int n = i / RC, c = i % RC;
-      us[i] = c < cn ? u[(o + n) * nrhs + c0 + c] : czero<C>();
-    }
+    staged_copy<4, C>(
+        Nh * RC,
+        [&](int i) {
+          const int n = i / RC, c = i % RC;
+          return c < cn ? u[(o + n) * nrhs + c0 + c] : czero<C>();
+        },
+        [&](int i, C v) { us[i] = v; });
     __syncthreads();
     for (int node = threadIdx.x; node < nodes; node += blockDim.x) {
       C acc[4][RC];
@@ -277,8 +302,11 @@ template <typename C, int RADIX, bool INV>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
                                                const C* __restrict__ tw, int lane, int nlanes) {
   const int nb = L / RADIX;
-  const int st = L / (Ns * RADIX);
-  const int stR = L / RADIX;
+  const int st = nb / Ns;
+  const int stR = nb;
+  // j / Ns and j % Ns by a float reciprocal and one correction step (exact for
+  // j < 2^22; an integer division would cost tens of instructions per butterfly)
+  const float rNs = 1.0f / (float)Ns;
   C wr[RADIX];   // roots of unity of order RADIX (conjugated for the inverse)
 #pragma unroll
   for (int m = 0; m < RADIX; ++m) {
@@ -286,7 +314,15 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
     if (INV) wr[m].y = -wr[m].y;
   }
   for (int j = lane; j < nb; j += nlanes) {
-    const int k = j % Ns;
+    int g = __float2int_rz((float)j * rNs);
+    int k = j - g * Ns;
+    if (k >= Ns) {
+      k -= Ns;
+      ++g;
+    } else if (k < 0) {
+      k += Ns;
+      --g;
+    }
     C v[RADIX];
 #pragma unroll
     for (int q = 0; q < RADIX; ++q) v[q] = a[PAD(j + q * nb)];
@@ -298,7 +334,7 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
         v[q] = cmul(v[q], w);
       }
     }
-    const int base = (j / Ns) * Ns * RADIX + k;
+    const int base = g * Ns * RADIX + k;
     if (RADIX == 2) {
       b[PAD(base)] = cadd(v[0], v[1]);
       b[PAD(base + Ns)] = csub(v[0], v[1]);
@@ -324,6 +360,7 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
 
 // Warp-level Stockham FFT of one line held in shared memory (buffers a, b of
 // length L); returns the buffer that holds the result.
+
 template <typename C, bool INV>
 __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
   int Ns = 1;
@@ -365,7 +402,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
   const C* src = grid + ((int64_t)b * Nx + x) * Ny * Nz;
-  for (int i = threadIdx.x; i < Ny * Nz; i += blockDim.x) b1[i] = src[i];   // staging [y][z]
+  staged_copy<8, C>(Ny * Nz, [&](int i) { return src[i]; }, [&](int i, C v) { b1[i] = v; });   // staging [y][z]
   __syncthreads();
   for (int i = threadIdx.x; i < Pz * Py; i += blockDim.x) {
     const int kz = i / Py, y = i % Py;
@@ -405,10 +442,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(
   const int ky = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Px; i += blockDim.x) tx[i] = twx[i];
   C* base = spec + (int64_t)b * Nx * Py * Pz + (int64_t)ky * Pz;
-  for (int i = threadIdx.x; i < Pz * Px; i += blockDim.x) {
-    const int x = i / Pz, kz = i % Pz;
-    if (x < Px) b0[kz * LpX + PAD(x)] = (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
-  }
+  staged_copy<8, C>(
+      Pz * Px,
+      [&](int i) {
+        const int x = i / Pz, kz = i % Pz;
+        return (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
+      },
+      [&](int i, C v) {
+        const int x = i / Pz, kz = i % Pz;
+        b0[kz * LpX + PAD(x)] = v;
+      });
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   for (int kz = warp; kz < Pz; kz += nw) {
@@ -449,10 +492,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
   const C* src = spec + ((int64_t)b * Nx + x) * Py * Pz;
-  for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
-    const int ky = i / Pz, kz = i % Pz;
-    b0[kz * LpY + PAD(ky)] = src[i];
-  }
+  staged_copy<8, C>(
+      Py * Pz, [&](int i) { return src[i]; },
+      [&](int i, C v) {
+        const int ky = i / Pz, kz = i % Pz;
+        b0[kz * LpY + PAD(ky)] = v;
+      });
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   for (int kz = warp; kz < Pz; kz += nw) warp_fft<C, true>(b0 + kz * LpY, b1 + kz * LpY, py, ty, lane);
@@ -494,13 +539,16 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
   cA.x = cAr; cA.y = cAi; cP.x = cPr; cP.y = cPi;
   for (int c0 = 0; c0 < nrhs; c0 += rc) {
     const int cn = min(rc, nrhs - c0);
-    for (int i = threadIdx.x; i < 4 * cn * nodes; i += blockDim.x) {
-      const int node = i % nodes, pc = i / nodes;
-      const int psi = pc / cn, c = pc % cn;
-      const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
-      const int64_t b = (int64_t)psi * nrhs + c0 + c;
-      box[i] = grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
-    }
+    staged_copy<8, C>(
+        4 * cn * nodes,
+        [&](int i) {
+          const int node = i % nodes, pc = i / nodes;
+          const int psi = pc / cn, c = pc % cn;
+          const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+          const int64_t b = (int64_t)psi * nrhs + c0 + c;
+          return grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
+        },
+        [&](int i, C v) { box[i] = v; });
     __syncthreads();
     if constexpr (CR == 1) {
       // item = (basis n, right-hand side c)
