@@ -947,9 +947,14 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     ensure_pt<double>(a, a->da.wd, nrhs);
     ensure_pt<float>(a, a->da.wf, nrhs);
   }
-  S.op64 = [arr, nrhs, pj](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
+  // With refinement the solution itself is kept (the FP64 residual uses the
+  // plain operator) and each inner correction y is mapped to P^-1 y in
+  // complex64, the precision it was solved in; without refinement GMRES runs on
+  // Z P^-1 throughout and the result is mapped once at the end.
+  const bool pj_outer = pj && !opts->refine;
+  S.op64 = [arr, nrhs, pj_outer](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
     const void* x = in;
-    if (pj) {
+    if (pj_outer) {
       cudaError_t e = mm::precond_apply<double>(arr->da, arr->da.pd, nrhs, in, arr->da.wd.pt, s2);
       if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
       x = arr->da.wd.pt;
@@ -969,6 +974,13 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
+  S.correction32 = nullptr;
+  if (pj && opts->refine)
+    S.correction32 = [arr, nrhs](const void* in, void* out, cudaStream_t s2) -> mm::Status {
+      cudaError_t e = mm::precond_apply<float>(arr->da, arr->da.pf, nrhs, in, out, s2);
+      if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
+      return {MM_OK, ""};
+    };
   int iters = 0, refs = 0;
   double relres = 0;
   bool conv = false;
@@ -976,7 +988,7 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
               opts->precision == MM_C128 ? MM_C128 : MM_C64,
               opts->refine, opts->inner_tol > 0 ? opts->inner_tol : 1e-2, opts->max_iter, iters, refs, relres, conv,
               st);
-  if (pj && (s.code == MM_OK || s.code == MM_ENOCONV)) {
+  if (pj_outer && (s.code == MM_OK || s.code == MM_ENOCONV)) {
     // the solution of Z P^-1 y = V is y; E = P^-1 y
     CU(mm::precond_apply<double>(a->da, a->da.pd, nrhs, E_dev, a->da.wd.pt, st));
     CU(cudaMemcpyAsync(E_dev, a->da.wd.pt, sizeof(double2) * (size_t)a->da.N * nrhs, cudaMemcpyDeviceToDevice, st));

@@ -1189,6 +1189,12 @@ Status Solver::solve(const Z* b, Z* x, double tol, int prec, int refine, double 
       if (s.code != MM_OK) return s;
       iters += it;
       ++refinements;
+      if (correction32) {
+        k_to_c64<<<grid_for(n), 256, 0, st>>>(dx, static_cast<float2*>(x32_), n);
+        Status s2 = correction32(x32_, y32_, st);
+        if (s2.code != MM_OK) return s2;
+        k_to_c128<<<grid_for(n), 256, 0, st>>>(static_cast<const float2*>(y32_), dx, n);
+      }
       k_add<<<grid_for(n), 256, 0, st>>>(dx, n, x);
       s = apply(x, rr, MM_C128, st);
       if (s.code != MM_OK) return s;

@@ -27,6 +27,10 @@ class Solver {
   // operators on device vectors of the current (N, r): complex128 and complex64
   std::function<Status(const double2*, double2*, cudaStream_t)> op64;
   std::function<Status(const void*, void*, cudaStream_t)> op32;
+  // optional: maps each refinement correction (complex64 in -> out) before it is
+  // added to the solution, e.g. a right preconditioner applied to the inner
+  // GMRES's solution in the precision of the inner solve
+  std::function<Status(const void*, void*, cudaStream_t)> correction32;
   int matvecs = 0;
   Profiler* prof = nullptr;   // optional stage profiler (Krylov kernels)
   int orth = 2;               // 1 one pass, 2 selective second pass, 3 two passes
