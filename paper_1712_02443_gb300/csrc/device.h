@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <vector>
 
 namespace mm {
@@ -152,6 +153,8 @@ struct DevArray {
   void* nfg_dev = nullptr;              // device copy of nfg (same layout)
   int2* nfg_pairs = nullptr;            // (row element, column element), grouped by block
   int near_mode = 0;                    // 0 blocks; 2 CSR rows (when assembled)
+  // autotuned block near-field shape per (right-hand sides, sizeof(R)): (column tile, k split)
+  std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;

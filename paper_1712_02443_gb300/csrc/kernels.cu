@@ -861,18 +861,63 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
 
 template <typename R, int TN>
 static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
-                               typename V2<R>::T* y, cudaStream_t st, int& nl) {
+                               typename V2<R>::T* y, cudaStream_t st, int& nl, int ksplit) {
   int64_t tiles = 0;
   for (const auto& g : a.nfg) tiles += ((g.npairs * nrhs + TN - 1) / TN) * ((g.Na + 63) / 64);
   if (tiles == 0) return;
-  // few output tiles: split each row tile's k tiles over four CTAs (the
-  // outputs are accumulated atomically anyway)
-  const int ksplit = tiles < 4 * 152 ? 4 : 1;
+  // ksplit > 1 splits each row tile's k tiles over several CTAs (the outputs are
+  // accumulated atomically anyway): more CTAs when the output tiles are few
   k_near_blocks<R, TN><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
       reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_pairs,
       static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, a.nfb_nmt, a.nfb_tptr, a.nfb_tlist,
       a.nfb_perm, a.nfb_pa, a.nfb_pb, a.off, nrhs, ksplit, u, y);
   ++nl;
+}
+
+// Autotuner of the block near field: on the first product of an array with a
+// given right-hand-side count and precision, each (column tile, k split) shape
+// is timed with CUDA events (one warm-up, three timed launches) writing into a
+// scratch buffer (the spectra, idle at this point of the product), and the
+// fastest is kept for that array.  Without a large enough scratch buffer the
+// size rule is used instead.
+template <typename R>
+static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p, int nrhs,
+                                         const typename V2<R>::T* u, typename V2<R>::T* scratch,
+                                         size_t scratch_elems, cudaStream_t st) {
+  int64_t cols = 0;
+  for (const auto& g : a.nfg) cols += g.npairs * nrhs;
+  std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 64 : 32, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
+  if (scratch == nullptr || scratch_elems < (size_t)a.N * nrhs) return best;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return best;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return best;
+  }
+  float best_ms = 1e30f;
+  for (int tn : {32, 64})
+    for (int ks : {1, 2, 4}) {
+      int nl = 0;
+      auto run = [&]() {
+        if (tn == 64)
+          near_blocks_launch<R, 64>(a, p, nrhs, u, scratch, st, nl, ks);
+        else
+          near_blocks_launch<R, 32>(a, p, nrhs, u, scratch, st, nl, ks);
+      };
+      run();
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3; ++rep) run();
+      cudaEventRecord(e1, st);
+      float ms = 0;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+          ms < best_ms) {
+        best_ms = ms;
+        best = {tn, ks};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 // (The FFT kernels' complex64 forms are bounded to 3 CTAs per SM, which they
@@ -1021,14 +1066,18 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // dense blocks costs more than streaming the CSR from HBM)
   const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
   if (a.nfb_entries > 0 && p.nfb_val != nullptr && !csr) {
+    const auto key = std::make_pair(nrhs, (int)sizeof(R));
+    auto it = a.near_tune.find(key);
+    if (it == a.near_tune.end())
+      it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
+                                                      (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
+    const int tn = it->second.first, ks = it->second.second;
     pr.begin(sb + 6, st);
     nl = 0;
-    int64_t cols = 0;
-    for (const auto& g : a.nfg) cols += g.npairs * nrhs;
-    if (cols >= (int64_t)64 * 4 * 152)
-      near_blocks_launch<R, 64>(a, p, nrhs, u, y, st, nl);
+    if (tn == 64)
+      near_blocks_launch<R, 64>(a, p, nrhs, u, y, st, nl, ks);
     else
-      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl);
+      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl, ks);
     pr.end(st, nl);
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, st);
