@@ -627,6 +627,9 @@ def batched_measure(ctx, side: int = 32) -> dict:
     return out
 
 
+PRECISION_RESTART = 200   # GMRES(200): 522 iterations on this array, against 1,442 at GMRES(50)
+
+
 def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
     """Precision configuration: side x side array of the multiscale element (square
     loop with a meandered inner trace, 2547 scatterer RWG, 0.005-wavelength gaps; box
@@ -648,7 +651,8 @@ def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
     V = torch.empty(la.n * nrhs, dtype=torch.complex128, device="cuda")
     mm.mm_rhs_planewave(la.array, th[:nrhs], ph[:nrhs], pol[:nrhs], V, mm.MM_C128, st)
     out = {"workload": "%dx%d multiscale elements (loop + meander, 2547 RWG; box 576 RWG), %d plane waves, tol 1e-4"
-           % (side, side, nrhs), "preconditioner": "block-Jacobi", "unknowns": la.n, "nnz_near": la.info["nnz_near"],
+           % (side, side, nrhs), "preconditioner": "block-Jacobi", "restart": PRECISION_RESTART,
+           "unknowns": la.n, "nnz_near": la.info["nnz_near"],
            "near_field": la.info["near_format"], "setup_s": round(setup_s, 1)}
     sols = {}
     for name, prec, inner in (("bf16", mm.MM_C64_BF16, 1e-3), ("fp16", mm.MM_C64_F16, 1e-3),
@@ -657,8 +661,8 @@ def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
         mm.mm_profile_enable(la.array, True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        s = mm.mm_solve(la.array, nrhs, V, E, tol=1e-4, restart=50, max_iter=3000, precision=prec, refine=1,
-                        inner_tol=inner, stream=st, check=False, precond=1)
+        s = mm.mm_solve(la.array, nrhs, V, E, tol=1e-4, restart=PRECISION_RESTART, max_iter=3000, precision=prec,
+                        refine=1, inner_tol=inner, stream=st, check=False, precond=1)
         e1.record(st)
         torch.cuda.synchronize()
         pr = mm.mm_profile_read(la.array, -1)
