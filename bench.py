@@ -618,7 +618,8 @@ def batched_measure(ctx, side: int = 32) -> dict:
         mm.mm_profile_enable(la.array, False)
         t = e0.elapsed_time(e1) / 1e3
         it = max(1, s["iterations"])
-        out[name] = {"s_per_batch": round(t, 3), "solves_per_s": round(64 / t, 2), "converged": s["converged"],
+        out[name] = {"s_per_batch": round(t, 3), "solves_per_s": round(64 / t, 2),
+                     "column_matvecs_per_s": round(64 * s["matvecs"] / t, 1), "converged": s["converged"],
                      "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
                      "refinements": s["refinements"],
                      "ms_per_iteration": {k: round(v["ms"] / it, 3) for k, v in pr.items() if v["launches"]}}

@@ -187,10 +187,12 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
 // Packed real operand of the tensor-core GEMM for one 16-bit format (mode 1 BF16,
 // 2 FP16): per type, row 2i = [Re W_i, -Im W_i], row 2i+1 = [Im W_i, Re W_i]
 // for W = [M; D], padded to the tile sizes.
-void upload_tc(mm_array* a, int mode) {
+// pre: the preconditioned operator's matrices [M PJ; D PJ] (p.AtcP) instead of [M; D]
+void upload_tc(mm_array* a, int mode, bool pre = false) {
   auto& p = a->da.pf;
   const int slot = mode - 1;
-  if (!p.Atc[slot].empty()) return;
+  auto& dst = pre ? p.AtcP[slot] : p.Atc[slot];
+  if (!dst.empty()) return;
   auto& da = a->da;
   const int TM = mm::tc_tile_m(), TK = mm::tc_tile_k();
   p.Mp.resize(da.n_types);
@@ -212,8 +214,8 @@ void upload_tc(mm_array* a, int mode) {
       return *reinterpret_cast<uint16_t*>(&h);
     };
     for (int64_t i = 0; i < 2 * Nh; ++i) {
-      const std::vector<mm::cd>& W = i < Nh ? tm.M : tm.D;
-      const int64_t ii = i < Nh ? i : i - Nh;
+      const std::vector<mm::cd>& W = pre ? tm.WPJ : (i < Nh ? tm.M : tm.D);
+      const int64_t ii = (pre || i < Nh) ? i : i - Nh;
       for (int64_t k = 0; k < Nh; ++k) {
         const mm::cd w = W[ii * Nh + k];
         A[(size_t)(2 * i) * Kp + k] = cvt(w.real());
@@ -222,7 +224,7 @@ void upload_tc(mm_array* a, int mode) {
         A[(size_t)(2 * i + 1) * Kp + Nhp + k] = cvt(w.real());
       }
     }
-    p.Atc[slot].push_back(dev_upload(A.data(), A.size(), da.bytes));
+    dst.push_back(dev_upload(A.data(), A.size(), da.bytes));
   }
 }
 
@@ -239,6 +241,12 @@ void upload_pj(mm_array* a, mm::DevPrec<R>& p) {
       W[i].y = (R)tm.PJ[i].imag();
     }
     p.PJ.push_back(dev_upload(W.data(), W.size(), a->da.bytes));
+    std::vector<C> WP(tm.WPJ.size());
+    for (size_t i = 0; i < WP.size(); ++i) {
+      WP[i].x = (R)tm.WPJ[i].real();
+      WP[i].y = (R)tm.WPJ[i].imag();
+    }
+    p.WP.push_back(dev_upload(WP.data(), WP.size(), a->da.bytes));
   }
 }
 
@@ -312,9 +320,13 @@ void free_prec_f(mm::DevPrec<float>& p) {
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
   for (void* q : p.PJ) cudaFree(q);
+  for (void* q : p.WP) cudaFree(q);
+  for (auto& v : p.AtcP)
+    for (void* q : v) cudaFree(q);
 }
 void free_prec_d(mm::DevPrec<double>& p) {
   for (void* q : p.PJ) cudaFree(q);
+  for (void* q : p.WP) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
@@ -348,6 +360,9 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
     if (q) cudaFree(q);
+  if (da.side) cudaStreamDestroy(da.side);
+  for (cudaEvent_t e : {da.ev_fork, da.ev_join})
+    if (e) cudaEventDestroy(e);
 }
 
 extern "C" {
@@ -704,6 +719,13 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     }
     upload_precision<float>(a.get(), da.pf);
     CU(mm::kernels_init(da));
+    // the near field's own stream (MACROAIM_NEAR_OVERLAP=0: one stream, in order)
+    const char* ov = std::getenv("MACROAIM_NEAR_OVERLAP");
+    if ((da.nfb_entries > 0 || da.nnz > 0) && !(ov && std::string(ov) == "0")) {
+      CU(cudaStreamCreateWithFlags(&da.side, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&da.ev_fork, cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&da.ev_join, cudaEventDisableTiming));
+    }
   }
   *out = a.release();
   return MM_OK;
@@ -944,33 +966,22 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     // right preconditioning: GMRES runs on Z P^-1 (P = the elements' own blocks)
     upload_pj<double>(a, a->da.pd);
     upload_pj<float>(a, a->da.pf);
+    if (mode) upload_tc(a, mode, true);
     ensure_pt<double>(a, a->da.wd, nrhs);
-    ensure_pt<float>(a, a->da.wf, nrhs);
   }
   // With refinement the solution itself is kept (the FP64 residual uses the
   // plain operator) and each inner correction y is mapped to P^-1 y in
   // complex64, the precision it was solved in; without refinement GMRES runs on
   // Z P^-1 throughout and the result is mapped once at the end.
   const bool pj_outer = pj && !opts->refine;
+  // Z P^-1 x is one product with the fused macromodel matrices [M PJ; D PJ]
   S.op64 = [arr, nrhs, pj_outer](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
-    const void* x = in;
-    if (pj_outer) {
-      cudaError_t e = mm::precond_apply<double>(arr->da, arr->da.pd, nrhs, in, arr->da.wd.pt, s2);
-      if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
-      x = arr->da.wd.pt;
-    }
-    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, x, out, s2);
+    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2, 0, pj_outer);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };
   S.op32 = [arr, nrhs, mode, pj](const void* in, void* out, cudaStream_t s2) -> mm::Status {
-    const void* x = in;
-    if (pj) {
-      cudaError_t e = mm::precond_apply<float>(arr->da, arr->da.pf, nrhs, in, arr->da.wf.pt, s2);
-      if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
-      x = arr->da.wf.pt;
-    }
-    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, x, out, s2, mode);
+    cudaError_t e = mm::matvec<float>(arr->da, arr->da.pf, arr->da.wf, nrhs, in, out, s2, mode, pj);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };

@@ -90,6 +90,10 @@ struct DevPrec {
   std::vector<int> Mp, Kp;
   void* nfb_val = nullptr;     // near-field blocks, dense row-major, at DevArray::nfb_off
   std::vector<void*> PJ;       // per type: block-Jacobi operator (Nh x Nh), uploaded on first use
+  // the right-preconditioned operator's macromodel matrices [M PJ; D PJ] (same
+  // layouts as W and Atc), uploaded with PJ: Z P^-1 x takes one GEMM
+  std::vector<void*> WP;
+  std::vector<void*> AtcP[2];
 };
 
 // Work buffers for one (precision, nrhs) pair.
@@ -155,6 +159,10 @@ struct DevArray {
   int near_mode = 0;                    // 0 blocks; 2 CSR rows (when assembled)
   // autotuned block near-field shape per (right-hand sides, sizeof(R)): (column tile, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
+  // second stream of the product: the near field runs on it, beside the
+  // projection and the convolution (fork / join events on the caller's stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;
@@ -168,9 +176,11 @@ struct DevArray {
 };
 
 // gemm_mode: 0 CUDA-core GEMM; 1 BF16 / 2 FP16 tensor-core GEMM (complex64 only)
+// pre: apply Z P^-1 (the block-Jacobi right-preconditioned operator) through
+// the fused macromodel matrices p.WP / p.AtcP
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st,
-                   int gemm_mode = 0);
+                   int gemm_mode = 0, bool pre = false);
 // y = P^-1 x with P^-1 the per-type block-Jacobi operators (p.PJ).
 template <typename R>
 cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* x, void* y, cudaStream_t st);

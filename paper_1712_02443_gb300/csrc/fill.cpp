@@ -416,6 +416,12 @@ void build_type(TypeModel& tm) {
     tm.PJ.assign(Nh * Nh, cd(0, 0));
     for (int64_t i = 0; i < Nh; ++i) tm.PJ[i * Nh + i] = cd(1, 0);
     lu_solve(ls, tm.PJ, Nh, em.nthreads);
+    // the right-preconditioned operator Z P^-1 applies M and D to P^-1 x:
+    // its macromodel matrices are M PJ and D PJ, formed here in FP64
+    std::vector<cd> MD(2 * Nh * Nh);
+    std::copy(tm.M.begin(), tm.M.end(), MD.begin());
+    std::copy(tm.D.begin(), tm.D.end(), MD.begin() + Nh * Nh);
+    gemm(MD, tm.PJ, tm.WPJ, 2 * Nh, Nh, Nh, em.nthreads);
   }
 }
 

@@ -146,6 +146,7 @@ struct TypeModel {
   std::vector<cd> M, D, T, A, B, GHH, GHE;   // row-major
   std::vector<cd> JE;                         // -A^-1 B (N x N^): scatterer currents from E^, eq. (JABE)
   std::vector<cd> PJ;                         // (D - G^(E^,H^) M)^-1 (N^ x N^): inverse of the element's self block
+  std::vector<cd> WPJ;                        // [M PJ; D PJ] (2 N^ x N^): macromodel of the preconditioned operator
   // near-field blocks with this type as the row type, computed by earlier
   // arrays (identical for every array with the same AIM options): arrays built
   // from the same types, on any thread, reuse them

@@ -960,7 +960,7 @@ cudaError_t kernels_init(DevArray& a) {
 
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st,
-                   int gemm_mode) {
+                   int gemm_mode, bool pre) {
   typedef typename V2<R>::T C;
   const C* x = static_cast<const C*>(xv);
   C* y = static_cast<C*>(yv);
@@ -982,7 +982,8 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   if (sizeof(R) == 4 && gemm_mode != 0) {
     for (int64_t t = 0; t < a.n_types; ++t) {
       if (a.n_of_type[t] == 0) continue;
-      cudaError_t e2 = tc_macro_gemm(gemm_mode == 1, static_cast<const uint16_t*>(p.Atc[gemm_mode - 1][t]), p.Mp[t],
+      const void* At = (pre ? p.AtcP : p.Atc)[gemm_mode - 1][t];
+      cudaError_t e2 = tc_macro_gemm(gemm_mode == 1, static_cast<const uint16_t*>(At), p.Mp[t],
                                      p.Kp[t], (int)a.Nh[t], a.elems[t], (int)a.n_of_type[t], nrhs, a.off,
                                      reinterpret_cast<const float2*>(x), static_cast<uint16_t*>(w.bt), w.bt_cap,
                                      reinterpret_cast<float2*>(u), reinterpret_cast<float2*>(v), w.err, st);
@@ -996,18 +997,67 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const int ncols = (int)(a.n_of_type[t] * nrhs);
     const int64_t big = (int64_t)((2 * Nh + 63) / 64) * ((ncols + 63) / 64);
     constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
+    const C* Wt = static_cast<const C*>((pre ? p.WP : p.W)[t]);
     if (big >= 2 * 152) {
       dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
-      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, 2 * Nh, a.elems[t], ncols,
-                                                     nrhs, a.off, x, u, v);
+      k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(Wt, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x, u, v);
     } else {
       dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
-      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(static_cast<const C*>(p.W[t]), Nh, 2 * Nh, a.elems[t], ncols,
-                                                      nrhs, a.off, x, u, v);
+      k_macro_gemm<R, 32, 32, BKs><<<g, 256, 0, st>>>(Wt, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x, u, v);
     }
     ++nl;
   }
   pr.end(st, nl);
+  // A5: v -= G_NF u (the interpolation then writes y = v - far field), as
+  // dense blocks (columns = pairs x right-hand sides), or as CSR rows when the
+  // array asked for them (DevArray::near_mode); complex128 products take CSR
+  // rows when assembled (FP64 arithmetic on the dense blocks costs more than
+  // streaming the CSR from HBM).  It only needs u, so it runs on the array's
+  // second stream beside A2-A3 and joins before A4.
+  const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
+  const bool nf_blocks = a.nfb_entries > 0 && p.nfb_val != nullptr && !csr;
+  const bool nf = nf_blocks || a.nnz > 0;
+  int tn = 32, ks = 1;
+  if (nf_blocks) {
+    // first product with this shape: tune on st while the spectra are idle
+    const auto key = std::make_pair(nrhs, (int)sizeof(R));
+    auto it = a.near_tune.find(key);
+    if (it == a.near_tune.end())
+      it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
+                                                      (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
+    tn = it->second.first;
+    ks = it->second.second;
+  }
+  cudaStream_t ns = st;
+  if (nf && a.side != nullptr) {
+    e = cudaEventRecord(a.ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    ns = a.side;
+  }
+  if (nf_blocks) {
+    pr.begin(sb + 6, ns);
+    nl = 0;
+    if (tn == 64)
+      near_blocks_launch<R, 64>(a, p, nrhs, u, v, ns, nl, ks);
+    else
+      near_blocks_launch<R, 32>(a, p, nrhs, u, v, ns, nl, ks);
+    pr.end(ns, nl);
+  } else if (a.nnz > 0) {
+    pr.begin(sb + 6, ns);
+    const unsigned blocks = (unsigned)((a.N + 7) / 8);
+    if (nrhs == 1)
+      k_spmv_near1<R><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), u, v);
+    else if (nrhs <= 4)
+      k_spmv_near<R, 4><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, v);
+    else
+      k_spmv_near<R, 8><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, v);
+    pr.end(ns, 1);
+  }
+  if (ns != st) {
+    e = cudaEventRecord(a.ev_join, ns);
+    if (e != cudaSuccess) return e;
+  }
   // A2: projection
   pr.begin(sb + 1, st);
   nl = 0;
@@ -1039,6 +1089,10 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
       spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
   pr.end(st, 1);
   (void)Px;
+  if (ns != st) {
+    e = cudaStreamWaitEvent(st, a.ev_join, 0);
+    if (e != cudaSuccess) return e;
+  }
   // A4: interpolation, y = v - y_ff
   pr.begin(sb + 5, st);
   nl = 0;
@@ -1060,36 +1114,6 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     ++nl;
   }
   pr.end(st, nl);
-  // A5: y -= G_NF u, as dense blocks (columns = pairs x right-hand sides), or
-  // as CSR rows when the array asked for them (DevArray::near_mode)
-  // complex128 products take CSR rows when assembled (FP64 arithmetic on the
-  // dense blocks costs more than streaming the CSR from HBM)
-  const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
-  if (a.nfb_entries > 0 && p.nfb_val != nullptr && !csr) {
-    const auto key = std::make_pair(nrhs, (int)sizeof(R));
-    auto it = a.near_tune.find(key);
-    if (it == a.near_tune.end())
-      it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
-                                                      (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
-    const int tn = it->second.first, ks = it->second.second;
-    pr.begin(sb + 6, st);
-    nl = 0;
-    if (tn == 64)
-      near_blocks_launch<R, 64>(a, p, nrhs, u, y, st, nl, ks);
-    else
-      near_blocks_launch<R, 32>(a, p, nrhs, u, y, st, nl, ks);
-    pr.end(st, nl);
-  } else if (a.nnz > 0) {
-    pr.begin(sb + 6, st);
-    const unsigned blocks = (unsigned)((a.N + 7) / 8);
-    if (nrhs == 1)
-      k_spmv_near1<R><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), u, y);
-    else if (nrhs <= 4)
-      k_spmv_near<R, 4><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
-    else
-      k_spmv_near<R, 8><<<blocks, 256, 0, st>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, y);
-    pr.end(st, 1);
-  }
   return cudaGetLastError();
 }
 
@@ -1122,8 +1146,10 @@ cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* xv, 
 
 template cudaError_t precond_apply<float>(DevArray&, DevPrec<float>&, int, const void*, void*, cudaStream_t);
 template cudaError_t precond_apply<double>(DevArray&, DevPrec<double>&, int, const void*, void*, cudaStream_t);
-template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t, int);
-template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t, int);
+template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t, int,
+                                   bool);
+template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t, int,
+                                    bool);
 template size_t fft_smem_bytes<float>(const DevArray&, int);
 template size_t fft_smem_bytes<double>(const DevArray&, int);
 

@@ -505,6 +505,9 @@ __device__ __forceinline__ double shfl_x(double a, int o) { return __shfl_xor_sy
 __device__ __forceinline__ DAcc shfl_x(DAcc a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)};
 }
+__device__ __forceinline__ Z shfl_idx(Z a, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
 
 // Sums of per-thread values a[q] (q < NQ) over the threads that hold the
 // same column (j = tid % r, tid < S = (blockDim / r) r) into out(q, j) for
@@ -703,8 +706,11 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
     block_norms(w, n0, n1, r, blk, nblk, ws, PN0);
   }
   grid.sync();
-  // phase 2
+  // phase 2 (when r divides the block, a thread keeps one column and sums the
+  // new norm as it updates: the same order as a separate pass)
   reduce_all_partials(P1, k, r, nblk, hs);
+  const bool fuse_norm = all_cols && (int)blockDim.x % r == 0;
+  double nacc = 0;
   for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
     const int j = (int)(t % r);
     Z a = w[t];
@@ -713,22 +719,50 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       zsub_mul(V[(int64_t)i * vs + t], hs[i * r + j], a);
     }
     w[t] = a;
+    nacc = fma(a.x, a.x, fma(a.y, a.y, nacc));
   }
-  __syncthreads();
-  if (all_cols)
-    block_norms_all(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN1);
-  else
-    block_norms(w, n0, n1, r, blk, nblk, ws, PN1);
+  if (fuse_norm) {
+    const double a1[1] = {nacc};
+    column_reduce<1>(a1, r, reinterpret_cast<double*>(ws),
+                     [&](int, int j, double v) { PN1[(int64_t)j * nblk + blk] = v; });
+  } else {
+    __syncthreads();
+    if (all_cols)
+      block_norms_all(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN1);
+    else
+      block_norms(w, n0, n1, r, blk, nblk, ws, PN1);
+  }
   grid.sync();
-  // phase 3: selective reorthogonalisation
+  // phase 3: selective reorthogonalisation.  orth = 2 compares the norms
+  // before and after the first pass, a warp per column (lane-strided sums of
+  // the block partials, then a butterfly: the same order in every block, so
+  // every block takes the same decision)
   int* need = reinterpret_cast<int*>(ws + wsn);   // r flags (shared)
-  __shared__ int any_s;
-  if (threadIdx.x == 0) any_s = 0;
+  __shared__ int any_s, kd_s;
+  if (threadIdx.x == 0) any_s = 0, kd_s = 0;
   __syncthreads();
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    const double b0 = sum_blocks(PN0, j, nblk), b1 = sum_blocks(PN1, j, nblk);
-    need[j] = gd.active[j] && (gd.orth == 3 || (gd.orth == 2 && b1 < 0.5 * b0));
-    if (need[j]) atomicOr(&any_s, 1);
+  if (gd.orth == 2) {
+    for (int j = warp; j < r; j += nw) {
+      double b0 = 0, b1 = 0;
+      for (int b = lane; b < nblk; b += 32) {
+        b0 += PN0[(int64_t)j * nblk + b];
+        b1 += PN1[(int64_t)j * nblk + b];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        b0 += shfl_x(b0, o);
+        b1 += shfl_x(b1, o);
+      }
+      if (lane == 0) {
+        need[j] = gd.active[j] && b1 < 0.5 * b0;
+        if (need[j]) atomicOr(&any_s, 1);
+      }
+    }
+  } else {
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+      need[j] = gd.orth == 3 && gd.active[j];
+      if (need[j]) atomicOr(&any_s, 1);
+    }
   }
   __syncthreads();
   const bool any_reorth = any_s != 0;
@@ -774,63 +808,81 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       block_norms(w, n0, n1, r, blk, nblk, ws, PN2);
     grid.sync();
   }
-  // phase 4: block 0, warp per column
+  // phase 4: block 0, a warp per column.  The lanes load the previous
+  // rotations 32 at a time and pass them on by shuffles, so the serial chain of
+  // rotations waits on no memory; every lane runs the chain (lane 0 stores).
   if (blk == 0) {
     for (int j = warp; j < r; j += nw) {
       if (!gd.active[j]) continue;
+      const Z gk = gd.g[(int64_t)k * r + j];
+      const double tolj = gd.tol[j];
       const double* PNf = (any_reorth && need[j]) ? PN2 : PN1;
       double s2 = 0;
       for (int b = lane; b < nblk; b += 32) s2 += PNf[(int64_t)j * nblk + b];
 #pragma unroll
-      for (int s = 16; s > 0; s >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, s);
+      for (int o = 16; o > 0; o >>= 1) s2 += shfl_x(s2, o);
+      for (int i = lane; i <= k; i += 32) {   // column j of h + h2 lives at hs[i r + j]
+        hs[i * r + j].x += h2s[i * r + j].x;
+        hs[i * r + j].y += h2s[i * r + j].y;
+      }
+      __syncwarp();
+      Z carry = hs[j];   // entry i of the column after rotations 0 .. i-1
+      for (int i0 = 0; i0 < k; i0 += 32) {
+        Z cl = make_double2(1, 0), sl = make_double2(0, 0);
+        if (i0 + lane < k) {
+          cl = gd.cs[(int64_t)(i0 + lane) * r + j];
+          sl = gd.sn[(int64_t)(i0 + lane) * r + j];
+        }
+        const int cnt = min(32, k - i0);
+        for (int ii = 0; ii < cnt; ++ii) {   // rotation i: [[conj c, conj s], [-s, c]]
+          const int i = i0 + ii;
+          const Z c = shfl_idx(cl, ii), sg = shfl_idx(sl, ii);
+          const Z bb = hs[(i + 1) * r + j];
+          const Z t1 = zconjmul(c, carry), t2 = zconjmul(sg, bb);
+          const Z u1 = zmul(sg, carry), u2 = zmul(c, bb);
+          if (lane == 0) hs[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
+          carry = make_double2(u2.x - u1.x, u2.y - u1.y);
+        }
+      }
+      __syncwarp();
+      Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
+      for (int i = lane; i < k; i += 32) H[i] = hs[i * r + j];
       if (lane == 0) {
-        Z* hc = hs;  // column j lives at hs[i r + j]
-        for (int i = 0; i <= k; ++i) {
-          hc[i * r + j].x += h2s[i * r + j].x;
-          hc[i * r + j].y += h2s[i * r + j].y;
-        }
+        const Z a = carry;   // rotated entry k; the new rotation pairs it with hn
         const double hn = sqrt(fmax(0.0, s2));
-        Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
-        for (int i = 0; i < k; ++i) {   // previous rotations [[conj c, conj s], [-s, c]]
-          const Z c = gd.cs[(int64_t)i * r + j], sg = gd.sn[(int64_t)i * r + j];
-          const Z a = hc[i * r + j], bb = hc[(i + 1) * r + j];
-          const Z t1 = zconjmul(c, a), t2 = zconjmul(sg, bb);
-          const Z u1 = zmul(sg, a), u2 = zmul(c, bb);
-          hc[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
-          hc[(i + 1) * r + j] = make_double2(u2.x - u1.x, u2.y - u1.y);
-        }
-        const Z a = hc[k * r + j];   // rotated entry k; the new rotation pairs it with hn
         const double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
-        const Z c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1, 0);
-        const Z sg = den > 0 ? make_double2(hn / den, 0) : make_double2(0, 0);
+        const double inv = den > 0 ? 1.0 / den : 0.0;
+        const Z c = den > 0 ? make_double2(a.x * inv, a.y * inv) : make_double2(1, 0);
+        const Z sg = make_double2(hn * inv, 0);
         gd.cs[(int64_t)k * r + j] = c;
         gd.sn[(int64_t)k * r + j] = sg;
-        for (int i = 0; i < k; ++i) H[i] = hc[i * r + j];
         H[k] = make_double2(den, 0);
-        const Z gk = gd.g[(int64_t)k * r + j];
         const Z sgk = zmul(sg, gk);
         gd.g[(int64_t)(k + 1) * r + j] = make_double2(-sgk.x, -sgk.y);
         gd.g[(int64_t)k * r + j] = zconjmul(c, gk);
         const double res = sqrt(sgk.x * sgk.x + sgk.y * sgk.y);
         gd.res[j] = res;
         gd.kdone[j] = k + 1;
-        const int stop = !(res > gd.tol[j]) || hn == 0.0 || !isfinite(hn);
+        const int stop = !(res > tolj) || hn == 0.0 || !isfinite(hn);
         gd.active[j] = stop ? 0 : 1;
         gd.scale[j] = stop ? 0.0 : 1.0 / hn;
       }
       __syncwarp();
     }
     __syncthreads();
+    // flags for the host: any column still active, the largest Krylov dimension
+    if (threadIdx.x == 0) any_s = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+      if (gd.active[j]) atomicOr(&any_s, 1);
+      atomicMax(&kd_s, gd.kdone[j]);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      int any = 0, kd = 0;
-      for (int j = 0; j < r; ++j) {
-        any |= gd.active[j];
-        kd = max(kd, gd.kdone[j]);
-      }
       *gd.k = k + 1;
-      gd.flag[0] = any;
+      gd.flag[0] = any_s;
       gd.flag[1] = k + 1;
-      gd.flag[2] = kd;
+      gd.flag[2] = kd_s;
       __threadfence_system();
     }
   }

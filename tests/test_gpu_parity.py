@@ -374,3 +374,36 @@ def test_c1_solve_block_jacobi(c1, prec, refine):
     assert st["iterations"] < st0["iterations"], (st["iterations"], st0["iterations"])
     err = np.linalg.norm(E.cpu().numpy() - g["E"]) / np.linalg.norm(g["E"])
     assert err <= 1e-4, err
+
+
+def test_300_rhs_product_and_solve(c1):
+    """More right-hand sides than the Arnoldi block has threads (300 > 256: the
+    per-column reduction path): columns are multiples alpha_j of the golden vector,
+    so by linearity y_j = alpha_j y and E_j = alpha_j E.  Both precisions of the
+    product, and a refined solve of all 300 columns."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    r = 300
+    alpha = (np.arange(1, r + 1) / r) * np.exp(1j * 0.37 * np.arange(r))
+    X = np.outer(g["x"], alpha)
+    for prec in (mm.MM_C128, mm.MM_C64):
+        Y = _apply(c1, X, prec, nrhs=r).reshape(c1.n, r)
+        _close(Y, np.outer(g["y"], alpha), prec)
+    V = torch.from_numpy(np.ascontiguousarray(np.outer(g["V"], alpha))).cuda()
+    E = torch.empty_like(V)
+    st = mm.mm_solve(c1.array, r, V, E, tol=1e-6, restart=50, max_iter=500, precision=mm.MM_C64, refine=1,
+                     precond=1)
+    assert st["converged"] and st["rel_residual"] <= 1e-6
+    ref = np.outer(g["E"], alpha)
+    Eg = E.cpu().numpy().reshape(c1.n, r)
+    assert np.linalg.norm(Eg - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_degenerate_arguments_rejected(ctx, c1):
+    x = torch.zeros(c1.n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(mm.MacroAIMError) as e:
+        mm.mm_apply(c1.array, 0, x, y, mm.MM_C64)            # no right-hand side
+    assert e.value.status == mm.MM_EINVAL
+    with pytest.raises(mm.MacroAIMError) as e:
+        mm.mm_array_create(ctx, [], np.zeros((0, 3)), 0.1, 2, 3, wl.DEFAULT_GRID_PHASE)   # no element
+    assert e.value.status == mm.MM_EINVAL
