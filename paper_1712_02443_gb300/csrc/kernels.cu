@@ -33,6 +33,16 @@ template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
   c.y = a.x * b.y + a.y * b.x;
   return c;
 }
+// acc += a b as four fused multiply-adds (the plain expression compiles to six
+// operations: a product, two FMAs and a separate add per component)
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename T> __device__ __forceinline__ void cmac(T& acc, const T& a, const T& b) {
+  acc.x = fmx(a.x, b.x, acc.x);
+  acc.x = fmx(-a.y, b.y, acc.x);
+  acc.y = fmx(a.x, b.y, acc.y);
+  acc.y = fmx(a.y, b.x, acc.y);
+}
 template <typename T> __device__ __forceinline__ T cadd(T a, T b) {
   T c;
   c.x = a.x + b.x;
@@ -173,8 +183,7 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
-          acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
+          cmac(acc[i][j], a[i], b[j]);
         }
     }
     __syncthreads();
@@ -335,10 +344,10 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
       }
     }
     const int base = g * Ns * RADIX + k;
-    if (RADIX == 2) {
+    if constexpr (RADIX == 2) {
       b[PAD(base)] = cadd(v[0], v[1]);
       b[PAD(base + Ns)] = csub(v[0], v[1]);
-    } else if (RADIX == 4) {
+    } else if constexpr (RADIX == 4) {
       const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
       C jb1;   // -i*b1 forward, +i*b1 inverse
       if (INV) { jb1.x = -b1.y; jb1.y = b1.x; } else { jb1.x = b1.y; jb1.y = -b1.x; }
@@ -346,13 +355,53 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
       b[PAD(base + Ns)] = cadd(a1, jb1);
       b[PAD(base + 2 * Ns)] = csub(a0, b0);
       b[PAD(base + 3 * Ns)] = csub(a1, jb1);
-    } else {
+    } else if constexpr (RADIX % 2 == 0) {
 #pragma unroll
       for (int p = 0; p < RADIX; ++p) {
         C acc = v[0];
 #pragma unroll
         for (int q = 1; q < RADIX; ++q) acc = cadd(acc, cmul(v[q], wr[(p * q) % RADIX]));
         b[PAD(base + p * Ns)] = acc;
+      }
+    } else {
+      // odd radix R: inputs q and R - q meet the roots e^(-/+ i theta) with
+      // theta = 2 pi p q / R, so with t_q = v_q + v_(R-q), d_q = v_q - v_(R-q)
+      // output p is A_p - i B_p and output R - p is A_p + i B_p (forward),
+      // A_p = v_0 + sum_q cos(theta) t_q, B_p = sum_q sin(theta) d_q: real
+      // multiply-adds over half the inputs instead of complex ones over all
+      typedef decltype(v[0].x) Rr;
+      constexpr int H = (RADIX - 1) / 2;
+      C t[H], d[H];
+      C s0 = v[0];
+#pragma unroll
+      for (int q = 1; q <= H; ++q) {
+        t[q - 1] = cadd(v[q], v[RADIX - q]);
+        d[q - 1] = csub(v[q], v[RADIX - q]);
+        s0 = cadd(s0, t[q - 1]);
+      }
+      b[PAD(base)] = s0;
+#pragma unroll
+      for (int p = 1; p <= H; ++p) {
+        C A = v[0], B = czero<C>();
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+          const int m = (p * q) % RADIX;
+          const Rr cs = wr[m].x, sn = INV ? wr[m].y : -wr[m].y;   // cos, sin of 2 pi m / R
+          A.x = fmx(cs, t[q - 1].x, A.x);
+          A.y = fmx(cs, t[q - 1].y, A.y);
+          B.x = fmx(sn, d[q - 1].x, B.x);
+          B.y = fmx(sn, d[q - 1].y, B.y);
+        }
+        C o1, o2;   // forward: o1 = A - i B (output p), o2 = A + i B (output R - p)
+        if (INV) {
+          o1.x = A.x - B.y; o1.y = A.y + B.x;
+          o2.x = A.x + B.y; o2.y = A.y - B.x;
+        } else {
+          o1.x = A.x + B.y; o1.y = A.y - B.x;
+          o2.x = A.x - B.y; o2.y = A.y + B.x;
+        }
+        b[PAD(base + p * Ns)] = o1;
+        b[PAD(base + (RADIX - p) * Ns)] = o2;
       }
     }
   }
@@ -636,7 +685,7 @@ __global__ void __launch_bounds__(256) k_spmv_near1(int64_t N, const int64_t* __
   const int lane = threadIdx.x % 32;
   if (row >= N) return;
   const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-  R ar = 0, ai = 0;
+  C s0 = czero<C>(), s1 = czero<C>();   // two accumulators: shorter FMA chains
   for (int64_t p = p0 + 4 * lane; p < p1; p += 128) {
     const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + p));
     C v[4];
@@ -650,11 +699,12 @@ __global__ void __launch_bounds__(256) k_spmv_near1(int64_t N, const int64_t* __
       for (int q = 0; q < 4; ++q) v[q] = val[p + q];
     }
     const C b0 = u[c4.x], b1 = u[c4.y], b2 = u[c4.z], b3 = u[c4.w];
-    ar += v[0].x * b0.x - v[0].y * b0.y + v[1].x * b1.x - v[1].y * b1.y;
-    ai += v[0].x * b0.y + v[0].y * b0.x + v[1].x * b1.y + v[1].y * b1.x;
-    ar += v[2].x * b2.x - v[2].y * b2.y + v[3].x * b3.x - v[3].y * b3.y;
-    ai += v[2].x * b2.y + v[2].y * b2.x + v[3].x * b3.y + v[3].y * b3.x;
+    cmac(s0, v[0], b0);
+    cmac(s1, v[1], b1);
+    cmac(s0, v[2], b2);
+    cmac(s1, v[3], b3);
   }
+  R ar = s0.x + s1.x, ai = s0.y + s1.y;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
     ar += __shfl_xor_sync(0xffffffffu, ar, s);
@@ -691,8 +741,7 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
       for (int c = 0; c < RC; ++c)
         if (c0 + c < nrhs) {
           const C b = u[cidx + c];
-          acc[c].x += a.x * b.x - a.y * b.y;
-          acc[c].y += a.x * b.y + a.y * b.x;
+          cmac(acc[c], a, b);
         }
     }
 #pragma unroll
@@ -837,8 +886,7 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
-          acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
+          cmac(acc[i][j], a[i], b[j]);
         }
     }
     __syncthreads();

@@ -8,9 +8,11 @@ namespace mm {
 
 typedef double2 Z;
 
-__device__ __forceinline__ Z zfma(Z acc, Z a, Z b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+__device__ __forceinline__ Z zfma(Z acc, Z a, Z b) {   // four fused multiply-adds
+  acc.x = __fma_rn(a.x, b.x, acc.x);
+  acc.x = __fma_rn(-a.y, b.y, acc.x);
+  acc.y = __fma_rn(a.x, b.y, acc.y);
+  acc.y = __fma_rn(a.y, b.x, acc.y);
   return acc;
 }
 

@@ -810,7 +810,9 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   }
   // phase 4: block 0, a warp per column.  The lanes load the previous
   // rotations 32 at a time and pass them on by shuffles, so the serial chain of
-  // rotations waits on no memory; every lane runs the chain (lane 0 stores).
+  // rotations waits on no memory.  Each rotation's four complex products are
+  // taken by lanes 0-3 in one instruction sequence (lane 0: conj(c) h_i,
+  // 1: conj(s) h_i+1, 2: s h_i, 3: c h_i+1) and combined by shuffles.
   if (blk == 0) {
     for (int j = warp; j < r; j += nw) {
       if (!gd.active[j]) continue;
@@ -834,12 +836,15 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
           sl = gd.sn[(int64_t)(i0 + lane) * r + j];
         }
         const int cnt = min(32, k - i0);
+        const int q = lane & 3;
         for (int ii = 0; ii < cnt; ++ii) {   // rotation i: [[conj c, conj s], [-s, c]]
           const int i = i0 + ii;
           const Z c = shfl_idx(cl, ii), sg = shfl_idx(sl, ii);
           const Z bb = hs[(i + 1) * r + j];
-          const Z t1 = zconjmul(c, carry), t2 = zconjmul(sg, bb);
-          const Z u1 = zmul(sg, carry), u2 = zmul(c, bb);
+          Z f = (q == 0 || q == 3) ? c : sg;
+          if (q < 2) f.y = -f.y;
+          const Z pq = zmul(f, (q == 0 || q == 2) ? carry : bb);
+          const Z t1 = shfl_idx(pq, 0), t2 = shfl_idx(pq, 1), u1 = shfl_idx(pq, 2), u2 = shfl_idx(pq, 3);
           if (lane == 0) hs[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
           carry = make_double2(u2.x - u1.x, u2.y - u1.y);
         }
@@ -866,24 +871,23 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
         const int stop = !(res > tolj) || hn == 0.0 || !isfinite(hn);
         gd.active[j] = stop ? 0 : 1;
         gd.scale[j] = stop ? 0.0 : 1.0 / hn;
+        if (!stop) atomicOr(&any_s, 2);   // bit 1: a column stays active
+        atomicMax(&kd_s, k + 1);
       }
       __syncwarp();
     }
     __syncthreads();
-    // flags for the host: any column still active, the largest Krylov dimension
-    if (threadIdx.x == 0) any_s = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-      if (gd.active[j]) atomicOr(&any_s, 1);
-      atomicMax(&kd_s, gd.kdone[j]);
-    }
+    // flags for the host (read after the step's event): any column still
+    // active, the largest Krylov dimension; kd_s stays 0 only when no column
+    // was active on entry, and then comes from the columns' records
+    if (kd_s == 0)
+      for (int j = threadIdx.x; j < r; j += blockDim.x) atomicMax(&kd_s, gd.kdone[j]);
     __syncthreads();
     if (threadIdx.x == 0) {
       *gd.k = k + 1;
-      gd.flag[0] = any_s;
+      gd.flag[0] = (any_s & 2) ? 1 : 0;
       gd.flag[1] = k + 1;
       gd.flag[2] = kd_s;
-      __threadfence_system();
     }
   }
   grid.sync();
