@@ -47,6 +47,7 @@ struct mm_array {
   double* d_ang = nullptr;        // device: theta, phi scratch for the excitation
   int32_t* d_pol = nullptr;
   int ang_cap = 0;
+  cudaEvent_t ang_ev = nullptr;   // the last excitation kernel (it reads d_ang, d_pol)
   void* hx = nullptr;             // device staging for mm_apply_host
   void* hy = nullptr;
   size_t h_cap = 0;
@@ -361,6 +362,7 @@ mm_array::~mm_array() {
   for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
+  if (ang_ev) cudaEventDestroy(ang_ev);
   for (cudaEvent_t e : {da.ev_fork, da.ev_join})
     if (e) cudaEventDestroy(e);
 }
@@ -903,11 +905,15 @@ mm_status mm_rhs_planewave(mm_array* a, int32_t nrhs, const double* theta, const
     CU(cudaMalloc(&a->d_pol, sizeof(int32_t) * nrhs));
     a->ang_cap = nrhs;
   }
+  // the copies come from pageable staging (copied out before the calls
+  // return), after the previous excitation kernel, on whatever stream it ran
+  if (a->ang_ev) CU(cudaStreamWaitEvent(st, a->ang_ev, 0));
   std::vector<double> ang(2 * nrhs);
   std::copy(theta, theta + nrhs, ang.begin());
   std::copy(phi, phi + nrhs, ang.begin() + nrhs);
+  std::vector<int32_t> pl(pol, pol + nrhs);
   CU(cudaMemcpyAsync(a->d_ang, ang.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(a->d_pol, pol, sizeof(int32_t) * nrhs, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(a->d_pol, pl.data(), sizeof(int32_t) * nrhs, cudaMemcpyHostToDevice, st));
   mm::Rule r7 = mm::rule_tri7();
   mm::QuadRule q;
   q.n = r7.n();
@@ -924,8 +930,8 @@ mm_status mm_rhs_planewave(mm_array* a, int32_t nrhs, const double* theta, const
   else
     return fail(ctx, MM_EINVAL, "unknown precision");
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("excitation: ") + cudaGetErrorString(e));
-  // the host staging of the angles must stay valid until the copies ran
-  CU(cudaStreamSynchronize(st));
+  if (!a->ang_ev) CU(cudaEventCreateWithFlags(&a->ang_ev, cudaEventDisableTiming));
+  CU(cudaEventRecord(a->ang_ev, st));
   return MM_OK;
   API_CATCH(ctx)
 }

@@ -157,6 +157,8 @@ struct GmresDev {
   Z* H;            // r (m+1) m, column j, Arnoldi column k: H[(j m + k)(m+1) + i]
   Z* y;            // m r
   int* flag;       // mapped host memory: [0] any column active, [1] k, [2] max kdone
+  double* hres;    // mapped host memory: max over active columns of res / tol after the
+                   // step (-1: not reported), for the host's convergence forecast
   int m, r;
   int orth;        // 1 one Gram-Schmidt pass, 2 selective second pass, 3 two passes
 };
@@ -362,6 +364,7 @@ __global__ void k_cycle_init(GmresDev gd, const double* __restrict__ PN, int nbl
     gd.flag[0] = any;
     gd.flag[1] = 0;
     gd.flag[2] = 0;
+    *gd.hres = -1.0;
     __threadfence_system();
   }
 }
@@ -434,6 +437,7 @@ __global__ void k_givens(GmresDev gd, const Z* __restrict__ P1, const Z* __restr
     gd.flag[0] = any;
     gd.flag[1] = k + 1;
     gd.flag[2] = kd;
+    *gd.hres = -1.0;
     __threadfence_system();
   }
 }
@@ -738,8 +742,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   // the block partials, then a butterfly: the same order in every block, so
   // every block takes the same decision)
   int* need = reinterpret_cast<int*>(ws + wsn);   // r flags (shared)
-  __shared__ int any_s, kd_s;
-  if (threadIdx.x == 0) any_s = 0, kd_s = 0;
+  __shared__ int any_s, kd_s, rq_s;
+  if (threadIdx.x == 0) any_s = 0, kd_s = 0, rq_s = 0;
   __syncthreads();
   if (gd.orth == 2) {
     for (int j = warp; j < r; j += nw) {
@@ -871,7 +875,11 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
         const int stop = !(res > tolj) || hn == 0.0 || !isfinite(hn);
         gd.active[j] = stop ? 0 : 1;
         gd.scale[j] = stop ? 0.0 : 1.0 / hn;
-        if (!stop) atomicOr(&any_s, 2);   // bit 1: a column stays active
+        if (!stop) {
+          atomicOr(&any_s, 2);   // bit 1: a column stays active
+          // res / tol >= 0: its float bits order like the values
+          atomicMax(&rq_s, __float_as_int((float)fmin(res / tolj, 1e30)));
+        }
         atomicMax(&kd_s, k + 1);
       }
       __syncwarp();
@@ -888,6 +896,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       gd.flag[0] = (any_s & 2) ? 1 : 0;
       gd.flag[1] = k + 1;
       gd.flag[2] = kd_s;
+      *gd.hres = (any_s & 2) ? (double)__int_as_float(rq_s) : -1.0;
     }
   }
   grid.sync();
@@ -990,10 +999,11 @@ Status Solver::ensure(int64_t N, int r, int m) {
     g.y = reinterpret_cast<Z*>(base + o_y);
     g.m = m;
     g.r = r;
-    MM_CK(cudaHostAlloc(&flag_h_, sizeof(int) * 4, cudaHostAllocMapped));
+    MM_CK(cudaHostAlloc(&flag_h_, sizeof(int) * 4 + sizeof(double), cudaHostAllocMapped));
     void* fd = nullptr;
     MM_CK(cudaHostGetDevicePointer(&fd, flag_h_, 0));
     g.flag = static_cast<int*>(fd);
+    g.hres = reinterpret_cast<double*>(static_cast<char*>(fd) + sizeof(int) * 4);
     MM_CK(cudaEventCreateWithFlags(&ev_[0], cudaEventDisableTiming));
     MM_CK(cudaEventCreateWithFlags(&ev_[1], cudaEventDisableTiming));
   }
@@ -1067,6 +1077,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
   GmresDev gd = *reinterpret_cast<GmresDev*>(gdev_);
   gd.orth = orth;
   volatile int* flag = static_cast<volatile int*>(flag_h_);
+  volatile double* hres = reinterpret_cast<volatile double*>(static_cast<char*>(flag_h_) + sizeof(int) * 4);
   iters = 0;
   res.assign(r, 0.0);
   MM_CK(cudaMemcpyAsync(gd.tol, tol_abs.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
@@ -1088,8 +1099,11 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     k_norm_partial<<<dim3(nblk_, r), 256, 0, st>>>(w, N, r, nblk_, static_cast<double*>(PN_));
     k_cycle_init<<<1, 256, 0, st>>>(gd, static_cast<const double*>(PN_), nblk_);
     MM_CK(cudaGetLastError());
-    MM_CK(cudaStreamSynchronize(st));
-    if (!flag[0] || iters >= max_iter) {
+    // The cycle's first steps are launched without waiting for the initial
+    // residual: a cycle whose columns already meet their targets has no active
+    // column, its steps change nothing, and the first check stops it.
+    if (iters >= max_iter) {
+      MM_CK(cudaStreamSynchronize(st));
       std::vector<double> rr(r);
       MM_CK(cudaMemcpy(rr.data(), gd.res, sizeof(double) * r, cudaMemcpyDeviceToHost));
       for (int j = 0; j < r; ++j) {
@@ -1100,6 +1114,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     }
     bool stopped = false;
     int launched = 0;
+    double q_last = -1.0;   // residual / target at the previous check
     // first basis vector V[0] = r0/||r0|| and the operator input
     if (prec == MM_C128)
       k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
@@ -1163,6 +1178,18 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
           stopped = true;
           break;
         }
+        // Steps run one ahead of the host's check, so the step after the last
+        // one would be launched for nothing.  When the residual's decay over
+        // the last step says this step may end the cycle, wait for it first.
+        const double q = *hres;
+        if (q > 0 && q_last > 0 && q * (q / q_last) <= 2.0) {
+          MM_CK(cudaEventSynchronize(ev_[it & 1]));
+          if (!flag[0]) {
+            stopped = true;
+            break;
+          }
+        }
+        q_last = *hres;
       }
     }
     MM_CK(cudaEventSynchronize(ev_[(launched - 1) & 1]));
