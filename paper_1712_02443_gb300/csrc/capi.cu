@@ -362,8 +362,9 @@ mm_array::~mm_array() {
   for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
+  if (da.chain) cudaStreamDestroy(da.chain);
   if (ang_ev) cudaEventDestroy(ang_ev);
-  for (cudaEvent_t e : {da.ev_fork, da.ev_join})
+  for (cudaEvent_t e : {da.ev_fork, da.ev_join, da.ev_done})
     if (e) cudaEventDestroy(e);
 }
 
@@ -724,9 +725,13 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     // the near field's own stream (MACROAIM_NEAR_OVERLAP=0: one stream, in order)
     const char* ov = std::getenv("MACROAIM_NEAR_OVERLAP");
     if ((da.nfb_entries > 0 || da.nnz > 0) && !(ov && std::string(ov) == "0")) {
-      CU(cudaStreamCreateWithFlags(&da.side, cudaStreamNonBlocking));
+      int lo = 0, hi = 0;   // numerically lower = served first
+      CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CU(cudaStreamCreateWithPriority(&da.side, cudaStreamNonBlocking, lo));
+      CU(cudaStreamCreateWithPriority(&da.chain, cudaStreamNonBlocking, hi));
       CU(cudaEventCreateWithFlags(&da.ev_fork, cudaEventDisableTiming));
       CU(cudaEventCreateWithFlags(&da.ev_join, cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&da.ev_done, cudaEventDisableTiming));
     }
   }
   *out = a.release();

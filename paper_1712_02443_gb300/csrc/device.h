@@ -159,10 +159,11 @@ struct DevArray {
   int near_mode = 0;                    // 0 blocks; 2 CSR rows (when assembled)
   // autotuned block near-field shape per (right-hand sides, sizeof(R)): (column tile, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
-  // second stream of the product: the near field runs on it, beside the
-  // projection and the convolution (fork / join events on the caller's stream)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // streams of the product: the near field runs on `side` beside the far-field
+  // chain (projection, convolution, interpolation) on `chain`, which has the
+  // higher priority; fork / join events order both against the caller's stream
+  cudaStream_t side = nullptr, chain = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
   FftPlan px, py;
   DevPrec<float> pf;
   DevPrec<double> pd;

@@ -1076,13 +1076,36 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     tn = it->second.first;
     ks = it->second.second;
   }
-  cudaStream_t ns = st;
+  // ns: the near field's stream; cs: the far-field chain's, of higher priority
+  // so that the block scheduler serves the chain first and the near field
+  // fills the SMs it leaves idle
+  cudaStream_t ns = st, cs = st;
   if (nf && a.side != nullptr) {
     e = cudaEventRecord(a.ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(a.chain, a.ev_fork, 0);
     if (e != cudaSuccess) return e;
     ns = a.side;
+    cs = a.chain;
   }
+  // A2: projection
+  pr.begin(sb + 1, cs);
+  nl = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
+    if (nrhs == 1)
+      k_project<R, 1><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh, cs>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+    else
+      k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+    ++nl;
+  }
+  pr.end(cs, nl);
+  // A5 on its stream, launched after the projection so that the chain's first
+  // kernel is dispatched ahead of it
   if (nf_blocks) {
     pr.begin(sb + 6, ns);
     nl = 0;
@@ -1106,43 +1129,27 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     e = cudaEventRecord(a.ev_join, ns);
     if (e != cudaSuccess) return e;
   }
-  // A2: projection
-  pr.begin(sb + 1, st);
-  nl = 0;
-  for (int64_t t = 0; t < a.n_types; ++t) {
-    if (a.n_of_type[t] == 0) continue;
-    const int Nh = (int)a.Nh[t];
-    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
-    if (nrhs == 1)
-      k_project<R, 1><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh, st>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
-    else
-      k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, st>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
-    ++nl;
-  }
-  pr.end(st, nl);
   const size_t slim = 96 * 1024;
   // A3: FFT convolution
-  pr.begin(sb + 2, st);
-  k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
+  pr.begin(sb + 2, cs);
+  k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
       grid, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), spec);
-  pr.end(st, 1);
-  pr.begin(sb + 3, st);
-  k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), st>>>(
+  pr.end(cs, 1);
+  pr.begin(sb + 3, cs);
+  k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), cs>>>(
       spec, Nx, Py, Pz, a.px, static_cast<const C*>(p.twx), static_cast<const C*>(p.Ghat));
-  pr.end(st, 1);
-  pr.begin(sb + 4, st);
-  k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), st>>>(
+  pr.end(cs, 1);
+  pr.begin(sb + 4, cs);
+  k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
       spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
-  pr.end(st, 1);
+  pr.end(cs, 1);
   (void)Px;
   if (ns != st) {
-    e = cudaStreamWaitEvent(st, a.ev_join, 0);
+    e = cudaStreamWaitEvent(cs, a.ev_join, 0);
     if (e != cudaSuccess) return e;
   }
   // A4: interpolation, y = v - y_ff
-  pr.begin(sb + 5, st);
+  pr.begin(sb + 5, cs);
   nl = 0;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
@@ -1150,18 +1157,23 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
     const size_t sm = 4 * rc * nodes * sizeof(C);
     if (rc >= 8)
-      k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+      k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
           p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
           y);
     else
-      k_interp<R, 1><<<(unsigned)a.n_of_type[t], 256, sm, st>>>(
+      k_interp<R, 1><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
           p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
           y);
     ++nl;
   }
-  pr.end(st, nl);
+  pr.end(cs, nl);
+  if (cs != st) {
+    e = cudaEventRecord(a.ev_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, a.ev_done, 0);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

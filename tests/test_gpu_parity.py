@@ -407,3 +407,30 @@ def test_degenerate_arguments_rejected(ctx, c1):
     with pytest.raises(mm.MacroAIMError) as e:
         mm.mm_array_create(ctx, [], np.zeros((0, 3)), 0.1, 2, 3, wl.DEFAULT_GRID_PHASE)   # no element
     assert e.value.status == mm.MM_EINVAL
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C128])
+def test_near_field_stream_matches_in_order(ctx, monkeypatch, prec):
+    """The near field runs on its own stream beside the far-field chain (joined
+    before the interpolation); the same array built with one in-order stream
+    (MACROAIM_NEAR_OVERLAP=0) gives the same product up to the summation order
+    of the near field's atomic adds.  Several products back to back, so that a
+    missing join between consecutive products would show."""
+    outs = []
+    for ov in ("1", "0"):
+        monkeypatch.setenv("MACROAIM_NEAR_OVERLAP", ov)
+        la = loop_array(ctx, 4, 4)
+        try:
+            X = wl.random_cvec(la.n, 0, 21, nrhs=2)
+            xd = torch.from_numpy(np.ascontiguousarray(X)).to(DT[prec]).cuda()
+            ys = [torch.empty_like(xd) for _ in range(3)]
+            for yk in ys:
+                mm.mm_apply(la.array, 2, xd, yk, prec, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            outs.append([yk.cpu().numpy().astype(np.complex128) for yk in ys])
+        finally:
+            la.close()
+    ref = outs[1][0]
+    for y in outs[0] + outs[1]:
+        rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        assert rel <= (1e-6 if prec == mm.MM_C64 else 1e-13), rel
