@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <cstdio>
 #include <mutex>
 #include <new>
 #include <string>
@@ -359,7 +360,7 @@ mm_array::~mm_array() {
   for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist,
                   (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
-  for (void* q : {da.nfg_dev, (void*)da.nfg_pairs})
+  for (void* q : {da.nfg_dev, (void*)da.nfg_poff})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
   if (da.chain) cudaStreamDestroy(da.chain);
@@ -712,12 +713,25 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
           da.nfg.push_back(ng);
         }
         static_assert(sizeof(mm::DevArray::NfGroup) == 24, "group record layout shared with the kernel");
-        da.nfg_pairs = dev_upload(allp.data(), allp.size(), acc);
+        std::vector<longlong2> poff(allp.size());
+        for (size_t i = 0; i < allp.size(); ++i) {
+          poff[i].x = ah.off[allp[i].x];
+          poff[i].y = ah.off[allp[i].y];
+        }
+        da.nfg_poff = dev_upload(poff.data(), poff.size(), acc);
         da.nfg_dev = dev_upload(reinterpret_cast<const unsigned char*>(da.nfg.data()),
                                 sizeof(mm::DevArray::NfGroup) * da.nfg.size(), acc);
         // tuning override: MACROAIM_NEAR=csr (CSR rows, when assembled)
         if (const char* nm = std::getenv("MACROAIM_NEAR"))
           if (std::string(nm) == "csr") da.near_mode = 2;
+        // tuning override: MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block kernel's shape
+        if (const char* ns = std::getenv("MACROAIM_NEAR_SHAPE")) {
+          int sh = -1, ks = 1;
+          if (std::sscanf(ns, "%d,%d", &sh, &ks) >= 1 && sh >= 0 && sh < 3 && ks >= 1 && ks <= 16) {
+            da.near_force_shape = sh;
+            da.near_force_ks = ks;
+          }
+        }
       }
     }
     upload_precision<float>(a.get(), da.pf);

@@ -151,14 +151,15 @@ struct DevArray {
   struct NfGroup {                      // the element pairs coupled by one block (host mirror)
     int q = 0;                          // block id
     int Na = 0;                         // its rows
-    int64_t first_pair = 0, npairs = 0; // range in nfg_pairs
+    int64_t first_pair = 0, npairs = 0; // range in nfg_poff
   };
   std::vector<NfGroup> nfg;
   void* nfg_dev = nullptr;              // device copy of nfg (same layout)
-  int2* nfg_pairs = nullptr;            // (row element, column element), grouped by block
+  longlong2* nfg_poff = nullptr;        // per pair: unknown offsets of (row element, column element), grouped by block
   int near_mode = 0;                    // 0 blocks; 2 CSR rows (when assembled)
-  // autotuned block near-field shape per (right-hand sides, sizeof(R)): (column tile, k split)
+  // autotuned block near-field shape per (right-hand sides, sizeof(R)): (kernel shape, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
+  int near_force_shape = -1, near_force_ks = 1;   // MACROAIM_NEAR_SHAPE="shape,ksplit": no tuning
   // streams of the product: the near field runs on `side` beside the far-field
   // chain (projection, convolution, interpolation) on `chain`, which has the
   // higher priority; fork / join events order both against the caller's stream

@@ -771,62 +771,84 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
 // columns are (pair, right-hand side), n = p nrhs + c, so one right-hand side
 // still fills the tiles.  Tiles are numbered group by
 // group (group = the pairs of one block: row tiles x column tiles); a CTA
-// finds its group by a prefix over the group sizes.  A row element has up to
-// one pair per lattice offset, so its outputs receive several block products:
-// they are accumulated with atomic adds (summation order not fixed).
+// finds its group by a prefix over the group sizes, staged in shared memory
+// 128 groups at a time.  A row element has up to one pair per lattice offset,
+// so its outputs receive several block products: they are accumulated with
+// atomic adds (summation order not fixed).  The CTA's set-up loads are issued
+// in as few dependent rounds as possible (the CTAs do only a few k tiles each).
 struct NearGroupDev {
   int q, Na;
   int64_t first_pair, npairs;
 };
 
-template <typename R, int TN>
-__global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
-    const NearGroupDev* __restrict__ groups, int ngroups, const int2* __restrict__ pairs,
+template <typename R, int TN, int MB>
+__global__ void __launch_bounds__(16 * (TN / 4), MB) k_near_blocks(
+    const NearGroupDev* __restrict__ groups, int ngroups, const longlong2* __restrict__ poff,
     const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
     int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int32_t* __restrict__ perm,
-    const int32_t* __restrict__ bpa, const int32_t* __restrict__ bpb, const int64_t* __restrict__ off, int nrhs,
+    const int32_t* __restrict__ bpa, const int32_t* __restrict__ bpb, int nrhs,
     int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
   typedef typename V2<R>::T C;
   constexpr int TM = 64, TK = 16, TX = TN / 4, NT = 16 * TX;
   __shared__ C As[TK][TM + 1];
   __shared__ C Bs[TK][TN + 1];
   __shared__ int64_t cin[TN], cout[TN];   // u / y index of row 0 of each column, -1 past the end
+  __shared__ int64_t s_nt[NT];            // tiles of up to NT groups (prefix search)
   __shared__ int s_g, s_mt;
-  __shared__ int64_t s_ct;
+  __shared__ int64_t s_ct, s_t;
+  __shared__ NearGroupDev s_gr;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const int part = blockIdx.y;   // which of the ksplit shares of the row tile's k tiles
   if (tid == 0) {
-    int64_t t = blockIdx.x;
-    int g = 0;
-    for (; g < ngroups; ++g) {
-      const int64_t nct = (groups[g].npairs * nrhs + TN - 1) / TN;
-      const int64_t nt = nct * ((groups[g].Na + TM - 1) / TM);
-      if (t < nt) {
-        s_mt = (int)(t / nct);
-        s_ct = t % nct;
-        break;
-      }
-      t -= nt;
+    s_g = ngroups;
+    s_t = blockIdx.x;
+  }
+  for (int g0 = 0; g0 < ngroups; g0 += NT) {
+    __syncthreads();
+    if (s_g < ngroups) break;   // found in an earlier chunk
+    const int g = g0 + tid;
+    if (g < ngroups) {
+      const NearGroupDev gg = groups[g];
+      s_nt[tid] = ((gg.npairs * nrhs + TN - 1) / TN) * ((gg.Na + TM - 1) / TM);
     }
-    s_g = g;
+    __syncthreads();
+    if (tid == 0) {
+      int64_t t = s_t;
+      for (int q = 0; q < NT && g0 + q < ngroups; ++q) {
+        if (t < s_nt[q]) {
+          const NearGroupDev gg = groups[g0 + q];
+          const int64_t nct = (gg.npairs * nrhs + TN - 1) / TN;
+          s_gr = gg;
+          s_g = g0 + q;
+          s_mt = (int)(t / nct);
+          s_ct = t % nct;
+          break;
+        }
+        t -= s_nt[q];
+      }
+      s_t = t;
+    }
   }
   __syncthreads();
   if (s_g >= ngroups) return;
-  const NearGroupDev gr = groups[s_g];
-  const int mt = s_mt, q = gr.q, Na = gr.Na, Nb = bnb[q];
-  const int m0 = mt * TM;
-  const int64_t ncol = gr.npairs * nrhs, n0 = s_ct * TN;
+  const NearGroupDev gr = s_gr;
+  const int mt = s_mt, q = gr.q, Na = gr.Na;
+  // one round of loads that depend only on the block and the tile
+  const int Nb = bnb[q];
   const C* Bq = vals + boff[q];
   const int32_t* pa = perm + bpa[q];   // the block's rows and columns are in anchor order
   const int32_t* pb = perm + bpb[q];
+  const int ea = tptr[q * nmt + mt], eb = tptr[q * nmt + mt + 1];
+  const int m0 = mt * TM;
+  const int64_t ncol = gr.npairs * nrhs, n0 = s_ct * TN;
   for (int cc = tid; cc < TN; cc += NT) {
     const int64_t n = n0 + cc;
     if (n < ncol) {
       const int64_t pp = n / nrhs;
       const int c = (int)(n - pp * nrhs);
-      const int2 pr = pairs[gr.first_pair + pp];
-      cin[cc] = off[pr.y] * nrhs + c;
-      cout[cc] = off[pr.x] * nrhs + c;
+      const longlong2 pr = poff[gr.first_pair + pp];   // (row element, column element) unknown offsets
+      cin[cc] = pr.y * nrhs + c;
+      cout[cc] = pr.x * nrhs + c;
     } else {
       cin[cc] = -1;
       cout[cc] = -1;
@@ -839,7 +861,6 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
     for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
   __syncthreads();
   const bool kfast = nrhs < 16;   // few right-hand sides: a column's rows are the contiguous run
-  const int ea = tptr[q * nmt + mt], eb = tptr[q * nmt + mt + 1];
   const int e0 = ea + (int)((int64_t)(eb - ea) * part / ksplit), e1 = ea + (int)((int64_t)(eb - ea) * (part + 1) / ksplit);
   if (e0 == e1) return;   // nothing in this share
   // the next k tile is loaded into registers while the current one is used
@@ -907,7 +928,7 @@ __global__ void __launch_bounds__(16 * (TN / 4)) k_near_blocks(
   }
 }
 
-template <typename R, int TN>
+template <typename R, int TN, int MB>
 static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
                                typename V2<R>::T* y, cudaStream_t st, int& nl, int ksplit) {
   int64_t tiles = 0;
@@ -915,15 +936,30 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
   if (tiles == 0) return;
   // ksplit > 1 splits each row tile's k tiles over several CTAs (the outputs are
   // accumulated atomically anyway): more CTAs when the output tiles are few
-  k_near_blocks<R, TN><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
-      reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_pairs,
+  k_near_blocks<R, TN, MB><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
+      reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_poff,
       static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, a.nfb_nmt, a.nfb_tptr, a.nfb_tlist,
-      a.nfb_perm, a.nfb_pa, a.nfb_pb, a.off, nrhs, ksplit, u, y);
+      a.nfb_perm, a.nfb_pa, a.nfb_pb, nrhs, ksplit, u, y);
   ++nl;
 }
 
+// Kernel shapes of the block near field: 0 = 32-column tiles, 1 = 32-column
+// tiles compiled for five CTAs per SM (fewer registers, more warps to hide the
+// loads), 2 = 64-column tiles.
+constexpr int kNearShapes = 3;
+template <typename R>
+static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
+                              const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks) {
+  if (shape == 2)
+    near_blocks_launch<R, 64, 1>(a, p, nrhs, u, y, st, nl, ks);
+  else if (shape == 1)
+    near_blocks_launch<R, 32, 5>(a, p, nrhs, u, y, st, nl, ks);
+  else
+    near_blocks_launch<R, 32, 1>(a, p, nrhs, u, y, st, nl, ks);
+}
+
 // Autotuner of the block near field: on the first product of an array with a
-// given right-hand-side count and precision, each (column tile, k split) shape
+// given right-hand-side count and precision, each (kernel shape, k split) pair
 // is timed with CUDA events (one warm-up, three timed launches) writing into a
 // scratch buffer (the spectra, idle at this point of the product), and the
 // fastest is kept for that array.  Without a large enough scratch buffer the
@@ -934,7 +970,7 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
                                          size_t scratch_elems, cudaStream_t st) {
   int64_t cols = 0;
   for (const auto& g : a.nfg) cols += g.npairs * nrhs;
-  std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 64 : 32, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
+  std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 2 : 0, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
   if (scratch == nullptr || scratch_elems < (size_t)a.N * nrhs) return best;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
@@ -943,15 +979,10 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
     return best;
   }
   float best_ms = 1e30f;
-  for (int tn : {32, 64})
+  for (int tn = 0; tn < kNearShapes; ++tn)
     for (int ks : {1, 2, 4}) {
       int nl = 0;
-      auto run = [&]() {
-        if (tn == 64)
-          near_blocks_launch<R, 64>(a, p, nrhs, u, scratch, st, nl, ks);
-        else
-          near_blocks_launch<R, 32>(a, p, nrhs, u, scratch, st, nl, ks);
-      };
+      auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks); };
       run();
       cudaEventRecord(e0, st);
       for (int rep = 0; rep < 3; ++rep) run();
@@ -1065,16 +1096,22 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
   const bool nf_blocks = a.nfb_entries > 0 && p.nfb_val != nullptr && !csr;
   const bool nf = nf_blocks || a.nnz > 0;
-  int tn = 32, ks = 1;
+  int tn = 0, ks = 1;   // kernel shape (near_shape_launch), k split
   if (nf_blocks) {
     // first product with this shape: tune on st while the spectra are idle
     const auto key = std::make_pair(nrhs, (int)sizeof(R));
     auto it = a.near_tune.find(key);
+    if (it == a.near_tune.end() && a.near_force_shape >= 0)
+      it = a.near_tune.emplace(key, std::make_pair(a.near_force_shape, a.near_force_ks)).first;
     if (it == a.near_tune.end())
       it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
                                                       (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
     tn = it->second.first;
     ks = it->second.second;
+    if (a.near_force_shape >= 0) {
+      tn = a.near_force_shape;
+      ks = a.near_force_ks;
+    }
   }
   // ns: the near field's stream; cs: the far-field chain's, of higher priority
   // so that the block scheduler serves the chain first and the near field
@@ -1109,10 +1146,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   if (nf_blocks) {
     pr.begin(sb + 6, ns);
     nl = 0;
-    if (tn == 64)
-      near_blocks_launch<R, 64>(a, p, nrhs, u, v, ns, nl, ks);
-    else
-      near_blocks_launch<R, 32>(a, p, nrhs, u, v, ns, nl, ks);
+    near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks);
     pr.end(ns, nl);
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, ns);
