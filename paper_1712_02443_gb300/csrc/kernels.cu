@@ -410,8 +410,123 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
 // Warp-level Stockham FFT of one line held in shared memory (buffers a, b of
 // length L); returns the buffer that holds the result.
 
+// Warp FFT of a line of L = 32 RR points kept in registers (complex64 lines).
+// With n = n1 + 32 n2 and k = k2 + RR k1 (n1, k1 < 32; n2, k2 < RR):
+//   X[k2 + RR k1] = sum_n1 W_32^(n1 k1) [W_L^(n1 k2) sum_n2 x[n1 + 32 n2] W_RR^(n2 k2)],
+// so lane n1 takes the RR-point DFT of its own points, multiplies by W_L^(n1 k2),
+// and the 32-point DFTs over n1 run across the lanes as five radix-2
+// decimation-in-frequency butterflies through shuffles, which leave lane l with
+// k1 = bit-reverse(l).  tw holds W_L^i = exp(-2 pi i / L) (conjugated for the
+// inverse); W_RR^m = tw[32 m] and W_32^m = tw[RR m].  The RR-point DFT pairs
+// inputs q and RR - q (real cos / sin multiply-adds, as in the odd-radix
+// Stockham stage).  a and dst may be the same buffer: every lane has read its
+// points before the first shuffle, and writes after the last one.
+template <typename C, int RR, bool INV>
+__device__ __forceinline__ void warp_fft_reg(const C* a, C* dst, const C* __restrict__ tw, int lane) {
+  typedef decltype(a[0].x) Rr;
+  C y[RR];
+  {
+    C x[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) x[r] = a[PAD(lane + 32 * r)];
+    if constexpr (RR == 1) {
+      y[0] = x[0];
+    } else {
+      constexpr int H = (RR - 1) / 2;
+      C t[H > 0 ? H : 1], d[H > 0 ? H : 1];
+      C s0 = x[0];
+#pragma unroll
+      for (int q = 1; q <= H; ++q) {
+        t[q - 1] = cadd(x[q], x[RR - q]);
+        d[q - 1] = csub(x[q], x[RR - q]);
+        s0 = cadd(s0, t[q - 1]);
+      }
+      if constexpr (RR % 2 == 0) s0 = cadd(s0, x[RR / 2]);
+      y[0] = s0;
+#pragma unroll
+      for (int p = 1; 2 * p <= RR; ++p) {
+        C A = x[0], B = czero<C>();
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+          const C w = tw[32 * ((p * q) % RR)];
+          const Rr cs = w.x, sn = -w.y;   // cos, sin of 2 pi m / RR
+          A.x = fmx(cs, t[q - 1].x, A.x);
+          A.y = fmx(cs, t[q - 1].y, A.y);
+          B.x = fmx(sn, d[q - 1].x, B.x);
+          B.y = fmx(sn, d[q - 1].y, B.y);
+        }
+        if constexpr (RR % 2 == 0) {
+          if (p & 1) A = csub(A, x[RR / 2]);
+          else A = cadd(A, x[RR / 2]);
+        }
+        if (2 * p == RR) {
+          y[p] = A;   // sin(pi q) = 0
+        } else {
+          C o1, o2;   // forward: A - i B (output p), A + i B (output RR - p)
+          if (INV) {
+            o1.x = A.x - B.y; o1.y = A.y + B.x;
+            o2.x = A.x + B.y; o2.y = A.y - B.x;
+          } else {
+            o1.x = A.x + B.y; o1.y = A.y - B.x;
+            o2.x = A.x - B.y; o2.y = A.y + B.x;
+          }
+          y[p] = o1;
+          y[RR - p] = o2;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k2 = 1; k2 < RR; ++k2) {
+    C w = tw[lane * k2];
+    if (INV) w.y = -w.y;
+    y[k2] = cmul(y[k2], w);
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+    C w = tw[RR * (lane & (h - 1)) * (16 / h)];   // W_(2h)^j, j = lane mod h
+    if (INV) w.y = -w.y;
+    if (!up) {
+      w.x = 1;
+      w.y = 0;
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < RR; ++k2) {
+      C o;
+      o.x = __shfl_xor_sync(0xffffffffu, y[k2].x, h);
+      o.y = __shfl_xor_sync(0xffffffffu, y[k2].y, h);
+      const C sd = up ? csub(o, y[k2]) : cadd(y[k2], o);
+      y[k2] = h == 1 ? sd : cmul(sd, w);
+    }
+  }
+  __syncwarp();
+  const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+  for (int k2 = 0; k2 < RR; ++k2) dst[PAD(k2 + RR * k1)] = y[k2];
+  __syncwarp();
+}
+
 template <typename C, bool INV>
 __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
+  if constexpr (sizeof(C) == 8) {
+    // complex64 lines of 32 RR points (RR <= 8) in registers; the result goes
+    // where the Stockham stages would leave it (a after an even stage count)
+    if ((P.L & 31) == 0 && P.L <= 256 && P.nst > 0) {
+      C* dst = (P.nst % 2 == 0) ? a : b;
+      switch (P.L >> 5) {
+        case 1: warp_fft_reg<C, 1, INV>(a, dst, tw, lane); break;
+        case 2: warp_fft_reg<C, 2, INV>(a, dst, tw, lane); break;
+        case 3: warp_fft_reg<C, 3, INV>(a, dst, tw, lane); break;
+        case 4: warp_fft_reg<C, 4, INV>(a, dst, tw, lane); break;
+        case 5: warp_fft_reg<C, 5, INV>(a, dst, tw, lane); break;
+        case 6: warp_fft_reg<C, 6, INV>(a, dst, tw, lane); break;
+        case 7: warp_fft_reg<C, 7, INV>(a, dst, tw, lane); break;
+        default: warp_fft_reg<C, 8, INV>(a, dst, tw, lane); break;
+      }
+      return dst;
+    }
+  }
   int Ns = 1;
   for (int s = 0; s < P.nst; ++s) {
     const int r = P.rad[s];
@@ -943,9 +1058,9 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
   ++nl;
 }
 
-// Kernel shapes of the block near field: 0 = 32-column tiles, 1 = 32-column
-// tiles compiled for five CTAs per SM (fewer registers, more warps to hide the
-// loads), 2 = 64-column tiles.
+// Kernel shapes of the block near field: 0 = 32-column tiles (four CTAs per
+// SM), 1 = 32-column tiles compiled for five CTAs per SM (fewer registers, more
+// warps to hide the loads), 2 = 64-column tiles.
 constexpr int kNearShapes = 3;
 template <typename R>
 static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
@@ -955,7 +1070,7 @@ static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p,
   else if (shape == 1)
     near_blocks_launch<R, 32, 5>(a, p, nrhs, u, y, st, nl, ks);
   else
-    near_blocks_launch<R, 32, 1>(a, p, nrhs, u, y, st, nl, ks);
+    near_blocks_launch<R, 32, 4>(a, p, nrhs, u, y, st, nl, ks);
 }
 
 // Autotuner of the block near field: on the first product of an array with a
