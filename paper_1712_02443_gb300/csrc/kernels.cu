@@ -307,6 +307,25 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
 __device__ __forceinline__ int PAD(int i) { return i + (i >> 4); }
 __host__ __device__ inline int padded_len(int L) { return L + (L >> 4) + 1; }
 
+// q = i / d, r = i % d for 0 <= i < 2^22 by a float reciprocal and one
+// correction step (an integer division costs tens of instructions)
+struct SmallDiv {
+  int d;
+  float rd;
+  __device__ explicit SmallDiv(int d_) : d(d_), rd(1.0f / (float)d_) {}
+  __device__ __forceinline__ void operator()(int i, int& q, int& r) const {
+    q = __float2int_rz((float)i * rd);
+    r = i - q * d;
+    if (r >= d) {
+      r -= d;
+      ++q;
+    } else if (r < 0) {
+      r += d;
+      --q;
+    }
+  }
+};
+
 template <typename C, int RADIX, bool INV>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
                                                const C* __restrict__ tw, int lane, int nlanes) {
@@ -568,12 +587,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(
   const C* src = grid + ((int64_t)b * Nx + x) * Ny * Nz;
   staged_copy<8, C>(Ny * Nz, [&](int i) { return src[i]; }, [&](int i, C v) { b1[i] = v; });   // staging [y][z]
   __syncthreads();
-  for (int i = threadIdx.x; i < Pz * Py; i += blockDim.x) {
-    const int kz = i / Py, y = i % Py;
-    C acc = czero<C>();
-    if (y < Ny)
-      for (int z = 0; z < Nz; ++z) acc = cadd(acc, cmul(b1[y * Nz + z], tz[(kz * z) % Pz]));
-    b0[kz * LpY + PAD(y)] = acc;
+  // z DFT: a thread per y line, the root index kz z mod Pz kept incrementally
+  for (int y = threadIdx.x; y < Py; y += blockDim.x) {
+    const C* xr = b1 + y * Nz;
+    for (int kz = 0; kz < Pz; ++kz) {
+      C acc = czero<C>();
+      if (y < Ny) {
+        int m = 0;
+        for (int z = 0; z < Nz; ++z) {
+          cmac(acc, xr[z], tz[m]);
+          m += kz;
+          if (m >= Pz) m -= Pz;
+        }
+      }
+      b0[kz * LpY + PAD(y)] = acc;
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -584,8 +612,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(
   (void)res;
   const C* out = in_b0 ? b0 : b1;
   C* dst = spec + ((int64_t)b * Nx + x) * Py * Pz;
+  const SmallDiv divz(Pz);
   for (int i = threadIdx.x; i < Py * Pz; i += blockDim.x) {
-    const int ky = i / Pz, kz = i % Pz;
+    int ky, kz;
+    divz(i, ky, kz);
     dst[i] = out[kz * LpY + PAD(ky)];
   }
 }
@@ -606,14 +636,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(
   const int ky = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Px; i += blockDim.x) tx[i] = twx[i];
   C* base = spec + (int64_t)b * Nx * Py * Pz + (int64_t)ky * Pz;
+  const SmallDiv divz(Pz);
   staged_copy<8, C>(
       Pz * Px,
       [&](int i) {
-        const int x = i / Pz, kz = i % Pz;
+        int x, kz;
+        divz(i, x, kz);
         return (x < Nx) ? base[(int64_t)x * Py * Pz + kz] : czero<C>();
       },
       [&](int i, C v) {
-        const int x = i / Pz, kz = i % Pz;
+        int x, kz;
+        divz(i, x, kz);
         b0[kz * LpX + PAD(x)] = v;
       });
   __syncthreads();
@@ -632,7 +665,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(
   // after 2 nst stages the result is back in the buffer that held the input
   const C* out = b0;
   for (int i = threadIdx.x; i < Pz * Nx; i += blockDim.x) {
-    const int x = i / Pz, kz = i % Pz;
+    int x, kz;
+    divz(i, x, kz);
     base[(int64_t)x * Py * Pz + kz] = out[kz * LpX + PAD(x)];
   }
 }
@@ -656,10 +690,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
   const C* src = spec + ((int64_t)b * Nx + x) * Py * Pz;
+  const SmallDiv divz(Pz);
   staged_copy<8, C>(
       Py * Pz, [&](int i) { return src[i]; },
       [&](int i, C v) {
-        const int ky = i / Pz, kz = i % Pz;
+        int ky, kz;
+        divz(i, ky, kz);
         b0[kz * LpY + PAD(ky)] = v;
       });
   __syncthreads();
@@ -668,15 +704,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
   __syncthreads();
   const C* res = (py.nst % 2 == 0) ? b0 : b1;
   C* dst = grid + ((int64_t)b * Nx + x) * Ny * Nz;
-  for (int i = threadIdx.x; i < Ny * Nz; i += blockDim.x) {
-    const int y = i / Nz, z = i % Nz;
-    C acc = czero<C>();
-    for (int kz = 0; kz < Pz; ++kz) {
-      C w = tz[(kz * z) % Pz];
-      w.y = -w.y;
-      acc = cadd(acc, cmul(res[kz * LpY + PAD(y)], w));
+  // inverse z DFT (first Nz outputs): a thread per y line
+  for (int y = threadIdx.x; y < Ny; y += blockDim.x) {
+    for (int z = 0; z < Nz; ++z) {
+      C acc = czero<C>();
+      int m = 0;
+      for (int kz = 0; kz < Pz; ++kz) {
+        C w = tz[m];
+        w.y = -w.y;
+        cmac(acc, res[kz * LpY + PAD(y)], w);
+        m += z;
+        if (m >= Pz) m -= Pz;
+      }
+      dst[y * Nz + z] = acc;
     }
-    dst[i] = acc;
   }
 }
 
