@@ -235,7 +235,7 @@ template <> struct W4<double> {
 };
 
 template <typename R, int RC>
-__global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+__global__ void __launch_bounds__(RC == 1 ? (sizeof(R) == 4 ? 1024 : 512) : 256) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
                                                  const int32_t* __restrict__ inv_ptr,
                                                  const int32_t* __restrict__ inv_ent, const R* __restrict__ Pi,
                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ boxorg,
@@ -259,7 +259,13 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
         },
         [&](int i, C v) { us[i] = v; });
     __syncthreads();
-    for (int node = threadIdx.x; node < nodes; node += blockDim.x) {
+    // T consecutive lanes share a node (T = 1, 2 or 4 when the block has the
+    // threads): each takes every T-th group of four entries, then they add up
+    // by shuffles within their group
+    const int T = (int)blockDim.x >= 4 * nodes ? 4 : ((int)blockDim.x >= 2 * nodes ? 2 : 1);
+    const int sub = threadIdx.x % T;
+    const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x % 32) & ~(T - 1));
+    for (int node = threadIdx.x / T; node < nodes; node += blockDim.x / T) {
       C acc[4][RC];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
         for (int c = 0; c < RC; ++c) acc[q][c] = czero<C>();
       const int q0 = inv_ptr[node], q1 = inv_ptr[node + 1];
       if (q0 == q1) continue;
-      for (int q = q0; q < q1; q += 4) {
+      for (int q = q0 + 4 * sub; q < q1; q += 4 * T) {
         int ent[4];
         typename W4<R>::T w[4];
 #pragma unroll
@@ -289,6 +295,15 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ ele
           }
         }
       }
+      for (int o = 1; o < T; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int c = 0; c < RC; ++c) {
+            acc[q][c].x += __shfl_xor_sync(gmask, acc[q][c].x, o);
+            acc[q][c].y += __shfl_xor_sync(gmask, acc[q][c].y, o);
+          }
+      if (sub != 0) continue;
       const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
       const int64_t gidx = ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz);
 #pragma unroll
@@ -1288,8 +1303,10 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     if (a.n_of_type[t] == 0) continue;
     const int Nh = (int)a.Nh[t];
     const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
+    // one right-hand side: up to four threads per box node (more CTA threads)
+    const int pthreads = std::min(sizeof(R) == 4 ? 1024 : 512, (4 * bx * by * bz + 31) / 32 * 32);
     if (nrhs == 1)
-      k_project<R, 1><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh, cs>>>(
+      k_project<R, 1><<<(unsigned)a.n_of_type[t], std::max(256, pthreads), sizeof(C) * Nh, cs>>>(
           a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
     else
       k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
