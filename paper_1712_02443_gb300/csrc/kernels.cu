@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
 // ---------------------------------------------------------------- A4: interpolation (step iii)
 // y = v - [c_A sum_{xyz} Pi.Phi + c_phi Pi_phi.Phi_phi]; one CTA per element.
 template <typename R, int CR>
-__global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+__global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 1024 : 512) : 256) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ boxorg, int nrhs, int rc,
@@ -757,38 +757,62 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
   const int64_t gstride = (int64_t)Nx * Ny * Nz;
   C cA, cP;
   cA.x = cAr; cA.y = cAi; cP.x = cPr; cP.y = cPi;
+  // stencil point s -> box-node offset (ix by + iy) bz + iz, once per CTA
+  int* soff = reinterpret_cast<int*>(box + 4 * rc * nodes);
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+    soff[s] = (ix * by + iy) * bz + iz;
+  }
+  const SmallDiv dnodes(nodes), dbyz(by * bz), dbz(bz);
   for (int c0 = 0; c0 < nrhs; c0 += rc) {
     const int cn = min(rc, nrhs - c0);
+    const SmallDiv dcn(cn);
     staged_copy<8, C>(
         4 * cn * nodes,
         [&](int i) {
-          const int node = i % nodes, pc = i / nodes;
-          const int psi = pc / cn, c = pc % cn;
-          const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+          int pc, node, psi, c, lx, r, ly, lz;
+          dnodes(i, pc, node);
+          dcn(pc, psi, c);
+          dbyz(node, lx, r);
+          dbz(r, ly, lz);
           const int64_t b = (int64_t)psi * nrhs + c0 + c;
           return grid[b * gstride + ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)];
         },
         [&](int i, C v) { box[i] = v; });
     __syncthreads();
     if constexpr (CR == 1) {
-      // item = (basis n, right-hand side c)
-      for (int p = threadIdx.x; p < Nh * cn; p += blockDim.x) {
-        const int n = p / cn, c = p % cn;
+      // item = (basis n, right-hand side c); T consecutive lanes share an item
+      // (T = 1, 2 or 4 when the block has the threads), each taking every
+      // T-th stencil point, and add up by shuffles within their group
+      const int items = Nh * cn;
+      const int T = (int)blockDim.x >= 4 * items ? 4 : ((int)blockDim.x >= 2 * items ? 2 : 1);
+      const int sub = threadIdx.x % T;
+      const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x % 32) & ~(T - 1));
+      for (int p = threadIdx.x / T; p < items; p += blockDim.x / T) {
+        int n, c;
+        dcn(p, n, c);
         C sA = czero<C>(), sP = czero<C>();
-        const int ax = anc[3 * n] + o1lo, ay = anc[3 * n + 1] + o1lo, az = anc[3 * n + 2] + o1lo;
-        for (int s = 0; s < S; ++s) {
-          const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
-          const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
+        const int nb = ((anc[3 * n] + o1lo) * by + (anc[3 * n + 1] + o1lo)) * bz + (anc[3 * n + 2] + o1lo);
+        const C* bx0 = box + c * nodes + nb;
+        for (int s = sub; s < S; s += T) {
+          const int node = soff[s];
           const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)s * Nh + n) * 4);
-          const C f0 = box[(0 * cn + c) * nodes + node];
-          const C f1 = box[(1 * cn + c) * nodes + node];
-          const C f2 = box[(2 * cn + c) * nodes + node];
-          const C f3 = box[(3 * cn + c) * nodes + node];
-          sA.x += w.x * f0.x + w.y * f1.x + w.z * f2.x;
-          sA.y += w.x * f0.y + w.y * f1.y + w.z * f2.y;
-          sP.x += w.w * f3.x;
-          sP.y += w.w * f3.y;
+          const C f0 = bx0[(0 * cn) * nodes + node];
+          const C f1 = bx0[(1 * cn) * nodes + node];
+          const C f2 = bx0[(2 * cn) * nodes + node];
+          const C f3 = bx0[(3 * cn) * nodes + node];
+          sA.x = fmx(w.x, f0.x, fmx(w.y, f1.x, fmx(w.z, f2.x, sA.x)));
+          sA.y = fmx(w.x, f0.y, fmx(w.y, f1.y, fmx(w.z, f2.y, sA.y)));
+          sP.x = fmx(w.w, f3.x, sP.x);
+          sP.y = fmx(w.w, f3.y, sP.y);
         }
+        for (int off2 = 1; off2 < T; off2 <<= 1) {
+          sA.x += __shfl_xor_sync(gmask, sA.x, off2);
+          sA.y += __shfl_xor_sync(gmask, sA.y, off2);
+          sP.x += __shfl_xor_sync(gmask, sP.x, off2);
+          sP.y += __shfl_xor_sync(gmask, sP.y, off2);
+        }
+        if (sub != 0) continue;
         const C yff = cadd(cmul(cA, sA), cmul(cP, sP));
         const int64_t idx = (o + n) * nrhs + c0 + c;
         y[idx] = csub(v[idx], yff);
@@ -808,10 +832,9 @@ __global__ void __launch_bounds__(256) k_interp(const int32_t* __restrict__ elem
         sA[c] = czero<C>();
         sP[c] = czero<C>();
       }
-      const int ax = anc[3 * n] + o1lo, ay = anc[3 * n + 1] + o1lo, az = anc[3 * n + 2] + o1lo;
+      const int nb = ((anc[3 * n] + o1lo) * by + (anc[3 * n + 1] + o1lo)) * bz + (anc[3 * n + 2] + o1lo);
       for (int s = 0; s < S; ++s) {
-        const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
-        const int node = ((ax + ix) * by + (ay + iy)) * bz + (az + iz);
+        const int node = nb + soff[s];
         const typename W4<R>::T w = W4<R>::load(Pi + ((int64_t)s * Nh + n) * 4);
         const C* b0 = box + cb * nodes + node;
 #pragma unroll
@@ -1362,14 +1385,16 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     if (a.n_of_type[t] == 0) continue;
     const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
     const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
-    const size_t sm = 4 * rc * nodes * sizeof(C);
+    const size_t sm = 4 * rc * nodes * sizeof(C) + sizeof(int) * (size_t)a.S;   // box + stencil offsets
+    // one right-hand side: up to four threads per basis (more CTA threads)
+    const int ithreads = std::min(sizeof(R) == 4 ? 1024 : 512, (int)((4 * a.Nh[t] + 31) / 32 * 32));
     if (rc >= 8)
       k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
           p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
           y);
     else
-      k_interp<R, 1><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
+      k_interp<R, 1><<<(unsigned)a.n_of_type[t], nrhs == 1 ? std::max(256, ithreads) : 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
           p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
           y);
