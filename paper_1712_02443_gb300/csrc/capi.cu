@@ -48,7 +48,9 @@ struct mm_array {
   double* d_ang = nullptr;        // device: theta, phi scratch for the excitation
   int32_t* d_pol = nullptr;
   int ang_cap = 0;
-  cudaEvent_t ang_ev = nullptr;   // the last excitation kernel (it reads d_ang, d_pol)
+  cudaEvent_t ang_ev = nullptr;   // the last excitation kernels (they use d_ang, d_pol, d_pw)
+  double2* d_pw = nullptr;        // excitation scratch: local sums and element phases
+  int64_t pw_cap = 0;             // its capacity (complex128 entries)
   void* hx = nullptr;             // device staging for mm_apply_host
   void* hy = nullptr;
   size_t h_cap = 0;
@@ -365,6 +367,8 @@ mm_array::~mm_array() {
   if (da.side) cudaStreamDestroy(da.side);
   if (da.chain) cudaStreamDestroy(da.chain);
   if (ang_ev) cudaEventDestroy(ang_ev);
+  if (d_pw) cudaFree(d_pw);
+  if (da.tbase) cudaFree(da.tbase);
   for (cudaEvent_t e : {da.ev_fork, da.ev_join, da.ev_done})
     if (e) cudaEventDestroy(e);
 }
@@ -600,6 +604,9 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     }
     a->geo_ptrs = dev_upload(gptr.data(), gptr.size(), acc);
     da.off = dev_upload(ah.off.data(), ah.off.size(), acc);
+    std::vector<int64_t> tbase(da.n_types + 1, 0);
+    for (int64_t t = 0; t < da.n_types; ++t) tbase[t + 1] = tbase[t] + da.Nh[t];
+    da.tbase = dev_upload(tbase.data(), tbase.size(), acc);
     std::vector<int32_t> boxorg(3 * n_elem), eo;
     std::vector<double> eoff(3 * n_elem);
     for (int64_t e = 0; e < n_elem; ++e) {
@@ -933,6 +940,16 @@ mm_status mm_rhs_planewave(mm_array* a, int32_t nrhs, const double* theta, const
   std::vector<int32_t> pl(pol, pol + nrhs);
   CU(cudaMemcpyAsync(a->d_ang, ang.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(a->d_pol, pl.data(), sizeof(int32_t) * nrhs, cudaMemcpyHostToDevice, st));
+  int64_t nloc = 0;
+  for (int64_t t = 0; t < a->da.n_types; ++t) nloc += a->da.Nh[t];
+  const int64_t pw_need = (nloc + a->da.n_elem) * nrhs;
+  if (a->pw_cap < pw_need) {
+    if (a->d_pw) cudaFree(a->d_pw);
+    a->d_pw = nullptr;
+    a->pw_cap = 0;
+    CU(cudaMalloc(&a->d_pw, sizeof(double2) * (size_t)pw_need));
+    a->pw_cap = pw_need;
+  }
   mm::Rule r7 = mm::rule_tri7();
   mm::QuadRule q;
   q.n = r7.n();
@@ -942,10 +959,10 @@ mm_status mm_rhs_planewave(mm_array* a, int32_t nrhs, const double* theta, const
   cudaError_t e;
   if (precision == MM_C64)
     e = mm::rhs_planewave<float>(a->da, a->elem_of, a->geo_ptrs, nrhs, a->d_ang, a->d_ang + nrhs, a->d_pol, a->k0, q,
-                                 V_dev, st);
+                                 V_dev, a->d_pw, st);
   else if (precision == MM_C128)
     e = mm::rhs_planewave<double>(a->da, a->elem_of, a->geo_ptrs, nrhs, a->d_ang, a->d_ang + nrhs, a->d_pol, a->k0,
-                                  q, V_dev, st);
+                                  q, V_dev, a->d_pw, st);
   else
     return fail(ctx, MM_EINVAL, "unknown precision");
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("excitation: ") + cudaGetErrorString(e));
@@ -1108,6 +1125,16 @@ mm_status mm_farfield(mm_array* a, int32_t nrhs, const void* Jhat_dev, int64_t n
   std::copy(theta, theta + ndir, dirs.begin());
   std::copy(phi, phi + ndir, dirs.begin() + ndir);
   CU(cudaMemcpyAsync(a->d_dir, dirs.data(), sizeof(double) * 2 * (size_t)ndir, cudaMemcpyHostToDevice, st));
+  int64_t nloc = 0;
+  for (int64_t t = 0; t < a->da.n_types; ++t) nloc += a->da.Nh[t];
+  const int64_t pw_need = (nloc + a->da.n_elem) * nrhs;
+  if (a->pw_cap < pw_need) {
+    if (a->d_pw) cudaFree(a->d_pw);
+    a->d_pw = nullptr;
+    a->pw_cap = 0;
+    CU(cudaMalloc(&a->d_pw, sizeof(double2) * (size_t)pw_need));
+    a->pw_cap = pw_need;
+  }
   mm::Rule r7 = mm::rule_tri7();
   mm::QuadRule q;
   q.n = r7.n();

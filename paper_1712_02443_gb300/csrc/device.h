@@ -127,6 +127,7 @@ struct DevArray {
   std::vector<int64_t> n_of_type;
   // per element
   int64_t* off = nullptr;               // n_elem + 1
+  int64_t* tbase = nullptr;             // n_types + 1: prefix of the types' N^_t (local bases of all types)
   int32_t* boxorg = nullptr;            // n_elem x 3: global grid coordinates of the type box origin
   int32_t* type_of = nullptr;
   double* eoff = nullptr;               // n_elem x 3 element offsets

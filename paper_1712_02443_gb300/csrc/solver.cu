@@ -63,15 +63,22 @@ __global__ void k_dot_partial(const Z* __restrict__ V, int64_t vstride, const Z*
 }
 
 // out[i * r + j] = sum_blk partial (fixed order: deterministic)
+// A warp per output: lane-strided sums of the block partials, then a butterfly
+// (a serial FP64 chain over the blocks costs far more at GB300's FP64 rate).
 __global__ void k_dot_final(const double* __restrict__ partial, int nvec, int r, int nblk, Z* __restrict__ out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
   if (t >= nvec * r) return;
   double sr = 0, si = 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     sr += partial[2 * ((int64_t)t * nblk + b)];
     si += partial[2 * ((int64_t)t * nblk + b) + 1];
   }
-  out[t] = make_double2(sr, si);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) out[t] = make_double2(sr, si);
 }
 
 // acc += conj(v) w and a -= v h with four FP64 fused multiply-adds each (the
@@ -345,11 +352,16 @@ __global__ void k_cycle_init(GmresDev gd, const double* __restrict__ PN, int nbl
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  for (int j = threadIdx.x; j < gd.r; j += blockDim.x) {
+  for (int i = threadIdx.x; i < (gd.m + 1) * gd.r; i += blockDim.x) gd.g[i] = make_double2(0, 0);
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int j = warp; j < gd.r; j += nw) {   // a warp per column
     double s2 = 0;
-    for (int b = 0; b < nblk; ++b) s2 += PN[(int64_t)j * nblk + b];
+    for (int b = lane; b < nblk; b += 32) s2 += PN[(int64_t)j * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane != 0) continue;
     const double beta = sqrt(fmax(0.0, s2));
-    for (int i = 0; i <= gd.m; ++i) gd.g[(int64_t)i * gd.r + j] = make_double2(0, 0);
     gd.g[j] = make_double2(beta, 0);
     gd.res[j] = beta;
     const int act = (beta > gd.tol[j]) && isfinite(beta);
@@ -443,23 +455,60 @@ __global__ void k_givens(GmresDev gd, const Z* __restrict__ P1, const Z* __restr
 }
 
 // y_j = H_j^-1 g_j by back substitution over kdone_j columns (lane 0 of a warp per column).
+// Back substitution R y = g per column, a warp per column, column-oriented: once
+// y_i is known every lane q < i removes H[q, i] y_i from its own right-hand
+// side entry in parallel, so the serial chain is one division per row (the
+// entries live in registers, 32 rows per lane slot, up to 8 slots = m <= 256;
+// larger restarts take the serial form).
 __global__ void k_solve_y(GmresDev gd) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   const int m = gd.m, r = gd.r;
   for (int j = warp; j < r; j += nw) {
-    if (lane != 0) continue;
     const int kj = gd.kdone[j];
-    for (int i = m - 1; i >= kj; --i) gd.y[(int64_t)i * r + j] = make_double2(0, 0);
-    for (int i = kj - 1; i >= 0; --i) {
-      Z acc = gd.g[(int64_t)i * r + j];
-      for (int q = i + 1; q < kj; ++q) {
-        const Z p = zmul(gd.H[((int64_t)j * m + q) * (m + 1) + i], gd.y[(int64_t)q * r + j]);
-        acc.x -= p.x;
-        acc.y -= p.y;
+    for (int i = kj + lane; i < m; i += 32) gd.y[(int64_t)i * r + j] = make_double2(0, 0);
+    const Z* Hj = gd.H + (int64_t)j * m * (m + 1);   // column c of R at Hj + c (m + 1)
+    if (kj <= 256) {
+      constexpr int SL = 8;
+      Z rhs[SL];
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) {
+        const int q = lane + 32 * sl;
+        rhs[sl] = q < kj ? gd.g[(int64_t)q * r + j] : make_double2(0, 0);
       }
-      const Z d = gd.H[((int64_t)j * m + i) * (m + 1) + i];
-      const double dd = d.x * d.x + d.y * d.y;
-      gd.y[(int64_t)i * r + j] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+      for (int i = kj - 1; i >= 0; --i) {
+        const int owner = i % 32, slot = i / 32;
+        Z gi = make_double2(0, 0);
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl)
+          if (sl == slot) gi = rhs[sl];
+        gi.x = __shfl_sync(0xffffffffu, gi.x, owner);
+        gi.y = __shfl_sync(0xffffffffu, gi.y, owner);
+        const Z d = Hj[(int64_t)i * (m + 1) + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        const Z yi = make_double2((gi.x * d.x + gi.y * d.y) / dd, (gi.y * d.x - gi.x * d.y) / dd);
+        if (lane == owner) gd.y[(int64_t)i * r + j] = yi;
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl) {
+          const int q = lane + 32 * sl;
+          if (q < i) {
+            const Z p = zmul(Hj[(int64_t)i * (m + 1) + q], yi);
+            rhs[sl].x -= p.x;
+            rhs[sl].y -= p.y;
+          }
+        }
+      }
+    } else if (lane == 0) {
+      for (int i = kj - 1; i >= 0; --i) {
+        Z acc = gd.g[(int64_t)i * r + j];
+        for (int q = i + 1; q < kj; ++q) {
+          const Z p = zmul(Hj[(int64_t)q * (m + 1) + i], gd.y[(int64_t)q * r + j]);
+          acc.x -= p.x;
+          acc.y -= p.y;
+        }
+        const Z d = Hj[(int64_t)i * (m + 1) + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        gd.y[(int64_t)i * r + j] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+      }
     }
   }
 }
@@ -1036,7 +1085,7 @@ Status Solver::dots(const Z* V, int64_t vstride, int nvec, const Z* w, Z* out, c
   if (prof) prof->begin(7, st);
   dim3 g(nblk_, nvec, r_);
   k_dot_partial<<<g, 256, 0, st>>>(V, vstride, w, N_, r_, nblk_, static_cast<double*>(partial_));
-  k_dot_final<<<(nvec * r_ + 127) / 128, 128, 0, st>>>(static_cast<const double*>(partial_), nvec, r_, nblk_, out);
+  k_dot_final<<<(nvec * r_ + 7) / 8, 256, 0, st>>>(static_cast<const double*>(partial_), nvec, r_, nblk_, out);
   if (prof) prof->end(st, 2);
   MM_CK(cudaGetLastError());
   return {MM_OK, ""};
@@ -1300,34 +1349,52 @@ Status Solver::solve(const Z* b, Z* x, double tol, int prec, int refine, double 
 
 // ---------------------------------------------------------------- plane-wave excitation
 // V[n, j] = -sum_{T+-} sum_q w_q A f_n(r_q) . p_j exp(-j k khat_j . r_q)  (7-point rule)
-template <typename R>
-__global__ void k_rhs_planewave(int64_t N, int nrhs, const int32_t* __restrict__ elem_of,
-                                const int32_t* __restrict__ type_of, const int64_t* __restrict__ off,
-                                const double* const* __restrict__ geo, const double* __restrict__ eoff,
-                                const double* __restrict__ theta, const double* __restrict__ phi,
-                                const int32_t* __restrict__ pol, double k0, QuadRule q,
-                                typename V2<R>::T* __restrict__ V) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= N * nrhs) return;
-  const int64_t n = t / nrhs;
-  const int j = (int)(t % nrhs);
-  const int e = elem_of[n];
-  const int ty = type_of[e];
-  const double* gp = geo[ty] + 13 * (n - off[e]);
-  const double ox = eoff[3 * e], oy = eoff[3 * e + 1], oz = eoff[3 * e + 2];
+// With r_q = o_e + r'_q (o_e the element offset, r'_q in the type's local
+// frame) and f_n depending on r_q - (free vertex) only, the phase splits:
+// V[n, j] = exp(-j k khat_j . o_e) Vloc[t, n', j], Vloc being the same sum in
+// the local frame, which is shared by every element of type t.  So the
+// quadrature (14 phase evaluations per basis) runs once per (type, local basis)
+// and each element adds one phase: the FP64 sine and cosine, slow at GB300's
+// FP64 rate, drop from 14 per unknown to about one per element.
+__device__ __forceinline__ void planewave_dirs(double th, double ph, int pol, double* k, double* p) {
   double st, ct, sp, cp;
-  sincos(theta[j], &st, &ct);
-  sincos(phi[j], &sp, &cp);
-  const double kx = -st * cp, ky = -st * sp, kz = -ct;
-  double px, py, pz;
-  if (pol[j] == 0) { px = ct * cp; py = ct * sp; pz = -st; }
-  else { px = -sp; py = cp; pz = 0.0; }
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  k[0] = -st * cp; k[1] = -st * sp; k[2] = -ct;
+  if (pol == 0) { p[0] = ct * cp; p[1] = ct * sp; p[2] = -st; }
+  else { p[0] = -sp; p[1] = cp; p[2] = 0.0; }
+}
+
+// Part 1: items (local basis of a type, then element) x right-hand sides.
+// vloc[(tbase[t] + n') nrhs + j] = -(local quadrature sum); eph[e nrhs + j] = exp(-j k khat_j . o_e).
+__global__ void k_rhs_parts(int ntypes, const int64_t* __restrict__ tbase, int64_t n_elem, int nrhs,
+                            const double* const* __restrict__ geo, const double* __restrict__ eoff,
+                            const double* __restrict__ theta, const double* __restrict__ phi,
+                            const int32_t* __restrict__ pol, double k0, QuadRule q, double2* __restrict__ vloc,
+                            double2* __restrict__ eph) {
+  const int64_t nloc = tbase[ntypes];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (nloc + n_elem) * nrhs) return;
+  const int64_t item = t / nrhs;
+  const int j = (int)(t - item * nrhs);
+  double kh[3], pv[3];
+  planewave_dirs(theta[j], phi[j], pol[j], kh, pv);
+  if (item >= nloc) {
+    const int64_t e = item - nloc;
+    double sn, cs;
+    sincos(-k0 * (kh[0] * eoff[3 * e] + kh[1] * eoff[3 * e + 1] + kh[2] * eoff[3 * e + 2]), &sn, &cs);
+    eph[e * nrhs + j] = make_double2(cs, sn);
+    return;
+  }
+  int ty = 0;
+  while (ty + 1 < ntypes && tbase[ty + 1] <= item) ++ty;
+  const double* gp = geo[ty] + 13 * (item - tbase[ty]);
   double accr = 0, acci = 0;
   const double l = gp[12];
   for (int side = 0; side < 2; ++side) {
-    const double ax = gp[0] + ox, ay = gp[1] + oy, az = gp[2] + oz;
-    const double bx = gp[3] + ox, by = gp[4] + oy, bz = gp[5] + oz;
-    const double fx = gp[6 + 3 * side] + ox, fy = gp[7 + 3 * side] + oy, fz = gp[8 + 3 * side] + oz;
+    const double ax = gp[0], ay = gp[1], az = gp[2];
+    const double bx = gp[3], by = gp[4], bz = gp[5];
+    const double fx = gp[6 + 3 * side], fy = gp[7 + 3 * side], fz = gp[8 + 3 * side];
     const double ux = bx - ax, uy = by - ay, uz = bz - az, vx = fx - ax, vy = fy - ay, vz = fz - az;
     const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
     const double A = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
@@ -1337,33 +1404,55 @@ __global__ void k_rhs_planewave(int64_t N, int nrhs, const int32_t* __restrict__
       const double ry = q.b0[i] * ay + q.b1[i] * by + q.b2[i] * fy;
       const double rz = q.b0[i] * az + q.b1[i] * bz + q.b2[i] * fz;
       const double s = sg * l / (2.0 * A);
-      const double dotp = s * ((rx - fx) * px + (ry - fy) * py + (rz - fz) * pz);
+      const double dotp = s * ((rx - fx) * pv[0] + (ry - fy) * pv[1] + (rz - fz) * pv[2]);
       double sn, cs;
-      sincos(-k0 * (kx * rx + ky * ry + kz * rz), &sn, &cs);
+      sincos(-k0 * (kh[0] * rx + kh[1] * ry + kh[2] * rz), &sn, &cs);
       const double wA = q.w[i] * A;
       accr += wA * dotp * cs;
       acci += wA * dotp * sn;
     }
   }
+  vloc[item * nrhs + j] = make_double2(-accr, -acci);
+}
+
+// Part 2: V[n, j] = eph[e, j] Vloc[t, n - off[e], j].
+template <typename R>
+__global__ void k_rhs_planewave(int64_t N, int nrhs, const int32_t* __restrict__ elem_of,
+                                const int32_t* __restrict__ type_of, const int64_t* __restrict__ off,
+                                const int64_t* __restrict__ tbase, const double2* __restrict__ vloc,
+                                const double2* __restrict__ eph, typename V2<R>::T* __restrict__ V) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int64_t n = t / nrhs;
+  const int j = (int)(t - n * nrhs);
+  const int e = elem_of[n];
+  const double2 a = vloc[(tbase[type_of[e]] + n - off[e]) * nrhs + j], b = eph[(int64_t)e * nrhs + j];
   typename V2<R>::T out;
-  out.x = (R)(-accr);
-  out.y = (R)(-acci);
+  out.x = (R)(a.x * b.x - a.y * b.y);
+  out.y = (R)(a.x * b.y + a.y * b.x);
   V[t] = out;
 }
 
 template <typename R>
 cudaError_t rhs_planewave(const DevArray& a, const int32_t* elem_of, const double* const* geo, int nrhs,
                           const double* th, const double* ph, const int32_t* pol, double k0, const QuadRule& q,
-                          void* V, cudaStream_t st) {
+                          void* V, double2* scratch, cudaStream_t st) {
+  int64_t nloc = 0;
+  for (int64_t t = 0; t < a.n_types; ++t) nloc += a.Nh[t];
+  const int64_t parts = (nloc + a.n_elem) * nrhs;
+  k_rhs_parts<<<(unsigned)((parts + 255) / 256), 256, 0, st>>>((int)a.n_types, a.tbase, a.n_elem, nrhs, geo, a.eoff,
+                                                               th, ph, pol, k0, q, scratch, scratch + nloc * nrhs);
   const int64_t tot = a.N * nrhs;
-  k_rhs_planewave<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-      a.N, nrhs, elem_of, a.type_of, a.off, geo, a.eoff, th, ph, pol, k0, q, static_cast<typename V2<R>::T*>(V));
+  k_rhs_planewave<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.N, nrhs, elem_of, a.type_of, a.off, a.tbase,
+                                                                     scratch, scratch + nloc * nrhs,
+                                                                     static_cast<typename V2<R>::T*>(V));
   return cudaGetLastError();
 }
 template cudaError_t rhs_planewave<float>(const DevArray&, const int32_t*, const double* const*, int, const double*,
-                                          const double*, const int32_t*, double, const QuadRule&, void*, cudaStream_t);
+                                          const double*, const int32_t*, double, const QuadRule&, void*, double2*,
+                                          cudaStream_t);
 template cudaError_t rhs_planewave<double>(const DevArray&, const int32_t*, const double* const*, int, const double*,
-                                           const double*, const int32_t*, double, const QuadRule&, void*,
+                                           const double*, const int32_t*, double, const QuadRule&, void*, double2*,
                                            cudaStream_t);
 
 }  // namespace mm

@@ -60,9 +60,10 @@ class Solver {
   size_t bytes_ = 0;
 };
 
+// scratch: (sum of the types' N^_t + n_elem) x nrhs complex128 (local sums, element phases)
 template <typename R>
 cudaError_t rhs_planewave(const DevArray& a, const int32_t* elem_of, const double* const* geo, int nrhs,
                           const double* th, const double* ph, const int32_t* pol, double k0, const QuadRule& q,
-                          void* V, cudaStream_t st);
+                          void* V, double2* scratch, cudaStream_t st);
 
 }  // namespace mm
