@@ -455,60 +455,68 @@ __global__ void k_givens(GmresDev gd, const Z* __restrict__ P1, const Z* __restr
 }
 
 // y_j = H_j^-1 g_j by back substitution over kdone_j columns (lane 0 of a warp per column).
-// Back substitution R y = g per column, a warp per column, column-oriented: once
-// y_i is known every lane q < i removes H[q, i] y_i from its own right-hand
-// side entry in parallel, so the serial chain is one division per row (the
-// entries live in registers, 32 rows per lane slot, up to 8 slots = m <= 256;
-// larger restarts take the serial form).
+// Back substitution R y = g, a CTA per column.  For k <= kSolveSmemK the CTA
+// first stages R's upper triangle in shared memory and every diagonal's
+// reciprocal conj(d) / |d|^2 (divisions side by side); warp 0 then runs the
+// column-oriented substitution: once y_i is known each lane q < i removes
+// R[q, i] y_i from its own right-hand side entry, so the serial chain is a
+// shuffle and a complex product per row (serial FP64 divisions and L2 loads
+// were the step's cost at GB300's FP64 rate).  Larger k: one thread, global memory.
+constexpr int kSolveSmemK = 64;
 __global__ void k_solve_y(GmresDev gd) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  const int m = gd.m, r = gd.r;
-  for (int j = warp; j < r; j += nw) {
-    const int kj = gd.kdone[j];
-    for (int i = kj + lane; i < m; i += 32) gd.y[(int64_t)i * r + j] = make_double2(0, 0);
-    const Z* Hj = gd.H + (int64_t)j * m * (m + 1);   // column c of R at Hj + c (m + 1)
-    if (kj <= 256) {
-      constexpr int SL = 8;
-      Z rhs[SL];
+  extern __shared__ Z rs[];   // [i][q], q <= i < k: R[q, i]; then k reciprocals
+  const int m = gd.m, r = gd.r, j = blockIdx.x;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int kj = gd.kdone[j];
+  for (int i = kj + threadIdx.x; i < m; i += blockDim.x) gd.y[(int64_t)i * r + j] = make_double2(0, 0);
+  const Z* Hj = gd.H + (int64_t)j * m * (m + 1);   // column c of R at Hj + c (m + 1)
+  if (kj <= kSolveSmemK) {
+    Z* rinv = rs + kSolveSmemK * kSolveSmemK;
+    for (int t = threadIdx.x; t < kj * kj; t += blockDim.x) {
+      const int i = t / kj, q = t - i * kj;
+      if (q <= i) rs[i * kSolveSmemK + q] = Hj[(int64_t)i * (m + 1) + q];
+    }
+    for (int i = threadIdx.x; i < kj; i += blockDim.x) {
+      const Z d = Hj[(int64_t)i * (m + 1) + i];
+      const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+      rinv[i] = make_double2(d.x * inv, -d.y * inv);
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    Z rhs[2];
 #pragma unroll
-      for (int sl = 0; sl < SL; ++sl) {
+    for (int sl = 0; sl < 2; ++sl) {
+      const int q = lane + 32 * sl;
+      rhs[sl] = q < kj ? gd.g[(int64_t)q * r + j] : make_double2(0, 0);
+    }
+    for (int i = kj - 1; i >= 0; --i) {
+      const int owner = i % 32;
+      Z gi = i >= 32 ? rhs[1] : rhs[0];
+      gi.x = __shfl_sync(0xffffffffu, gi.x, owner);
+      gi.y = __shfl_sync(0xffffffffu, gi.y, owner);
+      const Z yi = zmul(gi, rinv[i]);
+      if (lane == owner) gd.y[(int64_t)i * r + j] = yi;
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
         const int q = lane + 32 * sl;
-        rhs[sl] = q < kj ? gd.g[(int64_t)q * r + j] : make_double2(0, 0);
-      }
-      for (int i = kj - 1; i >= 0; --i) {
-        const int owner = i % 32, slot = i / 32;
-        Z gi = make_double2(0, 0);
-#pragma unroll
-        for (int sl = 0; sl < SL; ++sl)
-          if (sl == slot) gi = rhs[sl];
-        gi.x = __shfl_sync(0xffffffffu, gi.x, owner);
-        gi.y = __shfl_sync(0xffffffffu, gi.y, owner);
-        const Z d = Hj[(int64_t)i * (m + 1) + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        const Z yi = make_double2((gi.x * d.x + gi.y * d.y) / dd, (gi.y * d.x - gi.x * d.y) / dd);
-        if (lane == owner) gd.y[(int64_t)i * r + j] = yi;
-#pragma unroll
-        for (int sl = 0; sl < SL; ++sl) {
-          const int q = lane + 32 * sl;
-          if (q < i) {
-            const Z p = zmul(Hj[(int64_t)i * (m + 1) + q], yi);
-            rhs[sl].x -= p.x;
-            rhs[sl].y -= p.y;
-          }
+        if (q < i) {
+          const Z p = zmul(rs[i * kSolveSmemK + q], yi);
+          rhs[sl].x -= p.x;
+          rhs[sl].y -= p.y;
         }
       }
-    } else if (lane == 0) {
-      for (int i = kj - 1; i >= 0; --i) {
-        Z acc = gd.g[(int64_t)i * r + j];
-        for (int q = i + 1; q < kj; ++q) {
-          const Z p = zmul(Hj[(int64_t)q * (m + 1) + i], gd.y[(int64_t)q * r + j]);
-          acc.x -= p.x;
-          acc.y -= p.y;
-        }
-        const Z d = Hj[(int64_t)i * (m + 1) + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        gd.y[(int64_t)i * r + j] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+    }
+  } else if (threadIdx.x == 0) {
+    for (int i = kj - 1; i >= 0; --i) {
+      Z acc = gd.g[(int64_t)i * r + j];
+      for (int q = i + 1; q < kj; ++q) {
+        const Z p = zmul(Hj[(int64_t)q * (m + 1) + i], gd.y[(int64_t)q * r + j]);
+        acc.x -= p.x;
+        acc.y -= p.y;
       }
+      const Z d = Hj[(int64_t)i * (m + 1) + i];
+      const double dd = d.x * d.x + d.y * d.y;
+      gd.y[(int64_t)i * r + j] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
     }
   }
 }
@@ -982,6 +990,8 @@ Status Solver::ensure(int64_t N, int r, int m) {
   {
     // partial-sum blocks: the co-resident grid of the cooperative Arnoldi step
     int dev = 0, sms = 0, per = 0;
+    MM_CK(cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(Z) * (kSolveSmemK * kSolveSmemK + kSolveSmemK))));
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // hs, h2s: (m+1) r each; ws: max((m+1) warps, block threads); need flags
@@ -1243,7 +1253,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     }
     MM_CK(cudaEventSynchronize(ev_[(launched - 1) & 1]));
     if (!flag[0]) stopped = true;
-    k_solve_y<<<1, 32 * nw, 0, st>>>(gd);
+    k_solve_y<<<r, 256, sizeof(Z) * (kSolveSmemK * kSolveSmemK + kSolveSmemK), st>>>(gd);
     if (prof) prof->begin(7, st);
     k_add_basis_dev<<<grid_for(n), 256, 0, st>>>(V, vs, gd, n, x);
     if (prof) prof->end(st, 1);
@@ -1367,19 +1377,25 @@ __device__ __forceinline__ void planewave_dirs(double th, double ph, int pol, do
 
 // Part 1: items (local basis of a type, then element) x right-hand sides.
 // vloc[(tbase[t] + n') nrhs + j] = -(local quadrature sum); eph[e nrhs + j] = exp(-j k khat_j . o_e).
+// Sixteen lanes per item: lane (side, point) evaluates one quadrature term
+// (2 x up to 8 points) and the group adds by shuffles, so the FP64 sine and
+// cosine evaluations of one basis run side by side.
 __global__ void k_rhs_parts(int ntypes, const int64_t* __restrict__ tbase, int64_t n_elem, int nrhs,
                             const double* const* __restrict__ geo, const double* __restrict__ eoff,
                             const double* __restrict__ theta, const double* __restrict__ phi,
                             const int32_t* __restrict__ pol, double k0, QuadRule q, double2* __restrict__ vloc,
                             double2* __restrict__ eph) {
   const int64_t nloc = tbase[ntypes];
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (nloc + n_elem) * nrhs) return;
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 16;
+  const int sub = threadIdx.x % 16, side = sub / 8, i = sub % 8;
+  const unsigned gmask = 0xffffu << (threadIdx.x % 32 & 16);
+  if (t >= (nloc + n_elem) * nrhs) return;   // uniform over the 16-lane group
   const int64_t item = t / nrhs;
   const int j = (int)(t - item * nrhs);
   double kh[3], pv[3];
   planewave_dirs(theta[j], phi[j], pol[j], kh, pv);
   if (item >= nloc) {
+    if (sub != 0) return;
     const int64_t e = item - nloc;
     double sn, cs;
     sincos(-k0 * (kh[0] * eoff[3 * e] + kh[1] * eoff[3 * e + 1] + kh[2] * eoff[3 * e + 2]), &sn, &cs);
@@ -1390,8 +1406,8 @@ __global__ void k_rhs_parts(int ntypes, const int64_t* __restrict__ tbase, int64
   while (ty + 1 < ntypes && tbase[ty + 1] <= item) ++ty;
   const double* gp = geo[ty] + 13 * (item - tbase[ty]);
   double accr = 0, acci = 0;
-  const double l = gp[12];
-  for (int side = 0; side < 2; ++side) {
+  if (i < q.n) {
+    const double l = gp[12];
     const double ax = gp[0], ay = gp[1], az = gp[2];
     const double bx = gp[3], by = gp[4], bz = gp[5];
     const double fx = gp[6 + 3 * side], fy = gp[7 + 3 * side], fz = gp[8 + 3 * side];
@@ -1399,20 +1415,23 @@ __global__ void k_rhs_parts(int ntypes, const int64_t* __restrict__ tbase, int64
     const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
     const double A = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
     const double sg = side == 0 ? 1.0 : -1.0;
-    for (int i = 0; i < q.n; ++i) {
-      const double rx = q.b0[i] * ax + q.b1[i] * bx + q.b2[i] * fx;
-      const double ry = q.b0[i] * ay + q.b1[i] * by + q.b2[i] * fy;
-      const double rz = q.b0[i] * az + q.b1[i] * bz + q.b2[i] * fz;
-      const double s = sg * l / (2.0 * A);
-      const double dotp = s * ((rx - fx) * pv[0] + (ry - fy) * pv[1] + (rz - fz) * pv[2]);
-      double sn, cs;
-      sincos(-k0 * (kh[0] * rx + kh[1] * ry + kh[2] * rz), &sn, &cs);
-      const double wA = q.w[i] * A;
-      accr += wA * dotp * cs;
-      acci += wA * dotp * sn;
-    }
+    const double rx = q.b0[i] * ax + q.b1[i] * bx + q.b2[i] * fx;
+    const double ry = q.b0[i] * ay + q.b1[i] * by + q.b2[i] * fy;
+    const double rz = q.b0[i] * az + q.b1[i] * bz + q.b2[i] * fz;
+    const double s = sg * l / (2.0 * A);
+    const double dotp = s * ((rx - fx) * pv[0] + (ry - fy) * pv[1] + (rz - fz) * pv[2]);
+    double sn, cs;
+    sincos(-k0 * (kh[0] * rx + kh[1] * ry + kh[2] * rz), &sn, &cs);
+    const double wA = q.w[i] * A;
+    accr = wA * dotp * cs;
+    acci = wA * dotp * sn;
   }
-  vloc[item * nrhs + j] = make_double2(-accr, -acci);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    accr += __shfl_xor_sync(gmask, accr, o);
+    acci += __shfl_xor_sync(gmask, acci, o);
+  }
+  if (sub == 0) vloc[item * nrhs + j] = make_double2(-accr, -acci);
 }
 
 // Part 2: V[n, j] = eph[e, j] Vloc[t, n - off[e], j].
@@ -1440,8 +1459,10 @@ cudaError_t rhs_planewave(const DevArray& a, const int32_t* elem_of, const doubl
   int64_t nloc = 0;
   for (int64_t t = 0; t < a.n_types; ++t) nloc += a.Nh[t];
   const int64_t parts = (nloc + a.n_elem) * nrhs;
-  k_rhs_parts<<<(unsigned)((parts + 255) / 256), 256, 0, st>>>((int)a.n_types, a.tbase, a.n_elem, nrhs, geo, a.eoff,
-                                                               th, ph, pol, k0, q, scratch, scratch + nloc * nrhs);
+  if (q.n > 8) return cudaErrorInvalidValue;   // sixteen lanes: two sides of at most 8 points
+  k_rhs_parts<<<(unsigned)((16 * parts + 255) / 256), 256, 0, st>>>((int)a.n_types, a.tbase, a.n_elem, nrhs, geo,
+                                                                    a.eoff, th, ph, pol, k0, q, scratch,
+                                                                    scratch + nloc * nrhs);
   const int64_t tot = a.N * nrhs;
   k_rhs_planewave<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.N, nrhs, elem_of, a.type_of, a.off, a.tbase,
                                                                      scratch, scratch + nloc * nrhs,
