@@ -235,7 +235,7 @@ template <> struct W4<double> {
 };
 
 template <typename R, int RC>
-__global__ void __launch_bounds__(RC == 1 ? (sizeof(R) == 4 ? 1024 : 512) : 256) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+__global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 4 ? 2 : 1) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
                                                  const int32_t* __restrict__ inv_ptr,
                                                  const int32_t* __restrict__ inv_ent, const R* __restrict__ Pi,
                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ boxorg,
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
 // ---------------------------------------------------------------- A4: interpolation (step iii)
 // y = v - [c_A sum_{xyz} Pi.Phi + c_phi Pi_phi.Phi_phi]; one CTA per element.
 template <typename R, int CR>
-__global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 1024 : 512) : 256) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+__global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, CR == 1 && sizeof(R) == 4 ? 2 : 1) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ boxorg, int nrhs, int rc,
@@ -1327,7 +1327,10 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const int Nh = (int)a.Nh[t];
     const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
     // one right-hand side: up to four threads per box node (more CTA threads)
-    const int pthreads = std::min(sizeof(R) == 4 ? 1024 : 512, (4 * bx * by * bz + 31) / 32 * 32);
+    // T lanes per node with T nodes <= 512, so that two CTAs fit on an SM (one wave)
+    const int pnodes = bx * by * bz;
+    const int pT = 4 * pnodes <= 512 ? 4 : (2 * pnodes <= 512 ? 2 : 1);
+    const int pthreads = std::min(512, (pT * pnodes + 31) / 32 * 32);
     if (nrhs == 1)
       k_project<R, 1><<<(unsigned)a.n_of_type[t], std::max(256, pthreads), sizeof(C) * Nh, cs>>>(
           a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
@@ -1387,7 +1390,10 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
     const size_t sm = 4 * rc * nodes * sizeof(C) + sizeof(int) * (size_t)a.S;   // box + stencil offsets
     // one right-hand side: up to four threads per basis (more CTA threads)
-    const int ithreads = std::min(sizeof(R) == 4 ? 1024 : 512, (int)((4 * a.Nh[t] + 31) / 32 * 32));
+    // T lanes per basis with T N^_t <= 576 (512 for FP64): two CTAs per SM
+    const int icap = sizeof(R) == 4 ? 576 : 512;
+    const int iT = 4 * a.Nh[t] <= icap ? 4 : (2 * a.Nh[t] <= icap ? 2 : 1);
+    const int ithreads = std::min(icap, (int)((iT * a.Nh[t] + 31) / 32 * 32));
     if (rc >= 8)
       k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
