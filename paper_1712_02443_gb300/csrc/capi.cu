@@ -120,6 +120,17 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
       W[Nh * Nh + i].x = (R)tm.D[i].real(); W[Nh * Nh + i].y = (R)tm.D[i].imag();
     }
     p.W[t] = dev_upload(W.data(), W.size(), da.bytes);
+    if (sizeof(R) == 8) {
+      // three-multiplication form of the FP64 GEMM: (Re, Im, Re + Im) per entry
+      std::vector<double> W3(3 * 2 * Nh * Nh);
+      for (int64_t i = 0; i < 2 * Nh * Nh; ++i) {
+        const mm::cd w = i < Nh * Nh ? tm.M[i] : tm.D[i - Nh * Nh];
+        W3[3 * i] = w.real();
+        W3[3 * i + 1] = w.imag();
+        W3[3 * i + 2] = w.real() + w.imag();
+      }
+      p.W3.push_back(dev_upload(W3.data(), W3.size(), da.bytes));
+    }
     // device layout [s][n][4]: consecutive bases of one stencil node are contiguous
     const auto& Pi = ah.tai[t].Pi;
     const int S = ah.tai[t].S;
@@ -251,6 +262,15 @@ void upload_pj(mm_array* a, mm::DevPrec<R>& p) {
       WP[i].y = (R)tm.WPJ[i].imag();
     }
     p.WP.push_back(dev_upload(WP.data(), WP.size(), a->da.bytes));
+    if (sizeof(R) == 8) {
+      std::vector<double> W3(3 * tm.WPJ.size());
+      for (size_t i = 0; i < tm.WPJ.size(); ++i) {
+        W3[3 * i] = tm.WPJ[i].real();
+        W3[3 * i + 1] = tm.WPJ[i].imag();
+        W3[3 * i + 2] = tm.WPJ[i].real() + tm.WPJ[i].imag();
+      }
+      p.WP3.push_back(dev_upload(W3.data(), W3.size(), a->da.bytes));
+    }
   }
 }
 
@@ -331,6 +351,8 @@ void free_prec_f(mm::DevPrec<float>& p) {
 void free_prec_d(mm::DevPrec<double>& p) {
   for (void* q : p.PJ) cudaFree(q);
   for (void* q : p.WP) cudaFree(q);
+  for (void* q : p.W3) cudaFree(q);
+  for (void* q : p.WP3) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})

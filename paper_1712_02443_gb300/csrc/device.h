@@ -94,6 +94,8 @@ struct DevPrec {
   // layouts as W and Atc), uploaded with PJ: Z P^-1 x takes one GEMM
   std::vector<void*> WP;
   std::vector<void*> AtcP[2];
+  // FP64 only: W and WP with (Re, Im, Re + Im) per entry for the three-multiplication GEMM
+  std::vector<void*> W3, WP3;
 };
 
 // Work buffers for one (precision, nrhs) pair.

@@ -209,6 +209,119 @@ __global__ void __launch_bounds__(256) k_macro_gemm(const typename V2<R>::T* __r
   }
 }
 
+// FP64 form of the macromodel GEMM with three real products per complex term
+// (Gauss): with w = a + ib, x = c + id, t1 = a c, t2 = b d, t3 = (a + b)(c + d),
+// w x = (t1 - t2) + i (t3 - t1 - t2).  The three sums run as three real
+// accumulations (three FMAs per term instead of four); a + b is stored with the
+// matrix (W3: Re, Im, Re + Im per entry), c + d is formed when x is staged.  The
+// GEMM is bound by GB300's FP64 rate, so the FMA count sets its time.
+struct D3 {
+  double r, i, s;
+};
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_macro_gemm3(const double* __restrict__ W3, int Nh, int rows,
+                                                     const int32_t* __restrict__ elems, int ncols, int nrhs,
+                                                     const int64_t* __restrict__ off, const double2* __restrict__ x,
+                                                     double2* __restrict__ u, double2* __restrict__ v) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
+  __shared__ D3 As[BK][BM + 1];
+  __shared__ D3 Bs[BK][BN + 1];
+  __shared__ int64_t colbase[BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  for (int c = tid; c < BN; c += 256) {
+    const int gc = col0 + c;
+    colbase[c] = gc < ncols ? off[elems[gc / nrhs]] * nrhs + gc % nrhs : -1;
+  }
+  double t1[TM][TN], t2[TM][TN], t3[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
+  __syncthreads();
+  D3 ra[LA];
+  double2 rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      const int r = e / BK, kk = e % BK;
+      const int gr = row0 + r, gk = k0 + kk;
+      if (gr < rows && gk < Nh) {
+        const double* w = W3 + 3 * ((int64_t)gr * Nh + gk);
+        ra[q] = D3{w[0], w[1], w[2]};
+      } else {
+        ra[q] = D3{0, 0, 0};
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e % BK, c = e / BK;
+      const int gk = k0 + kk;
+      const int64_t cb = colbase[c];
+      rb[q] = (cb >= 0 && gk < Nh) ? x[cb + (int64_t)gk * nrhs] : make_double2(0, 0);
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      As[e % BK][e / BK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      Bs[e % BK][e / BK] = D3{rb[q].x, rb[q].y, rb[q].x + rb[q].y};
+    }
+  };
+  load(0);
+  store();
+  __syncthreads();
+  for (int k0 = 0; k0 < Nh; k0 += BK) {
+    const bool more = k0 + BK < Nh;
+    if (more) load(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      D3 a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          t1[i][j] = __fma_rn(a[i].r, b[j].r, t1[i][j]);
+          t2[i][j] = __fma_rn(a[i].i, b[j].i, t2[i][j]);
+          t3[i][j] = __fma_rn(a[i].s, b[j].s, t3[i][j]);
+        }
+    }
+    __syncthreads();
+    if (more) {
+      store();
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gr = row0 + ty * TM + i;
+    if (gr >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t cb = colbase[tx * TN + j];
+      if (cb < 0) continue;
+      const double2 o = make_double2(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
+      if (gr < Nh)
+        u[cb + (int64_t)gr * nrhs] = o;
+      else
+        v[cb + (int64_t)(gr - Nh) * nrhs] = o;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- A2: projection (step i)
 // One CTA per element.  Each thread owns nodes of the element's stencil box and
 // gathers the (basis, stencil node) contributions listed for that node (lists
@@ -1271,6 +1384,17 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const int64_t big = (int64_t)((2 * Nh + 63) / 64) * ((ncols + 63) / 64);
     constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
     const C* Wt = static_cast<const C*>((pre ? p.WP : p.W)[t]);
+    if constexpr (sizeof(R) == 8) {
+      const auto& W3v = pre ? p.WP3 : p.W3;
+      if ((size_t)t < W3v.size() && W3v[t] != nullptr) {
+        dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
+        k_macro_gemm3<32, 32, 16><<<g, 256, 0, st>>>(static_cast<const double*>(W3v[t]), Nh, 2 * Nh, a.elems[t],
+                                                     ncols, nrhs, a.off, reinterpret_cast<const double2*>(x),
+                                                     reinterpret_cast<double2*>(u), reinterpret_cast<double2*>(v));
+        ++nl;
+        continue;
+      }
+    }
     if (big >= 2 * 152) {
       dim3 g((2 * Nh + 63) / 64, (ncols + 63) / 64);
       k_macro_gemm<R, 64, 64, 16><<<g, 256, 0, st>>>(Wt, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x, u, v);
