@@ -141,15 +141,20 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
     p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
   }
   if (da.nnz > 0) {
-    // near-field values in the padded row layout of da.rowptr (pad entries are 0)
-    std::vector<C> v(da.nnz_padded);
-    for (auto& z : v) { z.x = 0; z.y = 0; }
+    // near-field values in the padded row layout of da.rowptr (pad entries are
+    // 0); complex64 interleaved, FP64 as (Re, Im, Re + Im) for the
+    // three-product form of the FP64 SpMV
+    const int per = sizeof(R) == 8 ? 3 : 2;
+    std::vector<R> v((size_t)per * da.nnz_padded, (R)0);
     int64_t q = 0;
     for (int64_t i = 0; i < ah.N; ++i) {
       int64_t len = ah.rowptr[i + 1] - ah.rowptr[i];
       for (int64_t k = 0; k < len; ++k) {
         const auto& z = ah.val[ah.rowptr[i] + k];
-        v[q + k].x = (R)z.real(); v[q + k].y = (R)z.imag();
+        R* d = v.data() + (size_t)per * (q + k);
+        d[0] = (R)z.real();
+        d[1] = (R)z.imag();
+        if (per == 3) d[2] = (R)(z.real() + z.imag());
       }
       q += (len + 3) / 4 * 4;
     }
@@ -321,7 +326,7 @@ template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
-  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -333,6 +338,10 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   CU(cudaMalloc(&w.grid, g));
   CU(cudaMalloc(&w.spec, s));
   w.bytes = 2 * vec + g + s;
+  if (sizeof(R) == 8 && da.nnz > 0) {
+    CU(cudaMalloc(&w.us, sizeof(double) * (size_t)da.N * nrhs));
+    w.bytes += sizeof(double) * (size_t)da.N * nrhs;
+  }
   w.nrhs = nrhs;
 }
 
@@ -368,7 +377,7 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
@@ -551,7 +560,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     else if (opts->near_csr == 2)
       ao.csr_max_nnz = 0;
     else
-      ao.csr_max_nnz = ((int64_t)8 << 30) / 28;
+      ao.csr_max_nnz = ((int64_t)8 << 30) / 36;   // 8 + 24 value bytes + 4 column bytes
   }
   mm::build_array_host(a->ah, tms, type_of, offs, ao, em);
   auto& ah = a->ah;

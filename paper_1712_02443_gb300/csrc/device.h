@@ -109,6 +109,7 @@ struct Work {
   size_t bt_cap = 0;      // elements
   int* err = nullptr;     // device error flag of bounded waits
   void* pt = nullptr;     // N x nrhs   preconditioned vector (block-Jacobi)
+  double* us = nullptr;   // N x nrhs   FP64 only: Re u + Im u for the three-product near field
   size_t bytes = 0;
 };
 

@@ -222,7 +222,9 @@ template <int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_macro_gemm3(const double* __restrict__ W3, int Nh, int rows,
                                                      const int32_t* __restrict__ elems, int ncols, int nrhs,
                                                      const int64_t* __restrict__ off, const double2* __restrict__ x,
-                                                     double2* __restrict__ u, double2* __restrict__ v) {
+                                                     double2* __restrict__ u, double2* __restrict__ v,
+                                                     double* __restrict__ us) {
+  // us (optional): Re u + Im u, the summed operand of the three-product near field
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
   __shared__ D3 As[BK][BM + 1];
@@ -314,10 +316,12 @@ __global__ void __launch_bounds__(256) k_macro_gemm3(const double* __restrict__ 
       const int64_t cb = colbase[tx * TN + j];
       if (cb < 0) continue;
       const double2 o = make_double2(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
-      if (gr < Nh)
+      if (gr < Nh) {
         u[cb + (int64_t)gr * nrhs] = o;
-      else
+        if (us != nullptr) us[cb + (int64_t)gr * nrhs] = o.x + o.y;
+      } else {
         v[cb + (int64_t)(gr - Nh) * nrhs] = o;
+      }
     }
   }
 }
@@ -1025,6 +1029,61 @@ __global__ void __launch_bounds__(256) k_spmv_near1(int64_t N, const int64_t* __
   }
 }
 
+// FP64 near field with three real products per term (values stored as Re,
+// Im, Re + Im; us = Re u + Im u from the GEMM, or formed here when absent):
+// sums t1 = sum Re a Re u, t2 = sum Im a Im u, t3 = sum (Re a + Im a)(Re u + Im u),
+// and y -= (t1 - t2) + i (t3 - t1 - t2).  Bound by GB300's FP64 rate: three FMAs
+// per non-zero instead of four.
+template <int RC>
+__global__ void __launch_bounds__(256) k_spmv_near_3m(int64_t N, const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ val3, int nrhs,
+                                                      const double2* __restrict__ u, const double* __restrict__ us,
+                                                      double2* __restrict__ y) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= N) return;
+  const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+  for (int c0 = 0; c0 < nrhs; c0 += RC) {
+    double t1[RC], t2[RC], t3[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) t1[c] = t2[c] = t3[c] = 0.0;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const double ar = val3[3 * p], ai = val3[3 * p + 1], as = val3[3 * p + 2];
+      const int64_t cidx = (int64_t)col[p] * nrhs + c0;
+#pragma unroll
+      for (int c = 0; c < RC; ++c)
+        if (c0 + c < nrhs) {
+          const double2 b = u[cidx + c];
+          const double bs = us != nullptr ? us[cidx + c] : b.x + b.y;
+          t1[c] = __fma_rn(ar, b.x, t1[c]);
+          t2[c] = __fma_rn(ai, b.y, t2[c]);
+          t3[c] = __fma_rn(as, bs, t3[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        t1[c] += __shfl_xor_sync(0xffffffffu, t1[c], s);
+        t2[c] += __shfl_xor_sync(0xffffffffu, t2[c], s);
+        t3[c] += __shfl_xor_sync(0xffffffffu, t3[c], s);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < RC; ++c)
+        if (c0 + c < nrhs) {
+          const int64_t idx = row * nrhs + c0 + c;
+          double2 o = y[idx];
+          o.x -= t1[c] - t2[c];
+          o.y -= t3[c] - t1[c] - t2[c];
+          y[idx] = o;
+        }
+    }
+  }
+}
+
 // Several RHS: warp per row, RHS columns in passes of RC.
 template <typename R, int RC>
 __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __restrict__ rowptr,
@@ -1390,7 +1449,8 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
         dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
         k_macro_gemm3<32, 32, 16><<<g, 256, 0, st>>>(static_cast<const double*>(W3v[t]), Nh, 2 * Nh, a.elems[t],
                                                      ncols, nrhs, a.off, reinterpret_cast<const double2*>(x),
-                                                     reinterpret_cast<double2*>(u), reinterpret_cast<double2*>(v));
+                                                     reinterpret_cast<double2*>(u), reinterpret_cast<double2*>(v),
+                                                     w.us);
         ++nl;
         continue;
       }
@@ -1474,7 +1534,17 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, ns);
     const unsigned blocks = (unsigned)((a.N + 7) / 8);
-    if (nrhs == 1)
+    if constexpr (sizeof(R) == 8) {
+      const double* val3 = static_cast<const double*>(p.val);
+      const double2* ud = reinterpret_cast<const double2*>(u);
+      double2* vd = reinterpret_cast<double2*>(v);
+      if (nrhs == 1)
+        k_spmv_near_3m<1><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+      else if (nrhs <= 4)
+        k_spmv_near_3m<4><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+      else
+        k_spmv_near_3m<8><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+    } else if (nrhs == 1)
       k_spmv_near1<R><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), u, v);
     else if (nrhs <= 4)
       k_spmv_near<R, 4><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), nrhs, u, v);

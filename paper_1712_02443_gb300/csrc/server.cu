@@ -200,7 +200,7 @@ mm_status mm_server_submit(mm_server* sv, const mm_request* q, uint64_t* ticket)
   // footprint estimate: Krylov basis and work vectors, grids, the near-field
   // blocks and, when the array assembles it (moderate sizes), the near-field
   // CSR (~650 entries per row, values of both precisions and columns)
-  const size_t csr = std::min<size_t>((size_t)nh * 650 * 28, (size_t)8 << 30);
+  const size_t csr = std::min<size_t>((size_t)nh * 650 * 36, (size_t)8 << 30);
   r->est = csr + (size_t)nh * q->nrhs * 16 * (q->solve.restart + 8) + (size_t)nh * q->nrhs * 256 + (size_t)ns * 64 +
            ((size_t)64 << 20);
   r->t_submit = now_s();
