@@ -379,7 +379,9 @@ __global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 4
     // T consecutive lanes share a node (T = 1, 2 or 4 when the block has the
     // threads): each takes every T-th group of four entries, then they add up
     // by shuffles within their group
-    const int T = (int)blockDim.x >= 4 * nodes ? 4 : ((int)blockDim.x >= 2 * nodes ? 2 : 1);
+    // (one right-hand side only: with several, the per-node accumulators are
+    // many and the shuffles cost more than the split saves)
+    const int T = RC > 1 ? 1 : ((int)blockDim.x >= 4 * nodes ? 4 : ((int)blockDim.x >= 2 * nodes ? 2 : 1));
     const int sub = threadIdx.x % T;
     const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x % 32) & ~(T - 1));
     for (int node = threadIdx.x / T; node < nodes; node += blockDim.x / T) {
