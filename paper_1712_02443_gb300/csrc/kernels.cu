@@ -352,7 +352,7 @@ template <> struct W4<double> {
 };
 
 template <typename R, int RC>
-__global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 4 ? 2 : 1) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+__global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 8 ? 1 : 2) k_project(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
                                                  const int32_t* __restrict__ inv_ptr,
                                                  const int32_t* __restrict__ inv_ent, const R* __restrict__ Pi,
                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ boxorg,
@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
 // ---------------------------------------------------------------- A4: interpolation (step iii)
 // y = v - [c_A sum_{xyz} Pi.Phi + c_phi Pi_phi.Phi_phi]; one CTA per element.
 template <typename R, int CR>
-__global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, CR == 1 && sizeof(R) == 4 ? 2 : 1) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+__global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, CR == 1 && sizeof(R) == 8 ? 1 : 2) k_interp(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
                                                 int bx, int by, int bz, const int32_t* __restrict__ anc,
                                                 const R* __restrict__ Pi, const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ boxorg, int nrhs, int rc,
@@ -1150,7 +1150,7 @@ struct NearGroupDev {
 };
 
 template <typename R, int TN, int MB>
-__global__ void __launch_bounds__(16 * (TN / 4), MB) k_near_blocks(
+__global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near_blocks(
     const NearGroupDev* __restrict__ groups, int ngroups, const longlong2* __restrict__ poff,
     const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
     int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int32_t* __restrict__ perm,
@@ -1313,13 +1313,14 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
 
 // Kernel shapes of the block near field: 0 = 32-column tiles (four CTAs per
 // SM), 1 = 32-column tiles compiled for five CTAs per SM (fewer registers, more
-// warps to hide the loads), 2 = 64-column tiles.
+// warps to hide the loads), 2 = 64-column tiles (two CTAs per SM).  The CTA
+// counts per SM apply to complex64; the FP64 forms keep their registers.
 constexpr int kNearShapes = 3;
 template <typename R>
 static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
                               const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks) {
   if (shape == 2)
-    near_blocks_launch<R, 64, 1>(a, p, nrhs, u, y, st, nl, ks);
+    near_blocks_launch<R, 64, 2>(a, p, nrhs, u, y, st, nl, ks);
   else if (shape == 1)
     near_blocks_launch<R, 32, 5>(a, p, nrhs, u, y, st, nl, ks);
   else
