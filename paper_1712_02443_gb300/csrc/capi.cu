@@ -390,6 +390,8 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : d_JE) cudaFree(q);
   for (void* q : d_T) cudaFree(q);
+  for (void* q : {(void*)da.nfb_tptr32, (void*)da.nfb_tlist32})
+    if (q) cudaFree(q);
   for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist,
                   (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
@@ -696,8 +698,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
       int64_t maxNa = 0;
       for (const auto& b : nb)
         if (!b.ptr.empty()) maxNa = std::max(maxNa, b.Na);
-      const int nmt = (int)((maxNa + 63) / 64);
-      std::vector<int32_t> na(nbk, 0), nbv(nbk, 0), tptr(nbk * std::max(nmt, 1) + 1, 0), tl;
+      std::vector<int32_t> na(nbk, 0), nbv(nbk, 0);
       std::vector<int64_t> boff(nbk, 0);
       int64_t o = 0;
       for (int64_t q = 0; q < nbk; ++q) {
@@ -705,20 +706,34 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         na[q] = (int32_t)b.Na;
         nbv[q] = (int32_t)b.Nb;
         boff[q] = o;
-        std::vector<char> used;
-        for (int mt = 0; mt < nmt; ++mt) {
-          tptr[q * nmt + mt] = (int32_t)tl.size();
-          if (b.ptr.empty() || (int64_t)mt * 64 >= b.Na) continue;
-          used.assign((size_t)((b.Nb + 15) / 16), 0);
-          const auto &pa = a->nf_perm[b.ta], &ib = a->nf_iperm[b.tb];
-          for (int64_t m = (int64_t)mt * 64; m < std::min<int64_t>(b.Na, (int64_t)mt * 64 + 64); ++m)
-            for (int64_t e = b.ptr[pa[m]]; e < b.ptr[pa[m] + 1]; ++e) used[ib[b.col[e]] / 16] = 1;
-          for (size_t kt = 0; kt < used.size(); ++kt)
-            if (used[kt]) tl.push_back((int32_t)kt);
-        }
         if (!b.ptr.empty()) o += b.Na * b.Nb;
       }
-      tptr[nbk * nmt] = (int32_t)tl.size();
+      // per (block, row tile of TM rows) the 16-column k tiles holding a non-zero,
+      // for the kernel's two row-tile heights (64 and 32)
+      auto tile_lists = [&](int TM, int& nmt, std::vector<int32_t>& tptr, std::vector<int32_t>& tl) {
+        nmt = (int)((maxNa + TM - 1) / TM);
+        tptr.assign(nbk * std::max(nmt, 1) + 1, 0);
+        tl.clear();
+        std::vector<char> used;
+        for (int64_t q = 0; q < nbk; ++q) {
+          const auto& b = nb[q];
+          for (int mt = 0; mt < nmt; ++mt) {
+            tptr[q * nmt + mt] = (int32_t)tl.size();
+            if (b.ptr.empty() || (int64_t)mt * TM >= b.Na) continue;
+            used.assign((size_t)((b.Nb + 15) / 16), 0);
+            const auto &pa = a->nf_perm[b.ta], &ib = a->nf_iperm[b.tb];
+            for (int64_t m = (int64_t)mt * TM; m < std::min<int64_t>(b.Na, (int64_t)mt * TM + TM); ++m)
+              for (int64_t e = b.ptr[pa[m]]; e < b.ptr[pa[m] + 1]; ++e) used[ib[b.col[e]] / 16] = 1;
+            for (size_t kt = 0; kt < used.size(); ++kt)
+              if (used[kt]) tl.push_back((int32_t)kt);
+          }
+        }
+        tptr[nbk * nmt] = (int32_t)tl.size();
+      };
+      int nmt = 0, nmt32 = 0;
+      std::vector<int32_t> tptr, tl, tptr32, tl32;
+      tile_lists(64, nmt, tptr, tl);
+      tile_lists(32, nmt32, tptr32, tl32);
       da.nfb_entries = o;
       if (o > 0) {
         da.nfb_nmt = nmt;
@@ -727,6 +742,9 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         da.nfb_off = dev_upload(boff.data(), boff.size(), acc);
         da.nfb_tptr = dev_upload(tptr.data(), tptr.size(), acc);
         da.nfb_tlist = dev_upload(tl.data(), tl.size(), acc);
+        da.nfb_nmt32 = nmt32;
+        da.nfb_tptr32 = dev_upload(tptr32.data(), tptr32.size(), acc);
+        da.nfb_tlist32 = dev_upload(tl32.data(), tl32.size(), acc);
         std::vector<int32_t> bpa(nbk, 0), bpb(nbk, 0);
         for (int64_t q = 0; q < nbk; ++q) {
           bpa[q] = perm_off[nb[q].ta];
@@ -765,7 +783,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         // tuning override: MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block kernel's shape
         if (const char* ns = std::getenv("MACROAIM_NEAR_SHAPE")) {
           int sh = -1, ks = 1;
-          if (std::sscanf(ns, "%d,%d", &sh, &ks) >= 1 && sh >= 0 && sh < 3 && ks >= 1 && ks <= 16) {
+          if (std::sscanf(ns, "%d,%d", &sh, &ks) >= 1 && sh >= 0 && sh < 5 && ks >= 1 && ks <= 16) {
             da.near_force_shape = sh;
             da.near_force_ks = ks;
           }

@@ -148,6 +148,9 @@ struct DevArray {
   int64_t* nfb_off = nullptr;           // per block: first entry in the dense values
   int32_t* nfb_tptr = nullptr;          // blocks x nfb_nmt + 1
   int32_t* nfb_tlist = nullptr;         // k-tile indices
+  int nfb_nmt32 = 0;                    // the same for 32-row tiles
+  int32_t* nfb_tptr32 = nullptr;
+  int32_t* nfb_tlist32 = nullptr;
   int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
   int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm
   int32_t* nfb_pb = nullptr;            // per block: offset of its column type's ordering

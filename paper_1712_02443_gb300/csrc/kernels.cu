@@ -1149,7 +1149,7 @@ struct NearGroupDev {
   int64_t first_pair, npairs;
 };
 
-template <typename R, int TN, int MB>
+template <typename R, int TN, int MB, int TM>
 __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near_blocks(
     const NearGroupDev* __restrict__ groups, int ngroups, const longlong2* __restrict__ poff,
     const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
@@ -1157,7 +1157,8 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
     const int32_t* __restrict__ bpa, const int32_t* __restrict__ bpb, int nrhs,
     int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
   typedef typename V2<R>::T C;
-  constexpr int TM = 64, TK = 16, TX = TN / 4, NT = 16 * TX;
+  // TM rows (64 or 32) x TN columns per CTA, MR x 4 complex outputs per thread
+  constexpr int TK = 16, TX = TN / 4, NT = 16 * TX, MR = TM / 16;
   __shared__ C As[TK][TM + 1];
   __shared__ C Bs[TK][TN + 1];
   __shared__ int64_t cin[TN], cout[TN];   // u / y index of row 0 of each column, -1 past the end
@@ -1222,9 +1223,9 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
       cout[cc] = -1;
     }
   }
-  C acc[4][4];
+  C acc[MR][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MR; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
   __syncthreads();
@@ -1266,13 +1267,13 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
     if (e + 1 < e1) fetch(e + 1);
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      C a[4], b[4];
+      C a[MR], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < MR; ++i) a[i] = As[kk][ty * MR + i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < MR; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           cmac(acc[i][j], a[i], b[j]);
@@ -1285,8 +1286,8 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
     const int64_t co = cout[tx * 4 + j];
     if (co < 0) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + ty * 4 + i;
+    for (int i = 0; i < MR; ++i) {
+      const int m = m0 + ty * MR + i;
       if (m < Na) {
         R* dst = reinterpret_cast<R*>(y + co + (int64_t)pa[m] * nrhs);
         atomicAdd(dst, -acc[i][j].x);
@@ -1296,30 +1297,38 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
   }
 }
 
-template <typename R, int TN, int MB>
+template <typename R, int TN, int MB, int TM = 64>
 static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
                                typename V2<R>::T* y, cudaStream_t st, int& nl, int ksplit) {
   int64_t tiles = 0;
-  for (const auto& g : a.nfg) tiles += ((g.npairs * nrhs + TN - 1) / TN) * ((g.Na + 63) / 64);
+  for (const auto& g : a.nfg) tiles += ((g.npairs * nrhs + TN - 1) / TN) * ((g.Na + TM - 1) / TM);
   if (tiles == 0) return;
   // ksplit > 1 splits each row tile's k tiles over several CTAs (the outputs are
   // accumulated atomically anyway): more CTAs when the output tiles are few
-  k_near_blocks<R, TN, MB><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
+  k_near_blocks<R, TN, MB, TM><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
       reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_poff,
-      static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, a.nfb_nmt, a.nfb_tptr, a.nfb_tlist,
+      static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, TM == 64 ? a.nfb_nmt : a.nfb_nmt32,
+      TM == 64 ? a.nfb_tptr : a.nfb_tptr32, TM == 64 ? a.nfb_tlist : a.nfb_tlist32,
       a.nfb_perm, a.nfb_pa, a.nfb_pb, nrhs, ksplit, u, y);
   ++nl;
 }
 
-// Kernel shapes of the block near field: 0 = 32-column tiles (four CTAs per
-// SM), 1 = 32-column tiles compiled for five CTAs per SM (fewer registers, more
-// warps to hide the loads), 2 = 64-column tiles (two CTAs per SM).  The CTA
-// counts per SM apply to complex64; the FP64 forms keep their registers.
-constexpr int kNearShapes = 3;
+// Kernel shapes of the block near field (64-row tiles unless named): 0 =
+// 32-column tiles (four CTAs per SM), 1 = 32-column tiles compiled for five CTAs
+// per SM (fewer registers, more warps to hide the loads), 2 = 64-column tiles
+// (two CTAs per SM), 3 = 32 x 32 tiles (eight CTAs per SM), 4 = 32 x 64 tiles
+// (four CTAs per SM).  32-row tiles skip more zero k tiles of the sparse blocks
+// (about 1.9 times the non-zero work instead of 2.3 at 16x16).  The CTA counts
+// per SM apply to complex64; the FP64 forms keep their registers.
+constexpr int kNearShapes = 5;
 template <typename R>
 static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
                               const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks) {
-  if (shape == 2)
+  if (shape == 4)
+    near_blocks_launch<R, 64, 4, 32>(a, p, nrhs, u, y, st, nl, ks);
+  else if (shape == 3)
+    near_blocks_launch<R, 32, 8, 32>(a, p, nrhs, u, y, st, nl, ks);
+  else if (shape == 2)
     near_blocks_launch<R, 64, 2>(a, p, nrhs, u, y, st, nl, ks);
   else if (shape == 1)
     near_blocks_launch<R, 32, 5>(a, p, nrhs, u, y, st, nl, ks);

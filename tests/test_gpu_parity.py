@@ -436,12 +436,13 @@ def test_near_field_stream_matches_in_order(ctx, monkeypatch, prec):
         assert rel <= (1e-6 if prec == mm.MM_C64 else 1e-13), rel
 
 
-@pytest.mark.parametrize("shape,ks", [(0, 1), (1, 2), (2, 4), (1, 3)])
+@pytest.mark.parametrize("shape,ks", [(0, 1), (1, 2), (2, 4), (1, 3), (3, 1), (3, 4), (4, 2)])
 @pytest.mark.parametrize("nrhs", [1, 5])
 def test_block_near_field_every_kernel_shape(ctx, c3, monkeypatch, shape, ks, nrhs):
-    """Every shape of the block near-field kernel (32-column tiles; the same for
-    five CTAs per SM; 64-column tiles) with several k splits, fixed through
-    MACROAIM_NEAR_SHAPE instead of the autotuner: sampled rows vs the oracle."""
+    """Every shape of the block near-field kernel (64-row tiles of 32 columns, the
+    same for five CTAs per SM, 64 columns; 32-row tiles of 32 and 64 columns) with
+    several k splits, fixed through MACROAIM_NEAR_SHAPE instead of the autotuner:
+    sampled rows vs the oracle."""
     monkeypatch.setenv("MACROAIM_NEAR_SHAPE", "%d,%d" % (shape, ks))
     g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
     la = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2, types=c3.types)
