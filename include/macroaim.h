@@ -191,7 +191,14 @@ void mm_array_destroy(mm_array* array);
  * v = D x, projection of u onto the grid (step i), FFT convolution with the
  * Green's spectrum (step ii), interpolation (step iii), near-field product,
  * y = v - (G_FF u + G_NF u).  x_dev, y_dev: (N^ x nrhs) complex in
- * `precision`; must not alias.  Queued on `stream`.                          */
+ * `precision`; must not alias.  Queued on `stream`: the near-field product runs
+ * on a second stream of the array beside the far-field chain (forked from and
+ * joined back into `stream` with events), so the call orders like one launch on
+ * `stream`.  An array serves one caller at a time.  Tuning overrides read when
+ * the array is created: MACROAIM_NEAR_OVERLAP=0 keeps the near field on
+ * `stream` in order; MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block
+ * near-field kernel's shape (0-4) instead of timing them on the first product;
+ * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                    void* stream);
 /* Same operator with host buffers: copies x in, applies, copies y out, and
@@ -202,8 +209,9 @@ mm_status mm_apply_host(mm_array* array, int32_t nrhs, const void* x_host, void*
  * equivalent-surface RWG functions): V^_n = <f^_n, n x n x E_inc> =
  * -<f^_n, E_inc>, E_inc = p exp(-j k0 k^.r), k^ = -(sin t cos p, sin t sin p,
  * cos t) (arriving from (theta, phi)), p = theta^ (pol 0) or phi^ (pol 1),
- * |E0| = 1.  theta/phi/pol are host arrays of length nrhs; V_dev is
- * (N^ x nrhs) in `precision`.                                                 */
+ * |E0| = 1.  theta/phi/pol are host arrays of length nrhs (copied before the
+ * call returns); V_dev is (N^ x nrhs) in `precision`.  Queued on `stream`
+ * (no host synchronisation).                                                  */
 mm_status mm_rhs_planewave(mm_array* array, int32_t nrhs, const double* theta, const double* phi,
                            const int32_t* pol, void* V_dev, int32_t precision, void* stream);
 
