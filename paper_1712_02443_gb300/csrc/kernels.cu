@@ -1338,7 +1338,7 @@ static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p,
 
 // Autotuner of the block near field: on the first product of an array with a
 // given right-hand-side count and precision, each (kernel shape, k split) pair
-// is timed with CUDA events (one warm-up, three timed launches) writing into a
+// is timed with CUDA events (one warm-up, one timed launch) writing into a
 // scratch buffer (the spectra, idle at this point of the product), and the
 // fastest is kept for that array.  Without a large enough scratch buffer the
 // size rule is used instead.
@@ -1363,7 +1363,7 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
       auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks); };
       run();
       cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 3; ++rep) run();
+      run();
       cudaEventRecord(e1, st);
       float ms = 0;
       if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
