@@ -4,18 +4,25 @@
 //   G_FF = sum_psi I_psi H_psi P_psi        (Sec. V, steps (i)-(iii))
 //
 //  k_macro_gemm   u = M_t x_e and v = D_t x_e for every element of type t (stacked
-//                 [M_t; D_t], one GEMM per type, shared by identical elements, Sec. III)
+//                 [M_t; D_t], one GEMM per type, shared by identical elements, Sec. III);
+//                 k_macro_gemm3 is its FP64 form with three real products per term
 //  k_project      step (i): grid currents (psi = x, y, z) and charges (phi) on each
-//                 element's stencil box, accumulated in shared memory, flushed with
-//                 atomics (neighbouring boxes overlap)
+//                 element's stencil box, gathered per box node from per-type lists,
+//                 added into the grids with atomics (neighbouring boxes overlap)
 //  k_fft_fwd_planes / k_fft_conv_lines / k_fft_inv_planes
 //                 step (ii): zero-padded 3D FFT convolution with the Green's
-//                 spectrum; direct DFT along the short z axis, Stockham mixed-radix
-//                 FFTs along y and x in shared memory, the spectrum multiply fused
-//                 between the forward and inverse x transforms
+//                 spectrum; direct DFT along the short z axis, warp FFTs along y and
+//                 x (in registers for complex64 lines of 32 R points, Stockham
+//                 mixed-radix stages in shared memory otherwise), the spectrum
+//                 multiply fused between the forward and inverse x transforms
 //  k_interp       step (iii): interpolation with I = P^T, psi-sum with c_A, c_phi,
 //                 and y = v - y_ff
-//  k_spmv_near    y -= G_NF u, precorrected near field (CSR, warp per row)
+//  k_near_blocks  v -= G_NF u as translation-invariant dense blocks (the default)
+//  k_spmv_near*   the same as CSR rows (warp per row; k_spmv_near_3m is the FP64
+//                 form with three real products per non-zero)
+//  matvec         the schedule: A1 on the caller's stream, then the near field on
+//                 the array's low-priority stream beside A2-A4 on its high-priority
+//                 stream, joined back into the caller's stream
 //
 // Layouts: vectors element-major with RHS innermost; grids [4 nrhs][Nx][Ny][Nz]
 // (batch b = psi * nrhs + j); partial spectra [b][x][ky][kz]; Green's spectrum
