@@ -166,6 +166,8 @@ struct GmresDev {
   int* flag;       // mapped host memory: [0] any column active, [1] k, [2] max kdone
   double* hres;    // mapped host memory: max over active columns of res / tol after the
                    // step (-1: not reported), for the host's convergence forecast
+  Z* hcol;         // (m+1) r: the step's Hessenberg column h + h2 (cooperative step)
+  double* hn2;     // r: the step's ||w||^2 (cooperative step)
   int m, r;
   int orth;        // 1 one Gram-Schmidt pass, 2 selective second pass, 3 two passes
 };
@@ -730,9 +732,10 @@ __device__ __forceinline__ double sum_blocks(const double* __restrict__ PN, int 
 //  2. h = sum of partials; w -= V h; partial ||w||^2;   [grid sync]
 //  3. if a column needs it: partial <V_i, w> [grid sync], h2, w -= V h2,
 //     partial ||w||^2                                   [grid sync]
-//  4. block 0: Hessenberg column h + h2, Givens rotations, residual
-//     estimate, k += 1;                                 [grid sync]
-//  5. V[k+1] = w / ||w|| (0 for finished columns), next operator input.
+//  4. every block: ||w|| per column from the partials; block 0 stores the
+//     column h + h2 and ||w||^2 for the Givens update (k_givens_col, launched
+//     after the step on a second stream) and sets k += 1;
+//  5. V[k+1] = w / ||w||, next operator input.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t vs, Z* __restrict__ w,
                                                       const Tin* __restrict__ yin, Tout* __restrict__ xnext,
@@ -799,8 +802,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   // the block partials, then a butterfly: the same order in every block, so
   // every block takes the same decision)
   int* need = reinterpret_cast<int*>(ws + wsn);   // r flags (shared)
-  __shared__ int any_s, kd_s, rq_s;
-  if (threadIdx.x == 0) any_s = 0, kd_s = 0, rq_s = 0;
+  __shared__ int any_s;
+  if (threadIdx.x == 0) any_s = 0;
   __syncthreads();
   if (gd.orth == 2) {
     for (int j = warp; j < r; j += nw) {
@@ -869,104 +872,127 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
       block_norms(w, n0, n1, r, blk, nblk, ws, PN2);
     grid.sync();
   }
-  // phase 4: block 0, a warp per column.  The lanes load the previous
-  // rotations 32 at a time and pass them on by shuffles, so the serial chain of
-  // rotations waits on no memory.  Each rotation's four complex products are
-  // taken by lanes 0-3 in one instruction sequence (lane 0: conj(c) h_i,
-  // 1: conj(s) h_i+1, 2: s h_i, 3: c h_i+1) and combined by shuffles.
-  if (blk == 0) {
-    for (int j = warp; j < r; j += nw) {
-      if (!gd.active[j]) continue;
-      const Z gk = gd.g[(int64_t)k * r + j];
-      const double tolj = gd.tol[j];
-      const double* PNf = (any_reorth && need[j]) ? PN2 : PN1;
-      double s2 = 0;
-      for (int b = lane; b < nblk; b += 32) s2 += PNf[(int64_t)j * nblk + b];
+  // phase 4: every block takes ||w|| of each column from the norm partials and
+  // scales its own rows; block 0 also stores the Hessenberg column h + h2 and
+  // ||w||^2 for the Givens update (k_givens_col), which runs on a second stream
+  // beside the next product, and advances k.  A column that met its target keeps
+  // producing basis vectors w / ||w||: its Krylov dimension stays where the
+  // Givens update stopped it, so they are never used.
+  double* scl = reinterpret_cast<double*>(ws);   // r column scales (the partials' space is free)
+  for (int j = warp; j < r; j += nw) {
+    const double* PNf = (any_reorth && need[j]) ? PN2 : PN1;
+    double s2 = 0;
+    for (int b = lane; b < nblk; b += 32) s2 += PNf[(int64_t)j * nblk + b];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s2 += shfl_x(s2, o);
-      for (int i = lane; i <= k; i += 32) {   // column j of h + h2 lives at hs[i r + j]
-        hs[i * r + j].x += h2s[i * r + j].x;
-        hs[i * r + j].y += h2s[i * r + j].y;
-      }
-      __syncwarp();
-      Z carry = hs[j];   // entry i of the column after rotations 0 .. i-1
-      for (int i0 = 0; i0 < k; i0 += 32) {
-        Z cl = make_double2(1, 0), sl = make_double2(0, 0);
-        if (i0 + lane < k) {
-          cl = gd.cs[(int64_t)(i0 + lane) * r + j];
-          sl = gd.sn[(int64_t)(i0 + lane) * r + j];
-        }
-        const int cnt = min(32, k - i0);
-        const int q = lane & 3;
-        for (int ii = 0; ii < cnt; ++ii) {   // rotation i: [[conj c, conj s], [-s, c]]
-          const int i = i0 + ii;
-          const Z c = shfl_idx(cl, ii), sg = shfl_idx(sl, ii);
-          const Z bb = hs[(i + 1) * r + j];
-          Z f = (q == 0 || q == 3) ? c : sg;
-          if (q < 2) f.y = -f.y;
-          const Z pq = zmul(f, (q == 0 || q == 2) ? carry : bb);
-          const Z t1 = shfl_idx(pq, 0), t2 = shfl_idx(pq, 1), u1 = shfl_idx(pq, 2), u2 = shfl_idx(pq, 3);
-          if (lane == 0) hs[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
-          carry = make_double2(u2.x - u1.x, u2.y - u1.y);
-        }
-      }
-      __syncwarp();
-      Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
-      for (int i = lane; i < k; i += 32) H[i] = hs[i * r + j];
-      if (lane == 0) {
-        const Z a = carry;   // rotated entry k; the new rotation pairs it with hn
-        const double hn = sqrt(fmax(0.0, s2));
-        const double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
-        const double inv = den > 0 ? 1.0 / den : 0.0;
-        const Z c = den > 0 ? make_double2(a.x * inv, a.y * inv) : make_double2(1, 0);
-        const Z sg = make_double2(hn * inv, 0);
-        gd.cs[(int64_t)k * r + j] = c;
-        gd.sn[(int64_t)k * r + j] = sg;
-        H[k] = make_double2(den, 0);
-        const Z sgk = zmul(sg, gk);
-        gd.g[(int64_t)(k + 1) * r + j] = make_double2(-sgk.x, -sgk.y);
-        gd.g[(int64_t)k * r + j] = zconjmul(c, gk);
-        const double res = sqrt(sgk.x * sgk.x + sgk.y * sgk.y);
-        gd.res[j] = res;
-        gd.kdone[j] = k + 1;
-        const int stop = !(res > tolj) || hn == 0.0 || !isfinite(hn);
-        gd.active[j] = stop ? 0 : 1;
-        gd.scale[j] = stop ? 0.0 : 1.0 / hn;
-        if (!stop) {
-          atomicOr(&any_s, 2);   // bit 1: a column stays active
-          // res / tol >= 0: its float bits order like the values
-          atomicMax(&rq_s, __float_as_int((float)fmin(res / tolj, 1e30)));
-        }
-        atomicMax(&kd_s, k + 1);
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    // flags for the host (read after the step's event): any column still
-    // active, the largest Krylov dimension; kd_s stays 0 only when no column
-    // was active on entry, and then comes from the columns' records
-    if (kd_s == 0)
-      for (int j = threadIdx.x; j < r; j += blockDim.x) atomicMax(&kd_s, gd.kdone[j]);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      *gd.k = k + 1;
-      gd.flag[0] = (any_s & 2) ? 1 : 0;
-      gd.flag[1] = k + 1;
-      gd.flag[2] = kd_s;
-      *gd.hres = (any_s & 2) ? (double)__int_as_float(rq_s) : -1.0;
+    for (int o = 16; o > 0; o >>= 1) s2 += shfl_x(s2, o);
+    if (lane == 0) {
+      scl[j] = (s2 > 0 && isfinite(s2)) ? 1.0 / sqrt(s2) : 0.0;
+      if (blk == 0) gd.hn2[j] = s2;
     }
   }
-  grid.sync();
+  if (blk == 0) {
+    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x)
+      gd.hcol[i] = make_double2(hs[i].x + h2s[i].x, hs[i].y + h2s[i].y);
+    if (threadIdx.x == 0) *gd.k = k + 1;
+  }
+  __syncthreads();
   // phase 5: next basis vector and the next operator input
   for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
     const int j = (int)(t % r);
-    const double sc = gd.scale[j];
+    const double sc = scl[j];
     const Z v = make_double2(w[t].x * sc, w[t].y * sc);
     V[(int64_t)(k + 1) * vs + t] = v;
     Tout o;
     o.x = v.x;
     o.y = v.y;
     xnext[t] = o;
+  }
+}
+
+// Givens update of the cooperative step's Hessenberg column (step k = *gd.k - 1:
+// the column h + h2 in gd.hcol, ||w||^2 in gd.hn2): previous rotations, the new
+// one, the residual estimate and the host flags; one CTA, a warp per column.  The
+// lanes load the previous rotations 32 at a time and pass them on by shuffles, so
+// the serial chain of rotations waits on no memory; each rotation's four complex
+// products are taken by lanes 0-3 in one instruction sequence (lane 0: conj(c)
+// h_i, 1: conj(s) h_i+1, 2: s h_i, 3: c h_i+1) and combined by shuffles.
+__global__ void __launch_bounds__(256) k_givens_col(GmresDev gd) {
+  extern __shared__ Z hs[];   // (k+1) r, column j at hs[i r + j]
+  const int m = gd.m, r = gd.r, k = *gd.k - 1;
+  const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __shared__ int any_s, kd_s, rq_s;
+  if (threadIdx.x == 0) any_s = 0, kd_s = 0, rq_s = 0;
+  for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hs[i] = gd.hcol[i];
+  __syncthreads();
+  for (int j = warp; j < r; j += nw) {
+    if (!gd.active[j]) continue;
+    const Z gk = gd.g[(int64_t)k * r + j];
+    const double tolj = gd.tol[j];
+    const double s2 = gd.hn2[j];
+    Z carry = hs[j];   // entry i of the column after rotations 0 .. i-1
+    for (int i0 = 0; i0 < k; i0 += 32) {
+      Z cl = make_double2(1, 0), sl = make_double2(0, 0);
+      if (i0 + lane < k) {
+        cl = gd.cs[(int64_t)(i0 + lane) * r + j];
+        sl = gd.sn[(int64_t)(i0 + lane) * r + j];
+      }
+      const int cnt = min(32, k - i0);
+      const int q = lane & 3;
+      for (int ii = 0; ii < cnt; ++ii) {   // rotation i: [[conj c, conj s], [-s, c]]
+        const int i = i0 + ii;
+        const Z c = shfl_idx(cl, ii), sg = shfl_idx(sl, ii);
+        const Z bb = hs[(i + 1) * r + j];
+        Z f = (q == 0 || q == 3) ? c : sg;
+        if (q < 2) f.y = -f.y;
+        const Z pq = zmul(f, (q == 0 || q == 2) ? carry : bb);
+        const Z t1 = shfl_idx(pq, 0), t2 = shfl_idx(pq, 1), u1 = shfl_idx(pq, 2), u2 = shfl_idx(pq, 3);
+        if (lane == 0) hs[i * r + j] = make_double2(t1.x + t2.x, t1.y + t2.y);
+        carry = make_double2(u2.x - u1.x, u2.y - u1.y);
+      }
+    }
+    __syncwarp();
+    Z* H = gd.H + ((int64_t)j * m + k) * (m + 1);
+    for (int i = lane; i < k; i += 32) H[i] = hs[i * r + j];
+    if (lane == 0) {
+      const Z a = carry;   // rotated entry k; the new rotation pairs it with hn
+      const double hn = sqrt(fmax(0.0, s2));
+      const double den = sqrt(a.x * a.x + a.y * a.y + hn * hn);
+      const double inv = den > 0 ? 1.0 / den : 0.0;
+      const Z c = den > 0 ? make_double2(a.x * inv, a.y * inv) : make_double2(1, 0);
+      const Z sg = make_double2(hn * inv, 0);
+      gd.cs[(int64_t)k * r + j] = c;
+      gd.sn[(int64_t)k * r + j] = sg;
+      H[k] = make_double2(den, 0);
+      const Z sgk = zmul(sg, gk);
+      gd.g[(int64_t)(k + 1) * r + j] = make_double2(-sgk.x, -sgk.y);
+      gd.g[(int64_t)k * r + j] = zconjmul(c, gk);
+      const double res = sqrt(sgk.x * sgk.x + sgk.y * sgk.y);
+      gd.res[j] = res;
+      gd.kdone[j] = k + 1;
+      const int stop = !(res > tolj) || hn == 0.0 || !isfinite(hn);
+      gd.active[j] = stop ? 0 : 1;
+      gd.scale[j] = stop ? 0.0 : 1.0 / hn;
+      if (!stop) {
+        atomicOr(&any_s, 2);   // bit 1: a column stays active
+        // res / tol >= 0: its float bits order like the values
+        atomicMax(&rq_s, __float_as_int((float)fmin(res / tolj, 1e30)));
+      }
+      atomicMax(&kd_s, k + 1);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // flags for the host (read after this kernel's event): any column still
+  // active, the largest Krylov dimension; kd_s stays 0 only when no column was
+  // active on entry, and then comes from the columns' records
+  if (kd_s == 0)
+    for (int j = threadIdx.x; j < r; j += blockDim.x) atomicMax(&kd_s, gd.kdone[j]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gd.flag[0] = (any_s & 2) ? 1 : 0;
+    gd.flag[1] = k + 1;
+    gd.flag[2] = kd_s;
+    *gd.hres = (any_s & 2) ? (double)__int_as_float(rq_s) : -1.0;
   }
 }
 
@@ -992,6 +1018,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
     int dev = 0, sms = 0, per = 0;
     MM_CK(cudaFuncSetAttribute(k_solve_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(Z) * (kSolveSmemK * kSolveSmemK + kSolveSmemK))));
+    MM_CK(cudaFuncSetAttribute(k_givens_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // hs, h2s: (m+1) r each; ws: max((m+1) warps, block threads); need flags
@@ -1042,6 +1069,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
     size_t o_tol = take(sizeof(double) * r), o_res = take(sizeof(double) * r), o_sc = take(sizeof(double) * r);
     size_t o_g = take(sizeof(Z) * (m + 1) * r), o_cs = take(sizeof(Z) * m * r), o_sn = take(sizeof(Z) * m * r);
     size_t o_H = take(sizeof(Z) * (size_t)r * (m + 1) * m), o_y = take(sizeof(Z) * (size_t)m * r);
+    size_t o_hc = take(sizeof(Z) * (size_t)(m + 1) * r), o_hn = take(sizeof(double) * r);
     MM_CK(cudaMalloc(&gstate_, b));
     char* base = static_cast<char*>(gstate_);
     GmresDev& g = *reinterpret_cast<GmresDev*>(gdev_);
@@ -1056,6 +1084,8 @@ Status Solver::ensure(int64_t N, int r, int m) {
     g.sn = reinterpret_cast<Z*>(base + o_sn);
     g.H = reinterpret_cast<Z*>(base + o_H);
     g.y = reinterpret_cast<Z*>(base + o_y);
+    g.hcol = reinterpret_cast<Z*>(base + o_hc);
+    g.hn2 = reinterpret_cast<double*>(base + o_hn);
     g.m = m;
     g.r = r;
     MM_CK(cudaHostAlloc(&flag_h_, sizeof(int) * 4 + sizeof(double), cudaHostAllocMapped));
@@ -1065,6 +1095,9 @@ Status Solver::ensure(int64_t N, int r, int m) {
     g.hres = reinterpret_cast<double*>(static_cast<char*>(fd) + sizeof(int) * 4);
     MM_CK(cudaEventCreateWithFlags(&ev_[0], cudaEventDisableTiming));
     MM_CK(cudaEventCreateWithFlags(&ev_[1], cudaEventDisableTiming));
+    // the Givens updates of the cooperative steps run on their own stream
+    MM_CK(cudaStreamCreateWithFlags(&gst_, cudaStreamNonBlocking));
+    for (auto* e : {&eva_, &evg_[0], &evg_[1]}) MM_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
   bytes_ = vec * (m + 5) + sizeof(float2) * 2 * (size_t)N * r;
   return {MM_OK, ""};
@@ -1078,6 +1111,12 @@ void Solver::release() {
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
   ev_[0] = ev_[1] = nullptr;
+  for (auto* e : {&eva_, &evg_[0], &evg_[1]}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  if (gst_) cudaStreamDestroy(gst_);
+  gst_ = nullptr;
   flag_h_ = nullptr;
   x64_ = P1_ = P2_ = PN_ = gstate_ = nullptr;
   V_ = w_ = t_ = nullptr;
@@ -1173,6 +1212,9 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     }
     bool stopped = false;
     int launched = 0;
+    // the events that mark a step's flags as written: the Givens kernel's for
+    // cooperative steps, the step's own otherwise
+    cudaEvent_t* sev = coop_ok_ ? evg_ : ev_;
     double q_last = -1.0;   // residual / target at the previous check
     // first basis vector V[0] = r0/||r0|| and the operator input
     if (prec == MM_C128)
@@ -1199,6 +1241,9 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
         Z* P2p = static_cast<Z*>(P2_);
         double* PNp = static_cast<double*>(PN_);
         int64_t Np = N;
+        // the previous step's Givens update (its own stream) wrote the flags this
+        // step reads; it has had the whole product to finish
+        if (it >= 1) MM_CK(cudaStreamWaitEvent(st, evg_[(it - 1) & 1], 0));
         if (prec == MM_C128) {
           const double2* yp = nullptr;
           double2* xp = static_cast<double2*>(x64_);
@@ -1213,6 +1258,11 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
                                             coop_smem_, st));
         }
         if (prof) prof->end(st, 1);
+        // Givens update beside the next product
+        MM_CK(cudaEventRecord(eva_, st));
+        MM_CK(cudaStreamWaitEvent(gst_, eva_, 0));
+        k_givens_col<<<1, 256, sizeof(Z) * (size_t)(m + 1) * r, gst_>>>(gd);
+        MM_CK(cudaEventRecord(evg_[it & 1], gst_));
       } else {
         if (yin) k_to_c128<<<grid_for(n), 256, 0, st>>>(static_cast<const float2*>(yin), w, n);
         k_cgs_dots<<<dim3(nblk_, r), 32 * nw, sh_dots, st>>>(V, vs, w, gd, N, nblk_, static_cast<Z*>(P1_));
@@ -1232,7 +1282,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
       MM_CK(cudaEventRecord(ev_[it & 1], st));
       launched = it + 1;
       if (it >= 1) {
-        MM_CK(cudaEventSynchronize(ev_[(it - 1) & 1]));
+        MM_CK(cudaEventSynchronize(sev[(it - 1) & 1]));
         if (!flag[0]) {
           stopped = true;
           break;
@@ -1242,7 +1292,7 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
         // the last step says this step may end the cycle, wait for it first.
         const double q = *hres;
         if (q > 0 && q_last > 0 && q * (q / q_last) <= 2.0) {
-          MM_CK(cudaEventSynchronize(ev_[it & 1]));
+          MM_CK(cudaEventSynchronize(sev[it & 1]));
           if (!flag[0]) {
             stopped = true;
             break;
@@ -1251,8 +1301,9 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
         q_last = *hres;
       }
     }
-    MM_CK(cudaEventSynchronize(ev_[(launched - 1) & 1]));
+    MM_CK(cudaEventSynchronize(sev[(launched - 1) & 1]));
     if (!flag[0]) stopped = true;
+    if (coop_ok_) MM_CK(cudaStreamWaitEvent(st, evg_[(launched - 1) & 1], 0));
     k_solve_y<<<r, 256, sizeof(Z) * (kSolveSmemK * kSolveSmemK + kSolveSmemK), st>>>(gd);
     if (prof) prof->begin(7, st);
     k_add_basis_dev<<<grid_for(n), 256, 0, st>>>(V, vs, gd, n, x);

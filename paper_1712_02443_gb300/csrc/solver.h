@@ -55,6 +55,8 @@ class Solver {
   void *x64_ = nullptr, *P1_ = nullptr, *P2_ = nullptr, *PN_ = nullptr, *gstate_ = nullptr, *flag_h_ = nullptr;
   alignas(16) unsigned char gdev_[160] = {0};   // GmresDev (device pointers of the cycle state)
   cudaEvent_t ev_[2] = {nullptr, nullptr};
+  cudaStream_t gst_ = nullptr;                    // Givens updates of the cooperative steps
+  cudaEvent_t eva_ = nullptr, evg_[2] = {nullptr, nullptr};
   bool coop_ok_ = false;       // the Arnoldi step runs as one cooperative launch
   size_t coop_smem_ = 0;
   size_t bytes_ = 0;
