@@ -298,12 +298,29 @@ mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev
  *  - the first call on a device looks up the scratch array's device address
  *    (cudaGetSymbolAddress, once per device, with that device current); make
  *    that first call before any stream capture;
+ *  - the call never times near-field kernel shapes (mm_apply does that on an
+ *    array's first product at a right-hand-side count, with CUDA events and a
+ *    host synchronisation): it reuses the shape that an earlier mm_apply or
+ *    mm_solve chose for this count and precision, else a size rule; it
+ *    creates no CUDA events and does not wait for the device;
  *  - every call shares the one scratch array and leaves its contents behind;
  *    calls that overlap on the GPU (other streams, other arrays, other
  *    threads) race on it: serialise them;
- *  - stage profiling is suspended during the call.                             */
+ *  - the call records nothing in the array's stage profiler and leaves the
+ *    profiler's state alone (profiling may stay enabled).                     */
 mm_status mm_apply_noalloc(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                            void* stream);
+
+/* ---------------------------------------------------------- testing hook
+ * Bounded waits of the tensor-core macromodel GEMM (MM_C64_BF16 and
+ * MM_C64_F16 products): with ms > 0, the GEMMs launched afterwards (by any
+ * array of the process) issue no products, so every wait of the kernel runs
+ * out after ms milliseconds; the kernel then waits for its copies in flight,
+ * frees its tensor memory and returns, and the call that next synchronises
+ * (mm_solve, mm_apply_host) returns MM_ETIMEOUT.  ms = 0 restores normal
+ * products.  For tests of the failure path only; no GPU fault is involved.
+ * The paper has no counterpart.  MM_EINVAL for ms < 0.                       */
+mm_status mm_test_tc_stall(int32_t ms);
 
 /* ----------------------------------------------------------------- server
  * A solve server for streams of requests (the library's request loop; the

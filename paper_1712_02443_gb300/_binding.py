@@ -107,6 +107,7 @@ _SIGS = {
     "mm_profile_enable": (ct.c_int, [P, ct.c_int32]),
     "mm_profile_stages": (ct.c_int, [P, ct.c_uint32]),
     "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    "mm_test_tc_stall": (ct.c_int, [ct.c_int32]),
 }
 
 _lib = None
@@ -282,6 +283,11 @@ def mm_apply_noalloc(array, nrhs: int, x_dev, y_dev, precision: int, stream=None
     """mm_apply without any device allocation (shared static scratch of at most 16 MiB)."""
     _check(load().mm_apply_noalloc(array, nrhs, _ptr(x_dev), _ptr(y_dev), precision, _stream(stream)),
            _ctx_of.get(array.value))
+
+
+def mm_test_tc_stall(ms: int) -> None:
+    """Testing hook: ms > 0 makes tensor-core GEMMs issue no products and give up their waits after ms ms."""
+    _check(load().mm_test_tc_stall(int(ms)), None)
 
 
 def mm_apply_host(array, nrhs: int, x_host: np.ndarray, y_host: np.ndarray, precision: int) -> None:

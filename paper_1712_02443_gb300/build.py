@@ -35,7 +35,7 @@ def _digest() -> str:
     h = hashlib.sha256()
     for d in (CSRC, INC):
         for f in sorted(os.listdir(d)):
-            if f.endswith((".cpp", ".cu", ".h")):
+            if f.endswith((".cpp", ".cu", ".cuh", ".h")):
                 with open(os.path.join(d, f), "rb") as fh:
                     h.update(f.encode() + fh.read())
     h.update(" ".join(ARCH).encode())

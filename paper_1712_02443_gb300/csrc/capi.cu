@@ -1301,6 +1301,7 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   if (precision == MM_C128 && !a->da.pd.ready)
     return fail(ctx, MM_EINVAL,
                 "complex128 operator not resident: call mm_apply or mm_solve at complex128 once before");
+  API_TRY
   const auto& da = a->da;
   const size_t cs = precision == MM_C128 ? 16 : 8;
   const size_t vec = align256(cs * (size_t)da.N * nrhs);
@@ -1334,13 +1335,22 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   w.spec = base + 2 * vec + grid;
   w.bytes = need;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const bool prof_on = a->da.prof.on;
-  a->da.prof.on = false;   // profiling creates CUDA events
+  // no stage events (they are created on demand) and no timing of near-field
+  // kernel shapes (it synchronises): an untuned right-hand-side count takes
+  // the size rule
+  const unsigned flags = mm::kMvNoTune | mm::kMvNoProfile;
   if (precision == MM_C64)
-    e = mm::matvec<float>(a->da, a->da.pf, w, nrhs, x_dev, y_dev, st);
+    e = mm::matvec<float>(a->da, a->da.pf, w, nrhs, x_dev, y_dev, st, 0, false, flags);
   else
-    e = mm::matvec<double>(a->da, a->da.pd, w, nrhs, x_dev, y_dev, st);
-  a->da.prof.on = prof_on;
+    e = mm::matvec<double>(a->da, a->da.pd, w, nrhs, x_dev, y_dev, st, 0, false, flags);
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("matvec: ") + cudaGetErrorString(e));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+// ---- testing hook of the bounded tensor-core waits ------------------------------
+extern "C" mm_status mm_test_tc_stall(int32_t ms) {
+  if (ms < 0) return MM_EINVAL;
+  mm::tc_set_stall(ms);
   return MM_OK;
 }

@@ -1,6 +1,7 @@
 // Device-side structures and kernel launchers of libmacroaim.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -66,6 +67,13 @@ struct Profiler {
   }
 };
 
+// Element pairs coupled by one near-field block, as the kernels read them (the
+// device copy of DevArray::NfGroup, same layout).
+struct NearGroupDev {
+  int q, Na;
+  int64_t first_pair, npairs;
+};
+
 // Radix plan of one FFT length (radices from {8, 4, 2, 3, 5, 7}).
 struct FftPlan {
   int L = 1;
@@ -89,6 +97,11 @@ struct DevPrec {
   std::vector<void*> Atc[2];   // [0] BF16, [1] FP16; (Mp x Kp) 16-bit
   std::vector<int> Mp, Kp;
   void* nfb_val = nullptr;     // near-field blocks, dense row-major, at DevArray::nfb_off
+  // complex64 only: the blocks for the tensor-core near field, complex rows of
+  // interleaved (re, im) FP32 at DevArray::nfb_arow, row pitch nfb_tc_pitch
+  // floats; TF32 hi parts in rows [0, nfb_tc_rows), lo parts below them
+  void* nfb_tc = nullptr;
+  CUtensorMap nfb_tmap;        // 2-D map over nfb_tc: box 32 floats x 128 rows, 128-byte swizzle
   std::vector<void*> PJ;       // per type: block-Jacobi operator (Nh x Nh), uploaded on first use
   // the right-preconditioned operator's macromodel matrices [M PJ; D PJ] (same
   // layouts as W and Atc), uploaded with PJ: Z P^-1 x takes one GEMM
@@ -151,6 +164,13 @@ struct DevArray {
   int nfb_nmt32 = 0;                    // the same for 32-row tiles
   int32_t* nfb_tptr32 = nullptr;
   int32_t* nfb_tlist32 = nullptr;
+  int nfb_nmt128 = 0;                   // the same for 128-row tiles (tensor-core near field)
+  int32_t* nfb_tptr128 = nullptr;
+  int32_t* nfb_tlist128 = nullptr;
+  int32_t* nfb_arow = nullptr;          // per block: its first row in the tensor-core block rows
+  int nfb_tc_rows = 0;                  // rows of all blocks (tensor-core layout)
+  int nfb_tc_pitch = 0;                 // floats per row (2 Nb of the widest block, rounded up to 32)
+  int* near_err = nullptr;              // device flag of the tensor-core near field's bounded waits
   int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
   int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm
   int32_t* nfb_pb = nullptr;            // per block: offset of its column type's ordering
@@ -184,12 +204,16 @@ struct DevArray {
   std::vector<double> hval, hGhat;      // complex128 interleaved
 };
 
+// Flags of matvec: kMvNoTune never times near-field kernel shapes (an untuned
+// right-hand-side count takes the size rule and is not remembered);
+// kMvNoProfile records no stage events (the array's profiler is left alone).
+constexpr unsigned kMvNoTune = 1u, kMvNoProfile = 2u;
 // gemm_mode: 0 CUDA-core GEMM; 1 BF16 / 2 FP16 tensor-core GEMM (complex64 only)
 // pre: apply Z P^-1 (the block-Jacobi right-preconditioned operator) through
 // the fused macromodel matrices p.WP / p.AtcP
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y, cudaStream_t st,
-                   int gemm_mode = 0, bool pre = false);
+                   int gemm_mode = 0, bool pre = false, unsigned flags = 0);
 // y = P^-1 x with P^-1 the per-type block-Jacobi operators (p.PJ).
 template <typename R>
 cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* x, void* y, cudaStream_t st);

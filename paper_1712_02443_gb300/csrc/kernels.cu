@@ -1151,11 +1151,6 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
 // so its outputs receive several block products: they are accumulated with
 // atomic adds (summation order not fixed).  The CTA's set-up loads are issued
 // in as few dependent rounds as possible (the CTAs do only a few k tiles each).
-struct NearGroupDev {
-  int q, Na;
-  int64_t first_pair, npairs;
-};
-
 template <typename R, int TN, int MB, int TM>
 __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near_blocks(
     const NearGroupDev* __restrict__ groups, int ngroups, const longlong2* __restrict__ poff,
@@ -1424,7 +1419,7 @@ cudaError_t kernels_init(DevArray& a) {
 
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st,
-                   int gemm_mode, bool pre) {
+                   int gemm_mode, bool pre, unsigned flags) {
   typedef typename V2<R>::T C;
   const C* x = static_cast<const C*>(xv);
   C* y = static_cast<C*>(yv);
@@ -1438,7 +1433,8 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   const size_t gbytes = sizeof(C) * (size_t)B * Nx * Ny * Nz;
   cudaError_t e = cudaMemsetAsync(grid, 0, gbytes, st);
   if (e != cudaSuccess) return e;
-  Profiler& pr = a.prof;
+  Profiler off;   // stays disabled: records nothing, creates no events
+  Profiler& pr = (flags & kMvNoProfile) ? off : a.prof;
   const int sb = sizeof(R) == 8 ? 8 : 0;   // profiler slot base of this precision
   // A1: u = M x, v = D x, per type
   pr.begin(sb + 0, st);
@@ -1500,11 +1496,20 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     auto it = a.near_tune.find(key);
     if (it == a.near_tune.end() && a.near_force_shape >= 0)
       it = a.near_tune.emplace(key, std::make_pair(a.near_force_shape, a.near_force_ks)).first;
-    if (it == a.near_tune.end())
+    if (it != a.near_tune.end()) {
+      tn = it->second.first;
+      ks = it->second.second;
+    } else if (flags & kMvNoTune) {
+      // size rule, not remembered: a later tuned product may still time the shapes
+      const auto rule = near_autotune<R>(a, p, nrhs, u, nullptr, 0, st);
+      tn = rule.first;
+      ks = rule.second;
+    } else {
       it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
                                                       (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
-    tn = it->second.first;
-    ks = it->second.second;
+      tn = it->second.first;
+      ks = it->second.second;
+    }
     if (a.near_force_shape >= 0) {
       tn = a.near_force_shape;
       ks = a.near_force_ks;
@@ -1658,9 +1663,9 @@ cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* xv, 
 template cudaError_t precond_apply<float>(DevArray&, DevPrec<float>&, int, const void*, void*, cudaStream_t);
 template cudaError_t precond_apply<double>(DevArray&, DevPrec<double>&, int, const void*, void*, cudaStream_t);
 template cudaError_t matvec<float>(DevArray&, DevPrec<float>&, Work&, int, const void*, void*, cudaStream_t, int,
-                                   bool);
+                                   bool, unsigned);
 template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, const void*, void*, cudaStream_t, int,
-                                    bool);
+                                    bool, unsigned);
 template size_t fft_smem_bytes<float>(const DevArray&, int);
 template size_t fft_smem_bytes<double>(const DevArray&, int);
 

@@ -14,11 +14,9 @@
 // K is laid out as [Re part: Nh entries | zeros up to Nhp = Nh rounded up to 8 |
 // Im part: Nh entries], so that both halves of a B row start 16-byte aligned.
 //
-// Kernel: persistent, one CTA per SM, 320 threads in three roles, CM CTAs per
-// cluster (CM = 1 or 2) working on CM consecutive M tiles of one N tile.
-//   warp 0     one lane issues TMA copies of its 128 x 64 A slice and of its
-//              share (256/CM rows) of the 256 x 64 B slice, the latter
-//              multicast to every CTA of the cluster, into a 4-stage ring of
+// Kernel: persistent, one CTA per SM, 320 threads in three roles.
+//   warp 0     one lane issues TMA copies of the 128 x 64 A slice and the
+//              256 x 64 B slice of each k step into a 4-stage ring of
 //              128-byte-swizzled K-major buffers;
 //   warp 1     allocates 512 TMEM columns; one lane issues tcgen05.mma
 //              (M 128, N 256, K 16) and commits each stage back to its slot;
@@ -28,22 +26,22 @@
 //              of complex rows to u (rows < Nh) or v.
 // Two accumulators (2 x 256 columns) let the epilogue of one tile overlap the
 // main loop of the next.  Tiles are ordered M-fastest so that the CTAs working
-// at one time share their B slices in L2; with CM = 2 each B slice is read from
-// L2 once per cluster, so L2 serves 32 KB instead of 48 KB per 128 x 256 x 64
-// step.  A stage is refilled only after the products of every CTA that holds
-// a copy of it have completed (each CTA's commit arrives on the stage barrier
-// of all CTAs in the cluster).  Every mbarrier wait is bounded in
-// time; on expiry the kernel records an error, the other roles stop, copies
-// and products in flight are waited for (bounded) and TMEM is freed.
+// at one time share their B slices in L2.  Each CTA copies its own operands
+// from this GPU's memory into its own shared memory (no cluster launch).
+// Every mbarrier wait is bounded in time; on expiry the kernel
+// records an error, the other roles stop, copies and products in flight are
+// waited for (bounded) and TMEM is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <mutex>
 
 #include "tc_gemm.h"
+#include "tcgen05.cuh"
 
 namespace mm {
 
@@ -55,127 +53,25 @@ constexpr int B_BYTES = TBN * TBK * 2;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t kTmemCols = 2 * TBN;
 constexpr int kThreads = 320;   // producer warp, MMA warp, 8 epilogue warps
-constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait (default limit)
+constexpr unsigned long long kDrainNs = 1000000000ull;  // 1 s for copies / products in flight at exit
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using namespace tcx;
 
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 1024-byte atoms.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 bytes
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor for kind::f16: FP32 accumulate, K-major A and B, M 128, N 256.
-__host__ __device__ constexpr uint32_t make_idesc(bool bf16) {
-  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(TBN >> 3) << 17) |
-         ((uint32_t)(TBM >> 4) << 24);
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for completion of the phase with the given parity.  Gives up after
-// kWaitNs, or (when stop is non-null) as soon as another role has aborted.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stop) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 63) == 0) {
-      if (stop && *stop) return false;
-      if (global_ns() - t0 > kWaitNs) return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint32_t dst, uint32_t bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint32_t dst, uint32_t bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) { return make_desc_sw128(saddr); }
 
 }  // namespace
 
 // C (Mp x Np, FP32) = A (Mp x Kp) B^T (Np x Kp); epilogue writes complex rows
 // (2i, 2i+1) of C to out_u (i < Nh) or out_v (i >= Nh) for column n = j*nrhs+c.
-template <bool BF16, int CM>
+// wait_ns bounds every wait of the main loops; stall != 0 (a testing hook) makes
+// the MMA issuer issue nothing, so that the other roles' waits run out.
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int num_m,
               int num_groups, int nk, int Nh, int ncols, int nrhs, const int32_t* __restrict__ elems,
               const int64_t* __restrict__ off, float2* __restrict__ out_u, float2* __restrict__ out_v,
-              int* __restrict__ err) {
+              int* __restrict__ err, uint64_t wait_ns, int stall) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -184,12 +80,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int abort_flag;
   volatile int* stop = &abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // tile groups: CM consecutive M tiles of one N tile per cluster
-  const int num_mg = (num_m + CM - 1) / CM;
-  const int rank = CM > 1 ? (int)cluster_rank() : 0;
-  const int cid = blockIdx.x / CM, ncl = gridDim.x / CM;
-  constexpr uint16_t kMask = (uint16_t)((1u << CM) - 1);
-  constexpr int B_ROWS = TBN / CM;   // B rows this CTA copies (and multicasts)
+  // tiles g = (n tile) * num_m + (m tile), M fastest
+  const int cid = blockIdx.x, ncl = gridDim.x;
 
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -200,21 +92,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), CM);   // one commit from each CTA of the cluster
+      mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull_bar[b]), 1);
       mbar_init(smem_u32(&tempty_bar[b]), 8);   // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&drain_bar), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (CM > 1) cluster_sync();   // peers signal these barriers: all must be initialised first
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
@@ -224,11 +114,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       for (int g = cid; g < num_groups && ok; g += ncl) {
-        const int m0 = ((g % num_mg) * CM + rank) * TBM, n0 = (g / num_mg) * TBN;
+        const int m0 = (g % num_m) * TBM, n0 = (g / num_m) * TBN;
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t r = it / STAGES;
-          if (!mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop)) {
+          if (!mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop, wait_ns)) {
             ok = false;
             break;
           }
@@ -236,11 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* sa = base + s * STAGE_BYTES;
           mbar_expect_tx(fb, STAGE_BYTES);
           tma_load_2d(&tmA, smem_u32(sa), fb, kt * TBK, m0);
-          if (CM == 1)
-            tma_load_2d(&tmB, smem_u32(sa + A_BYTES), fb, kt * TBK, n0);
-          else
-            tma_load_2d_mc(&tmB, smem_u32(sa + A_BYTES + rank * B_ROWS * 128), fb, kt * TBK, n0 + rank * B_ROWS,
-                           kMask);
+          tma_load_2d(&tmB, smem_u32(sa + A_BYTES), fb, kt * TBK, n0);
         }
       }
       if (!ok && !*stop) {
@@ -249,17 +135,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // copies still in flight land before the CTA's shared memory is released
       for (uint32_t q = it > (uint32_t)STAGES ? it - STAGES : 0; q < it; ++q)
-        mbar_wait(smem_u32(&full_bar[q % STAGES]), (q / STAGES) & 1, nullptr);
+        mbar_wait(smem_u32(&full_bar[q % STAGES]), (q / STAGES) & 1, nullptr, kDrainNs);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      const uint32_t idesc = make_idesc(BF16);
+      constexpr uint32_t idesc = make_idesc(BF16 ? 1u : 0u, TBM, TBN);
       uint32_t it = 0, lt = 0;
       bool ok = true;
-      for (int g = cid; g < num_groups && ok; g += ncl, ++lt) {
+      for (int g = stall ? num_groups : cid; g < num_groups && ok; g += ncl, ++lt) {
         const uint32_t b = lt & 1, ub = lt >> 1;
-        if (!mbar_wait(smem_u32(&tempty_bar[b]), (ub & 1) ^ 1, stop)) {
+        if (!mbar_wait(smem_u32(&tempty_bar[b]), (ub & 1) ^ 1, stop, wait_ns)) {
           ok = false;
           break;
         }
@@ -268,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int s = (int)(it % STAGES);
           const uint32_t r = it / STAGES;
-          if (!mbar_wait(smem_u32(&full_bar[s]), r & 1, stop)) {
+          if (!mbar_wait(smem_u32(&full_bar[s]), r & 1, stop, wait_ns)) {
             ok = false;
             break;
           }
@@ -284,10 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
                 "l"(a), "l"(bb), "r"(idesc), "r"(acc));
           }
-          if (CM == 1)
-            umma_commit(smem_u32(&empty_bar[s]));
-          else
-            umma_commit_mc(smem_u32(&empty_bar[s]), kMask);
+          umma_commit(smem_u32(&empty_bar[s]));
         }
         if (!ok) break;
         umma_commit(smem_u32(&tfull_bar[b]));
@@ -298,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // every product issued here completes before TMEM and the stage buffers go away
       umma_commit(smem_u32(&drain_bar));
-      mbar_wait(smem_u32(&drain_bar), 0, nullptr);
+      mbar_wait(smem_u32(&drain_bar), 0, nullptr, kDrainNs);
     }
   } else {
     // ---- epilogue (warps 2-9).  Warp w reads TMEM lane quarter q = w % 4 (C
@@ -318,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int g = cid; g < num_groups; g += ncl, ++lt) {
       const uint32_t b = lt & 1, ub = lt >> 1;
-      const int m0 = ((g % num_mg) * CM + rank) * TBM;
-      const int nw = (g / num_mg) * TBN + half * (TBN / 2);   // first column of this warp
+      const int m0 = (g % num_m) * TBM;
+      const int nw = (g / num_m) * TBN + half * (TBN / 2);   // first column of this warp
       // output offsets of this lane's column in each chunk, loaded while the
       // accumulator is still being computed
       int64_t eb[NCH];
@@ -334,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int k = 0; k < NCH; ++k) eb[k] = off[eb[k]];
       int w_ok = 1;
-      if (lane == 0) w_ok = mbar_wait(smem_u32(&tfull_bar[b]), ub & 1, stop) ? 1 : 0;
+      if (lane == 0) w_ok = mbar_wait(smem_u32(&tfull_bar[b]), ub & 1, stop, wait_ns) ? 1 : 0;
       w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
       if (!w_ok) {
         ok = false;
@@ -380,9 +263,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // peers may still multicast into this CTA's buffers or arrive on its
-  // barriers until they are done: leave together
-  if (CM > 1) cluster_sync();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -444,6 +324,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
+std::atomic<int> g_stall_ms{0};
 std::once_flag g_encode_once;
 int g_sms[64] = {0};
 
@@ -451,29 +332,35 @@ int g_sms[64] = {0};
 // ld elements; box = box_inner x box_rows, 128-byte swizzle, zero fill outside.
 bool encode_2d(CUtensorMap* m, bool bf16, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
                uint32_t box_inner, uint32_t box_rows) {
+  return tc_encode_2d(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, base, inner,
+                      rows, ld * 2, box_inner, box_rows);
+}
+
+}  // namespace
+
+bool tc_encode_2d(CUtensorMap* m, CUtensorMapDataType dtype, const void* base, uint64_t inner, uint64_t rows,
+                  uint64_t ld_bytes, uint32_t box_inner, uint32_t box_rows) {
+  if (!g_encode) return false;
   const cuuint64_t dims[2] = {inner, rows};
-  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint64_t strides[1] = {ld_bytes};
   const cuuint32_t box[2] = {box_inner, box_rows};
   const cuuint32_t es[2] = {1, 1};
-  return g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
-                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  return g_encode(m, dtype, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
+int tc_stall_ms() { return g_stall_ms.load(); }
 
 // stage ring + epilogue staging (8 warps x 16 x 17 complex) + alignment slack
 size_t tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 8 * 16 * 17 * 8 + 1024; }
 
 int tc_k_split(int Nh) { return (Nh + 7) / 8 * 8; }
 
-// CTAs per cluster along M.  1 by default: multicasting B to a pair measured
-// no faster on GB300 (the main loop is not bound by L2 reads) and pads an odd
-// number of M tiles.
-int g_cluster_m = 1;
-
-void tc_set_cluster(int cm) { g_cluster_m = cm == 1 ? 1 : 2; }
+// Testing hook (mm_test_tc_stall): a non-zero limit makes the following
+// tensor-core kernels issue no products and give up every wait after that many
+// milliseconds.
+void tc_set_stall(int ms) { g_stall_ms.store(ms < 0 ? 0 : ms); }
 
 cudaError_t tc_gemm_init() {
   std::call_once(g_encode_once, [] {
@@ -483,8 +370,6 @@ cudaError_t tc_gemm_init() {
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       g_encode = reinterpret_cast<EncodeTiledFn>(fn);
-    // tuning override: MACROAIM_TC_CLUSTER=2 multicasts B slices to CTA pairs
-    if (const char* c = std::getenv("MACROAIM_TC_CLUSTER")) tc_set_cluster(std::atoi(c));
   });
   if (!g_encode) return cudaErrorNotSupported;
   int dev = 0;
@@ -494,53 +379,26 @@ cudaError_t tc_gemm_init() {
     e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-#define MM_TC_ATTR(B, C)                                                                                  \
-  e = cudaFuncSetAttribute(k_tc_gemm<B, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()); \
+  e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
   if (e != cudaSuccess) return e;
-  MM_TC_ATTR(true, 1) MM_TC_ATTR(false, 1) MM_TC_ATTR(true, 2) MM_TC_ATTR(false, 2)
-#undef MM_TC_ATTR
+  e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+  if (e != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 namespace {
 
-template <bool BF16, int CM>
+template <bool BF16>
 cudaError_t launch_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, int num_m, int num_n, int nk, int Nh,
                       int ncols, int nrhs, const int32_t* elems, const int64_t* off, float2* u, float2* v, int* err,
                       int sms, cudaStream_t st) {
-  const int num_groups = (num_m + CM - 1) / CM * num_n;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = tc_smem_bytes();
-  cfg.stream = st;
-  int clusters = sms / CM;
-  if (CM > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CM;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3((unsigned)(CM * clusters));
-    // co-resident clusters, queried once per device (-1: query failed)
-    static int active_cache[64];
-    static std::once_flag active_once[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64) {
-      std::call_once(active_once[dev], [&] {
-        int a = 0;
-        active_cache[dev] =
-            cudaOccupancyMaxActiveClusters(&a, k_tc_gemm<BF16, CM>, &cfg) == cudaSuccess && a > 0 ? a : -1;
-      });
-      if (active_cache[dev] > 0) clusters = std::min(clusters, active_cache[dev]);
-    }
-  }
-  clusters = std::max(1, std::min(clusters, num_groups));
-  cfg.gridDim = dim3((unsigned)(CM * clusters));
-  return cudaLaunchKernelEx(&cfg, k_tc_gemm<BF16, CM>, tmA, tmB, num_m, num_groups, nk, Nh, ncols, nrhs, elems, off,
-                            u, v, err);
+  const int num_groups = num_m * num_n;
+  const int ctas = std::max(1, std::min(sms, num_groups));
+  const int stall_ms = g_stall_ms.load();
+  const uint64_t wait_ns = stall_ms > 0 ? (uint64_t)stall_ms * 1000000ull : kWaitNs;
+  k_tc_gemm<BF16><<<ctas, kThreads, tc_smem_bytes(), st>>>(tmA, tmB, num_m, num_groups, nk, Nh, ncols, nrhs, elems,
+                                                          off, u, v, err, wait_ns, stall_ms > 0 ? 1 : 0);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -560,21 +418,17 @@ cudaError_t tc_macro_gemm(bool bf16, const uint16_t* A, int Mp, int Kp, int Nh, 
     else
       k_pack_b<false><<<pg, 256, 0, st>>>(x, Nh, Nhp, nrhs, nel, elems, off, Kp, Bt);
   }
-  const int cm = g_cluster_m;
   CUtensorMap tmA, tmB;
   if (!encode_2d(&tmA, bf16, A, (uint64_t)Kp, (uint64_t)Mp, (uint64_t)Kp, TBK, TBM) ||
-      !encode_2d(&tmB, bf16, Bt, (uint64_t)(Nhp + Nh), (uint64_t)ncols, (uint64_t)Kp, TBK, TBN / cm))
+      !encode_2d(&tmB, bf16, Bt, (uint64_t)(Nhp + Nh), (uint64_t)ncols, (uint64_t)Kp, TBK, TBN))
     return cudaErrorInvalidValue;
   const int num_m = Mp / TBM, num_n = (ncols + TBN - 1) / TBN;
   int dev = 0;
   cudaGetDevice(&dev);
   const int sms = (dev >= 0 && dev < 64 && g_sms[dev] > 0) ? g_sms[dev] : 148;
   const int nk = Kp / TBK;
-  if (cm == 1)
-    return bf16 ? launch_tc<true, 1>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st)
-                : launch_tc<false, 1>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st);
-  return bf16 ? launch_tc<true, 2>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st)
-              : launch_tc<false, 2>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st);
+  return bf16 ? launch_tc<true>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st)
+              : launch_tc<false>(tmA, tmB, num_m, num_n, nk, Nh, ncols, nrhs, elems, off, u, v, err, sms, st);
 }
 
 int tc_tile_m() { return TBM; }

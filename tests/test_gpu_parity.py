@@ -6,7 +6,8 @@ computed live by the oracle.  Tolerances:
   relative L2 <= 1e-11, worst element <= 1e-10 of max |y|;
 * complex64 operator: FP32 arithmetic over sums of a few hundred terms
   (GEMM k = N^_t, ~400 near-field terms, FFT) gives ~1e-6 relative per entry;
-  the bar is relative L2 <= 2e-5 and worst element <= 1e-4 of max |y|.
+  the bar is the stated matvec tolerance, relative L2 <= 1e-5, and worst
+  element <= 1e-4 of max |y|.
 """
 import os
 
@@ -22,7 +23,7 @@ from paper_1712_02443_gb300.arrays import loop_array  # noqa: E402
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 K0 = 2.0 * np.pi
-TOL = {mm.MM_C128: (1e-11, 1e-10), mm.MM_C64: (2e-5, 1e-4)}
+TOL = {mm.MM_C128: (1e-11, 1e-10), mm.MM_C64: (1e-5, 1e-4)}
 DT = {mm.MM_C128: torch.complex128, mm.MM_C64: torch.complex64}
 
 

@@ -120,3 +120,23 @@ def test_tensorcore_many_tiles_per_cta(c1, loop_model):
             assert rel <= BAR[prec], (prec, rel)
     finally:
         mm.mm_array_destroy(la.array)
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C64_F16, mm.MM_C64_BF16])
+def test_tensorcore_wait_limit_reports_timeout(c1, prec):
+    """The failure path of the bounded waits, with no GPU fault: the testing
+    hook makes the GEMM issue no products, so its waits run out after 20 ms;
+    the call returns MM_ETIMEOUT, and the next product (hook off) is correct."""
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    x = np.ascontiguousarray(g["x"].astype(np.complex64))
+    y = np.zeros_like(x)
+    mm.mm_test_tc_stall(20)
+    try:
+        with pytest.raises(mm.MacroAIMError) as e:
+            mm.mm_apply_host(c1.array, 1, x, y, prec)
+        assert e.value.status == mm.MM_ETIMEOUT
+    finally:
+        mm.mm_test_tc_stall(0)
+    mm.mm_apply_host(c1.array, 1, x, y, prec)
+    rel = np.linalg.norm(y.astype(np.complex128) - g["y"]) / np.linalg.norm(g["y"])
+    assert rel <= BAR[prec], rel

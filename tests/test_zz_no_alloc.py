@@ -14,8 +14,9 @@ from paper_1712_02443_gb300.arrays import loop_array  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-# same bars as the other GPU parity tests (FP32 sums of a few hundred terms; FP64 rounding)
-TOL = {mm.MM_C64: 2e-5, mm.MM_C128: 1e-11}
+# same bars as the other GPU parity tests (the complex64 product bar of 1e-5
+# relative L2; FP64 rounding for complex128)
+TOL = {mm.MM_C64: 1e-5, mm.MM_C128: 1e-11}
 DT = {mm.MM_C64: torch.complex64, mm.MM_C128: torch.complex128}
 
 
@@ -49,6 +50,36 @@ def test_noalloc_matches_apply_twice(arr, prec):
         assert rel <= TOL[prec], rel
         # and both agree with the oracle's expected values
         assert np.linalg.norm(got - g["y"]) / np.linalg.norm(g["y"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
+def test_noalloc_16x16_fits_the_scratch(prec):
+    """The 16x16 loop array (73,728 unknowns, one right-hand side) fits the
+    16 MiB scratch at either precision: two calls in a row match mm_apply."""
+    from paper_1712_02443_gb300.build import build
+    build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = mm.mm_ctx_create(0)
+    la = loop_array(ctx, 16, 16)
+    try:
+        rng = np.random.default_rng(20171206)
+        xh = rng.standard_normal(la.n) + 1j * rng.standard_normal(la.n)
+        st = torch.cuda.current_stream()
+        x = torch.from_numpy(xh).to(DT[prec]).cuda()
+        y_ref = torch.empty_like(x)
+        mm.mm_apply(la.array, 1, x, y_ref, prec, st)
+        ref = y_ref.cpu().numpy().astype(np.complex128)
+        for _ in range(2):
+            y = torch.full_like(x, float("nan"))
+            mm.mm_apply_noalloc(la.array, 1, x, y, prec, st)
+            torch.cuda.synchronize()
+            got = y.cpu().numpy().astype(np.complex128)
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel <= TOL[prec], rel
+    finally:
+        la.close()
+        mm.mm_ctx_destroy(ctx)
 
 
 def test_noalloc_rejects_oversized_requests(arr):
