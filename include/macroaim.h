@@ -197,7 +197,9 @@ void mm_array_destroy(mm_array* array);
  * `stream`.  An array serves one caller at a time.  Tuning overrides read when
  * the array is created: MACROAIM_NEAR_OVERLAP=0 keeps the near field on
  * `stream` in order; MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block
- * near-field kernel's shape (0-4) instead of timing them on the first product;
+ * near-field kernel's shape instead of timing them on the first product
+ * (0-4 CUDA-core tiles, k split 1-16; 5-6 tensor-core tiles, complex64 only,
+ * TF32 with a three-product split, no k split);
  * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                    void* stream);

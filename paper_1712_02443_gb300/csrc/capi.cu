@@ -18,6 +18,7 @@
 #include "macroaim.h"
 #include "post.h"
 #include "solver.h"
+#include "near_tc.h"
 #include "tc_gemm.h"
 
 #include <cuda_bf16.h>
@@ -64,6 +65,7 @@ struct mm_array {
   // host: per type, the near-field block ordering of its bases (sorted position ->
   // basis) and its inverse
   std::vector<std::vector<int32_t>> nf_perm, nf_iperm;
+  std::vector<int32_t> nfb_arow_h;   // per block: first row in the tensor-core block layout
   ~mm_array();
 };
 
@@ -177,6 +179,39 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
       o += b.Na * b.Nb;
     }
     p.nfb_val = dev_upload(d.data(), d.size(), da.bytes);
+    if (sizeof(R) == 4 && da.nfb_tc_rows > 0 && !a->nfb_arow_h.empty()) {
+      // the same blocks for the tensor-core near field: complex rows of
+      // interleaved FP32 (row pitch nfb_tc_pitch), TF32 hi parts in rows
+      // [0, rows), lo parts in rows [rows, 2 rows)
+      const int64_t rows = da.nfb_tc_rows, pitch = da.nfb_tc_pitch;
+      std::vector<float> A((size_t)(2 * rows * pitch), 0.0f);
+      int64_t q = 0;
+      for (const auto& b : ah.nf_blocks) {
+        if (!b.ptr.empty()) {
+          const auto &ia = a->nf_iperm[b.ta], &ib = a->nf_iperm[b.tb];
+          for (int64_t m = 0; m < b.Na; ++m)
+            for (int64_t e = b.ptr[m]; e < b.ptr[m + 1]; ++e) {
+              const int64_t row = a->nfb_arow_h[q] + ia[m], kc = ib[b.col[e]];
+              float hi[2], lo[2];
+              mm::near_tc_split(b.val[e].real(), b.val[e].imag(), hi, lo);
+              float* dh = A.data() + (size_t)(row * pitch + 2 * kc);
+              float* dl = A.data() + (size_t)((rows + row) * pitch + 2 * kc);
+              dh[0] = hi[0];
+              dh[1] = hi[1];
+              dl[0] = lo[0];
+              dl[1] = lo[1];
+            }
+        }
+        ++q;
+      }
+      CU(mm::tc_gemm_init());
+      void* dA = dev_upload(A.data(), A.size(), da.bytes);
+      if (mm::tc_encode_2d(&p.nfb_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, dA, (uint64_t)pitch, (uint64_t)(2 * rows),
+                           (uint64_t)pitch * 4, 32, 128))
+        p.nfb_tc = dA;
+      else
+        cudaFree(dA);   // no tensor-map encoder: the CUDA-core block kernels apply the near field
+    }
   }
   {
     const int64_t Px = ah.fft[0], Py = ah.fft[1], Pz = ah.fft[2];
@@ -313,11 +348,20 @@ void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
 // A bounded wait of the tensor-core GEMM expired (checked where the call synchronises).
 mm_status check_tc(mm_array* a) {
   int h = 0;
-  if (!a->da.wf.err) return MM_OK;
-  if (cudaMemcpy(&h, a->da.wf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
-  if (h) {
-    cudaMemset(a->da.wf.err, 0, sizeof(int));
-    return fail(a->ctx, MM_ETIMEOUT, "a tensor-core GEMM wait expired; results of that product are invalid");
+  if (a->da.wf.err) {
+    if (cudaMemcpy(&h, a->da.wf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
+    if (h) {
+      cudaMemset(a->da.wf.err, 0, sizeof(int));
+      return fail(a->ctx, MM_ETIMEOUT, "a tensor-core GEMM wait expired; results of that product are invalid");
+    }
+  }
+  if (a->da.near_err) {
+    if (cudaMemcpy(&h, a->da.near_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
+    if (h) {
+      cudaMemset(a->da.near_err, 0, sizeof(int));
+      return fail(a->ctx, MM_ETIMEOUT,
+                  "a tensor-core near-field wait expired; results of that product are invalid");
+    }
   }
   return MM_OK;
 }
@@ -326,7 +370,7 @@ template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
-  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -342,10 +386,15 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
     CU(cudaMalloc(&w.us, sizeof(double) * (size_t)da.N * nrhs));
     w.bytes += sizeof(double) * (size_t)da.N * nrhs;
   }
+  if (sizeof(R) == 4 && da.pf.nfb_tc && da.nfg_prows > 0) {
+    CU(cudaMalloc(&w.np, sizeof(float2) * (size_t)da.nfg_prows * nrhs));
+    w.bytes += sizeof(float2) * (size_t)da.nfg_prows * nrhs;
+  }
   w.nrhs = nrhs;
 }
 
 void free_prec_f(mm::DevPrec<float>& p) {
+  if (p.nfb_tc) cudaFree(p.nfb_tc);
   for (auto& v : p.Atc)
     for (void* q : v) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
@@ -377,7 +426,7 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us, w->np})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
@@ -390,12 +439,14 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : d_JE) cudaFree(q);
   for (void* q : d_T) cudaFree(q);
-  for (void* q : {(void*)da.nfb_tptr32, (void*)da.nfb_tlist32})
+  for (void* q : {(void*)da.nfb_tptr32, (void*)da.nfb_tlist32, (void*)da.nfb_tptr128, (void*)da.nfb_tlist128,
+                  (void*)da.nfb_arow})
     if (q) cudaFree(q);
   for (void* q : {(void*)da.nfb_na, (void*)da.nfb_nb, (void*)da.nfb_off, (void*)da.nfb_tptr, (void*)da.nfb_tlist,
                   (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
-  for (void* q : {da.nfg_dev, (void*)da.nfg_poff})
+  for (void* q : {da.nfg_dev, (void*)da.nfg_poff, (void*)da.nfg_prow, (void*)da.nfe_ptr, (void*)da.nfe_pair,
+                  (void*)da.nfb_tperm})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
   if (da.chain) cudaStreamDestroy(da.chain);
@@ -730,10 +781,20 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         }
         tptr[nbk * nmt] = (int32_t)tl.size();
       };
-      int nmt = 0, nmt32 = 0;
-      std::vector<int32_t> tptr, tl, tptr32, tl32;
+      int nmt = 0, nmt32 = 0, nmt128 = 0;
+      std::vector<int32_t> tptr, tl, tptr32, tl32, tptr128, tl128;
       tile_lists(64, nmt, tptr, tl);
       tile_lists(32, nmt32, tptr32, tl32);
+      tile_lists(128, nmt128, tptr128, tl128);
+      // rows of the tensor-core block layout: the non-empty blocks one after another
+      a->nfb_arow_h.assign(nbk, 0);
+      int64_t trows = 0, tpitch = 0;
+      for (int64_t q = 0; q < nbk; ++q) {
+        a->nfb_arow_h[q] = (int32_t)trows;
+        if (nb[q].ptr.empty()) continue;
+        trows += nb[q].Na;
+        tpitch = std::max<int64_t>(tpitch, (2 * nb[q].Nb + 31) / 32 * 32);
+      }
       da.nfb_entries = o;
       if (o > 0) {
         da.nfb_nmt = nmt;
@@ -745,6 +806,14 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         da.nfb_nmt32 = nmt32;
         da.nfb_tptr32 = dev_upload(tptr32.data(), tptr32.size(), acc);
         da.nfb_tlist32 = dev_upload(tl32.data(), tl32.size(), acc);
+        if (2 * trows <= 0x7fffffffLL && tpitch * 4 < ((int64_t)1 << 40)) {
+          da.nfb_nmt128 = nmt128;
+          da.nfb_tptr128 = dev_upload(tptr128.data(), tptr128.size(), acc);
+          da.nfb_tlist128 = dev_upload(tl128.data(), tl128.size(), acc);
+          da.nfb_arow = dev_upload(a->nfb_arow_h.data(), a->nfb_arow_h.size(), acc);
+          da.nfb_tc_rows = (int)trows;
+          da.nfb_tc_pitch = (int)tpitch;
+        }
         std::vector<int32_t> bpa(nbk, 0), bpb(nbk, 0);
         for (int64_t q = 0; q < nbk; ++q) {
           bpa[q] = perm_off[nb[q].ta];
@@ -775,6 +844,28 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
           poff[i].y = ah.off[allp[i].y];
         }
         da.nfg_poff = dev_upload(poff.data(), poff.size(), acc);
+        {
+          // partial sums of the tensor-core near field: one slice of the row
+          // type's N^ rows per pair, and per element the pairs it is the row of
+          std::vector<int64_t> prow(allp.size());
+          std::vector<int32_t> eptr(n_elem + 1, 0), epair(allp.size());
+          int64_t rows = 0;
+          for (const auto& ng : da.nfg)
+            for (int64_t k = 0; k < ng.npairs; ++k) {
+              prow[ng.first_pair + k] = rows;
+              rows += ng.Na;
+            }
+          for (const auto& pr : allp) ++eptr[pr.x + 1];
+          for (int64_t e = 0; e < n_elem; ++e) eptr[e + 1] += eptr[e];
+          std::vector<int32_t> fillp(eptr.begin(), eptr.end() - 1);
+          for (size_t k = 0; k < allp.size(); ++k) epair[fillp[allp[k].x]++] = (int32_t)k;
+          std::vector<int32_t> tperm(perm_off.begin(), perm_off.end());
+          da.nfg_prows = rows;
+          da.nfg_prow = dev_upload(prow.data(), prow.size(), acc);
+          da.nfe_ptr = dev_upload(eptr.data(), eptr.size(), acc);
+          da.nfe_pair = dev_upload(epair.data(), epair.size(), acc);
+          da.nfb_tperm = dev_upload(tperm.data(), tperm.size(), acc);
+        }
         da.nfg_dev = dev_upload(reinterpret_cast<const unsigned char*>(da.nfg.data()),
                                 sizeof(mm::DevArray::NfGroup) * da.nfg.size(), acc);
         // tuning override: MACROAIM_NEAR=csr (CSR rows, when assembled)
@@ -783,7 +874,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         // tuning override: MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block kernel's shape
         if (const char* ns = std::getenv("MACROAIM_NEAR_SHAPE")) {
           int sh = -1, ks = 1;
-          if (std::sscanf(ns, "%d,%d", &sh, &ks) >= 1 && sh >= 0 && sh < 5 && ks >= 1 && ks <= 16) {
+          if (std::sscanf(ns, "%d,%d", &sh, &ks) >= 1 && sh >= 0 && sh < mm::kNearShapes && ks >= 1 && ks <= 16) {
             da.near_force_shape = sh;
             da.near_force_ks = ks;
           }
@@ -840,7 +931,9 @@ mm_status mm_array_footprint(const mm_array* a, int32_t nrhs, int32_t precision,
   size_t g = cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2];
   size_t s = cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2];
   size_t kry = 16 * (size_t)da.N * nrhs * (restart + 4) + 16 * (size_t)da.N * nrhs;
-  *bytes = 2 * vec + g + s + kry;
+  // partial sums of the tensor-core near field (complex64 products)
+  size_t np = da.pf.nfb_tc ? sizeof(float) * 2 * (size_t)da.nfg_prows * nrhs : 0;
+  *bytes = 2 * vec + g + s + kry + np;
   return MM_OK;
 }
 
@@ -1307,7 +1400,11 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   const size_t vec = align256(cs * (size_t)da.N * nrhs);
   const size_t grid = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2]);
   const size_t spec = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2]);
-  const size_t need = 2 * vec + grid + spec;
+  // complex64 with tensor-core near-field blocks: their partial sums too
+  const size_t npart = precision == MM_C64 && da.pf.nfb_tc && da.nfg_prows > 0
+                           ? align256(sizeof(float2) * (size_t)da.nfg_prows * nrhs)
+                           : 0;
+  const size_t need = 2 * vec + grid + spec + npart;
   if (need > kNoAllocScratchBytes)
     return fail(ctx, MM_EINVAL,
                 "mm_apply_noalloc needs " + std::to_string(need) + " bytes of scratch; the static maximum is " +
@@ -1333,6 +1430,7 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   w.v = base + vec;
   w.grid = base + 2 * vec;
   w.spec = base + 2 * vec + grid;
+  w.np = npart ? base + 2 * vec + grid + spec : nullptr;
   w.bytes = need;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // no stage events (they are created on demand) and no timing of near-field

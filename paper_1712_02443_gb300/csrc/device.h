@@ -123,6 +123,7 @@ struct Work {
   int* err = nullptr;     // device error flag of bounded waits
   void* pt = nullptr;     // N x nrhs   preconditioned vector (block-Jacobi)
   double* us = nullptr;   // N x nrhs   FP64 only: Re u + Im u for the three-product near field
+  void* np = nullptr;     // complex64 only: partial sums of the tensor-core near field (nfg_prows x nrhs)
   size_t bytes = 0;
 };
 
@@ -171,6 +172,11 @@ struct DevArray {
   int nfb_tc_rows = 0;                  // rows of all blocks (tensor-core layout)
   int nfb_tc_pitch = 0;                 // floats per row (2 Nb of the widest block, rounded up to 32)
   int* near_err = nullptr;              // device flag of the tensor-core near field's bounded waits
+  int64_t* nfg_prow = nullptr;          // per pair: first row of its slice in the partial-sum buffer
+  int64_t nfg_prows = 0;                // rows of the partial-sum buffer (sum over pairs of the row type's N^)
+  int32_t* nfe_ptr = nullptr;           // per element: its pairs as row element (n_elem + 1) ...
+  int32_t* nfe_pair = nullptr;          // ... and the pair indices
+  int32_t* nfb_tperm = nullptr;         // per type: offset of its anchor ordering in nfb_perm
   int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
   int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm
   int32_t* nfb_pb = nullptr;            // per block: offset of its column type's ordering
@@ -204,6 +210,9 @@ struct DevArray {
   std::vector<double> hval, hGhat;      // complex128 interleaved
 };
 
+// Shapes of the block near field: 0-4 CUDA-core tiles (k_near_blocks), 5-6
+// tensor-core tiles (near_tc.cu, complex64).
+constexpr int kNearShapes = 7;
 // Flags of matvec: kMvNoTune never times near-field kernel shapes (an untuned
 // right-hand-side count takes the size rule and is not remembered);
 // kMvNoProfile records no stage events (the array's profiler is left alone).

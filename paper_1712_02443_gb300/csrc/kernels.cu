@@ -30,6 +30,7 @@
 #include <cstdio>
 
 #include "device.h"
+#include "near_tc.h"
 #include "tc_gemm.h"
 
 namespace mm {
@@ -1322,10 +1323,28 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
 // (four CTAs per SM).  32-row tiles skip more zero k tiles of the sparse blocks
 // (about 1.9 times the non-zero work instead of 2.3 at 16x16).  The CTA counts
 // per SM apply to complex64; the FP64 forms keep their registers.
-constexpr int kNearShapes = 5;
+// Shapes 5 and 6 are the tensor-core form (near_tc.cu: 32 or 64 complex
+// columns per tile), complex64 only.
+template <typename R>
+static bool near_shape_ok(int shape, const DevPrec<R>& p, const void* np) {
+  return shape < 5 || (sizeof(R) == 4 && p.nfb_tc != nullptr && np != nullptr);
+}
+
 template <typename R>
 static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
-                              const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks) {
+                              const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks,
+                              void* np) {
+  if (shape >= 5) {
+    if constexpr (sizeof(R) == 4) {
+      if (p.nfb_tc != nullptr && np != nullptr) {
+        near_tc_launch(shape - 5, a, p, nrhs, u, y, static_cast<float2*>(np), st);
+        nl += 2;
+        return;
+      }
+    }
+    shape = 0;
+    ks = 1;
+  }
   if (shape == 4)
     near_blocks_launch<R, 64, 4, 32>(a, p, nrhs, u, y, st, nl, ks);
   else if (shape == 3)
@@ -1347,10 +1366,11 @@ static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p,
 template <typename R>
 static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p, int nrhs,
                                          const typename V2<R>::T* u, typename V2<R>::T* scratch,
-                                         size_t scratch_elems, cudaStream_t st) {
+                                         size_t scratch_elems, cudaStream_t st, void* np) {
   int64_t cols = 0;
   for (const auto& g : a.nfg) cols += g.npairs * nrhs;
   std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 2 : 0, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
+  if (near_shape_ok<R>(5, p, np)) best = {cols >= (int64_t)64 * 4 * 152 ? 6 : 5, 1};
   if (scratch == nullptr || scratch_elems < (size_t)a.N * nrhs) return best;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
@@ -1361,8 +1381,9 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
   float best_ms = 1e30f;
   for (int tn = 0; tn < kNearShapes; ++tn)
     for (int ks : {1, 2, 4}) {
+      if (!near_shape_ok<R>(tn, p, np) || (tn >= 5 && ks > 1)) continue;   // tensor-core shapes: no k split
       int nl = 0;
-      auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks); };
+      auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, np); };
       run();
       cudaEventRecord(e0, st);
       run();
@@ -1413,8 +1434,7 @@ cudaError_t kernels_init(DevArray& a) {
 #undef MM_ATTR
   e = tc_gemm_init();
   if (e != cudaSuccess) return e;
-  (void)a;
-  return cudaSuccess;
+  return near_tc_init(a);
 }
 
 template <typename R>
@@ -1501,12 +1521,12 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
       ks = it->second.second;
     } else if (flags & kMvNoTune) {
       // size rule, not remembered: a later tuned product may still time the shapes
-      const auto rule = near_autotune<R>(a, p, nrhs, u, nullptr, 0, st);
+      const auto rule = near_autotune<R>(a, p, nrhs, u, nullptr, 0, st, w.np);
       tn = rule.first;
       ks = rule.second;
     } else {
       it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
-                                                      (size_t)4 * nrhs * Nx * Py * Pz, st)).first;
+                                                      (size_t)4 * nrhs * Nx * Py * Pz, st, w.np)).first;
       tn = it->second.first;
       ks = it->second.second;
     }
@@ -1553,7 +1573,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   if (nf_blocks) {
     pr.begin(sb + 6, ns);
     nl = 0;
-    near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks);
+    near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks, w.np);
     pr.end(ns, nl);
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, ns);

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&tempty_bar[b]), 8);   // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");

@@ -437,7 +437,7 @@ def test_near_field_stream_matches_in_order(ctx, monkeypatch, prec):
         assert rel <= (1e-6 if prec == mm.MM_C64 else 1e-13), rel
 
 
-@pytest.mark.parametrize("shape,ks", [(0, 1), (1, 2), (2, 4), (1, 3), (3, 1), (3, 4), (4, 2)])
+@pytest.mark.parametrize("shape,ks", [(0, 1), (1, 2), (2, 4), (1, 3), (3, 1), (3, 4), (4, 2), (5, 1), (6, 2)])
 @pytest.mark.parametrize("nrhs", [1, 5])
 def test_block_near_field_every_kernel_shape(ctx, c3, monkeypatch, shape, ks, nrhs):
     """Every shape of the block near-field kernel (64-row tiles of 32 columns, the
