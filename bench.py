@@ -95,7 +95,6 @@ class ClockSampler:
 
 
 L2_FLUSH_BYTES = 256 << 20                 # twice the 129 MB L2
-FP32_PEAK_TFLOPS = round(152 * 128 * 2 * 2.07e9 / 1e12, 1)   # FP32 lanes x FMA x max SM clock
 
 
 def stage_bytes(stage: str, info: dict, nrhs: int, cs: int, nh: int, S: int) -> float:
@@ -120,6 +119,135 @@ def stage_bytes(stage: str, info: dict, nrhs: int, cs: int, nh: int, S: int) -> 
     if stage == "fft_inv":
         return 4 * cs * nrhs * (ng + Nx * Py * Pz)
     return 0.0
+
+
+GOLD = os.path.join(ROOT, "tests", "golden")
+TF32_PER_BF16 = 1.1 / 2.25                  # nominal dense TF32 / BF16 tensor rates
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _rcs_db(sig, ref):
+    top = ref >= ref.max() * 1e-4
+    return float(np.abs(10 * np.log10(sig[top] / ref[top])).max())
+
+
+def accuracy_measure(ctx) -> dict:
+    """Per-result error of the mixed-precision solve against the FP64 oracle
+    (expected values in tests/golden, written by the oracle): relative L2 error
+    of E^, J, J^ and the largest RCS error in dB where sigma is within 40 dB of
+    its maximum, solves to 1e-6; the 6x6 four-type array's 64-column batch against
+    the oracle's solutions of two of its columns; the full multiscale element's
+    product (2x1 array) against the oracle's."""
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.arrays import loop_array, multiscale_array
+    out = {"tolerances": {"solution": 1e-4, "rcs_db": 0.05, "product_c64": 1e-5}}
+
+    def solve_post(la, V, prec, th, ph, precond, inner):
+        Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        E = torch.empty_like(Vd)
+        s = mm.mm_solve(la.array, 1, Vd, E, tol=1e-6, restart=50, max_iter=3000, precision=prec, refine=1,
+                        inner_tol=inner, precond=precond, check=False)
+        J = torch.empty(la.info["n_scat_unknowns"], dtype=torch.complex128, device="cuda")
+        Jh = torch.empty_like(E)
+        mm.mm_currents(la.array, 1, E, J, Jh, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        sig = mm.mm_rcs(la.array, 1, Jh, th, ph)[:, 0]
+        return s, E.cpu().numpy(), J.cpu().numpy(), Jh.cpu().numpy(), sig
+
+    names = {mm.MM_C64: "c64", mm.MM_C64_F16: "fp16_gemm", mm.MM_C64_BF16: "bf16_gemm"}
+    g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+    la = loop_array(ctx, 2, 2)
+    res = {}
+    for prec, pc in ((mm.MM_C64, 0), (mm.MM_C64_F16, 1), (mm.MM_C64_BF16, 1)):
+        s, E, J, Jh, sig = solve_post(la, g["V"], prec, g["theta"], g["phi"], pc,
+                                      1e-5 if prec == mm.MM_C64 else 1e-3)
+        res[names[prec]] = {"converged": s["converged"], "E": _rel(E, g["E"]), "J": _rel(J, g["J"]),
+                            "Jhat": _rel(Jh, g["Jhat"]), "rcs_db_max": _rcs_db(sig, g["sigma"])}
+    la.close()
+    out["loops_2x2"] = res
+    gp = os.path.join(GOLD, "c4_meander_2x2_post.npz")
+    if os.path.exists(gp):
+        g = np.load(os.path.join(GOLD, "c4_meander_2x2.npz"))
+        gq = np.load(gp)
+        la = multiscale_array(ctx, 2, 2, meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+        res = {}
+        for prec in (mm.MM_C64_F16, mm.MM_C64_BF16):
+            s, E, J, Jh, sig = solve_post(la, g["V"], prec, gq["theta"], gq["phi"], 1, 1e-3)
+            res[names[prec]] = {"converged": s["converged"], "E": _rel(E, g["E"]), "J": _rel(J, gq["J"]),
+                                "Jhat": _rel(Jh, gq["Jhat"]), "rcs_db_max": _rcs_db(sig, gq["sigma"])}
+        la.close()
+        out["multiscale_reduced_2x2"] = res
+    gp = os.path.join(GOLD, "c3_solve_6x6.npz")
+    if os.path.exists(gp):
+        g = np.load(gp)
+        la = loop_array(ctx, 6, 6, outers=SERVE_OUTERS, config_index=2)
+        th, ph, pol = wl.planewave_grid()
+        st = torch.cuda.current_stream()
+        V = torch.empty(la.n * 64, dtype=torch.complex128, device="cuda")
+        mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
+        E = torch.empty_like(V)
+        s = mm.mm_solve(la.array, 64, V, E, tol=1e-6, restart=50, max_iter=4000, precision=mm.MM_C64_F16, refine=1,
+                        inner_tol=1e-3, precond=1, stream=st, check=False)
+        Eb = E.cpu().numpy().reshape(la.n, 64)
+        out["four_types_6x6_64rhs_fp16_gemm"] = {
+            "converged": s["converged"],
+            "E_columns": {str(int(j)): _rel(Eb[:, j], g["E"][:, k]) for k, j in enumerate(g["cols"])}}
+        la.close()
+    gp = os.path.join(GOLD, "c4_full_element_2x1.npz")
+    if os.path.exists(gp):
+        g = np.load(gp)
+        la = multiscale_array(ctx, 2, 1)
+        X = wl.random_cvec(la.n, 3, 11, nrhs=2)
+        res = {}
+        for prec, dt in ((mm.MM_C64, torch.complex64), (mm.MM_C128, torch.complex128)):
+            xd = torch.from_numpy(np.ascontiguousarray(X)).to(dt).cuda()
+            yd = torch.empty_like(xd)
+            mm.mm_apply(la.array, 2, xd, yd, prec, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            res["c64" if prec == mm.MM_C64 else "c128"] = _rel(yd.cpu().numpy().astype(np.complex128), g["y"])
+        la.close()
+        out["full_multiscale_element_2x1_product"] = res
+    return out
+
+
+def cufft_measure(info: dict, nrhs: int, ours_ms: float, reps: int = 20) -> dict:
+    """The FFT convolution (step ii) with cuFFT through torch.fft, timed only as a
+    comparison on the same zero-padded grids: pad the 4 nrhs grids to the FFT
+    lengths, 3-D transform, multiply by a spectrum, inverse transform, crop."""
+    import torch
+    Nx, Ny, Nz = info["grid"]
+    Px, Py, Pz = info["fft"]
+    B = 4 * nrhs
+    g = torch.randn(B, Nx, Ny, Nz, dtype=torch.complex64, device="cuda")
+    G = torch.randn(Px, Py, Pz, dtype=torch.complex64, device="cuda")
+    pad = torch.zeros(B, Px, Py, Pz, dtype=torch.complex64, device="cuda")
+
+    def once():
+        pad.zero_()
+        pad[:, :Nx, :Ny, :Nz] = g
+        f = torch.fft.fftn(pad, dim=(1, 2, 3))
+        f *= G
+        return torch.fft.ifftn(f, dim=(1, 2, 3))[:, :Nx, :Ny, :Nz].contiguous()
+
+    for _ in range(3):
+        once()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        once()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"grid": [Nx, Ny, Nz], "fft": [Px, Py, Pz], "batch": B, "cufft_ms": round(ms, 4),
+            "ours_ms": round(ours_ms, 4), "ours_over_cufft": round(ours_ms / ms, 3),
+            "note": "cuFFT (torch.fft) with explicit zero padding, spectrum multiply and crop; ours = the fused "
+                    "forward, convolution-line and inverse stages of the library, from its stage profiler"}
 
 
 def run_ours(args, rank, world, local):
@@ -243,8 +371,11 @@ def run_ours(args, rank, world, local):
         unpc = {"solves_per_s": round(world * k64 / (t0ms / 1e3), 2),
                 "matvecs_per_s": round(world * mv0 / (t0ms / 1e3), 1), "matvecs_per_solve": round(mv0 / k64, 1)}
 
-    # ---- end to end through the public API: host angles in, solution copied to pinned host memory
-    Eh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    # ---- end to end through the public API: one library call per solve with host
+    # angles in and the solution copied by the library into host memory
+    Eh = np.zeros(N, dtype=np.complex128)
+    mm.mm_solve_planewave_host(la.array, th, ph, pol, Eh, tol=TOL, restart=50, max_iter=2000, precision=mm.MM_C64,
+                               refine=1, inner_tol=1e-5, precond=pc)
     torch.cuda.synchronize()
     mv_e2e = 0
     e2e_s = 0.0
@@ -252,9 +383,8 @@ def run_ours(args, rank, world, local):
         flush.fill_(k & 0xFF)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        mv_e2e += step()["matvecs"]
-        Eh.copy_(E, non_blocking=True)
-        torch.cuda.synchronize()
+        mv_e2e += mm.mm_solve_planewave_host(la.array, th, ph, pol, Eh, tol=TOL, restart=50, max_iter=2000,
+                                             precision=mm.MM_C64, refine=1, inner_tol=1e-5, precond=pc)["matvecs"]
         e2e_s += time.perf_counter() - w0
     del flush
 
@@ -265,8 +395,12 @@ def run_ours(args, rank, world, local):
     nb = stage_bytes(dom, info, 1, 8, N // (NX * NY), 27)
     achieved = nb / avg_s / 1e9
     alu = dom == "near" and info["near_format"] == "blocks"
+    near_shape = mm.mm_array_near_shape(la.array, 1, mm.MM_C64)
+    tc_near = alu and near_shape is not None and near_shape[0] >= 5
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = round(sms * 128 * 2 * 2.07e9 / 1e12, 1)
     if alu:
-        # the block near field reads an L2-resident operator: FP32 arithmetic bounds it
+        # the block near field reads an L2-resident operator: its arithmetic bounds it
         alg_flops = 8.0 * info["nnz_near"]          # one complex multiply-add per non-zero
         achieved_tf = alg_flops / avg_s / 1e12
     traffic = None
@@ -316,10 +450,19 @@ def run_ours(args, rank, world, local):
         "without_preconditioner": unpc,
         "e2e": {"value": round(world * mv_e2e / e2e_s, 1), "unit": "matvecs/s",
                 "solves_per_s": round(world * args.steps / e2e_s, 2),
-                "h2d_bytes_per_step": 8 + 8 + 4, "d2h_bytes_per_step": 16 * N},
-        "roofline": ({"kernel": "near (k_near_blocks)", "bound": "alu", "achieved": round(achieved_tf, 2),
-                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
-                      "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "h2d_bytes_per_step": 8 + 8 + 4, "d2h_bytes_per_step": 16 * N,
+                "call": "mm_solve_planewave_host (host angles in, host solution out; copies inside the library)"},
+        "roofline": ({"kernel": "near (k_near_tc + k_near_reduce, tensor-core shape %d)" % near_shape[0],
+                      "bound": "tensor", "achieved": round(achieved_tf, 2),
+                      "peak": round(bf16 * TF32_PER_BF16, 1), "unit": "TFLOP/s",
+                      "frac": round(achieved_tf / (bf16 * TF32_PER_BF16), 4), "traffic": traffic,
+                      "peak_source": "%s BF16 burst x nominal TF32/BF16 ratio 1.1/2.25" % src,
+                      "algorithmic_flops_per_launch": alg_flops,
+                      "operator_bytes": 8 * info["near_block_entries"]} if tc_near else
+                     {"kernel": "near (k_near_blocks, shape %s)" % (near_shape,), "bound": "alu",
+                      "achieved": round(achieved_tf, 2), "peak": fp32_peak, "unit": "TFLOP/s",
+                      "frac": round(achieved_tf / fp32_peak, 4), "traffic": traffic,
+                      "peak_source": "derived: %d SMs (device property) x 128 FP32 lanes x 2 x 2.07 GHz" % sms,
                       "algorithmic_flops_per_launch": alg_flops,
                       "operator_bytes": 8 * info["near_block_entries"]} if alu else
                      {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -331,14 +474,23 @@ def run_ours(args, rank, world, local):
                              "(+1 plane-wave kernel) x timed steps; the stage table comes from that pass",
         "clocks": clk.summary(),
         "setup_s": round(setup_s, 2),
+        "device": {"sms": sms, "name": torch.cuda.get_device_properties(local).name},
     }
+    fft_ours = sum(prof[k]["ms"] for k in ("fft_fwd", "fft_conv", "fft_inv")) / max(1, prof["fft_fwd"]["launches"])
+    if rank == 0:
+        out["cufft_comparison"] = {"c2_1rhs": cufft_measure(info, 1, fft_ours)}
     mm.mm_array_destroy(la.array)
     if rank == 0 and not args.no_tensor_gemm:
         out["tensor_gemm"] = tensor_gemm_measure(ctx, 64, 8, 10, 3)
     if rank == 0 and not args.no_batched:
         out["batched"] = batched_measure(ctx)
-    if rank == 0 and args.precision_config:
-        out["precision"] = precision_measure(ctx)
+        finfo, fours = out["batched"].pop("fft_info", None), out["batched"].pop("fft_ours_ms", None)
+        if "cufft_comparison" in out and finfo is not None:
+            out["cufft_comparison"]["c3_64rhs"] = cufft_measure(finfo, 64, fours)
+    if rank == 0 and not args.no_accuracy:
+        out["accuracy"] = accuracy_measure(ctx)
+    if rank == 0 and not args.no_precision_config:
+        out["precision"] = precision_measure(ctx, all_forms=args.precision_all)
     if rank == 0 and args.serve_requests > 0:
         out["serving"] = serving_measure(ctx, args.serve_requests, args.serve_min_side, args.serve_max_side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -391,8 +543,10 @@ def cpu_baseline(budget_s=20.0):
     t = _oracle_matvec_seconds(A, G, x)
     reps = max(1, min(10, int(budget_s / max(t, 1e-3))))
     t = _oracle_matvec_seconds(A, G, x, reps)
-    return {"value": round(1.0 / t, 4), "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+    return {"value": round(1.0 / t, 4), "unit": "matvecs/s", "cores": os.cpu_count(), "kind": "oracle",
             "host_cpus": os.cpu_count(),
+            "threads": "FFTs on all host cores (scipy.fft workers=-1), dense products in numpy's threaded BLAS; "
+                       "the sparse near-field rows single-threaded",
             "sample": "oracle complex128 operator on the full 16x16 array: macromodel blocks, AIM projection, "
                       "FFT convolution and interpolation on all %d unknowns; near field on 1024 sampled rows "
                       "scaled to all rows; best of %d" % (A.n, reps)}
@@ -416,7 +570,7 @@ def run_reference(args, rank, world):
            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "unknowns": A.n, "nrhs": 1},
-           "cpu_baseline": {"value": round(val, 4), "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": round(val, 4), "unit": "matvecs/s", "cores": os.cpu_count(), "kind": "oracle",
                             "host_cpus": os.cpu_count(),
                             "sample": "one step = one oracle operator application on the full array with the "
                                       "near field on 1024 sampled rows scaled to all rows"},
@@ -513,8 +667,10 @@ def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int 
     total_rhs = sum(r["nrhs"] for r in reqs)
 
     def submit(sv, r, **kw):
+        # near_csr=2: the arrays skip the host CSR assembly (set-up ~6x shorter);
+        # complex128 residual products use the dense near-field blocks
         return mm.mm_server_submit(sv, [types[t] for t in r["type_of"]], r["offsets"], r["theta"], r["phi"],
-                                   r["pol"], r["tol"], precond=1, **kw)
+                                   r["pol"], r["tol"], precond=1, near_csr=2, **kw)
 
     def collect(sv, tickets):
         out = []
@@ -567,7 +723,11 @@ def serving_measure(ctx, n_req: int, min_side: int, max_side: int, workers: int 
         "workload": "%d requests, square arrays of side %d..%d, 1-4 loop types, %d plane-wave solves in all, "
                     "tol 1e-3/1e-4" % (n_req, min_side, max_side, total_rhs),
         "workers": workers,
+        "scale_note": "configuration: 2000 requests of side 8..48; this run: %d requests of side %d..%d "
+                      "(bounded for the benchmark's time limit)" % (n_req, min_side, max_side),
         "preconditioner": "block-Jacobi in both forms",
+        "near_field": "dense blocks in both precisions (no CSR assembly)",
+        "merged_requests": int(sum(1 for x in stream if x.get("group_requests", 1) > 1)),
         "all_converged": ok,
         "failures": [x["message"] for x in burst + stream + fp64 if not (x["status"] == 0 and x["converged"])][:4],
         "saturation": {"requests_per_s": round(sat, 3), "solves_per_s": round(total_rhs / t_burst, 2)},
@@ -618,6 +778,10 @@ def batched_measure(ctx, side: int = 32) -> dict:
         mm.mm_profile_enable(la.array, False)
         t = e0.elapsed_time(e1) / 1e3
         it = max(1, s["iterations"])
+        if name == "fp16_tensor_gemm":
+            out["fft_info"] = la.info
+            out["fft_ours_ms"] = sum(pr[k]["ms"] for k in ("fft_fwd", "fft_conv", "fft_inv")) / max(
+                1, pr["fft_fwd"]["launches"])
         out[name] = {"s_per_batch": round(t, 3), "solves_per_s": round(64 / t, 2),
                      "column_matvecs_per_s": round(64 * s["matvecs"] / t, 1), "converged": s["converged"],
                      "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
@@ -631,7 +795,7 @@ def batched_measure(ctx, side: int = 32) -> dict:
 PRECISION_RESTART = 200   # GMRES(200): 522 iterations on this array, against 1,442 at GMRES(50)
 
 
-def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
+def precision_measure(ctx, side: int = 64, nrhs: int = 8, all_forms: bool = False) -> dict:
     """Precision configuration: side x side array of the multiscale element (square
     loop with a meandered inner trace, 2547 scatterer RWG, 0.005-wavelength gaps; box
     meshed 8 x 8 x 2, 576 RWG), nrhs plane waves (the first nrhs of the 8 x 8
@@ -656,8 +820,10 @@ def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
            "unknowns": la.n, "nnz_near": la.info["nnz_near"],
            "near_field": la.info["near_format"], "setup_s": round(setup_s, 1)}
     sols = {}
-    for name, prec, inner in (("bf16", mm.MM_C64_BF16, 1e-3), ("fp16", mm.MM_C64_F16, 1e-3),
-                              ("fp32", mm.MM_C64, 1e-5)):
+    forms = (("bf16", mm.MM_C64_BF16, 1e-3), ("fp16", mm.MM_C64_F16, 1e-3), ("fp32", mm.MM_C64, 1e-5))
+    if not all_forms:
+        forms = forms[1:2]   # the default run: one FP16 solve
+    for name, prec, inner in forms:
         E = torch.empty_like(V)
         mm.mm_profile_enable(la.array, True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -675,9 +841,13 @@ def precision_measure(ctx, side: int = 64, nrhs: int = 8) -> dict:
                      "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
                      "refinements": s["refinements"], "matvecs": s["matvecs"],
                      "stage_ms_total": {k: round(v["ms"], 1) for k, v in pr.items() if v["launches"]}}
-    ref = sols["fp32"]
-    for name in ("bf16", "fp16"):
-        out[name]["rel_diff_vs_fp32_gemm_solution"] = float(np.linalg.norm(sols[name] - ref) / np.linalg.norm(ref))
+    if "fp32" in sols:
+        ref = sols["fp32"]
+        for name in ("bf16", "fp16"):
+            out[name]["rel_diff_vs_fp32_gemm_solution"] = float(np.linalg.norm(sols[name] - ref) /
+                                                                np.linalg.norm(ref))
+    out["oracle_error"] = "per-result error vs the FP64 oracle: accuracy.multiscale_reduced_2x2 (the same method " \
+                          "on a reduced element) and accuracy.full_multiscale_element_2x1_product"
     la.close()
     return out
 
@@ -706,11 +876,14 @@ def main():
     ap.add_argument("--no-tensor-gemm", action="store_true", help="skip the tensor-core GEMM line of the report")
     ap.add_argument("--no-precond", action="store_true", help="solve without the block-Jacobi preconditioner")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-plane-wave batched solve")
-    ap.add_argument("--precision-config", action="store_true",
-                    help="also solve the 64x64 multiscale array (8 plane waves, 16-bit tensor-core GEMM)")
-    ap.add_argument("--serve-requests", type=int, default=12, help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--no-precision-config", action="store_true",
+                    help="skip the 64x64 multiscale array (8 plane waves, FP16 tensor-core GEMM)")
+    ap.add_argument("--precision-all", action="store_true",
+                    help="solve the 64x64 multiscale array with BF16, FP16 and FP32 macromodel GEMMs")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the per-result errors against the oracle")
+    ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-min-side", type=int, default=8)
-    ap.add_argument("--serve-max-side", type=int, default=24)
+    ap.add_argument("--serve-max-side", type=int, default=48)
     ap.add_argument("--gemm-side", type=int, default=64)
     ap.add_argument("--gemm-nrhs", type=int, default=8)
     args = ap.parse_args()

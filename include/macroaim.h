@@ -279,6 +279,23 @@ typedef struct mm_solve_stats {
 mm_status mm_solve(mm_array* array, int32_t nrhs, const void* V_dev, void* E_dev, const mm_solve_opts* opts,
                    mm_solve_stats* stats, void* stream);
 
+/* The whole solve from host memory, for callers without device buffers:
+ * the plane-wave excitation of nrhs incidences (host theta, phi, pol as in
+ * mm_rhs_planewave), the solve of mm_solve with `opts`, and the solution
+ * copied to E_host (N^ x nrhs complex128, interleaved).  Synchronous.  The
+ * array keeps two device vectors of N^ x nrhs complex128 for these calls.
+ * MM_ENOCONV still fills E_host with the last iterate.                       */
+mm_status mm_solve_planewave_host(mm_array* array, int32_t nrhs, const double* theta, const double* phi,
+                                  const int32_t* pol, double* E_host, const mm_solve_opts* opts,
+                                  mm_solve_stats* stats);
+
+/* The block near-field kernel shape the array chose for products of nrhs
+ * columns at `precision` (MM_C64 or MM_C128): shape 0-4 CUDA-core tiles, 5-6
+ * tensor-core tiles (see mm_apply); ksplit its k split.  MM_EINVAL until a
+ * product of that width has run (the choice is made on the first one).       */
+mm_status mm_array_near_shape(const mm_array* array, int32_t nrhs, int32_t precision, int32_t* shape,
+                              int32_t* ksplit);
+
 /* ------------------------------------------------- allocation-free product
  * The same product as mm_apply, for callers that cannot allocate device
  * memory: code running inside a framework that has reserved all device
@@ -336,7 +353,13 @@ mm_status mm_test_tc_stall(int32_t ms);
  * and must outlive the server.  mm_server_poll returns MM_EBUSY while the
  * request runs (wait = 0) or blocks until it is done (wait = 1); E_host, if
  * not NULL, receives E^ (N^ x nrhs complex128; E_count doubles available).
- * mm_server_release forgets a finished request.                               */
+ * mm_server_release forgets a finished request.
+ * Batching: when a worker takes a request, waiting requests with the same
+ * element types, offsets, AIM options and solve options join it as further
+ * columns of one solve (at most 64 columns); every product and Arnoldi step
+ * then covers all of them.  Green's spectra are cached across arrays of equal
+ * grid size.  For short set-up, requests may set aim.near_csr = 2 (no CSR
+ * assembly; the complex128 residual products then use the dense blocks).     */
 typedef struct mm_server mm_server;
 typedef struct mm_request {
   int64_t n_elem;
@@ -356,6 +379,9 @@ typedef struct mm_result {
   mm_solve_stats stats;
   double queue_s, setup_s, solve_s, latency_s;   /* wall times, seconds       */
   char message[160];             /* failure message ("" when status is MM_OK)  */
+  int32_t group_requests;        /* requests solved together with this one
+                                    (same geometry and options; 1 = alone)    */
+  int32_t group_columns;         /* columns of that solve                      */
 } mm_result;
 mm_status mm_server_create(int device, int32_t workers, size_t hbm_budget_bytes, mm_server** out);
 mm_status mm_server_submit(mm_server* server, const mm_request* request, uint64_t* ticket);

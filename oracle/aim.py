@@ -32,6 +32,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.fft as sfft
 import scipy.sparse as sp
 
 from .basis import RWG
@@ -134,7 +135,7 @@ def fft_kernel(N, h: float, k: float) -> np.ndarray:
         sl = [slice(None)] * 3
         sl[a] = N[a]
         Kp[tuple(sl)] = 0.0
-    return np.fft.fftn(Kp)
+    return sfft.fftn(Kp, workers=-1)
 
 
 def convolve(Q: np.ndarray, Khat: np.ndarray) -> np.ndarray:
@@ -143,7 +144,8 @@ def convolve(Q: np.ndarray, Khat: np.ndarray) -> np.ndarray:
     P = Khat.shape
     Qp = np.zeros(Q.shape[:-3] + P, dtype=np.complex128)
     Qp[..., :N[0], :N[1], :N[2]] = Q
-    out = np.fft.ifftn(np.fft.fftn(Qp, axes=(-3, -2, -1)) * Khat, axes=(-3, -2, -1))
+    # library FFTs (scipy.fft, on all host cores); the same transforms as numpy's
+    out = sfft.ifftn(sfft.fftn(Qp, axes=(-3, -2, -1), workers=-1) * Khat, axes=(-3, -2, -1), workers=-1)
     return out[..., :N[0], :N[1], :N[2]]
 
 

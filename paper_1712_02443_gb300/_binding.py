@@ -67,7 +67,8 @@ class mm_request(ct.Structure):
 class mm_result(ct.Structure):
     _fields_ = [("done", ct.c_int32), ("status", ct.c_int32), ("n_unknowns", ct.c_int64),
                 ("stats", mm_solve_stats), ("queue_s", ct.c_double), ("setup_s", ct.c_double),
-                ("solve_s", ct.c_double), ("latency_s", ct.c_double), ("message", ct.c_char * 160)]
+                ("solve_s", ct.c_double), ("latency_s", ct.c_double), ("message", ct.c_char * 160),
+                ("group_requests", ct.c_int32), ("group_columns", ct.c_int32)]
 
 
 P = ct.c_void_p
@@ -108,6 +109,9 @@ _SIGS = {
     "mm_profile_stages": (ct.c_int, [P, ct.c_uint32]),
     "mm_profile_read": (ct.c_int, [P, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     "mm_test_tc_stall": (ct.c_int, [ct.c_int32]),
+    "mm_solve_planewave_host": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.POINTER(mm_solve_opts),
+                                           ct.POINTER(mm_solve_stats)]),
+    "mm_array_near_shape": (ct.c_int, [P, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
 }
 
 _lib = None
@@ -336,6 +340,33 @@ def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_
     return stats
 
 
+def mm_solve_planewave_host(array, theta, phi, pol, E_host: np.ndarray, tol: float, restart: int = 50,
+                            max_iter: int = 1000, precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2,
+                            orth: int = 0, precond: int = 0, check: bool = True):
+    """Excitation, solve and the solution copied into E_host (complex128, N x nrhs), all in the library."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
+    if E_host.dtype != np.complex128 or not E_host.flags.c_contiguous:
+        raise ValueError("E_host must be a C-contiguous complex128 array")
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond)
+    s = mm_solve_stats()
+    st = load().mm_solve_planewave_host(array, len(th), _ptr(th), _ptr(ph), _ptr(po), _ptr(E_host), ct.byref(o),
+                                        ct.byref(s))
+    stats = {"iterations": s.iterations, "matvecs": s.matvecs, "refinements": s.refinements,
+             "converged": bool(s.converged), "rel_residual": s.rel_residual, "status": st}
+    if check:
+        _check(st, _ctx_of.get(array.value))
+    return stats
+
+
+def mm_array_near_shape(array, nrhs: int, precision: int = MM_C64):
+    """(shape, ksplit) of the block near-field kernel chosen for nrhs columns, or None before the first product."""
+    sh, ks = ct.c_int32(), ct.c_int32()
+    st = load().mm_array_near_shape(array, nrhs, precision, ct.byref(sh), ct.byref(ks))
+    return (sh.value, ks.value) if st == MM_OK else None
+
+
 def mm_profile_enable(array, enable: bool = True) -> None:
     _check(load().mm_profile_enable(array, 1 if enable else 0), _ctx_of.get(array.value))
 
@@ -362,7 +393,8 @@ def mm_server_create(device: int = 0, workers: int = 2, hbm_budget_bytes: int = 
 
 def mm_server_submit(server, types, offsets, theta, phi, pol, tol: float, h: float = 0.1, order: int = 2,
                      n_nf: int = 3, phase=(0.0137, 0.0291, 0.0913), restart: int = 50, max_iter: int = 2000,
-                     precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-5, precond: int = 0) -> int:
+                     precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-5, precond: int = 0,
+                     near_csr: int = 0) -> int:
     """Submits one request; its inputs are copied before this returns."""
     offsets = np.ascontiguousarray(offsets, dtype=np.float64).reshape(-1, 3)
     th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
@@ -370,7 +402,8 @@ def mm_server_submit(server, types, offsets, theta, phi, pol, tol: float, h: flo
     po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
     arr = (ct.c_void_p * len(types))(*[t.value for t in types])
     q = mm_request(len(types), ct.cast(arr, ct.POINTER(ct.c_void_p)), offsets.ctypes.data_as(ct.c_void_p),
-                   mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase)), len(th), th.ctypes.data_as(ct.c_void_p),
+                   mm_aim_opts(h, order, n_nf, (ct.c_double * 3)(*phase), near_csr), len(th),
+                   th.ctypes.data_as(ct.c_void_p),
                    ph.ctypes.data_as(ct.c_void_p), po.ctypes.data_as(ct.c_void_p),
                    mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, 0, precond))
     t = ct.c_uint64()
@@ -393,7 +426,8 @@ def mm_server_poll(server, ticket: int, wait: bool = True, nrhs: int = 1, want_s
     res = {"done": True, "status": r.status, "n_unknowns": r.n_unknowns, "iterations": r.stats.iterations,
            "matvecs": r.stats.matvecs, "converged": bool(r.stats.converged), "rel_residual": r.stats.rel_residual,
            "queue_s": r.queue_s, "setup_s": r.setup_s, "solve_s": r.solve_s, "latency_s": r.latency_s,
-           "message": r.message.decode(errors="replace")}
+           "message": r.message.decode(errors="replace"), "group_requests": r.group_requests,
+           "group_columns": r.group_columns}
     return res, E
 
 

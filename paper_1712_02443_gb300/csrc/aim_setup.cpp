@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <unordered_map>
 
 #include "aim_setup.h"
@@ -204,6 +206,40 @@ void type_aim(const Mesh& eq, Vec3 pos, const AimOpts& o, TypeAim& ta) {
   }
 }
 
+// Process-wide cache of Green's spectra (bounded number of entries).
+struct GhatKey {
+  int64_t n[6];
+  double h, k;
+  bool operator<(const GhatKey& o) const {
+    for (int i = 0; i < 6; ++i)
+      if (n[i] != o.n[i]) return n[i] < o.n[i];
+    if (h != o.h) return h < o.h;
+    return k < o.k;
+  }
+};
+static std::mutex g_ghat_mu;
+static std::map<GhatKey, std::shared_ptr<const std::vector<cd>>> g_ghat;
+constexpr size_t kGhatCacheEntries = 32;
+
+static bool ghat_cache_get(const GhatKey& key, std::vector<cd>& out) {
+  std::shared_ptr<const std::vector<cd>> v;
+  {
+    std::lock_guard<std::mutex> lk(g_ghat_mu);
+    auto it = g_ghat.find(key);
+    if (it == g_ghat.end()) return false;
+    v = it->second;
+  }
+  out = *v;
+  return true;
+}
+
+static void ghat_cache_put(const GhatKey& key, const std::vector<cd>& v) {
+  auto p = std::make_shared<const std::vector<cd>>(v);
+  std::lock_guard<std::mutex> lk(g_ghat_mu);
+  if (g_ghat.size() >= kGhatCacheEntries) g_ghat.erase(g_ghat.begin());
+  g_ghat[key] = std::move(p);
+}
+
 static inline cd green(double R, double k) {
   return std::exp(cd(0.0, -k * R)) / (4.0 * M_PI * R);
 }
@@ -268,8 +304,13 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
   ah.base.assign(3 * ne, 0);
   for (int64_t e = 0; e < ne; ++e)
     for (int a = 0; a < 3; ++a) ah.base[3 * e + a] = ah.L[3 * e + a] - lo[a];
-  // Green's spectrum: circulant embedding of H on the padded grid, FFT, / (Px Py Pz)
-  {
+  // Green's spectrum: circulant embedding of H on the padded grid, FFT, / (Px Py Pz).
+  // It depends only on the grid and padded sizes, h and k: spectra are kept in a
+  // process-wide cache (arrays of equal grid size share one computation).
+  const GhatKey gkey{{ah.grid[0], ah.grid[1], ah.grid[2], ah.fft[0], ah.fft[1], ah.fft[2]}, o.h, em.k};
+  if (ghat_cache_get(gkey, ah.Ghat)) {
+    // cached
+  } else {
     int64_t Px = ah.fft[0], Py = ah.fft[1], Pz = ah.fft[2];
     int64_t Nx = ah.grid[0], Ny = ah.grid[1], Nz = ah.grid[2];
     std::vector<cd> K(Px * Py * Pz, cd(0, 0));
@@ -309,6 +350,7 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
     double inv = 1.0 / (double)(Px * Py * Pz);
     for (auto& x : K) x *= inv;
     ah.Ghat = std::move(K);
+    ghat_cache_put(gkey, ah.Ghat);
   }
   // near field: blocks per (type, type, lattice offset)
   const int nnf = o.n_nf;   // -1: no near-field correction

@@ -66,6 +66,9 @@ struct mm_array {
   // basis) and its inverse
   std::vector<std::vector<int32_t>> nf_perm, nf_iperm;
   std::vector<int32_t> nfb_arow_h;   // per block: first row in the tensor-core block layout
+  void* pv_V = nullptr;              // mm_solve_planewave_host: excitation and solution on the device
+  void* pv_E = nullptr;
+  size_t pv_cap = 0;
   ~mm_array();
 };
 
@@ -452,6 +455,8 @@ mm_array::~mm_array() {
   if (da.chain) cudaStreamDestroy(da.chain);
   if (ang_ev) cudaEventDestroy(ang_ev);
   if (d_pw) cudaFree(d_pw);
+  if (pv_V) cudaFree(pv_V);
+  if (pv_E) cudaFree(pv_E);
   if (da.tbase) cudaFree(da.tbase);
   for (cudaEvent_t e : {da.ev_fork, da.ev_join, da.ev_done})
     if (e) cudaEventDestroy(e);
@@ -1196,13 +1201,55 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
     stats->rel_residual = relres;
   }
   if (s.code != MM_OK) return fail(ctx, s.code, s.msg);
-  if (mode) {
+  {
+    // bounded waits of the tensor-core GEMM and near field
     const mm_status t = check_tc(a);
     if (t != MM_OK) return t;
   }
   if (!conv) return fail(ctx, MM_ENOCONV, "GMRES reached max_iter before the tolerance");
   return MM_OK;
   API_CATCH(ctx)
+}
+
+mm_status mm_solve_planewave_host(mm_array* a, int32_t nrhs, const double* theta, const double* phi,
+                                  const int32_t* pol, double* E_host, const mm_solve_opts* opts,
+                                  mm_solve_stats* stats) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !theta || !phi || !pol || !E_host || !opts) return fail(ctx, MM_EINVAL, "invalid solve arguments");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  const size_t bytes = sizeof(double2) * (size_t)a->da.N * nrhs;
+  if (a->pv_cap < bytes) {
+    if (a->pv_V) cudaFree(a->pv_V);
+    if (a->pv_E) cudaFree(a->pv_E);
+    a->pv_V = a->pv_E = nullptr;
+    a->pv_cap = 0;
+    CU(cudaMalloc(&a->pv_V, bytes));
+    CU(cudaMalloc(&a->pv_E, bytes));
+    a->pv_cap = bytes;
+  }
+  mm_status s = mm_rhs_planewave(a, nrhs, theta, phi, pol, a->pv_V, MM_C128, nullptr);
+  if (s != MM_OK) return s;
+  s = mm_solve(a, nrhs, a->pv_V, a->pv_E, opts, stats, nullptr);
+  if (s != MM_OK && s != MM_ENOCONV) return s;
+  const std::string msg = s == MM_ENOCONV ? ctx->err : std::string();
+  CU(cudaMemcpy(E_host, a->pv_E, bytes, cudaMemcpyDeviceToHost));
+  if (s == MM_ENOCONV) return fail(ctx, s, msg);
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_array_near_shape(const mm_array* a, int32_t nrhs, int32_t precision, int32_t* shape,
+                              int32_t* ksplit) {
+  if (!a || !shape || !ksplit || nrhs < 1) return MM_EINVAL;
+  if (precision != MM_C64 && precision != MM_C128) return MM_EINVAL;
+  const auto it = a->da.near_tune.find(std::make_pair((int)nrhs, precision == MM_C128 ? 8 : 4));
+  if (it == a->da.near_tune.end()) return MM_EINVAL;
+  *shape = it->second.first;
+  *ksplit = it->second.second;
+  return MM_OK;
 }
 
 mm_status mm_currents(mm_array* a, int32_t nrhs, const void* E_dev, void* J_dev, void* Jhat_dev, void* stream) {

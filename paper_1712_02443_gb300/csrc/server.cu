@@ -7,6 +7,12 @@
 // context and CUDA stream, so the products and Krylov iterations of requests
 // that are in flight at the same time overlap on the device, and a request that
 // arrives while others run starts as soon as a worker and memory are free.
+// When a worker takes a request, the waiting requests with the same geometry
+// and solve options join it: their incidences become further columns of one
+// batched solve (one product and one Arnoldi step per iteration for all of
+// them), and each request receives its own columns of the solution.  Green's
+// spectra are shared across arrays of equal grid size (the set-up cache), the
+// near-field blocks across arrays of the same element types.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +32,8 @@
 
 namespace {
 
+constexpr int kMaxMergedRhs = 64;   // columns of one merged solve
+
 double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -40,7 +48,8 @@ struct Req {
   std::vector<double> th, ph;
   std::vector<int32_t> pol;
   mm_solve_opts opts{};
-  size_t est = 0;
+  size_t est = 0;           // device footprint estimate of the request solved alone
+  size_t est_per_rhs = 0;   // its part that grows with the number of columns
   int64_t n = 0;
   // results
   bool done = false;
@@ -49,6 +58,7 @@ struct Req {
   std::vector<double> E;   // complex128 interleaved, N^ x nrhs
   mm_solve_stats stats{};
   double t_submit = 0, t_start = 0, t_setup = 0, t_end = 0;
+  int group_requests = 1, group_columns = 0;   // the solve this request was part of
 };
 
 }  // namespace
@@ -65,37 +75,67 @@ struct mm_server {
   bool stop = false;
   uint64_t next_id = 1;
   int64_t completed = 0;
+  int64_t merged = 0;   // requests that joined another request's solve
 };
 
 namespace {
 
-void run_request(int device, mm_ctx* ctx, cudaStream_t st, Req* r) {
+bool same_geometry(const Req* a, const Req* b) {
+  return a->types == b->types && a->offsets == b->offsets && a->aim.h == b->aim.h && a->aim.order == b->aim.order &&
+         a->aim.n_nf == b->aim.n_nf && a->aim.near_csr == b->aim.near_csr && a->aim.phase[0] == b->aim.phase[0] &&
+         a->aim.phase[1] == b->aim.phase[1] && a->aim.phase[2] == b->aim.phase[2] && a->opts.tol == b->opts.tol &&
+         a->opts.restart == b->opts.restart && a->opts.max_iter == b->opts.max_iter &&
+         a->opts.precision == b->opts.precision && a->opts.refine == b->opts.refine &&
+         a->opts.inner_tol == b->opts.inner_tol && a->opts.orth == b->opts.orth && a->opts.precond == b->opts.precond;
+}
+
+// One solve for a group of requests of the same geometry and options: their
+// incidences become the columns of one batched solve (every product and
+// Arnoldi step covers all of them), and each request receives its columns.
+void run_group(int device, mm_ctx* ctx, cudaStream_t st, const std::vector<Req*>& g) {
   mm_array* arr = nullptr;
   void* V = nullptr;
   void* E = nullptr;
+  Req* r = g[0];
+  int nrhs = 0;
+  std::vector<double> th, ph;
+  std::vector<int32_t> pol;
+  for (Req* q : g) {
+    th.insert(th.end(), q->th.begin(), q->th.end());
+    ph.insert(ph.end(), q->ph.begin(), q->ph.end());
+    pol.insert(pol.end(), q->pol.begin(), q->pol.end());
+    nrhs += q->nrhs;
+  }
   auto finish = [&](mm_status s, const std::string& msg) {
-    r->status = s;
-    if (s != MM_OK) r->err = msg.empty() ? std::string(mm_last_error(ctx)) : msg;
+    for (Req* q : g) {
+      q->status = s;
+      if (s != MM_OK) q->err = msg.empty() ? std::string(mm_last_error(ctx)) : msg;
+    }
   };
-  r->t_start = now_s();
+  const double t_start = now_s();
+  for (Req* q : g) q->t_start = t_start;
   mm_status s = mm_array_create(ctx, (int64_t)r->types.size(), r->types.data(), r->offsets.data(), &r->aim, &arr);
-  r->t_setup = now_s();
+  const double t_setup = now_s();
+  for (Req* q : g) q->t_setup = t_setup;
   if (s != MM_OK) return finish(s, "");
   mm_array_info info{};
   mm_array_info_get(arr, &info);
-  r->n = info.n_unknowns;
-  const size_t bytes = sizeof(double) * 2 * (size_t)r->n * r->nrhs;
+  for (Req* q : g) q->n = info.n_unknowns;
+  const int64_t n = info.n_unknowns;
+  const size_t bytes = sizeof(double) * 2 * (size_t)n * nrhs;
   cudaSetDevice(device);
   if (cudaMallocAsync(&V, bytes, st) != cudaSuccess || cudaMallocAsync(&E, bytes, st) != cudaSuccess) {
     mm_array_destroy(arr);
     if (V) cudaFreeAsync(V, st);
     return finish(MM_ENOMEM, "device allocation for the request failed");
   }
-  s = mm_rhs_planewave(arr, r->nrhs, r->th.data(), r->ph.data(), r->pol.data(), V, MM_C128, st);
-  if (s == MM_OK) s = mm_solve(arr, r->nrhs, V, E, &r->opts, &r->stats, st);
+  mm_solve_stats stats{};
+  s = mm_rhs_planewave(arr, nrhs, th.data(), ph.data(), pol.data(), V, MM_C128, st);
+  if (s == MM_OK) s = mm_solve(arr, nrhs, V, E, &r->opts, &stats, st);
+  std::vector<double> Eall;
   if (s == MM_OK || s == MM_ENOCONV) {
-    r->E.resize(2 * (size_t)r->n * r->nrhs);
-    if (cudaMemcpyAsync(r->E.data(), E, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    Eall.resize(2 * (size_t)n * nrhs);
+    if (cudaMemcpyAsync(Eall.data(), E, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       s = MM_ECUDA;
   }
@@ -105,6 +145,20 @@ void run_request(int device, mm_ctx* ctx, cudaStream_t st, Req* r) {
   cudaFreeAsync(E, st);
   cudaStreamSynchronize(st);
   mm_array_destroy(arr);
+  // each request's columns of E (rows of nrhs interleaved complex entries)
+  int c0 = 0;
+  for (Req* q : g) {
+    q->stats = stats;
+    q->group_requests = (int)g.size();
+    q->group_columns = nrhs;
+    if (!Eall.empty()) {
+      q->E.resize(2 * (size_t)n * q->nrhs);
+      for (int64_t i = 0; i < n; ++i)
+        std::copy(Eall.begin() + 2 * (i * nrhs + c0), Eall.begin() + 2 * (i * nrhs + c0 + q->nrhs),
+                  q->E.begin() + 2 * i * q->nrhs);
+    }
+    c0 += q->nrhs;
+  }
   finish(s_final, msg);
 }
 
@@ -133,18 +187,44 @@ void worker_main(mm_server* sv) {
       if (!r) continue;
       sv->in_use += r->est;
     }
-    if (ok)
-      run_request(sv->device, ctx, st, r);
-    else {
-      r->status = MM_ECUDA;
-      r->err = "worker could not create its context or stream";
+    // waiting requests of the same geometry and options join this solve as
+    // further columns (up to kMaxMergedRhs columns); the merged request's
+    // extra columns cost its per-column share of the footprint
+    std::vector<Req*> group{r};
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      int cols = r->nrhs;
+      for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+        Req* q = *it;
+        if (cols + q->nrhs <= kMaxMergedRhs && same_geometry(r, q) &&
+            sv->in_use + q->est_per_rhs * q->nrhs <= sv->budget) {
+          group.push_back(q);
+          cols += q->nrhs;
+          sv->in_use += q->est_per_rhs * q->nrhs;
+          it = sv->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
     }
-    r->t_end = now_s();
+    if (ok)
+      run_group(sv->device, ctx, st, group);
+    else
+      for (Req* q : group) {
+        q->status = MM_ECUDA;
+        q->err = "worker could not create its context or stream";
+      }
+    const double t_end = now_s();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->in_use -= r->est;
-      r->done = true;
-      ++sv->completed;
+      for (size_t i = 1; i < group.size(); ++i) sv->in_use -= group[i]->est_per_rhs * group[i]->nrhs;
+      for (Req* q : group) {
+        q->t_end = t_end;
+        q->done = true;
+        ++sv->completed;
+      }
+      sv->merged += (int64_t)group.size() - 1;
     }
     sv->cv_done.notify_all();
     sv->cv_work.notify_all();
@@ -201,8 +281,8 @@ mm_status mm_server_submit(mm_server* sv, const mm_request* q, uint64_t* ticket)
   // blocks and, when the array assembles it (moderate sizes), the near-field
   // CSR (~650 entries per row, values of both precisions and columns)
   const size_t csr = std::min<size_t>((size_t)nh * 650 * 36, (size_t)8 << 30);
-  r->est = csr + (size_t)nh * q->nrhs * 16 * (q->solve.restart + 8) + (size_t)nh * q->nrhs * 256 + (size_t)ns * 64 +
-           ((size_t)64 << 20);
+  r->est_per_rhs = (size_t)nh * 16 * (q->solve.restart + 8) + (size_t)nh * 256;
+  r->est = (q->aim.near_csr == 2 ? 0 : csr) + r->est_per_rhs * q->nrhs + (size_t)ns * 64 + ((size_t)64 << 20);
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -233,6 +313,8 @@ mm_status mm_server_poll(mm_server* sv, uint64_t ticket, int32_t wait, mm_result
   res->solve_s = r->t_end - r->t_setup;
   res->latency_s = r->t_end - r->t_submit;
   std::snprintf(res->message, sizeof(res->message), "%s", r->err.c_str());
+  res->group_requests = r->group_requests;
+  res->group_columns = r->group_columns;
   if (E_host) {
     if (E_count < 2 * r->n * r->nrhs) return MM_EINVAL;
     std::copy(r->E.begin(), r->E.end(), E_host);

@@ -22,7 +22,15 @@ Files (numpy .npz, complex128):
                   Y = Z_AIM X (full) for X = workloads.random_cvec(N, 3, 7, nrhs=8),
                   V (theta = 0, x-pol) and E = its solution to 1e-12.
 
-python tests/golden/make_golden.py [c4]   (c4: only the multiscale file)
+  c3_solve_6x6.npz  the 6x6 four-type array: excitations and solutions (GMRES
+                  to 1e-11) of incidences 0 and 37 of the 8 x 8 grid.
+  c4_meander_2x2_post.npz  currents J, J^ of the stored multiscale solution E
+                  and the far field F and RCS of J^ on 38 directions.
+  c4_full_element_2x1.npz  2x1 array of the full multiscale element (2,547
+                  scatterer RWG, 8x8x2 box): Y = Z_AIM X for
+                  X = workloads.random_cvec(N, 3, 11, nrhs=2) (checksum stored).
+
+python tests/golden/make_golden.py [c4 | extra]   (only that part)
 """
 from __future__ import annotations
 
@@ -143,9 +151,67 @@ def multiscale():
     print("c4", time.time() - t0)
 
 
+def extra():
+    """Solutions and post-processing for the end-to-end tests (oracle only)."""
+    t0 = time.time()
+    params = AIMParams(H, ORDER, NNF, wl.DEFAULT_GRID_PHASE)
+    # c3 family 6x6: the solutions of two incidences of the 8 x 8 grid
+    outers = (0.30, 0.34, 0.38, 0.42)
+    lay = wl.loop_array(6, 6, outers=outers, config_index=2)
+    ems = [build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0) for et in lay.types]
+    A = AIMArray(ems, lay.type_of, lay.offsets, params, K0)
+    th, ph, pol = wl.planewave_grid()
+    cols = np.array([0, 37])
+    V = np.zeros((A.n, len(cols)), dtype=np.complex128)
+    for e in range(len(lay.offsets)):
+        Ve = excitation(translated_rwg(ems[lay.type_of[e]].rwg_e, lay.offsets[e]), th[cols], ph[cols], pol[cols], K0)
+        V[A.off[e]:A.off[e + 1]] = Ve
+    E = np.zeros_like(V)
+    for j in range(len(cols)):
+        E[:, j], it, hist = gmres(A.matvec, V[:, j], tol=1e-11, restart=200, max_iter=4000)
+        print("c3 column", cols[j], "iterations", it, hist[-1])
+    np.savez_compressed(os.path.join(HERE, "c3_solve_6x6.npz"), cols=cols, V=V, E=E, type_of=lay.type_of)
+    print("c3 solve", time.time() - t0)
+
+    # reduced multiscale 2x2: currents and far field of the stored solution
+    et = wl.multiscale_element(meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    lay = wl.multiscale_array(2, 2, meander=wl.MEANDER_REDUCED, box_div=wl.MEANDER_REDUCED_BOX)
+    g = np.load(os.path.join(HERE, "c4_meander_2x2.npz"))
+    E = g["E"]
+    nh = em.rwg_e.n
+    JJ = [em.currents(E[e * nh:(e + 1) * nh]) for e in range(len(lay.offsets))]
+    J = np.concatenate([c[0] for c in JJ])
+    Jh = np.concatenate([c[1] for c in JJ])
+    xyz, tri = merge_meshes([lay.types[0].equiv.translated(o) for o in lay.offsets])
+    rw = build_rwg(xyz, tri)
+    thd = np.deg2rad(np.concatenate([np.arange(0, 181, 10.0), np.arange(0, 181, 10.0)]))
+    phd = np.deg2rad(np.concatenate([np.zeros(19), np.full(19, 90.0)]))
+    F = far_field(rw, Jh, thd, phd, K0)
+    np.savez_compressed(os.path.join(HERE, "c4_meander_2x2_post.npz"), J=J, Jhat=Jh, theta=thd, phi=phd, F=F,
+                        sigma=rcs(F))
+    print("c4 post", time.time() - t0)
+
+    # the full multiscale element (2,547 scatterer RWG, 8x8x2 box) on a 2x1 array:
+    # the product of two right-hand sides, every entry
+    et = wl.multiscale_element()
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    print("full multiscale element", time.time() - t0)
+    lay = wl.multiscale_array(2, 1)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0)
+    X = wl.random_cvec(A.n, 3, 11, nrhs=2)
+    Y = np.stack([A.matvec(np.ascontiguousarray(X[:, j])) for j in range(2)], axis=1)
+    np.savez_compressed(os.path.join(HERE, "c4_full_element_2x1.npz"), x_check=_check(X), y=Y,
+                        n_scat=em.rwg_s.n if hasattr(em, "rwg_s") else -1)
+    print("c4 full element", time.time() - t0)
+
+
 if __name__ == "__main__":
     if sys.argv[1:] == ["c4"]:
         multiscale()
+    elif sys.argv[1:] == ["extra"]:
+        extra()
     else:
         main()
         multiscale()
+        extra()

@@ -148,6 +148,29 @@ def test_mom_sphere_rcs_converges_to_mie():
     assert errs[1] < 0.5 and errs[1] < 0.5 * errs[0]
 
 
+def test_mie_small_sphere_matches_rayleigh_dipoles():
+    """Rayleigh limit of the series (ka -> 0): the sphere scatters as an electric
+    dipole p = 4 pi eps0 a^3 E0 plus a magnetic dipole m = -2 pi a^3 H0, so with
+    mu = cos(scattering angle) the bistatic RCS is
+      E-plane: 4 pi a^2 (ka)^4 (mu - 1/2)^2,   H-plane: 4 pi a^2 (ka)^4 (1 - mu/2)^2
+    (backscatter 9 pi a^2 (ka)^4, forward pi a^2 (ka)^4).  The next terms are
+    O((ka)^2) relative, so at ka = 1e-3 the series must agree to ~1e-6 of the
+    pattern's maximum; a sign slip between the electric and magnetic terms, or
+    the two amplitudes swapped, moves it by O(1)."""
+    k = K0
+    for ka in (1e-3, 3e-3):
+        a = ka / k
+        T = np.linspace(0.0, np.pi, 37)
+        mu = np.cos(T)
+        sE, sH = pec_sphere_rcs(ka, k, T)
+        rE = 4 * np.pi * a * a * ka ** 4 * (mu - 0.5) ** 2
+        rH = 4 * np.pi * a * a * ka ** 4 * (1 - 0.5 * mu) ** 2
+        top = 9 * np.pi * a * a * ka ** 4
+        assert np.abs(sE - rE).max() <= 20 * ka ** 2 * top
+        assert np.abs(sH - rH).max() <= 20 * ka ** 2 * top
+        assert abs(sE[-1] / top - 1) <= 20 * ka ** 2 and abs(sE[0] / (np.pi * a * a * ka ** 4) - 1) <= 20 * ka ** 2
+
+
 def test_mie_large_sphere_backscatter_tends_to_geometric_optics():
     # sigma_back -> pi a^2 as k a -> infinity (textbook limit)
     a = 3.0
