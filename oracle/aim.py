@@ -322,6 +322,10 @@ class AIMArray:
     def far(self, u: np.ndarray, rows=None) -> np.ndarray:
         return self.interpolate(convolve(self.project(u), self.Khat), rows)
 
+    def gapply(self, u: np.ndarray) -> np.ndarray:
+        """G^(E^,J^) u by AIM: far field (steps i-iii) plus the precorrected near field."""
+        return self.far(u) + self.GNF @ u
+
     # ---- full operator ----------------------------------------------------
     def macro(self, x: np.ndarray) -> np.ndarray:
         """u = T A^-1 B x, block diagonal (Sec. III)."""

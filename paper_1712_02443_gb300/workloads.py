@@ -235,6 +235,83 @@ def loop_array(nx: int, ny: int, pitch: float = 0.5, outers=(0.4,), config_index
     return ArrayLayout(types, type_of, offs, nx, ny, pitch)
 
 
+def fed_loop_mesh(outer: float = 0.4, width: float = 0.04, n_per_side: int = 22):
+    """Structured mesh of the square loop for a driven element: three square rings
+    (outer edge, middle, inner edge) with the same number of nodes per side,
+    joined by quads split into two triangles, so that every radial line of nodes
+    is a chain of mesh edges.  The feed gap is the chain at the middle of the side
+    y = -outer/2 (n_per_side even: a node at x = 0); the feed direction is +x
+    (along the trace there).  Returns (mesh, gap edges as vertex pairs, direction)."""
+    if n_per_side % 2:
+        raise ValueError("n_per_side must be even (a node at the middle of each side)")
+    rings = [_square_ring(outer - 2.0 * width * f, n_per_side) for f in (0.0, 0.5, 1.0)]
+    npr = 4 * n_per_side
+    pts = np.vstack(rings)
+    tri = []
+    for k in range(2):
+        for i in range(npr):
+            a, b = k * npr + i, k * npr + (i + 1) % npr
+            c, d = (k + 1) * npr + i, (k + 1) * npr + (i + 1) % npr
+            if (i // (n_per_side // 2)) % 2 == 0:
+                tri += [[a, b, d], [a, d, c]]
+            else:
+                tri += [[a, b, c], [b, d, c]]
+    tri = np.array(tri, dtype=np.int32)
+    p = pts[tri]
+    cr = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0])
+    flip = cr < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    xyz = np.zeros((len(pts), 3))
+    xyz[:, :2] = pts
+    m = Mesh(xyz, tri, "fed_loop")
+    i0 = n_per_side // 2   # node at x = 0 on the side y = -outer/2
+    gap = [(i0, npr + i0), (npr + i0, 2 * npr + i0)]
+    return m, gap, (1.0, 0.0, 0.0)
+
+
+def rwg_index(mesh: Mesh, pairs) -> np.ndarray:
+    """Index of the RWG function on each interior edge (vertex pair), in the
+    library's numbering: interior edges in lexicographic (min, max) order."""
+    cnt: dict = {}
+    for t in mesh.tri:
+        for i in range(3):
+            a, b = int(t[(i + 1) % 3]), int(t[(i + 2) % 3])
+            k = (min(a, b), max(a, b))
+            cnt[k] = cnt.get(k, 0) + 1
+    interior = sorted(k for k, c in cnt.items() if c == 2)
+    pos = {k: i for i, k in enumerate(interior)}
+    return np.array([pos[(min(a, b), max(a, b))] for a, b in pairs], dtype=np.int64)
+
+
+def fed_loop_element(outer: float = 0.4, box=(0.45, 0.45, 0.1), box_div=(6, 6, 1)):
+    """Driven loop element: (ElementType, gap RWG indices, feed direction)."""
+    m, gap, d = fed_loop_mesh(outer)
+    return ElementType(m, box_mesh(*box, *box_div), "fed_loop%g" % outer), rwg_index(m, gap), d
+
+
+def fed_loop_array(nx: int, ny: int, pitch: float = 0.5) -> ArrayLayout:
+    """nx x ny array of the driven loop; layout.extra holds the feed (gap, direction)."""
+    et, gap, d = fed_loop_element()
+    offs = np.array([(pitch * i, pitch * j, 0.0) for j in range(ny) for i in range(nx)], dtype=np.float64)
+    return ArrayLayout([et], np.zeros(nx * ny, dtype=np.int32), offs, nx, ny, pitch,
+                       extra={"gap": gap, "direction": d})
+
+
+def ground_plane_array(layout: ArrayLayout, z_ground: float) -> ArrayLayout:
+    """The layout plus the image of every element in the PEC plane z = z_ground
+    (image theory).  The loop elements are planar at z = 0 of their own frame, so
+    an image element has the same type at the mirrored offset (x, y, 2 z_g - z);
+    images follow the originals (elements n .. 2n - 1)."""
+    off = np.array(layout.offsets, dtype=np.float64, copy=True)
+    img = off.copy()
+    img[:, 2] = 2.0 * z_ground - img[:, 2]
+    extra = dict(layout.extra)
+    extra["z_ground"] = z_ground
+    extra["n_original"] = layout.n_elem
+    return ArrayLayout(layout.types, np.concatenate([layout.type_of, layout.type_of]), np.vstack([off, img]),
+                       layout.nx, layout.ny, layout.pitch, extra=extra)
+
+
 def meander_mesh(extent: float = 0.28, width: float = 0.01, gap: float = 0.005, dx: float = 0.005) -> Mesh:
     """Serpentine strip at z = 0 inside a square of side `extent` (centred): runs
     along x of trace width `width`, separated by `gap` (the smallest feature),
