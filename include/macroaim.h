@@ -226,6 +226,52 @@ mm_status mm_rhs_planewave(mm_array* array, int32_t nrhs, const double* theta, c
  * (N^ x nrhs) complex128 or NULL.  FP64 throughout.  Queued on `stream`.    */
 mm_status mm_currents(mm_array* array, int32_t nrhs, const void* E_dev, void* J_dev, void* Jhat_dev, void* stream);
 
+/* ------------------------------------------------------- driven elements
+ * Delta-gap feed of an element type (Sec. VI: driven array elements; the
+ * paper states that the macromodel carries over to them without giving the
+ * equations; this library's reading): a gap of voltage V across the scatterer
+ * RWG edges rwg[0..n_edges) is the impressed field V delta(xi) xi^, xi^ along
+ * `direction` (3 doubles, not parallel to the gap edges); in the MoM form
+ * (Z = j k0 eta0 L, right-hand side <f, E>) edge g gets f_g = s_g V l_g, s_g the
+ * sign of xi^ . n_g with n_g the in-plane normal of edge g from its T+ to its
+ * T- triangle (T+ the lower-numbered triangle of the edge).  The feed enters
+ * the scatterer's equation, eq. (EFIEdiscretized1), so with A and B of eq. (JM)
+ * the currents are J = -A^-1 B E^ + J_f V, J_f = -A^-1 f (FP64, host, per
+ * volt), and the equivalent current J^ = T J carries J^_f = T J_f into the
+ * exterior problem.  Set feeds before creating arrays with the type.
+ * MM_EINVAL for an edge index out of range or a direction parallel to an edge. */
+mm_status mm_type_set_feed(mm_type* type, int32_t n_edges, const int64_t* rwg, const double* direction);
+
+/* Excitation of driven elements: with the feed in the scatterers, the
+ * exterior system keeps the operator of eq. (finalsystem) and its right-hand
+ * side becomes V^_eff = -G^(E^,J^) J^_f V (no incident field), G applied by
+ * AIM like the product's coupling part (complex128).  volts: host, n_elem x
+ * nrhs complex128 interleaved (element-major, right-hand sides innermost);
+ * elements of types without a feed get no source.  V_dev: (N^ x nrhs)
+ * complex128.  Queued on `stream`.  Add a plane-wave excitation for mixed
+ * problems.  MM_EINVAL when no type of the array has a feed.               */
+mm_status mm_rhs_deltagap(mm_array* array, int32_t nrhs, const double* volts, void* V_dev, void* stream);
+
+/* Currents of a driven solution: mm_currents plus the feed's share,
+ * J += J_f V and J^ += J^_f V per driven element (volts as in
+ * mm_rhs_deltagap).  The port current of a gap is sum_g s_g J_g l_g.        */
+mm_status mm_currents_fed(mm_array* array, int32_t nrhs, const void* E_dev, const double* volts, void* J_dev,
+                          void* Jhat_dev, void* stream);
+
+/* ----------------------------------------------------------- ground plane
+ * Plane-wave excitation above a PEC plane z = z_ground by image theory (Sec.
+ * VI, the reflectarrays' ground plane): the array must hold every element and
+ * its image (same type at (x, y, 2 z_ground - z) for elements symmetric under
+ * z -> -z in their own frame); the incident field is the plane wave plus its
+ * image, E_img(r) = S E_inc(R r), R the reflection in the plane and
+ * S = diag(-1, -1, 1).  The image of the wave arriving from (theta, phi) with
+ * polarisation theta^ (phi^) is the wave arriving from (pi - theta, phi) with
+ * theta^ (-phi^), times exp(2 j k0 z_ground cos theta): V^ is the sum of two
+ * mm_rhs_planewave excitations.  Arguments as mm_rhs_planewave.             */
+mm_status mm_rhs_planewave_ground(mm_array* array, int32_t nrhs, const double* theta, const double* phi,
+                                  const int32_t* pol, double z_ground, void* V_dev, int32_t precision,
+                                  void* stream);
+
 /* Far-field pattern radiated by the equivalent currents (the radiation
  * integral of the array's patterns, Sec. VI): with E ~ F exp(-j k0 r)/r,
  *   F(r^) = -j k0 eta0/(4 pi) (I - r^ r^) . sum_n J^_n int f^_n exp(j k0 r^.r') dS'

@@ -111,6 +111,10 @@ _SIGS = {
     "mm_test_tc_stall": (ct.c_int, [ct.c_int32]),
     "mm_solve_planewave_host": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.POINTER(mm_solve_opts),
                                            ct.POINTER(mm_solve_stats)]),
+    "mm_type_set_feed": (ct.c_int, [P, ct.c_int32, P, P]),
+    "mm_rhs_deltagap": (ct.c_int, [P, ct.c_int32, P, P, P]),
+    "mm_currents_fed": (ct.c_int, [P, ct.c_int32, P, P, P, P, P]),
+    "mm_rhs_planewave_ground": (ct.c_int, [P, ct.c_int32, P, P, P, ct.c_double, P, ct.c_int32, P]),
     "mm_array_near_shape": (ct.c_int, [P, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
 }
 
@@ -304,6 +308,34 @@ def mm_rhs_planewave(array, theta, phi, pol, V_dev, precision: int, stream=None)
     po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
     _check(load().mm_rhs_planewave(array, len(th), _ptr(th), _ptr(ph), _ptr(po), _ptr(V_dev), precision,
                                    _stream(stream)), _ctx_of.get(array.value))
+
+
+def mm_type_set_feed(type_, rwg, direction) -> None:
+    """Delta-gap feed across the scatterer RWG edges `rwg` along `direction`."""
+    r = np.ascontiguousarray(rwg, dtype=np.int64).ravel()
+    d = np.ascontiguousarray(direction, dtype=np.float64).ravel()
+    _check(load().mm_type_set_feed(type_, len(r), _ptr(r), _ptr(d)), _ctx_of.get(type_.value))
+
+
+def mm_rhs_deltagap(array, volts, V_dev, stream=None) -> None:
+    """V^_eff of the driven elements; volts (n_elem, nrhs) complex."""
+    v = np.ascontiguousarray(volts, dtype=np.complex128)
+    nrhs = v.shape[1] if v.ndim == 2 else 1
+    _check(load().mm_rhs_deltagap(array, nrhs, _ptr(v), _ptr(V_dev), _stream(stream)), _ctx_of.get(array.value))
+
+
+def mm_currents_fed(array, nrhs: int, E_dev, volts, J_dev=None, Jhat_dev=None, stream=None) -> None:
+    v = np.ascontiguousarray(volts, dtype=np.complex128)
+    _check(load().mm_currents_fed(array, nrhs, _ptr(E_dev), _ptr(v), _ptr(J_dev), _ptr(Jhat_dev), _stream(stream)),
+           _ctx_of.get(array.value))
+
+
+def mm_rhs_planewave_ground(array, theta, phi, pol, z_ground: float, V_dev, precision: int, stream=None) -> None:
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
+    _check(load().mm_rhs_planewave_ground(array, len(th), _ptr(th), _ptr(ph), _ptr(po), float(z_ground), _ptr(V_dev),
+                                          precision, _stream(stream)), _ctx_of.get(array.value))
 
 
 def mm_currents(array, nrhs: int, E_dev, J_dev=None, Jhat_dev=None, stream=None) -> None:

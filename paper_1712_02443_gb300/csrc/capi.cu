@@ -18,6 +18,7 @@
 #include "macroaim.h"
 #include "post.h"
 #include "solver.h"
+#include "drive.h"
 #include "near_tc.h"
 #include "tc_gemm.h"
 
@@ -36,6 +37,10 @@ struct mm_mesh {
 struct mm_type {
   mm_ctx* ctx;
   mm::TypeModel tm;
+  // delta-gap feed (mm_type_set_feed): J_f = -A^-1 f (N) and J^_f = T J_f (N^)
+  // of one volt, f the gap's MoM right-hand side
+  bool fed = false;
+  std::vector<mm::cd> feed_Jf, feed_Jhf;
 };
 struct mm_array {
   mm_ctx* ctx = nullptr;
@@ -66,6 +71,15 @@ struct mm_array {
   // basis) and its inverse
   std::vector<std::vector<int32_t>> nf_perm, nf_iperm;
   std::vector<int32_t> nfb_arow_h;   // per block: first row in the tensor-core block layout
+  std::vector<void*> d_Jf, d_Jhf;    // per type: device copies of the feed vectors (nullptr: not fed)
+  void* d_volts = nullptr;           // driven elements' volts (n_elem x nrhs complex128)
+  void* d_fu = nullptr;              // the driven elements' equivalent currents J^_f V (N^ x nrhs)
+  size_t fu_cap = 0;
+  size_t volts_cap = 0;
+  void* d_pw2 = nullptr;             // ground plane: the image wave's excitation
+  size_t pw2_cap = 0;
+  double* d_gc = nullptr;            // ground plane: per right-hand side factor of the image wave
+  int gc_cap = 0;
   void* pv_V = nullptr;              // mm_solve_planewave_host: excitation and solution on the device
   void* pv_E = nullptr;
   size_t pv_cap = 0;
@@ -455,6 +469,12 @@ mm_array::~mm_array() {
   if (da.chain) cudaStreamDestroy(da.chain);
   if (ang_ev) cudaEventDestroy(ang_ev);
   if (d_pw) cudaFree(d_pw);
+  for (void* q : d_Jf)
+    if (q) cudaFree(q);
+  for (void* q : d_Jhf)
+    if (q) cudaFree(q);
+  for (void* q : {d_volts, d_fu, d_pw2, (void*)d_gc})
+    if (q) cudaFree(q);
   if (pv_V) cudaFree(pv_V);
   if (pv_E) cudaFree(pv_E);
   if (da.tbase) cudaFree(da.tbase);
@@ -1268,7 +1288,7 @@ mm_status mm_currents(mm_array* a, int32_t nrhs, const void* E_dev, void* J_dev,
       a->d_JE.push_back(dev_upload(tm.JE.data(), tm.JE.size(), acc));
       a->d_T.push_back(dev_upload(tm.T.data(), tm.T.size(), acc));
     }
-    a->d_offs = dev_upload(a->offs.data(), a->offs.size(), acc);
+    if (!a->d_offs) a->d_offs = dev_upload(a->offs.data(), a->offs.size(), acc);
     da.bytes += acc;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1289,6 +1309,196 @@ mm_status mm_currents(mm_array* a, int32_t nrhs, const void* E_dev, void* J_dev,
   }
   if (tmp) cudaFreeAsync(tmp, st);
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("currents: ") + cudaGetErrorString(e));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_type_set_feed(mm_type* type, int32_t n_edges, const int64_t* rwg, const double* direction) {
+  if (!type) return MM_EINVAL;
+  mm_ctx* ctx = type->ctx;
+  auto& tm = type->tm;
+  if (n_edges < 1 || !rwg || !direction) return fail(ctx, MM_EINVAL, "invalid feed arguments");
+  const mm::Mesh& ms = tm.scat;
+  const mm::Vec3 d{direction[0], direction[1], direction[2]};
+  if (!(mm::norm(d) > 0)) return fail(ctx, MM_EINVAL, "feed direction must be non-zero");
+  API_TRY
+  const int64_t N = tm.N;
+  std::vector<mm::cd> f(N, mm::cd(0, 0));
+  for (int32_t i = 0; i < n_edges; ++i) {
+    const int64_t g = rwg[i];
+    if (g < 0 || g >= N) return fail(ctx, MM_EINVAL, "feed edge out of range");
+    // s = sign(d . n_g), n_g the in-plane normal of edge g from its T+ to its T- triangle
+    const mm::Vec3 a = ms.v[ms.edge_a[g]], b = ms.v[ms.edge_b[g]];
+    const mm::Vec3 e = (1.0 / mm::norm(b - a)) * (b - a);
+    const int64_t tp = ms.tplus[g], tq = ms.tminus[g];
+    const mm::Vec3 cp = (1.0 / 3.0) * (ms.tv(tp, 0) + ms.tv(tp, 1) + ms.tv(tp, 2));
+    const mm::Vec3 cq = (1.0 / 3.0) * (ms.tv(tq, 0) + ms.tv(tq, 1) + ms.tv(tq, 2));
+    const mm::Vec3 c = cq - cp;
+    const mm::Vec3 n = c - mm::dot(c, e) * e;
+    const double sd = mm::dot(n, d);
+    if (sd == 0) return fail(ctx, MM_EINVAL, "feed direction parallel to a gap edge");
+    f[g] += (sd > 0 ? 1.0 : -1.0) * ms.length[g];
+  }
+  // J_f = -A^-1 f, J^_f = T J_f (FP64)
+  mm::LU lu;
+  mm::lu_factor(lu, tm.A, N);
+  std::vector<mm::cd> Jf(f);
+  mm::lu_solve(lu, Jf, 1, ctx->nthreads);
+  for (auto& z : Jf) z = -z;
+  std::vector<mm::cd> Jhf(tm.Nh, mm::cd(0, 0));
+  for (int64_t m = 0; m < tm.Nh; ++m) {
+    mm::cd acc(0, 0);
+    for (int64_t n = 0; n < N; ++n) acc += tm.T[m * N + n] * Jf[n];
+    Jhf[m] = acc;
+  }
+  type->feed_Jf = std::move(Jf);
+  type->feed_Jhf = std::move(Jhf);
+  type->fed = true;
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+namespace {
+
+// Device copies of the feed vectors of the array's types and of the volts.
+void upload_feeds(mm_array* a, const double* volts, int nrhs, cudaStream_t st) {
+  auto& da = a->da;
+  if (a->d_Jf.empty()) {
+    size_t acc = 0;
+    for (int64_t t = 0; t < da.n_types; ++t) {
+      const mm_type* ty = a->types[t];
+      a->d_Jf.push_back(ty->fed ? dev_upload(ty->feed_Jf.data(), ty->feed_Jf.size(), acc) : nullptr);
+      a->d_Jhf.push_back(ty->fed ? dev_upload(ty->feed_Jhf.data(), ty->feed_Jhf.size(), acc) : nullptr);
+    }
+    da.bytes += acc;
+  }
+  if (a->d_offs == nullptr) {
+    size_t acc = 0;
+    a->d_offs = dev_upload(a->offs.data(), a->offs.size(), acc);
+    da.bytes += acc;
+  }
+  const size_t vb = sizeof(double2) * (size_t)da.n_elem * nrhs;
+  if (a->volts_cap < vb) {
+    if (a->d_volts) cudaFree(a->d_volts);
+    a->d_volts = nullptr;
+    a->volts_cap = 0;
+    CU(cudaMalloc(&a->d_volts, vb));
+    a->volts_cap = vb;
+  }
+  CU(cudaMemcpyAsync(a->d_volts, volts, vb, cudaMemcpyHostToDevice, st));
+}
+
+bool any_fed(const mm_array* a) {
+  for (const mm_type* t : a->types)
+    if (t->fed) return true;
+  return false;
+}
+
+}  // namespace
+
+mm_status mm_rhs_deltagap(mm_array* a, int32_t nrhs, const double* volts, void* V_dev, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !volts || !V_dev) return fail(ctx, MM_EINVAL, "invalid excitation arguments");
+  if (!any_fed(a)) return fail(ctx, MM_EINVAL, "no element type of the array has a feed (mm_type_set_feed)");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto& da = a->da;
+  upload_precision<double>(a, da.pd);
+  ensure_work<double>(a, da.wd, nrhs);
+  upload_feeds(a, volts, nrhs, st);
+  // u = J^_f V per driven element (zero elsewhere), then V^_eff = -G u
+  const size_t ub = sizeof(double2) * (size_t)da.N * nrhs;
+  if (a->fu_cap < ub) {
+    if (a->d_fu) cudaFree(a->d_fu);
+    a->d_fu = nullptr;
+    a->fu_cap = 0;
+    CU(cudaMalloc(&a->d_fu, ub));
+    a->fu_cap = ub;
+  }
+  void* u = a->d_fu;
+  CU(cudaMemsetAsync(u, 0, ub, st));
+  for (int64_t t = 0; t < da.n_types; ++t)
+    if (a->d_Jhf[t]) CU(mm::feed_axpy(a->d_Jhf[t], (int)da.Nh[t], da.elems[t], (int)da.n_of_type[t], nrhs, da.off,
+                                      a->d_volts, u, false, st));
+  CU(mm::matvec<double>(da, da.pd, da.wd, nrhs, u, V_dev, st, 0, false, mm::kMvUInput));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_currents_fed(mm_array* a, int32_t nrhs, const void* E_dev, const double* volts, void* J_dev,
+                          void* Jhat_dev, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!volts) return fail(ctx, MM_EINVAL, "invalid currents arguments");
+  mm_status s = mm_currents(a, nrhs, E_dev, J_dev, Jhat_dev, stream);
+  if (s != MM_OK) return s;
+  if (!J_dev && !Jhat_dev) return MM_OK;
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto& da = a->da;
+  upload_feeds(a, volts, nrhs, st);
+  for (int64_t t = 0; t < da.n_types; ++t) {
+    if (!a->d_Jf[t]) continue;
+    if (J_dev)
+      CU(mm::feed_axpy(a->d_Jf[t], (int)a->types[t]->tm.N, da.elems[t], (int)da.n_of_type[t], nrhs, a->d_offs,
+                       a->d_volts, J_dev, true, st));
+    if (Jhat_dev)
+      CU(mm::feed_axpy(a->d_Jhf[t], (int)da.Nh[t], da.elems[t], (int)da.n_of_type[t], nrhs, da.off, a->d_volts,
+                       Jhat_dev, true, st));
+  }
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_rhs_planewave_ground(mm_array* a, int32_t nrhs, const double* theta, const double* phi,
+                                  const int32_t* pol, double z_ground, void* V_dev, int32_t precision, void* stream) {
+  if (!a) return MM_EINVAL;
+  mm_ctx* ctx = a->ctx;
+  if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
+  if (nrhs < 1 || !theta || !phi || !pol || !V_dev) return fail(ctx, MM_EINVAL, "invalid excitation arguments");
+  if (precision != MM_C64 && precision != MM_C128) return fail(ctx, MM_EINVAL, "unknown precision");
+  API_TRY
+  CU(cudaSetDevice(a->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t cs = precision == MM_C128 ? 16 : 8;
+  const size_t bytes = cs * (size_t)a->da.N * nrhs;
+  if (a->pw2_cap < bytes) {
+    if (a->d_pw2) cudaFree(a->d_pw2);
+    a->d_pw2 = nullptr;
+    a->pw2_cap = 0;
+    CU(cudaMalloc(&a->d_pw2, bytes));
+    a->pw2_cap = bytes;
+  }
+  if (a->gc_cap < nrhs) {
+    if (a->d_gc) cudaFree(a->d_gc);
+    a->d_gc = nullptr;
+    a->gc_cap = 0;
+    CU(cudaMalloc(&a->d_gc, sizeof(double) * 2 * nrhs));
+    a->gc_cap = nrhs;
+  }
+  // the image of a plane wave arriving from (theta, phi) with polarisation p is
+  // the plane wave arriving from (pi - theta, phi) with polarisation S p =
+  // +theta^ (p = theta^) or -phi^ (p = phi^), times exp(2 j k0 z_g cos theta)
+  std::vector<double> th2(nrhs), c(2 * nrhs);
+  for (int j = 0; j < nrhs; ++j) {
+    th2[j] = M_PI - theta[j];
+    const double s = pol[j] == 0 ? 1.0 : -1.0;
+    const double arg = 2.0 * a->k0 * z_ground * std::cos(theta[j]);
+    c[2 * j] = s * std::cos(arg);
+    c[2 * j + 1] = s * std::sin(arg);
+  }
+  mm_status r = mm_rhs_planewave(a, nrhs, theta, phi, pol, V_dev, precision, stream);
+  if (r != MM_OK) return r;
+  r = mm_rhs_planewave(a, nrhs, th2.data(), phi, pol, a->d_pw2, precision, stream);
+  if (r != MM_OK) return r;
+  CU(cudaMemcpyAsync(a->d_gc, c.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+  CU(mm::rhs_combine(precision == MM_C64, a->da.N, nrhs, a->d_gc, a->d_pw2, V_dev, st));
+  // the factors come from pageable host memory: the copy is staged before the
+  // call returns, so c may go out of scope
   return MM_OK;
   API_CATCH(ctx)
 }

@@ -216,7 +216,8 @@ constexpr int kNearShapes = 7;
 // Flags of matvec: kMvNoTune never times near-field kernel shapes (an untuned
 // right-hand-side count takes the size rule and is not remembered);
 // kMvNoProfile records no stage events (the array's profiler is left alone).
-constexpr unsigned kMvNoTune = 1u, kMvNoProfile = 2u;
+// kMvUInput takes x as u (the macromodel stage skipped) and v = 0: y = -G x.
+constexpr unsigned kMvNoTune = 1u, kMvNoProfile = 2u, kMvUInput = 4u;
 // gemm_mode: 0 CUDA-core GEMM; 1 BF16 / 2 FP16 tensor-core GEMM (complex64 only)
 // pre: apply Z P^-1 (the block-Jacobi right-preconditioned operator) through
 // the fused macromodel matrices p.WP / p.AtcP

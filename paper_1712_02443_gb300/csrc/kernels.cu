@@ -1456,10 +1456,19 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   Profiler off;   // stays disabled: records nothing, creates no events
   Profiler& pr = (flags & kMvNoProfile) ? off : a.prof;
   const int sb = sizeof(R) == 8 ? 8 : 0;   // profiler slot base of this precision
-  // A1: u = M x, v = D x, per type
+  // A1: u = M x, v = D x, per type (with kMvUInput, u = x and v = 0 instead:
+  // the product is then y = -G x, the coupling operator alone)
   pr.begin(sb + 0, st);
   int nl = 0;
-  if (sizeof(R) == 4 && gemm_mode != 0) {
+  const bool u_input = (flags & kMvUInput) != 0;
+  if (u_input) {
+    u = const_cast<C*>(x);
+    e = cudaMemsetAsync(v, 0, sizeof(C) * (size_t)a.N * nrhs, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (u_input) {
+    // no macromodel stage
+  } else if (sizeof(R) == 4 && gemm_mode != 0) {
     for (int64_t t = 0; t < a.n_types; ++t) {
       if (a.n_of_type[t] == 0) continue;
       const void* At = (pre ? p.AtcP : p.Atc)[gemm_mode - 1][t];
@@ -1471,7 +1480,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
       nl += 2;
     }
   }
-  for (int64_t t = 0; t < a.n_types && !(sizeof(R) == 4 && gemm_mode != 0); ++t) {
+  for (int64_t t = 0; t < a.n_types && !u_input && !(sizeof(R) == 4 && gemm_mode != 0); ++t) {
     if (a.n_of_type[t] == 0) continue;
     const int Nh = (int)a.Nh[t];
     const int ncols = (int)(a.n_of_type[t] * nrhs);
@@ -1580,14 +1589,15 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     const unsigned blocks = (unsigned)((a.N + 7) / 8);
     if constexpr (sizeof(R) == 8) {
       const double* val3 = static_cast<const double*>(p.val);
+      const double* us = u_input ? nullptr : w.us;   // Re u + Im u, written by the GEMM
       const double2* ud = reinterpret_cast<const double2*>(u);
       double2* vd = reinterpret_cast<double2*>(v);
       if (nrhs == 1)
-        k_spmv_near_3m<1><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+        k_spmv_near_3m<1><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, us, vd);
       else if (nrhs <= 4)
-        k_spmv_near_3m<4><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+        k_spmv_near_3m<4><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, us, vd);
       else
-        k_spmv_near_3m<8><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, w.us, vd);
+        k_spmv_near_3m<8><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, val3, nrhs, ud, us, vd);
     } else if (nrhs == 1)
       k_spmv_near1<R><<<blocks, 256, 0, ns>>>(a.N, a.rowptr, a.col, static_cast<const C*>(p.val), u, v);
     else if (nrhs <= 4)

@@ -30,7 +30,14 @@ Files (numpy .npz, complex128):
                   scatterer RWG, 8x8x2 box): Y = Z_AIM X for
                   X = workloads.random_cvec(N, 3, 11, nrhs=2) (checksum stored).
 
-python tests/golden/make_golden.py [c4 | extra]   (only that part)
+  fed_2x2.npz     2x2 array of the driven loop (delta gap at the middle of one
+                  side, oracle/drive.py): volts of two excitations, V^_eff,
+                  E (GMRES to 1e-12), J, J^ and the port currents.
+  ground_2x2.npz  2x2 loops over a PEC plane z = -0.1 with their images (8
+                  elements): V^ of two incidences (incident + image wave), E,
+                  and the RCS of all J^ on 20 upper-half-space directions.
+
+python tests/golden/make_golden.py [c4 | extra | drive]   (only that part)
 """
 from __future__ import annotations
 
@@ -206,12 +213,76 @@ def extra():
     print("c4 full element", time.time() - t0)
 
 
+def drive():
+    """Driven elements and the ground plane (oracle/drive.py), on 2x2 arrays."""
+    from oracle import drive as dr
+    t0 = time.time()
+    params = AIMParams(H, ORDER, NNF, wl.DEFAULT_GRID_PHASE)
+    # fed loops: two excitations (all elements at 1 V; element 0 at 1 V and element 2 at 0.5j V)
+    lay = wl.fed_loop_array(2, 2)
+    et = lay.types[0]
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    gap, d = lay.extra["gap"], lay.extra["direction"]
+    f = dr.feed_vector(em.rwg_s, gap, d, 1.0)
+    Jf, Jhf = dr.element_feed(em, f)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0)
+    volts = np.zeros((4, 2), dtype=np.complex128)
+    volts[:, 0] = 1.0
+    volts[0, 1], volts[2, 1] = 1.0, 0.5j
+    nh, ns = em.rwg_e.n, em.rwg_s.n
+    V = np.zeros((A.n, 2), dtype=np.complex128)
+    E = np.zeros_like(V)
+    J = np.zeros((4 * ns, 2), dtype=np.complex128)
+    Jh = np.zeros_like(V)
+    Ip = np.zeros((4, 2), dtype=np.complex128)
+    for j in range(2):
+        u = np.concatenate([Jhf * volts[e, j] for e in range(4)])
+        V[:, j] = -A.gapply(u)
+        E[:, j], it, hist = gmres(A.matvec, V[:, j], tol=1e-12, restart=100, max_iter=2000)
+        for e in range(4):
+            Je, Jhe = dr.driven_currents(em, E[e * nh:(e + 1) * nh, j], Jf * volts[e, j])
+            J[e * ns:(e + 1) * ns, j] = Je
+            Jh[e * nh:(e + 1) * nh, j] = Jhe
+            Ip[e, j] = dr.port_current(em.rwg_s, Je, gap, d)
+        print("fed column", j, "iterations", it, hist[-1])
+    np.savez_compressed(os.path.join(HERE, "fed_2x2.npz"), volts=volts, V=V, E=E, J=J, Jhat=Jh, port_current=Ip,
+                        gap=gap, direction=np.asarray(d))
+    print("fed", time.time() - t0)
+    # 2x2 loops over a PEC plane z = -0.1 (8 elements with the images), two incidences
+    zg = -0.1
+    base = wl.loop_array(2, 2)
+    lay = wl.ground_plane_array(base, zg)
+    et = base.types[0]
+    em = build_element(et.scatterer.xyz, et.scatterer.tri, et.equiv.xyz, et.equiv.tri, K0)
+    A = AIMArray([em], lay.type_of, lay.offsets, params, K0)
+    th = np.array([0.5, 0.3]); ph = np.array([0.35, 1.0]); pol = np.array([0, 1])
+    V = np.concatenate([dr.ground_excitation(translated_rwg(em.rwg_e, o), th, ph, pol, K0, zg) for o in lay.offsets])
+    E = np.zeros_like(V)
+    for j in range(2):
+        E[:, j], it, hist = gmres(A.matvec, V[:, j], tol=1e-12, restart=100, max_iter=2000)
+        print("ground column", j, "iterations", it, hist[-1])
+    nh = em.rwg_e.n
+    Jh = np.concatenate([np.stack([em.currents(E[e * nh:(e + 1) * nh, j])[1] for j in range(2)], axis=1)
+                         for e in range(lay.n_elem)])
+    xyz, tri = merge_meshes([et.equiv.translated(o) for o in lay.offsets])
+    rw = build_rwg(xyz, tri)
+    thd = np.deg2rad(np.concatenate([np.arange(0, 91, 10.0), np.arange(0, 91, 10.0)]))
+    phd = np.deg2rad(np.concatenate([np.zeros(10), np.full(10, 90.0)]))
+    sig = np.stack([rcs(far_field(rw, Jh[:, j], thd, phd, K0)) for j in range(2)], axis=1)
+    np.savez_compressed(os.path.join(HERE, "ground_2x2.npz"), z_ground=zg, theta=th, phi=ph, pol=pol, V=V, E=E,
+                        theta_ff=thd, phi_ff=phd, sigma=sig, offsets=lay.offsets)
+    print("ground", time.time() - t0)
+
+
 if __name__ == "__main__":
     if sys.argv[1:] == ["c4"]:
         multiscale()
     elif sys.argv[1:] == ["extra"]:
         extra()
+    elif sys.argv[1:] == ["drive"]:
+        drive()
     else:
         main()
         multiscale()
         extra()
+        drive()
