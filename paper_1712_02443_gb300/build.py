@@ -21,7 +21,7 @@ LIB = os.path.join(LIBDIR, "libmacroaim.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SRC = ["geom.cpp", "fill.cpp", "aim_setup.cpp"]
-CU_SRC = ["kernels.cu", "tc_gemm.cu", "near_tc.cu", "drive.cu", "solver.cu", "post.cu", "capi.cu", "server.cu"]
+CU_SRC = ["kernels.cu", "tc_gemm.cu", "near_tc.cu", "drive.cu", "dense_gpu.cu", "solver.cu", "post.cu", "capi.cu", "server.cu"]
 
 
 def _nvcc() -> str:
@@ -74,7 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     objs = [os.path.join(BUILD, f + ".o") for f in CXX_SRC + CU_SRC]
     tmp = LIB + ".tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-lcublas"])
     os.replace(tmp, LIB)
     with open(stamp, "w") as fh:
         fh.write(dig)

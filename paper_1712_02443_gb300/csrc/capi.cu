@@ -558,7 +558,7 @@ mm_status mm_element_type_create(mm_ctx* ctx, const mm_mesh* scatterer, const mm
   t->tm.em.k = opts->k0;
   t->tm.em.eta0 = opts->eta0 > 0 ? opts->eta0 : 376.730313668;
   t->tm.em.nthreads = ctx->nthreads;
-  mm::build_type(t->tm);
+  mm::build_type(t->tm, ctx->device);
   *out = t.release();
   return MM_OK;
   API_CATCH(ctx)

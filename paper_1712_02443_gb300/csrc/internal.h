@@ -153,7 +153,11 @@ struct TypeModel {
   mutable std::mutex nf_mu;
   mutable std::map<NearBlockKey, std::shared_ptr<const NearBlockData>> nf_cache;
 };
-void build_type(TypeModel& tm);
+// device >= 0: the dense linear algebra of the build on that GPU.
+void build_type(TypeModel& tm, int device = -1);
+bool build_type_dense_gpu(TypeModel& tm, const std::vector<cd>& Lss, const std::vector<cd>& Lse,
+                          const std::vector<cd>& Les, const std::vector<cd>& Lee, const std::vector<cd>& Kse,
+                          int device, std::string& msg);
 
 // ---- host FFT (mixed radix, FP64), used for the Green's spectrum ------------
 void fft_inplace(std::vector<cd>& a, int64_t n, int64_t stride, int64_t count, int64_t dist, int sign);
