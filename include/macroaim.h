@@ -94,9 +94,10 @@ void mm_mesh_destroy(mm_mesh* mesh);
  * (eq. (Tm1)) and the composed block M = T A^-1 B applied in eq.
  * (MV_product1), plus D (Sec. IV).  FP64; computed once per distinct element
  * and shared by every identical element of an array (Sec. III).  The fills
- * run on the host (all context threads); with a device context the dense
- * steps (LU factorisations with partial pivoting, the solves and the
- * products) run on that GPU, on a host-only context on the host.
+ * run on the host (all context threads); with a device context and a
+ * scatterer of at least 1024 RWG functions the dense steps (LU factorisations
+ * with partial pivoting, the solves and the products) run on that GPU,
+ * otherwise on the host.
  * The dual functions of eq. (Ehat_expand) are built on the barycentric
  * refinement of `equiv`.  `equiv` must be closed; k0 > 0.                    */
 typedef struct mm_em_opts {

@@ -356,8 +356,12 @@ static void gemm(const std::vector<cd>& A, const std::vector<cd>& B, std::vector
 // G^(E^,H^) = c L(S^,S^), c = -j w mu0; G^(E,E^) = K(S, S^'),
 // G^(E^,E^) = K_PV(S^, S^') + D/2 (limit from outside the equivalent surface).
 // T = G^(E^,H^)^-1 G^(E^,J) (eq. (Tm1)); A, B of eq. (JM); M = T A^-1 B.
-// The fills run on the host; with device >= 0 the dense steps run on that GPU
-// (build_type_dense_gpu), otherwise on the host.
+// The fills run on the host; with device >= 0 and a large scatterer the dense
+// steps run on that GPU (build_type_dense_gpu), otherwise on the host.
+// Scatterers of at least this many RWG functions take the device path: below
+// it the host's factorisation is as fast as the device's latency-bound panels.
+constexpr int64_t kDenseGpuMinN = 1024;
+
 void build_type(TypeModel& tm, int device) {
   const EM& em = tm.em;
   tm.N = tm.scat.nrwg();
@@ -385,7 +389,7 @@ void build_type(TypeModel& tm, int device) {
   tm.GHE = Kee;
   for (int64_t i = 0; i < Nh * Nh; ++i) tm.GHE[i] += 0.5 * D[i];
   tm.GHH = Lee;
-  if (device >= 0) {
+  if (device >= 0 && N >= kDenseGpuMinN) {
     // the dense steps (LU factorisations, solves, products) on the device
     std::string msg;
     if (!build_type_dense_gpu(tm, Lss, Lse, Les, Lee, Kse, device, msg)) throw Error{MM_ECUDA, msg};

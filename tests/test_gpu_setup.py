@@ -1,9 +1,10 @@
 """Macromodel build with its dense FP64 steps on the GPU (blocked LU with partial
-pivoting, triangular solves, ZGEMM products) against the host build of the same
-element (host-only context): every matrix of the type within 1e-10 relative
-(Frobenius) -- the two differ only in the order of FP64 rounding.  Element
-sizes: the loop (384 scatterer RWG, 288 box RWG), the reduced multiscale
-element (535 / 288) and the full multiscale element (2,547 / 576)."""
+pivoting, triangular solves, ZGEMM products; taken for scatterers of at least
+1024 RWG functions) against the host build of the same element (host-only
+context): every matrix of the type within 1e-10 relative (Frobenius) -- the
+two differ only in the order of FP64 rounding.  Elements: the loop (384
+scatterer RWG, host path on both), the reduced multiscale element (535, host
+path on both) and the full multiscale element (2,547 / 576, device path)."""
 import time
 
 import numpy as np
