@@ -23,18 +23,18 @@
 // (the block's bases are in anchor order).  Persistent kernel: one CTA per SM
 // takes units blockIdx.x, blockIdx.x + gridDim.x, ...; it finds a unit's group
 // by a binary search over the per-group prefix of unit counts, built once in
-// shared memory.  Roles (320 threads):
+// shared memory.  Roles (448 threads):
 //   warp 0     one lane: TMA copies of the A tiles (hi and lo, 128 rows x 32
 //              FP32, 128-byte swizzle) into the stage ring;
 //   warp 1     allocates two accumulators of 2 NC tensor-memory columns; one
 //              lane issues tcgen05.mma kind::tf32 (M 128, N 2 NC, K 8), 12 per
 //              k tile, alternating accumulators from unit to unit so that the
 //              epilogue of one unit overlaps the products of the next;
-//   warps 2-5  gather u for the B tiles: 8-byte cp.async copies of the
+//   warps 2-9  gather u for the B tiles: 8-byte cp.async copies of the
 //              columns' entries (pair offsets and the column type's anchor
 //              order) into a raw ring several k tiles deep, then the split into
 //              hi / lo and the two real rows per column, stored swizzled;
-//   warps 6-9  epilogue: tensor memory -> registers -> the pair's slice of a
+//   warps 10-13 epilogue: tensor memory -> registers -> the pair's slice of a
 //              partial-sum buffer, P_p[c][m] (consecutive lanes store
 //              consecutive rows).
 // A row element has one pair per lattice offset, so the slices never overlap
@@ -64,9 +64,10 @@ using namespace tcx;
 constexpr int kRowsT = 128;                 // block rows per tile (MMA M)
 constexpr int kKT = 16;                     // complex block columns per k tile (32 FP32 = 128 bytes)
 constexpr int kATile = kRowsT * 128;        // bytes of one A tile (hi or lo)
-constexpr int kThreadsNT = 320;             // A copies, MMA, 4 gather warps, 4 epilogue warps
-constexpr int kProd = 128;                  // gather threads (warps 2-5)
-constexpr int kEpi = 128;                   // epilogue threads (warps 6-9)
+constexpr int kThreadsNT = 448;             // A copies, MMA, 8 gather warps, 4 epilogue warps
+constexpr int kProd = 256;                  // gather threads (warps 2-9)
+constexpr int kEpi = 128;                   // epilogue threads (warps 10-13)
+constexpr int kEpiWarp0 = 2 + kProd / 32;   // first epilogue warp
 constexpr int kMaxGroups = 512;             // groups whose unit prefix a CTA keeps in shared memory
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr unsigned long long kDrainNs = 1000000000ull;
@@ -298,8 +299,8 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
       umma_commit(smem_u32(&drain_bar));
       mbar_wait(smem_u32(&drain_bar), 0, nullptr, kDrainNs);
     }
-  } else if (warp < 6) {
-    // ---- gather (warps 2-5, pt = 0..127): u of the units' columns -> B tiles
+  } else if (warp < kEpiWarp0) {
+    // ---- gather (warps 2-9, pt = 0..255): u of the units' columns -> B tiles
     const int pt = threadIdx.x - 64;
     const uint32_t raw0 = smem_u32(rawbuf);
     uint32_t it = 0;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
         const uint32_t r = it / STAGES;
         cp_async_wait<RAWD - 2>();   // this thread's copies of k tile i have landed
         // one thread waits for the stage and tells the others through the named
-        // barrier, so that all 128 take the same branch; two flags alternate, so
+        // barrier, so that all gather threads take the same branch; two flags alternate, so
         // a value is not overwritten before every thread has read it
         if (pt == 0) s_gok[it & 1] = mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop, wait_ns) ? 1 : 0;
         gather_sync();               // everyone's copies landed; slot (i - 1) % RAWD is free again
@@ -387,9 +388,9 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
       atomicExch(&g_near_tc_err, 1);
     }
   } else {
-    // ---- epilogue (warps 6-9): thread = block row m (TMEM lane), the unit's
+    // ---- epilogue (warps 10-13): thread = block row m (TMEM lane), the unit's
     // columns 16 at a time, into the pairs' slices of P
-    const int et = threadIdx.x - 192, qd = warp & 3;
+    const int et = threadIdx.x - 32 * kEpiWarp0, qd = warp & 3;
     uint32_t lt = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
