@@ -215,6 +215,50 @@ def accuracy_measure(ctx) -> dict:
     return out
 
 
+def batch_call_measure(ctx, reps: int = 20) -> dict:
+    """One product call over several arrays of uneven size (mm_apply_batch: each
+    array's product on its own stream) against the same products issued one after
+    another on one stream; complex64, timed with CUDA events after warm-up."""
+    import torch
+    import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
+    from paper_1712_02443_gb300.arrays import loop_array
+    spec = [(8, 1), (12, 4), (16, 8), (24, 16)]
+    arrs, X, Y = [], [], []
+    base = loop_array(ctx, 2, 2, outers=SERVE_OUTERS, config_index=2)
+    for side, r in spec:
+        la = loop_array(ctx, side, side, outers=SERVE_OUTERS, config_index=2, types=base.types)
+        arrs.append(la)
+        X.append(torch.from_numpy(wl.random_cvec(la.n, 5, side, nrhs=r).reshape(-1)).to(torch.complex64).cuda())
+        Y.append(torch.empty_like(X[-1]))
+    st = torch.cuda.current_stream()
+    nr = [r for _, r in spec]
+    hs = [la.array for la in arrs]
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_batch = timed(lambda: mm.mm_apply_batch(hs, nr, X, Y, mm.MM_C64, st))
+    t_seq = timed(lambda: [mm.mm_apply(h, r, x, y, mm.MM_C64, st) for h, r, x, y in zip(hs, nr, X, Y)])
+    tuning = {"%dx%d_r%d" % (side, side, r): mm.mm_array_tuning(la.array, r) for (side, r), la in zip(spec, arrs)}
+    for la in arrs:
+        mm.mm_array_destroy(la.array)
+    base.close()
+    return {"arrays": ["%dx%d, %d RHS" % (side, side, r) for side, r in spec],
+            "columns": int(sum(la.n * r for la, (_, r) in zip(arrs, spec))),
+            "one_call_ms": round(t_batch, 3), "one_after_another_ms": round(t_seq, 3),
+            "speedup": round(t_seq / t_batch, 3), "tuning": tuning}
+
+
 def cufft_measure(info: dict, nrhs: int, ours_ms: float, reps: int = 20) -> dict:
     """The FFT convolution (step ii) with cuFFT through torch.fft, timed only as a
     comparison on the same zero-padded grids: pad the 4 nrhs grids to the FFT
@@ -476,6 +520,7 @@ def run_ours(args, rank, world, local):
         "setup_s": round(setup_s, 2),
         "device": {"sms": sms, "name": torch.cuda.get_device_properties(local).name},
     }
+    out["tuning"] = {"c2_1rhs": mm.mm_array_tuning(la.array, 1)}
     fft_ours = sum(prof[k]["ms"] for k in ("fft_fwd", "fft_conv", "fft_inv")) / max(1, prof["fft_fwd"]["launches"])
     if rank == 0:
         out["cufft_comparison"] = {"c2_1rhs": cufft_measure(info, 1, fft_ours)}
@@ -487,6 +532,8 @@ def run_ours(args, rank, world, local):
         finfo, fours = out["batched"].pop("fft_info", None), out["batched"].pop("fft_ours_ms", None)
         if "cufft_comparison" in out and finfo is not None:
             out["cufft_comparison"]["c3_64rhs"] = cufft_measure(finfo, 64, fours)
+    if rank == 0:
+        out["batch_call"] = batch_call_measure(ctx)
     if rank == 0 and not args.no_accuracy:
         out["accuracy"] = accuracy_measure(ctx)
     if rank == 0 and not args.no_precision_config:
@@ -787,6 +834,7 @@ def batched_measure(ctx, side: int = 32) -> dict:
                      "rel_residual": s["rel_residual"], "gmres_iterations": s["iterations"],
                      "refinements": s["refinements"],
                      "ms_per_iteration": {k: round(v["ms"] / it, 3) for k, v in pr.items() if v["launches"]}}
+    out["tuning_64rhs"] = mm.mm_array_tuning(la.array, 64)
     del flush
     la.close()
     return out

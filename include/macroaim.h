@@ -207,6 +207,15 @@ void mm_array_destroy(mm_array* array);
  * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                    void* stream);
+/* Products of several arrays in one call (arrays of different sizes, element
+ * types and right-hand-side counts): entry i computes y_dev[i] = Z_i x_dev[i]
+ * for arrays[i] with nrhs[i] columns, as mm_apply.  Each array's product runs
+ * on a stream of its own, forked from `stream` and joined back into it, so the
+ * products run concurrently on the device and the call orders like one launch
+ * on `stream`.  Every array appears at most once; all on one device.  The
+ * batch's message on failure is on arrays[0]'s context.                       */
+mm_status mm_apply_batch(mm_array* const* arrays, int32_t count, const int32_t* nrhs, const void* const* x_dev,
+                         void* const* y_dev, int32_t precision, void* stream);
 /* Same operator with host buffers: copies x in, applies, copies y out, and
  * returns after the result is in y_host (synchronous).                       */
 mm_status mm_apply_host(mm_array* array, int32_t nrhs, const void* x_host, void* y_host, int32_t precision);
@@ -345,6 +354,21 @@ mm_status mm_solve_planewave_host(mm_array* array, int32_t nrhs, const double* t
  * product of that width has run (the choice is made on the first one).       */
 mm_status mm_array_near_shape(const mm_array* array, int32_t nrhs, int32_t precision, int32_t* shape,
                               int32_t* ksplit);
+
+/* The launch choices an array made for products of nrhs columns at
+ * `precision` (MM_C64 or MM_C128), -1 where none was made yet:
+ * choices[0], [1]: block near-field shape and k split (mm_array_near_shape);
+ * choices[2]: projection schedule, choices[3]: interpolation schedule, chosen
+ * on the array's first product of that width by timing each variant with CUDA
+ * events (projection with one right-hand side: 4, 2 or 1 lanes per stencil-box
+ * node for variants 0-2; several: four or one right-hand side per pass;
+ * interpolation with one right-hand side: 4, 2 or 1 lanes per basis; eight or
+ * more: eight or one right-hand side per thread).  project_ms, interp_ms (3
+ * floats each, may be NULL): the timed variants' times, -1 where not timed.
+ * MACROAIM_GRID_TUNE=0 (read when the array is created) keeps variant 0
+ * without timing.  MM_EINVAL before any product of that width.              */
+mm_status mm_array_tuning(const mm_array* array, int32_t nrhs, int32_t precision, int32_t* choices,
+                          float* project_ms, float* interp_ms);
 
 /* ------------------------------------------------- allocation-free product
  * The same product as mm_apply, for callers that cannot allocate device

@@ -112,6 +112,8 @@ _SIGS = {
     "mm_solve_planewave_host": (ct.c_int, [P, ct.c_int32, P, P, P, P, ct.POINTER(mm_solve_opts),
                                            ct.POINTER(mm_solve_stats)]),
     "mm_type_set_feed": (ct.c_int, [P, ct.c_int32, P, P]),
+    "mm_apply_batch": (ct.c_int, [P, ct.c_int32, P, P, P, ct.c_int32, P]),
+    "mm_array_tuning": (ct.c_int, [P, ct.c_int32, ct.c_int32, P, P, P]),
     "mm_rhs_deltagap": (ct.c_int, [P, ct.c_int32, P, P, P]),
     "mm_currents_fed": (ct.c_int, [P, ct.c_int32, P, P, P, P, P]),
     "mm_rhs_planewave_ground": (ct.c_int, [P, ct.c_int32, P, P, P, ct.c_double, P, ct.c_int32, P]),
@@ -287,6 +289,16 @@ def mm_apply(array, nrhs: int, x_dev, y_dev, precision: int, stream=None) -> Non
            _ctx_of.get(array.value))
 
 
+def mm_apply_batch(arrays, nrhs, xs, ys, precision: int, stream=None) -> None:
+    """Products of several arrays in one call; entry i: ys[i] = Z_i xs[i] with nrhs[i] columns."""
+    n = len(arrays)
+    ar = (ct.c_void_p * n)(*[a.value for a in arrays])
+    nr = np.ascontiguousarray(nrhs, dtype=np.int32)
+    xp = (ct.c_void_p * n)(*[_ptr(x) for x in xs])
+    yp = (ct.c_void_p * n)(*[_ptr(y) for y in ys])
+    _check(load().mm_apply_batch(ar, n, _ptr(nr), xp, yp, precision, _stream(stream)), _ctx_of.get(arrays[0].value))
+
+
 def mm_apply_noalloc(array, nrhs: int, x_dev, y_dev, precision: int, stream=None) -> None:
     """mm_apply without any device allocation (shared static scratch of at most 16 MiB)."""
     _check(load().mm_apply_noalloc(array, nrhs, _ptr(x_dev), _ptr(y_dev), precision, _stream(stream)),
@@ -397,6 +409,19 @@ def mm_array_near_shape(array, nrhs: int, precision: int = MM_C64):
     sh, ks = ct.c_int32(), ct.c_int32()
     st = load().mm_array_near_shape(array, nrhs, precision, ct.byref(sh), ct.byref(ks))
     return (sh.value, ks.value) if st == MM_OK else None
+
+
+def mm_array_tuning(array, nrhs: int, precision: int = MM_C64):
+    """The array's launch choices for nrhs columns (near shape, k split, projection and
+    interpolation schedules) and the grid tuner's timings, or None before the first product."""
+    ch = np.zeros(4, dtype=np.int32)
+    pm = np.zeros(3, dtype=np.float32)
+    im = np.zeros(3, dtype=np.float32)
+    st = load().mm_array_tuning(array, nrhs, precision, _ptr(ch), _ptr(pm), _ptr(im))
+    if st != MM_OK:
+        return None
+    return {"near_shape": int(ch[0]), "near_ksplit": int(ch[1]), "project": int(ch[2]), "interp": int(ch[3]),
+            "project_ms": [float(x) for x in pm if x >= 0], "interp_ms": [float(x) for x in im if x >= 0]}
 
 
 def mm_profile_enable(array, enable: bool = True) -> None:

@@ -80,6 +80,8 @@ struct mm_array {
   size_t pw2_cap = 0;
   double* d_gc = nullptr;            // ground plane: per right-hand side factor of the image wave
   int gc_cap = 0;
+  cudaStream_t bst = nullptr;        // mm_apply_batch: this array's product stream and its event
+  cudaEvent_t bev_done = nullptr, bev_fork = nullptr;
   void* pv_V = nullptr;              // mm_solve_planewave_host: excitation and solution on the device
   void* pv_E = nullptr;
   size_t pv_cap = 0;
@@ -475,6 +477,9 @@ mm_array::~mm_array() {
     if (q) cudaFree(q);
   for (void* q : {d_volts, d_fu, d_pw2, (void*)d_gc})
     if (q) cudaFree(q);
+  if (bst) cudaStreamDestroy(bst);
+  for (cudaEvent_t e : {bev_done, bev_fork})
+    if (e) cudaEventDestroy(e);
   if (pv_V) cudaFree(pv_V);
   if (pv_E) cudaFree(pv_E);
   if (da.tbase) cudaFree(da.tbase);
@@ -906,6 +911,17 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         }
       }
     }
+    // tuning override: MACROAIM_GRID_TUNE=0 keeps the grid stages' default schedules
+    if (const char* gt = std::getenv("MACROAIM_GRID_TUNE"))
+      if (std::string(gt) == "0") da.tune_grid = false;
+    // tuning override: MACROAIM_GRID_SCHED="p,i" fixes the projection and interpolation variants
+    if (const char* gs = std::getenv("MACROAIM_GRID_SCHED")) {
+      int gp = -1, gi = -1;
+      if (std::sscanf(gs, "%d,%d", &gp, &gi) == 2 && gp >= 0 && gp <= 2 && gi >= 0 && gi <= 2) {
+        da.grid_force_p = gp;
+        da.grid_force_i = gi;
+      }
+    }
     upload_precision<float>(a.get(), da.pf);
     CU(mm::kernels_init(da));
     // the near field's own stream (MACROAIM_NEAR_OVERLAP=0: one stream, in order)
@@ -1048,6 +1064,45 @@ mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, in
     return fail(ctx, MM_EINVAL, "unknown precision");
   }
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("matvec: ") + cudaGetErrorString(e));
+  return MM_OK;
+  API_CATCH(ctx)
+}
+
+mm_status mm_apply_batch(mm_array* const* arrays, int32_t count, const int32_t* nrhs, const void* const* x_dev,
+                         void* const* y_dev, int32_t precision, void* stream) {
+  if (!arrays || count < 1 || !nrhs || !x_dev || !y_dev) return MM_EINVAL;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!arrays[i] || !arrays[i]->on_device || nrhs[i] < 1 || !x_dev[i] || !y_dev[i] || x_dev[i] == y_dev[i])
+      return arrays[i] ? fail(arrays[i]->ctx, MM_EINVAL, "invalid batch entry " + std::to_string(i)) : MM_EINVAL;
+    for (int32_t j = 0; j < i; ++j)
+      if (arrays[j] == arrays[i])
+        return fail(arrays[i]->ctx, MM_EINVAL, "an array appears twice in the batch (it serves one product at a time)");
+    if (arrays[i]->da.device != arrays[0]->da.device)
+      return fail(arrays[i]->ctx, MM_EINVAL, "the arrays of a batch must be on one device");
+  }
+  mm_ctx* ctx = arrays[0]->ctx;
+  API_TRY
+  CU(cudaSetDevice(arrays[0]->da.device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // fork: every array's product on its own stream, after the caller's work
+  if (!arrays[0]->bev_fork) CU(cudaEventCreateWithFlags(&arrays[0]->bev_fork, cudaEventDisableTiming));
+  CU(cudaEventRecord(arrays[0]->bev_fork, st));
+  for (int32_t i = 0; i < count; ++i) {
+    mm_array* a = arrays[i];
+    if (!a->bst) {
+      CU(cudaStreamCreateWithFlags(&a->bst, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&a->bev_done, cudaEventDisableTiming));
+    }
+    CU(cudaStreamWaitEvent(a->bst, arrays[0]->bev_fork, 0));
+    const mm_status s = mm_apply(a, nrhs[i], x_dev[i], y_dev[i], precision, a->bst);
+    if (s != MM_OK) {
+      if (a != arrays[0]) ctx->err = a->ctx->err;
+      return s;
+    }
+    CU(cudaEventRecord(a->bev_done, a->bst));
+  }
+  // join: the caller's stream waits for every product
+  for (int32_t i = 0; i < count; ++i) CU(cudaStreamWaitEvent(st, arrays[i]->bev_done, 0));
   return MM_OK;
   API_CATCH(ctx)
 }
@@ -1259,6 +1314,29 @@ mm_status mm_solve_planewave_host(mm_array* a, int32_t nrhs, const double* theta
   if (s == MM_ENOCONV) return fail(ctx, s, msg);
   return MM_OK;
   API_CATCH(ctx)
+}
+
+mm_status mm_array_tuning(const mm_array* a, int32_t nrhs, int32_t precision, int32_t* choices, float* project_ms,
+                          float* interp_ms) {
+  if (!a || !choices || nrhs < 1) return MM_EINVAL;
+  if (precision != MM_C64 && precision != MM_C128) return MM_EINVAL;
+  const auto key = std::make_pair((int)nrhs, precision == MM_C128 ? 8 : 4);
+  const auto nt = a->da.near_tune.find(key);
+  const auto gt = a->da.grid_tune.find(key);
+  if (nt == a->da.near_tune.end() && gt == a->da.grid_tune.end()) return MM_EINVAL;
+  choices[0] = nt != a->da.near_tune.end() ? nt->second.first : -1;
+  choices[1] = nt != a->da.near_tune.end() ? nt->second.second : -1;
+  choices[2] = gt != a->da.grid_tune.end() ? gt->second.project : -1;
+  choices[3] = gt != a->da.grid_tune.end() ? gt->second.interp : -1;
+  for (int i = 0; i < 3; ++i) {
+    if (project_ms)
+      project_ms[i] = gt != a->da.grid_tune.end() && i < (int)gt->second.project_ms.size() ? gt->second.project_ms[i]
+                                                                                          : -1.f;
+    if (interp_ms)
+      interp_ms[i] = gt != a->da.grid_tune.end() && i < (int)gt->second.interp_ms.size() ? gt->second.interp_ms[i]
+                                                                                        : -1.f;
+  }
+  return MM_OK;
 }
 
 mm_status mm_array_near_shape(const mm_array* a, int32_t nrhs, int32_t precision, int32_t* shape,

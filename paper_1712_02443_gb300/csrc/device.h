@@ -127,6 +127,13 @@ struct Work {
   size_t bytes = 0;
 };
 
+// Grid-stage tuner's choice for one (right-hand-side count, precision): the
+// projection and interpolation variants and the times of every variant (ms).
+struct GridTune {
+  int project = 0, interp = 0;
+  std::vector<float> project_ms, interp_ms;
+};
+
 struct DevArray {
   int device = 0;
   int64_t N = 0, n_elem = 0, n_types = 0, nnz = 0;
@@ -193,6 +200,9 @@ struct DevArray {
   // autotuned block near-field shape per (right-hand sides, sizeof(R)): (kernel shape, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
   int near_force_shape = -1, near_force_ks = 1;   // MACROAIM_NEAR_SHAPE="shape,ksplit": no tuning
+  std::map<std::pair<int, int>, GridTune> grid_tune;   // per (right-hand sides, sizeof(R))
+  bool tune_grid = true;                           // MACROAIM_GRID_TUNE=0: variant 0, no timing
+  int grid_force_p = -1, grid_force_i = -1;        // MACROAIM_GRID_SCHED="p,i": fixed variants
   // streams of the product: the near field runs on `side` beside the far-field
   // chain (projection, convolution, interpolation) on `chain`, which has the
   // higher priority; fork / join events order both against the caller's stream

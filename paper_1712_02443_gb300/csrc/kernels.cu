@@ -28,6 +28,7 @@
 // (batch b = psi * nrhs + j); partial spectra [b][x][ky][kz]; Green's spectrum
 // [ky][kz][kx].
 #include <cstdio>
+#include <functional>
 
 #include "device.h"
 #include "near_tc.h"
@@ -1437,6 +1438,120 @@ cudaError_t kernels_init(DevArray& a) {
   return near_tc_init(a);
 }
 
+// Launch schedules of the projection and the interpolation (the grid-stage
+// tuner's choices).  Projection, one right-hand side: variant v gives 4 >> v
+// lanes per stencil-box node (4, 2, 1; CTAs of up to 512 threads); several:
+// variant 0 stages four right-hand sides per pass (RC = 4), variant 1 one.
+// Interpolation, one right-hand side: 4 >> v lanes per basis; eight or more:
+// variant 0 takes eight right-hand sides per thread (CR = 8), variant 1 one.
+template <typename R>
+static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
+                           typename V2<R>::T* grid, cudaStream_t cs, int& nl) {
+  typedef typename V2<R>::T C;
+  const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
+    const int pnodes = bx * by * bz;
+    if (nrhs == 1 || var == 1) {
+      // T lanes per node with T nodes <= 512 (two CTAs fit on an SM: one wave)
+      int pT = nrhs == 1 ? (4 >> var) : 1;
+      while (pT > 1 && pT * pnodes > 512) pT >>= 1;
+      const int pthreads = std::min(512, (pT * pnodes + 31) / 32 * 32);
+      k_project<R, 1><<<(unsigned)a.n_of_type[t], std::max(256, pthreads), sizeof(C) * Nh, cs>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+    } else {
+      k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+    }
+    ++nl;
+  }
+}
+
+template <typename R>
+static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* grid,
+                          const typename V2<R>::T* v, typename V2<R>::T* y, cudaStream_t cs, int& nl) {
+  typedef typename V2<R>::T C;
+  const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
+  const size_t slim = 96 * 1024;
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
+    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+    const size_t sm = 4 * rc * nodes * sizeof(C) + sizeof(int) * (size_t)a.S;   // box + stencil offsets
+    // T lanes per basis with T N^_t <= 576 (512 for FP64): two CTAs per SM
+    const int icap = sizeof(R) == 4 ? 576 : 512;
+    int iT = 4 >> (nrhs == 1 ? var : 0);
+    while (iT > 1 && iT * a.Nh[t] > icap) iT >>= 1;
+    const int ithreads = std::min(icap, (int)((iT * a.Nh[t] + 31) / 32 * 32));
+    if (rc >= 8 && var == 0)
+      k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
+          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
+          y);
+    else
+      k_interp<R, 1><<<(unsigned)a.n_of_type[t], nrhs == 1 ? std::max(256, ithreads) : 256, sm, cs>>>(
+          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
+          y);
+    ++nl;
+  }
+}
+
+// Grid-stage tuner: on an array's first product for a right-hand-side count and
+// precision, each projection and each interpolation variant is timed with CUDA
+// events (one warm-up and one timed launch, into the product's own grid and
+// into the idle spectrum buffer as y); the fastest of each is kept, with the
+// times, for the array.  Without a large enough spectrum buffer variant 0 is used.
+template <typename R>
+static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int nrhs, Work& w, cudaStream_t st) {
+  typedef typename V2<R>::T C;
+  const int np = nrhs == 1 ? 3 : 2, ni = nrhs == 1 ? 3 : 2;
+  std::pair<int, int> best = {0, 0};
+  const size_t spec_elems = (size_t)4 * nrhs * a.grid[0] * a.fft[1] * a.fft[2];
+  if (spec_elems < (size_t)a.N * nrhs) return best;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return best;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return best;
+  }
+  std::vector<float> tp(np, -1.f), ti(ni, -1.f);
+  C* grid = static_cast<C*>(w.grid);
+  const C* u = static_cast<const C*>(w.u);
+  const C* v = static_cast<const C*>(w.v);
+  C* yscr = static_cast<C*>(w.spec);
+  auto timeit = [&](const std::function<void()>& run) -> float {
+    run();
+    cudaEventRecord(e0, st);
+    run();
+    cudaEventRecord(e1, st);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.f;
+    return ms;
+  };
+  for (int var = 0; var < np; ++var) {
+    int nl = 0;
+    tp[var] = timeit([&] { project_launch<R>(var, a, p, nrhs, u, grid, st, nl); });
+    if (tp[var] >= 0 && (tp[best.first] < 0 || tp[var] < tp[best.first])) best.first = var;
+  }
+  for (int var = 0; var < ni; ++var) {
+    int nl = 0;
+    ti[var] = timeit([&] { interp_launch<R>(var, a, p, nrhs, grid, v, yscr, st, nl); });
+    if (ti[var] >= 0 && (ti[best.second] < 0 || ti[var] < ti[best.second])) best.second = var;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GridTune g;
+  g.project = best.first;
+  g.interp = best.second;
+  g.project_ms = tp;
+  g.interp_ms = ti;
+  a.grid_tune[std::make_pair(nrhs, (int)sizeof(R))] = g;
+  return best;
+}
+
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st,
                    int gemm_mode, bool pre, unsigned flags) {
@@ -1451,6 +1566,19 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   const int Px = a.fft[0], Py = a.fft[1], Pz = a.fft[2];
   const int B = 4 * nrhs;
   const size_t gbytes = sizeof(C) * (size_t)B * Nx * Ny * Nz;
+  // launch schedules of the projection and the interpolation (tuned once per
+  // right-hand-side count and precision; the size rule's variant 0 otherwise)
+  std::pair<int, int> gv = {0, 0};
+  {
+    const auto gk = std::make_pair(nrhs, (int)sizeof(R));
+    const auto gt = a.grid_tune.find(gk);
+    if (a.grid_force_p >= 0)
+      gv = {a.grid_force_p, a.grid_force_i};
+    else if (gt != a.grid_tune.end())
+      gv = {gt->second.project, gt->second.interp};
+    else if (!(flags & kMvNoTune) && a.tune_grid)
+      gv = grid_autotune<R>(a, p, nrhs, w, st);
+  }
   cudaError_t e = cudaMemsetAsync(grid, 0, gbytes, st);
   if (e != cudaSuccess) return e;
   Profiler off;   // stays disabled: records nothing, creates no events
@@ -1559,23 +1687,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A2: projection
   pr.begin(sb + 1, cs);
   nl = 0;
-  for (int64_t t = 0; t < a.n_types; ++t) {
-    if (a.n_of_type[t] == 0) continue;
-    const int Nh = (int)a.Nh[t];
-    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
-    // one right-hand side: up to four threads per box node (more CTA threads)
-    // T lanes per node with T nodes <= 512, so that two CTAs fit on an SM (one wave)
-    const int pnodes = bx * by * bz;
-    const int pT = 4 * pnodes <= 512 ? 4 : (2 * pnodes <= 512 ? 2 : 1);
-    const int pthreads = std::min(512, (pT * pnodes + 31) / 32 * 32);
-    if (nrhs == 1)
-      k_project<R, 1><<<(unsigned)a.n_of_type[t], std::max(256, pthreads), sizeof(C) * Nh, cs>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
-    else
-      k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
-    ++nl;
-  }
+  project_launch<R>(gv.first, a, p, nrhs, u, grid, cs, nl);
   pr.end(cs, nl);
   // A5 on its stream, launched after the projection so that the chain's first
   // kernel is dispatched ahead of it
@@ -1610,7 +1722,6 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     e = cudaEventRecord(a.ev_join, ns);
     if (e != cudaSuccess) return e;
   }
-  const size_t slim = 96 * 1024;
   // A3: FFT convolution
   pr.begin(sb + 2, cs);
   k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
@@ -1632,28 +1743,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A4: interpolation, y = v - y_ff
   pr.begin(sb + 5, cs);
   nl = 0;
-  for (int64_t t = 0; t < a.n_types; ++t) {
-    if (a.n_of_type[t] == 0) continue;
-    const int rc = box_rc(a, (int)t, nrhs, sizeof(C), slim);
-    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
-    const size_t sm = 4 * rc * nodes * sizeof(C) + sizeof(int) * (size_t)a.S;   // box + stencil offsets
-    // one right-hand side: up to four threads per basis (more CTA threads)
-    // T lanes per basis with T N^_t <= 576 (512 for FP64): two CTAs per SM
-    const int icap = sizeof(R) == 4 ? 576 : 512;
-    const int iT = 4 * a.Nh[t] <= icap ? 4 : (2 * a.Nh[t] <= icap ? 2 : 1);
-    const int ithreads = std::min(icap, (int)((iT * a.Nh[t] + 31) / 32 * 32));
-    if (rc >= 8)
-      k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
-          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
-          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
-          y);
-    else
-      k_interp<R, 1><<<(unsigned)a.n_of_type[t], nrhs == 1 ? std::max(256, ithreads) : 256, sm, cs>>>(
-          a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
-          p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
-          y);
-    ++nl;
-  }
+  interp_launch<R>(gv.second, a, p, nrhs, grid, v, y, cs, nl);
   pr.end(cs, nl);
   if (cs != st) {
     e = cudaEventRecord(a.ev_done, cs);
