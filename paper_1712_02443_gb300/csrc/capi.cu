@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <cstdio>
@@ -389,7 +390,7 @@ template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
-  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np, w.boxbuf})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -404,6 +405,12 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (sizeof(R) == 8 && da.nnz > 0) {
     CU(cudaMalloc(&w.us, sizeof(double) * (size_t)da.N * nrhs));
     w.bytes += sizeof(double) * (size_t)da.N * nrhs;
+  }
+  if (nrhs >= 8 && da.gptr) {
+    // the two-pass projection's per-element boxes (a tuner variant from 8 RHS on)
+    const size_t bb = sizeof(C) * (size_t)da.n_elem * 4 * nrhs * da.box_nodes_max;
+    CU(cudaMalloc(&w.boxbuf, bb));
+    w.bytes += bb;
   }
   if (sizeof(R) == 4 && da.pf.nfb_tc && da.nfg_prows > 0) {
     CU(cudaMalloc(&w.np, sizeof(float2) * (size_t)da.nfg_prows * nrhs));
@@ -445,13 +452,15 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us, w->np})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us, w->np, w->boxbuf})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
   for (auto* p : da.elems) cudaFree(p);
   for (auto* p : da.inv_ptr) cudaFree(p);
   for (auto* p : da.inv_ent) cudaFree(p);
+  for (void* q : {(void*)da.gptr, (void*)da.gent})
+    if (q) cudaFree(q);
   for (void* q : {(void*)da.off, (void*)da.boxorg, (void*)da.type_of, (void*)da.eoff, (void*)da.rowptr,
                   (void*)da.col, (void*)elem_of, (void*)geo_ptrs, (void*)d_ang, (void*)d_pol, hx, hy, (void*)d_offs,
                   (void*)d_dir})
@@ -729,6 +738,59 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
       eoff[3 * e] = offs[e].x; eoff[3 * e + 1] = offs[e].y; eoff[3 * e + 2] = offs[e].z;
     }
     da.boxorg = dev_upload(boxorg.data(), boxorg.size(), acc);
+    {
+      // the two-pass projection's gather lists: per grid node, the (element,
+      // local box node) pairs whose box covers it, for box nodes that receive
+      // a projection weight
+      int nmax = 1;
+      std::vector<std::vector<char>> live(da.n_types);
+      for (int64_t t = 0; t < da.n_types; ++t) {
+        const auto& ta = ah.tai[t];
+        const int nodes = (int)(ta.box_dim[0] * ta.box_dim[1] * ta.box_dim[2]);
+        nmax = std::max(nmax, nodes);
+        live[t].assign(nodes, 0);
+      }
+      {
+        // a node is live if some (basis, stencil point) of the type lands on it
+        for (int64_t t = 0; t < da.n_types; ++t) {
+          const auto& ta = ah.tai[t];
+          const int by = (int)ta.box_dim[1], bz = (int)ta.box_dim[2], n1 = da.n1;
+          for (int64_t n = 0; n < ta.Nh; ++n)
+            for (int sn = 0; sn < da.S; ++sn) {
+              const int ix = sn % n1, iy = (sn / n1) % n1, iz = sn / (n1 * n1);
+              const int x = (int)(ta.anc[3 * n] - ta.box_lo[0]) + da.o1lo + ix;
+              const int y = (int)(ta.anc[3 * n + 1] - ta.box_lo[1]) + da.o1lo + iy;
+              const int z = (int)(ta.anc[3 * n + 2] - ta.box_lo[2]) + da.o1lo + iz;
+              live[t][(x * by + y) * bz + z] = 1;
+            }
+        }
+      }
+      const int64_t Ny = ah.grid[1], Nz = ah.grid[2], ng = ah.grid[0] * Ny * Nz;
+      std::vector<int32_t> cnt(ng + 1, 0);
+      auto each = [&](const std::function<void(int64_t, int64_t)>& f) {
+        for (int64_t e = 0; e < n_elem; ++e) {
+          const int t = type_of[e];
+          const auto& ta = ah.tai[t];
+          const int bx = (int)ta.box_dim[0], by = (int)ta.box_dim[1], bz = (int)ta.box_dim[2];
+          for (int lx = 0; lx < bx; ++lx)
+            for (int ly = 0; ly < by; ++ly)
+              for (int lz = 0; lz < bz; ++lz) {
+                const int node = (lx * by + ly) * bz + lz;
+                if (!live[t][node]) continue;
+                const int64_t g = ((boxorg[3 * e] + lx) * Ny + (boxorg[3 * e + 1] + ly)) * Nz + boxorg[3 * e + 2] + lz;
+                f(g, e * nmax + node);
+              }
+        }
+      };
+      each([&](int64_t g, int64_t) { ++cnt[g + 1]; });
+      for (int64_t g = 0; g < ng; ++g) cnt[g + 1] += cnt[g];
+      std::vector<int64_t> ent(cnt[ng]);
+      std::vector<int32_t> fillp(cnt.begin(), cnt.end() - 1);
+      each([&](int64_t g, int64_t v) { ent[fillp[g]++] = v; });
+      da.box_nodes_max = nmax;
+      da.gptr = dev_upload(cnt.data(), cnt.size(), acc);
+      da.gent = dev_upload(ent.data(), ent.size(), acc);
+    }
     da.type_of = dev_upload(type_of.data(), type_of.size(), acc);
     da.eoff = dev_upload(eoff.data(), eoff.size(), acc);
     std::vector<int32_t> eof(ah.N);
@@ -974,7 +1036,8 @@ mm_status mm_array_footprint(const mm_array* a, int32_t nrhs, int32_t precision,
   size_t kry = 16 * (size_t)da.N * nrhs * (restart + 4) + 16 * (size_t)da.N * nrhs;
   // partial sums of the tensor-core near field (complex64 products)
   size_t np = da.pf.nfb_tc ? sizeof(float) * 2 * (size_t)da.nfg_prows * nrhs : 0;
-  *bytes = 2 * vec + g + s + kry + np;
+  size_t bb = nrhs >= 8 ? cs * (size_t)da.n_elem * 4 * nrhs * da.box_nodes_max : 0;   // two-pass projection
+  *bytes = 2 * vec + g + s + kry + np + bb;
   return MM_OK;
 }
 

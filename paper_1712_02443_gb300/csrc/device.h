@@ -124,6 +124,7 @@ struct Work {
   void* pt = nullptr;     // N x nrhs   preconditioned vector (block-Jacobi)
   double* us = nullptr;   // N x nrhs   FP64 only: Re u + Im u for the three-product near field
   void* np = nullptr;     // complex64 only: partial sums of the tensor-core near field (nfg_prows x nrhs)
+  void* boxbuf = nullptr; // from 8 RHS on: per-element projection boxes (n_elem x 4 nrhs x box_nodes_max)
   size_t bytes = 0;
 };
 
@@ -153,6 +154,9 @@ struct DevArray {
   int64_t* off = nullptr;               // n_elem + 1
   int64_t* tbase = nullptr;             // n_types + 1: prefix of the types' N^_t (local bases of all types)
   int32_t* boxorg = nullptr;            // n_elem x 3: global grid coordinates of the type box origin
+  int box_nodes_max = 1;                // largest stencil box (nodes) over the types
+  int32_t* gptr = nullptr;              // grid nodes + 1: the two-pass projection's gather lists ...
+  int64_t* gent = nullptr;              // ... entries element * box_nodes_max + local node
   int32_t* type_of = nullptr;
   double* eoff = nullptr;               // n_elem x 3 element offsets
   // near field pattern (shared by both precisions)

@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 8
                                                  const int32_t* __restrict__ inv_ent, const R* __restrict__ Pi,
                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ boxorg,
                                                  int nrhs, const typename V2<R>::T* __restrict__ u, int Nx, int Ny,
-                                                 int Nz, typename V2<R>::T* __restrict__ grid) {
+                                                 int Nz, typename V2<R>::T* __restrict__ grid,
+                                                 typename V2<R>::T* __restrict__ boxbuf, int nodes_max) {
   typedef typename V2<R>::T C;
   extern __shared__ unsigned char smem_raw[];
   C* us = reinterpret_cast<C*>(smem_raw);  // [n][c] element's u for this RHS chunk
@@ -438,10 +439,37 @@ __global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 8
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int c = 0; c < RC; ++c)
-          if (c < cn) atomic_add_c(grid + ((int64_t)q * nrhs + c0 + c) * gstride + gidx, acc[q][c]);
+          if (c < cn) {
+            if (boxbuf)   // two-pass form: the element's own box, plain stores
+              boxbuf[(((int64_t)e * 4 + q) * nrhs + c0 + c) * nodes_max + node] = acc[q][c];
+            else
+              atomic_add_c(grid + ((int64_t)q * nrhs + c0 + c) * gstride + gidx, acc[q][c]);
+          }
     }
     __syncthreads();
   }
+}
+
+// Second pass of the two-pass projection: every grid point (plane b = psi
+// nrhs + c, node g) sums the boxes of the elements whose stencil box covers g
+// (per node the list of (element, local node), gptr / gent, fixed at set-up);
+// no atomics, and every point is written (the grid needs no clearing).
+template <typename C>
+__global__ void __launch_bounds__(256) k_grid_gather(int64_t ng, int B, const int32_t* __restrict__ gptr,
+                                                     const int64_t* __restrict__ gent, const C* __restrict__ boxbuf,
+                                                     int nodes_max, int nrhs, C* __restrict__ grid) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ng * B) return;
+  const int64_t g = t % ng, b = t / ng;
+  C acc = czero<C>();
+  for (int k = gptr[g]; k < gptr[g + 1]; ++k) {
+    const int64_t ent = gent[k];   // element * nodes_max + local node
+    const int64_t e = ent / nodes_max, ln = ent - e * nodes_max;
+    const C v = boxbuf[((e * 4) * nrhs + b) * nodes_max + ln];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  grid[t] = acc;
 }
 
 // ---------------------------------------------------------------- A3: FFT convolution (step ii)
@@ -1441,12 +1469,15 @@ cudaError_t kernels_init(DevArray& a) {
 // Launch schedules of the projection and the interpolation (the grid-stage
 // tuner's choices).  Projection, one right-hand side: variant v gives 4 >> v
 // lanes per stencil-box node (4, 2, 1; CTAs of up to 512 threads); several:
-// variant 0 stages four right-hand sides per pass (RC = 4), variant 1 one.
+// variant 0 stages four right-hand sides per pass (RC = 4), variant 1 one,
+// variant 2 (eight or more, when the array has a box buffer) is the two-pass
+// form: each element writes its box, then every grid point sums the boxes
+// covering it (no atomics).
 // Interpolation, one right-hand side: 4 >> v lanes per basis; eight or more:
 // variant 0 takes eight right-hand sides per thread (CR = 8), variant 1 one.
 template <typename R>
 static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
-                           typename V2<R>::T* grid, cudaStream_t cs, int& nl) {
+                           typename V2<R>::T* grid, void* boxbuf, cudaStream_t cs, int& nl) {
   typedef typename V2<R>::T C;
   const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
   for (int64_t t = 0; t < a.n_types; ++t) {
@@ -1460,11 +1491,20 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
       while (pT > 1 && pT * pnodes > 512) pT >>= 1;
       const int pthreads = std::min(512, (pT * pnodes + 31) / 32 * 32);
       k_project<R, 1><<<(unsigned)a.n_of_type[t], std::max(256, pthreads), sizeof(C) * Nh, cs>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid,
+          nullptr, 0);
     } else {
       k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
-          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+          a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid,
+          var == 2 ? static_cast<C*>(boxbuf) : nullptr, a.box_nodes_max);
     }
+    ++nl;
+  }
+  if (var == 2 && nrhs > 1) {
+    const int64_t ng = (int64_t)Nx * Ny * Nz, items = ng * 4 * nrhs;
+    k_grid_gather<C><<<(unsigned)((items + 255) / 256), 256, 0, cs>>>(ng, 4 * nrhs, a.gptr, a.gent,
+                                                                      static_cast<const C*>(boxbuf),
+                                                                      a.box_nodes_max, nrhs, grid);
     ++nl;
   }
 }
@@ -1507,7 +1547,7 @@ static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int n
 template <typename R>
 static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int nrhs, Work& w, cudaStream_t st) {
   typedef typename V2<R>::T C;
-  const int np = nrhs == 1 ? 3 : 2, ni = nrhs == 1 ? 3 : 2;
+  const int np = nrhs == 1 ? 3 : (w.boxbuf != nullptr ? 3 : 2), ni = nrhs == 1 ? 3 : 2;
   std::pair<int, int> best = {0, 0};
   const size_t spec_elems = (size_t)4 * nrhs * a.grid[0] * a.fft[1] * a.fft[2];
   if (spec_elems < (size_t)a.N * nrhs) return best;
@@ -1533,7 +1573,7 @@ static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int n
   };
   for (int var = 0; var < np; ++var) {
     int nl = 0;
-    tp[var] = timeit([&] { project_launch<R>(var, a, p, nrhs, u, grid, st, nl); });
+    tp[var] = timeit([&] { project_launch<R>(var, a, p, nrhs, u, grid, w.boxbuf, st, nl); });
     if (tp[var] >= 0 && (tp[best.first] < 0 || tp[var] < tp[best.first])) best.first = var;
   }
   for (int var = 0; var < ni; ++var) {
@@ -1579,7 +1619,9 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     else if (!(flags & kMvNoTune) && a.tune_grid)
       gv = grid_autotune<R>(a, p, nrhs, w, st);
   }
-  cudaError_t e = cudaMemsetAsync(grid, 0, gbytes, st);
+  // the two-pass projection writes every grid point; the atomic forms add into a cleared grid
+  const bool two_pass = gv.first == 2 && w.boxbuf != nullptr && nrhs > 1;
+  cudaError_t e = two_pass ? cudaSuccess : cudaMemsetAsync(grid, 0, gbytes, st);
   if (e != cudaSuccess) return e;
   Profiler off;   // stays disabled: records nothing, creates no events
   Profiler& pr = (flags & kMvNoProfile) ? off : a.prof;
@@ -1687,7 +1729,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A2: projection
   pr.begin(sb + 1, cs);
   nl = 0;
-  project_launch<R>(gv.first, a, p, nrhs, u, grid, cs, nl);
+  project_launch<R>(gv.first == 2 && !w.boxbuf ? 0 : gv.first, a, p, nrhs, u, grid, w.boxbuf, cs, nl);
   pr.end(cs, nl);
   // A5 on its stream, launched after the projection so that the chain's first
   // kernel is dispatched ahead of it

@@ -99,7 +99,7 @@ def test_every_grid_schedule_one_rhs(ctx, monkeypatch, sched):
         la.close()
 
 
-@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0"])
+@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0", "2,0", "2,1"])
 @pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C128])
 def test_every_grid_schedule_64_rhs(ctx, monkeypatch, sched, prec):
     monkeypatch.setenv("MACROAIM_GRID_SCHED", sched)
