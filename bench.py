@@ -383,6 +383,20 @@ def run_ours(args, rank, world, local):
         t_ms = float(tt.item())
     solves_per_s = world * args.steps / (t_ms / 1e3)
     matvecs_per_s = world * matvecs / (t_ms / 1e3)
+    if args.headline_only:
+        # the timed mixed-precision steps alone (for a launch list of exactly them)
+        if rank == 0:
+            print(json.dumps({"metric": "macromodel-AIM matvecs/s (timed steps only)", "value": round(matvecs_per_s, 1),
+                              "unit": "matvecs/s", "solves_per_s": round(solves_per_s, 2), "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3),
+                              "matvecs_per_solve": round(matvecs / args.steps, 1),
+                              "stages": {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"]}
+                                         for k, v in prof.items()},
+                              "tuning": mm.mm_array_tuning(la.array, 1)}))
+        mm.mm_array_destroy(la.array)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     # ---- plain FP64 GPU form (complex128 operator, FP64 GMRES, no refinement)
     k64 = max(3, min(args.steps, 5))
@@ -929,6 +943,8 @@ def main():
     ap.add_argument("--precision-all", action="store_true",
                     help="solve the 64x64 multiscale array with BF16, FP16 and FP32 macromodel GEMMs")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the per-result errors against the oracle")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="stop after the timed mixed-precision solves (warm-up, profiled pass, timed steps)")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-min-side", type=int, default=8)
     ap.add_argument("--serve-max-side", type=int, default=48)

@@ -415,13 +415,19 @@ def mm_array_tuning(array, nrhs: int, precision: int = MM_C64):
     """The array's launch choices for nrhs columns (near shape, k split, projection and
     interpolation schedules) and the grid tuner's timings, or None before the first product."""
     ch = np.zeros(4, dtype=np.int32)
-    pm = np.zeros(3, dtype=np.float32)
+    pm = np.zeros(4, dtype=np.float32)
     im = np.zeros(3, dtype=np.float32)
     st = load().mm_array_tuning(array, nrhs, precision, _ptr(ch), _ptr(pm), _ptr(im))
     if st != MM_OK:
         return None
+
+    def times(a):   # per variant, None where the variant was not timed; trailing untimed ones dropped
+        t = [float(x) if x >= 0 else None for x in a]
+        while t and t[-1] is None:
+            t.pop()
+        return t
     return {"near_shape": int(ch[0]), "near_ksplit": int(ch[1]), "project": int(ch[2]), "interp": int(ch[3]),
-            "project_ms": [float(x) for x in pm if x >= 0], "interp_ms": [float(x) for x in im if x >= 0]}
+            "project_ms": times(pm), "interp_ms": times(im)}
 
 
 def mm_profile_enable(array, enable: bool = True) -> None:

@@ -12,7 +12,7 @@
 //    stencil node s (moment matching up to degree N_O per axis), integrated
 //    exactly (degree 3 N_O + 1); interpolation is the transpose;
 //  - H[u, u'] = G(r_u - r_u'), G(0) := 0, applied as a linear convolution by a
-//    zero-padded FFT (each axis padded to a 2,3,5,7-smooth length >= 2N - 1);
+//    zero-padded FFT (each axis padded to an 11-smooth length >= 2N - 1);
 //  - near pairs: Chebyshev distance of anchors <= N_NF cells; entry = exact
 //    Galerkin G^(E^,J^) minus its grid approximation (precorrection).
 // Elements must sit on the grid lattice, so that identical elements share
@@ -70,7 +70,7 @@ void fft_inplace(std::vector<cd>& a, int64_t n, int64_t stride, int64_t count, i
 
 bool fft_length_ok(int64_t n) {
   if (n < 1) return false;
-  for (int64_t p : {2, 3, 5, 7})
+  for (int64_t p : {2, 3, 5, 7, 11})
     while (n % p == 0) n /= p;
   return n == 1;
 }
@@ -81,25 +81,36 @@ int64_t fft_good_length(int64_t n) {
   return m;
 }
 
-// Padded length for the device's shared-memory Stockham FFT: the 2,3,5,7-smooth
-// length in [n, 2n] with the lowest modelled cost L * sum over stages of a
-// per-radix weight (radices taken as 4s first, then 2, 3, 5, 7).
+// Padded length of the x and y transforms: the 11-smooth length in [n, 2n]
+// with the lowest modelled instruction count of the device's complex64 line
+// FFT, L times a per-point cost.  Lines of 32 RR points (RR <= kRegFftMax) run
+// in registers: five shuffle butterfly levels plus the RR-point lane DFT,
+// modelled as 50 + 1.5 RR per point.  Other lengths take Stockham stages in
+// shared memory at about 40 per point and stage, scaled by the radix (4 first,
+// then 2, 3, 5, 7, 11).  The weights are rough per-point instruction
+// counts of the two forms.
 int64_t fft_fast_length(int64_t n) {
   n = std::max<int64_t>(n, 1);
   int64_t best = fft_good_length(n);
   double best_cost = 1e300;
   for (int64_t L = n; L <= 2 * n; ++L) {
     if (!fft_length_ok(L)) continue;
-    int64_t m = L;
-    double w = 0;
-    for (int r : {4, 2, 3, 5, 7}) {
-      const double wr = r == 4 ? 1.25 : r == 2 ? 1.0 : r == 3 ? 1.6 : r == 5 ? 2.6 : 3.6;
-      while (m % r == 0) {
-        m /= r;
-        w += wr + 0.3;
+    double per_point;
+    if (L % 32 == 0 && L / 32 <= kRegFftMax) {
+      per_point = 50.0 + 1.5 * (double)(L / 32);
+    } else {
+      int64_t m = L;
+      double w = 0;
+      for (int r : {4, 2, 3, 5, 7, 11}) {
+        const double wr = r == 4 ? 1.0 : r == 2 ? 0.8 : r == 3 ? 1.1 : r == 5 ? 1.5 : r == 7 ? 2.0 : 3.0;
+        while (m % r == 0) {
+          m /= r;
+          w += wr;
+        }
       }
+      per_point = 40.0 * w;
     }
-    const double cost = (double)L * w;
+    const double cost = (double)L * per_point;
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = L;

@@ -72,6 +72,7 @@ struct mm_array {
   // basis) and its inverse
   std::vector<std::vector<int32_t>> nf_perm, nf_iperm;
   std::vector<int32_t> nfb_arow_h;   // per block: first row in the tensor-core block layout
+  std::vector<std::vector<int32_t>> inv_ent_h;   // per type: the inverse stencil lists (host copy)
   std::vector<void*> d_Jf, d_Jhf;    // per type: device copies of the feed vectors (nullptr: not fed)
   void* d_volts = nullptr;           // driven elements' volts (n_elem x nrhs complex128)
   void* d_fu = nullptr;              // the driven elements' equivalent currents J^_f V (N^ x nrhs)
@@ -161,6 +162,21 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
       for (int sn = 0; sn < S; ++sn)
         for (int c = 0; c < 4; ++c) P[((size_t)sn * Nh + n) * 4 + c] = (R)Pi[((size_t)n * S + sn) * 4 + c];
     p.Pi[t] = dev_upload(P.data(), P.size(), da.bytes);
+    if (sizeof(R) == 4 && (size_t)t < a->inv_ent_h.size()) {
+      // the same weights in inverse-list order, with the basis indices as uint16
+      const auto& ent = a->inv_ent_h[t];
+      const size_t E = ent.size(), nb = (2 * E + 15) / 16 * 16;
+      std::vector<unsigned char> tab(16 * E + nb, 0);
+      for (size_t q = 0; q < E; ++q) {
+        const int n = ent[q] & 0xffff, sn = ent[q] >> 16;
+        float w[4];
+        for (int c = 0; c < 4; ++c) w[c] = (float)Pi[((size_t)n * S + sn) * 4 + c];
+        std::memcpy(&tab[16 * q], w, 16);
+        const uint16_t n16 = (uint16_t)n;
+        std::memcpy(&tab[16 * E + 2 * q], &n16, 2);
+      }
+      p.prj_tab.push_back(dev_upload(tab.data(), tab.size(), da.bytes));
+    }
   }
   if (da.nnz > 0) {
     // near-field values in the padded row layout of da.rowptr (pad entries are
@@ -425,6 +441,7 @@ void free_prec_f(mm::DevPrec<float>& p) {
     for (void* q : v) cudaFree(q);
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
+  for (void* q : p.prj_tab) cudaFree(q);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
   for (void* q : p.PJ) cudaFree(q);
@@ -474,7 +491,7 @@ mm_array::~mm_array() {
                   (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
   for (void* q : {da.nfg_dev, (void*)da.nfg_poff, (void*)da.nfg_prow, (void*)da.nfe_ptr, (void*)da.nfe_pair,
-                  (void*)da.nfb_tperm})
+                  (void*)da.nfe_qb, (void*)da.nfb_tperm})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
   if (da.chain) cudaStreamDestroy(da.chain);
@@ -723,6 +740,8 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         }
         da.inv_ptr.push_back(dev_upload(ptr.data(), ptr.size(), acc));
         da.inv_ent.push_back(dev_upload(ent.data(), ent.size(), acc));
+        da.inv_len.push_back((int32_t)ent.size());
+        a->inv_ent_h.push_back(ent);
       }
     }
     a->geo_ptrs = dev_upload(gptr.data(), gptr.size(), acc);
@@ -952,6 +971,17 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
           std::vector<int32_t> fillp(eptr.begin(), eptr.end() - 1);
           for (size_t k = 0; k < allp.size(); ++k) epair[fillp[allp[k].x]++] = (int32_t)k;
           std::vector<int32_t> tperm(perm_off.begin(), perm_off.end());
+          // per entry of epair: (block q, column element's unknown offset), for
+          // the direct form that walks an element's pairs in this order
+          std::vector<int32_t> pair_q(allp.size());
+          for (const auto& ng : da.nfg)
+            for (int64_t k = 0; k < ng.npairs; ++k) pair_q[ng.first_pair + k] = ng.q;
+          std::vector<longlong2> qb(allp.size());
+          for (size_t i = 0; i < allp.size(); ++i) {
+            qb[i].x = pair_q[epair[i]];
+            qb[i].y = ah.off[allp[epair[i]].y];
+          }
+          da.nfe_qb = dev_upload(qb.data(), qb.size(), acc);
           da.nfg_prows = rows;
           da.nfg_prow = dev_upload(prow.data(), prow.size(), acc);
           da.nfe_ptr = dev_upload(eptr.data(), eptr.size(), acc);
@@ -979,7 +1009,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     // tuning override: MACROAIM_GRID_SCHED="p,i" fixes the projection and interpolation variants
     if (const char* gs = std::getenv("MACROAIM_GRID_SCHED")) {
       int gp = -1, gi = -1;
-      if (std::sscanf(gs, "%d,%d", &gp, &gi) == 2 && gp >= 0 && gp <= 2 && gi >= 0 && gi <= 2) {
+      if (std::sscanf(gs, "%d,%d", &gp, &gi) == 2 && gp >= 0 && gp <= 3 && gi >= 0 && gi <= 2) {
         da.grid_force_p = gp;
         da.grid_force_i = gi;
       }
@@ -1391,14 +1421,13 @@ mm_status mm_array_tuning(const mm_array* a, int32_t nrhs, int32_t precision, in
   choices[1] = nt != a->da.near_tune.end() ? nt->second.second : -1;
   choices[2] = gt != a->da.grid_tune.end() ? gt->second.project : -1;
   choices[3] = gt != a->da.grid_tune.end() ? gt->second.interp : -1;
-  for (int i = 0; i < 3; ++i) {
+  const bool has = gt != a->da.grid_tune.end();
+  for (int i = 0; i < 4; ++i)
     if (project_ms)
-      project_ms[i] = gt != a->da.grid_tune.end() && i < (int)gt->second.project_ms.size() ? gt->second.project_ms[i]
-                                                                                          : -1.f;
+      project_ms[i] = has && i < (int)gt->second.project_ms.size() ? gt->second.project_ms[i] : -1.f;
+  for (int i = 0; i < 3; ++i)
     if (interp_ms)
-      interp_ms[i] = gt != a->da.grid_tune.end() && i < (int)gt->second.interp_ms.size() ? gt->second.interp_ms[i]
-                                                                                        : -1.f;
-  }
+      interp_ms[i] = has && i < (int)gt->second.interp_ms.size() ? gt->second.interp_ms[i] : -1.f;
   return MM_OK;
 }
 

@@ -8,6 +8,8 @@
 #include <map>
 #include <vector>
 
+#include "fft_plan.h"
+
 namespace mm {
 
 template <typename R> struct V2;
@@ -74,7 +76,7 @@ struct NearGroupDev {
   int64_t first_pair, npairs;
 };
 
-// Radix plan of one FFT length (radices from {8, 4, 2, 3, 5, 7}).
+// Radix plan of one FFT length (radices from {4, 2, 3, 5, 7, 11}).
 struct FftPlan {
   int L = 1;
   int nst = 0;
@@ -88,6 +90,10 @@ struct DevPrec {
   bool ready = false;
   std::vector<void*> W;   // per type: stacked [M_t; D_t], 2 Nh x Nh complex, row-major
   std::vector<R*> Pi;     // per type: S x Nh x 4 projection weights (stencil node outermost)
+  // complex64 only: per type the projection weights in the order of the inverse
+  // stencil lists (inv_ent): E float4 weights, then E uint16 basis indices
+  // (padded to 16 bytes); the table of the shared-memory projection
+  std::vector<void*> prj_tab;
   void* val = nullptr;    // near-field values (nnz complex)
   void* Ghat = nullptr;   // Green's spectrum [ky][kz][kx] complex, divided by Px Py Pz
   void* twx = nullptr;    // exp(-2 pi i k / Px), k < Px
@@ -149,6 +155,7 @@ struct DevArray {
   std::vector<int32_t*> elems;          // per type: element ids of that type
   std::vector<int32_t*> inv_ptr;        // per type: box node -> first stencil entry touching it (nodes + 1)
   std::vector<int32_t*> inv_ent;        // per type: stencil entries n | (s << 16), grouped by box node
+  std::vector<int32_t> inv_len;         // per type: number of those entries
   std::vector<int64_t> n_of_type;
   // per element
   int64_t* off = nullptr;               // n_elem + 1
@@ -187,6 +194,7 @@ struct DevArray {
   int64_t nfg_prows = 0;                // rows of the partial-sum buffer (sum over pairs of the row type's N^)
   int32_t* nfe_ptr = nullptr;           // per element: its pairs as row element (n_elem + 1) ...
   int32_t* nfe_pair = nullptr;          // ... and the pair indices
+  longlong2* nfe_qb = nullptr;          // per entry of nfe_pair: (block q, unknown offset of the column element)
   int32_t* nfb_tperm = nullptr;         // per type: offset of its anchor ordering in nfb_perm
   int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
   int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm
@@ -225,8 +233,9 @@ struct DevArray {
 };
 
 // Shapes of the block near field: 0-4 CUDA-core tiles (k_near_blocks), 5-6
-// tensor-core tiles (near_tc.cu, complex64).
-constexpr int kNearShapes = 7;
+// tensor-core tiles with partial sums, 7-8 the tensor-core direct form
+// (near_tc.cu, complex64).
+constexpr int kNearShapes = 9;
 // Flags of matvec: kMvNoTune never times near-field kernel shapes (an untuned
 // right-hand-side count takes the size rule and is not remembered);
 // kMvNoProfile records no stage events (the array's profiler is left alone).

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <vector>
 
+#include "fft_plan.h"
 #include "macroaim.h"
 
 namespace mm {

@@ -99,11 +99,30 @@ __device__ __forceinline__ void staged_copy(int n, Load load, Store store) {
 }
 
 
+// q = i / d, r = i % d for 0 <= i < 2^22 by a float reciprocal and one
+// correction step (an integer division costs tens of instructions)
+struct SmallDiv {
+  int d;
+  float rd;
+  __device__ explicit SmallDiv(int d_) : d(d_), rd(1.0f / (float)d_) {}
+  __device__ __forceinline__ void operator()(int i, int& q, int& r) const {
+    q = __float2int_rz((float)i * rd);
+    r = i - q * d;
+    if (r >= d) {
+      r -= d;
+      ++q;
+    } else if (r < 0) {
+      r += d;
+      --q;
+    }
+  }
+};
+
 FftPlan make_plan(int L) {
   FftPlan p;
   p.L = L;
   int n = L;
-  for (int r : {4, 2, 3, 5, 7})
+  for (int r : {4, 2, 3, 5, 7, 11})
     while (n % r == 0 && p.nst < 16) {
       p.rad[p.nst++] = r;
       n /= r;
@@ -472,30 +491,114 @@ __global__ void __launch_bounds__(256) k_grid_gather(int64_t ng, int B, const in
   grid[t] = acc;
 }
 
+// Projection of many right-hand sides from shared-memory tables (complex64):
+// persistent CTAs over the elements of one type.  The type's inverse stencil
+// lists (weights and basis indices in box-node order, DevPrec::prj_tab) are
+// copied into shared memory once per CTA.  Per element and chunk of CH
+// right-hand sides, u of the element's bases is staged; a warp takes a box
+// node, its lanes = CH right-hand sides x 32 / CH groups that stride the node's
+// entries (all table and u reads from shared memory, conflict-free), folded by
+// shuffles; the box (4 components x CH x nodes) passes through shared memory
+// and is added into the grids with atomics along consecutive nodes.
+__host__ __device__ inline size_t prj_tab_bytes(int E) { return 16 * (size_t)E + ((size_t)2 * E + 15) / 16 * 16; }
+__host__ __device__ inline size_t prj_us_offset(int E, int nodes) {
+  return (prj_tab_bytes(E) + 4 * (size_t)(2 * nodes + 1) + 15) / 16 * 16;
+}
+constexpr size_t kPrjSmemMax = 220 * 1024;        // shared memory the table-driven projection may take
+constexpr size_t kInterpRhsSmemMax = 200 * 1024;  // ... and the right-hand-side-lane interpolation
+template <int CH>
+__host__ __device__ inline size_t prj_smem_bytes(int E, int nodes, int Nh) {
+  return prj_us_offset(E, nodes) + 8 * (size_t)CH * ((size_t)Nh + 4 * (size_t)nodes);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(512, 1) k_project_tab(const int32_t* __restrict__ elems, int ne, int Nh, int bx,
+                                                        int by, int bz, const int32_t* __restrict__ inv_ptr,
+                                                        const unsigned char* __restrict__ tab, int E,
+                                                        const int64_t* __restrict__ off,
+                                                        const int32_t* __restrict__ boxorg, int nrhs,
+                                                        const float2* __restrict__ u, int Nx, int Ny, int Nz,
+                                                        float2* __restrict__ grid) {
+  static_assert(CH >= 1 && CH <= 8 && 32 % CH == 0, "lanes: CH right-hand sides x at least four entry groups");
+  constexpr int G = 32 / CH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nodes = bx * by * bz;
+  const float4* sw = reinterpret_cast<const float4*>(smem_raw);
+  const uint16_t* sn = reinterpret_cast<const uint16_t*>(smem_raw + 16 * (size_t)E);
+  int* sptr = reinterpret_cast<int*>(smem_raw + prj_tab_bytes(E));
+  int* goff = sptr + nodes + 1;
+  float2* us = reinterpret_cast<float2*>(smem_raw + prj_us_offset(E, nodes));
+  float2* box = us + (size_t)Nh * CH;
+  {
+    const int n16 = (int)(prj_tab_bytes(E) / 16);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x)
+      reinterpret_cast<float4*>(smem_raw)[i] = __ldg(reinterpret_cast<const float4*>(tab) + i);
+    for (int i = threadIdx.x; i <= nodes; i += blockDim.x) sptr[i] = inv_ptr[i];
+    for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
+      const int lz = i % bz, ly = (i / bz) % by, lx = i / (by * bz);
+      goff[i] = (lx * Ny + ly) * Nz + lz;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int c = lane % CH, g = lane / CH;
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  const SmallDiv dnodes(nodes);
+  for (int ei = blockIdx.x; ei < ne; ei += gridDim.x) {
+    const int e = elems[ei];
+    const int64_t o = off[e];
+    const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
+    for (int c0 = 0; c0 < nrhs; c0 += CH) {
+      for (int i = threadIdx.x; i < Nh * CH; i += blockDim.x) {
+        const int n = i / CH, cc = i % CH;
+        us[i] = c0 + cc < nrhs ? u[(o + n) * nrhs + c0 + cc] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int node = warp; node < nodes; node += nw) {
+        float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ax2 = 0.f, ay2 = 0.f, ax3 = 0.f, ay3 = 0.f;
+        const int q1 = sptr[node + 1];
+#pragma unroll 2
+        for (int q = sptr[node] + g; q < q1; q += G) {
+          const float4 w = sw[q];
+          const float2 uv = us[(int)sn[q] * CH + c];
+          ax0 = fmaf(w.x, uv.x, ax0); ay0 = fmaf(w.x, uv.y, ay0);
+          ax1 = fmaf(w.y, uv.x, ax1); ay1 = fmaf(w.y, uv.y, ay1);
+          ax2 = fmaf(w.z, uv.x, ax2); ay2 = fmaf(w.z, uv.y, ay2);
+          ax3 = fmaf(w.w, uv.x, ax3); ay3 = fmaf(w.w, uv.y, ay3);
+        }
+#pragma unroll
+        for (int o2 = CH; o2 < 32; o2 <<= 1) {
+          ax0 += __shfl_xor_sync(0xffffffffu, ax0, o2); ay0 += __shfl_xor_sync(0xffffffffu, ay0, o2);
+          ax1 += __shfl_xor_sync(0xffffffffu, ax1, o2); ay1 += __shfl_xor_sync(0xffffffffu, ay1, o2);
+          ax2 += __shfl_xor_sync(0xffffffffu, ax2, o2); ay2 += __shfl_xor_sync(0xffffffffu, ay2, o2);
+          ax3 += __shfl_xor_sync(0xffffffffu, ax3, o2); ay3 += __shfl_xor_sync(0xffffffffu, ay3, o2);
+        }
+        // every lane now holds the four sums of its right-hand side; group g
+        // (g < 4) stores component g
+        if (g < 4) {
+          const float sx = g == 0 ? ax0 : g == 1 ? ax1 : g == 2 ? ax2 : ax3;
+          const float sy = g == 0 ? ay0 : g == 1 ? ay1 : g == 2 ? ay2 : ay3;
+          box[(g * CH + c) * nodes + node] = make_float2(sx, sy);
+        }
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < 4 * CH * nodes; i += blockDim.x) {
+        int pc, node;
+        dnodes(i, pc, node);
+        const int q = pc / CH, cc = pc % CH;
+        if (c0 + cc < nrhs) atomicAdd(grid + ((int64_t)q * nrhs + c0 + cc) * gstride + gbase + goff[node], box[i]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ---------------------------------------------------------------- A3: FFT convolution (step ii)
 // Line buffers in shared memory hold element i at PAD(i) = i + i/16, which
 // breaks the bank conflicts of the strided Stockham stores.
 __device__ __forceinline__ int PAD(int i) { return i + (i >> 4); }
 __host__ __device__ inline int padded_len(int L) { return L + (L >> 4) + 1; }
 
-// q = i / d, r = i % d for 0 <= i < 2^22 by a float reciprocal and one
-// correction step (an integer division costs tens of instructions)
-struct SmallDiv {
-  int d;
-  float rd;
-  __device__ explicit SmallDiv(int d_) : d(d_), rd(1.0f / (float)d_) {}
-  __device__ __forceinline__ void operator()(int i, int& q, int& r) const {
-    q = __float2int_rz((float)i * rd);
-    r = i - q * d;
-    if (r >= d) {
-      r -= d;
-      ++q;
-    } else if (r < 0) {
-      r += d;
-      --q;
-    }
-  }
-};
 
 template <typename C, int RADIX, bool INV>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
@@ -700,9 +803,9 @@ __device__ __forceinline__ void warp_fft_reg(const C* a, C* dst, const C* __rest
 template <typename C, bool INV>
 __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
   if constexpr (sizeof(C) == 8) {
-    // complex64 lines of 32 RR points (RR <= 8) in registers; the result goes
+    // complex64 lines of 32 RR points (RR <= 16) in registers; the result goes
     // where the Stockham stages would leave it (a after an even stage count)
-    if ((P.L & 31) == 0 && P.L <= 256 && P.nst > 0) {
+    if ((P.L & 31) == 0 && P.L <= 32 * kRegFftMax && P.nst > 0) {
       C* dst = (P.nst % 2 == 0) ? a : b;
       switch (P.L >> 5) {
         case 1: warp_fft_reg<C, 1, INV>(a, dst, tw, lane); break;
@@ -712,7 +815,11 @@ __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
         case 5: warp_fft_reg<C, 5, INV>(a, dst, tw, lane); break;
         case 6: warp_fft_reg<C, 6, INV>(a, dst, tw, lane); break;
         case 7: warp_fft_reg<C, 7, INV>(a, dst, tw, lane); break;
-        default: warp_fft_reg<C, 8, INV>(a, dst, tw, lane); break;
+        case 8: warp_fft_reg<C, 8, INV>(a, dst, tw, lane); break;
+        case 9: warp_fft_reg<C, 9, INV>(a, dst, tw, lane); break;
+        case 10: warp_fft_reg<C, 10, INV>(a, dst, tw, lane); break;
+        case 11: warp_fft_reg<C, 11, INV>(a, dst, tw, lane); break;
+        default: warp_fft_reg<C, 12, INV>(a, dst, tw, lane); break;
       }
       return dst;
     }
@@ -726,7 +833,8 @@ __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
       case 2: stockham_stage<C, 2, INV>(a, b, P.L, Ns, tw, lane, 32); break;
       case 3: stockham_stage<C, 3, INV>(a, b, P.L, Ns, tw, lane, 32); break;
       case 5: stockham_stage<C, 5, INV>(a, b, P.L, Ns, tw, lane, 32); break;
-      default: stockham_stage<C, 7, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      case 7: stockham_stage<C, 7, INV>(a, b, P.L, Ns, tw, lane, 32); break;
+      default: stockham_stage<C, 11, INV>(a, b, P.L, Ns, tw, lane, 32); break;
     }
     __syncwarp();
     C* t = a;
@@ -1020,6 +1128,82 @@ __global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, 
   }
 }
 
+
+// Interpolation of many right-hand sides (complex64), lanes over right-hand
+// sides: one CTA per element; per chunk of CH right-hand sides the element's box
+// of grid potentials is staged as [psi][node][c] (c fastest, node stride CH + 1
+// so that the staging stores of consecutive nodes spread over the banks); a
+// warp takes four bases at a time, its lanes = CH right-hand sides x 4 bases,
+// and walks the S stencil points: one weight load per point for CH columns,
+// four conflict-free box loads.  y = v - (c_A sum_xyz + c_phi sum_phi).
+template <int CH>
+__global__ void __launch_bounds__(256) k_interp_rhs(const int32_t* __restrict__ elems, int Nh, int S, int n1, int o1lo,
+                                                    int bx, int by, int bz, const int32_t* __restrict__ anc,
+                                                    const float* __restrict__ Pi, const int64_t* __restrict__ off,
+                                                    const int32_t* __restrict__ boxorg, int nrhs,
+                                                    const float2* __restrict__ grid, int Nx, int Ny, int Nz, float cAr,
+                                                    float cAi, float cPr, float cPi, const float2* __restrict__ v,
+                                                    float2* __restrict__ y) {
+  static_assert(CH == 8, "lanes: 8 right-hand sides x 4 bases");
+  constexpr int LD = CH + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nodes = bx * by * bz;
+  float2* box = reinterpret_cast<float2*>(smem_raw);                   // [psi][node][LD]
+  int* soff = reinterpret_cast<int*>(box + (size_t)4 * nodes * LD);    // S
+  int* goff = soff + S;                                                 // nodes
+  const int e = elems[blockIdx.x];
+  const int64_t o = off[e];
+  const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+    soff[s] = (ix * by + iy) * bz + iz;
+  }
+  for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
+    const int lz = i % bz, ly = (i / bz) % by, lx = i / (by * bz);
+    goff[i] = (lx * Ny + ly) * Nz + lz;
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int c = lane % CH, g = lane / CH;
+  const SmallDiv dnodes(nodes);
+  float2 cA, cP;
+  cA.x = cAr; cA.y = cAi; cP.x = cPr; cP.y = cPi;
+  for (int c0 = 0; c0 < nrhs; c0 += CH) {
+    __syncthreads();   // tables written; the previous chunk's box no longer read
+    // stage: consecutive threads take consecutive nodes of one (psi, c) plane
+    for (int i = threadIdx.x; i < 4 * CH * nodes; i += blockDim.x) {
+      int pc, node;
+      dnodes(i, pc, node);
+      const int q = pc / CH, cc = pc % CH;
+      float2 val = make_float2(0.f, 0.f);
+      if (c0 + cc < nrhs) val = grid[((int64_t)q * nrhs + c0 + cc) * gstride + gbase + goff[node]];
+      box[((size_t)q * nodes + node) * LD + cc] = val;
+    }
+    __syncthreads();
+    for (int n0 = 4 * warp; n0 < Nh; n0 += 4 * nw) {
+      const int n = n0 + g;
+      if (n >= Nh) continue;
+      const int nb = ((anc[3 * n] + o1lo) * by + (anc[3 * n + 1] + o1lo)) * bz + (anc[3 * n + 2] + o1lo);
+      float2 sA = make_float2(0.f, 0.f), sP = make_float2(0.f, 0.f);
+#pragma unroll 3
+      for (int s = 0; s < S; ++s) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(Pi) + ((int64_t)s * Nh + n));
+        const float2* b = box + (size_t)(nb + soff[s]) * LD + c;
+        const float2 f0 = b[0], f1 = b[(size_t)nodes * LD], f2 = b[(size_t)2 * nodes * LD],
+                     f3 = b[(size_t)3 * nodes * LD];
+        sA.x = fmaf(w.x, f0.x, fmaf(w.y, f1.x, fmaf(w.z, f2.x, sA.x)));
+        sA.y = fmaf(w.x, f0.y, fmaf(w.y, f1.y, fmaf(w.z, f2.y, sA.y)));
+        sP.x = fmaf(w.w, f3.x, sP.x);
+        sP.y = fmaf(w.w, f3.y, sP.y);
+      }
+      if (c0 + c < nrhs) {
+        const float2 yff = cadd(cmul(cA, sA), cmul(cP, sP));
+        const int64_t idx = (o + n) * nrhs + c0 + c;
+        y[idx] = csub(v[idx], yff);
+      }
+    }
+  }
+}
 // ---------------------------------------------------------------- A5: near field
 // y[row] -= sum_k val[k] u[col[k]].  Rows are padded to multiples of 4 entries
 // (zero values), so a lane reads 4 columns with one 16-byte load and 4 values
@@ -1353,10 +1537,15 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
 // (about 1.9 times the non-zero work instead of 2.3 at 16x16).  The CTA counts
 // per SM apply to complex64; the FP64 forms keep their registers.
 // Shapes 5 and 6 are the tensor-core form (near_tc.cu: 32 or 64 complex
-// columns per tile), complex64 only.
+// columns per tile, partial sums), 7 and 8 its direct form (32 or 64
+// right-hand sides per tile, an even count of them), complex64 only.
 template <typename R>
-static bool near_shape_ok(int shape, const DevPrec<R>& p, const void* np) {
-  return shape < 5 || (sizeof(R) == 4 && p.nfb_tc != nullptr && np != nullptr);
+static bool near_shape_ok(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs, const void* u, const void* v,
+                          const void* np) {
+  if (shape < 5) return true;
+  if (sizeof(R) != 4 || p.nfb_tc == nullptr) return false;
+  if (shape < 7) return np != nullptr;
+  return nrhs >= 16 && near_tc_direct_ok(a, nrhs, u, v);
 }
 
 template <typename R>
@@ -1365,9 +1554,9 @@ static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p,
                               void* np) {
   if (shape >= 5) {
     if constexpr (sizeof(R) == 4) {
-      if (p.nfb_tc != nullptr && np != nullptr) {
+      if (near_shape_ok<R>(shape, a, p, nrhs, u, y, np)) {
         near_tc_launch(shape - 5, a, p, nrhs, u, y, static_cast<float2*>(np), st);
-        nl += 2;
+        nl += shape >= 7 ? 1 : 2;
         return;
       }
     }
@@ -1399,7 +1588,8 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
   int64_t cols = 0;
   for (const auto& g : a.nfg) cols += g.npairs * nrhs;
   std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 2 : 0, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
-  if (near_shape_ok<R>(5, p, np)) best = {cols >= (int64_t)64 * 4 * 152 ? 6 : 5, 1};
+  if (near_shape_ok<R>(5, a, p, nrhs, u, scratch, np)) best = {cols >= (int64_t)64 * 4 * 152 ? 6 : 5, 1};
+  if (nrhs >= 64 && near_shape_ok<R>(8, a, p, nrhs, u, scratch, np)) best = {8, 1};
   if (scratch == nullptr || scratch_elems < (size_t)a.N * nrhs) return best;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
@@ -1410,7 +1600,7 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
   float best_ms = 1e30f;
   for (int tn = 0; tn < kNearShapes; ++tn)
     for (int ks : {1, 2, 4}) {
-      if (!near_shape_ok<R>(tn, p, np) || (tn >= 5 && ks > 1)) continue;   // tensor-core shapes: no k split
+      if (!near_shape_ok<R>(tn, a, p, nrhs, u, scratch, np) || (tn >= 5 && ks > 1)) continue;   // tensor-core shapes: no k split
       int nl = 0;
       auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, np); };
       run();
@@ -1461,6 +1651,10 @@ cudaError_t kernels_init(DevArray& a) {
   MM_ATTR((k_interp<float, 1>)) MM_ATTR((k_interp<double, 1>)) MM_ATTR((k_interp<float, 8>))
   MM_ATTR((k_interp<double, 8>))
 #undef MM_ATTR
+  e = cudaFuncSetAttribute(k_project_tab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrjSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_interp_rhs<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInterpRhsSmemMax);
+  if (e != cudaSuccess) return e;
   e = tc_gemm_init();
   if (e != cudaSuccess) return e;
   return near_tc_init(a);
@@ -1472,9 +1666,28 @@ cudaError_t kernels_init(DevArray& a) {
 // variant 0 stages four right-hand sides per pass (RC = 4), variant 1 one,
 // variant 2 (eight or more, when the array has a box buffer) is the two-pass
 // form: each element writes its box, then every grid point sums the boxes
-// covering it (no atomics).
+// covering it (no atomics); variant 3 (complex64, eight or more, when the
+// type's tables fit in shared memory) is the table-driven form k_project_tab,
+// eight right-hand sides per pass.
 // Interpolation, one right-hand side: 4 >> v lanes per basis; eight or more:
-// variant 0 takes eight right-hand sides per thread (CR = 8), variant 1 one.
+// variant 0 takes eight right-hand sides per thread (CR = 8), variant 1 one,
+// variant 2 (complex64) puts eight right-hand sides on the lanes of a warp
+// (k_interp_rhs).
+// The table-driven projection applies to a type when its tables, u chunk and
+// box fit in shared memory (complex64, eight or more right-hand sides).
+template <typename R>
+static bool project_tab_ok(const DevArray& a, const DevPrec<R>& p, int t, int nrhs) {
+  if (sizeof(R) != 4 || nrhs < 8 || (size_t)t >= p.prj_tab.size() || p.prj_tab[t] == nullptr) return false;
+  const int nodes = a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+  return prj_smem_bytes<8>(a.inv_len[t], nodes, (int)a.Nh[t]) <= kPrjSmemMax;
+}
+template <typename R>
+static bool project_tab_all(const DevArray& a, const DevPrec<R>& p, int nrhs) {
+  for (int64_t t = 0; t < a.n_types; ++t)
+    if (a.n_of_type[t] > 0 && !project_tab_ok(a, p, (int)t, nrhs)) return false;
+  return a.n_types > 0;
+}
+
 template <typename R>
 static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int nrhs, const typename V2<R>::T* u,
                            typename V2<R>::T* grid, void* boxbuf, cudaStream_t cs, int& nl) {
@@ -1485,6 +1698,19 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
     const int Nh = (int)a.Nh[t];
     const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
     const int pnodes = bx * by * bz;
+    if constexpr (sizeof(R) == 4) {
+      if (var == 3 && project_tab_ok(a, p, (int)t, nrhs)) {
+        const int E = a.inv_len[t];
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int ctas = (int)std::min<int64_t>(a.n_of_type[t], sms);
+        k_project_tab<8><<<ctas, 512, prj_smem_bytes<8>(E, pnodes, Nh), cs>>>(
+            a.elems[t], (int)a.n_of_type[t], Nh, bx, by, bz, a.inv_ptr[t],
+            static_cast<const unsigned char*>(p.prj_tab[t]), E, a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+        ++nl;
+        continue;
+      }
+    }
     if (nrhs == 1 || var == 1) {
       // T lanes per node with T nodes <= 512 (two CTAs fit on an SM: one wave)
       int pT = nrhs == 1 ? (4 >> var) : 1;
@@ -1496,7 +1722,7 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
     } else {
       k_project<R, 4><<<(unsigned)a.n_of_type[t], 256, sizeof(C) * Nh * 4, cs>>>(
           a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], p.Pi[t], a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid,
-          var == 2 ? static_cast<C*>(boxbuf) : nullptr, a.box_nodes_max);
+          var == 2 && boxbuf != nullptr ? static_cast<C*>(boxbuf) : nullptr, a.box_nodes_max);
     }
     ++nl;
   }
@@ -1507,6 +1733,13 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
                                                                       a.box_nodes_max, nrhs, grid);
     ++nl;
   }
+}
+
+// shared memory of k_interp_rhs<8> for type t: the box [psi][node][9], the
+// stencil offsets and the node offsets
+static size_t interp_rhs_smem(const DevArray& a, int t) {
+  const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+  return 8 * 4 * nodes * 9 + 4 * (size_t)a.S + 4 * nodes;
 }
 
 template <typename R>
@@ -1525,7 +1758,17 @@ static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int n
     int iT = 4 >> (nrhs == 1 ? var : 0);
     while (iT > 1 && iT * a.Nh[t] > icap) iT >>= 1;
     const int ithreads = std::min(icap, (int)((iT * a.Nh[t] + 31) / 32 * 32));
-    if (rc >= 8 && var == 0)
+    if constexpr (sizeof(R) == 4) {
+      if (var == 2 && nrhs >= 8 && interp_rhs_smem(a, (int)t) <= kInterpRhsSmemMax) {
+        k_interp_rhs<8><<<(unsigned)a.n_of_type[t], 256, interp_rhs_smem(a, (int)t), cs>>>(
+            a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+            p.Pi[t], a.off, a.boxorg, nrhs, grid, Nx, Ny, Nz, (float)a.cA[0], (float)a.cA[1], (float)a.cphi[0],
+            (float)a.cphi[1], v, y);
+        ++nl;
+        continue;
+      }
+    }
+    if (rc >= 8 && var != 1)
       k_interp<R, 8><<<(unsigned)a.n_of_type[t], 256, sm, cs>>>(
           a.elems[t], (int)a.Nh[t], a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
           p.Pi[t], a.off, a.boxorg, nrhs, rc, grid, Nx, Ny, Nz, (R)a.cA[0], (R)a.cA[1], (R)a.cphi[0], (R)a.cphi[1], v,
@@ -1547,7 +1790,7 @@ static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int n
 template <typename R>
 static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int nrhs, Work& w, cudaStream_t st) {
   typedef typename V2<R>::T C;
-  const int np = nrhs == 1 ? 3 : (w.boxbuf != nullptr ? 3 : 2), ni = nrhs == 1 ? 3 : 2;
+  const int np = nrhs == 1 ? 3 : 4, ni = 3;
   std::pair<int, int> best = {0, 0};
   const size_t spec_elems = (size_t)4 * nrhs * a.grid[0] * a.fft[1] * a.fft[2];
   if (spec_elems < (size_t)a.N * nrhs) return best;
@@ -1573,11 +1816,15 @@ static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int n
   };
   for (int var = 0; var < np; ++var) {
     int nl = 0;
+    // variants a product could not run are not timed (the two-pass form without
+    // a box buffer, the table form where a type's tables do not fit)
+    if (nrhs > 1 && ((var == 2 && w.boxbuf == nullptr) || (var == 3 && !project_tab_all(a, p, nrhs)))) continue;
     tp[var] = timeit([&] { project_launch<R>(var, a, p, nrhs, u, grid, w.boxbuf, st, nl); });
     if (tp[var] >= 0 && (tp[best.first] < 0 || tp[var] < tp[best.first])) best.first = var;
   }
   for (int var = 0; var < ni; ++var) {
     int nl = 0;
+    if (nrhs > 1 && var == 2 && (sizeof(R) != 4 || nrhs < 8)) continue;   // the right-hand-side-lane form: complex64, 8+
     ti[var] = timeit([&] { interp_launch<R>(var, a, p, nrhs, grid, v, yscr, st, nl); });
     if (ti[var] >= 0 && (ti[best.second] < 0 || ti[var] < ti[best.second])) best.second = var;
   }

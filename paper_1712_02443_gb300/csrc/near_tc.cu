@@ -91,6 +91,10 @@ __device__ __forceinline__ float tf32_rn(float x) {
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
 }
+// 16-byte copy (L2 only); bytes = 16 or 0 (zero fill)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -143,6 +147,80 @@ __device__ __forceinline__ Unit decode_unit(int64_t t, const int64_t* gpre, int 
   un.e0 = tptr[un.q * nmt + un.mt];
   un.e1 = tptr[un.q * nmt + un.mt + 1];
   return un;
+}
+
+// Direct form: unit t = (row element a, 128-row tile mt, NC right-hand-side
+// columns from c0), tiles fastest-varying last.
+struct DUnit {
+  int a, mt, Na, p0, p1;
+  int64_t c0, offa;
+  bool live;
+};
+
+template <int NC>
+__device__ __forceinline__ DUnit decode_dunit(int64_t t, int nmt, int nnt, const int32_t* __restrict__ type_of,
+                                              const int64_t* __restrict__ tbase, const int32_t* __restrict__ eptr,
+                                              const int64_t* __restrict__ off) {
+  DUnit un;
+  const int64_t per = (int64_t)nmt * nnt;
+  un.a = (int)(t / per);
+  const int64_t r = t - (int64_t)un.a * per;
+  un.mt = (int)(r / nnt);
+  un.c0 = (r - (int64_t)un.mt * nnt) * NC;
+  const int ta = type_of[un.a];
+  un.Na = (int)(tbase[ta + 1] - tbase[ta]);
+  un.p0 = eptr[un.a];
+  un.p1 = eptr[un.a + 1];
+  un.offa = off[un.a];
+  un.live = un.mt * kRowsT < un.Na && un.p1 > un.p0;
+  return un;
+}
+
+// Walks the k tiles of a direct unit: the element's pairs in order (block q,
+// column element offset), and for each the non-zero k tiles [tptr, tptr + 1)
+// of (q, mt); pairs without one are skipped.
+struct KCursor {
+  int ip, p1, e, e1, q, mt, nmt;
+  int64_t offb;
+  const longlong2* qb;
+  const int32_t* tptr;
+  __device__ __forceinline__ void start(int p0_, int p1_, int mt_, int nmt_, const longlong2* qb_,
+                                        const int32_t* tptr_) {
+    ip = p0_ - 1;
+    p1 = p1_;
+    mt = mt_;
+    nmt = nmt_;
+    qb = qb_;
+    tptr = tptr_;
+    e = e1 = 0;
+    next_pair();
+  }
+  __device__ __forceinline__ bool valid() const { return ip < p1; }
+  __device__ __forceinline__ void next_pair() {
+    for (++ip; ip < p1; ++ip) {
+      const longlong2 v = qb[ip];
+      q = (int)v.x;
+      offb = v.y;
+      e = tptr[q * nmt + mt];
+      e1 = tptr[q * nmt + mt + 1];
+      if (e < e1) return;
+    }
+  }
+  __device__ __forceinline__ void advance() {
+    if (++e >= e1) next_pair();
+  }
+};
+
+// number of k tiles of a direct unit
+__device__ __forceinline__ int dunit_tiles(const DUnit& un, int nmt, const longlong2* __restrict__ qb,
+                                           const int32_t* __restrict__ tptr) {
+  int nk = 0;
+  if (!un.live) return 0;
+  for (int ip = un.p0; ip < un.p1; ++ip) {
+    const int q = (int)qb[ip].x;
+    nk += tptr[q * nmt + un.mt + 1] - tptr[q * nmt + un.mt];
+  }
+  return nk;
 }
 
 }  // namespace
@@ -456,6 +534,290 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
   }
 }
 
+// Direct form of the same products for many right-hand sides: work unit =
+// (row element a, 128-row tile mt, NC right-hand-side columns from c0).  Its k
+// tiles run over all pairs (a, b) of the element (block q of the pair and its
+// non-zero k tiles of row tile mt) into one accumulator, and the epilogue
+// subtracts the accumulator from v in place (every (row, column) of v belongs
+// to one unit): no partial sums and no reduction pass.  A k tile's B rows are
+// 16 basis functions of element b with NC consecutive right-hand sides each,
+// copied with 16-byte cp.async (nrhs even, so every row starts 16-byte
+// aligned).  Roles, waits and error handling as in k_near_tc.
+template <int NC, int STAGES, int RAWD>
+__global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
+    const __grid_constant__ CUtensorMap tmA, int rows_total, const int32_t* __restrict__ arow,
+    const int32_t* __restrict__ bnb, int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist,
+    const int32_t* __restrict__ perm, const int32_t* __restrict__ bpb, const int32_t* __restrict__ eptr,
+    const longlong2* __restrict__ qb, const int32_t* __restrict__ type_of, const int64_t* __restrict__ tbase,
+    const int32_t* __restrict__ tperm, const int64_t* __restrict__ off, int nrhs, int64_t units,
+    const float2* __restrict__ u, float2* __restrict__ v, uint64_t wait_ns, int stall) {
+  typedef NearTcCfg<NC, STAGES, RAWD> Cfg;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* rawbuf = base + STAGES * Cfg::Stage;
+  __shared__ __align__(8) uint64_t full_a[STAGES], full_b[STAGES], empty_bar[STAGES], tfull[2], tempty[2], drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ volatile int s_gok[2], s_eok[2];
+  volatile int* stop = &abort_flag;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nnt = (nrhs + NC - 1) / NC;
+
+  if (warp == 0 && lane == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_a[s]), 1);
+      mbar_init(smem_u32(&full_b[s]), kProd);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpi / 32);
+    }
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)(4 * NC)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- A producer: hi and lo tiles of every k tile of every pair of the unit
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
+        const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+        if (!un.live) continue;
+        KCursor c;
+        for (c.start(un.p0, un.p1, un.mt, nmt, qb, tptr); c.valid(); c.advance(), ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop, wait_ns)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_a[s]);
+          unsigned char* sa = base + s * Cfg::Stage;
+          const int x = tlist[c.e] * 2 * kKT;
+          const int row0 = arow[c.q] + un.mt * kRowsT;
+          mbar_expect_tx(fb, 2 * kATile);
+          tma_load_2d(&tmA, smem_u32(sa), fb, x, row0);
+          tma_load_2d(&tmA, smem_u32(sa + kATile), fb, x, row0 + rows_total);
+        }
+      }
+      if (!ok && !*stop) {
+        *stop = 1;
+        atomicExch(&g_near_tc_err, 1);
+      }
+      for (uint32_t j = it > (uint32_t)STAGES ? it - STAGES : 0; j < it; ++j)
+        mbar_wait(smem_u32(&full_a[j % STAGES]), (j / STAGES) & 1, nullptr, kDrainNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && !stall) {
+      // ---- MMA issuer: one accumulator (of two) per unit, over all its k tiles
+      constexpr uint32_t idesc = make_idesc(2u, kRowsT, 2 * NC);
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
+        const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+        const int nk = dunit_tiles(un, nmt, qb, tptr);
+        if (nk == 0) continue;
+        const uint32_t b = lt & 1, ub = lt >> 1;
+        if (!mbar_wait(smem_u32(&tempty[b]), (ub & 1) ^ 1, stop, wait_ns)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + b * (uint32_t)(2 * NC);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(smem_u32(&full_a[s]), r & 1, stop, wait_ns) ||
+              !mbar_wait(smem_u32(&full_b[s]), r & 1, stop, wait_ns)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(base + s * Cfg::Stage);
+          const uint64_t dah = make_desc_sw128(sa), dal = make_desc_sw128(sa + kATile);
+          const uint64_t dbh = make_desc_sw128(sa + 2 * kATile);
+          const uint64_t dbl = make_desc_sw128(sa + 2 * kATile + Cfg::BTile);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t o = (uint64_t)((kk * 32) >> 4);
+            mma_tf32(d, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, dah + o, dbl + o, idesc, 1u);
+            mma_tf32(d, dal + o, dbh + o, idesc, 1u);
+          }
+          umma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&tfull[b]));
+        ++lt;
+      }
+      if (!ok && !*stop) {
+        *stop = 1;
+        atomicExch(&g_near_tc_err, 1);
+      }
+    }
+    if (lane == 0) {
+      umma_commit(smem_u32(&drain_bar));
+      mbar_wait(smem_u32(&drain_bar), 0, nullptr, kDrainNs);
+    }
+  } else if (warp < kEpiWarp0) {
+    // ---- gather (warps 2-9, pt = 0..255): rows of u -> B tiles
+    const int pt = threadIdx.x - 64;
+    const uint32_t raw0 = smem_u32(rawbuf);
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
+      const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+      const int nk = dunit_tiles(un, nmt, qb, tptr);
+      if (nk == 0) continue;   // the same for every gather thread
+      KCursor pre;
+      pre.start(un.p0, un.p1, un.mt, nmt, qb, tptr);
+      // raw k tile i -> slot i % RAWD: [k row kk][column n], 16-byte copies of two
+      // right-hand sides; consecutive threads take consecutive pieces of a row
+      auto issue = [&](int i) {
+        if (i < nk) {
+          const int kt = tlist[pre.e];
+          const int Nb = bnb[pre.q];
+          const int32_t* pb = perm + bpb[pre.q];
+          const int64_t ob = pre.offb;
+          const uint32_t slot = raw0 + (uint32_t)((i % RAWD) * Cfg::Raw);
+#pragma unroll
+          for (int r = 0; r < NC * kKT / 2 / kProd; ++r) {
+            const int h = pt + kProd * r, kk = h / (NC / 2), m2 = h - kk * (NC / 2);
+            const int k = kt * kKT + kk;
+            const int64_t c = un.c0 + 2 * m2;
+            const bool valid = k < Nb && c < nrhs;
+            const float2* src = valid ? u + ((ob + (int64_t)__ldg(pb + k)) * nrhs + c) : u;
+            cp_async16(slot + (uint32_t)(kk * NC + 2 * m2) * 8u, src, valid ? 16u : 0u);
+          }
+          pre.advance();
+        }
+        cp_async_commit();
+      };
+#pragma unroll
+      for (int i = 0; i < RAWD - 1; ++i) issue(i);
+      for (int i = 0; i < nk; ++i, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t r = it / STAGES;
+        cp_async_wait<RAWD - 2>();
+        if (pt == 0) s_gok[it & 1] = mbar_wait(smem_u32(&empty_bar[s]), (r & 1) ^ 1, stop, wait_ns) ? 1 : 0;
+        gather_sync();
+        if (!s_gok[it & 1]) {
+          ok = false;
+          break;
+        }
+        issue(i + RAWD - 1);
+        const uint32_t slot = raw0 + (uint32_t)((i % RAWD) * Cfg::Raw);
+        const uint32_t bh = smem_u32(base + s * Cfg::Stage + 2 * kATile), bl = bh + Cfg::BTile;
+        // chunk (n, j): complex entries 2j, 2j + 1 of column n; consecutive
+        // threads take consecutive columns (conflict-free reads of the raw rows,
+        // and the swizzle spreads the 16-byte stores over all banks)
+#pragma unroll
+        for (int rr = 0; rr < NC * 8 / kProd; ++rr) {
+          const int h = pt + kProd * rr, n = h % NC, j = h / NC;
+          float2 e0, e1;
+          asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(e0.x), "=f"(e0.y)
+                       : "r"(slot + (uint32_t)((2 * j) * NC + n) * 8u));
+          asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(e1.x), "=f"(e1.y)
+                       : "r"(slot + (uint32_t)((2 * j + 1) * NC + n) * 8u));
+          const float hr0 = tf32_rn(e0.x), hi0 = tf32_rn(e0.y), hr1 = tf32_rn(e1.x), hi1 = tf32_rn(e1.y);
+          const float lr0 = tf32_rn(e0.x - hr0), li0 = tf32_rn(e0.y - hi0), lr1 = tf32_rn(e1.x - hr1),
+                      li1 = tf32_rn(e1.y - hi1);
+          const uint32_t o1 = (uint32_t)(n * 128 + ((j ^ (n & 7)) << 4));
+          const uint32_t o2 = (uint32_t)((NC + n) * 128 + ((j ^ (n & 7)) << 4));
+          st_shared_v4(bh + o1, hr0, -hi0, hr1, -hi1);
+          st_shared_v4(bh + o2, hi0, hr0, hi1, hr1);
+          st_shared_v4(bl + o1, lr0, -li0, lr1, -li1);
+          st_shared_v4(bl + o2, li0, lr0, li1, lr1);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_b[s]));
+      }
+      cp_async_wait<0>();
+    }
+    cp_async_wait<0>();
+    if (!ok && !*stop) {
+      *stop = 1;
+      atomicExch(&g_near_tc_err, 1);
+    }
+  } else {
+    // ---- epilogue (warps 10-13): thread = block row m (TMEM lane); v row of
+    // the row element (anchor order -> basis), 16 columns at a time, v -= acc
+    const int et = threadIdx.x - 32 * kEpiWarp0, qd = warp & 3;
+    uint32_t lt = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
+      const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+      const int nk = dunit_tiles(un, nmt, qb, tptr);
+      if (nk == 0) continue;
+      const int m = un.mt * kRowsT + 32 * qd + lane;
+      const uint32_t b = lt & 1, ub = lt >> 1;
+      if (et == 0) s_eok[lt & 1] = mbar_wait(smem_u32(&tfull[b]), ub & 1, stop, wait_ns) ? 1 : 0;
+      epi_sync();
+      if (!s_eok[lt & 1]) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + b * (uint32_t)(2 * NC);
+      float2* row = nullptr;
+      if (m < un.Na) {
+        const int32_t* pa = perm + tperm[type_of[un.a]];
+        row = v + (un.offa + pa[m]) * nrhs + un.c0;
+      }
+#pragma unroll 1
+      for (int c0 = 0; c0 < NC; c0 += 16) {
+        uint32_t re[16], im[16];
+        tmem_ld16(tl + (uint32_t)c0, re);
+        tmem_ld16(tl + (uint32_t)(NC + c0), im);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row != nullptr) {
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {   // two right-hand sides per 16-byte access (nrhs even)
+            if (un.c0 + c0 + c < nrhs) {
+              float4* d = reinterpret_cast<float4*>(row + c0 + c);
+              float4 o = *d;
+              o.x -= __uint_as_float(re[c]);
+              o.y -= __uint_as_float(im[c]);
+              o.z -= __uint_as_float(re[c + 1]);
+              o.w -= __uint_as_float(im[c + 1]);
+              *d = o;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+      ++lt;
+    }
+    if (!ok && et == 0 && !*stop) {
+      *stop = 1;
+      atomicExch(&g_near_tc_err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(4 * NC)));
+  }
+}
+
 namespace {
 
 template <int NC, int STAGES, int RAWD>
@@ -479,6 +841,28 @@ cudaError_t near_tc_launch_t(const DevArray& a, const DevPrec<float>& p, int nrh
   return cudaGetLastError();
 }
 
+template <int NC, int STAGES, int RAWD>
+cudaError_t near_tc_direct_launch_t(const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u, float2* v,
+                                    cudaStream_t st) {
+  if (nrhs % 2 != 0 || (reinterpret_cast<uintptr_t>(u) & 15) != 0 || (reinterpret_cast<uintptr_t>(v) & 15) != 0 ||
+      a.nfe_qb == nullptr)
+    return cudaErrorInvalidValue;
+  const int64_t nnt = (nrhs + NC - 1) / NC;
+  const int64_t units = a.n_elem * (int64_t)a.nfb_nmt128 * nnt;
+  if (units == 0) return cudaSuccess;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = (int)std::min<int64_t>(units, std::max(1, sms));
+  const int stall_ms = tc_stall_ms();
+  const uint64_t wait_ns = stall_ms > 0 ? (uint64_t)stall_ms * 1000000ull : kWaitNs;
+  typedef NearTcCfg<NC, STAGES, RAWD> Cfg;
+  k_near_tc_direct<NC, STAGES, RAWD><<<ctas, kThreadsNT, Cfg::Smem, st>>>(
+      p.nfb_tmap, a.nfb_tc_rows, a.nfb_arow, a.nfb_nb, a.nfb_nmt128, a.nfb_tptr128, a.nfb_tlist128, a.nfb_perm,
+      a.nfb_pb, a.nfe_ptr, a.nfe_qb, a.type_of, a.tbase, a.nfb_tperm, a.off, nrhs, units, u, v, wait_ns,
+      stall_ms > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t near_tc_init(DevArray& a) {
@@ -486,6 +870,12 @@ cudaError_t near_tc_init(DevArray& a) {
                                        (int)NearTcCfg<32, 4, 4>::Smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_near_tc<64, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)NearTcCfg<64, 3, 3>::Smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_near_tc_direct<32, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)NearTcCfg<32, 4, 4>::Smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_near_tc_direct<64, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)NearTcCfg<64, 3, 3>::Smem);
   if (e != cudaSuccess) return e;
   void* p = nullptr;
@@ -568,9 +958,18 @@ __global__ void __launch_bounds__(256) k_near_reduce(const int32_t* __restrict__
     }
 }
 
+bool near_tc_direct_ok(const DevArray& a, int nrhs, const void* u, const void* v) {
+  return nrhs % 2 == 0 && a.nfe_qb != nullptr && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(v) & 15) == 0;
+}
+
 cudaError_t near_tc_launch(int shape, const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u,
                            float2* v, float2* P, cudaStream_t st) {
-  if (!p.nfb_tc || a.nfb_tptr128 == nullptr || P == nullptr || a.nfe_ptr == nullptr) return cudaErrorInvalidValue;
+  if (!p.nfb_tc || a.nfb_tptr128 == nullptr || a.nfe_ptr == nullptr) return cudaErrorInvalidValue;
+  if (shape >= 2)
+    return shape == 3 ? near_tc_direct_launch_t<64, 3, 3>(a, p, nrhs, u, v, st)
+                      : near_tc_direct_launch_t<32, 4, 4>(a, p, nrhs, u, v, st);
+  if (P == nullptr) return cudaErrorInvalidValue;
   cudaError_t e = shape == 1 ? near_tc_launch_t<64, 3, 3>(a, p, nrhs, u, P, st)
                              : near_tc_launch_t<32, 4, 4>(a, p, nrhs, u, P, st);
   if (e != cudaSuccess) return e;

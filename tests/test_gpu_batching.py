@@ -99,7 +99,7 @@ def test_every_grid_schedule_one_rhs(ctx, monkeypatch, sched):
         la.close()
 
 
-@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0", "2,0", "2,1"])
+@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0", "2,0", "2,1", "3,0", "3,1", "0,2", "3,2"])
 @pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C128])
 def test_every_grid_schedule_64_rhs(ctx, monkeypatch, sched, prec):
     monkeypatch.setenv("MACROAIM_GRID_SCHED", sched)
@@ -114,5 +114,27 @@ def test_every_grid_schedule_64_rhs(ctx, monkeypatch, sched, prec):
         torch.cuda.synchronize()
         Y = y.cpu().numpy().astype(np.complex128).reshape(la.n, 64)
         assert _rel(Y[g["rows"]], g["y_rows"]) <= (1e-11 if prec == mm.MM_C128 else 1e-5)
+    finally:
+        la.close()
+
+
+@pytest.mark.parametrize("nrhs", [8, 12, 20])
+@pytest.mark.parametrize("sched", ["3,0", "0,2", "3,2"])
+def test_table_projection_ragged_chunks(ctx, monkeypatch, nrhs, sched):
+    """Table-driven projection (projection schedule 3) and the
+    right-hand-side-lane interpolation (interpolation schedule 2), eight
+    right-hand sides per pass: counts that leave a partial last pass,
+    complex64, sampled rows vs the oracle."""
+    monkeypatch.setenv("MACROAIM_GRID_SCHED", sched)
+    g = np.load(os.path.join(GOLD, "c3_types_6x6.npz"))
+    la = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2)
+    try:
+        X = wl.random_cvec(la.n, 2, 7, nrhs=64)[:, :nrhs]
+        x = torch.from_numpy(np.ascontiguousarray(X).reshape(-1)).to(torch.complex64).cuda()
+        y = torch.empty_like(x)
+        mm.mm_apply(la.array, nrhs, x, y, mm.MM_C64, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        Y = y.cpu().numpy().astype(np.complex128).reshape(la.n, nrhs)
+        assert _rel(Y[g["rows"]], g["y_rows"][:, :nrhs]) <= 1e-5
     finally:
         la.close()

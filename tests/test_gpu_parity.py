@@ -455,18 +455,20 @@ def test_block_near_field_every_kernel_shape(ctx, c3, monkeypatch, shape, ks, nr
         mm.mm_array_destroy(la.array)
 
 
-@pytest.mark.parametrize("nx", [10, 15, 19])
+@pytest.mark.parametrize("nx", [10, 15, 19, 24, 30, 34, 38])
 def test_register_fft_lengths(ctx, c1, loop_model, nx):
-    """Linear arrays whose padded x length is 128, 160 and 256 points (32 R with
-    R = 4, 5, 8: the register FFT's even, odd and largest lane DFTs; the other
-    tests reach R = 1, 2, 3, 6).  Far-field operator only (N_NF = -1), whole
-    product vs the oracle, complex64 and complex128."""
+    """Linear arrays whose padded x length is 128, 160, 224, 256, 320, 352 and 384
+    points (32 R with R = 4, 5, 7, 8, 10, 11, 12: the register FFT's even and odd
+    lane DFTs up to the largest; the other tests reach R = 1, 2, 3, 6).  The
+    complex128 product takes Stockham stages at the same lengths (radix 11 at
+    352).  Far-field operator only (N_NF = -1), whole product vs the oracle,
+    complex64 and complex128."""
     from oracle.aim import AIMArray, AIMParams
     lay = wl.loop_array(nx, 1)
     A = AIMArray([loop_model], lay.type_of, lay.offsets, AIMParams(0.1, 2, -1, wl.DEFAULT_GRID_PHASE), 2 * np.pi)
     la = loop_array(ctx, nx, 1, n_nf=-1, types=c1.types)
     try:
-        assert la.info["fft"][0] == {10: 128, 15: 160, 19: 256}[nx]
+        assert la.info["fft"][0] == {10: 128, 15: 160, 19: 224, 24: 256, 30: 320, 34: 352, 38: 384}[nx]
         x = wl.random_cvec(la.n, 0, 30 + nx)
         ref = A.matvec(np.ascontiguousarray(x))
         for prec in (mm.MM_C64, mm.MM_C128):
