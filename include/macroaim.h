@@ -361,15 +361,16 @@ mm_status mm_array_near_shape(const mm_array* array, int32_t nrhs, int32_t preci
  * choices[2]: projection schedule, choices[3]: interpolation schedule, chosen
  * on the array's first product of that width by timing each variant with CUDA
  * events (projection with one right-hand side: 4, 2 or 1 lanes per stencil-box
- * node for variants 0-2; several: 0 = four right-hand sides per pass, 1 = one,
+ * node for variants 0-2, 3 = complex64 from the type's stencil tables, four
+ * lanes per node; several: 0 = four right-hand sides per pass, 1 = one,
  * 2 = two passes through a per-element box buffer without atomics (eight or
  * more), 3 = complex64 from the type's stencil tables in shared memory, eight
  * right-hand sides per pass (eight or more, where the tables fit);
  * interpolation with one right-hand side: 4, 2 or 1 lanes per basis; eight or
  * more: 0 = eight right-hand sides per thread, 1 = one, 2 = complex64 with
- * eight right-hand sides across the lanes of a warp).  project_ms (4 floats) and
- * interp_ms (3 floats), each may be NULL: the variants' times, -1 where not
- * timed.  MACROAIM_GRID_SCHED="p,i" (read when the array is created) fixes
+ * eight right-hand sides across the lanes of a warp, 3 = the same from the
+ * types' weights in shared memory).  project_ms and interp_ms (4 floats each,
+ * may be NULL): the variants' times, -1 where not timed.  MACROAIM_GRID_SCHED="p,i" (read when the array is created) fixes
  * the two schedules.
  * MACROAIM_GRID_TUNE=0 (read when the array is created) keeps variant 0
  * without timing.  MM_EINVAL before any product of that width.              */

@@ -416,7 +416,7 @@ def mm_array_tuning(array, nrhs: int, precision: int = MM_C64):
     interpolation schedules) and the grid tuner's timings, or None before the first product."""
     ch = np.zeros(4, dtype=np.int32)
     pm = np.zeros(4, dtype=np.float32)
-    im = np.zeros(3, dtype=np.float32)
+    im = np.zeros(4, dtype=np.float32)
     st = load().mm_array_tuning(array, nrhs, precision, _ptr(ch), _ptr(pm), _ptr(im))
     if st != MM_OK:
         return None

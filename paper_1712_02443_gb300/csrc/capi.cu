@@ -178,6 +178,42 @@ void upload_precision(mm_array* a, mm::DevPrec<R>& p) {
       p.prj_tab.push_back(dev_upload(tab.data(), tab.size(), da.bytes));
     }
   }
+  if (sizeof(R) == 4 && (int64_t)p.prj_tab.size() == da.n_types && da.n_types > 0) {
+    std::vector<mm::PrjTypeDev> pt(da.n_types);
+    size_t smem = 0;
+    int64_t total = 0;
+    for (int64_t t = 0; t < da.n_types; ++t) {
+      pt[t].tab = static_cast<const unsigned char*>(p.prj_tab[t]);
+      pt[t].inv_ptr = da.inv_ptr[t];
+      pt[t].elems = da.elems[t];
+      pt[t].E = da.inv_len[t];
+      pt[t].Nh = (int)da.Nh[t];
+      pt[t].bx = da.box[3 * t];
+      pt[t].by = da.box[3 * t + 1];
+      pt[t].bz = da.box[3 * t + 2];
+      pt[t].ne = da.n_of_type[t];
+      smem = std::max(smem, mm::project_tab_smem(pt[t].E, pt[t].bx * pt[t].by * pt[t].bz, pt[t].Nh));
+      total += pt[t].ne;
+    }
+    p.prj_types = dev_upload(pt.data(), pt.size(), da.bytes);
+    p.prj_smem = smem;
+    p.prj_total = total;
+    std::vector<mm::ItpTypeDev> it(da.n_types);
+    size_t ismem = 0;
+    for (int64_t t = 0; t < da.n_types; ++t) {
+      it[t].Pi = reinterpret_cast<const float*>(p.Pi[t]);
+      it[t].anc = da.anc[t];
+      it[t].elems = da.elems[t];
+      it[t].Nh = (int)da.Nh[t];
+      it[t].bx = da.box[3 * t];
+      it[t].by = da.box[3 * t + 1];
+      it[t].bz = da.box[3 * t + 2];
+      it[t].ne = da.n_of_type[t];
+      ismem = std::max(ismem, mm::interp_tab_smem((int)da.S, it[t].Nh, it[t].bx * it[t].by * it[t].bz));
+    }
+    p.itp_types = dev_upload(it.data(), it.size(), da.bytes);
+    p.itp_smem = ismem;
+  }
   if (da.nnz > 0) {
     // near-field values in the padded row layout of da.rowptr (pad entries are
     // 0); complex64 interleaved, FP64 as (Re, Im, Re + Im) for the
@@ -442,6 +478,8 @@ void free_prec_f(mm::DevPrec<float>& p) {
   for (void* q : p.W) cudaFree(q);
   for (void* q : p.Pi) cudaFree(q);
   for (void* q : p.prj_tab) cudaFree(q);
+  if (p.prj_types) cudaFree(p.prj_types);
+  if (p.itp_types) cudaFree(p.itp_types);
   for (void* q : {p.val, p.Ghat, p.twx, p.twy, p.twz, p.nfb_val})
     if (q) cudaFree(q);
   for (void* q : p.PJ) cudaFree(q);
@@ -1009,7 +1047,7 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     // tuning override: MACROAIM_GRID_SCHED="p,i" fixes the projection and interpolation variants
     if (const char* gs = std::getenv("MACROAIM_GRID_SCHED")) {
       int gp = -1, gi = -1;
-      if (std::sscanf(gs, "%d,%d", &gp, &gi) == 2 && gp >= 0 && gp <= 3 && gi >= 0 && gi <= 2) {
+      if (std::sscanf(gs, "%d,%d", &gp, &gi) == 2 && gp >= 0 && gp <= 3 && gi >= 0 && gi <= 3) {
         da.grid_force_p = gp;
         da.grid_force_i = gi;
       }
@@ -1425,7 +1463,7 @@ mm_status mm_array_tuning(const mm_array* a, int32_t nrhs, int32_t precision, in
   for (int i = 0; i < 4; ++i)
     if (project_ms)
       project_ms[i] = has && i < (int)gt->second.project_ms.size() ? gt->second.project_ms[i] : -1.f;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if (interp_ms)
       interp_ms[i] = has && i < (int)gt->second.interp_ms.size() ? gt->second.interp_ms[i] : -1.f;
   return MM_OK;

@@ -76,6 +76,24 @@ struct NearGroupDev {
   int64_t first_pair, npairs;
 };
 
+// Per-type parameters of the table-driven projection (device copy).
+struct PrjTypeDev {
+  const unsigned char* tab;     // E float4 weights, then E uint16 basis indices (16-byte padded)
+  const int32_t* inv_ptr;       // box node -> first entry (nodes + 1)
+  const int32_t* elems;         // the type's element ids
+  int E, Nh, bx, by, bz;
+  int64_t ne;                   // number of elements of the type
+};
+
+// Per-type parameters of the table-driven interpolation (device copy).
+struct ItpTypeDev {
+  const float* Pi;              // S x Nh x 4 weights (stencil node outermost)
+  const int32_t* anc;           // per basis: stencil anchor in the type's box (3 ints)
+  const int32_t* elems;
+  int Nh, bx, by, bz;
+  int64_t ne;
+};
+
 // Radix plan of one FFT length (radices from {4, 2, 3, 5, 7, 11}).
 struct FftPlan {
   int L = 1;
@@ -94,6 +112,11 @@ struct DevPrec {
   // stencil lists (inv_ent): E float4 weights, then E uint16 basis indices
   // (padded to 16 bytes); the table of the shared-memory projection
   std::vector<void*> prj_tab;
+  PrjTypeDev* prj_types = nullptr;   // per type (n_types), when every type has a table
+  size_t prj_smem = 0;               // shared memory of the largest type's tables, u chunk and box
+  int64_t prj_total = 0;             // elements of all types
+  ItpTypeDev* itp_types = nullptr;   // the same for the table-driven interpolation
+  size_t itp_smem = 0;
   void* val = nullptr;    // near-field values (nnz complex)
   void* Ghat = nullptr;   // Green's spectrum [ky][kz][kx] complex, divided by Px Py Pz
   void* twx = nullptr;    // exp(-2 pi i k / Px), k < Px
@@ -253,5 +276,9 @@ cudaError_t precond_apply(DevArray& a, DevPrec<R>& p, int nrhs, const void* x, v
 template <typename R>
 size_t fft_smem_bytes(const DevArray& a, int which);
 cudaError_t kernels_init(DevArray& a);
+// shared memory the table-driven projection needs for one type
+size_t project_tab_smem(int E, int nodes, int Nh);
+// ... and the table-driven interpolation (weights, box of eight right-hand sides)
+size_t interp_tab_smem(int S, int Nh, int nodes);
 
 }  // namespace mm

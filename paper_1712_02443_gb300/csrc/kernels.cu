@@ -491,10 +491,74 @@ __global__ void __launch_bounds__(256) k_grid_gather(int64_t ng, int B, const in
   grid[t] = acc;
 }
 
+// Projection of one right-hand side from the same tables (complex64), read
+// from global memory (L1 / L2): one CTA per element, u of its bases staged in
+// shared memory; a warp takes eight box nodes, four lanes per node striding
+// its entries (weight and basis index loaded together, four entries per step:
+// no dependent loads), folded by two shuffle levels; lane g of a node adds
+// component g into the grid.
+__global__ void __launch_bounds__(256) k_project_g1(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+                                                    const int32_t* __restrict__ inv_ptr,
+                                                    const unsigned char* __restrict__ tab, int E,
+                                                    const int64_t* __restrict__ off,
+                                                    const int32_t* __restrict__ boxorg, const float2* __restrict__ u,
+                                                    int Nx, int Ny, int Nz, float2* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* us = reinterpret_cast<float2*>(smem_raw);
+  const float4* tw = reinterpret_cast<const float4*>(tab);
+  const uint16_t* tn = reinterpret_cast<const uint16_t*>(tab + 16 * (size_t)E);
+  const int e = elems[blockIdx.x];
+  const int64_t o = off[e];
+  const int nodes = bx * by * bz;
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
+  for (int n = threadIdx.x; n < Nh; n += blockDim.x) us[n] = u[o + n];
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int j = lane / 4, g = lane % 4;
+  for (int node0 = 8 * warp; node0 < nodes; node0 += 8 * nw) {
+    const int node = node0 + j;
+    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ax2 = 0.f, ay2 = 0.f, ax3 = 0.f, ay3 = 0.f;
+    auto mac = [&](const float4 w, const float2 uv) {
+      ax0 = fmaf(w.x, uv.x, ax0); ay0 = fmaf(w.x, uv.y, ay0);
+      ax1 = fmaf(w.y, uv.x, ax1); ay1 = fmaf(w.y, uv.y, ay1);
+      ax2 = fmaf(w.z, uv.x, ax2); ay2 = fmaf(w.z, uv.y, ay2);
+      ax3 = fmaf(w.w, uv.x, ax3); ay3 = fmaf(w.w, uv.y, ay3);
+    };
+    if (node < nodes) {
+      const int q1 = inv_ptr[node + 1];
+      int q = inv_ptr[node] + g;
+      for (; q + 12 < q1; q += 16) {
+        const float4 w0 = __ldg(tw + q), w1 = __ldg(tw + q + 4), w2 = __ldg(tw + q + 8), w3 = __ldg(tw + q + 12);
+        const int n0 = __ldg(tn + q), n1 = __ldg(tn + q + 4), n2 = __ldg(tn + q + 8), n3 = __ldg(tn + q + 12);
+        mac(w0, us[n0]);
+        mac(w1, us[n1]);
+        mac(w2, us[n2]);
+        mac(w3, us[n3]);
+      }
+      for (; q < q1; q += 4) mac(__ldg(tw + q), us[__ldg(tn + q)]);
+    }
+#pragma unroll
+    for (int o2 = 1; o2 < 4; o2 <<= 1) {
+      ax0 += __shfl_xor_sync(0xffffffffu, ax0, o2); ay0 += __shfl_xor_sync(0xffffffffu, ay0, o2);
+      ax1 += __shfl_xor_sync(0xffffffffu, ax1, o2); ay1 += __shfl_xor_sync(0xffffffffu, ay1, o2);
+      ax2 += __shfl_xor_sync(0xffffffffu, ax2, o2); ay2 += __shfl_xor_sync(0xffffffffu, ay2, o2);
+      ax3 += __shfl_xor_sync(0xffffffffu, ax3, o2); ay3 += __shfl_xor_sync(0xffffffffu, ay3, o2);
+    }
+    if (node < nodes) {
+      const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+      const float sx = g == 0 ? ax0 : g == 1 ? ax1 : g == 2 ? ax2 : ax3;
+      const float sy = g == 0 ? ay0 : g == 1 ? ay1 : g == 2 ? ay2 : ay3;
+      atomicAdd(grid + (int64_t)g * gstride + gbase + ((int64_t)lx * Ny + ly) * Nz + lz, make_float2(sx, sy));
+    }
+  }
+}
+
 // Projection of many right-hand sides from shared-memory tables (complex64):
-// persistent CTAs over the elements of one type.  The type's inverse stencil
-// lists (weights and basis indices in box-node order, DevPrec::prj_tab) are
-// copied into shared memory once per CTA.  Per element and chunk of CH
+// one launch for all types; each CTA takes a contiguous range of the elements
+// listed type by type, and copies a type's inverse stencil lists (weights and
+// basis indices in box-node order, DevPrec::prj_tab) into shared memory when
+// its walk enters that type.  Per element and chunk of CH
 // right-hand sides, u of the element's bases is staged; a warp takes a box
 // node, its lanes = CH right-hand sides x 32 / CH groups that stride the node's
 // entries (all table and u reads from shared memory, conflict-free), folded by
@@ -506,15 +570,14 @@ __host__ __device__ inline size_t prj_us_offset(int E, int nodes) {
 }
 constexpr size_t kPrjSmemMax = 220 * 1024;        // shared memory the table-driven projection may take
 constexpr size_t kInterpRhsSmemMax = 200 * 1024;  // ... and the right-hand-side-lane interpolation
+constexpr size_t kInterpTabSmemMax = 220 * 1024;  // ... and the table-driven interpolation
 template <int CH>
 __host__ __device__ inline size_t prj_smem_bytes(int E, int nodes, int Nh) {
   return prj_us_offset(E, nodes) + 8 * (size_t)CH * ((size_t)Nh + 4 * (size_t)nodes);
 }
 
 template <int CH>
-__global__ void __launch_bounds__(512, 1) k_project_tab(const int32_t* __restrict__ elems, int ne, int Nh, int bx,
-                                                        int by, int bz, const int32_t* __restrict__ inv_ptr,
-                                                        const unsigned char* __restrict__ tab, int E,
+__global__ void __launch_bounds__(512, 1) k_project_tab(const PrjTypeDev* __restrict__ types, int64_t total,
                                                         const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ boxorg, int nrhs,
                                                         const float2* __restrict__ u, int Nx, int Ny, int Nz,
@@ -522,33 +585,64 @@ __global__ void __launch_bounds__(512, 1) k_project_tab(const int32_t* __restric
   static_assert(CH >= 1 && CH <= 8 && 32 % CH == 0, "lanes: CH right-hand sides x at least four entry groups");
   constexpr int G = 32 / CH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nodes = bx * by * bz;
-  const float4* sw = reinterpret_cast<const float4*>(smem_raw);
-  const uint16_t* sn = reinterpret_cast<const uint16_t*>(smem_raw + 16 * (size_t)E);
-  int* sptr = reinterpret_cast<int*>(smem_raw + prj_tab_bytes(E));
-  int* goff = sptr + nodes + 1;
-  float2* us = reinterpret_cast<float2*>(smem_raw + prj_us_offset(E, nodes));
-  float2* box = us + (size_t)Nh * CH;
-  {
-    const int n16 = (int)(prj_tab_bytes(E) / 16);
-    for (int i = threadIdx.x; i < n16; i += blockDim.x)
-      reinterpret_cast<float4*>(smem_raw)[i] = __ldg(reinterpret_cast<const float4*>(tab) + i);
-    for (int i = threadIdx.x; i <= nodes; i += blockDim.x) sptr[i] = inv_ptr[i];
-    for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
-      const int lz = i % bz, ly = (i / bz) % by, lx = i / (by * bz);
-      goff[i] = (lx * Ny + ly) * Nz + lz;
-    }
-  }
-  __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   const int c = lane % CH, g = lane / CH;
   const int64_t gstride = (int64_t)Nx * Ny * Nz;
-  const SmallDiv dnodes(nodes);
-  for (int ei = blockIdx.x; ei < ne; ei += gridDim.x) {
-    const int e = elems[ei];
-    const int64_t o = off[e];
-    const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
-    for (int c0 = 0; c0 < nrhs; c0 += CH) {
+  // this CTA's contiguous range of the elements (all types, in type order)
+  const int64_t i0 = (int64_t)blockIdx.x * total / gridDim.x, i1 = (int64_t)(blockIdx.x + 1) * total / gridDim.x;
+  int t = -1;   // type whose tables are in shared memory
+  int64_t tb = 0, te = 0;
+  int E = 0, Nh = 0, nodes = 0;
+  const int32_t* elems = nullptr;
+  const float4* sw = nullptr;
+  const uint16_t* sn = nullptr;
+  int* sptr = nullptr;
+  int* goff = nullptr;
+  float2* us = nullptr;
+  float2* box = nullptr;
+  // right-hand-side chunks outermost: the CTAs move through the chunks together,
+  // so the grid planes being added to (4 CH of them) stay in L2; the element
+  // range is walked forwards and backwards in turn, so that one chunk ends on
+  // the type the next begins with
+  int pass = 0;
+  for (int c0 = 0; c0 < nrhs; c0 += CH, ++pass) {
+    for (int64_t k = 0; k < i1 - i0; ++k) {
+      const int64_t gi = (pass & 1) ? i1 - 1 - k : i0 + k;
+      if (gi < tb || gi >= te) {
+        // another type: its tables into shared memory (every thread takes this branch)
+        t = 0;
+        tb = 0;
+        te = types[0].ne;
+        while (gi >= te) {
+          ++t;
+          tb = te;
+          te += types[t].ne;
+        }
+        const PrjTypeDev ty = types[t];
+        E = ty.E;
+        Nh = ty.Nh;
+        nodes = ty.bx * ty.by * ty.bz;
+        elems = ty.elems;
+        sw = reinterpret_cast<const float4*>(smem_raw);
+        sn = reinterpret_cast<const uint16_t*>(smem_raw + 16 * (size_t)E);
+        sptr = reinterpret_cast<int*>(smem_raw + prj_tab_bytes(E));
+        goff = sptr + nodes + 1;
+        us = reinterpret_cast<float2*>(smem_raw + prj_us_offset(E, nodes));
+        box = us + (size_t)Nh * CH;
+        __syncthreads();   // the previous type's tables are no longer read
+        const int n16 = (int)(prj_tab_bytes(E) / 16);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x)
+          reinterpret_cast<float4*>(smem_raw)[i] = __ldg(reinterpret_cast<const float4*>(ty.tab) + i);
+        for (int i = threadIdx.x; i <= nodes; i += blockDim.x) sptr[i] = ty.inv_ptr[i];
+        for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
+          const int lz = i % ty.bz, ly = (i / ty.bz) % ty.by, lx = i / (ty.by * ty.bz);
+          goff[i] = (lx * Ny + ly) * Nz + lz;
+        }
+      }
+      const SmallDiv dnodes(nodes);
+      const int e = elems[gi - tb];
+      const int64_t o = off[e];
+      const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
       for (int i = threadIdx.x; i < Nh * CH; i += blockDim.x) {
         const int n = i / CH, cc = i % CH;
         us[i] = c0 + cc < nrhs ? u[(o + n) * nrhs + c0 + cc] : make_float2(0.f, 0.f);
@@ -556,16 +650,25 @@ __global__ void __launch_bounds__(512, 1) k_project_tab(const int32_t* __restric
       __syncthreads();
       for (int node = warp; node < nodes; node += nw) {
         float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ax2 = 0.f, ay2 = 0.f, ax3 = 0.f, ay3 = 0.f;
-        const int q1 = sptr[node + 1];
-#pragma unroll 2
-        for (int q = sptr[node] + g; q < q1; q += G) {
-          const float4 w = sw[q];
-          const float2 uv = us[(int)sn[q] * CH + c];
+        auto mac = [&](const float4 w, const float2 uv) {
           ax0 = fmaf(w.x, uv.x, ax0); ay0 = fmaf(w.x, uv.y, ay0);
           ax1 = fmaf(w.y, uv.x, ax1); ay1 = fmaf(w.y, uv.y, ay1);
           ax2 = fmaf(w.z, uv.x, ax2); ay2 = fmaf(w.z, uv.y, ay2);
           ax3 = fmaf(w.w, uv.x, ax3); ay3 = fmaf(w.w, uv.y, ay3);
+        };
+        const int q1 = sptr[node + 1];
+        int q = sptr[node] + g;
+        // four entries per step: their table and u reads are issued together
+        for (; q + 3 * G < q1; q += 4 * G) {
+          const float4 w0 = sw[q], w1 = sw[q + G], w2 = sw[q + 2 * G], w3 = sw[q + 3 * G];
+          const int n0 = sn[q], n1 = sn[q + G], n2 = sn[q + 2 * G], n3 = sn[q + 3 * G];
+          const float2 u0 = us[n0 * CH + c], u1 = us[n1 * CH + c], u2 = us[n2 * CH + c], u3 = us[n3 * CH + c];
+          mac(w0, u0);
+          mac(w1, u1);
+          mac(w2, u2);
+          mac(w3, u3);
         }
+        for (; q < q1; q += G) mac(sw[q], us[(int)sn[q] * CH + c]);
 #pragma unroll
         for (int o2 = CH; o2 < 32; o2 <<= 1) {
           ax0 += __shfl_xor_sync(0xffffffffu, ax0, o2); ay0 += __shfl_xor_sync(0xffffffffu, ay0, o2);
@@ -1129,6 +1232,130 @@ __global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, 
 }
 
 
+// Interpolation of many right-hand sides from shared-memory tables (complex64):
+// one launch for all types, each CTA a contiguous range of the elements listed
+// type by type (walked forwards and backwards in turn, right-hand-side chunks
+// outermost so that the grid planes being read stay in L2).  On entering a
+// type its weights Pi ([s][n] float4) and the bases' first box nodes are
+// copied into shared memory; per element and chunk of CH right-hand sides the
+// box of grid potentials is staged as [psi][node][CH + 1]; a warp takes four
+// bases at a time, lanes = CH right-hand sides x 4 bases, and walks the S
+// stencil points with every read from shared memory.  y = v - (c_A sum_xyz +
+// c_phi sum_phi).
+__host__ __device__ inline size_t itp_box_offset(int S, int Nh, int nodes) {
+  return ((size_t)16 * S * Nh + 4 * ((size_t)Nh + S + nodes) + 15) / 16 * 16;
+}
+template <int CH>
+__host__ __device__ inline size_t itp_smem_bytes(int S, int Nh, int nodes) {
+  return itp_box_offset(S, Nh, nodes) + (size_t)8 * 4 * nodes * (CH + 1);
+}
+size_t interp_tab_smem(int S, int Nh, int nodes) { return itp_smem_bytes<8>(S, Nh, nodes); }
+
+template <int CH>
+__global__ void __launch_bounds__(512, 1) k_interp_tab(const ItpTypeDev* __restrict__ types, int64_t total, int S,
+                                                       int n1, int o1lo, const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ boxorg, int nrhs,
+                                                       const float2* __restrict__ grid, int Nx, int Ny, int Nz,
+                                                       float cAr, float cAi, float cPr, float cPi,
+                                                       const float2* __restrict__ v, float2* __restrict__ y) {
+  static_assert(CH == 8, "lanes: 8 right-hand sides x 4 bases");
+  constexpr int LD = CH + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int c = lane % CH, g = lane / CH;
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  const int64_t i0 = (int64_t)blockIdx.x * total / gridDim.x, i1 = (int64_t)(blockIdx.x + 1) * total / gridDim.x;
+  float2 cA, cP;
+  cA.x = cAr; cA.y = cAi; cP.x = cPr; cP.y = cPi;
+  int t = -1;
+  int64_t tb = 0, te = 0;
+  int Nh = 0, nodes = 0, by = 1, bz = 1;
+  const int32_t* elems = nullptr;
+  const float4* sPi = reinterpret_cast<const float4*>(smem_raw);
+  int* nbt = nullptr;
+  int* soff = nullptr;
+  int* goff = nullptr;
+  float2* box = nullptr;
+  int pass = 0;
+  for (int c0 = 0; c0 < nrhs; c0 += CH, ++pass) {
+    for (int64_t k = 0; k < i1 - i0; ++k) {
+      const int64_t gi = (pass & 1) ? i1 - 1 - k : i0 + k;
+      if (gi < tb || gi >= te) {
+        t = 0;
+        tb = 0;
+        te = types[0].ne;
+        while (gi >= te) {
+          ++t;
+          tb = te;
+          te += types[t].ne;
+        }
+        const ItpTypeDev ty = types[t];
+        Nh = ty.Nh;
+        by = ty.by;
+        bz = ty.bz;
+        nodes = ty.bx * by * bz;
+        elems = ty.elems;
+        nbt = reinterpret_cast<int*>(smem_raw + (size_t)16 * S * Nh);
+        soff = nbt + Nh;
+        goff = soff + S;
+        box = reinterpret_cast<float2*>(smem_raw + itp_box_offset(S, Nh, nodes));
+        __syncthreads();   // the previous type's tables are no longer read
+        for (int i = threadIdx.x; i < S * Nh; i += blockDim.x)
+          reinterpret_cast<float4*>(smem_raw)[i] = __ldg(reinterpret_cast<const float4*>(ty.Pi) + i);
+        for (int n = threadIdx.x; n < Nh; n += blockDim.x)
+          nbt[n] = ((ty.anc[3 * n] + o1lo) * by + (ty.anc[3 * n + 1] + o1lo)) * bz + (ty.anc[3 * n + 2] + o1lo);
+        for (int sp = threadIdx.x; sp < S; sp += blockDim.x) {
+          const int ix = sp % n1, iy = (sp / n1) % n1, iz = sp / (n1 * n1);
+          soff[sp] = (ix * by + iy) * bz + iz;
+        }
+        for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
+          const int lz = i % bz, ly = (i / bz) % by, lx = i / (by * bz);
+          goff[i] = (lx * Ny + ly) * Nz + lz;
+        }
+        __syncthreads();
+      }
+      const SmallDiv dnodes(nodes);
+      const int e = elems[gi - tb];
+      const int64_t o = off[e];
+      const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
+      // stage: consecutive threads take consecutive nodes of one (psi, c) plane
+      for (int i = threadIdx.x; i < 4 * CH * nodes; i += blockDim.x) {
+        int pc, node;
+        dnodes(i, pc, node);
+        const int q = pc / CH, cc = pc % CH;
+        float2 val = make_float2(0.f, 0.f);
+        if (c0 + cc < nrhs) val = grid[((int64_t)q * nrhs + c0 + cc) * gstride + gbase + goff[node]];
+        box[((size_t)q * nodes + node) * LD + cc] = val;
+      }
+      __syncthreads();
+      for (int n0 = 4 * warp; n0 < Nh; n0 += 4 * nw) {
+        const int n = n0 + g;
+        if (n < Nh) {
+          const int nb = nbt[n];
+          float2 sA = make_float2(0.f, 0.f), sP = make_float2(0.f, 0.f);
+#pragma unroll 3
+          for (int sp = 0; sp < S; ++sp) {
+            const float4 w = sPi[sp * Nh + n];
+            const float2* b = box + (size_t)(nb + soff[sp]) * LD + c;
+            const float2 f0 = b[0], f1 = b[(size_t)nodes * LD], f2 = b[(size_t)2 * nodes * LD],
+                         f3 = b[(size_t)3 * nodes * LD];
+            sA.x = fmaf(w.x, f0.x, fmaf(w.y, f1.x, fmaf(w.z, f2.x, sA.x)));
+            sA.y = fmaf(w.x, f0.y, fmaf(w.y, f1.y, fmaf(w.z, f2.y, sA.y)));
+            sP.x = fmaf(w.w, f3.x, sP.x);
+            sP.y = fmaf(w.w, f3.y, sP.y);
+          }
+          if (c0 + c < nrhs) {
+            const float2 yff = cadd(cmul(cA, sA), cmul(cP, sP));
+            const int64_t idx = (o + n) * nrhs + c0 + c;
+            y[idx] = csub(v[idx], yff);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Interpolation of many right-hand sides (complex64), lanes over right-hand
 // sides: one CTA per element; per chunk of CH right-hand sides the element's box
 // of grid potentials is staged as [psi][node][c] (c fastest, node stride CH + 1
@@ -1655,14 +1882,17 @@ cudaError_t kernels_init(DevArray& a) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_interp_rhs<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInterpRhsSmemMax);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_interp_tab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInterpTabSmemMax);
+  if (e != cudaSuccess) return e;
   e = tc_gemm_init();
   if (e != cudaSuccess) return e;
   return near_tc_init(a);
 }
 
 // Launch schedules of the projection and the interpolation (the grid-stage
-// tuner's choices).  Projection, one right-hand side: variant v gives 4 >> v
-// lanes per stencil-box node (4, 2, 1; CTAs of up to 512 threads); several:
+// tuner's choices).  Projection, one right-hand side: variant v < 3 gives 4 >> v
+// lanes per stencil-box node (4, 2, 1; CTAs of up to 512 threads), variant 3
+// (complex64) reads the type's stencil tables (k_project_g1); several:
 // variant 0 stages four right-hand sides per pass (RC = 4), variant 1 one,
 // variant 2 (eight or more, when the array has a box buffer) is the two-pass
 // form: each element writes its box, then every grid point sums the boxes
@@ -1672,20 +1902,16 @@ cudaError_t kernels_init(DevArray& a) {
 // Interpolation, one right-hand side: 4 >> v lanes per basis; eight or more:
 // variant 0 takes eight right-hand sides per thread (CR = 8), variant 1 one,
 // variant 2 (complex64) puts eight right-hand sides on the lanes of a warp
-// (k_interp_rhs).
-// The table-driven projection applies to a type when its tables, u chunk and
+// (k_interp_rhs), variant 3 (complex64, where the weights fit) does the same
+// from shared-memory weights in one launch for all types (k_interp_tab).
+size_t project_tab_smem(int E, int nodes, int Nh) { return prj_smem_bytes<8>(E, nodes, Nh); }
+
+// The table-driven projection applies when every type's tables, u chunk and
 // box fit in shared memory (complex64, eight or more right-hand sides).
 template <typename R>
-static bool project_tab_ok(const DevArray& a, const DevPrec<R>& p, int t, int nrhs) {
-  if (sizeof(R) != 4 || nrhs < 8 || (size_t)t >= p.prj_tab.size() || p.prj_tab[t] == nullptr) return false;
-  const int nodes = a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
-  return prj_smem_bytes<8>(a.inv_len[t], nodes, (int)a.Nh[t]) <= kPrjSmemMax;
-}
-template <typename R>
 static bool project_tab_all(const DevArray& a, const DevPrec<R>& p, int nrhs) {
-  for (int64_t t = 0; t < a.n_types; ++t)
-    if (a.n_of_type[t] > 0 && !project_tab_ok(a, p, (int)t, nrhs)) return false;
-  return a.n_types > 0;
+  (void)a;
+  return sizeof(R) == 4 && nrhs >= 8 && p.prj_types != nullptr && p.prj_smem <= kPrjSmemMax && p.prj_total > 0;
 }
 
 template <typename R>
@@ -1693,20 +1919,27 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
                            typename V2<R>::T* grid, void* boxbuf, cudaStream_t cs, int& nl) {
   typedef typename V2<R>::T C;
   const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
+  if constexpr (sizeof(R) == 4) {
+    if (var == 3 && project_tab_all(a, p, nrhs)) {
+      int dev = 0, sms = 148;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int ctas = (int)std::min<int64_t>(p.prj_total, sms);
+      k_project_tab<8><<<ctas, 512, p.prj_smem, cs>>>(p.prj_types, p.prj_total, a.off, a.boxorg, nrhs, u, Nx, Ny,
+                                                     Nz, grid);
+      ++nl;
+      return;
+    }
+  }
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
     const int Nh = (int)a.Nh[t];
     const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
     const int pnodes = bx * by * bz;
     if constexpr (sizeof(R) == 4) {
-      if (var == 3 && project_tab_ok(a, p, (int)t, nrhs)) {
-        const int E = a.inv_len[t];
-        int dev = 0, sms = 148;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int ctas = (int)std::min<int64_t>(a.n_of_type[t], sms);
-        k_project_tab<8><<<ctas, 512, prj_smem_bytes<8>(E, pnodes, Nh), cs>>>(
-            a.elems[t], (int)a.n_of_type[t], Nh, bx, by, bz, a.inv_ptr[t],
-            static_cast<const unsigned char*>(p.prj_tab[t]), E, a.off, a.boxorg, nrhs, u, Nx, Ny, Nz, grid);
+      if (var == 3 && nrhs == 1 && (size_t)t < p.prj_tab.size()) {
+        k_project_g1<<<(unsigned)a.n_of_type[t], 256, sizeof(float2) * Nh, cs>>>(
+            a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], static_cast<const unsigned char*>(p.prj_tab[t]), a.inv_len[t],
+            a.off, a.boxorg, reinterpret_cast<const float2*>(u), Nx, Ny, Nz, reinterpret_cast<float2*>(grid));
         ++nl;
         continue;
       }
@@ -1735,6 +1968,14 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
   }
 }
 
+// the table-driven interpolation: complex64, eight or more right-hand sides,
+// every type's weights and box within the shared-memory limit
+template <typename R>
+static bool interp_tab_ok(const DevPrec<R>& p, int nrhs) {
+  return sizeof(R) == 4 && nrhs >= 8 && p.itp_types != nullptr && p.itp_smem <= kInterpTabSmemMax &&
+         p.prj_total > 0;
+}
+
 // shared memory of k_interp_rhs<8> for type t: the box [psi][node][9], the
 // stencil offsets and the node offsets
 static size_t interp_rhs_smem(const DevArray& a, int t) {
@@ -1747,6 +1988,18 @@ static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int n
                           const typename V2<R>::T* v, typename V2<R>::T* y, cudaStream_t cs, int& nl) {
   typedef typename V2<R>::T C;
   const int Nx = a.grid[0], Ny = a.grid[1], Nz = a.grid[2];
+  if constexpr (sizeof(R) == 4) {
+    if (var == 3 && interp_tab_ok(p, nrhs)) {
+      int dev = 0, sms = 148;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int ctas = (int)std::min<int64_t>(p.prj_total, sms);
+      k_interp_tab<8><<<ctas, 512, p.itp_smem, cs>>>(p.itp_types, p.prj_total, a.S, a.n1, a.o1lo, a.off, a.boxorg,
+                                                    nrhs, grid, Nx, Ny, Nz, (float)a.cA[0], (float)a.cA[1],
+                                                    (float)a.cphi[0], (float)a.cphi[1], v, y);
+      ++nl;
+      return;
+    }
+  }
   const size_t slim = 96 * 1024;
   for (int64_t t = 0; t < a.n_types; ++t) {
     if (a.n_of_type[t] == 0) continue;
@@ -1790,7 +2043,7 @@ static void interp_launch(int var, const DevArray& a, const DevPrec<R>& p, int n
 template <typename R>
 static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int nrhs, Work& w, cudaStream_t st) {
   typedef typename V2<R>::T C;
-  const int np = nrhs == 1 ? 3 : 4, ni = 3;
+  const int np = 4, ni = nrhs == 1 ? 3 : 4;
   std::pair<int, int> best = {0, 0};
   const size_t spec_elems = (size_t)4 * nrhs * a.grid[0] * a.fft[1] * a.fft[2];
   if (spec_elems < (size_t)a.N * nrhs) return best;
@@ -1819,12 +2072,14 @@ static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int n
     // variants a product could not run are not timed (the two-pass form without
     // a box buffer, the table form where a type's tables do not fit)
     if (nrhs > 1 && ((var == 2 && w.boxbuf == nullptr) || (var == 3 && !project_tab_all(a, p, nrhs)))) continue;
+    if (nrhs == 1 && var == 3 && (sizeof(R) != 4 || (int64_t)p.prj_tab.size() != a.n_types)) continue;
     tp[var] = timeit([&] { project_launch<R>(var, a, p, nrhs, u, grid, w.boxbuf, st, nl); });
     if (tp[var] >= 0 && (tp[best.first] < 0 || tp[var] < tp[best.first])) best.first = var;
   }
   for (int var = 0; var < ni; ++var) {
     int nl = 0;
     if (nrhs > 1 && var == 2 && (sizeof(R) != 4 || nrhs < 8)) continue;   // the right-hand-side-lane form: complex64, 8+
+    if (nrhs > 1 && var == 3 && !interp_tab_ok(p, nrhs)) continue;
     ti[var] = timeit([&] { interp_launch<R>(var, a, p, nrhs, grid, v, yscr, st, nl); });
     if (ti[var] >= 0 && (ti[best.second] < 0 || ti[var] < ti[best.second])) best.second = var;
   }

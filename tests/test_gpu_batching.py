@@ -84,7 +84,7 @@ def test_batch_rejects_an_array_twice(ctx):
         la.close()
 
 
-@pytest.mark.parametrize("sched", ["0,0", "1,1", "2,2", "0,2", "2,0"])
+@pytest.mark.parametrize("sched", ["0,0", "1,1", "2,2", "0,2", "2,0", "3,0", "3,2"])
 def test_every_grid_schedule_one_rhs(ctx, monkeypatch, sched):
     monkeypatch.setenv("MACROAIM_GRID_SCHED", sched)
     g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
@@ -99,7 +99,7 @@ def test_every_grid_schedule_one_rhs(ctx, monkeypatch, sched):
         la.close()
 
 
-@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0", "2,0", "2,1", "3,0", "3,1", "0,2", "3,2"])
+@pytest.mark.parametrize("sched", ["0,0", "1,1", "0,1", "1,0", "2,0", "2,1", "3,0", "3,1", "0,2", "3,2", "0,3", "3,3"])
 @pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C128])
 def test_every_grid_schedule_64_rhs(ctx, monkeypatch, sched, prec):
     monkeypatch.setenv("MACROAIM_GRID_SCHED", sched)
@@ -119,7 +119,7 @@ def test_every_grid_schedule_64_rhs(ctx, monkeypatch, sched, prec):
 
 
 @pytest.mark.parametrize("nrhs", [8, 12, 20])
-@pytest.mark.parametrize("sched", ["3,0", "0,2", "3,2"])
+@pytest.mark.parametrize("sched", ["3,0", "0,2", "3,2", "3,3"])
 def test_table_projection_ragged_chunks(ctx, monkeypatch, nrhs, sched):
     """Table-driven projection (projection schedule 3) and the
     right-hand-side-lane interpolation (interpolation schedule 2), eight
