@@ -529,7 +529,7 @@ mm_array::~mm_array() {
                   (void*)da.nfb_perm, (void*)da.nfb_pa, (void*)da.nfb_pb})
     if (q) cudaFree(q);
   for (void* q : {da.nfg_dev, (void*)da.nfg_poff, (void*)da.nfg_prow, (void*)da.nfe_ptr, (void*)da.nfe_pair,
-                  (void*)da.nfe_qb, (void*)da.nfb_tperm})
+                  (void*)da.nfe_qb, (void*)da.nfe_order, (void*)da.nfb_tperm})
     if (q) cudaFree(q);
   if (da.side) cudaStreamDestroy(da.side);
   if (da.chain) cudaStreamDestroy(da.chain);
@@ -1020,6 +1020,11 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
             qb[i].y = ah.off[allp[epair[i]].y];
           }
           da.nfe_qb = dev_upload(qb.data(), qb.size(), acc);
+          std::vector<int32_t> order(n_elem);
+          for (int64_t e = 0; e < n_elem; ++e) order[e] = (int32_t)e;
+          std::stable_sort(order.begin(), order.end(),
+                           [&](int32_t x, int32_t y) { return ah.type_of[x] < ah.type_of[y]; });
+          da.nfe_order = dev_upload(order.data(), order.size(), acc);
           da.nfg_prows = rows;
           da.nfg_prow = dev_upload(prow.data(), prow.size(), acc);
           da.nfe_ptr = dev_upload(eptr.data(), eptr.size(), acc);

@@ -218,6 +218,7 @@ struct DevArray {
   int32_t* nfe_ptr = nullptr;           // per element: its pairs as row element (n_elem + 1) ...
   int32_t* nfe_pair = nullptr;          // ... and the pair indices
   longlong2* nfe_qb = nullptr;          // per entry of nfe_pair: (block q, unknown offset of the column element)
+  int32_t* nfe_order = nullptr;         // element ids sorted by type, then id (the direct near field's unit order)
   int32_t* nfb_tperm = nullptr;         // per type: offset of its anchor ordering in nfb_perm
   int32_t* nfb_perm = nullptr;          // per type (concatenated): sorted position -> local basis
   int32_t* nfb_pa = nullptr;            // per block: offset of its row type's ordering in nfb_perm

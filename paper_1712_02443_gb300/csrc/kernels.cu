@@ -887,12 +887,17 @@ __device__ __forceinline__ void warp_fft_reg(const C* a, C* dst, const C* __rest
       w.x = 1;
       w.y = 0;
     }
+    // sum (lower lane) or difference (upper lane) of the pair as one signed
+    // multiply-add per component: s y + o with s = +1 or -1
+    const Rr sg = up ? Rr(-1) : Rr(1);
 #pragma unroll
     for (int k2 = 0; k2 < RR; ++k2) {
       C o;
       o.x = __shfl_xor_sync(0xffffffffu, y[k2].x, h);
       o.y = __shfl_xor_sync(0xffffffffu, y[k2].y, h);
-      const C sd = up ? csub(o, y[k2]) : cadd(y[k2], o);
+      C sd;
+      sd.x = fmx(sg, y[k2].x, o.x);
+      sd.y = fmx(sg, y[k2].y, o.y);
       y[k2] = h == 1 ? sd : cmul(sd, w);
     }
   }

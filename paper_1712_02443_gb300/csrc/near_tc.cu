@@ -150,7 +150,10 @@ __device__ __forceinline__ Unit decode_unit(int64_t t, const int64_t* gpre, int 
 }
 
 // Direct form: unit t = (row element a, 128-row tile mt, NC right-hand-side
-// columns from c0), tiles fastest-varying last.
+// columns from c0), tiles fastest-varying last; the elements are taken in the
+// order aorder (by type, then by index), so that the CTAs working at one time
+// read the blocks of one row type (they stay in L2) and the u of a band of
+// neighbouring elements.
 struct DUnit {
   int a, mt, Na, p0, p1;
   int64_t c0, offa;
@@ -158,13 +161,15 @@ struct DUnit {
 };
 
 template <int NC>
-__device__ __forceinline__ DUnit decode_dunit(int64_t t, int nmt, int nnt, const int32_t* __restrict__ type_of,
+__device__ __forceinline__ DUnit decode_dunit(int64_t t, int nmt, int nnt, const int32_t* __restrict__ aorder,
+                                              const int32_t* __restrict__ type_of,
                                               const int64_t* __restrict__ tbase, const int32_t* __restrict__ eptr,
                                               const int64_t* __restrict__ off) {
   DUnit un;
   const int64_t per = (int64_t)nmt * nnt;
-  un.a = (int)(t / per);
-  const int64_t r = t - (int64_t)un.a * per;
+  const int64_t ai = t / per;
+  un.a = aorder[ai];
+  const int64_t r = t - ai * per;
   un.mt = (int)(r / nnt);
   un.c0 = (r - (int64_t)un.mt * nnt) * NC;
   const int ta = type_of[un.a];
@@ -548,7 +553,8 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
     const __grid_constant__ CUtensorMap tmA, int rows_total, const int32_t* __restrict__ arow,
     const int32_t* __restrict__ bnb, int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist,
     const int32_t* __restrict__ perm, const int32_t* __restrict__ bpb, const int32_t* __restrict__ eptr,
-    const longlong2* __restrict__ qb, const int32_t* __restrict__ type_of, const int64_t* __restrict__ tbase,
+    const longlong2* __restrict__ qb, const int32_t* __restrict__ aorder, const int32_t* __restrict__ type_of,
+    const int64_t* __restrict__ tbase,
     const int32_t* __restrict__ tperm, const int64_t* __restrict__ off, int nrhs, int64_t units,
     const float2* __restrict__ u, float2* __restrict__ v, uint64_t wait_ns, int stall) {
   typedef NearTcCfg<NC, STAGES, RAWD> Cfg;
@@ -596,7 +602,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-        const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+        const DUnit un = decode_dunit<NC>(t, nmt, nnt, aorder, type_of, tbase, eptr, off);
         if (!un.live) continue;
         KCursor c;
         for (c.start(un.p0, un.p1, un.mt, nmt, qb, tptr); c.valid(); c.advance(), ++it) {
@@ -629,7 +635,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
       uint32_t it = 0, lt = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-        const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+        const DUnit un = decode_dunit<NC>(t, nmt, nnt, aorder, type_of, tbase, eptr, off);
         const int nk = dunit_tiles(un, nmt, qb, tptr);
         if (nk == 0) continue;
         const uint32_t b = lt & 1, ub = lt >> 1;
@@ -681,7 +687,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
     uint32_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-      const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+      const DUnit un = decode_dunit<NC>(t, nmt, nnt, aorder, type_of, tbase, eptr, off);
       const int nk = dunit_tiles(un, nmt, qb, tptr);
       if (nk == 0) continue;   // the same for every gather thread
       KCursor pre;
@@ -761,7 +767,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc_direct(
     uint32_t lt = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-      const DUnit un = decode_dunit<NC>(t, nmt, nnt, type_of, tbase, eptr, off);
+      const DUnit un = decode_dunit<NC>(t, nmt, nnt, aorder, type_of, tbase, eptr, off);
       const int nk = dunit_tiles(un, nmt, qb, tptr);
       if (nk == 0) continue;
       const int m = un.mt * kRowsT + 32 * qd + lane;
@@ -845,7 +851,7 @@ template <int NC, int STAGES, int RAWD>
 cudaError_t near_tc_direct_launch_t(const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u, float2* v,
                                     cudaStream_t st) {
   if (nrhs % 2 != 0 || (reinterpret_cast<uintptr_t>(u) & 15) != 0 || (reinterpret_cast<uintptr_t>(v) & 15) != 0 ||
-      a.nfe_qb == nullptr)
+      a.nfe_qb == nullptr || a.nfe_order == nullptr)
     return cudaErrorInvalidValue;
   const int64_t nnt = (nrhs + NC - 1) / NC;
   const int64_t units = a.n_elem * (int64_t)a.nfb_nmt128 * nnt;
@@ -858,7 +864,7 @@ cudaError_t near_tc_direct_launch_t(const DevArray& a, const DevPrec<float>& p, 
   typedef NearTcCfg<NC, STAGES, RAWD> Cfg;
   k_near_tc_direct<NC, STAGES, RAWD><<<ctas, kThreadsNT, Cfg::Smem, st>>>(
       p.nfb_tmap, a.nfb_tc_rows, a.nfb_arow, a.nfb_nb, a.nfb_nmt128, a.nfb_tptr128, a.nfb_tlist128, a.nfb_perm,
-      a.nfb_pb, a.nfe_ptr, a.nfe_qb, a.type_of, a.tbase, a.nfb_tperm, a.off, nrhs, units, u, v, wait_ns,
+      a.nfb_pb, a.nfe_ptr, a.nfe_qb, a.nfe_order, a.type_of, a.tbase, a.nfb_tperm, a.off, nrhs, units, u, v, wait_ns,
       stall_ms > 0 ? 1 : 0);
   return cudaGetLastError();
 }
@@ -959,7 +965,7 @@ __global__ void __launch_bounds__(256) k_near_reduce(const int32_t* __restrict__
 }
 
 bool near_tc_direct_ok(const DevArray& a, int nrhs, const void* u, const void* v) {
-  return nrhs % 2 == 0 && a.nfe_qb != nullptr && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
+  return nrhs % 2 == 0 && a.nfe_qb != nullptr && a.nfe_order != nullptr && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
          (reinterpret_cast<uintptr_t>(v) & 15) == 0;
 }
 
