@@ -461,13 +461,18 @@ def run_ours(args, rank, world, local):
         # the block near field reads an L2-resident operator: its arithmetic bounds it
         alg_flops = 8.0 * info["nnz_near"]          # one complex multiply-add per non-zero
         achieved_tf = alg_flops / avg_s / 1e12
+    # DRAM bytes per launch of the dominant kernel from the committed ncu capture
+    # (profiles/traffic.json), only while the library sources are the ones it
+    # was taken on and, for the near field, for the kernel shape chosen here
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         from paper_1712_02443_gb300.build import _digest
-        if tr.get("digest") == _digest() and dom in tr.get("per_launch_bytes", {}):
-            traffic = tr["per_launch_bytes"][dom]
+        ent = tr.get("per_launch_bytes", {}).get(dom) if tr.get("digest") == _digest() else None
+        if ent is not None and (dom != "near" or (near_shape is not None and
+                                                  list(ent.get("shape", [])) == list(near_shape))):
+            traffic = ent["bytes"]
     except Exception:
         pass
     gpu_launches = int(round(launches_per_step * args.steps))

@@ -1337,6 +1337,10 @@ __global__ void __launch_bounds__(512, 1) k_interp_tab(const ItpTypeDev* __restr
         const int n = n0 + g;
         if (n < Nh) {
           const int nb = nbt[n];
+          // v of this output is loaded first, so that its latency passes during the sums
+          const bool live = c0 + c < nrhs;
+          const int64_t idx = (o + n) * nrhs + c0 + c;
+          const float2 vv = live ? v[idx] : make_float2(0.f, 0.f);
           float2 sA = make_float2(0.f, 0.f), sP = make_float2(0.f, 0.f);
 #pragma unroll 3
           for (int sp = 0; sp < S; ++sp) {
@@ -1349,11 +1353,7 @@ __global__ void __launch_bounds__(512, 1) k_interp_tab(const ItpTypeDev* __restr
             sP.x = fmaf(w.w, f3.x, sP.x);
             sP.y = fmaf(w.w, f3.y, sP.y);
           }
-          if (c0 + c < nrhs) {
-            const float2 yff = cadd(cmul(cA, sA), cmul(cP, sP));
-            const int64_t idx = (o + n) * nrhs + c0 + c;
-            y[idx] = csub(v[idx], yff);
-          }
+          if (live) y[idx] = csub(vv, cadd(cmul(cA, sA), cmul(cP, sP)));
         }
       }
       __syncthreads();
@@ -1830,9 +1830,14 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
     return best;
   }
   float best_ms = 1e30f;
+  // with 16 or more right-hand sides and the tensor-core forms available, the
+  // CUDA-core shapes are not timed (4-5x slower there: 6.3-7.9 ms against 1.5 ms
+  // per product at 32x32, 64 RHS; timing them cost 0.23 s of the first product)
+  const bool skip_cuda_cores = nrhs >= 16 && near_shape_ok<R>(7, a, p, nrhs, u, scratch, np);
   for (int tn = 0; tn < kNearShapes; ++tn)
     for (int ks : {1, 2, 4}) {
       if (!near_shape_ok<R>(tn, a, p, nrhs, u, scratch, np) || (tn >= 5 && ks > 1)) continue;   // tensor-core shapes: no k split
+      if (skip_cuda_cores && tn < 5) continue;
       int nl = 0;
       auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, np); };
       run();
