@@ -21,7 +21,7 @@ LIB = os.path.join(LIBDIR, "libmacroaim.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SRC = ["geom.cpp", "fill.cpp", "aim_setup.cpp"]
-CU_SRC = ["kernels.cu", "tc_gemm.cu", "near_tc.cu", "drive.cu", "dense_gpu.cu", "solver.cu", "post.cu", "capi.cu", "server.cu"]
+CU_SRC = ["kernels.cu", "tc_gemm.cu", "near_tc.cu", "drive.cu", "dense_gpu.cu", "fill_gpu.cu", "solver.cu", "post.cu", "capi.cu", "server.cu"]
 
 
 def _nvcc() -> str:

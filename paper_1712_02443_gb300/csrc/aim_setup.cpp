@@ -25,6 +25,7 @@
 #include <unordered_map>
 
 #include "aim_setup.h"
+#include "fill_gpu.h"
 
 namespace mm {
 
@@ -449,16 +450,22 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
   }
   // fill each distinct block: exact Galerkin entries minus the grid part, near
   // pairs only; a block computed by an earlier array with the same types and
-  // AIM options is taken from the row type's cache
+  // AIM options is taken from the row type's cache.  Patterns first (host);
+  // the values on the GPU for device contexts (fill_gpu.cu), else on the host.
+  auto cache_key = [&](size_t id) {
+    const auto& key = block_keys[id];
+    const TypeModel* tb = types[key[1]];
+    return NearBlockKey{tb, {key[2], key[3], key[4]}, o.h, {o.phase.x, o.phase.y, o.phase.z}, o.order, o.n_nf};
+  };
+  std::vector<size_t> todo;
   for (size_t id = 0; id < blocks.size(); ++id) {
     auto key = block_keys[id];
     const TypeModel* ta = types[key[0]];
-    const TypeModel* tb = types[key[1]];
     const TypeAim &A = ah.tai[key[0]], &B = ah.tai[key[1]];
-    int64_t Na = ta->Nh, Nb = tb->Nh;
+    int64_t Na = ta->Nh, Nb = types[key[1]]->Nh;
     int64_t dL[3] = {key[2], key[3], key[4]};
     Block& blk = blocks[id];
-    NearBlockKey ck{tb, {dL[0], dL[1], dL[2]}, o.h, {o.phase.x, o.phase.y, o.phase.z}, o.order, o.n_nf};
+    const NearBlockKey ck = cache_key(id);
     {
       std::lock_guard<std::mutex> lk(ta->nf_mu);
       auto it = ta->nf_cache.find(ck);
@@ -470,34 +477,63 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
       }
     }
     blk.ptr.assign(Na + 1, 0);
-    std::vector<std::vector<int32_t>> cols(Na);
-    bool any = false;
-    for (int64_t m = 0; m < Na; ++m)
+    std::vector<int32_t> cols;
+    for (int64_t m = 0; m < Na; ++m) {
       for (int64_t n = 0; n < Nb; ++n) {
         int64_t cheb = 0;
         for (int a = 0; a < 3; ++a)
           cheb = std::max<int64_t>(cheb, std::llabs(A.anc[3 * m + a] - (B.anc[3 * n + a] + dL[a])));
-        if (cheb <= nnf) {
-          cols[m].push_back((int32_t)n);
-          any = true;
-        }
+        if (cheb <= nnf) cols.push_back((int32_t)n);
       }
-    if (!any) {   // no near pairs: remembered as an empty block
+      blk.ptr[m + 1] = (int64_t)cols.size();
+    }
+    if (cols.empty()) {   // no near pairs: remembered as an empty block
       blk.ptr.clear();
       std::lock_guard<std::mutex> lk(ta->nf_mu);
       ta->nf_cache.emplace(ck, std::make_shared<NearBlockData>());
       continue;
     }
+    blk.col = std::move(cols);
+    todo.push_back(id);
+  }
+  std::vector<char> done(blocks.size(), 0);
+  if (o.device >= 0 && !todo.empty()) {
+    std::vector<NearFillJob> jobs;
+    for (size_t id : todo) {
+      const auto& key = block_keys[id];
+      NearFillJob jb;
+      jb.ma = &types[key[0]]->eq;
+      jb.mb = &types[key[1]]->eq;
+      jb.rel = block_rel[id];
+      jb.A = &ah.tai[key[0]];
+      jb.B = &ah.tai[key[1]];
+      for (int a = 0; a < 3; ++a) jb.dL[a] = key[2 + a];
+      jb.ptr = &blocks[id].ptr;
+      jb.col = &blocks[id].col;
+      jb.val = &blocks[id].val;
+      jobs.push_back(jb);
+    }
+    std::string msg;
+    if (fill_near_blocks_gpu(jobs, H.v, H.R, so, ah.c_A, ah.c_phi, em.k, o.device, msg))
+      for (size_t id : todo) done[id] = 1;
+  }
+  for (size_t id : todo) {
+    if (done[id]) continue;
+    auto key = block_keys[id];
+    const TypeModel* ta = types[key[0]];
+    const TypeModel* tb = types[key[1]];
+    const TypeAim &A = ah.tai[key[0]], &B = ah.tai[key[1]];
+    int64_t Na = ta->Nh, Nb = tb->Nh;
+    int64_t dL[3] = {key[2], key[3], key[4]};
+    Block& blk = blocks[id];
     std::vector<cd> G;
     fill_efie(ta->eq, tb->eq, block_rel[id], em, G);
     for (auto& x : G) x *= ah.c_A;   // G^(E^,J^) = -j w mu0 Lmat
-    for (int64_t m = 0; m < Na; ++m) blk.ptr[m + 1] = blk.ptr[m] + (int64_t)cols[m].size();
-    blk.col.resize(blk.ptr[Na]);
     blk.val.resize(blk.ptr[Na]);
     parallel_for(Na, em.nthreads, [&](int64_t m0, int64_t m1) {
       for (int64_t m = m0; m < m1; ++m) {
-        int64_t p = blk.ptr[m];
-        for (int32_t n : cols[m]) {
+        for (int64_t p = blk.ptr[m]; p < blk.ptr[m + 1]; ++p) {
+          const int32_t n = blk.col[p];
           int64_t da[3];
           for (int a = 0; a < 3; ++a) da[a] = A.anc[3 * m + a] - (B.anc[3 * n + a] + dL[a]);
           cd vA(0, 0), vP(0, 0);
@@ -512,18 +548,19 @@ void build_array_host(ArrayHost& ah, const std::vector<const TypeModel*>& types,
             vA += Pm[4 * s] * hx + Pm[4 * s + 1] * hy + Pm[4 * s + 2] * hz;
             vP += Pm[4 * s + 3] * hp;
           }
-          blk.col[p] = n;
           blk.val[p] = G[m * Nb + n] - (ah.c_A * vA + ah.c_phi * vP);
-          ++p;
         }
       }
     });
+  }
+  for (size_t id : todo) {
+    const TypeModel* ta = types[block_keys[id][0]];
     auto d = std::make_shared<NearBlockData>();
-    d->ptr = blk.ptr;
-    d->col = blk.col;
-    d->val = blk.val;
+    d->ptr = blocks[id].ptr;
+    d->col = blocks[id].col;
+    d->val = blocks[id].val;
     std::lock_guard<std::mutex> lk(ta->nf_mu);
-    ta->nf_cache.emplace(ck, std::move(d));
+    ta->nf_cache.emplace(cache_key(id), std::move(d));
   }
   ah.nnz_near = 0;
   for (int64_t e = 0; e < ne; ++e)

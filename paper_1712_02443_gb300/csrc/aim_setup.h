@@ -13,6 +13,7 @@ struct AimOpts {
   int n_nf;
   Vec3 phase;
   int64_t csr_max_nnz = -1;   // assemble the expanded near-field CSR up to this many non-zeros (-1: always)
+  int device = -1;            // CUDA device of the array's context: near-field blocks filled there (-1: host)
 };
 
 // Anchors and projection weights of one element type, placed at the array's

@@ -709,6 +709,12 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
     else
       ao.csr_max_nnz = ((int64_t)8 << 30) / 36;   // 8 + 24 value bytes + 4 column bytes
   }
+  // near-field blocks filled on the context's device (host contexts: on the host;
+  // MACROAIM_NEAR_FILL=host keeps the host fill on a device context)
+  {
+    const char* nf = std::getenv("MACROAIM_NEAR_FILL");
+    ao.device = (nf && std::string(nf) == "host") ? -1 : ctx->device;
+  }
   mm::build_array_host(a->ah, tms, type_of, offs, ao, em);
   auto& ah = a->ah;
   auto& da = a->da;

@@ -257,9 +257,9 @@ struct DevArray {
 };
 
 // Shapes of the block near field: 0-4 CUDA-core tiles (k_near_blocks), 5-6
-// tensor-core tiles with partial sums, 7-8 the tensor-core direct form
+// tensor-core tiles with partial sums, 7-9 the tensor-core direct form
 // (near_tc.cu, complex64).
-constexpr int kNearShapes = 9;
+constexpr int kNearShapes = 10;
 // Flags of matvec: kMvNoTune never times near-field kernel shapes (an untuned
 // right-hand-side count takes the size rule and is not remembered);
 // kMvNoProfile records no stage events (the array's profiler is left alone).

@@ -1845,9 +1845,14 @@ static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p,
       run();
       cudaEventRecord(e1, st);
       float ms = 0;
-      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-          ms < best_ms) {
-        best_ms = ms;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+      // the two-stage direct form (shape 9, 153 KB of shared memory) leaves room
+      // for an FFT block beside it on an SM, so in the product it overlaps the
+      // far-field chain; it is kept while within 10 % of the fastest alone
+      // (32x32, 64 RHS: alone slightly slower, product 7.70 -> 7.46 ms)
+      const float cmp = tn == 9 ? ms / 1.1f : ms;
+      if (cmp < best_ms) {
+        best_ms = cmp;
         best = {tn, ks};
       }
     }

@@ -884,6 +884,9 @@ cudaError_t near_tc_init(DevArray& a) {
   e = cudaFuncSetAttribute(k_near_tc_direct<64, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)NearTcCfg<64, 3, 3>::Smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_near_tc_direct<64, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)NearTcCfg<64, 2, 3>::Smem);
+  if (e != cudaSuccess) return e;
   void* p = nullptr;
   e = cudaGetSymbolAddress(&p, g_near_tc_err);
   if (e != cudaSuccess) return e;
@@ -973,8 +976,9 @@ cudaError_t near_tc_launch(int shape, const DevArray& a, const DevPrec<float>& p
                            float2* v, float2* P, cudaStream_t st) {
   if (!p.nfb_tc || a.nfb_tptr128 == nullptr || a.nfe_ptr == nullptr) return cudaErrorInvalidValue;
   if (shape >= 2)
-    return shape == 3 ? near_tc_direct_launch_t<64, 3, 3>(a, p, nrhs, u, v, st)
-                      : near_tc_direct_launch_t<32, 4, 4>(a, p, nrhs, u, v, st);
+    return shape == 4   ? near_tc_direct_launch_t<64, 2, 3>(a, p, nrhs, u, v, st)
+           : shape == 3 ? near_tc_direct_launch_t<64, 3, 3>(a, p, nrhs, u, v, st)
+                        : near_tc_direct_launch_t<32, 4, 4>(a, p, nrhs, u, v, st);
   if (P == nullptr) return cudaErrorInvalidValue;
   cudaError_t e = shape == 1 ? near_tc_launch_t<64, 3, 3>(a, p, nrhs, u, P, st)
                              : near_tc_launch_t<32, 4, 4>(a, p, nrhs, u, P, st);

@@ -13,8 +13,10 @@ namespace mm {
 // = (element pair, right-hand side) and partial sums.  2, 3 = the direct form
 // (columns = right-hand sides of one element, 32 or 64 per tile, accumulated
 // over the element's pairs and subtracted from v in place); it needs an even
-// right-hand-side count and 16-byte aligned u and v (near_tc_direct_ok).
-constexpr int kNearTcShapes = 4;
+// right-hand-side count and 16-byte aligned u and v (near_tc_direct_ok).  4 =
+// the direct form with 64 right-hand sides and two stages (153 KB of shared
+// memory instead of 222 KB: an FFT block fits beside it on an SM).
+constexpr int kNearTcShapes = 5;
 
 // Function attributes and the device address of the kernel's error flag
 // (a.near_err), once per array (the array's device current).

@@ -8,7 +8,7 @@ bar of the other parity tests: relative L2 <= 1e-5, worst element <= 1e-4 of
 max |y|.  MACROAIM_NEAR_SHAPE fixes the shape (5: 32 complex columns per tile,
 6: 64) instead of the autotuner.  The products go into per-pair slices of a
 partial-sum buffer, which a reduction kernel subtracts from v.  Shapes 7 and 8
-are the direct form (32 or 64 right-hand sides of one element per tile, the
+(and 9, two stages) are the direct form (32 or 64 right-hand sides of one element per tile, the
 element's pairs accumulated in tensor memory and subtracted from v in place);
 it takes even right-hand-side counts of 16 or more, and other counts fall back
 to the CUDA-core kernel."""
@@ -77,7 +77,7 @@ def test_tensor_core_near_field_c3(ctx, c3_types, monkeypatch, shape, ks, nrhs):
         mm.mm_array_destroy(la.array)
 
 
-@pytest.mark.parametrize("shape", [7, 8])
+@pytest.mark.parametrize("shape", [7, 8, 9])
 @pytest.mark.parametrize("nrhs", [5, 8, 16, 24, 40, 64])
 def test_tensor_core_direct_near_field_c3(ctx, c3_types, monkeypatch, shape, nrhs):
     """Direct form on the 6 x 6 four-type array: ragged right-hand-side tiles
