@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "fill_gpu.h"
 
 namespace mm {
 
@@ -373,12 +374,24 @@ void build_type(TypeModel& tm, int device) {
   Vec3 z{0, 0, 0};
   std::vector<cd> Lss, Lse, Les, Lee, Kse, Kee;
   std::vector<double> D;
-  fill_efie(tm.scat, tm.scat, z, em, Lss);
-  fill_efie(tm.scat, tm.eq, z, em, Lse);
-  fill_efie(tm.eq, tm.scat, z, em, Les);
-  fill_efie(tm.eq, tm.eq, z, em, Lee);
-  fill_k(tm.scat, tm.eq, tm.duals, em, Kse);
-  fill_k(tm.eq, tm.eq, tm.duals, em, Kee);
+  // the four EFIE fills on the GPU for large elements of a device context
+  // (the same integrals; the host fill otherwise or if the device fails)
+  auto efie = [&](const Mesh& t, const Mesh& sm, std::vector<cd>& out) {
+    std::string msg;
+    if (device >= 0 && N >= kDenseGpuMinN && fill_efie_gpu(t, sm, z, em.k, device, out, msg)) return;
+    fill_efie(t, sm, z, em, out);
+  };
+  efie(tm.scat, tm.scat, Lss);
+  efie(tm.scat, tm.eq, Lse);
+  efie(tm.eq, tm.scat, Les);
+  efie(tm.eq, tm.eq, Lee);
+  auto kfill = [&](const Mesh& t, std::vector<cd>& out) {
+    std::string msg;
+    if (device >= 0 && N >= kDenseGpuMinN && fill_k_gpu(t, tm.duals, em.k, device, out, msg)) return;
+    fill_k(t, tm.eq, tm.duals, em, out);
+  };
+  kfill(tm.scat, Kse);
+  kfill(tm.eq, Kee);
   fill_dual_gram(tm.eq, tm.duals, D);
   for (auto& x : Lss) x *= c;
   for (auto& x : Lse) x *= c;

@@ -244,6 +244,153 @@ __global__ void __launch_bounds__(128) k_near_assemble(
   out[p] = make_double2(Gr - gr, Gi - gi);
 }
 
+// Full EFIE matrix: out[m Nn + n] = sum over the (up to) four triangle pairs of
+// RWG m and RWG n of sign x length products times the pair integral.
+__global__ void __launch_bounds__(256) k_efie_assemble(int Nm, int Nn, const Side* __restrict__ sa,
+                                                       const Side* __restrict__ sb, const double2* __restrict__ I,
+                                                       int nS, double2* __restrict__ out) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)Nm * Nn) return;
+  const int m = (int)(id / Nn), n = (int)(id % Nn);
+  double lr = 0.0, li = 0.0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const Side A = sa[2 * m + u];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const Side B = sb[2 * n + v];
+      const double2 x = I[((int64_t)A.tri * nS + B.tri) * 9 + 3 * A.loc + B.loc];
+      const double c = A.c * B.c;
+      lr += c * x.x;
+      li += c * x.y;
+    }
+  }
+  out[id] = make_double2(lr, li);
+}
+
+// grad_r of int_T 1/R in closed form (principal value on the plane of T)
+__device__ __forceinline__ D3 static_grad(D3 r, const Tri& g) {
+  double d = dotd(r - g.v[0], g.n);
+  const D3 rho = r - d * g.n;
+  if (fabs(d) < kSnap * g.scale) d = 0.0;
+  const double ad = fabs(d);
+  D3 gt = d3(0, 0, 0);
+  double bsum = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const D3 Pm = g.v[i], Pp = g.v[(i + 1) % 3];
+    D3 s = Pp - Pm;
+    s = (1.0 / normd(s)) * s;
+    const D3 m = crossd(s, g.n);
+    const double lp = dotd(Pp - rho, s), lm = dotd(Pm - rho, s);
+    double t0 = dotd(Pm - rho, m);
+    if (fabs(t0) < kSnap * g.scale) t0 = 0.0;
+    const double R0sq = t0 * t0 + d * d;
+    const double Rp = normd(r - Pp), Rm = normd(r - Pm);
+    const double f2 = f2_of(lp, lm, Rp, Rm, R0sq);
+    double beta = 0.0;
+    if (R0sq > 0.0) beta = atan2(t0 * lp, R0sq + ad * Rp) - atan2(t0 * lm, R0sq + ad * Rm);
+    bsum += beta;
+    gt = gt - f2 * m;
+  }
+  const double sg = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+  return gt - (sg * bsum) * g.n;
+}
+
+// c(R) with grad_r G1(|r - r'|) = c(R) (r - r'), as (re, im); 0 at R = 0
+__device__ __forceinline__ void g1grad_of(double R, double k, double& re, double& im) {
+  if (R == 0.0) {
+    re = im = 0.0;
+    return;
+  }
+  const double x = k * R, s = sin(0.5 * x);
+  const double a = -2.0 * s * s + x * sin(x);
+  const double b = x * cos(x) - sin(x);
+  const double f = -kInv4Pi / (R * R * R);
+  re = a * f;
+  im = b * f;
+}
+
+struct Rule3 {
+  double b0[3], b1[3], b2[3], w[3];
+};
+
+// Dual support entry: refined triangle, alpha, beta (the dual field there is
+// alpha r - beta).
+struct DualEnt {
+  int rt;
+  double alpha, bx, by, bz;
+};
+
+// rows[(t 3 + i) Nn + n] = <phi_i of test triangle t, curl int G g_n> (the
+// host fill_k's rows): one thread per (test triangle, dual function); per test
+// point the dual's field on its support entries, with grad int_s G from the
+// closed-form static part and the 3-point smooth part.
+__global__ void __launch_bounds__(128) k_fillk_rows(const double* __restrict__ tc, int nT,
+                                                    const double* __restrict__ rc, int Nn,
+                                                    const int32_t* __restrict__ eptr,
+                                                    const DualEnt* __restrict__ ent, double k, Rule7 q7, Rule3 q3,
+                                                    double2* __restrict__ rows) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)nT * Nn) return;
+  const int t = (int)(id / Nn), n = (int)(id % Nn);
+  const Tri tg = make_tri(tc + 9 * (int64_t)t, d3(0, 0, 0));
+  double accr[3] = {0, 0, 0}, acci[3] = {0, 0, 0};
+  const int e0 = eptr[n], e1 = eptr[n + 1];
+  for (int a = 0; a < 7; ++a) {
+    const D3 r = q7.b0[a] * tg.v[0] + q7.b1[a] * tg.v[1] + q7.b2[a] * tg.v[2];
+    const double wq = q7.w[a] * tg.area;
+    double Wr[3] = {0, 0, 0}, Wi[3] = {0, 0, 0};
+    for (int e = e0; e < e1; ++e) {
+      const DualEnt de = ent[e];
+      const Tri g = make_tri(rc + 9 * (int64_t)de.rt, d3(0, 0, 0));
+      const D3 gs = static_grad(r, g);
+      double vr[3] = {kInv4Pi * gs.x, kInv4Pi * gs.y, kInv4Pi * gs.z}, vi[3] = {0, 0, 0};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const D3 rp = q3.b0[p] * g.v[0] + q3.b1[p] * g.v[1] + q3.b2[p] * g.v[2];
+        const D3 dd = r - rp;
+        double cr, ci;
+        g1grad_of(normd(dd), k, cr, ci);
+        const double wgt = q3.w[p] * g.area;
+        cr *= wgt;
+        ci *= wgt;
+        vr[0] += cr * dd.x; vr[1] += cr * dd.y; vr[2] += cr * dd.z;
+        vi[0] += ci * dd.x; vi[1] += ci * dd.y; vi[2] += ci * dd.z;
+      }
+      const D3 bt = d3(de.alpha * r.x - de.bx, de.alpha * r.y - de.by, de.alpha * r.z - de.bz);
+      // V x bt (complex V, real bt)
+      Wr[0] += vr[1] * bt.z - vr[2] * bt.y; Wi[0] += vi[1] * bt.z - vi[2] * bt.y;
+      Wr[1] += vr[2] * bt.x - vr[0] * bt.z; Wi[1] += vi[2] * bt.x - vi[0] * bt.z;
+      Wr[2] += vr[0] * bt.y - vr[1] * bt.x; Wi[2] += vi[0] * bt.y - vi[1] * bt.x;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const D3 phi = (wq / (2.0 * tg.area)) * (r - tg.v[i]);
+      accr[i] += phi.x * Wr[0] + phi.y * Wr[1] + phi.z * Wr[2];
+      acci[i] += phi.x * Wi[0] + phi.y * Wi[1] + phi.z * Wi[2];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rows[((int64_t)t * 3 + i) * Nn + n] = make_double2(accr[i], acci[i]);
+}
+
+// out[m Nn + n] = sum over the two triangles of test RWG m of sign x length x rows
+__global__ void __launch_bounds__(256) k_fillk_assemble(int Nm, int Nn, const Side* __restrict__ sa,
+                                                        const double2* __restrict__ rows, double2* __restrict__ out) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)Nm * Nn) return;
+  const int m = (int)(id / Nn), n = (int)(id % Nn);
+  double lr = 0.0, li = 0.0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const Side A = sa[2 * m + u];
+    const double2 x = rows[((int64_t)A.tri * 3 + A.loc) * Nn + n];
+    lr += A.c * x.x;
+    li += A.c * x.y;
+  }
+  out[id] = make_double2(lr, li);
+}
+
 struct DevMesh {
   double* tc = nullptr;   // nT x 9 vertex coordinates
   Side* side = nullptr;   // nRWG x 2 (T+, T-)
@@ -412,6 +559,146 @@ bool fill_near_blocks_gpu(std::vector<NearFillJob>& jobs, const std::vector<cd>&
   if (prev >= 0) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     msg = std::string("near-field fill on the GPU: ") + cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+bool fill_efie_gpu(const Mesh& test, const Mesh& src, Vec3 shift, double k, int device, std::vector<cd>& out,
+                   std::string& msg) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    msg = "cudaSetDevice failed";
+    return false;
+  }
+  DevMesh MT, MS;
+  double2 *dI = nullptr, *dout = nullptr;
+  cudaError_t e = upload_mesh(test, MT);
+  if (e == cudaSuccess && &src != &test) e = upload_mesh(src, MS);
+  const DevMesh& MSr = (&src == &test) ? MT : MS;
+  const size_t np = (size_t)MT.nT * MSr.nT, ne = (size_t)MT.nR * MSr.nR;
+  if (e == cudaSuccess) e = cudaMalloc(&dI, sizeof(double2) * 9 * np);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double2) * ne);
+  if (e == cudaSuccess) {
+    const Rule r7 = rule_tri7();
+    Rule7 q;
+    for (int a = 0; a < 7; ++a) {
+      q.b0[a] = r7.b0[a];
+      q.b1[a] = r7.b1[a];
+      q.b2[a] = r7.b2[a];
+      q.w[a] = r7.w[a];
+    }
+    k_efie_tri_pairs<<<(unsigned)((np + 127) / 128), 128>>>(MT.tc, MT.nT, MSr.tc, MSr.nT, D3{shift.x, shift.y, shift.z},
+                                                             k, q, dI);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_efie_assemble<<<(unsigned)((ne + 255) / 256), 256>>>(MT.nR, MSr.nR, MT.side, MSr.side, dI, MSr.nT, dout);
+    e = cudaGetLastError();
+  }
+  std::vector<double2> h;
+  if (e == cudaSuccess) {
+    h.resize(ne);
+    e = cudaMemcpy(h.data(), dout, sizeof(double2) * ne, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) {
+    out.resize(ne);
+    for (size_t i = 0; i < ne; ++i) out[i] = cd(h[i].x, h[i].y);
+  }
+  for (void* p : {(void*)MT.tc, (void*)MT.side, (void*)MS.tc, (void*)MS.side, (void*)dI, (void*)dout})
+    if (p) cudaFree(p);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    msg = std::string("EFIE fill on the GPU: ") + cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+bool fill_k_gpu(const Mesh& test, const DualSet& d, double k, int device, std::vector<cd>& out, std::string& msg) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    msg = "cudaSetDevice failed";
+    return false;
+  }
+  const int nR = (int)d.rarea.size(), Nn = (int)d.n, E = (int)d.fn.size();
+  // refined triangles' vertices; support entries grouped by dual function
+  // (entries of one function in increasing entry order, as the host sums them)
+  std::vector<double> rc(9 * (size_t)nR);
+  for (int r = 0; r < nR; ++r)
+    for (int i = 0; i < 3; ++i) {
+      const Vec3 v = d.rvert(r, i);
+      rc[9 * r + 3 * i] = v.x;
+      rc[9 * r + 3 * i + 1] = v.y;
+      rc[9 * r + 3 * i + 2] = v.z;
+    }
+  std::vector<int32_t> eptr(Nn + 1, 0);
+  for (int e = 0; e < E; ++e) ++eptr[d.fn[e] + 1];
+  for (int n = 0; n < Nn; ++n) eptr[n + 1] += eptr[n];
+  std::vector<DualEnt> ent(E);
+  {
+    std::vector<int32_t> fill(eptr.begin(), eptr.end() - 1);
+    for (int e = 0; e < E; ++e) {
+      const int64_t r = d.rt[e];
+      const double A2 = 2.0 * d.rarea[r];
+      const double fs = d.flux[3 * e] + d.flux[3 * e + 1] + d.flux[3 * e + 2];
+      Vec3 b{0, 0, 0};
+      for (int i = 0; i < 3; ++i) b = b + (d.flux[3 * e + i] / A2) * d.rvert(r, i);
+      ent[fill[d.fn[e]]++] = DualEnt{(int)r, fs / A2, b.x, b.y, b.z};
+    }
+  }
+  DevMesh MT;
+  double* drc = nullptr;
+  int32_t* deptr = nullptr;
+  DualEnt* dent = nullptr;
+  double2 *drows = nullptr, *dout = nullptr;
+  cudaError_t e = upload_mesh(test, MT);
+  if (e == cudaSuccess) e = upload(&drc, rc.data(), rc.size());
+  if (e == cudaSuccess) e = upload(&deptr, eptr.data(), eptr.size());
+  if (e == cudaSuccess) e = upload(&dent, ent.data(), ent.size());
+  const size_t nrows = (size_t)MT.nT * 3 * Nn, ne = (size_t)MT.nR * Nn;
+  if (e == cudaSuccess) e = cudaMalloc(&drows, sizeof(double2) * nrows);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double2) * ne);
+  if (e == cudaSuccess) {
+    const Rule r7 = rule_tri7(), r3 = rule_tri3();
+    Rule7 q7;
+    Rule3 q3;
+    for (int a = 0; a < 7; ++a) {
+      q7.b0[a] = r7.b0[a];
+      q7.b1[a] = r7.b1[a];
+      q7.b2[a] = r7.b2[a];
+      q7.w[a] = r7.w[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      q3.b0[a] = r3.b0[a];
+      q3.b1[a] = r3.b1[a];
+      q3.b2[a] = r3.b2[a];
+      q3.w[a] = r3.w[a];
+    }
+    const size_t nth = (size_t)MT.nT * Nn;
+    k_fillk_rows<<<(unsigned)((nth + 127) / 128), 128>>>(MT.tc, MT.nT, drc, Nn, deptr, dent, k, q7, q3, drows);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_fillk_assemble<<<(unsigned)((ne + 255) / 256), 256>>>(MT.nR, Nn, MT.side, drows, dout);
+    e = cudaGetLastError();
+  }
+  std::vector<double2> h;
+  if (e == cudaSuccess) {
+    h.resize(ne);
+    e = cudaMemcpy(h.data(), dout, sizeof(double2) * ne, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) {
+    out.resize(ne);
+    for (size_t i = 0; i < ne; ++i) out[i] = cd(h[i].x, h[i].y);
+  }
+  for (void* p : {(void*)MT.tc, (void*)MT.side, (void*)drc, (void*)deptr, (void*)dent, (void*)drows, (void*)dout})
+    if (p) cudaFree(p);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    msg = std::string("K fill on the GPU: ") + cudaGetErrorString(e);
     return false;
   }
   return true;

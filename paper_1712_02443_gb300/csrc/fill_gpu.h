@@ -36,4 +36,15 @@ bool fill_near_blocks_gpu(std::vector<NearFillJob>& jobs, const std::vector<cd>&
                           const std::vector<std::array<int, 3>>& so, cd cA, cd cphi, double k, int device,
                           std::string& msg);
 
+// The full EFIE Galerkin matrix (Nm x Nn, row-major, before the -j k eta0
+// factor) of the test mesh against the source mesh shifted by `shift`, the
+// host fill_efie's integrals on `device`.  False with msg set on a CUDA error.
+bool fill_efie_gpu(const Mesh& test, const Mesh& src, Vec3 shift, double k, int device, std::vector<cd>& out,
+                   std::string& msg);
+
+// The K matrix <f_m, curl int G g_n> of the test mesh's RWG functions against
+// the dual functions d (principal value), the host fill_k's integrals on
+// `device`.  False with msg set on a CUDA error.
+bool fill_k_gpu(const Mesh& test, const DualSet& d, double k, int device, std::vector<cd>& out, std::string& msg);
+
 }  // namespace mm
