@@ -203,7 +203,8 @@ void mm_array_destroy(mm_array* array);
  * `stream` in order; MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block
  * near-field kernel's shape instead of timing them on the first product
  * (0-4 CUDA-core tiles, k split 1-16; 5-6 tensor-core tiles, complex64 only,
- * TF32 with a three-product split, no k split);
+ * TF32 with a three-product split, no k split; 7-9 the tensor-core direct form
+ * for 16 or more right-hand sides of even count);
  * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                    void* stream);
@@ -212,10 +213,20 @@ mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev
  * for arrays[i] with nrhs[i] columns, as mm_apply.  Each array's product runs
  * on a stream of its own, forked from `stream` and joined back into it, so the
  * products run concurrently on the device and the call orders like one launch
- * on `stream`.  Every array appears at most once; all on one device.  The
- * batch's message on failure is on arrays[0]'s context.                       */
+ * on `stream`.  Every array appears at most once; all on one device.  Once
+ * every array has done a product of its width and precision (its tuners have
+ * run) and none records stage events (mm_profile_enable), the call captures
+ * the batch's launches into one CUDA graph and launches that graph; later
+ * calls with the same arrays, widths, x_dev / y_dev pointers and precision
+ * replay it as one launch (on a library stream ordered after and before
+ * `stream` by events).  A graph is dropped when an array is destroyed, and not
+ * used after an array's work buffers were reallocated (a product of another
+ * width in between).  The batch's message on failure is on arrays[0]'s
+ * context.                                                                   */
 mm_status mm_apply_batch(mm_array* const* arrays, int32_t count, const int32_t* nrhs, const void* const* x_dev,
                          void* const* y_dev, int32_t precision, void* stream);
+/* Number of batch graphs held for `array` (NULL: all arrays) by mm_apply_batch. */
+mm_status mm_batch_graphs(const mm_array* array, int32_t* count);
 /* Same operator with host buffers: copies x in, applies, copies y out, and
  * returns after the result is in y_host (synchronous).                       */
 mm_status mm_apply_host(mm_array* array, int32_t nrhs, const void* x_host, void* y_host, int32_t precision);

@@ -113,6 +113,7 @@ _SIGS = {
                                            ct.POINTER(mm_solve_stats)]),
     "mm_type_set_feed": (ct.c_int, [P, ct.c_int32, P, P]),
     "mm_apply_batch": (ct.c_int, [P, ct.c_int32, P, P, P, ct.c_int32, P]),
+    "mm_batch_graphs": (ct.c_int, [P, P]),
     "mm_array_tuning": (ct.c_int, [P, ct.c_int32, ct.c_int32, P, P, P]),
     "mm_rhs_deltagap": (ct.c_int, [P, ct.c_int32, P, P, P]),
     "mm_currents_fed": (ct.c_int, [P, ct.c_int32, P, P, P, P, P]),
@@ -297,6 +298,13 @@ def mm_apply_batch(arrays, nrhs, xs, ys, precision: int, stream=None) -> None:
     xp = (ct.c_void_p * n)(*[_ptr(x) for x in xs])
     yp = (ct.c_void_p * n)(*[_ptr(y) for y in ys])
     _check(load().mm_apply_batch(ar, n, _ptr(nr), xp, yp, precision, _stream(stream)), _ctx_of.get(arrays[0].value))
+
+
+def mm_batch_graphs(array=None) -> int:
+    """Number of CUDA graphs mm_apply_batch holds for the array (None: all)."""
+    n = ct.c_int32()
+    _check(load().mm_batch_graphs(array, ct.byref(n)), _ctx_of.get(array.value) if array is not None else None)
+    return n.value
 
 
 def mm_apply_noalloc(array, nrhs: int, x_dev, y_dev, precision: int, stream=None) -> None:

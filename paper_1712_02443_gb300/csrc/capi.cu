@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <set>
 #include <functional>
 #include <map>
 #include <memory>
@@ -84,6 +85,8 @@ struct mm_array {
   int gc_cap = 0;
   cudaStream_t bst = nullptr;        // mm_apply_batch: this array's product stream and its event
   cudaEvent_t bev_done = nullptr, bev_fork = nullptr;
+  uint64_t epoch = 0;                // bumped whenever a work buffer a product uses is reallocated
+  std::set<std::pair<int, int>> settled;   // (nrhs, precision) with a product done (tuners run)
   void* pv_V = nullptr;              // mm_solve_planewave_host: excitation and solution on the device
   void* pv_E = nullptr;
   size_t pv_cap = 0;
@@ -91,6 +94,41 @@ struct mm_array {
 };
 
 namespace {
+
+// Batch products replayed as one CUDA graph: once every array of a batch has
+// done a product of its width and precision (tuners run, work buffers
+// allocated), the batch's launch sequence is captured into a graph on a
+// library stream and later calls with the same arrays, widths, buffers,
+// precision and work-buffer epochs launch that graph instead of every kernel.
+// A graph is dropped when one of its arrays is destroyed.
+struct BatchGraph {
+  std::vector<const mm_array*> arrays;
+  std::vector<int32_t> nrhs;
+  std::vector<const void*> x, y;
+  std::vector<uint64_t> epochs;
+  int32_t precision = 0;
+  int device = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<BatchGraph> g_graphs;
+constexpr size_t kMaxGraphs = 16;
+cudaStream_t g_cap_stream[64] = {nullptr};
+cudaEvent_t g_cap_in[64] = {nullptr}, g_cap_out[64] = {nullptr};
+
+void drop_graphs_of(const mm_array* a) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size();) {
+    const auto& g = g_graphs[i];
+    if (std::find(g.arrays.begin(), g.arrays.end(), a) != g.arrays.end()) {
+      cudaGraphExecDestroy(g.exec);
+      g_graphs.erase(g_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 
 mm_status fail(mm_ctx* ctx, mm_status code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -389,6 +427,7 @@ void upload_pj(mm_array* a, mm::DevPrec<R>& p) {
 template <typename R>
 void ensure_pt(mm_array* a, mm::Work& w, int nrhs) {
   if (w.pt) return;
+  ++a->epoch;
   CU(cudaMalloc(&w.pt, sizeof(typename mm::V2<R>::T) * (size_t)a->da.N * nrhs));
 }
 
@@ -403,6 +442,7 @@ void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
     need = std::max(need, (size_t)(Np * Kp));
   }
   if (w.bt_cap < need) {
+    ++a->epoch;
     if (w.bt) cudaFree(w.bt);
     w.bt = nullptr;
     CU(cudaMalloc(&w.bt, sizeof(uint16_t) * need));
@@ -442,6 +482,7 @@ template <typename R>
 void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
+  ++a->epoch;
   for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np, w.boxbuf})
     if (q) cudaFree(q);
   w = mm::Work();
@@ -1179,7 +1220,20 @@ mm_status mm_array_export(const mm_array* a, int32_t which, void* out, int64_t* 
   }
 }
 
-void mm_array_destroy(mm_array* a) { delete a; }
+void mm_array_destroy(mm_array* a) {
+  if (a) drop_graphs_of(a);
+  delete a;
+}
+
+mm_status mm_batch_graphs(const mm_array* array, int32_t* count) {
+  if (!count) return MM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  int32_t n = 0;
+  for (const auto& g : g_graphs)
+    if (!array || std::find(g.arrays.begin(), g.arrays.end(), array) != g.arrays.end()) ++n;
+  *count = n;
+  return MM_OK;
+}
 
 mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision, void* stream) {
   if (!a) return MM_EINVAL;
@@ -1206,6 +1260,7 @@ mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, in
     return fail(ctx, MM_EINVAL, "unknown precision");
   }
   if (e != cudaSuccess) return fail(ctx, MM_ECUDA, std::string("matvec: ") + cudaGetErrorString(e));
+  a->settled.insert({nrhs, precision});
   return MM_OK;
   API_CATCH(ctx)
 }
@@ -1224,28 +1279,104 @@ mm_status mm_apply_batch(mm_array* const* arrays, int32_t count, const int32_t* 
   }
   mm_ctx* ctx = arrays[0]->ctx;
   API_TRY
-  CU(cudaSetDevice(arrays[0]->da.device));
+  const int dev = arrays[0]->da.device;
+  if (dev < 0 || dev >= 64) return fail(ctx, MM_EINVAL, "device index out of range");
+  CU(cudaSetDevice(dev));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // fork: every array's product on its own stream, after the caller's work
-  if (!arrays[0]->bev_fork) CU(cudaEventCreateWithFlags(&arrays[0]->bev_fork, cudaEventDisableTiming));
-  CU(cudaEventRecord(arrays[0]->bev_fork, st));
-  for (int32_t i = 0; i < count; ++i) {
-    mm_array* a = arrays[i];
-    if (!a->bst) {
-      CU(cudaStreamCreateWithFlags(&a->bst, cudaStreamNonBlocking));
-      CU(cudaEventCreateWithFlags(&a->bev_done, cudaEventDisableTiming));
+  // fork (from stream `from`): every array's product on its own stream, joined back into `from`
+  auto launch_all = [&](cudaStream_t from) -> mm_status {
+    if (!arrays[0]->bev_fork) CU(cudaEventCreateWithFlags(&arrays[0]->bev_fork, cudaEventDisableTiming));
+    CU(cudaEventRecord(arrays[0]->bev_fork, from));
+    for (int32_t i = 0; i < count; ++i) {
+      mm_array* a = arrays[i];
+      if (!a->bst) {
+        CU(cudaStreamCreateWithFlags(&a->bst, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&a->bev_done, cudaEventDisableTiming));
+      }
+      CU(cudaStreamWaitEvent(a->bst, arrays[0]->bev_fork, 0));
+      const mm_status s = mm_apply(a, nrhs[i], x_dev[i], y_dev[i], precision, a->bst);
+      if (s != MM_OK) {
+        if (a != arrays[0]) ctx->err = a->ctx->err;
+        return s;
+      }
+      CU(cudaEventRecord(a->bev_done, a->bst));
     }
-    CU(cudaStreamWaitEvent(a->bst, arrays[0]->bev_fork, 0));
-    const mm_status s = mm_apply(a, nrhs[i], x_dev[i], y_dev[i], precision, a->bst);
-    if (s != MM_OK) {
-      if (a != arrays[0]) ctx->err = a->ctx->err;
-      return s;
+    for (int32_t i = 0; i < count; ++i) CU(cudaStreamWaitEvent(from, arrays[i]->bev_done, 0));
+    return MM_OK;
+  };
+  // a graph applies when no array records stage events and every array has
+  // done a product of this width and precision
+  bool graphable = true;
+  for (int32_t i = 0; i < count && graphable; ++i)
+    graphable = !arrays[i]->da.prof.on && arrays[i]->settled.count({nrhs[i], precision}) > 0;
+  auto matches = [&](const BatchGraph& g) {
+    if (g.precision != precision || g.device != dev || (int32_t)g.arrays.size() != count) return false;
+    for (int32_t i = 0; i < count; ++i)
+      if (g.arrays[i] != arrays[i] || g.nrhs[i] != nrhs[i] || g.x[i] != x_dev[i] || g.y[i] != y_dev[i] ||
+          g.epochs[i] != arrays[i]->epoch)
+        return false;
+    return true;
+  };
+  if (graphable) {
+    cudaGraphExec_t exec = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_graph_mu);
+      for (const auto& g : g_graphs)
+        if (matches(g)) {
+          exec = g.exec;
+          break;
+        }
     }
-    CU(cudaEventRecord(a->bev_done, a->bst));
+    if (!g_cap_stream[dev]) {
+      CU(cudaStreamCreateWithFlags(&g_cap_stream[dev], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&g_cap_in[dev], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&g_cap_out[dev], cudaEventDisableTiming));
+    }
+    cudaStream_t cs = g_cap_stream[dev];
+    if (exec == nullptr) {
+      // capture the launch sequence (nothing runs during capture), then replay it below
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      mm_status ls = MM_OK;
+      if (ce == cudaSuccess) {
+        ls = launch_all(cs);
+        ce = cudaStreamEndCapture(cs, &graph);
+      }
+      if (ce == cudaSuccess && ls == MM_OK && graph != nullptr &&
+          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        BatchGraph g;
+        for (int32_t i = 0; i < count; ++i) {
+          g.arrays.push_back(arrays[i]);
+          g.nrhs.push_back(nrhs[i]);
+          g.x.push_back(x_dev[i]);
+          g.y.push_back(y_dev[i]);
+          g.epochs.push_back(arrays[i]->epoch);
+        }
+        g.precision = precision;
+        g.device = dev;
+        g.exec = exec;
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        if (g_graphs.size() >= kMaxGraphs) {
+          cudaGraphExecDestroy(g_graphs.front().exec);
+          g_graphs.erase(g_graphs.begin());
+        }
+        g_graphs.push_back(g);
+      } else {
+        exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();   // a failed capture leaves no error behind: the kernels run below
+    }
+    if (exec != nullptr) {
+      CU(cudaEventRecord(g_cap_in[dev], st));
+      CU(cudaStreamWaitEvent(cs, g_cap_in[dev], 0));
+      CU(cudaGraphLaunch(exec, cs));
+      CU(cudaEventRecord(g_cap_out[dev], cs));
+      CU(cudaStreamWaitEvent(st, g_cap_out[dev], 0));
+      return MM_OK;
+    }
   }
-  // join: the caller's stream waits for every product
-  for (int32_t i = 0; i < count; ++i) CU(cudaStreamWaitEvent(st, arrays[i]->bev_done, 0));
-  return MM_OK;
+  return launch_all(st);
   API_CATCH(ctx)
 }
 

@@ -72,6 +72,50 @@ def test_batch_of_uneven_arrays(ctx):
         a1.close()
 
 
+@pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C64_F16, mm.MM_C128])
+def test_batch_graph_replay(ctx, prec):
+    """From the second call with the same arrays, widths, buffers and precision
+    the batch is captured into one CUDA graph and replayed: new inputs in the
+    same buffers give the new products (each equal to mm_apply alone), and
+    destroying an array of a captured batch drops its graph (a later batch with a
+    new array of the same size is computed afresh)."""
+    a1 = loop_array(ctx, 2, 2)
+    a2 = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2)
+    dt = torch.complex128 if prec == mm.MM_C128 else torch.complex64
+    tol = 1e-11 if prec == mm.MM_C128 else 1e-5
+    try:
+        nr = [1, 16]
+        X = [torch.empty(la.n * r, dtype=dt, device="cuda") for la, r in zip((a1, a2), nr)]
+        Y = [torch.empty_like(x) for x in X]
+        st = torch.cuda.current_stream()
+        for call in range(4):   # call 0: tuned; 1: captured and replayed; 2, 3: replayed
+            xs = [wl.random_cvec(a1.n, 0, 40 + call), wl.random_cvec(a2.n, 2, 50 + call, nrhs=16)]
+            for x, h in zip(X, xs):
+                x.copy_(torch.from_numpy(np.ascontiguousarray(h).reshape(-1)).to(dt))
+            mm.mm_apply_batch([a1.array, a2.array], nr, X, Y, prec, st)
+            torch.cuda.synchronize()
+            for la, x, y, r in zip((a1, a2), X, Y, nr):
+                y1 = torch.empty_like(x)
+                mm.mm_apply(la.array, r, x, y1, prec, st)
+                torch.cuda.synchronize()
+                assert _rel(y.cpu().numpy().astype(np.complex128), y1.cpu().numpy().astype(np.complex128)) <= tol
+            assert mm.mm_batch_graphs(a2.array) == (0 if call == 0 else 1)
+        a3 = loop_array(ctx, 2, 2, types=a1.types)
+        mm.mm_array_destroy(a1.array)
+        assert mm.mm_batch_graphs(a2.array) == 0
+        a1.array = a3.array
+        g1 = np.load(os.path.join(GOLD, "c1_2x2.npz"))
+        X[0].copy_(torch.from_numpy(g1["x"]).to(dt))
+        for _ in range(3):
+            mm.mm_apply_batch([a1.array, a2.array], nr, X, Y, prec, st)
+            torch.cuda.synchronize()
+            bar = {mm.MM_C128: 1e-10, mm.MM_C64: 1e-5, mm.MM_C64_F16: 3e-3}[prec]   # the 16-bit bar of the GEMM tests
+            assert _rel(Y[0].cpu().numpy().astype(np.complex128), g1["y"]) <= bar
+    finally:
+        a2.close()
+        a1.close()
+
+
 def test_batch_rejects_an_array_twice(ctx):
     la = loop_array(ctx, 2, 2)
     try:
