@@ -1807,57 +1807,18 @@ static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p,
     near_blocks_launch<R, 32, 4>(a, p, nrhs, u, y, st, nl, ks);
 }
 
-// Autotuner of the block near field: on the first product of an array with a
-// given right-hand-side count and precision, each (kernel shape, k split) pair
-// is timed with CUDA events (one warm-up, one timed launch) writing into a
-// scratch buffer (the spectra, idle at this point of the product), and the
-// fastest is kept for that array.  Without a large enough scratch buffer the
-// size rule is used instead.
+// Size rule of the block near field (products that may not time shapes, and
+// the fallback when timing fails): tensor cores when their blocks exist (the
+// direct form from 64 right-hand sides), else 64 x 64 tiles for many columns,
+// 64 x 32 tiles with a k split of 4 for few.
 template <typename R>
-static std::pair<int, int> near_autotune(const DevArray& a, const DevPrec<R>& p, int nrhs,
-                                         const typename V2<R>::T* u, typename V2<R>::T* scratch,
-                                         size_t scratch_elems, cudaStream_t st, void* np) {
+static std::pair<int, int> near_size_rule(const DevArray& a, const DevPrec<R>& p, int nrhs, const void* u,
+                                          const void* v, void* np) {
   int64_t cols = 0;
   for (const auto& g : a.nfg) cols += g.npairs * nrhs;
   std::pair<int, int> best = {cols >= (int64_t)64 * 4 * 152 ? 2 : 0, cols >= (int64_t)64 * 4 * 152 ? 1 : 4};
-  if (near_shape_ok<R>(5, a, p, nrhs, u, scratch, np)) best = {cols >= (int64_t)64 * 4 * 152 ? 6 : 5, 1};
-  if (nrhs >= 64 && near_shape_ok<R>(8, a, p, nrhs, u, scratch, np)) best = {8, 1};
-  if (scratch == nullptr || scratch_elems < (size_t)a.N * nrhs) return best;
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return best;
-  if (cudaEventCreate(&e1) != cudaSuccess) {
-    cudaEventDestroy(e0);
-    return best;
-  }
-  float best_ms = 1e30f;
-  // with 16 or more right-hand sides and the tensor-core forms available, the
-  // CUDA-core shapes are not timed (4-5x slower there: 6.3-7.9 ms against 1.5 ms
-  // per product at 32x32, 64 RHS; timing them cost 0.23 s of the first product)
-  const bool skip_cuda_cores = nrhs >= 16 && near_shape_ok<R>(7, a, p, nrhs, u, scratch, np);
-  for (int tn = 0; tn < kNearShapes; ++tn)
-    for (int ks : {1, 2, 4}) {
-      if (!near_shape_ok<R>(tn, a, p, nrhs, u, scratch, np) || (tn >= 5 && ks > 1)) continue;   // tensor-core shapes: no k split
-      if (skip_cuda_cores && tn < 5) continue;
-      int nl = 0;
-      auto run = [&]() { near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, np); };
-      run();
-      cudaEventRecord(e0, st);
-      run();
-      cudaEventRecord(e1, st);
-      float ms = 0;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
-      // the two-stage direct form (shape 9, 153 KB of shared memory) leaves room
-      // for an FFT block beside it on an SM, so in the product it overlaps the
-      // far-field chain; it is kept while within 10 % of the fastest alone
-      // (32x32, 64 RHS: alone slightly slower, product 7.70 -> 7.46 ms)
-      const float cmp = tn == 9 ? ms / 1.1f : ms;
-      if (cmp < best_ms) {
-        best_ms = cmp;
-        best = {tn, ks};
-      }
-    }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (near_shape_ok<R>(5, a, p, nrhs, u, v, np)) best = {cols >= (int64_t)64 * 4 * 152 ? 6 : 5, 1};
+  if (nrhs >= 64 && near_shape_ok<R>(8, a, p, nrhs, u, v, np)) best = {8, 1};
   return best;
 }
 
@@ -2109,10 +2070,106 @@ static std::pair<int, int> grid_autotune(DevArray& a, const DevPrec<R>& p, int n
   return best;
 }
 
+// Near-field tuner, on the first product of an array with a given
+// right-hand-side count and precision.  (1) The CUDA-core (shape, k split)
+// pairs are timed alone (one warm-up and one timed launch, CUDA events, into
+// the idle spectrum buffer); complex128 keeps the fastest.  (2) Complex64: that
+// pair and every tensor-core shape are timed over whole products (one warm-up
+// and one timed product): the near field runs beside the far-field chain, and
+// what it takes from the chain's SMs counts as much as its own time (16x16,
+// 1 RHS: the tensor-core shape 5 is slower alone than CUDA-core shape 0 with a
+// k split of 2 but gives 325 instead of 300 solves/s).  With 16 or more
+// right-hand sides and the tensor-core direct form available, step (1) is
+// skipped (those shapes are 4-5x slower there).  The choice is kept for the
+// array; the products write y, which the caller's product then overwrites.
+template <typename R>
+static cudaError_t near_tune_products(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* x, void* y,
+                                      cudaStream_t st, int gemm_mode, bool pre, unsigned flags) {
+  typedef typename V2<R>::T C;
+  const auto key = std::make_pair(nrhs, (int)sizeof(R));
+  const C* u = static_cast<const C*>((flags & kMvUInput) ? x : w.u);
+  C* scratch = static_cast<C*>(w.spec);
+  const size_t scratch_elems = (size_t)4 * nrhs * a.grid[0] * a.fft[1] * a.fft[2];
+  std::pair<int, int> best = near_size_rule<R>(a, p, nrhs, u, w.v, w.np);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  auto elapsed = [&](float& ms) -> cudaError_t {
+    cudaError_t r = cudaEventSynchronize(e1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+    return r;
+  };
+  const bool skip_cuda_cores = nrhs >= 16 && near_shape_ok<R>(7, a, p, nrhs, u, w.v, w.np);
+  std::vector<std::pair<int, int>> cand;
+  if (!skip_cuda_cores && scratch != nullptr && scratch_elems >= (size_t)a.N * nrhs) {
+    float best_ms = 1e30f;
+    std::pair<int, int> bs = best;
+    for (int tn = 0; tn < 5 && e == cudaSuccess; ++tn)
+      for (int ks : {1, 2, 4}) {
+        int nl = 0;
+        near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, w.np);
+        e = cudaEventRecord(e0, st);
+        near_shape_launch<R>(tn, a, p, nrhs, u, scratch, st, nl, ks, w.np);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        float ms = 0;
+        if (e == cudaSuccess) e = elapsed(ms);
+        if (e != cudaSuccess) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          bs = {tn, ks};
+        }
+      }
+    best = bs;
+    cand.push_back(bs);
+  }
+  if (sizeof(R) == 4 && e == cudaSuccess) {
+    for (int tn = 5; tn < kNearShapes; ++tn)
+      if (near_shape_ok<R>(tn, a, p, nrhs, u, w.v, w.np)) cand.push_back({tn, 1});
+    if (cand.size() > 1) {
+      float best_ms = 1e30f;
+      for (const auto& c : cand) {
+        a.near_tune[key] = c;
+        e = matvec<R>(a, p, w, nrhs, x, y, st, gemm_mode, pre, flags | kMvNoProfile);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = matvec<R>(a, p, w, nrhs, x, y, st, gemm_mode, pre, flags | kMvNoProfile);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        float ms = 0;
+        if (e == cudaSuccess) e = elapsed(ms);
+        if (e != cudaSuccess) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    } else if (cand.size() == 1) {
+      best = cand[0];
+    }
+  }
+  a.near_tune[key] = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
+}
+
 template <typename R>
 cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv, void* yv, cudaStream_t st,
                    int gemm_mode, bool pre, unsigned flags) {
   typedef typename V2<R>::T C;
+  {
+    // first product of this width and precision with block near field: tune it over whole products
+    const bool csr0 = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
+    const bool blocks0 = a.nfb_entries > 0 && p.nfb_val != nullptr && !csr0;
+    if (blocks0 && !(flags & kMvNoTune) && a.near_force_shape < 0 &&
+        a.near_tune.find(std::make_pair(nrhs, (int)sizeof(R))) == a.near_tune.end()) {
+      const cudaError_t te = near_tune_products<R>(a, p, w, nrhs, xv, yv, st, gemm_mode, pre, flags);
+      if (te != cudaSuccess) return te;
+    }
+  }
   const C* x = static_cast<const C*>(xv);
   C* y = static_cast<C*>(yv);
   C* u = static_cast<C*>(w.u);
@@ -2215,16 +2272,12 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     if (it != a.near_tune.end()) {
       tn = it->second.first;
       ks = it->second.second;
-    } else if (flags & kMvNoTune) {
-      // size rule, not remembered: a later tuned product may still time the shapes
-      const auto rule = near_autotune<R>(a, p, nrhs, u, nullptr, 0, st, w.np);
+    } else {
+      // size rule, not remembered (kMvNoTune, or timing failed): a later tuned
+      // product may still time the shapes
+      const auto rule = near_size_rule<R>(a, p, nrhs, u, v, w.np);
       tn = rule.first;
       ks = rule.second;
-    } else {
-      it = a.near_tune.emplace(key, near_autotune<R>(a, p, nrhs, u, static_cast<C*>(w.spec),
-                                                      (size_t)4 * nrhs * Nx * Py * Pz, st, w.np)).first;
-      tn = it->second.first;
-      ks = it->second.second;
     }
     if (a.near_force_shape >= 0) {
       tn = a.near_force_shape;
