@@ -210,26 +210,29 @@ def test_c3_four_types_64_rhs(c3, prec):
 
 def test_c3_batched_solve_equals_columns_alone(c3):
     """64 incidences solved together (independent Krylov spaces, one product per
-    iteration) give the same solutions as the columns solved alone, within the
-    solver tolerance (P13), and every column meets it."""
+    iteration) give the same solutions as the columns solved alone (P13): both
+    solved to a residual of 1e-6, so that the solutions agree within the 1e-4
+    solution tolerance (the residual bound times the condition number of this
+    preconditioned operator, about 10, stays below it), and every column meets
+    the residual."""
     th, ph, pol = wl.planewave_grid()
     st = torch.cuda.current_stream()
     V = torch.empty(c3.n * 64, dtype=torch.complex128, device="cuda")
     mm.mm_rhs_planewave(c3.array, th, ph, pol, V, mm.MM_C128, st)
     E = torch.empty_like(V)
-    s = mm.mm_solve(c3.array, 64, V, E, tol=1e-4, restart=50, max_iter=2000, precision=mm.MM_C64, refine=1,
-                    inner_tol=1e-5, stream=st)
-    assert s["converged"] and s["rel_residual"] <= 1e-4
+    s = mm.mm_solve(c3.array, 64, V, E, tol=1e-6, restart=50, max_iter=4000, precision=mm.MM_C64, refine=1,
+                    inner_tol=1e-5, stream=st, precond=1)
+    assert s["converged"] and s["rel_residual"] <= 1e-6
     Eb = E.cpu().numpy().reshape(c3.n, 64)
     for j in (0, 37):
         V1 = torch.empty(c3.n, dtype=torch.complex128, device="cuda")
         mm.mm_rhs_planewave(c3.array, [th[j]], [ph[j]], [pol[j]], V1, mm.MM_C128, st)
         E1 = torch.empty_like(V1)
-        s1 = mm.mm_solve(c3.array, 1, V1, E1, tol=1e-4, restart=50, max_iter=2000, precision=mm.MM_C64, refine=1,
-                         inner_tol=1e-5, stream=st)
+        s1 = mm.mm_solve(c3.array, 1, V1, E1, tol=1e-6, restart=50, max_iter=4000, precision=mm.MM_C64, refine=1,
+                         inner_tol=1e-5, stream=st, precond=1)
         assert s1["converged"]
         e1 = E1.cpu().numpy()
-        assert np.linalg.norm(Eb[:, j] - e1) / np.linalg.norm(e1) <= 2e-3
+        assert np.linalg.norm(Eb[:, j] - e1) / np.linalg.norm(e1) <= 1e-4
 
 
 @pytest.mark.parametrize("prec", [mm.MM_C128, mm.MM_C64])
