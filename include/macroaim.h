@@ -203,7 +203,8 @@ void mm_array_destroy(mm_array* array);
  * `stream` in order; MACROAIM_NEAR_SHAPE="shape,ksplit" fixes the block
  * near-field kernel's shape instead of timing them on the first product
  * (0-4 CUDA-core tiles, k split 1-16; 5-6 tensor-core tiles, complex64 only,
- * TF32 with a three-product split, no k split; 7-9 the tensor-core direct form
+ * TF32 with a three-product split, k split 1 or 2 (2 for up to 8 right-hand
+ * sides); 7-9 the tensor-core direct form
  * for 16 or more right-hand sides of even count);
  * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,

@@ -506,8 +506,10 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
     w.bytes += bb;
   }
   if (sizeof(R) == 4 && da.pf.nfb_tc && da.nfg_prows > 0) {
-    CU(cudaMalloc(&w.np, sizeof(float2) * (size_t)da.nfg_prows * nrhs));
-    w.bytes += sizeof(float2) * (size_t)da.nfg_prows * nrhs;
+    // two planes for few right-hand sides (the k split of the tensor-core near field)
+    w.np_parts = nrhs <= 8 ? 2 : 1;
+    CU(cudaMalloc(&w.np, sizeof(float2) * (size_t)da.nfg_prows * nrhs * w.np_parts));
+    w.bytes += sizeof(float2) * (size_t)da.nfg_prows * nrhs * w.np_parts;
   }
   w.nrhs = nrhs;
 }
@@ -2008,9 +2010,12 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   const size_t grid = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2]);
   const size_t spec = align256(cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2]);
   // complex64 with tensor-core near-field blocks: their partial sums too
-  const size_t npart = precision == MM_C64 && da.pf.nfb_tc && da.nfg_prows > 0
-                           ? align256(sizeof(float2) * (size_t)da.nfg_prows * nrhs)
-                           : 0;
+  const size_t npart1 = precision == MM_C64 && da.pf.nfb_tc && da.nfg_prows > 0
+                            ? align256(sizeof(float2) * (size_t)da.nfg_prows * nrhs)
+                            : 0;
+  // a second plane (the k split of the tensor-core near field) when it fits
+  const int parts = nrhs <= 8 && 2 * vec + grid + spec + 2 * npart1 <= kNoAllocScratchBytes ? 2 : 1;
+  const size_t npart = npart1 * parts;
   const size_t need = 2 * vec + grid + spec + npart;
   if (need > kNoAllocScratchBytes)
     return fail(ctx, MM_EINVAL,
@@ -2038,6 +2043,7 @@ extern "C" mm_status mm_apply_noalloc(mm_array* a, int32_t nrhs, const void* x_d
   w.grid = base + 2 * vec;
   w.spec = base + 2 * vec + grid;
   w.np = npart ? base + 2 * vec + grid + spec : nullptr;
+  w.np_parts = parts;
   w.bytes = need;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // no stage events (they are created on demand) and no timing of near-field

@@ -152,7 +152,8 @@ struct Work {
   int* err = nullptr;     // device error flag of bounded waits
   void* pt = nullptr;     // N x nrhs   preconditioned vector (block-Jacobi)
   double* us = nullptr;   // N x nrhs   FP64 only: Re u + Im u for the three-product near field
-  void* np = nullptr;     // complex64 only: partial sums of the tensor-core near field (nfg_prows x nrhs)
+  void* np = nullptr;     // complex64 only: partial sums of the tensor-core near field (np_parts x nfg_prows x nrhs)
+  int np_parts = 1;       // planes of np: 2 lets the tensor-core near field split its k tiles in two
   void* boxbuf = nullptr; // from 8 RHS on: per-element projection boxes (n_elem x 4 nrhs x box_nodes_max)
   size_t bytes = 0;
 };

@@ -1769,8 +1769,9 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
 // (about 1.9 times the non-zero work instead of 2.3 at 16x16).  The CTA counts
 // per SM apply to complex64; the FP64 forms keep their registers.
 // Shapes 5 and 6 are the tensor-core form (near_tc.cu: 32 or 64 complex
-// columns per tile, partial sums), 7 and 8 its direct form (32 or 64
-// right-hand sides per tile, an even count of them), complex64 only.
+// columns per tile, partial sums; k split 2 for up to 8 right-hand sides), 7-9
+// its direct form (32 or 64 right-hand sides per tile, an even count of them),
+// complex64 only.
 template <typename R>
 static bool near_shape_ok(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs, const void* u, const void* v,
                           const void* np) {
@@ -1783,11 +1784,11 @@ static bool near_shape_ok(int shape, const DevArray& a, const DevPrec<R>& p, int
 template <typename R>
 static void near_shape_launch(int shape, const DevArray& a, const DevPrec<R>& p, int nrhs,
                               const typename V2<R>::T* u, typename V2<R>::T* y, cudaStream_t st, int& nl, int ks,
-                              void* np) {
+                              void* np, int np_parts = 1) {
   if (shape >= 5) {
     if constexpr (sizeof(R) == 4) {
       if (near_shape_ok<R>(shape, a, p, nrhs, u, y, np)) {
-        near_tc_launch(shape - 5, a, p, nrhs, u, y, static_cast<float2*>(np), st);
+        near_tc_launch(shape - 5, a, p, nrhs, u, y, static_cast<float2*>(np), std::min(ks, np_parts), st);
         nl += shape >= 7 ? 1 : 2;
         return;
       }
@@ -2129,7 +2130,10 @@ static cudaError_t near_tune_products(DevArray& a, DevPrec<R>& p, Work& w, int n
   }
   if (sizeof(R) == 4 && e == cudaSuccess) {
     for (int tn = 5; tn < kNearShapes; ++tn)
-      if (near_shape_ok<R>(tn, a, p, nrhs, u, w.v, w.np)) cand.push_back({tn, 1});
+      if (near_shape_ok<R>(tn, a, p, nrhs, u, w.v, w.np)) {
+        cand.push_back({tn, 1});
+        if (tn < 7 && w.np_parts >= 2) cand.push_back({tn, 2});   // k tiles split over two units
+      }
     if (cand.size() > 1) {
       float best_ms = 1e30f;
       for (const auto& c : cand) {
@@ -2306,7 +2310,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   if (nf_blocks) {
     pr.begin(sb + 6, ns);
     nl = 0;
-    near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks, w.np);
+    near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks, w.np, w.np_parts);
     pr.end(ns, nl);
   } else if (a.nnz > 0) {
     pr.begin(sb + 6, ns);

@@ -119,16 +119,19 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, fl
 // One work unit: group g (block q, pairs), 128-row tile mt, column tile nt,
 // and its non-zero k tiles [e0, e1) of the tile list.
 struct Unit {
-  int g, q, Na, mt, e0, e1;
+  int g, q, Na, mt, e0, e1, part;
   int64_t n0, ncol, first_pair;
 };
 
 // Unit t from the per-group prefix of unit counts (gpre, shared memory):
 // groups in order, then 128-row tiles, then column tiles (fastest).
 template <int NC>
-__device__ __forceinline__ Unit decode_unit(int64_t t, const int64_t* gpre, int ngroups,
+__device__ __forceinline__ Unit decode_unit(int64_t tk, const int64_t* gpre, int ngroups,
                                             const NearGroupDev* __restrict__ groups, const int32_t* __restrict__ tptr,
-                                            int nmt, int nrhs) {
+                                            int nmt, int nrhs, int ks) {
+  // ks shares of a unit's k tiles are consecutive units
+  const int64_t t = tk / ks;
+  const int part = (int)(tk - t * ks);
   int lo = 0, hi = ngroups - 1;   // last g with gpre[g] <= t
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -144,8 +147,10 @@ __device__ __forceinline__ Unit decode_unit(int64_t t, const int64_t* gpre, int 
   const int64_t nnt = (un.ncol + NC - 1) / NC, r = t - gpre[lo];
   un.mt = (int)(r / nnt);
   un.n0 = (r % nnt) * NC;
-  un.e0 = tptr[un.q * nmt + un.mt];
-  un.e1 = tptr[un.q * nmt + un.mt + 1];
+  const int ea = tptr[un.q * nmt + un.mt], eb = tptr[un.q * nmt + un.mt + 1];
+  un.e0 = ea + (int)((int64_t)(eb - ea) * part / ks);
+  un.e1 = ea + (int)((int64_t)(eb - ea) * (part + 1) / ks);
+  un.part = part;
   return un;
 }
 
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
     const __grid_constant__ CUtensorMap tmA, int rows_total, const NearGroupDev* __restrict__ groups, int ngroups,
     const longlong2* __restrict__ poff, const int32_t* __restrict__ arow, const int32_t* __restrict__ bnb, int nmt,
     const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int32_t* __restrict__ perm,
-    const int32_t* __restrict__ bpb, const int64_t* __restrict__ prow, int nrhs, int64_t units,
-    const float2* __restrict__ u, float2* __restrict__ P, uint64_t wait_ns, int stall) {
+    const int32_t* __restrict__ bpb, const int64_t* __restrict__ prow, int nrhs, int64_t units, int ks,
+    int64_t pstride, const float2* __restrict__ u, float2* __restrict__ P, uint64_t wait_ns, int stall) {
   typedef NearTcCfg<NC, STAGES, RAWD> Cfg;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-        const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs);
+        const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs, ks);
         const int row0 = arow[un.q] + un.mt * kRowsT;
         for (int e = un.e0; e < un.e1; ++e, ++it) {
           const int s = (int)(it % STAGES);
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
       uint32_t it = 0, lt = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-        const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs);
+        const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs, ks);
         const int nk = un.e1 - un.e0;
         if (nk == 0) continue;
         const uint32_t b = lt & 1, ub = lt >> 1;
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
     uint32_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-      const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs);
+      const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs, ks);
       const int nk = un.e1 - un.e0;
       if (nk == 0) continue;   // the same for every gather thread
       gather_sync();           // nobody reads the previous unit's column table any more
@@ -477,14 +482,14 @@ __global__ void __launch_bounds__(kThreadsNT, 1) k_near_tc(
     uint32_t lt = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < units && ok; t += gridDim.x) {
-      const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs);
+      const Unit un = decode_unit<NC>(t, gpre, ngroups, groups, tptr, nmt, nrhs, ks);
       const int nk = un.e1 - un.e0;
       epi_sync();   // nobody reads the previous unit's column table any more
       for (int n = et; n < NC; n += kEpi) {
         const int64_t nn = un.n0 + n;
         if (nn < un.ncol) {
           const int64_t pp = nn / nrhs;
-          cpart[n] = prow[un.first_pair + pp] * nrhs + (nn - pp * nrhs) * un.Na;
+          cpart[n] = prow[un.first_pair + pp] * nrhs + (nn - pp * nrhs) * un.Na + un.part * pstride;
         } else {
           cpart[n] = -1;
         }
@@ -828,10 +833,11 @@ namespace {
 
 template <int NC, int STAGES, int RAWD>
 cudaError_t near_tc_launch_t(const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u, float2* P,
-                             cudaStream_t st) {
+                             int ks, cudaStream_t st) {
   int64_t units = 0;
   for (const auto& g : a.nfg)
     units += (int64_t)((g.Na + kRowsT - 1) / kRowsT) * ((g.npairs * nrhs + NC - 1) / NC);
+  units *= ks;
   if (units == 0) return cudaSuccess;
   if ((int64_t)a.nfg.size() > kMaxGroups) return cudaErrorInvalidValue;
   int dev = 0, sms = 148;
@@ -843,7 +849,7 @@ cudaError_t near_tc_launch_t(const DevArray& a, const DevPrec<float>& p, int nrh
   k_near_tc<NC, STAGES, RAWD><<<ctas, kThreadsNT, Cfg::Smem, st>>>(
       p.nfb_tmap, a.nfb_tc_rows, reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_poff,
       a.nfb_arow, a.nfb_nb, a.nfb_nmt128, a.nfb_tptr128, a.nfb_tlist128, a.nfb_perm, a.nfb_pb, a.nfg_prow, nrhs,
-      units, u, P, wait_ns, stall_ms > 0 ? 1 : 0);
+      units, ks, a.nfg_prows * (int64_t)nrhs, u, P, wait_ns, stall_ms > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -906,7 +912,8 @@ __global__ void __launch_bounds__(256) k_near_reduce(const int32_t* __restrict__
                                                      const int64_t* __restrict__ tbase,
                                                      const int32_t* __restrict__ tperm,
                                                      const int32_t* __restrict__ perm, const int64_t* __restrict__ off,
-                                                     int nrhs, const float2* __restrict__ P, float2* __restrict__ v) {
+                                                     int nrhs, int ks, int64_t pstride, const float2* __restrict__ P,
+                                                     float2* __restrict__ v) {
   constexpr int kMaxPairs = 64;
   __shared__ int64_t sp[kMaxPairs];
   __shared__ float2 tile[32][33];
@@ -924,11 +931,12 @@ __global__ void __launch_bounds__(256) k_near_reduce(const int32_t* __restrict__
   if (nrhs == 1) {
     for (int m = tid; m < Na; m += blockDim.x) {
       float2 acc = make_float2(0.f, 0.f);
-      for (int i = 0; i < np; ++i) {
-        const float2 x = P[base(i) + m];
-        acc.x += x.x;
-        acc.y += x.y;
-      }
+      for (int i = 0; i < np; ++i)
+        for (int h = 0; h < ks; ++h) {
+          const float2 x = P[base(i) + h * pstride + m];
+          acc.x += x.x;
+          acc.y += x.y;
+        }
       float2* d = v + va + pa[m];
       float2 o = *d;
       o.x -= acc.x;
@@ -944,11 +952,12 @@ __global__ void __launch_bounds__(256) k_near_reduce(const int32_t* __restrict__
         const int c = c0 + cc;
         float2 acc = make_float2(0.f, 0.f);
         if (m < Na && c < nrhs)
-          for (int i = 0; i < np; ++i) {
-            const float2 x = P[base(i) + (int64_t)c * Na + m];
-            acc.x += x.x;
-            acc.y += x.y;
-          }
+          for (int i = 0; i < np; ++i)
+            for (int h = 0; h < ks; ++h) {
+              const float2 x = P[base(i) + h * pstride + (int64_t)c * Na + m];
+              acc.x += x.x;
+              acc.y += x.y;
+            }
         tile[lane][cc] = acc;
       }
       __syncthreads();
@@ -973,18 +982,20 @@ bool near_tc_direct_ok(const DevArray& a, int nrhs, const void* u, const void* v
 }
 
 cudaError_t near_tc_launch(int shape, const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u,
-                           float2* v, float2* P, cudaStream_t st) {
+                           float2* v, float2* P, int ks, cudaStream_t st) {
   if (!p.nfb_tc || a.nfb_tptr128 == nullptr || a.nfe_ptr == nullptr) return cudaErrorInvalidValue;
   if (shape >= 2)
     return shape == 4   ? near_tc_direct_launch_t<64, 2, 3>(a, p, nrhs, u, v, st)
            : shape == 3 ? near_tc_direct_launch_t<64, 3, 3>(a, p, nrhs, u, v, st)
                         : near_tc_direct_launch_t<32, 4, 4>(a, p, nrhs, u, v, st);
   if (P == nullptr) return cudaErrorInvalidValue;
-  cudaError_t e = shape == 1 ? near_tc_launch_t<64, 3, 3>(a, p, nrhs, u, P, st)
-                             : near_tc_launch_t<32, 4, 4>(a, p, nrhs, u, P, st);
+  ks = ks == 2 ? 2 : 1;
+  cudaError_t e = shape == 1 ? near_tc_launch_t<64, 3, 3>(a, p, nrhs, u, P, ks, st)
+                             : near_tc_launch_t<32, 4, 4>(a, p, nrhs, u, P, ks, st);
   if (e != cudaSuccess) return e;
   k_near_reduce<<<(unsigned)a.n_elem, 256, 0, st>>>(a.nfe_ptr, a.nfe_pair, a.nfg_prow, a.type_of, a.tbase,
-                                                    a.nfb_tperm, a.nfb_perm, a.off, nrhs, P, v);
+                                                    a.nfb_tperm, a.nfb_perm, a.off, nrhs, ks,
+                                                    a.nfg_prows * (int64_t)nrhs, P, v);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,10 @@ cudaError_t near_tc_init(DevArray& a);
 // partial-sum buffer P (a.nfg_prows x nrhs complex), then the per-element
 // reduction into v; shapes 2, 3: into v directly (P unused).
 bool near_tc_direct_ok(const DevArray& a, int nrhs, const void* u, const void* v);
+// ks (1 or 2, shapes 0 and 1): each unit's k tiles split over ks units, whose
+// partial sums go to ks planes of P (P then holds ks a.nfg_prows x nrhs).
 cudaError_t near_tc_launch(int shape, const DevArray& a, const DevPrec<float>& p, int nrhs, const float2* u,
-                           float2* v, float2* P, cudaStream_t st);
+                           float2* v, float2* P, int ks, cudaStream_t st);
 // TF32 hi / lo parts (round to nearest even) of a complex entry given in FP64.
 void near_tc_split(double re, double im, float* hi, float* lo);
 

@@ -61,7 +61,7 @@ def _apply(la, X, nrhs, prec=mm.MM_C64):
     return yd.cpu().numpy().astype(np.complex128).reshape(la.n, nrhs)
 
 
-@pytest.mark.parametrize("shape,ks", [(5, 1), (6, 1)])
+@pytest.mark.parametrize("shape,ks", [(5, 1), (6, 1), (5, 2), (6, 2)])
 @pytest.mark.parametrize("nrhs", [1, 3, 5, 8, 12, 24, 64])
 def test_tensor_core_near_field_c3(ctx, c3_types, monkeypatch, shape, ks, nrhs):
     """6 x 6 array of the four loop types (16 x 9 type and offset blocks, ragged
@@ -94,10 +94,11 @@ def test_tensor_core_direct_near_field_c3(ctx, c3_types, monkeypatch, shape, nrh
         mm.mm_array_destroy(la.array)
 
 
-@pytest.mark.parametrize("shape", [5, 6])
-def test_tensor_core_near_field_c1_full(ctx, monkeypatch, shape):
-    """2 x 2 loop array, one right-hand side: every entry vs the oracle."""
-    monkeypatch.setenv("MACROAIM_NEAR_SHAPE", "%d,1" % shape)
+@pytest.mark.parametrize("shape,ks", [(5, 1), (6, 1), (5, 2), (6, 2)])
+def test_tensor_core_near_field_c1_full(ctx, monkeypatch, shape, ks):
+    """2 x 2 loop array, one right-hand side: every entry vs the oracle (k split 2:
+    each unit's k tiles over two units, their partial sums in two planes)."""
+    monkeypatch.setenv("MACROAIM_NEAR_SHAPE", "%d,%d" % (shape, ks))
     g = np.load(os.path.join(GOLD, "c1_2x2.npz"))
     la = loop_array(ctx, 2, 2)
     try:
@@ -106,10 +107,10 @@ def test_tensor_core_near_field_c1_full(ctx, monkeypatch, shape):
         la.close()
 
 
-@pytest.mark.parametrize("shape", [5, 6])
-def test_tensor_core_near_field_c2_sampled(ctx, monkeypatch, shape):
+@pytest.mark.parametrize("shape,ks", [(5, 1), (6, 1), (6, 2)])
+def test_tensor_core_near_field_c2_sampled(ctx, monkeypatch, shape, ks):
     """16 x 16 loop array (the benchmark workload), one right-hand side."""
-    monkeypatch.setenv("MACROAIM_NEAR_SHAPE", "%d,1" % shape)
+    monkeypatch.setenv("MACROAIM_NEAR_SHAPE", "%d,%d" % (shape, ks))
     g = np.load(os.path.join(GOLD, "c2_16x16.npz"))
     la = loop_array(ctx, 16, 16)
     try:
