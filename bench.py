@@ -297,6 +297,7 @@ def cufft_measure(info: dict, nrhs: int, ours_ms: float, reps: int = 20) -> dict
 def run_ours(args, rank, world, local):
     import torch
     import paper_1712_02443_gb300 as mm
+    from paper_1712_02443_gb300 import workloads as wl
     from paper_1712_02443_gb300.arrays import loop_array
     from paper_1712_02443_gb300.build import build
 
@@ -324,10 +325,10 @@ def run_ours(args, rank, world, local):
 
     pc = 0 if args.no_precond else 1
 
-    def step(prec=mm.MM_C64, refine=1, precond=None):
+    def step(prec=mm.MM_C64, refine=1, precond=None, residual=0):
         mm.mm_rhs_planewave(la.array, th, ph, pol, V, mm.MM_C128, st)
         return mm.mm_solve(la.array, 1, V, E, tol=TOL, restart=50, max_iter=2000, precision=prec, refine=refine,
-                           inner_tol=1e-5, stream=st, precond=pc if precond is None else precond)
+                           inner_tol=1e-5, stream=st, precond=pc if precond is None else precond, residual=residual)
 
     for _ in range(args.warmup):
         step()
@@ -392,6 +393,8 @@ def run_ours(args, rank, world, local):
                               "matvecs_per_solve": round(matvecs / args.steps, 1),
                               "stages": {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"]}
                                          for k, v in prof.items()},
+                              "stages_c128": {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"]}
+                                              for k, v in prof128.items() if k != "krylov"},
                               "tuning": mm.mm_array_tuning(la.array, 1)}))
         mm.mm_array_destroy(la.array)
         if dist is not None:
@@ -428,6 +431,44 @@ def run_ours(args, rank, world, local):
             t0ms += e0.elapsed_time(e1)
         unpc = {"solves_per_s": round(world * k64 / (t0ms / 1e3), 2),
                 "matvecs_per_s": round(world * mv0 / (t0ms / 1e3), 1), "matvecs_per_solve": round(mv0 / k64, 1)}
+
+    # ---- the refinement residual's two forms: one complex128 product each, with
+    # the float-float contractions (the default) and in plain FP64, and the
+    # solve rate with the FP64 residual
+    xr = torch.from_numpy(wl.random_cvec(N, 1, 7)).cuda()
+    yr = {p_: torch.empty_like(xr) for p_ in (mm.MM_C128_FF, mm.MM_C128)}
+    res_ms = {}
+    for p_ in (mm.MM_C128_FF, mm.MM_C128):
+        for _ in range(2):
+            mm.mm_apply(la.array, 1, xr, yr[p_], p_, st)
+        tt = 0.0
+        for k in range(10):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            mm.mm_apply(la.array, 1, xr, yr[p_], p_, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tt += e0.elapsed_time(e1)
+        res_ms[p_] = tt / 10
+    rdiff = float(torch.linalg.vector_norm(yr[mm.MM_C128_FF] - yr[mm.MM_C128]) / torch.linalg.vector_norm(yr[mm.MM_C128]))
+    step(residual=1)
+    torch.cuda.synchronize()
+    tres = 0.0
+    for k in range(k64):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step(residual=1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tres += e0.elapsed_time(e1)
+    residual_forms = {"float_float_product_ms": round(res_ms[mm.MM_C128_FF], 4),
+                      "fp64_product_ms": round(res_ms[mm.MM_C128], 4),
+                      "rel_diff_vs_fp64_product": rdiff,
+                      "solves_per_s_with_fp64_residual": round(world * k64 / (tres / 1e3), 2),
+                      "note": "complex128 product (c2, 1 RHS, L2 flushed): macromodel GEMM and block near field in "
+                              "float-float arithmetic on the FP32 pipe (the solves' default residual) vs plain FP64"}
 
     # ---- end to end through the public API: one library call per solve with host
     # angles in and the solution copied by the library into host memory
@@ -497,7 +538,8 @@ def run_ours(args, rank, world, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "precision": "complex64 operator (FP32 FFT, SpMV, macromodel GEMM); FP64 Arnoldi, Givens, refinement",
+        "precision": "complex64 operator (FP32 FFT, SpMV, macromodel GEMM); FP64 Arnoldi, Givens; refinement "
+                     "residual with the complex128 operator, its GEMM and near field in float-float arithmetic",
         "preconditioner": "block-Jacobi (inverse element self blocks), right, in both forms" if pc else "none",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": N, "nrhs": 1, "tol": TOL, "restart": 50,
@@ -515,6 +557,7 @@ def run_ours(args, rank, world, local):
                             "matvecs_per_solve": round(mv64 / k64, 1)},
         "speedup_vs_fp64_form_solves": round(solves_per_s / (world * k64 / (t64 / 1e3)), 3),
         "without_preconditioner": unpc,
+        "refinement_residual": residual_forms,
         "e2e": {"value": round(world * mv_e2e / e2e_s, 1), "unit": "matvecs/s",
                 "solves_per_s": round(world * args.steps / e2e_s, 2),
                 "h2d_bytes_per_step": 8 + 8 + 4, "d2h_bytes_per_step": 16 * N,

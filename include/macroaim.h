@@ -55,7 +55,12 @@ typedef enum mm_precision {
   MM_C128 = 1,      /* complex128 operator (the plain FP64 GPU form)             */
   MM_C64_BF16 = 2,  /* complex64 operator, macromodel product on tensor cores   */
                     /* with BF16 inputs and FP32 accumulation (vectors: c64)     */
-  MM_C64_F16 = 3    /* same with FP16 inputs                                     */
+  MM_C64_F16 = 3,   /* same with FP16 inputs                                     */
+  MM_C128_FF = 4    /* complex128 vectors and operator data; every stage of the   */
+                    /* product in float-float arithmetic (each value an           */
+                    /* unevaluated sum of two floats, Dekker 1971) on the FP32    */
+                    /* pipe, FP64 between the stages: within 1e-12 of the MM_C128 */
+                    /* product (relative 2-norm).  mm_apply and mm_apply_batch.   */
 } mm_precision;
 
 typedef struct mm_ctx mm_ctx;
@@ -339,6 +344,9 @@ typedef struct mm_solve_opts {
                          shared by identical elements.  The solution is the
                          same; GMRES needs fewer iterations.  Not a method of
                          the paper (which names ILU), a library option.         */
+  int32_t residual;   /* refinement residual b - Z x: 0 = complex128 operator
+                         with the float-float contractions (MM_C128_FF, the
+                         default); 1 = plain FP64 (MM_C128)                     */
 } mm_solve_opts;
 typedef struct mm_solve_stats {
   int32_t iterations;     /* inner GMRES iterations (max over columns)        */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmacroaim.so")
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENOCONV, MM_EBREAKDOWN, MM_ETIMEOUT, MM_EBUSY, MM_EINTERNAL = range(9)
 STATUS_NAMES = ["MM_OK", "MM_EINVAL", "MM_ENOMEM", "MM_ECUDA", "MM_ENOCONV", "MM_EBREAKDOWN", "MM_ETIMEOUT",
                 "MM_EBUSY", "MM_EINTERNAL"]
-MM_C64, MM_C128, MM_C64_BF16, MM_C64_F16 = 0, 1, 2, 3
+MM_C64, MM_C128, MM_C64_BF16, MM_C64_F16, MM_C128_FF = 0, 1, 2, 3, 4
 MM_MAT_M, MM_MAT_D, MM_MAT_T, MM_MAT_A, MM_MAT_B, MM_MAT_GHH, MM_MAT_GHE, MM_MAT_PJ = range(8)
 STAGES = ["gemm", "project", "fft_fwd", "fft_conv", "fft_inv", "interp", "near", "krylov"]
 MM_EXPORT_ANCHORS, MM_EXPORT_PI, MM_EXPORT_NEAR_PTR, MM_EXPORT_NEAR_COL, MM_EXPORT_NEAR_VAL, MM_EXPORT_GHAT = range(6)
@@ -50,7 +50,8 @@ class mm_array_info(ct.Structure):
 
 class mm_solve_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
-                ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32), ("precond", ct.c_int32)]
+                ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32), ("precond", ct.c_int32),
+                ("residual", ct.c_int32)]
 
 
 class mm_solve_stats(ct.Structure):
@@ -381,8 +382,8 @@ def mm_rcs(array, nrhs: int, Jhat_dev, theta, phi) -> np.ndarray:
 
 def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_iter: int = 1000,
              precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2, stream=None, check: bool = True,
-             orth: int = 0, precond: int = 0):
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond)
+             orth: int = 0, precond: int = 0, residual: int = 0):
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, residual)
     s = mm_solve_stats()
     st = load().mm_solve(array, nrhs, _ptr(V_dev), _ptr(E_dev), ct.byref(o), ct.byref(s), _stream(stream))
     stats = {"iterations": s.iterations, "matvecs": s.matvecs, "refinements": s.refinements,
@@ -394,14 +395,14 @@ def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_
 
 def mm_solve_planewave_host(array, theta, phi, pol, E_host: np.ndarray, tol: float, restart: int = 50,
                             max_iter: int = 1000, precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2,
-                            orth: int = 0, precond: int = 0, check: bool = True):
+                            orth: int = 0, precond: int = 0, check: bool = True, residual: int = 0):
     """Excitation, solve and the solution copied into E_host (complex128, N x nrhs), all in the library."""
     th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
     ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
     po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
     if E_host.dtype != np.complex128 or not E_host.flags.c_contiguous:
         raise ValueError("E_host must be a C-contiguous complex128 array")
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond)
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, residual)
     s = mm_solve_stats()
     st = load().mm_solve_planewave_host(array, len(th), _ptr(th), _ptr(ph), _ptr(po), _ptr(E_host), ct.byref(o),
                                         ct.byref(s))

@@ -16,6 +16,7 @@
 
 #include "aim_setup.h"
 #include "device.h"
+#include "ffops.cuh"
 #include "internal.h"
 #include "macroaim.h"
 #include "post.h"
@@ -424,6 +425,103 @@ void upload_pj(mm_array* a, mm::DevPrec<R>& p) {
   }
 }
 
+// Operands of the float-float complex128 product (matvec flag kMvFF): [M; D]
+// per type and the near-field blocks, each complex entry as re, im and re + im
+// split into a float and the float nearest to the remainder.
+mm::F6 f6_host(mm::cd z) {
+  auto split = [](double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
+  mm::F6 f;
+  split(z.real(), f.rh, f.rl);
+  split(z.imag(), f.ih, f.il);
+  split(z.real() + z.imag(), f.sh, f.sl);
+  return f;
+}
+
+void upload_ff(mm_array* a) {
+  auto& p = a->da.pd;
+  if (p.ff_ready) return;
+  auto& da = a->da;
+  const auto& ah = a->ah;
+  for (int64_t t = 0; t < da.n_types; ++t) {
+    const auto& tm = a->types[t]->tm;
+    const int64_t Nh = tm.Nh;
+    std::vector<mm::F6> W(2 * Nh * Nh);
+    for (int64_t i = 0; i < Nh * Nh; ++i) {
+      W[i] = f6_host(tm.M[i]);
+      W[Nh * Nh + i] = f6_host(tm.D[i]);
+    }
+    p.ffW.push_back(dev_upload(W.data(), W.size(), da.bytes));
+    // projection / interpolation weights: [s][n] -> (hi x, y, z, phi), (lo x, y, z, phi)
+    const auto& Pi = ah.tai[t].Pi;
+    const int S = ah.tai[t].S;
+    std::vector<float> P((size_t)S * Nh * 8);
+    for (int64_t n = 0; n < Nh; ++n)
+      for (int sn = 0; sn < S; ++sn)
+        for (int c = 0; c < 4; ++c) {
+          const double w = Pi[((size_t)n * S + sn) * 4 + c];
+          const float hi = (float)w;
+          float* d = P.data() + ((size_t)sn * Nh + n) * 8;
+          d[c] = hi;
+          d[4 + c] = (float)(w - (double)hi);
+        }
+    p.ff_Pi.push_back(dev_upload(P.data(), P.size(), da.bytes));
+  }
+  if (da.nfb_entries > 0) {
+    std::vector<mm::F6> d((size_t)da.nfb_entries, f6_host(mm::cd(0.0, 0.0)));
+    int64_t o = 0;
+    for (const auto& b : ah.nf_blocks) {
+      if (b.ptr.empty()) continue;
+      const auto &ia = a->nf_iperm[b.ta], &ib = a->nf_iperm[b.tb];   // original -> sorted position
+      for (int64_t m = 0; m < b.Na; ++m)
+        for (int64_t q = b.ptr[m]; q < b.ptr[m + 1]; ++q)
+          d[(size_t)(o + (int64_t)ia[m] * b.Nb + ib[b.col[q]])] = f6_host(b.val[q]);
+      o += b.Na * b.Nb;
+    }
+    p.ff_nfb = dev_upload(d.data(), d.size(), da.bytes);
+  }
+  auto ffv = [](double x) {
+    const float hi = (float)x;
+    return mm::FFv(hi, (float)(x - (double)hi));
+  };
+  {
+    // the Green's spectrum [ky][kz][kx] and the twiddles of the FFT stages
+    const int64_t Px = ah.fft[0], Py = ah.fft[1], Pz = ah.fft[2];
+    std::vector<mm::CF> g(Px * Py * Pz);
+    for (int64_t i = 0; i < Px; ++i)
+      for (int64_t j = 0; j < Py; ++j)
+        for (int64_t l = 0; l < Pz; ++l) {
+          const auto& z = ah.Ghat[(i * Py + j) * Pz + l];
+          g[(j * Pz + l) * Px + i] = mm::CF{ffv(z.real()), ffv(z.imag())};
+        }
+    p.ff_Ghat = dev_upload(g.data(), g.size(), da.bytes);
+    auto tw = [&](int64_t L) {
+      std::vector<mm::CF> t(L);
+      for (int64_t k = 0; k < L; ++k) {
+        const double th = -2.0 * M_PI * (double)k / (double)L;
+        t[k] = mm::CF{ffv(std::cos(th)), ffv(std::sin(th))};
+      }
+      return dev_upload(t.data(), t.size(), da.bytes);
+    };
+    p.ff_twx = tw(Px);
+    p.ff_twy = tw(Py);
+    p.ff_twz = tw(Pz);
+  }
+  p.ff_ready = true;
+}
+
+// x and u as F6 for the float-float product (after ensure_work<double>)
+void ensure_ff_work(mm_array* a, mm::Work& w, int nrhs) {
+  if (w.x6 && w.u6) return;
+  ++a->epoch;
+  const size_t b = sizeof(mm::F6) * (size_t)a->da.N * nrhs;
+  CU(cudaMalloc(&w.x6, b));
+  CU(cudaMalloc(&w.u6, b));
+  w.bytes += 2 * b;
+}
+
 template <typename R>
 void ensure_pt(mm_array* a, mm::Work& w, int nrhs) {
   if (w.pt) return;
@@ -483,7 +581,7 @@ void ensure_work(mm_array* a, mm::Work& w, int nrhs) {
   if (w.nrhs == nrhs) return;
   typedef typename mm::V2<R>::T C;
   ++a->epoch;
-  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np, w.boxbuf})
+  for (void* q : {w.u, w.v, w.grid, w.spec, w.bt, (void*)w.err, w.pt, (void*)w.us, w.np, w.boxbuf, w.x6, w.u6})
     if (q) cudaFree(q);
   w = mm::Work();
   auto& da = a->da;
@@ -531,6 +629,10 @@ void free_prec_f(mm::DevPrec<float>& p) {
     for (void* q : v) cudaFree(q);
 }
 void free_prec_d(mm::DevPrec<double>& p) {
+  for (void* q : p.ffW) cudaFree(q);
+  for (void* q : p.ff_Pi) cudaFree(q);
+  for (void* q : {p.ff_nfb, p.ff_twx, p.ff_twy, p.ff_twz, p.ff_Ghat})
+    if (q) cudaFree(q);
   for (void* q : p.PJ) cudaFree(q);
   for (void* q : p.WP) cudaFree(q);
   for (void* q : p.W3) cudaFree(q);
@@ -550,7 +652,8 @@ mm_array::~mm_array() {
   free_prec_f(da.pf);
   free_prec_d(da.pd);
   for (mm::Work* w : {&da.wf, &da.wd})
-    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us, w->np, w->boxbuf})
+    for (void* q : {w->u, w->v, w->grid, w->spec, w->bt, (void*)w->err, w->pt, (void*)w->us, w->np, w->boxbuf,
+                    w->x6, w->u6})
       if (q) cudaFree(q);
   for (auto* p : da.anc) cudaFree(p);
   for (auto* p : da.geo) cudaFree(p);
@@ -1106,6 +1209,14 @@ mm_status mm_array_create(mm_ctx* ctx, int64_t n_elem, const mm_type* const* typ
         da.grid_force_i = gi;
       }
     }
+    // tuning override: MACROAIM_FF_SHAPE="gemm,near" fixes the float-float kernels' tile shapes
+    if (const char* fs = std::getenv("MACROAIM_FF_SHAPE")) {
+      int fg = 0, fn = 0;
+      if (std::sscanf(fs, "%d,%d", &fg, &fn) == 2 && fg >= 0 && fg <= 2 && fn >= 0 && fn <= 3) {
+        da.ff_gemm_shape = fg;
+        da.ff_near_shape = fn;
+      }
+    }
     upload_precision<float>(a.get(), da.pf);
     CU(mm::kernels_init(da));
     // the near field's own stream (MACROAIM_NEAR_OVERLAP=0: one stream, in order)
@@ -1151,7 +1262,7 @@ mm_status mm_array_info_get(const mm_array* a, mm_array_info* info) {
 mm_status mm_array_footprint(const mm_array* a, int32_t nrhs, int32_t precision, int32_t restart, size_t* bytes) {
   if (!a || !bytes || nrhs < 1 || restart < 1) return MM_EINVAL;
   const auto& da = a->da;
-  size_t cs = precision == MM_C128 ? 16 : 8;
+  size_t cs = (precision == MM_C128 || precision == MM_C128_FF) ? 16 : 8;
   size_t vec = cs * (size_t)da.N * nrhs;
   size_t g = cs * (size_t)4 * nrhs * da.grid[0] * da.grid[1] * da.grid[2];
   size_t s = cs * (size_t)4 * nrhs * da.grid[0] * da.fft[1] * da.fft[2];
@@ -1159,7 +1270,9 @@ mm_status mm_array_footprint(const mm_array* a, int32_t nrhs, int32_t precision,
   // partial sums of the tensor-core near field (complex64 products)
   size_t np = da.pf.nfb_tc ? sizeof(float) * 2 * (size_t)da.nfg_prows * nrhs : 0;
   size_t bb = nrhs >= 8 ? cs * (size_t)da.n_elem * 4 * nrhs * da.box_nodes_max : 0;   // two-pass projection
-  *bytes = 2 * vec + g + s + kry + np + bb;
+  // x and u as F6 (float-float products: MM_C128_FF, and the refinement residuals of complex64 solves)
+  size_t f6 = precision != MM_C128 ? 2 * sizeof(mm::F6) * (size_t)da.N * nrhs : 0;
+  *bytes = 2 * vec + g + s + kry + np + bb + f6;
   return MM_OK;
 }
 
@@ -1254,10 +1367,16 @@ mm_status mm_apply(mm_array* a, int32_t nrhs, const void* x_dev, void* y_dev, in
       ensure_tc_work(a, a->da.wf, nrhs);
     }
     e = mm::matvec<float>(a->da, a->da.pf, a->da.wf, nrhs, x_dev, y_dev, st, mode);
-  } else if (precision == MM_C128) {
+  } else if (precision == MM_C128 || precision == MM_C128_FF) {
     upload_precision<double>(a, a->da.pd);
     ensure_work<double>(a, a->da.wd, nrhs);
-    e = mm::matvec<double>(a->da, a->da.pd, a->da.wd, nrhs, x_dev, y_dev, st);
+    unsigned fl = 0;
+    if (precision == MM_C128_FF) {
+      upload_ff(a);
+      ensure_ff_work(a, a->da.wd, nrhs);
+      fl = mm::kMvFF;
+    }
+    e = mm::matvec<double>(a->da, a->da.pd, a->da.wd, nrhs, x_dev, y_dev, st, 0, false, fl);
   } else {
     return fail(ctx, MM_EINVAL, "unknown precision");
   }
@@ -1387,10 +1506,10 @@ mm_status mm_apply_host(mm_array* a, int32_t nrhs, const void* x_host, void* y_h
   mm_ctx* ctx = a->ctx;
   if (!a->on_device) return fail(ctx, MM_EINVAL, "array has no device (host-only context)");
   if (nrhs < 1 || !x_host || !y_host) return fail(ctx, MM_EINVAL, "invalid apply arguments");
-  if (precision < MM_C64 || precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
+  if (precision < MM_C64 || precision > MM_C128_FF) return fail(ctx, MM_EINVAL, "unknown precision");
   API_TRY
   CU(cudaSetDevice(a->da.device));
-  size_t bytes = (precision == MM_C128 ? 16 : 8) * (size_t)a->da.N * nrhs;
+  size_t bytes = ((precision == MM_C128 || precision == MM_C128_FF) ? 16 : 8) * (size_t)a->da.N * nrhs;
   if (a->h_cap < bytes) {
     if (a->hx) cudaFree(a->hx);
     if (a->hy) cudaFree(a->hy);
@@ -1479,6 +1598,7 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (opts->precision < MM_C64 || opts->precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
   if (opts->orth < 0 || opts->orth > 3) return fail(ctx, MM_EINVAL, "orth must be 0, 1, 2 or 3");
   if (opts->precond < 0 || opts->precond > 1) return fail(ctx, MM_EINVAL, "precond must be 0 or 1");
+  if (opts->residual < 0 || opts->residual > 1) return fail(ctx, MM_EINVAL, "residual must be 0 or 1");
   if (opts->refine && opts->precision == MM_C128)
     return fail(ctx, MM_EINVAL, "refinement needs a complex64 operator precision");
   API_TRY
@@ -1494,6 +1614,12 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   upload_precision<double>(a, a->da.pd);
   ensure_work<double>(a, a->da.wd, nrhs);
   ensure_work<float>(a, a->da.wf, nrhs);
+  // refinement residuals in float-float arithmetic (the default) or FP64
+  const bool ff_res = opts->refine && opts->residual == 0;
+  if (ff_res) {
+    upload_ff(a);
+    ensure_ff_work(a, a->da.wd, nrhs);
+  }
   const int mode = opts->precision == MM_C64_BF16 ? 1 : (opts->precision == MM_C64_F16 ? 2 : 0);
   if (mode) {
     upload_tc(a, mode);
@@ -1514,8 +1640,9 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   // Z P^-1 throughout and the result is mapped once at the end.
   const bool pj_outer = pj && !opts->refine;
   // Z P^-1 x is one product with the fused macromodel matrices [M PJ; D PJ]
-  S.op64 = [arr, nrhs, pj_outer](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
-    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2, 0, pj_outer);
+  S.op64 = [arr, nrhs, pj_outer, ff_res](const double2* in, double2* out, cudaStream_t s2) -> mm::Status {
+    cudaError_t e = mm::matvec<double>(arr->da, arr->da.pd, arr->da.wd, nrhs, in, out, s2, 0, pj_outer,
+                                       ff_res ? mm::kMvFF : 0u);
     if (e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(e)};
     return {MM_OK, ""};
   };

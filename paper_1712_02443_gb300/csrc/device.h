@@ -15,6 +15,14 @@ namespace mm {
 template <typename R> struct V2;
 template <> struct V2<float> { typedef float2 T; };
 template <> struct V2<double> { typedef double2 T; };
+// The float-float form of the complex128 FFT stages (kernels.cu): complex
+// values CF (ffops.cuh) inside, FP64 grids outside.
+struct FFTag {};
+struct CF;
+template <> struct V2<FFTag> { typedef CF T; };
+// element type of the grids the FFT stages read and write
+template <typename R> struct GridT { typedef typename V2<R>::T T; };
+template <> struct GridT<FFTag> { typedef double2 T; };
 
 // Stage profiler: CUDA events around stages on the launching stream.
 struct Profiler {
@@ -138,6 +146,17 @@ struct DevPrec {
   std::vector<void*> AtcP[2];
   // FP64 only: W and WP with (Re, Im, Re + Im) per entry for the three-multiplication GEMM
   std::vector<void*> W3, WP3;
+  // FP64 only, the float-float contractions (kMvFF): per type [M; D] as F6
+  // entries (2 Nh x Nh, row-major), and the near-field blocks as F6 in the
+  // dense layout of nfb_val; uploaded on first use
+  std::vector<void*> ffW;
+  void* ff_nfb = nullptr;
+  // ... and the FFT stages' twiddles and Green's spectrum as CF (same layouts as twx, twy, twz, Ghat)
+  void *ff_twx = nullptr, *ff_twy = nullptr, *ff_twz = nullptr, *ff_Ghat = nullptr;
+  // ... and per type the projection / interpolation weights as float pairs:
+  // float4 hi, float4 lo (x, y, z, phi) per (stencil node s, basis n), s outermost
+  std::vector<void*> ff_Pi;
+  bool ff_ready = false;
 };
 
 // Work buffers for one (precision, nrhs) pair.
@@ -155,6 +174,8 @@ struct Work {
   void* np = nullptr;     // complex64 only: partial sums of the tensor-core near field (np_parts x nfg_prows x nrhs)
   int np_parts = 1;       // planes of np: 2 lets the tensor-core near field split its k tiles in two
   void* boxbuf = nullptr; // from 8 RHS on: per-element projection boxes (n_elem x 4 nrhs x box_nodes_max)
+  void* x6 = nullptr;     // FP64 only, float-float products: x and u split into F6 entries (N x nrhs)
+  void* u6 = nullptr;
   size_t bytes = 0;
 };
 
@@ -237,6 +258,10 @@ struct DevArray {
   // autotuned block near-field shape per (right-hand sides, sizeof(R)): (kernel shape, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
   int near_force_shape = -1, near_force_ks = 1;   // MACROAIM_NEAR_SHAPE="shape,ksplit": no tuning
+  // tile shapes of the float-float GEMM (0: 32 x 32, 1: 16 x 32, 2: 32 x 64) and
+  // block near field (0: 32 x 32, 1: the same held to three CTAs per SM, 2: 32
+  // rows x 64 columns, 3: 32 x 16); MACROAIM_FF_SHAPE="gemm,near"
+  int ff_gemm_shape = 0, ff_near_shape = 0;
   std::map<std::pair<int, int>, GridTune> grid_tune;   // per (right-hand sides, sizeof(R))
   bool tune_grid = true;                           // MACROAIM_GRID_TUNE=0: variant 0, no timing
   int grid_force_p = -1, grid_force_i = -1;        // MACROAIM_GRID_SCHED="p,i": fixed variants
@@ -265,7 +290,10 @@ constexpr int kNearShapes = 10;
 // right-hand-side count takes the size rule and is not remembered);
 // kMvNoProfile records no stage events (the array's profiler is left alone).
 // kMvUInput takes x as u (the macromodel stage skipped) and v = 0: y = -G x.
-constexpr unsigned kMvNoTune = 1u, kMvNoProfile = 2u, kMvUInput = 4u;
+// kMvFF (complex128 only): every stage in float-float arithmetic on the FP32
+// pipe (DevPrec::ffW and the other ff_ operands, Work::x6 and u6 must be in
+// place); the stages exchange FP64 vectors and grids.
+constexpr unsigned kMvNoTune = 1u, kMvNoProfile = 2u, kMvUInput = 4u, kMvFF = 8u;
 // gemm_mode: 0 CUDA-core GEMM; 1 BF16 / 2 FP16 tensor-core GEMM (complex64 only)
 // pre: apply Z P^-1 (the block-Jacobi right-preconditioned operator) through
 // the fused macromodel matrices p.WP / p.AtcP

@@ -31,6 +31,7 @@
 #include <functional>
 
 #include "device.h"
+#include "ffops.cuh"
 #include "near_tc.h"
 #include "tc_gemm.h"
 
@@ -354,6 +355,125 @@ __global__ void __launch_bounds__(256) k_macro_gemm3(const double* __restrict__ 
   }
 }
 
+// x (complex128) -> F6: each of re, im, re + im as a float pair (the
+// float-float GEMM's right-hand operand, split once per product)
+__global__ void k_split_f6(const double2* __restrict__ x, int64_t n, F6* __restrict__ x6) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z = x[i];
+    f6_store(x6 + i, f6_from(z.x, z.y));
+  }
+}
+
+// The complex128 macromodel GEMM in float-float arithmetic (the three-product
+// form of k_macro_gemm3, each real product and sum carried as a float pair):
+// W6 and x6 hold re, im and re + im split into hi + lo floats.  Writes u and v
+// in FP64 and, when u6 is given, u split again for the float-float near
+// field.  About 2^-44 relative error on the sums of |w x|, against 2^-53 for
+// FP64; the FP32 pipe runs it several times faster than GB300's FP64 pipe.
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_macro_gemm_ff(const F6* __restrict__ W6, int Nh, int rows,
+                                                       const int32_t* __restrict__ elems, int ncols, int nrhs,
+                                                       const int64_t* __restrict__ off, const F6* __restrict__ x6,
+                                                       double2* __restrict__ u, double2* __restrict__ v,
+                                                       F6* __restrict__ u6, double* __restrict__ us) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
+  __shared__ F6 As[BK][BM + 1];
+  __shared__ F6 Bs[BK][BN + 1];
+  __shared__ int64_t colbase[BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  for (int c = tid; c < BN; c += 256) {
+    const int gc = col0 + c;
+    colbase[c] = gc < ncols ? off[elems[gc / nrhs]] * nrhs + gc % nrhs : -1;
+  }
+  FF3 acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = ff3_zero();
+  __syncthreads();
+  F6 ra[LA], rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      const int r = e / BK, kk = e % BK;
+      const int gr = row0 + r, gk = k0 + kk;
+      ra[q] = (gr < rows && gk < Nh) ? f6_load(W6 + (int64_t)gr * Nh + gk) : f6_zero();
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e % BK, c = e / BK;
+      const int gk = k0 + kk;
+      const int64_t cb = colbase[c];
+      rb[q] = (cb >= 0 && gk < Nh) ? f6_load(x6 + cb + (int64_t)gk * nrhs) : f6_zero();
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      As[e % BK][e / BK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      Bs[e % BK][e / BK] = rb[q];
+    }
+  };
+  load(0);
+  store();
+  __syncthreads();
+  for (int k0 = 0; k0 < Nh; k0 += BK) {
+    const bool more = k0 + BK < Nh;
+    if (more) load(k0 + BK);
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      F6 a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) ff3_mac(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+    if (more) {
+      store();
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gr = row0 + ty * TM + i;
+    if (gr >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t cb = colbase[tx * TN + j];
+      if (cb < 0) continue;
+      FF re, im;
+      ff3_result(acc[i][j], re, im);
+      const double2 o = make_double2(ff_to_double(re), ff_to_double(im));
+      if (gr < Nh) {
+        const int64_t idx = cb + (int64_t)gr * nrhs;
+        u[idx] = o;
+        if (u6 != nullptr) {
+          const FF sm = ff_add(re, im);
+          f6_store(u6 + idx, F6{re.s, im.s, sm.s, re.c, im.c, sm.c});
+        }
+        if (us != nullptr) us[idx] = o.x + o.y;
+      } else {
+        v[cb + (int64_t)(gr - Nh) * nrhs] = o;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- A2: projection (step i)
 // One CTA per element.  Each thread owns nodes of the element's stencil box and
 // gathers the (basis, stencil node) contributions listed for that node (lists
@@ -464,6 +584,76 @@ __global__ void __launch_bounds__(RC == 1 ? 512 : 256, RC == 1 && sizeof(R) == 8
             else
               atomic_add_c(grid + ((int64_t)q * nrhs + c0 + c) * gstride + gidx, acc[q][c]);
           }
+    }
+    __syncthreads();
+  }
+}
+
+// Projection of the float-float complex128 product: the schedule of
+// k_project for one right-hand side at a time (T lanes per box node, shuffles),
+// u from the GEMM's F6 split (re, im as float pairs in shared memory), the
+// weights as float pairs Pf[(s Nh + n) 2 + {0: hi, 1: lo}] (x, y, z, phi), every
+// node's four complex sums in float-float, added into the FP64 grid.
+__global__ void __launch_bounds__(512, 2) k_project_ff(const int32_t* __restrict__ elems, int Nh, int bx, int by,
+                                                       int bz, const int32_t* __restrict__ inv_ptr,
+                                                       const int32_t* __restrict__ inv_ent,
+                                                       const float4* __restrict__ Pf,
+                                                       const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ boxorg, int nrhs,
+                                                       const F6* __restrict__ u6, int Nx, int Ny, int Nz,
+                                                       double2* __restrict__ grid) {
+  extern __shared__ float4 us4[];   // [n]: (re hi, im hi, re lo, im lo)
+  const int e = elems[blockIdx.x];
+  const int nodes = bx * by * bz;
+  const int64_t o = off[e];
+  const int gx0 = boxorg[3 * e], gy0 = boxorg[3 * e + 1], gz0 = boxorg[3 * e + 2];
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  const int T = (int)blockDim.x >= 4 * nodes ? 4 : ((int)blockDim.x >= 2 * nodes ? 2 : 1);
+  const int sub = threadIdx.x % T;
+  const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x % 32) & ~(T - 1));
+  for (int c = 0; c < nrhs; ++c) {
+    for (int n = threadIdx.x; n < Nh; n += blockDim.x) {
+      const F6 f = f6_load(u6 + (o + n) * nrhs + c);
+      us4[n] = make_float4(f.rh, f.ih, f.rl, f.il);
+    }
+    __syncthreads();
+    for (int node = threadIdx.x / T; node < nodes; node += blockDim.x / T) {
+      const int q0 = inv_ptr[node], q1 = inv_ptr[node + 1];
+      if (q0 == q1) continue;
+      FF acc[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = ff_zero();
+      for (int q = q0 + sub; q < q1; q += T) {
+        const int ent = __ldg(inv_ent + q);
+        const int n = ent & 0xffff, sn = ent >> 16;
+        const float4 wh = __ldg(Pf + ((int64_t)sn * Nh + n) * 2), wl = __ldg(Pf + ((int64_t)sn * Nh + n) * 2 + 1);
+        const float4 uv = us4[n];
+        ff_mac(acc[0][0], wh.x, wl.x, uv.x, uv.z);
+        ff_mac(acc[0][1], wh.x, wl.x, uv.y, uv.w);
+        ff_mac(acc[1][0], wh.y, wl.y, uv.x, uv.z);
+        ff_mac(acc[1][1], wh.y, wl.y, uv.y, uv.w);
+        ff_mac(acc[2][0], wh.z, wl.z, uv.x, uv.z);
+        ff_mac(acc[2][1], wh.z, wl.z, uv.y, uv.w);
+        ff_mac(acc[3][0], wh.w, wl.w, uv.x, uv.z);
+        ff_mac(acc[3][1], wh.w, wl.w, uv.y, uv.w);
+      }
+      for (int o2 = 1; o2 < T; o2 <<= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const FF other{__shfl_xor_sync(gmask, acc[q][r].s, o2), __shfl_xor_sync(gmask, acc[q][r].c, o2)};
+            acc[q][r] = ff_add(acc[q][r], other);
+          }
+      if (sub != 0) continue;
+      const int lz = node % bz, ly = (node / bz) % by, lx = node / (by * bz);
+      const int64_t gidx = ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double2* g = grid + ((int64_t)q * nrhs + c) * gstride + gidx;
+        atomicAdd(&g->x, ff_to_double(acc[q][0]));
+        atomicAdd(&g->y, ff_to_double(acc[q][1]));
+      }
     }
     __syncthreads();
   }
@@ -697,6 +887,22 @@ __global__ void __launch_bounds__(512, 1) k_project_tab(const PrjTypeDev* __rest
 }
 
 // ---------------------------------------------------------------- A3: FFT convolution (step ii)
+// CTAs per SM asked of the compiler for the FFT stages: three for complex64,
+// one for FP64, two for float-float (its radix-11 and radix-7 butterflies
+// spill rather than hold the SM to one CTA)
+template <typename R> struct FftOcc { static constexpr int kMinBlocks = sizeof(R) == 4 ? 3 : 1; };
+template <> struct FftOcc<FFTag> { static constexpr int kMinBlocks = 2; };
+// Grid values in and out of the FFT stages: the same type, or FP64 grids
+// around the float-float stages (split on the way in, summed on the way out).
+template <typename C, typename G> __device__ __forceinline__ C grid_in(const G& g) { return g; }
+template <> __device__ __forceinline__ CF grid_in<CF, double2>(const double2& g) {
+  return CF{ffv_from(g.x), ffv_from(g.y)};
+}
+template <typename G, typename C> __device__ __forceinline__ G grid_out(const C& c) { return c; }
+template <> __device__ __forceinline__ double2 grid_out<double2, CF>(const CF& c) {
+  return make_double2(ffv_to_double(c.x), ffv_to_double(c.y));
+}
+
 // Line buffers in shared memory hold element i at PAD(i) = i + i/16, which
 // breaks the bank conflicts of the strided Stockham stores.
 __device__ __forceinline__ int PAD(int i) { return i + (i >> 4); }
@@ -955,7 +1161,7 @@ __device__ C* warp_fft(C* a, C* b, const FftPlan& P, const C* tw, int lane) {
 
 // Forward: z DFT (direct, Nz -> Pz) then y FFT (Ny -> Py) of plane (b, x).
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(const typename V2<R>::T* __restrict__ grid, int Nx, int Ny,
+__global__ void __launch_bounds__(256, FftOcc<R>::kMinBlocks) k_fft_fwd_planes(const typename GridT<R>::T* __restrict__ grid, int Nx, int Ny,
                                                         int Nz, FftPlan py, int Pz,
                                                         const typename V2<R>::T* __restrict__ twy,
                                                         const typename V2<R>::T* __restrict__ twz,
@@ -971,8 +1177,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(
   const int x = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < Pz; i += blockDim.x) tz[i] = twz[i];
-  const C* src = grid + ((int64_t)b * Nx + x) * Ny * Nz;
-  staged_copy<8, C>(Ny * Nz, [&](int i) { return src[i]; }, [&](int i, C v) { b1[i] = v; });   // staging [y][z]
+  const typename GridT<R>::T* src = grid + ((int64_t)b * Nx + x) * Ny * Nz;
+  staged_copy<8, C>(Ny * Nz, [&](int i) { return grid_in<C>(src[i]); }, [&](int i, C v) { b1[i] = v; });   // staging [y][z]
   __syncthreads();
   // z DFT: a thread per y line, the root index kz z mod Pz kept incrementally
   for (int y = threadIdx.x; y < Py; y += blockDim.x) {
@@ -1010,7 +1216,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_fwd_planes(
 // x FFT (Nx -> Px), multiply by the Green's spectrum, inverse x FFT (keep Nx),
 // for the Pz lines of one (b, ky); warp per line.
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(typename V2<R>::T* __restrict__ spec, int Nx, int Py,
+__global__ void __launch_bounds__(256, FftOcc<R>::kMinBlocks) k_fft_conv_lines(typename V2<R>::T* __restrict__ spec, int Nx, int Py,
                                                         int Pz, FftPlan px, const typename V2<R>::T* __restrict__ twx,
                                                         const typename V2<R>::T* __restrict__ Ghat) {
   typedef typename V2<R>::T C;
@@ -1060,11 +1266,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_conv_lines(
 
 // Inverse: y FFT (keep Ny) then z DFT (keep Nz) of plane (b, x).
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(const typename V2<R>::T* __restrict__ spec, int Nx, int Ny,
+__global__ void __launch_bounds__(256, FftOcc<R>::kMinBlocks) k_fft_inv_planes(const typename V2<R>::T* __restrict__ spec, int Nx, int Ny,
                                                         int Nz, FftPlan py, int Pz,
                                                         const typename V2<R>::T* __restrict__ twy,
                                                         const typename V2<R>::T* __restrict__ twz,
-                                                        typename V2<R>::T* __restrict__ grid) {
+                                                        typename GridT<R>::T* __restrict__ grid) {
   typedef typename V2<R>::T C;
   extern __shared__ unsigned char smem_raw[];
   const int Py = py.L;
@@ -1090,7 +1296,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
   for (int kz = warp; kz < Pz; kz += nw) warp_fft<C, true>(b0 + kz * LpY, b1 + kz * LpY, py, ty, lane);
   __syncthreads();
   const C* res = (py.nst % 2 == 0) ? b0 : b1;
-  C* dst = grid + ((int64_t)b * Nx + x) * Ny * Nz;
+  typename GridT<R>::T* dst = grid + ((int64_t)b * Nx + x) * Ny * Nz;
   // inverse z DFT (first Nz outputs): a thread per y line
   for (int y = threadIdx.x; y < Ny; y += blockDim.x) {
     for (int z = 0; z < Nz; ++z) {
@@ -1103,7 +1309,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_fft_inv_planes(
         m += z;
         if (m >= Pz) m -= Pz;
       }
-      dst[y * Nz + z] = acc;
+      dst[y * Nz + z] = grid_out<typename GridT<R>::T>(acc);
     }
   }
 }
@@ -1236,6 +1442,82 @@ __global__ void __launch_bounds__(CR == 1 ? (sizeof(R) == 4 ? 576 : 512) : 256, 
   }
 }
 
+
+// Interpolation of the float-float complex128 product: the schedule of
+// k_interp for one right-hand side at a time (T lanes per basis), the element's
+// box of FP64 potentials split into CF in shared memory, the weights as float
+// pairs (Pf, as for the projection), the two sums per basis in float-float;
+// y = v - (c_A sA + c_phi sP) in FP64.
+__global__ void __launch_bounds__(576, 1) k_interp_ff(const int32_t* __restrict__ elems, int Nh, int S, int n1,
+                                                      int o1lo, int bx, int by, int bz,
+                                                      const int32_t* __restrict__ anc, const float4* __restrict__ Pf,
+                                                      const int64_t* __restrict__ off,
+                                                      const int32_t* __restrict__ boxorg, int nrhs,
+                                                      const double2* __restrict__ grid, int Nx, int Ny, int Nz,
+                                                      double cAr, double cAi, double cPr, double cPi,
+                                                      const double2* __restrict__ v, double2* __restrict__ y) {
+  extern __shared__ unsigned char smem_raw[];
+  CF* box = reinterpret_cast<CF*>(smem_raw);   // [psi][node]
+  const int e = elems[blockIdx.x];
+  const int nodes = bx * by * bz;
+  const int64_t o = off[e];
+  const int gx0 = boxorg[3 * e], gy0 = boxorg[3 * e + 1], gz0 = boxorg[3 * e + 2];
+  const int64_t gstride = (int64_t)Nx * Ny * Nz;
+  int* soff = reinterpret_cast<int*>(box + 4 * nodes);
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int ix = s % n1, iy = (s / n1) % n1, iz = s / (n1 * n1);
+    soff[s] = (ix * by + iy) * bz + iz;
+  }
+  const int T = (int)blockDim.x >= 4 * Nh ? 4 : ((int)blockDim.x >= 2 * Nh ? 2 : 1);
+  const int sub = threadIdx.x % T;
+  const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x % 32) & ~(T - 1));
+  const SmallDiv dnodes(nodes), dbyz(by * bz), dbz(bz);
+  for (int c = 0; c < nrhs; ++c) {
+    staged_copy<8, CF>(
+        4 * nodes,
+        [&](int i) {
+          int psi, node, lx, r, ly, lz;
+          dnodes(i, psi, node);
+          dbyz(node, lx, r);
+          dbz(r, ly, lz);
+          return grid_in<CF>(grid[((int64_t)psi * nrhs + c) * gstride +
+                                  ((int64_t)(gx0 + lx) * Ny + (gy0 + ly)) * Nz + (gz0 + lz)]);
+        },
+        [&](int i, CF val) { box[i] = val; });
+    __syncthreads();
+    for (int n = threadIdx.x / T; n < Nh; n += blockDim.x / T) {
+      FF sAr = ff_zero(), sAi = ff_zero(), sPr = ff_zero(), sPi = ff_zero();
+      const int nb = ((anc[3 * n] + o1lo) * by + (anc[3 * n + 1] + o1lo)) * bz + (anc[3 * n + 2] + o1lo);
+      for (int s = sub; s < S; s += T) {
+        const int node = nb + soff[s];
+        const float4 wh = __ldg(Pf + ((int64_t)s * Nh + n) * 2), wl = __ldg(Pf + ((int64_t)s * Nh + n) * 2 + 1);
+        const CF f0 = box[node], f1 = box[nodes + node], f2 = box[2 * nodes + node], f3 = box[3 * nodes + node];
+        ff_mac(sAr, wh.x, wl.x, f0.x.h, f0.x.l);
+        ff_mac(sAi, wh.x, wl.x, f0.y.h, f0.y.l);
+        ff_mac(sAr, wh.y, wl.y, f1.x.h, f1.x.l);
+        ff_mac(sAi, wh.y, wl.y, f1.y.h, f1.y.l);
+        ff_mac(sAr, wh.z, wl.z, f2.x.h, f2.x.l);
+        ff_mac(sAi, wh.z, wl.z, f2.y.h, f2.y.l);
+        ff_mac(sPr, wh.w, wl.w, f3.x.h, f3.x.l);
+        ff_mac(sPi, wh.w, wl.w, f3.y.h, f3.y.l);
+      }
+      for (int o2 = 1; o2 < T; o2 <<= 1) {
+        sAr = ff_add(sAr, FF{__shfl_xor_sync(gmask, sAr.s, o2), __shfl_xor_sync(gmask, sAr.c, o2)});
+        sAi = ff_add(sAi, FF{__shfl_xor_sync(gmask, sAi.s, o2), __shfl_xor_sync(gmask, sAi.c, o2)});
+        sPr = ff_add(sPr, FF{__shfl_xor_sync(gmask, sPr.s, o2), __shfl_xor_sync(gmask, sPr.c, o2)});
+        sPi = ff_add(sPi, FF{__shfl_xor_sync(gmask, sPi.s, o2), __shfl_xor_sync(gmask, sPi.c, o2)});
+      }
+      if (sub != 0) continue;
+      const double ar = ff_to_double(sAr), ai = ff_to_double(sAi), pr = ff_to_double(sPr), pi = ff_to_double(sPi);
+      const double yr = cAr * ar - cAi * ai + cPr * pr - cPi * pi;
+      const double yi = cAr * ai + cAi * ar + cPr * pi + cPi * pr;
+      const int64_t idx = (o + n) * nrhs + c;
+      const double2 vv = v[idx];
+      y[idx] = make_double2(vv.x - yr, vv.y - yi);
+    }
+    __syncthreads();
+  }
+}
 
 // Interpolation of many right-hand sides from shared-memory tables (complex64):
 // one launch for all types, each CTA a contiguous range of the elements listed
@@ -1597,14 +1879,49 @@ __global__ void __launch_bounds__(256) k_spmv_near(int64_t N, const int64_t* __r
 // so its outputs receive several block products: they are accumulated with
 // atomic adds (summation order not fixed).  The CTA's set-up loads are issued
 // in as few dependent rounds as possible (the CTAs do only a few k tiles each).
-template <typename R, int TN, int MB, int TM>
-__global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near_blocks(
+// Arithmetic of the block near field: plain complex (R = float or double), or
+// float-float (NearFF: F6 operands, three Gauss sums per output, FP64 output).
+template <typename R> struct NearPlain {
+  typedef typename V2<R>::T V;   // staged operand entry (block value, u)
+  typedef typename V2<R>::T A;   // accumulator of one output
+  typedef typename V2<R>::T Y;   // output element
+  // CTAs per SM asked of the compiler: the shape's count for complex64, one for FP64
+  static constexpr int min_blocks(int mb) { return sizeof(R) == 4 ? mb : 1; }
+  static __device__ __forceinline__ V vzero() { return czero<V>(); }
+  static __device__ __forceinline__ A azero() { return czero<A>(); }
+  static __device__ __forceinline__ V load(const V* p) { return *p; }
+  static __device__ __forceinline__ void mac(A& acc, const V& a, const V& b) { cmac(acc, a, b); }
+  static __device__ __forceinline__ void sub(Y* dst, const A& acc) {
+    R* d = reinterpret_cast<R*>(dst);
+    atomicAdd(d, -acc.x);
+    atomicAdd(d + 1, -acc.y);
+  }
+};
+struct NearFF {
+  typedef F6 V;
+  typedef FF3 A;
+  typedef double2 Y;
+  static constexpr int min_blocks(int mb) { return mb; }
+  static __device__ __forceinline__ V vzero() { return f6_zero(); }
+  static __device__ __forceinline__ A azero() { return ff3_zero(); }
+  static __device__ __forceinline__ V load(const V* p) { return f6_load(p); }
+  static __device__ __forceinline__ void mac(A& acc, const V& a, const V& b) { ff3_mac(acc, a, b); }
+  static __device__ __forceinline__ void sub(Y* dst, const A& acc) {
+    FF re, im;
+    ff3_result(acc, re, im);
+    atomicAdd(&dst->x, -ff_to_double(re));
+    atomicAdd(&dst->y, -ff_to_double(im));
+  }
+};
+
+template <typename Ar, int TN, int MB, int TM>
+__global__ void __launch_bounds__(16 * (TN / 4), Ar::min_blocks(MB)) k_near_blocks(
     const NearGroupDev* __restrict__ groups, int ngroups, const longlong2* __restrict__ poff,
-    const typename V2<R>::T* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
+    const typename Ar::V* __restrict__ vals, const int64_t* __restrict__ boff, const int32_t* __restrict__ bnb,
     int nmt, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tlist, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ bpa, const int32_t* __restrict__ bpb, int nrhs,
-    int ksplit, const typename V2<R>::T* __restrict__ u, typename V2<R>::T* __restrict__ y) {
-  typedef typename V2<R>::T C;
+    int ksplit, const typename Ar::V* __restrict__ u, typename Ar::Y* __restrict__ y) {
+  typedef typename Ar::V C;
   // TM rows (64 or 32) x TN columns per CTA, MR x 4 complex outputs per thread
   constexpr int TK = 16, TX = TN / 4, NT = 16 * TX, MR = TM / 16;
   __shared__ C As[TK][TM + 1];
@@ -1671,11 +1988,11 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
       cout[cc] = -1;
     }
   }
-  C acc[MR][4];
+  typename Ar::A acc[MR][4];
 #pragma unroll
   for (int i = 0; i < MR; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+    for (int j = 0; j < 4; ++j) acc[i][j] = Ar::azero();
   __syncthreads();
   const bool kfast = nrhs < 16;   // few right-hand sides: a column's rows are the contiguous run
   const int e0 = ea + (int)((int64_t)(eb - ea) * part / ksplit), e1 = ea + (int)((int64_t)(eb - ea) * (part + 1) / ksplit);
@@ -1688,14 +2005,14 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
 #pragma unroll
     for (int r = 0; r < NA; ++r) {
       const int idx = tid + r * NT, m = idx / TK, kk = idx % TK;
-      ra[r] = (m0 + m < Na && k0 + kk < Nb) ? Bq[(int64_t)(m0 + m) * Nb + k0 + kk] : czero<C>();
+      ra[r] = (m0 + m < Na && k0 + kk < Nb) ? Ar::load(Bq + (int64_t)(m0 + m) * Nb + k0 + kk) : Ar::vzero();
     }
 #pragma unroll
     for (int r = 0; r < NB; ++r) {
       const int idx = tid + r * NT;
       const int kk = kfast ? idx % TK : idx / TN, cc = kfast ? idx / TK : idx % TN;
       const int64_t ci = cin[cc];
-      rb[r] = (ci >= 0 && k0 + kk < Nb) ? u[ci + (int64_t)pb[k0 + kk] * nrhs] : czero<C>();
+      rb[r] = (ci >= 0 && k0 + kk < Nb) ? Ar::load(u + ci + (int64_t)pb[k0 + kk] * nrhs) : Ar::vzero();
     }
   };
   if (e0 < e1) fetch(e0);
@@ -1724,7 +2041,7 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
       for (int i = 0; i < MR; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          cmac(acc[i][j], a[i], b[j]);
+          Ar::mac(acc[i][j], a[i], b[j]);
         }
     }
     __syncthreads();
@@ -1736,11 +2053,7 @@ __global__ void __launch_bounds__(16 * (TN / 4), sizeof(R) == 4 ? MB : 1) k_near
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
       const int m = m0 + ty * MR + i;
-      if (m < Na) {
-        R* dst = reinterpret_cast<R*>(y + co + (int64_t)pa[m] * nrhs);
-        atomicAdd(dst, -acc[i][j].x);
-        atomicAdd(dst + 1, -acc[i][j].y);
-      }
+      if (m < Na) Ar::sub(y + co + (int64_t)pa[m] * nrhs, acc[i][j]);
     }
   }
 }
@@ -1753,11 +2066,37 @@ static void near_blocks_launch(const DevArray& a, const DevPrec<R>& p, int nrhs,
   if (tiles == 0) return;
   // ksplit > 1 splits each row tile's k tiles over several CTAs (the outputs are
   // accumulated atomically anyway): more CTAs when the output tiles are few
-  k_near_blocks<R, TN, MB, TM><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
+  k_near_blocks<NearPlain<R>, TN, MB, TM><<<dim3((unsigned)tiles, (unsigned)ksplit), 16 * (TN / 4), 0, st>>>(
       reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_poff,
       static_cast<const typename V2<R>::T*>(p.nfb_val), a.nfb_off, a.nfb_nb, TM == 64 ? a.nfb_nmt : a.nfb_nmt32,
       TM == 64 ? a.nfb_tptr : a.nfb_tptr32, TM == 64 ? a.nfb_tlist : a.nfb_tlist32,
       a.nfb_perm, a.nfb_pa, a.nfb_pb, nrhs, ksplit, u, y);
+  ++nl;
+}
+
+// The block near field of the float-float complex128 product: 32 x 32 tiles,
+// one CTA per tile (the F6 operands and three Gauss sums per output hold about
+// 150 registers per thread), outputs added to v in FP64.
+template <int TN, int MB, int TM>
+static void near_ff_shape(const DevArray& a, const DevPrec<double>& pd, int nrhs, const F6* u6, double2* y,
+                          cudaStream_t st) {
+  int64_t tiles = 0;
+  for (const auto& g : a.nfg) tiles += ((g.npairs * nrhs + TN - 1) / TN) * ((g.Na + TM - 1) / TM);
+  if (tiles == 0) return;
+  k_near_blocks<NearFF, TN, MB, TM><<<dim3((unsigned)tiles, 1u), 16 * (TN / 4), 0, st>>>(
+      reinterpret_cast<const NearGroupDev*>(a.nfg_dev), (int)a.nfg.size(), a.nfg_poff,
+      static_cast<const F6*>(pd.ff_nfb), a.nfb_off, a.nfb_nb, TM == 64 ? a.nfb_nmt : a.nfb_nmt32,
+      TM == 64 ? a.nfb_tptr : a.nfb_tptr32, TM == 64 ? a.nfb_tlist : a.nfb_tlist32, a.nfb_perm, a.nfb_pa, a.nfb_pb,
+      nrhs, 1, u6, y);
+}
+static void near_blocks_ff_launch(const DevArray& a, const DevPrec<double>& pd, int nrhs, const F6* u6, double2* y,
+                                  cudaStream_t st, int& nl) {
+  switch (a.ff_near_shape) {
+    case 1: near_ff_shape<32, 3, 32>(a, pd, nrhs, u6, y, st); break;
+    case 2: near_ff_shape<64, 1, 32>(a, pd, nrhs, u6, y, st); break;
+    case 3: near_ff_shape<16, 1, 32>(a, pd, nrhs, u6, y, st); break;
+    default: near_ff_shape<32, 1, 32>(a, pd, nrhs, u6, y, st); break;
+  }
   ++nl;
 }
 
@@ -1850,6 +2189,8 @@ cudaError_t kernels_init(DevArray& a) {
   MM_ATTR(k_fft_fwd_planes<float>) MM_ATTR(k_fft_fwd_planes<double>)
   MM_ATTR(k_fft_conv_lines<float>) MM_ATTR(k_fft_conv_lines<double>)
   MM_ATTR(k_fft_inv_planes<float>) MM_ATTR(k_fft_inv_planes<double>)
+  MM_ATTR(k_fft_fwd_planes<FFTag>) MM_ATTR(k_fft_conv_lines<FFTag>) MM_ATTR(k_fft_inv_planes<FFTag>)
+  MM_ATTR(k_project_ff) MM_ATTR(k_interp_ff)
   MM_ATTR((k_project<float, 1>)) MM_ATTR((k_project<double, 1>)) MM_ATTR((k_project<float, 4>))
   MM_ATTR((k_project<double, 4>))
   MM_ATTR((k_interp<float, 1>)) MM_ATTR((k_interp<double, 1>)) MM_ATTR((k_interp<float, 8>))
@@ -1958,6 +2299,41 @@ static bool interp_tab_ok(const DevPrec<R>& p, int nrhs) {
 static size_t interp_rhs_smem(const DevArray& a, int t) {
   const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
   return 8 * 4 * nodes * 9 + 4 * (size_t)a.S + 4 * nodes;
+}
+
+// The float-float projection and interpolation, per type (T lanes per box node
+// or basis as in the FP64 schedules).
+static void project_ff_launch(const DevArray& a, const DevPrec<double>& pd, int nrhs, const F6* u6, double2* grid,
+                              cudaStream_t cs, int& nl) {
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const int bx = a.box[3 * t], by = a.box[3 * t + 1], bz = a.box[3 * t + 2];
+    const int pnodes = bx * by * bz;
+    int pT = 4;
+    while (pT > 1 && pT * pnodes > 512) pT >>= 1;
+    const int threads = std::max(256, std::min(512, (pT * pnodes + 31) / 32 * 32));
+    k_project_ff<<<(unsigned)a.n_of_type[t], threads, sizeof(float4) * Nh, cs>>>(
+        a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], a.inv_ent[t], static_cast<const float4*>(pd.ff_Pi[t]), a.off,
+        a.boxorg, nrhs, u6, a.grid[0], a.grid[1], a.grid[2], grid);
+    ++nl;
+  }
+}
+static void interp_ff_launch(const DevArray& a, const DevPrec<double>& pd, int nrhs, const double2* grid,
+                             const double2* v, double2* y, cudaStream_t cs, int& nl) {
+  for (int64_t t = 0; t < a.n_types; ++t) {
+    if (a.n_of_type[t] == 0) continue;
+    const int Nh = (int)a.Nh[t];
+    const size_t nodes = (size_t)a.box[3 * t] * a.box[3 * t + 1] * a.box[3 * t + 2];
+    int iT = 4;
+    while (iT > 1 && iT * Nh > 576) iT >>= 1;
+    const int threads = std::max(64, std::min(576, (iT * Nh + 31) / 32 * 32));
+    k_interp_ff<<<(unsigned)a.n_of_type[t], threads, sizeof(CF) * 4 * nodes + sizeof(int) * (size_t)a.S, cs>>>(
+        a.elems[t], Nh, a.S, a.n1, a.o1lo, a.box[3 * t], a.box[3 * t + 1], a.box[3 * t + 2], a.anc[t],
+        static_cast<const float4*>(pd.ff_Pi[t]), a.off, a.boxorg, nrhs, grid, a.grid[0], a.grid[1], a.grid[2],
+        a.cA[0], a.cA[1], a.cphi[0], a.cphi[1], v, y);
+    ++nl;
+  }
 }
 
 template <typename R>
@@ -2168,7 +2544,7 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     // first product of this width and precision with block near field: tune it over whole products
     const bool csr0 = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
     const bool blocks0 = a.nfb_entries > 0 && p.nfb_val != nullptr && !csr0;
-    if (blocks0 && !(flags & kMvNoTune) && a.near_force_shape < 0 &&
+    if (blocks0 && !(flags & (kMvNoTune | kMvFF)) && a.near_force_shape < 0 &&
         a.near_tune.find(std::make_pair(nrhs, (int)sizeof(R))) == a.near_tune.end()) {
       const cudaError_t te = near_tune_products<R>(a, p, w, nrhs, xv, yv, st, gemm_mode, pre, flags);
       if (te != cudaSuccess) return te;
@@ -2194,8 +2570,9 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
       gv = {a.grid_force_p, a.grid_force_i};
     else if (gt != a.grid_tune.end())
       gv = {gt->second.project, gt->second.interp};
-    else if (!(flags & kMvNoTune) && a.tune_grid)
+    else if (!(flags & (kMvNoTune | kMvFF)) && a.tune_grid)
       gv = grid_autotune<R>(a, p, nrhs, w, st);
+    if (sizeof(R) == 8 && (flags & kMvFF)) gv = {0, 0};   // the float-float stages have one schedule
   }
   // the two-pass projection writes every grid point; the atomic forms add into a cleared grid
   const bool two_pass = gv.first == 2 && w.boxbuf != nullptr && nrhs > 1;
@@ -2206,6 +2583,11 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   const int sb = sizeof(R) == 8 ? 8 : 0;   // profiler slot base of this precision
   // A1: u = M x, v = D x, per type (with kMvUInput, u = x and v = 0 instead:
   // the product is then y = -G x, the coupling operator alone)
+  // float-float contractions: complex128 only, with the F6 operands uploaded
+  const DevPrec<double>& ffd = a.pd;
+  const bool ff = sizeof(R) == 8 && (flags & kMvFF) != 0;
+  if (ff && (!ffd.ff_ready || w.x6 == nullptr || w.u6 == nullptr || pre)) return cudaErrorInvalidValue;
+  const bool ff_near_u6 = ff && a.nfb_entries > 0 && ffd.ff_nfb != nullptr && a.near_mode != 2;
   pr.begin(sb + 0, st);
   int nl = 0;
   const bool u_input = (flags & kMvUInput) != 0;
@@ -2213,6 +2595,13 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     u = const_cast<C*>(x);
     e = cudaMemsetAsync(v, 0, sizeof(C) * (size_t)a.N * nrhs, st);
     if (e != cudaSuccess) return e;
+  }
+  if (ff) {
+    // the float-float GEMM's right-hand operand (or, without the GEMM, the near field's)
+    const int64_t n = a.N * nrhs;
+    k_split_f6<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(
+        reinterpret_cast<const double2*>(x), n, static_cast<F6*>(u_input ? w.u6 : w.x6));
+    ++nl;
   }
   if (u_input) {
     // no macromodel stage
@@ -2236,6 +2625,29 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
     constexpr int BKs = sizeof(R) == 4 ? 32 : 16;
     const C* Wt = static_cast<const C*>((pre ? p.WP : p.W)[t]);
     if constexpr (sizeof(R) == 8) {
+      if (ff) {
+        const F6* W6 = static_cast<const F6*>(ffd.ffW[t]);
+        const F6* x6 = static_cast<const F6*>(w.x6);
+        double2* ud = reinterpret_cast<double2*>(u);
+        double2* vd = reinterpret_cast<double2*>(v);
+        F6* u6 = static_cast<F6*>(w.u6);   // the projection's and the block near field's operand
+        double* us = ff_near_u6 ? nullptr : w.us;
+        if (a.ff_gemm_shape == 1) {
+          dim3 g((2 * Nh + 15) / 16, (ncols + 31) / 32);
+          k_macro_gemm_ff<16, 32, 16><<<g, 256, 0, st>>>(W6, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x6, ud, vd,
+                                                         u6, us);
+        } else if (a.ff_gemm_shape == 2) {
+          dim3 g((2 * Nh + 31) / 32, (ncols + 63) / 64);
+          k_macro_gemm_ff<32, 64, 16><<<g, 256, 0, st>>>(W6, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x6, ud, vd,
+                                                         u6, us);
+        } else {
+          dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
+          k_macro_gemm_ff<32, 32, 16><<<g, 256, 0, st>>>(W6, Nh, 2 * Nh, a.elems[t], ncols, nrhs, a.off, x6, ud, vd,
+                                                         u6, us);
+        }
+        ++nl;
+        continue;
+      }
       const auto& W3v = pre ? p.WP3 : p.W3;
       if ((size_t)t < W3v.size() && W3v[t] != nullptr) {
         dim3 g((2 * Nh + 31) / 32, (ncols + 31) / 32);
@@ -2263,9 +2675,11 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // rows when assembled (FP64 arithmetic on the dense blocks costs more than
   // streaming the CSR from HBM).  It only needs u, so it runs on the array's
   // second stream beside A2-A3 and joins before A4.
-  const bool csr = a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
-  const bool nf_blocks = a.nfb_entries > 0 && p.nfb_val != nullptr && !csr;
-  const bool nf = nf_blocks || a.nnz > 0;
+  // float-float products take the block near field whenever the blocks exist
+  const bool ff_near = ff && a.nfb_entries > 0 && ffd.ff_nfb != nullptr && a.near_mode != 2;
+  const bool csr = !ff_near && a.nnz > 0 && (a.near_mode == 2 || sizeof(R) == 8);
+  const bool nf_blocks = !ff_near && a.nfb_entries > 0 && p.nfb_val != nullptr && !csr;
+  const bool nf = ff_near || nf_blocks || a.nnz > 0;
   int tn = 0, ks = 1;   // kernel shape (near_shape_launch), k split
   if (nf_blocks) {
     // first product with this shape: tune on st while the spectra are idle
@@ -2303,11 +2717,19 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A2: projection
   pr.begin(sb + 1, cs);
   nl = 0;
-  project_launch<R>(gv.first == 2 && !w.boxbuf ? 0 : gv.first, a, p, nrhs, u, grid, w.boxbuf, cs, nl);
+  if (ff)
+    project_ff_launch(a, ffd, nrhs, static_cast<const F6*>(w.u6), reinterpret_cast<double2*>(grid), cs, nl);
+  else
+    project_launch<R>(gv.first == 2 && !w.boxbuf ? 0 : gv.first, a, p, nrhs, u, grid, w.boxbuf, cs, nl);
   pr.end(cs, nl);
   // A5 on its stream, launched after the projection so that the chain's first
   // kernel is dispatched ahead of it
-  if (nf_blocks) {
+  if (ff_near) {
+    pr.begin(sb + 6, ns);
+    nl = 0;
+    near_blocks_ff_launch(a, ffd, nrhs, static_cast<const F6*>(w.u6), reinterpret_cast<double2*>(v), ns, nl);
+    pr.end(ns, nl);
+  } else if (nf_blocks) {
     pr.begin(sb + 6, ns);
     nl = 0;
     near_shape_launch<R>(tn, a, p, nrhs, u, v, ns, nl, ks, w.np, w.np_parts);
@@ -2340,17 +2762,34 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   }
   // A3: FFT convolution
   pr.begin(sb + 2, cs);
-  k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
-      grid, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), spec);
-  pr.end(cs, 1);
-  pr.begin(sb + 3, cs);
-  k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), cs>>>(
-      spec, Nx, Py, Pz, a.px, static_cast<const C*>(p.twx), static_cast<const C*>(p.Ghat));
-  pr.end(cs, 1);
-  pr.begin(sb + 4, cs);
-  k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
-      spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
-  pr.end(cs, 1);
+  if (ff) {
+    // float-float stages (CF spectra in the FP64 spectrum buffer, same size)
+    CF* fspec = reinterpret_cast<CF*>(spec);
+    double2* dgrid = reinterpret_cast<double2*>(grid);
+    k_fft_fwd_planes<FFTag><<<dim3(Nx, B), 256, fft_smem_bytes<FFTag>(a, 0), cs>>>(
+        dgrid, Nx, Ny, Nz, a.py, Pz, static_cast<const CF*>(ffd.ff_twy), static_cast<const CF*>(ffd.ff_twz), fspec);
+    pr.end(cs, 1);
+    pr.begin(sb + 3, cs);
+    k_fft_conv_lines<FFTag><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<FFTag>(a, 1), cs>>>(
+        fspec, Nx, Py, Pz, a.px, static_cast<const CF*>(ffd.ff_twx), static_cast<const CF*>(ffd.ff_Ghat));
+    pr.end(cs, 1);
+    pr.begin(sb + 4, cs);
+    k_fft_inv_planes<FFTag><<<dim3(Nx, B), 256, fft_smem_bytes<FFTag>(a, 0), cs>>>(
+        fspec, Nx, Ny, Nz, a.py, Pz, static_cast<const CF*>(ffd.ff_twy), static_cast<const CF*>(ffd.ff_twz), dgrid);
+    pr.end(cs, 1);
+  } else {
+    k_fft_fwd_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
+        grid, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), spec);
+    pr.end(cs, 1);
+    pr.begin(sb + 3, cs);
+    k_fft_conv_lines<R><<<dim3(Py, B), 32 * std::min(Pz, 8), fft_smem_bytes<R>(a, 1), cs>>>(
+        spec, Nx, Py, Pz, a.px, static_cast<const C*>(p.twx), static_cast<const C*>(p.Ghat));
+    pr.end(cs, 1);
+    pr.begin(sb + 4, cs);
+    k_fft_inv_planes<R><<<dim3(Nx, B), 256, fft_smem_bytes<R>(a, 0), cs>>>(
+        spec, Nx, Ny, Nz, a.py, Pz, static_cast<const C*>(p.twy), static_cast<const C*>(p.twz), grid);
+    pr.end(cs, 1);
+  }
   (void)Px;
   if (ns != st) {
     e = cudaStreamWaitEvent(cs, a.ev_join, 0);
@@ -2359,7 +2798,11 @@ cudaError_t matvec(DevArray& a, DevPrec<R>& p, Work& w, int nrhs, const void* xv
   // A4: interpolation, y = v - y_ff
   pr.begin(sb + 5, cs);
   nl = 0;
-  interp_launch<R>(gv.second, a, p, nrhs, grid, v, y, cs, nl);
+  if (ff)
+    interp_ff_launch(a, ffd, nrhs, reinterpret_cast<const double2*>(grid), reinterpret_cast<const double2*>(v),
+                     reinterpret_cast<double2*>(y), cs, nl);
+  else
+    interp_launch<R>(gv.second, a, p, nrhs, grid, v, y, cs, nl);
   pr.end(cs, nl);
   if (cs != st) {
     e = cudaEventRecord(a.ev_done, cs);
@@ -2404,5 +2847,6 @@ template cudaError_t matvec<double>(DevArray&, DevPrec<double>&, Work&, int, con
                                     bool, unsigned);
 template size_t fft_smem_bytes<float>(const DevArray&, int);
 template size_t fft_smem_bytes<double>(const DevArray&, int);
+template size_t fft_smem_bytes<FFTag>(const DevArray&, int);
 
 }  // namespace mm
