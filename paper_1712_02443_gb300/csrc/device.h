@@ -258,10 +258,12 @@ struct DevArray {
   // autotuned block near-field shape per (right-hand sides, sizeof(R)): (kernel shape, k split)
   std::map<std::pair<int, int>, std::pair<int, int>> near_tune;
   int near_force_shape = -1, near_force_ks = 1;   // MACROAIM_NEAR_SHAPE="shape,ksplit": no tuning
-  // tile shapes of the float-float GEMM (0: 32 x 32, 1: 16 x 32, 2: 32 x 64) and
-  // block near field (0: 32 x 32, 1: the same held to three CTAs per SM, 2: 32
-  // rows x 64 columns, 3: 32 x 16); MACROAIM_FF_SHAPE="gemm,near"
-  int ff_gemm_shape = 0, ff_near_shape = 0;
+  // tile shapes of the float-float GEMM (0: 32 x 32, 1: 16 x 32, the default,
+  // 2: 32 x 64) and block near field (0: 32 x 32, 1: the same held to three CTAs
+  // per SM, the default, 2: 32 rows x 64 columns, 3: 32 x 16);
+  // MACROAIM_FF_SHAPE="gemm,near" (16x16 loop array, one column, alone: GEMM 97,
+  // 81, 161 us; near field 172, 162, 199, 183 us)
+  int ff_gemm_shape = 1, ff_near_shape = 1;
   std::map<std::pair<int, int>, GridTune> grid_tune;   // per (right-hand sides, sizeof(R))
   bool tune_grid = true;                           // MACROAIM_GRID_TUNE=0: variant 0, no timing
   int grid_force_p = -1, grid_force_i = -1;        // MACROAIM_GRID_SCHED="p,i": fixed variants

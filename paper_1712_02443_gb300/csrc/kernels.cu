@@ -1887,6 +1887,7 @@ template <typename R> struct NearPlain {
   typedef typename V2<R>::T Y;   // output element
   // CTAs per SM asked of the compiler: the shape's count for complex64, one for FP64
   static constexpr int min_blocks(int mb) { return sizeof(R) == 4 ? mb : 1; }
+  static constexpr int kUnrollK = 16;   // the whole k tile
   static __device__ __forceinline__ V vzero() { return czero<V>(); }
   static __device__ __forceinline__ A azero() { return czero<A>(); }
   static __device__ __forceinline__ V load(const V* p) { return *p; }
@@ -1902,6 +1903,9 @@ struct NearFF {
   typedef FF3 A;
   typedef double2 Y;
   static constexpr int min_blocks(int mb) { return mb; }
+  // two k steps per loop body: the unrolled float-float tile is some 5,000
+  // instructions, which the instruction cache does not hold
+  static constexpr int kUnrollK = 2;
   static __device__ __forceinline__ V vzero() { return f6_zero(); }
   static __device__ __forceinline__ A azero() { return ff3_zero(); }
   static __device__ __forceinline__ V load(const V* p) { return f6_load(p); }
@@ -2030,7 +2034,7 @@ __global__ void __launch_bounds__(16 * (TN / 4), Ar::min_blocks(MB)) k_near_bloc
     }
     __syncthreads();
     if (e + 1 < e1) fetch(e + 1);
-#pragma unroll
+#pragma unroll Ar::kUnrollK
     for (int kk = 0; kk < TK; ++kk) {
       C a[MR], b[4];
 #pragma unroll
