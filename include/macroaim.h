@@ -344,9 +344,12 @@ typedef struct mm_solve_opts {
                          shared by identical elements.  The solution is the
                          same; GMRES needs fewer iterations.  Not a method of
                          the paper (which names ILU), a library option.         */
-  int32_t residual;   /* refinement residual b - Z x: 0 = complex128 operator
-                         with the float-float contractions (MM_C128_FF, the
-                         default); 1 = plain FP64 (MM_C128)                     */
+  int32_t fp64;       /* the FP64-class steps of refinement solves (the
+                         residual b - Z x with the complex128 operator, and the
+                         inner solves' Arnoldi products on a Krylov basis of
+                         complex128 precision): 0 = in float-float arithmetic
+                         on the FP32 pipe (MM_C128_FF; the default), 1 = in
+                         FP64                                                   */
 } mm_solve_opts;
 typedef struct mm_solve_stats {
   int32_t iterations;     /* inner GMRES iterations (max over columns)        */

@@ -51,7 +51,7 @@ class mm_array_info(ct.Structure):
 class mm_solve_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
                 ("refine", ct.c_int32), ("inner_tol", ct.c_double), ("orth", ct.c_int32), ("precond", ct.c_int32),
-                ("residual", ct.c_int32)]
+                ("fp64", ct.c_int32)]
 
 
 class mm_solve_stats(ct.Structure):
@@ -382,8 +382,8 @@ def mm_rcs(array, nrhs: int, Jhat_dev, theta, phi) -> np.ndarray:
 
 def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_iter: int = 1000,
              precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2, stream=None, check: bool = True,
-             orth: int = 0, precond: int = 0, residual: int = 0):
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, residual)
+             orth: int = 0, precond: int = 0, fp64: int = 0):
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, fp64)
     s = mm_solve_stats()
     st = load().mm_solve(array, nrhs, _ptr(V_dev), _ptr(E_dev), ct.byref(o), ct.byref(s), _stream(stream))
     stats = {"iterations": s.iterations, "matvecs": s.matvecs, "refinements": s.refinements,
@@ -395,14 +395,14 @@ def mm_solve(array, nrhs: int, V_dev, E_dev, tol: float, restart: int = 50, max_
 
 def mm_solve_planewave_host(array, theta, phi, pol, E_host: np.ndarray, tol: float, restart: int = 50,
                             max_iter: int = 1000, precision: int = MM_C64, refine: int = 1, inner_tol: float = 1e-2,
-                            orth: int = 0, precond: int = 0, check: bool = True, residual: int = 0):
+                            orth: int = 0, precond: int = 0, check: bool = True, fp64: int = 0):
     """Excitation, solve and the solution copied into E_host (complex128, N x nrhs), all in the library."""
     th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
     ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
     po = np.ascontiguousarray(pol, dtype=np.int32).ravel()
     if E_host.dtype != np.complex128 or not E_host.flags.c_contiguous:
         raise ValueError("E_host must be a C-contiguous complex128 array")
-    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, residual)
+    o = mm_solve_opts(tol, restart, max_iter, precision, refine, inner_tol, orth, precond, fp64)
     s = mm_solve_stats()
     st = load().mm_solve_planewave_host(array, len(th), _ptr(th), _ptr(ph), _ptr(po), _ptr(E_host), ct.byref(o),
                                         ct.byref(s))

@@ -555,24 +555,22 @@ void ensure_tc_work(mm_array* a, mm::Work& w, int nrhs) {
   }
 }
 
-// A bounded wait of the tensor-core GEMM expired (checked where the call synchronises).
+// A bounded wait of the tensor-core GEMM or near field expired (checked where
+// the call synchronises).  Both flags are read and cleared before either is
+// reported, so that a later call does not report this call's expiry.
 mm_status check_tc(mm_array* a) {
-  int h = 0;
+  int hg = 0, hn = 0;
   if (a->da.wf.err) {
-    if (cudaMemcpy(&h, a->da.wf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
-    if (h) {
-      cudaMemset(a->da.wf.err, 0, sizeof(int));
-      return fail(a->ctx, MM_ETIMEOUT, "a tensor-core GEMM wait expired; results of that product are invalid");
-    }
+    if (cudaMemcpy(&hg, a->da.wf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
+    if (hg) cudaMemset(a->da.wf.err, 0, sizeof(int));
   }
   if (a->da.near_err) {
-    if (cudaMemcpy(&h, a->da.near_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
-    if (h) {
-      cudaMemset(a->da.near_err, 0, sizeof(int));
-      return fail(a->ctx, MM_ETIMEOUT,
-                  "a tensor-core near-field wait expired; results of that product are invalid");
-    }
+    if (cudaMemcpy(&hn, a->da.near_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MM_ECUDA;
+    if (hn) cudaMemset(a->da.near_err, 0, sizeof(int));
   }
+  if (hg) return fail(a->ctx, MM_ETIMEOUT, "a tensor-core GEMM wait expired; results of that product are invalid");
+  if (hn)
+    return fail(a->ctx, MM_ETIMEOUT, "a tensor-core near-field wait expired; results of that product are invalid");
   return MM_OK;
 }
 
@@ -1598,7 +1596,7 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   if (opts->precision < MM_C64 || opts->precision > MM_C64_F16) return fail(ctx, MM_EINVAL, "unknown precision");
   if (opts->orth < 0 || opts->orth > 3) return fail(ctx, MM_EINVAL, "orth must be 0, 1, 2 or 3");
   if (opts->precond < 0 || opts->precond > 1) return fail(ctx, MM_EINVAL, "precond must be 0 or 1");
-  if (opts->residual < 0 || opts->residual > 1) return fail(ctx, MM_EINVAL, "residual must be 0 or 1");
+  if (opts->fp64 < 0 || opts->fp64 > 1) return fail(ctx, MM_EINVAL, "fp64 must be 0 or 1");
   if (opts->refine && opts->precision == MM_C128)
     return fail(ctx, MM_EINVAL, "refinement needs a complex64 operator precision");
   API_TRY
@@ -1614,8 +1612,10 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   upload_precision<double>(a, a->da.pd);
   ensure_work<double>(a, a->da.wd, nrhs);
   ensure_work<float>(a, a->da.wf, nrhs);
-  // refinement residuals in float-float arithmetic (the default) or FP64
-  const bool ff_res = opts->refine && opts->residual == 0;
+  // refinement residuals and the inner Arnoldi products in float-float
+  // arithmetic (the default) or FP64
+  const bool ff_res = opts->refine && opts->fp64 == 0;
+  S.ff_arnoldi = ff_res;
   if (ff_res) {
     upload_ff(a);
     ensure_ff_work(a, a->da.wd, nrhs);

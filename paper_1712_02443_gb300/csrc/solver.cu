@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "ffops.cuh"
 #include "solver.h"
 
 namespace cg = cooperative_groups;
@@ -909,6 +910,323 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(Z* __restrict__ V, int64_t
   }
 }
 
+// ---------------------------------------------------------------- float-float Krylov basis
+// The inner solves of iterative refinement may keep their Krylov basis V and
+// work vector w as float-float values (F4 = (re hi, im hi, re lo, im lo), 16
+// bytes like complex128) and take the Arnoldi dot products, updates and norms
+// in float-float arithmetic on the FP32 pipe (ffops.cuh; GB300 runs FP64 at
+// about 1/70 of its FP32 rate).  What crosses the blocks stays FP64: the
+// blocks' partial sums, the Hessenberg entries, the norms and the scales.
+typedef float4 F4;
+struct FFC {   // complex float-float accumulator
+  FF re, im;
+};
+__device__ __forceinline__ FFC ffc_zero() { return FFC{ff_zero(), ff_zero()}; }
+__device__ __forceinline__ FFC ffc_of(F4 a) { return FFC{FF{a.x, a.z}, FF{a.y, a.w}}; }
+// acc += conj(v) w
+__device__ __forceinline__ void ffc_conj_mac(FFC& acc, F4 v, F4 w) {
+  ff_mac(acc.re, v.x, v.z, w.x, w.z);
+  ff_mac(acc.re, v.y, v.w, w.y, w.w);
+  ff_mac(acc.im, v.x, v.z, w.y, w.w);
+  ff_mac(acc.im, -v.y, -v.w, w.x, w.z);
+}
+// acc -= v h
+__device__ __forceinline__ void ffc_sub_mul(FFC& acc, F4 v, F4 h) {
+  ff_mac(acc.re, -v.x, -v.z, h.x, h.z);
+  ff_mac(acc.re, v.y, v.w, h.y, h.w);
+  ff_mac(acc.im, -v.x, -v.z, h.y, h.w);
+  ff_mac(acc.im, -v.y, -v.w, h.x, h.z);
+}
+// acc += v h
+__device__ __forceinline__ void ffc_add_mul(FFC& acc, F4 v, F4 h) {
+  ff_mac(acc.re, v.x, v.z, h.x, h.z);
+  ff_mac(acc.re, -v.y, -v.w, h.y, h.w);
+  ff_mac(acc.im, v.x, v.z, h.y, h.w);
+  ff_mac(acc.im, v.y, v.w, h.x, h.z);
+}
+__device__ __forceinline__ void ff_norm_mac(FF& acc, F4 a) {   // acc += |a|^2
+  ff_mac(acc, a.x, a.z, a.x, a.z);
+  ff_mac(acc, a.y, a.w, a.y, a.w);
+}
+__device__ __forceinline__ F4 ffc_pack(FFC a) {   // renormalised (hi, lo) pairs
+  const FF r = ff_add(a.re, ff_zero()), i = ff_add(a.im, ff_zero());
+  return make_float4(r.s, i.s, r.c, i.c);
+}
+__device__ __forceinline__ F4 f4_split(Z z) {
+  F4 o;
+  ff_split(z.x, o.x, o.z);
+  ff_split(z.y, o.y, o.w);
+  return o;
+}
+__device__ __forceinline__ DAcc ffc_dacc(FFC a) { return DAcc{ff_to_double(a.re), ff_to_double(a.im)}; }
+
+// V[k] = w * scale (per column) as float-float; out = its high parts, the
+// complex64 operator's input.
+__global__ void k_fetch_ff(F4* __restrict__ V, int64_t vs, const Z* __restrict__ w, GmresDev gd, int64_t n,
+                           float2* __restrict__ out) {
+  const int k = *gd.k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % gd.r);
+    const double sc = gd.scale[j];
+    const F4 v = f4_split(make_double2(w[t].x * sc, w[t].y * sc));
+    V[(int64_t)k * vs + t] = v;
+    out[t] = make_float2(v.x, v.y);
+  }
+}
+
+// yf[i r + j] = gd.y[i r + j] split, i < k (once per cycle, for k_add_basis_ff)
+__global__ void k_split_y(GmresDev gd, F4* __restrict__ yf) {
+  const int n = *gd.k * gd.r;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) yf[i] = f4_split(gd.y[i]);
+}
+
+// x += sum_{i < k} V_i y_i: float-float products and sums, FP64 result.
+__global__ void k_add_basis_ff(const F4* __restrict__ V, int64_t vs, GmresDev gd, const F4* __restrict__ yf,
+                               int64_t n, Z* __restrict__ x) {
+  const int k = *gd.k, r = gd.r;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % r);
+    FFC acc = ffc_zero();
+    for (int i = 0; i < k; ++i) ffc_add_mul(acc, V[(int64_t)i * vs + t], yf[i * r + j]);
+    const Z a = x[t];
+    x[t] = make_double2(a.x + ff_to_double(acc.re), a.y + ff_to_double(acc.im));
+  }
+}
+
+// w[t] -= sum_{i <= k} V_i[t] h_i[t mod r] for the flat rows t in [t0, t1) of
+// this block (columns with need[j] == 0 skipped when need is given), two rows
+// per thread and round and four basis vectors per load group; with nacc, the
+// thread's sum of |w[t]|^2 after the update (a thread keeps one column when
+// r divides the block).
+__device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t vs, F4* __restrict__ w,
+                                               const F4* hf, int k, int r, int64_t t0, int64_t t1,
+                                               const int* need, FF* nacc) {
+  const F4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const int B = blockDim.x;
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += 2 * B) {
+    const int64_t tb = t + B;
+    const int ja = (int)(t % r), jb = (int)(tb % r);
+    const bool ua = need == nullptr || need[ja];
+    const bool ub = tb < t1 && (need == nullptr || need[jb]);
+    if (!ua && !ub) continue;
+    FFC a = ffc_of(ua ? w[t] : z4), b = ffc_of(ub ? w[tb] : z4);
+    for (int i0 = 0; i0 <= k; i0 += 4) {
+      F4 va[4], vb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        va[q] = (ua && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + t] : z4;
+        vb[q] = (ub && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tb] : z4;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (i0 + q <= k) {
+          ffc_sub_mul(a, va[q], hf[(i0 + q) * r + ja]);
+          ffc_sub_mul(b, vb[q], hf[(i0 + q) * r + jb]);
+        }
+    }
+    if (ua) {
+      const F4 o = ffc_pack(a);
+      w[t] = o;
+      if (nacc) ff_norm_mac(*nacc, o);
+    }
+    if (ub) {
+      const F4 o = ffc_pack(b);
+      w[tb] = o;
+      if (nacc) ff_norm_mac(*nacc, o);
+    }
+  }
+}
+
+// block_dots_all and block_norms_all on the float-float vectors: each thread's
+// sums in float-float, the block reduction in FP64 (column_reduce).
+__device__ void block_dots_all_ff(const F4* __restrict__ V, int64_t vs, const F4* __restrict__ w, int k, int64_t n0,
+                                  int64_t n1, int r, int blk, int nblk, DAcc* red, Z* __restrict__ P) {
+  const int tid = threadIdx.x;
+  const int S = (blockDim.x / r) * r;
+  const int64_t t1 = n1 * r;
+  const F4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int i0 = 0; i0 <= k; i0 += 4) {
+    FFC acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = ffc_zero();
+    // two rows per round, every load of the round issued before the products
+    // (the basis streams from HBM at large sizes: ten 16-byte loads in flight)
+    if (tid < S)
+      for (int64_t t = n0 * r + tid; t < t1; t += 2 * S) {
+        const int64_t tb = t + S;
+        const bool two = tb < t1;
+        const F4 wa = w[t], wb = two ? w[tb] : z4;
+        F4 va[4], vb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          va[q] = i0 + q <= k ? V[(int64_t)(i0 + q) * vs + t] : z4;
+          vb[q] = (two && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tb] : z4;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ffc_conj_mac(acc[q], va[q], wa);
+          ffc_conj_mac(acc[q], vb[q], wb);
+        }
+      }
+    DAcc ad[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ad[q] = ffc_dacc(acc[q]);
+    column_reduce<4>(ad, r, red, [&](int q, int j, DAcc v) {
+      if (i0 + q <= k) P[((int64_t)(i0 + q) * r + j) * nblk + blk] = make_double2(v.x, v.y);
+    });
+  }
+}
+__device__ void block_norms_all_ff(const F4* __restrict__ w, int64_t n0, int64_t n1, int r, int blk, int nblk,
+                                   double* red, double* __restrict__ PN) {
+  const int tid = threadIdx.x;
+  const int S = (blockDim.x / r) * r;
+  FF acc = ff_zero();
+  if (tid < S)
+    for (int64_t t = n0 * r + tid; t < n1 * r; t += S) ff_norm_mac(acc, w[t]);
+  const double a1[1] = {ff_to_double(acc)};
+  column_reduce<1>(a1, r, red, [&](int, int j, double v) { PN[(int64_t)j * nblk + blk] = v; });
+}
+
+// The cooperative Arnoldi step of k_arnoldi_step (same phases, barriers,
+// orthogonalisation modes and outputs) on the float-float basis, for r <= the
+// block's threads.  Shared memory: that of k_arnoldi_step, then (m+1) r F4
+// (the Hessenberg column, split for the updates).
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int64_t vs, F4* __restrict__ w,
+                                                         const Tin* __restrict__ yin, float2* __restrict__ xnext,
+                                                         GmresDev gd, int64_t N, Z* __restrict__ P1,
+                                                         Z* __restrict__ P2, double* __restrict__ PN) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ Z sm[];
+  const int m = gd.m, r = gd.r;
+  const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  Z* hs = sm;                        // (m+1) r   h, then h + h2 in block 0
+  Z* h2s = hs + (m + 1) * r;         // (m+1) r
+  Z* ws = h2s + (m + 1) * r;         // max((m+1) nw, 4 blockDim) warp / column partials
+  const int wsn = max((m + 1) * nw, 4 * (int)blockDim.x);
+  int* need = reinterpret_cast<int*>(ws + wsn);   // r flags
+  F4* hf = reinterpret_cast<F4*>(ws + wsn) + (r + 3) / 4 + 1;   // (m+1) r, after the flags (16-byte aligned)
+  const int k = *gd.k;
+  const int nblk = gridDim.x, blk = blockIdx.x;
+  const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+  double* PN0 = PN;
+  double* PN1 = PN + (int64_t)r * nblk;
+  double* PN2 = PN + 2 * (int64_t)r * nblk;
+  // phase 0: the operator output is complex64, exact as hi parts
+  for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x)
+    w[t] = make_float4((float)yin[t].x, (float)yin[t].y, 0.0f, 0.0f);
+  __syncthreads();
+  // phase 1
+  block_dots_all_ff(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P1);
+  block_norms_all_ff(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN0);
+  grid.sync();
+  // phase 2
+  reduce_all_partials(P1, k, r, nblk, hs);
+  for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hf[i] = f4_split(hs[i]);
+  __syncthreads();
+  const bool fuse_norm = (int)blockDim.x % r == 0;
+  FF nacc = ff_zero();
+  ff_update_rows(V, vs, w, hf, k, r, n0 * r, n1 * r, nullptr, &nacc);
+  if (fuse_norm) {
+    const double a1[1] = {ff_to_double(nacc)};
+    column_reduce<1>(a1, r, reinterpret_cast<double*>(ws),
+                     [&](int, int j, double v) { PN1[(int64_t)j * nblk + blk] = v; });
+  } else {
+    __syncthreads();
+    block_norms_all_ff(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN1);
+  }
+  grid.sync();
+  // phase 3: selective reorthogonalisation (the decision as in k_arnoldi_step)
+  __shared__ int any_s;
+  if (threadIdx.x == 0) any_s = 0;
+  __syncthreads();
+  if (gd.orth == 2) {
+    for (int j = warp; j < r; j += nw) {
+      double b0 = 0, b1 = 0;
+      for (int b = lane; b < nblk; b += 32) {
+        b0 += PN0[(int64_t)j * nblk + b];
+        b1 += PN1[(int64_t)j * nblk + b];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        b0 += shfl_x(b0, o);
+        b1 += shfl_x(b1, o);
+      }
+      if (lane == 0) {
+        need[j] = gd.active[j] && b1 < 0.5 * b0;
+        if (need[j]) atomicOr(&any_s, 1);
+      }
+    }
+  } else {
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+      need[j] = gd.orth == 3 && gd.active[j];
+      if (need[j]) atomicOr(&any_s, 1);
+    }
+  }
+  __syncthreads();
+  const bool any_reorth = any_s != 0;
+  for (int i = threadIdx.x; i < (m + 1) * r; i += blockDim.x) h2s[i] = make_double2(0, 0);
+  __syncthreads();
+  if (any_reorth) {
+    block_dots_all_ff(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P2);
+    grid.sync();
+    for (int p = warp; p < (k + 1) * r; p += nw) {
+      const int i = p / r, j = p % r;
+      if (!need[j]) continue;
+      const Z* src = P2 + ((int64_t)i * r + j) * nblk;
+      Z acc = make_double2(0, 0);
+      for (int b = lane; b < nblk; b += 32) {
+        acc.x += src[b].x;
+        acc.y += src[b].y;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) h2s[i * r + j] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hf[i] = f4_split(h2s[i]);
+    __syncthreads();
+    ff_update_rows(V, vs, w, hf, k, r, n0 * r, n1 * r, need, nullptr);
+    __syncthreads();
+    block_norms_all_ff(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN2);
+    grid.sync();
+  }
+  // phase 4: norms, scales, the Hessenberg column (block 0), k += 1
+  double* scl = reinterpret_cast<double*>(ws);
+  for (int j = warp; j < r; j += nw) {
+    const double* PNf = (any_reorth && need[j]) ? PN2 : PN1;
+    double s2 = 0;
+    for (int b = lane; b < nblk; b += 32) s2 += PNf[(int64_t)j * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += shfl_x(s2, o);
+    if (lane == 0) {
+      scl[j] = (s2 > 0 && isfinite(s2)) ? 1.0 / sqrt(s2) : 0.0;
+      if (blk == 0) gd.hn2[j] = s2;
+    }
+  }
+  if (blk == 0) {
+    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x)
+      gd.hcol[i] = make_double2(hs[i].x + h2s[i].x, hs[i].y + h2s[i].y);
+    if (threadIdx.x == 0) *gd.k = k + 1;
+  }
+  __syncthreads();
+  // phase 5: V[k+1] = w / ||w|| (float-float), the next operator input its high parts
+  F4* sclf = hf;   // per column: the scale split (hf is free again)
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    float sh, sl;
+    ff_split(scl[j], sh, sl);
+    sclf[j] = make_float4(sh, sl, 0.0f, 0.0f);
+  }
+  __syncthreads();
+  for (int64_t t = n0 * r + threadIdx.x; t < n1 * r; t += blockDim.x) {
+    const int j = (int)(t % r);
+    const F4 a = w[t];
+    const FFv sc(sclf[j].x, sclf[j].y);
+    const FFv re = ffv_mul(FFv(a.x, a.z), sc), im = ffv_mul(FFv(a.y, a.w), sc);
+    V[(int64_t)(k + 1) * vs + t] = make_float4(re.h, im.h, re.l, im.l);
+    xnext[t] = make_float2(re.h, im.h);
+  }
+}
+
 // Givens update of the cooperative step's Hessenberg column (step k = *gd.k - 1:
 // the column h + h2 in gd.hcol, ||w||^2 in gd.hn2): previous rotations, the new
 // one, the residual estimate and the host flags; one CTA, a warp per column.  The
@@ -1009,6 +1327,8 @@ static unsigned grid_for(int64_t n) {
     if (_e != cudaSuccess) return {MM_ECUDA, cudaGetErrorString(_e)}; \
   } while (0)
 
+constexpr int kCoopSmemMax = 200 * 1024;   // dynamic shared memory ceiling of the cooperative steps
+
 Status Solver::ensure(int64_t N, int r, int m) {
   if (N == N_ && r == r_ && m <= m_) return {MM_OK, ""};
   release();
@@ -1024,7 +1344,6 @@ Status Solver::ensure(int64_t N, int r, int m) {
     // hs, h2s: (m+1) r each; ws: max((m+1) warps, block threads); need flags
     coop_smem_ = sizeof(Z) * ((size_t)(m + 1) * 2 * r + std::max<size_t>((size_t)(m + 1) * 8, 4 * 256)) +
                  sizeof(int) * (size_t)r + 16;
-    constexpr int kCoopSmemMax = 200 * 1024;
     coop_ok_ = coop_smem_ <= (size_t)kCoopSmemMax;
     if (coop_ok_) {
       // The attribute is per kernel and process-wide: it is set to the one fixed
@@ -1044,6 +1363,17 @@ Status Solver::ensure(int64_t N, int r, int m) {
     }
     int64_t want = coop_ok_ ? (int64_t)sms * per : 128;
     nblk_ = (int)std::max<int64_t>(1, std::min<int64_t>(want, (N + 63) / 64));
+    // the float-float step: the same layout, the r flags padded to 16 bytes, then
+    // the split Hessenberg column ((m+1) r F4); r at most one column per thread
+    coop_smem_ff_ = coop_smem_ + sizeof(F4) * ((size_t)(r + 3) / 4 + 1) + sizeof(F4) * (size_t)(m + 1) * r;
+    ffa_ok_ = coop_ok_ && r <= 256 && coop_smem_ff_ <= (size_t)kCoopSmemMax;
+    if (ffa_ok_) {
+      MM_CK(cudaFuncSetAttribute(k_arnoldi_step_ff<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kCoopSmemMax));
+      int p3 = 0;
+      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_arnoldi_step_ff<float2>, 256, coop_smem_ff_));
+      ffa_ok_ = p3 >= per;
+    }
   }
   size_t vec = sizeof(Z) * (size_t)N * r;
   MM_CK(cudaMalloc(&V_, vec * (m + 1)));
@@ -1058,6 +1388,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
   MM_CK(cudaMalloc(&active_, sizeof(int32_t) * r));
   MM_CK(cudaMalloc(&dx_, vec));
   MM_CK(cudaMalloc(&x64_, vec));
+  MM_CK(cudaMalloc(&yf_, sizeof(F4) * (size_t)(m + 1) * r));
   MM_CK(cudaMalloc(&P1_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
   MM_CK(cudaMalloc(&P2_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
   MM_CK(cudaMalloc(&PN_, sizeof(double) * 3 * (size_t)r * nblk_));
@@ -1104,7 +1435,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
 }
 
 void Solver::release() {
-  void* ps[] = {V_, w_, t_, x32_, y32_, partial_, h_, h2_, scale_, active_, dx_, x64_, P1_, P2_, PN_, gstate_};
+  void* ps[] = {V_, w_, t_, x32_, y32_, partial_, h_, h2_, scale_, active_, dx_, x64_, P1_, P2_, PN_, gstate_, yf_};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (flag_h_) cudaFreeHost(flag_h_);
@@ -1118,7 +1449,7 @@ void Solver::release() {
   if (gst_) cudaStreamDestroy(gst_);
   gst_ = nullptr;
   flag_h_ = nullptr;
-  x64_ = P1_ = P2_ = PN_ = gstate_ = nullptr;
+  x64_ = P1_ = P2_ = PN_ = gstate_ = yf_ = nullptr;
   V_ = w_ = t_ = nullptr;
   x32_ = y32_ = nullptr;
   partial_ = nullptr;
@@ -1174,6 +1505,9 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
   Z* w = static_cast<Z*>(w_);
   GmresDev gd = *reinterpret_cast<GmresDev*>(gdev_);
   gd.orth = orth;
+  // complex64 inner solves: the float-float basis when asked for and the step fits
+  const bool ffk = ff_arnoldi && ffa_ok_ && prec != MM_C128;
+  F4* Vf = static_cast<F4*>(V_);
   volatile int* flag = static_cast<volatile int*>(flag_h_);
   volatile double* hres = reinterpret_cast<volatile double*>(static_cast<char*>(flag_h_) + sizeof(int) * 4);
   iters = 0;
@@ -1219,6 +1553,8 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     // first basis vector V[0] = r0/||r0|| and the operator input
     if (prec == MM_C128)
       k_fetch<Z><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<Z*>(x64_));
+    else if (ffk)
+      k_fetch_ff<<<grid_for(n), 256, 0, st>>>(Vf, vs, w, gd, n, static_cast<float2*>(x32_));
     else
       k_fetch<float2><<<grid_for(n), 256, 0, st>>>(V, vs, w, gd, n, static_cast<float2*>(x32_));
     for (int it = 0; it < m && iters + it < max_iter; ++it) {
@@ -1250,6 +1586,14 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
           void* args[] = {&Vp, &vsp, &wp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
           MM_CK(cudaLaunchCooperativeKernel((void*)k_arnoldi_step<double2, double2>, dim3(nblk_), dim3(256), args,
                                             coop_smem_, st));
+        } else if (ffk) {
+          F4* Vfp = Vf;
+          F4* wfp = reinterpret_cast<F4*>(w);
+          const float2* yp = static_cast<const float2*>(yin);
+          float2* xp = static_cast<float2*>(x32_);
+          void* args[] = {&Vfp, &vsp, &wfp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
+          MM_CK(cudaLaunchCooperativeKernel((void*)k_arnoldi_step_ff<float2>, dim3(nblk_), dim3(256), args,
+                                            coop_smem_ff_, st));
         } else {
           const float2* yp = static_cast<const float2*>(yin);
           float2* xp = static_cast<float2*>(x32_);
@@ -1306,7 +1650,12 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
     if (coop_ok_) MM_CK(cudaStreamWaitEvent(st, evg_[(launched - 1) & 1], 0));
     k_solve_y<<<r, 256, sizeof(Z) * (kSolveSmemK * kSolveSmemK + kSolveSmemK), st>>>(gd);
     if (prof) prof->begin(7, st);
-    k_add_basis_dev<<<grid_for(n), 256, 0, st>>>(V, vs, gd, n, x);
+    if (ffk) {
+      k_split_y<<<(unsigned)std::max(1, (m * r + 255) / 256), 256, 0, st>>>(gd, static_cast<F4*>(yf_));
+      k_add_basis_ff<<<grid_for(n), 256, 0, st>>>(Vf, vs, gd, static_cast<const F4*>(yf_), n, x);
+    } else {
+      k_add_basis_dev<<<grid_for(n), 256, 0, st>>>(V, vs, gd, n, x);
+    }
     if (prof) prof->end(st, 1);
     MM_CK(cudaGetLastError());
     MM_CK(cudaStreamSynchronize(st));

@@ -34,6 +34,9 @@ class Solver {
   int matvecs = 0;
   Profiler* prof = nullptr;   // optional stage profiler (Krylov kernels)
   int orth = 2;               // 1 one pass, 2 selective second pass, 3 two passes
+  // complex64 inner solves keep the Krylov basis as float-float values and take
+  // the Arnoldi products on the FP32 pipe (when the cooperative step fits)
+  bool ff_arnoldi = true;
 
   ~Solver() { release(); }
   Status ensure(int64_t N, int r, int m);
@@ -59,6 +62,9 @@ class Solver {
   cudaEvent_t eva_ = nullptr, evg_[2] = {nullptr, nullptr};
   bool coop_ok_ = false;       // the Arnoldi step runs as one cooperative launch
   size_t coop_smem_ = 0;
+  bool ffa_ok_ = false;        // ... and its float-float form fits (r <= 256, shared memory, occupancy)
+  size_t coop_smem_ff_ = 0;
+  void* yf_ = nullptr;         // the cycle's y split for the float-float basis sum
   size_t bytes_ = 0;
 };
 

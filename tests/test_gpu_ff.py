@@ -15,8 +15,9 @@ complex128 oracle (the FP64 product itself is within about 1e-13 of it), the
 accuracy the refinement residual is held to.
 
 The refinement residual of a complex64 solve uses this product by default
-(mm_solve_opts.residual = 0): the solutions of both residual forms meet the
-tolerance and agree with the oracle's solve.
+(mm_solve_opts.fp64 = 0), and the inner solves then keep their Krylov basis
+in float-float and take the Arnoldi products on the FP32 pipe: the solutions
+of both forms meet the tolerance and agree with the oracle's solve.
 """
 import os
 
@@ -158,7 +159,7 @@ def test_refinement_residual_forms(c1, residual):
     V = torch.from_numpy(g["V"]).cuda()
     E = torch.empty_like(V)
     st = mm.mm_solve(c1.array, 1, V, E, tol=1e-6, restart=50, max_iter=500, precision=mm.MM_C64, refine=1,
-                     residual=residual)
+                     fp64=residual)
     assert st["converged"] and st["rel_residual"] <= 1e-6
     err = _rel(E.cpu().numpy(), g["E"])
     assert err <= 1e-4, err
@@ -175,7 +176,7 @@ def test_refinement_residual_forms_agree_at_1e_10(ctx, c1):
     for residual in (0, 1):
         E = torch.empty_like(V)
         st = mm.mm_solve(c1.array, 1, V, E, tol=1e-10, restart=50, max_iter=2000, precision=mm.MM_C64, refine=1,
-                         inner_tol=1e-4, residual=residual)
+                         inner_tol=1e-4, fp64=residual)
         assert st["converged"] and st["rel_residual"] <= 1e-10
         assert st["refinements"] >= 2
         out.append(E.cpu().numpy())
@@ -185,7 +186,7 @@ def test_refinement_residual_forms_agree_at_1e_10(ctx, c1):
 def test_ff_rejected_where_unsupported(c1):
     x = torch.zeros(c1.n, dtype=torch.complex128, device="cuda")
     with pytest.raises(mm.MacroAIMError) as e:
-        mm.mm_solve(c1.array, 1, x, torch.empty_like(x), tol=1e-6, precision=mm.MM_C64, refine=1, residual=2)
+        mm.mm_solve(c1.array, 1, x, torch.empty_like(x), tol=1e-6, precision=mm.MM_C64, refine=1, fp64=2)
     assert e.value.status == mm.MM_EINVAL
 
 
