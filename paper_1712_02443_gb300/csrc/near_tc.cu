@@ -50,6 +50,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "cp_async.cuh"
 #include "device.h"
 #include "near_tc.h"
 #include "tc_gemm.h"
@@ -88,18 +89,6 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(b & 0xFFFFE000u);
 }
 
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
-}
-// 16-byte copy (L2 only); bytes = 16 or 0 (zero fill)
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 // named barriers of the gather warps (1) and of the epilogue warps (2)
 __device__ __forceinline__ void gather_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, %0;" ::"n"(kEpi) : "memory"); }
