@@ -320,10 +320,12 @@ mm_status mm_rcs(mm_array* array, int32_t nrhs, const void* Jhat_dev, int64_t nd
 
 /* GMRES solve of (D - G T A^-1 B) E^ = V^ (eq. (finalsystem); Sec. V) for
  * nrhs independent columns, x0 = 0.  precision MM_C128: plain FP64 GMRES on
- * the complex128 operator.  precision MM_C64 with refine = 1: complex64
- * operator inside GMRES (FP64 Arnoldi and Givens), wrapped in FP64
- * iterative refinement against the complex128 operator until
- * ||V^ - Z E^|| <= tol ||V^|| per column.  V_dev, E_dev: (N^ x nrhs)
+ * the complex128 operator.  precision MM_C64 (or a tensor-core mode) with
+ * refine = 1: complex64 operator inside GMRES (Arnoldi products on a Krylov
+ * basis of complex128 precision, FP64 Givens), wrapped in iterative
+ * refinement against the complex128 operator until ||V^ - Z E^|| <= tol ||V^||
+ * per column; opts->fp64 chooses float-float (default) or FP64 arithmetic for
+ * the residual and the inner Arnoldi products.  V_dev, E_dev: (N^ x nrhs)
  * complex128.  Synchronous: returns when done.  MM_ENOCONV if max_iter was
  * reached (E_dev holds the last iterate).                                     */
 typedef struct mm_solve_opts {

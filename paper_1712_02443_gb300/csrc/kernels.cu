@@ -23,6 +23,10 @@
 //  matvec         the schedule: A1 on the caller's stream, then the near field on
 //                 the array's low-priority stream beside A2-A4 on its high-priority
 //                 stream, joined back into the caller's stream
+//  *_ff, <FFTag>, <NearFF>
+//                 the complex128 product in float-float arithmetic (ffops.cuh):
+//                 k_split_f6, k_macro_gemm_ff, k_project_ff, the FFT stages on
+//                 CF values, k_interp_ff, k_near_blocks<NearFF>
 //
 // Layouts: vectors element-major with RHS innermost; grids [4 nrhs][Nx][Ny][Nz]
 // (batch b = psi * nrhs + j); partial spectra [b][x][ky][kz]; Green's spectrum

@@ -1,8 +1,10 @@
 // GMRES (Sec. V; Saad and Schultz 1986) for the final system (eq. (finalsystem)),
-// with FP64 Arnoldi (classical Gram-Schmidt, one pass, a selective second pass,
-// or two passes) and Givens rotations, independent columns for several
-// right-hand sides, and FP64 iterative refinement around a complex64 inner
-// operator.  Also the plane-wave excitation kernels (Sec. IV, eq. (V1)).
+// with Arnoldi (classical Gram-Schmidt, one pass, a selective second pass, or
+// two passes) in FP64 or, for the inner solves of refinement, on a float-float
+// Krylov basis, FP64 Givens rotations, independent columns for several
+// right-hand sides, and iterative refinement around a complex64 inner operator
+// (residuals through the complex128 operator).  Also the plane-wave excitation
+// kernels (Sec. IV, eq. (V1)).
 #include <cooperative_groups.h>
 
 #include <cmath>
