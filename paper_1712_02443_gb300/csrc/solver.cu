@@ -995,9 +995,14 @@ __global__ void k_add_basis_ff(const F4* __restrict__ V, int64_t vs, GmresDev gd
   }
 }
 
+// Rows per thread and round of the float-float Arnoldi loops: all their loads
+// are issued before their products (memory-level parallelism for the basis,
+// which streams from HBM at large sizes).
+constexpr int kFfRows = 4;
+
 // w[t] -= sum_{i <= k} V_i[t] h_i[t mod r] for the flat rows t in [t0, t1) of
-// this block (columns with need[j] == 0 skipped when need is given), two rows
-// per thread and round and four basis vectors per load group; with nacc, the
+// this block (columns with need[j] == 0 skipped when need is given), kFfRows
+// rows per thread and round and four basis vectors per load group; with nacc, the
 // thread's sum of |w[t]|^2 after the update (a thread keeps one column when
 // r divides the block).
 __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t vs, F4* __restrict__ w,
@@ -1005,37 +1010,40 @@ __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t
                                                const int* need, FF* nacc) {
   const F4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const int B = blockDim.x;
-  for (int64_t t = t0 + threadIdx.x; t < t1; t += 2 * B) {
-    const int64_t tb = t + B;
-    const int ja = (int)(t % r), jb = (int)(tb % r);
-    const bool ua = need == nullptr || need[ja];
-    const bool ub = tb < t1 && (need == nullptr || need[jb]);
-    if (!ua && !ub) continue;
-    FFC a = ffc_of(ua ? w[t] : z4), b = ffc_of(ub ? w[tb] : z4);
-    for (int i0 = 0; i0 <= k; i0 += 4) {
-      F4 va[4], vb[4];
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += kFfRows * B) {
+    int ju[kFfRows];
+    bool uu[kFfRows];
+    bool any = false;
+    FFC a[kFfRows];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        va[q] = (ua && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + t] : z4;
-        vb[q] = (ub && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tb] : z4;
-      }
+    for (int u = 0; u < kFfRows; ++u) {
+      const int64_t tu = t + (int64_t)u * B;
+      ju[u] = (int)(tu % r);
+      uu[u] = tu < t1 && (need == nullptr || need[ju[u]]);
+      any |= uu[u];
+      a[u] = ffc_of(uu[u] ? w[tu] : z4);
+    }
+    if (!any) continue;
+    for (int i0 = 0; i0 <= k; i0 += 4) {
+      F4 vv[kFfRows][4];
+#pragma unroll
+      for (int u = 0; u < kFfRows; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          vv[u][q] = (uu[u] && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + t + (int64_t)u * B] : z4;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (i0 + q <= k) {
-          ffc_sub_mul(a, va[q], hf[(i0 + q) * r + ja]);
-          ffc_sub_mul(b, vb[q], hf[(i0 + q) * r + jb]);
-        }
+        if (i0 + q <= k)
+#pragma unroll
+          for (int u = 0; u < kFfRows; ++u) ffc_sub_mul(a[u], vv[u][q], hf[(i0 + q) * r + ju[u]]);
     }
-    if (ua) {
-      const F4 o = ffc_pack(a);
-      w[t] = o;
-      if (nacc) ff_norm_mac(*nacc, o);
-    }
-    if (ub) {
-      const F4 o = ffc_pack(b);
-      w[tb] = o;
-      if (nacc) ff_norm_mac(*nacc, o);
-    }
+#pragma unroll
+    for (int u = 0; u < kFfRows; ++u)
+      if (uu[u]) {
+        const F4 o = ffc_pack(a[u]);
+        w[t + (int64_t)u * B] = o;
+        if (nacc) ff_norm_mac(*nacc, o);
+      }
   }
 }
 
@@ -1051,24 +1059,24 @@ __device__ void block_dots_all_ff(const F4* __restrict__ V, int64_t vs, const F4
     FFC acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = ffc_zero();
-    // two rows per round, every load of the round issued before the products
-    // (the basis streams from HBM at large sizes: ten 16-byte loads in flight)
+    // kFfRows rows per round, every load of the round issued before the
+    // products (the basis streams from HBM at large sizes: 5 kFfRows 16-byte
+    // loads in flight per thread)
     if (tid < S)
-      for (int64_t t = n0 * r + tid; t < t1; t += 2 * S) {
-        const int64_t tb = t + S;
-        const bool two = tb < t1;
-        const F4 wa = w[t], wb = two ? w[tb] : z4;
-        F4 va[4], vb[4];
+      for (int64_t t = n0 * r + tid; t < t1; t += kFfRows * S) {
+        F4 wv[kFfRows], vv[kFfRows][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          va[q] = i0 + q <= k ? V[(int64_t)(i0 + q) * vs + t] : z4;
-          vb[q] = (two && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tb] : z4;
+        for (int u = 0; u < kFfRows; ++u) {
+          const int64_t tu = t + (int64_t)u * S;
+          const bool in = tu < t1;
+          wv[u] = in ? w[tu] : z4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) vv[u][q] = (in && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tu] : z4;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          ffc_conj_mac(acc[q], va[q], wa);
-          ffc_conj_mac(acc[q], vb[q], wb);
-        }
+        for (int u = 0; u < kFfRows; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ffc_conj_mac(acc[q], vv[u][q], wv[u]);
       }
     DAcc ad[4];
 #pragma unroll
