@@ -211,7 +211,9 @@ void mm_array_destroy(mm_array* array);
  * TF32 with a three-product split, k split 1 or 2 (2 for up to 8 right-hand
  * sides); 7-9 the tensor-core direct form
  * for 16 or more right-hand sides of even count);
- * MACROAIM_NEAR=csr applies the near field as CSR rows.                      */
+ * MACROAIM_NEAR=csr applies the near field as CSR rows;
+ * MACROAIM_FF_SHAPE="gemm,near" fixes the tile shapes of the MM_C128_FF
+ * GEMM (0-2) and near field (0-3).                                           */
 mm_status mm_apply(mm_array* array, int32_t nrhs, const void* x_dev, void* y_dev, int32_t precision,
                    void* stream);
 /* Products of several arrays in one call (arrays of different sizes, element
@@ -325,7 +327,8 @@ mm_status mm_rcs(mm_array* array, int32_t nrhs, const void* Jhat_dev, int64_t nd
  * basis of complex128 precision, FP64 Givens), wrapped in iterative
  * refinement against the complex128 operator until ||V^ - Z E^|| <= tol ||V^||
  * per column; opts->fp64 chooses float-float (default) or FP64 arithmetic for
- * the residual and the inner Arnoldi products.  V_dev, E_dev: (N^ x nrhs)
+ * the residual and the inner Arnoldi products (tuning override read at each
+ * call: MACROAIM_FF_ARNOLDI=0 keeps the inner Arnoldi in FP64).  V_dev, E_dev: (N^ x nrhs)
  * complex128.  Synchronous: returns when done.  MM_ENOCONV if max_iter was
  * reached (E_dev holds the last iterate).                                     */
 typedef struct mm_solve_opts {

@@ -1615,7 +1615,11 @@ mm_status mm_solve(mm_array* a, int32_t nrhs, const void* V_dev, void* E_dev, co
   // refinement residuals and the inner Arnoldi products in float-float
   // arithmetic (the default) or FP64
   const bool ff_res = opts->refine && opts->fp64 == 0;
-  S.ff_arnoldi = ff_res;
+  // tuning override: MACROAIM_FF_ARNOLDI=0 keeps the inner Arnoldi in FP64 (the residual stays float-float)
+  {
+    const char* fa = std::getenv("MACROAIM_FF_ARNOLDI");
+    S.ff_arnoldi = ff_res && !(fa && std::string(fa) == "0");
+  }
   if (ff_res) {
     upload_ff(a);
     ensure_ff_work(a, a->da.wd, nrhs);

@@ -995,28 +995,30 @@ __global__ void k_add_basis_ff(const F4* __restrict__ V, int64_t vs, GmresDev gd
   }
 }
 
-// Rows per thread and round of the float-float Arnoldi loops: all their loads
-// are issued before their products (memory-level parallelism for the basis,
-// which streams from HBM at large sizes).
-constexpr int kFfRows = 4;
+// Rows per thread and round of the float-float Arnoldi loops (RR): all their
+// loads are issued before their products, for memory-level parallelism where
+// the basis streams from HBM (four rows); where a thread has only a few rows
+// (one column at 16x16: about two) the smaller unrolled body of two rows
+// keeps the step's code in the instruction cache.
 
 // w[t] -= sum_{i <= k} V_i[t] h_i[t mod r] for the flat rows t in [t0, t1) of
-// this block (columns with need[j] == 0 skipped when need is given), kFfRows
+// this block (columns with need[j] == 0 skipped when need is given), RR
 // rows per thread and round and four basis vectors per load group; with nacc, the
 // thread's sum of |w[t]|^2 after the update (a thread keeps one column when
 // r divides the block).
+template <int RR>
 __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t vs, F4* __restrict__ w,
                                                const F4* hf, int k, int r, int64_t t0, int64_t t1,
                                                const int* need, FF* nacc) {
   const F4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const int B = blockDim.x;
-  for (int64_t t = t0 + threadIdx.x; t < t1; t += kFfRows * B) {
-    int ju[kFfRows];
-    bool uu[kFfRows];
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += RR * B) {
+    int ju[RR];
+    bool uu[RR];
     bool any = false;
-    FFC a[kFfRows];
+    FFC a[RR];
 #pragma unroll
-    for (int u = 0; u < kFfRows; ++u) {
+    for (int u = 0; u < RR; ++u) {
       const int64_t tu = t + (int64_t)u * B;
       ju[u] = (int)(tu % r);
       uu[u] = tu < t1 && (need == nullptr || need[ju[u]]);
@@ -1025,9 +1027,9 @@ __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t
     }
     if (!any) continue;
     for (int i0 = 0; i0 <= k; i0 += 4) {
-      F4 vv[kFfRows][4];
+      F4 vv[RR][4];
 #pragma unroll
-      for (int u = 0; u < kFfRows; ++u)
+      for (int u = 0; u < RR; ++u)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           vv[u][q] = (uu[u] && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + t + (int64_t)u * B] : z4;
@@ -1035,10 +1037,10 @@ __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t
       for (int q = 0; q < 4; ++q)
         if (i0 + q <= k)
 #pragma unroll
-          for (int u = 0; u < kFfRows; ++u) ffc_sub_mul(a[u], vv[u][q], hf[(i0 + q) * r + ju[u]]);
+          for (int u = 0; u < RR; ++u) ffc_sub_mul(a[u], vv[u][q], hf[(i0 + q) * r + ju[u]]);
     }
 #pragma unroll
-    for (int u = 0; u < kFfRows; ++u)
+    for (int u = 0; u < RR; ++u)
       if (uu[u]) {
         const F4 o = ffc_pack(a[u]);
         w[t + (int64_t)u * B] = o;
@@ -1049,6 +1051,7 @@ __device__ __forceinline__ void ff_update_rows(const F4* __restrict__ V, int64_t
 
 // block_dots_all and block_norms_all on the float-float vectors: each thread's
 // sums in float-float, the block reduction in FP64 (column_reduce).
+template <int RR>
 __device__ void block_dots_all_ff(const F4* __restrict__ V, int64_t vs, const F4* __restrict__ w, int k, int64_t n0,
                                   int64_t n1, int r, int blk, int nblk, DAcc* red, Z* __restrict__ P) {
   const int tid = threadIdx.x;
@@ -1059,14 +1062,14 @@ __device__ void block_dots_all_ff(const F4* __restrict__ V, int64_t vs, const F4
     FFC acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = ffc_zero();
-    // kFfRows rows per round, every load of the round issued before the
-    // products (the basis streams from HBM at large sizes: 5 kFfRows 16-byte
+    // RR rows per round, every load of the round issued before the
+    // products (the basis streams from HBM at large sizes: 5 RR 16-byte
     // loads in flight per thread)
     if (tid < S)
-      for (int64_t t = n0 * r + tid; t < t1; t += kFfRows * S) {
-        F4 wv[kFfRows], vv[kFfRows][4];
+      for (int64_t t = n0 * r + tid; t < t1; t += RR * S) {
+        F4 wv[RR], vv[RR][4];
 #pragma unroll
-        for (int u = 0; u < kFfRows; ++u) {
+        for (int u = 0; u < RR; ++u) {
           const int64_t tu = t + (int64_t)u * S;
           const bool in = tu < t1;
           wv[u] = in ? w[tu] : z4;
@@ -1074,7 +1077,7 @@ __device__ void block_dots_all_ff(const F4* __restrict__ V, int64_t vs, const F4
           for (int q = 0; q < 4; ++q) vv[u][q] = (in && i0 + q <= k) ? V[(int64_t)(i0 + q) * vs + tu] : z4;
         }
 #pragma unroll
-        for (int u = 0; u < kFfRows; ++u)
+        for (int u = 0; u < RR; ++u)
 #pragma unroll
           for (int q = 0; q < 4; ++q) ffc_conj_mac(acc[q], vv[u][q], wv[u]);
       }
@@ -1101,7 +1104,7 @@ __device__ void block_norms_all_ff(const F4* __restrict__ w, int64_t n0, int64_t
 // orthogonalisation modes and outputs) on the float-float basis, for r <= the
 // block's threads.  Shared memory: that of k_arnoldi_step, then (m+1) r F4
 // (the Hessenberg column, split for the updates).
-template <typename Tin>
+template <typename Tin, int RR>
 __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int64_t vs, F4* __restrict__ w,
                                                          const Tin* __restrict__ yin, float2* __restrict__ xnext,
                                                          GmresDev gd, int64_t N, Z* __restrict__ P1,
@@ -1127,7 +1130,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
     w[t] = make_float4((float)yin[t].x, (float)yin[t].y, 0.0f, 0.0f);
   __syncthreads();
   // phase 1
-  block_dots_all_ff(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P1);
+  block_dots_all_ff<RR>(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P1);
   block_norms_all_ff(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN0);
   grid.sync();
   // phase 2
@@ -1136,7 +1139,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
   __syncthreads();
   const bool fuse_norm = (int)blockDim.x % r == 0;
   FF nacc = ff_zero();
-  ff_update_rows(V, vs, w, hf, k, r, n0 * r, n1 * r, nullptr, &nacc);
+  ff_update_rows<RR>(V, vs, w, hf, k, r, n0 * r, n1 * r, nullptr, &nacc);
   if (fuse_norm) {
     const double a1[1] = {ff_to_double(nacc)};
     column_reduce<1>(a1, r, reinterpret_cast<double*>(ws),
@@ -1178,7 +1181,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
   for (int i = threadIdx.x; i < (m + 1) * r; i += blockDim.x) h2s[i] = make_double2(0, 0);
   __syncthreads();
   if (any_reorth) {
-    block_dots_all_ff(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P2);
+    block_dots_all_ff<RR>(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P2);
     grid.sync();
     for (int p = warp; p < (k + 1) * r; p += nw) {
       const int i = p / r, j = p % r;
@@ -1195,7 +1198,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
     __syncthreads();
     for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hf[i] = f4_split(h2s[i]);
     __syncthreads();
-    ff_update_rows(V, vs, w, hf, k, r, n0 * r, n1 * r, need, nullptr);
+    ff_update_rows<RR>(V, vs, w, hf, k, r, n0 * r, n1 * r, need, nullptr);
     __syncthreads();
     block_norms_all_ff(w, n0, n1, r, blk, nblk, reinterpret_cast<double*>(ws), PN2);
     grid.sync();
@@ -1378,11 +1381,14 @@ Status Solver::ensure(int64_t N, int r, int m) {
     coop_smem_ff_ = coop_smem_ + sizeof(F4) * ((size_t)(r + 3) / 4 + 1) + sizeof(F4) * (size_t)(m + 1) * r;
     ffa_ok_ = coop_ok_ && r <= 256 && coop_smem_ff_ <= (size_t)kCoopSmemMax;
     if (ffa_ok_) {
-      MM_CK(cudaFuncSetAttribute(k_arnoldi_step_ff<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      MM_CK(cudaFuncSetAttribute(k_arnoldi_step_ff<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kCoopSmemMax));
-      int p3 = 0;
-      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_arnoldi_step_ff<float2>, 256, coop_smem_ff_));
-      ffa_ok_ = p3 >= per;
+      MM_CK(cudaFuncSetAttribute(k_arnoldi_step_ff<float2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kCoopSmemMax));
+      int p3 = 0, p4 = 0;
+      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_arnoldi_step_ff<float2, 2>, 256, coop_smem_ff_));
+      MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_arnoldi_step_ff<float2, 4>, 256, coop_smem_ff_));
+      ffa_ok_ = std::min(p3, p4) >= per;
     }
   }
   size_t vec = sizeof(Z) * (size_t)N * r;
@@ -1602,7 +1608,10 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
           const float2* yp = static_cast<const float2*>(yin);
           float2* xp = static_cast<float2*>(x32_);
           void* args[] = {&Vfp, &vsp, &wfp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
-          MM_CK(cudaLaunchCooperativeKernel((void*)k_arnoldi_step_ff<float2>, dim3(nblk_), dim3(256), args,
+          // four rows per round once a thread has eight or more rows
+          const bool deep = (int64_t)N * r >= (int64_t)nblk_ * 256 * 8;
+          MM_CK(cudaLaunchCooperativeKernel(deep ? (void*)k_arnoldi_step_ff<float2, 4> : (void*)k_arnoldi_step_ff<float2, 2>,
+                                            dim3(nblk_), dim3(256), args,
                                             coop_smem_ff_, st));
         } else {
           const float2* yp = static_cast<const float2*>(yin);
