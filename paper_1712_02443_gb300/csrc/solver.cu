@@ -1380,6 +1380,7 @@ Status Solver::ensure(int64_t N, int r, int m) {
     // the split Hessenberg column ((m+1) r F4); r at most one column per thread
     coop_smem_ff_ = coop_smem_ + sizeof(F4) * ((size_t)(r + 3) / 4 + 1) + sizeof(F4) * (size_t)(m + 1) * r;
     ffa_ok_ = coop_ok_ && r <= 256 && coop_smem_ff_ <= (size_t)kCoopSmemMax;
+    nblk_ff_ = nblk_;
     if (ffa_ok_) {
       MM_CK(cudaFuncSetAttribute(k_arnoldi_step_ff<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kCoopSmemMax));
@@ -1389,6 +1390,12 @@ Status Solver::ensure(int64_t N, int r, int m) {
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_arnoldi_step_ff<float2, 2>, 256, coop_smem_ff_));
       MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_arnoldi_step_ff<float2, 4>, 256, coop_smem_ff_));
       ffa_ok_ = std::min(p3, p4) >= per;
+      // where every thread has many rows (the basis streams from HBM), two CTAs
+      // per SM when the shared memory allows: twice the loads in flight
+      const bool deep = (int64_t)N * r >= (int64_t)sms * 256 * 8;
+      const int per_ff = deep ? std::min(std::min(p3, p4), 2) : per;
+      nblk_ff_ = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_ff, 1), (N + 63) / 64));
+      if (!deep) nblk_ff_ = nblk_;
     }
   }
   size_t vec = sizeof(Z) * (size_t)N * r;
@@ -1405,9 +1412,10 @@ Status Solver::ensure(int64_t N, int r, int m) {
   MM_CK(cudaMalloc(&dx_, vec));
   MM_CK(cudaMalloc(&x64_, vec));
   MM_CK(cudaMalloc(&yf_, sizeof(F4) * (size_t)(m + 1) * r));
-  MM_CK(cudaMalloc(&P1_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
-  MM_CK(cudaMalloc(&P2_, sizeof(Z) * (size_t)(m + 1) * r * nblk_));
-  MM_CK(cudaMalloc(&PN_, sizeof(double) * 3 * (size_t)r * nblk_));
+  const size_t nbmax = (size_t)std::max(nblk_, nblk_ff_);   // partial sums of either step
+  MM_CK(cudaMalloc(&P1_, sizeof(Z) * (size_t)(m + 1) * r * nbmax));
+  MM_CK(cudaMalloc(&P2_, sizeof(Z) * (size_t)(m + 1) * r * nbmax));
+  MM_CK(cudaMalloc(&PN_, sizeof(double) * 3 * (size_t)r * nbmax));
   {
     // GMRES cycle state: k, active, kdone, tol, res, scale, g, cs, sn, H, y
     size_t b = 0;
@@ -1609,9 +1617,9 @@ Status Solver::gmres(const Z* b, Z* x, bool x_zero, const std::vector<double>& t
           float2* xp = static_cast<float2*>(x32_);
           void* args[] = {&Vfp, &vsp, &wfp, &yp, &xp, &gd, &Np, &P1p, &P2p, &PNp};
           // four rows per round once a thread has eight or more rows
-          const bool deep = (int64_t)N * r >= (int64_t)nblk_ * 256 * 8;
+          const bool deep = (int64_t)N * r >= (int64_t)nblk_ff_ * 256 * 8;
           MM_CK(cudaLaunchCooperativeKernel(deep ? (void*)k_arnoldi_step_ff<float2, 4> : (void*)k_arnoldi_step_ff<float2, 2>,
-                                            dim3(nblk_), dim3(256), args,
+                                            dim3(nblk_ff_), dim3(256), args,
                                             coop_smem_ff_, st));
         } else {
           const float2* yp = static_cast<const float2*>(yin);

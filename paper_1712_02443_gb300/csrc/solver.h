@@ -53,6 +53,7 @@ class Solver {
                int& iters, std::vector<double>& res, cudaStream_t st);
   int64_t N_ = 0;
   int r_ = 0, m_ = 0, nblk_ = 1;
+  int nblk_ff_ = 1;            // blocks of the float-float step (two per SM at large sizes when they fit)
   void *V_ = nullptr, *w_ = nullptr, *t_ = nullptr, *x32_ = nullptr, *y32_ = nullptr;
   void *partial_ = nullptr, *h_ = nullptr, *h2_ = nullptr, *scale_ = nullptr, *active_ = nullptr, *dx_ = nullptr;
   void *x64_ = nullptr, *P1_ = nullptr, *P2_ = nullptr, *PN_ = nullptr, *gstate_ = nullptr, *flag_h_ = nullptr;

@@ -72,17 +72,19 @@ def test_batch_of_uneven_arrays(ctx):
         a1.close()
 
 
-@pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C64_F16, mm.MM_C128])
+@pytest.mark.parametrize("prec", [mm.MM_C64, mm.MM_C64_F16, mm.MM_C128, mm.MM_C128_FF])
 def test_batch_graph_replay(ctx, prec):
     """From the second call with the same arrays, widths, buffers and precision
-    the batch is captured into one CUDA graph and replayed: new inputs in the
+    (the float-float complex128 product included) the batch is captured into one
+    CUDA graph and replayed: new inputs in the
     same buffers give the new products (each equal to mm_apply alone), and
     destroying an array of a captured batch drops its graph (a later batch with a
     new array of the same size is computed afresh)."""
     a1 = loop_array(ctx, 2, 2)
     a2 = loop_array(ctx, 6, 6, outers=C3_OUTERS, config_index=2)
-    dt = torch.complex128 if prec == mm.MM_C128 else torch.complex64
-    tol = 1e-11 if prec == mm.MM_C128 else 1e-5
+    wide = prec in (mm.MM_C128, mm.MM_C128_FF)
+    dt = torch.complex128 if wide else torch.complex64
+    tol = 1e-11 if wide else 1e-5
     try:
         nr = [1, 16]
         X = [torch.empty(la.n * r, dtype=dt, device="cuda") for la, r in zip((a1, a2), nr)]
@@ -109,7 +111,8 @@ def test_batch_graph_replay(ctx, prec):
         for _ in range(3):
             mm.mm_apply_batch([a1.array, a2.array], nr, X, Y, prec, st)
             torch.cuda.synchronize()
-            bar = {mm.MM_C128: 1e-10, mm.MM_C64: 1e-5, mm.MM_C64_F16: 3e-3}[prec]   # the 16-bit bar of the GEMM tests
+            # the 16-bit bar of the GEMM tests; the float-float bar of tests/test_gpu_ff.py
+            bar = {mm.MM_C128: 1e-10, mm.MM_C128_FF: 1e-12, mm.MM_C64: 1e-5, mm.MM_C64_F16: 3e-3}[prec]
             assert _rel(Y[0].cpu().numpy().astype(np.complex128), g1["y"]) <= bar
     finally:
         a2.close()
