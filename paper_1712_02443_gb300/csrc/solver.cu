@@ -1113,12 +1113,13 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
   extern __shared__ Z sm[];
   const int m = gd.m, r = gd.r;
   const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  Z* hs = sm;                        // (m+1) r   h, then h + h2 in block 0
-  Z* h2s = hs + (m + 1) * r;         // (m+1) r
-  Z* ws = h2s + (m + 1) * r;         // max((m+1) nw, 4 blockDim) warp / column partials
+  // (m+1) r entries of 16 bytes: the Hessenberg column h (then h2) in FP64,
+  // split in place into F4 for the updates once block 0 has stored it
+  Z* hs = sm;
+  F4* hf = reinterpret_cast<F4*>(sm);
+  Z* ws = hs + (m + 1) * r;          // max((m+1) nw, 4 blockDim) warp / column partials
   const int wsn = max((m + 1) * nw, 4 * (int)blockDim.x);
   int* need = reinterpret_cast<int*>(ws + wsn);   // r flags
-  F4* hf = reinterpret_cast<F4*>(ws + wsn) + (r + 3) / 4 + 1;   // (m+1) r, after the flags (16-byte aligned)
   const int k = *gd.k;
   const int nblk = gridDim.x, blk = blockIdx.x;
   const int64_t chunk = (N + nblk - 1) / nblk, n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
@@ -1135,7 +1136,11 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
   grid.sync();
   // phase 2
   reduce_all_partials(P1, k, r, nblk, hs);
-  for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hf[i] = f4_split(hs[i]);
+  for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) {
+    const Z z = hs[i];
+    if (blk == 0) gd.hcol[i] = z;   // the Hessenberg column for the Givens update (plus h2 below)
+    hf[i] = f4_split(z);
+  }
   __syncthreads();
   const bool fuse_norm = (int)blockDim.x % r == 0;
   FF nacc = ff_zero();
@@ -1178,9 +1183,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
   }
   __syncthreads();
   const bool any_reorth = any_s != 0;
-  for (int i = threadIdx.x; i < (m + 1) * r; i += blockDim.x) h2s[i] = make_double2(0, 0);
-  __syncthreads();
   if (any_reorth) {
+    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hs[i] = make_double2(0, 0);   // h2
     block_dots_all_ff<RR>(V, vs, w, k, n0, n1, r, blk, nblk, reinterpret_cast<DAcc*>(ws), P2);
     grid.sync();
     for (int p = warp; p < (k + 1) * r; p += nw) {
@@ -1193,10 +1197,14 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
         acc.y += src[b].y;
       }
       acc = warp_sum(acc);
-      if (lane == 0) h2s[i * r + j] = acc;
+      if (lane == 0) hs[i * r + j] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) hf[i] = f4_split(h2s[i]);
+    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x) {
+      const Z z = hs[i];
+      if (blk == 0) gd.hcol[i] = make_double2(gd.hcol[i].x + z.x, gd.hcol[i].y + z.y);   // h + h2
+      hf[i] = f4_split(z);
+    }
     __syncthreads();
     ff_update_rows<RR>(V, vs, w, hf, k, r, n0 * r, n1 * r, need, nullptr);
     __syncthreads();
@@ -1216,11 +1224,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_step_ff(F4* __restrict__ V, int
       if (blk == 0) gd.hn2[j] = s2;
     }
   }
-  if (blk == 0) {
-    for (int i = threadIdx.x; i < (k + 1) * r; i += blockDim.x)
-      gd.hcol[i] = make_double2(hs[i].x + h2s[i].x, hs[i].y + h2s[i].y);
-    if (threadIdx.x == 0) *gd.k = k + 1;
-  }
+  if (blk == 0 && threadIdx.x == 0) *gd.k = k + 1;
   __syncthreads();
   // phase 5: V[k+1] = w / ||w|| (float-float), the next operator input its high parts
   F4* sclf = hf;   // per column: the scale split (hf is free again)
@@ -1376,9 +1380,10 @@ Status Solver::ensure(int64_t N, int r, int m) {
     }
     int64_t want = coop_ok_ ? (int64_t)sms * per : 128;
     nblk_ = (int)std::max<int64_t>(1, std::min<int64_t>(want, (N + 63) / 64));
-    // the float-float step: the same layout, the r flags padded to 16 bytes, then
-    // the split Hessenberg column ((m+1) r F4); r at most one column per thread
-    coop_smem_ff_ = coop_smem_ + sizeof(F4) * ((size_t)(r + 3) / 4 + 1) + sizeof(F4) * (size_t)(m + 1) * r;
+    // the float-float step: one (m+1) r Hessenberg column (split in place), the
+    // partial-sum space and the flags; r at most one column per thread
+    coop_smem_ff_ = sizeof(Z) * ((size_t)(m + 1) * r + std::max<size_t>((size_t)(m + 1) * 8, 4 * 256)) +
+                    sizeof(int) * (size_t)r + 16;
     ffa_ok_ = coop_ok_ && r <= 256 && coop_smem_ff_ <= (size_t)kCoopSmemMax;
     nblk_ff_ = nblk_;
     if (ffa_ok_) {
