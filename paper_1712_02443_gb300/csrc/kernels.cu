@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(256) k_grid_gather(int64_t ng, int B, const in
 // its entries (weight and basis index loaded together, four entries per step:
 // no dependent loads), folded by two shuffle levels; lane g of a node adds
 // component g into the grid.
-__global__ void __launch_bounds__(256) k_project_g1(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
+__global__ void __launch_bounds__(512) k_project_g1(const int32_t* __restrict__ elems, int Nh, int bx, int by, int bz,
                                                     const int32_t* __restrict__ inv_ptr,
                                                     const unsigned char* __restrict__ tab, int E,
                                                     const int64_t* __restrict__ off,
@@ -699,6 +699,7 @@ __global__ void __launch_bounds__(256) k_project_g1(const int32_t* __restrict__ 
                                                     int Nx, int Ny, int Nz, float2* __restrict__ grid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* us = reinterpret_cast<float2*>(smem_raw);
+  int* ip = reinterpret_cast<int*>(us + Nh);   // the box nodes' list starts (nodes + 1), staged with u
   const float4* tw = reinterpret_cast<const float4*>(tab);
   const uint16_t* tn = reinterpret_cast<const uint16_t*>(tab + 16 * (size_t)E);
   const int e = elems[blockIdx.x];
@@ -707,6 +708,7 @@ __global__ void __launch_bounds__(256) k_project_g1(const int32_t* __restrict__ 
   const int64_t gstride = (int64_t)Nx * Ny * Nz;
   const int64_t gbase = ((int64_t)boxorg[3 * e] * Ny + boxorg[3 * e + 1]) * Nz + boxorg[3 * e + 2];
   for (int n = threadIdx.x; n < Nh; n += blockDim.x) us[n] = u[o + n];
+  for (int n = threadIdx.x; n <= nodes; n += blockDim.x) ip[n] = __ldg(inv_ptr + n);
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   const int j = lane / 4, g = lane % 4;
@@ -720,8 +722,8 @@ __global__ void __launch_bounds__(256) k_project_g1(const int32_t* __restrict__ 
       ax3 = fmaf(w.w, uv.x, ax3); ay3 = fmaf(w.w, uv.y, ay3);
     };
     if (node < nodes) {
-      const int q1 = inv_ptr[node + 1];
-      int q = inv_ptr[node] + g;
+      const int q1 = ip[node + 1];
+      int q = ip[node] + g;
       for (; q + 12 < q1; q += 16) {
         const float4 w0 = __ldg(tw + q), w1 = __ldg(tw + q + 4), w2 = __ldg(tw + q + 8), w3 = __ldg(tw + q + 12);
         const int n0 = __ldg(tn + q), n1 = __ldg(tn + q + 4), n2 = __ldg(tn + q + 8), n3 = __ldg(tn + q + 12);
@@ -2263,7 +2265,8 @@ static void project_launch(int var, const DevArray& a, const DevPrec<R>& p, int 
     const int pnodes = bx * by * bz;
     if constexpr (sizeof(R) == 4) {
       if (var == 3 && nrhs == 1 && (size_t)t < p.prj_tab.size()) {
-        k_project_g1<<<(unsigned)a.n_of_type[t], 256, sizeof(float2) * Nh, cs>>>(
+        // 16 warps of 8 nodes per round; u and the list starts in shared memory
+        k_project_g1<<<(unsigned)a.n_of_type[t], 512, sizeof(float2) * Nh + sizeof(int) * (pnodes + 1), cs>>>(
             a.elems[t], Nh, bx, by, bz, a.inv_ptr[t], static_cast<const unsigned char*>(p.prj_tab[t]), a.inv_len[t],
             a.off, a.boxorg, reinterpret_cast<const float2*>(u), Nx, Ny, Nz, reinterpret_cast<float2*>(grid));
         ++nl;
